@@ -1,0 +1,563 @@
+"""Plain FP64 CPU oracle of the Difference Potentials Method hot path.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / reference legs of ``bench.py`` may import this module.  The
+product path (the CUDA library and its Python binding) never calls it, and this
+module shares no code with it.
+
+Every function restates one definition of Epshteyn & Xia, "Efficient Numerical
+Algorithms based on Difference Potentials for Chemotaxis Systems in 3D"
+(arXiv:1811.03557), in the paper's order and notation, using numpy in float64.
+No blocking, fusion or reordering beyond what the definition states: the
+auxiliary problem is the dense 3D DST-I written out with the explicit sine
+matrix (a library matmul per axis), the point sets are the literal set unions
+of Definition 2.1, and so on.
+
+Readings where the paper is silent or ambiguous (all listed in the design doc):
+  * grid: N interior nodes per axis of the cube [lo, hi]^3, x_j = lo + j*h,
+    j = 1..N, h = (hi - lo)/(N + 1); the Dirichlet ghost layer j = 0, N+1 is
+    the set N^0 \\ M^0.
+  * M^+ is the strict interior: F(x) < 1 with F the ellipsoid form evaluated
+    in a fixed order, so nodes exactly on Gamma belong to M^-.
+  * the AP operator is sigma - Lap_h; the paper's L_{h,dt} = I - dt Lap_h is
+    dt*(sigma - Lap_h) with sigma = 1/dt, so the PKS right-hand side is f/dt.
+  * basis: real orthonormal spherical harmonics without the Condon-Shortley
+    phase, theta from +z and phi = atan2(y, x) of the foot point relative to
+    the domain centre; column order nu = l^2 + l + m, then the (d^2/2) copies.
+  * a minmod slope whose stencil leaves N^+ is 0.
+  * after the extension the PKS densities are clamped at 0 (Theorem 2.4,
+    condition 3).
+
+Parity pins: every function here is checked by tests/test_oracle_*.py against
+closed forms, brute force, library routines or the paper's theorems.  The
+ellipsoid foot point is pinned by its optimality conditions and the sphere
+limit only ("parity unpinned" beyond Newton convergence).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# Label bits of a node (one uint8 per node of M^0).
+LBL_MPLUS = 1     # x in M^+            (Definition 2.1)
+LBL_GIN = 2       # x in gamma_in       (Definition 2.1)
+LBL_GEX = 4       # x in gamma_ex       (Definition 2.1)
+
+
+# ---------------------------------------------------------------------------
+# Grid (Section 2, "Introduction of the Auxiliary Domain"; reading: node grid)
+# ---------------------------------------------------------------------------
+def grid_spacing(N: int, lo: float, hi: float) -> float:
+    """h of the uniform mesh with N interior nodes per axis on [lo, hi]."""
+    return (hi - lo) / (N + 1)
+
+
+def node_coords(N: int, lo: float, hi: float) -> np.ndarray:
+    """x_j = lo + j*h for j = 1..N (float64, evaluated as lo + (j*h))."""
+    h = grid_spacing(N, lo, hi)
+    j = np.arange(1, N + 1, dtype=np.float64)
+    return lo + j * h
+
+
+def mesh(N, lo, hi):
+    x = node_coords(N, lo, hi)
+    return np.meshgrid(x, x, x, indexing="ij")
+
+
+# ---------------------------------------------------------------------------
+# Point sets (Definition 2.1)
+# ---------------------------------------------------------------------------
+def ellipsoid_form(geom, X, Y, Z):
+    """F = ((x-cx)/ax)^2 + ((y-cy)/ay)^2 + ((z-cz)/az)^2, summed as (Fx+Fy)+Fz."""
+    (cx, cy, cz), (ax, ay, az) = geom.center, geom.axes
+    tx = (X - cx) / ax
+    ty = (Y - cy) / ay
+    tz = (Z - cz) / az
+    return (tx * tx + ty * ty) + tz * tz
+
+
+def inside_mask(geom, N, lo, hi) -> np.ndarray:
+    """Membership of each node of M^0 in the open domain Omega (F < 1)."""
+    x = node_coords(N, lo, hi)
+    return ellipsoid_form(geom, x[:, None, None], x[None, :, None], x[None, None, :]) < 1.0
+
+
+def _stencil_union(S: np.ndarray) -> np.ndarray:
+    """Union of the 7-point stencils (eq. stencil:7-point) centred at the nodes of S."""
+    U = S.copy()
+    for ax in range(3):
+        U |= np.roll(S, 1, axis=ax) & _not_wrapped(S.shape, ax, +1)
+        U |= np.roll(S, -1, axis=ax) & _not_wrapped(S.shape, ax, -1)
+    return U
+
+
+def _not_wrapped(shape, ax, s):
+    m = np.ones(shape, dtype=bool)
+    idx = [slice(None)] * 3
+    idx[ax] = 0 if s > 0 else shape[ax] - 1
+    m[tuple(idx)] = False
+    return m
+
+
+def point_sets(inside: np.ndarray) -> dict:
+    """Definition 2.1 written out on the grid padded with the ghost layer N^0\\M^0.
+
+    Returns boolean arrays (shape N^3) for M^+, M^-, N^+, N^-, gamma,
+    gamma_in and gamma_ex (the ghost layer itself is cut off).
+    """
+    N = inside.shape[0]
+    M0 = np.zeros((N + 2,) * 3, dtype=bool)
+    M0[1:-1, 1:-1, 1:-1] = True
+    In = np.zeros_like(M0)
+    In[1:-1, 1:-1, 1:-1] = inside
+    Mp = M0 & In
+    Mm = M0 & ~In
+    Np = _stencil_union(Mp)
+    Nm = _stencil_union(Mm)
+    gamma = Np & Nm
+    gin = Mp & gamma
+    gex = Mm & gamma
+    core = (slice(1, -1),) * 3
+    return dict(Mp=Mp[core], Mm=Mm[core], Np=Np[core], Nm=Nm[core], gamma=gamma[core],
+                gin=gin[core], gex=gex[core])
+
+
+def labels_from_sets(sets) -> np.ndarray:
+    lab = np.zeros(sets["Mp"].shape, dtype=np.uint8)
+    lab[sets["Mp"]] |= LBL_MPLUS
+    lab[sets["gin"]] |= LBL_GIN
+    lab[sets["gex"]] |= LBL_GEX
+    return lab
+
+
+def classify(geom, N, lo, hi):
+    """Labels and the ascending linear-index lists of gamma_in and gamma_ex."""
+    sets = point_sets(inside_mask(geom, N, lo, hi))
+    lab = labels_from_sets(sets)
+    flat = lab.reshape(-1)
+    gin = np.flatnonzero(flat & LBL_GIN).astype(np.int64)
+    gex = np.flatnonzero(flat & LBL_GEX).astype(np.int64)
+    return lab, gin, gex
+
+
+def margin_ok(lab: np.ndarray, margin: int = 2) -> bool:
+    """True when no node of M^+ lies within ``margin`` nodes of a cube face."""
+    idx = np.argwhere(lab & LBL_MPLUS)
+    if idx.size == 0:
+        return False
+    N = lab.shape[0]
+    return bool(idx.min() >= margin and idx.max() <= N - 1 - margin)
+
+
+# ---------------------------------------------------------------------------
+# Orthogonal projection on Gamma, signed distance, normal (Definition 2.6)
+# ---------------------------------------------------------------------------
+def foot_point(geom, P: np.ndarray, tol: float = 1e-15, maxit: int = 200):
+    """Closest point x' on Gamma to each row of P, the signed distance d (> 0
+    outside Omega, along the outward normal) and the unit outward normal at x'.
+
+    Sphere: x' = c + r (p-c)/|p-c|, d = |p-c| - r.
+    Ellipsoid: x'_i = c_i + (p_i-c_i) a_i^2/(a_i^2 + mu), with mu the root in
+    (-min a_i^2, inf) of sum (p_i-c_i)^2 a_i^2/(a_i^2+mu)^2 = 1, found by plain
+    bisection (slow, monotone, no starting-guess logic).
+    """
+    P = np.asarray(P, dtype=np.float64)
+    c = np.asarray(geom.center, dtype=np.float64)
+    a = np.asarray(geom.axes, dtype=np.float64)
+    q = P - c
+    if geom.kind == 0:
+        r = a[0]
+        rho = np.linalg.norm(q, axis=1)
+        n = q / rho[:, None]
+        xf = c + r * n
+        return xf, rho - r, n
+    a2 = a * a
+
+    def F(mu):
+        return np.sum(q * q * a2 / (a2 + mu[:, None]) ** 2, axis=1) - 1.0
+
+    lo = np.full(len(P), -a2.min() * (1 - 1e-15))
+    hi = np.full(len(P), 1.0)
+    while np.any(F(hi) > 0):
+        hi = np.where(F(hi) > 0, 2 * hi + 1.0, hi)
+    # F is decreasing on (-min a^2, inf): bisection to full double precision.
+    for _ in range(maxit):
+        mid = 0.5 * (lo + hi)
+        pos = F(mid) > 0
+        lo = np.where(pos, mid, lo)
+        hi = np.where(pos, hi, mid)
+        if np.all(hi - lo <= tol * np.maximum(1.0, np.abs(mid))):
+            break
+    mu = 0.5 * (lo + hi)
+    xf = c + q * a2 / (a2 + mu[:, None])
+    g = (xf - c) / a2
+    n = g / np.linalg.norm(g, axis=1)[:, None]
+    outside = np.sum(q * q / a2, axis=1) > 1.0
+    d = np.linalg.norm(P - xf, axis=1) * np.where(outside, 1.0, -1.0)
+    return xf, d, n
+
+
+# ---------------------------------------------------------------------------
+# Spherical harmonics (eq. spectral_approximation_sd)
+# ---------------------------------------------------------------------------
+def assoc_legendre(K: int, x: np.ndarray) -> np.ndarray:
+    """P_l^m(x) for 0 <= m <= l <= K without the Condon-Shortley phase, by the
+    textbook three-term recurrence in l.  Returns shape (K+1, K+1, len(x))."""
+    x = np.asarray(x, dtype=np.float64)
+    P = np.zeros((K + 1, K + 1) + x.shape)
+    s = np.sqrt(np.maximum(0.0, 1.0 - x * x))
+    for m in range(K + 1):
+        # P_m^m = (2m-1)!! (1-x^2)^{m/2}
+        dfact = 1.0
+        for k in range(1, 2 * m, 2):
+            dfact *= k
+        P[m, m] = dfact * s ** m
+        if m + 1 <= K:
+            P[m + 1, m] = x * (2 * m + 1) * P[m, m]
+        for l in range(m + 2, K + 1):
+            P[l, m] = ((2 * l - 1) * x * P[l - 1, m] - (l + m - 1) * P[l - 2, m]) / (l - m)
+    return P
+
+
+def real_sph_harm(K: int, cos_theta: np.ndarray, phi: np.ndarray) -> np.ndarray:
+    """Real orthonormal spherical harmonics phi_nu, nu = l^2 + l + m, for
+    l <= K, -l <= m <= l.  Returns shape (n_points, (K+1)^2).
+
+    Y_l0 = N_l0 P_l^0, Y_lm = sqrt(2) N_lm P_l^m cos(m phi) (m > 0),
+    Y_l,-m = sqrt(2) N_lm P_l^m sin(m phi), N_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!).
+    """
+    P = assoc_legendre(K, cos_theta)
+    out = np.zeros((len(cos_theta), (K + 1) ** 2))
+    for l in range(K + 1):
+        for m in range(0, l + 1):
+            Nlm = math.sqrt((2 * l + 1) / (4 * math.pi) * math.factorial(l - m) / math.factorial(l + m))
+            if m == 0:
+                out[:, l * l + l] = Nlm * P[l, 0]
+            else:
+                out[:, l * l + l + m] = math.sqrt(2.0) * Nlm * P[l, m] * np.cos(m * phi)
+                out[:, l * l + l - m] = math.sqrt(2.0) * Nlm * P[l, m] * np.sin(m * phi)
+    return out
+
+
+def boundary_basis(geom, xf: np.ndarray, K: int) -> np.ndarray:
+    """phi_nu(theta, phi) at foot points xf (angles relative to the centre)."""
+    q = xf - np.asarray(geom.center)
+    rad = np.linalg.norm(q, axis=1)
+    cos_t = q[:, 2] / rad
+    ph = np.arctan2(q[:, 1], q[:, 0])
+    return real_sph_harm(K, cos_t, ph)
+
+
+# ---------------------------------------------------------------------------
+# The Auxiliary Problem (Definition 2.4): (sigma - Lap_h) v = q on M^0,
+# v = 0 on N^0 \ M^0, diagonalised by the 3D DST-I.
+# ---------------------------------------------------------------------------
+def dst1_matrix(N: int) -> np.ndarray:
+    """S[a, m] = sin(pi a m / (N+1)), a, m = 1..N."""
+    a = np.arange(1, N + 1, dtype=np.float64)
+    return np.sin(np.pi * np.outer(a, a) / (N + 1))
+
+
+def ap_eigenvalues(N: int, h: float, sigma: float) -> np.ndarray:
+    """lambda_abc = sigma + (4/h^2)(sin^2(pi a/2(N+1)) + sin^2(pi b/..) + sin^2(pi c/..))."""
+    a = np.arange(1, N + 1, dtype=np.float64)
+    s2 = np.sin(np.pi * a / (2 * (N + 1))) ** 2
+    return sigma + (4.0 / (h * h)) * (s2[:, None, None] + s2[None, :, None] + s2[None, None, :])
+
+
+def dst3(X: np.ndarray, S: np.ndarray) -> np.ndarray:
+    """Apply S along each of the three axes (one matmul per axis)."""
+    Y = np.einsum("ai,ijk->ajk", S, X, optimize=True)
+    Y = np.einsum("bj,ajk->abk", S, Y, optimize=True)
+    return np.einsum("ck,abk->abc", S, Y, optimize=True)
+
+
+def aux_solve(q: np.ndarray, h: float, sigma: float) -> np.ndarray:
+    """Solve the AP for one right-hand side q (N^3 array on M^0).
+
+    Forward DST-I on x, y, z; divide by lambda_abc; inverse DST-I (the same
+    sine matrix times 2/(N+1) per axis)."""
+    N = q.shape[0]
+    S = dst1_matrix(N)
+    qh = dst3(np.asarray(q, dtype=np.float64), S)
+    uh = qh / ap_eigenvalues(N, h, sigma)
+    return (2.0 / (N + 1)) ** 3 * dst3(uh, S)
+
+
+def apply_L(v: np.ndarray, h: float, sigma: float) -> np.ndarray:
+    """(sigma - Lap_h) v at every node of M^0 with v = 0 on the ghost layer
+    (the 7-point operator of eq. discrete_chemotaxis, shifted form)."""
+    vp = np.pad(np.asarray(v, dtype=np.float64), 1)
+    c = vp[1:-1, 1:-1, 1:-1]
+    nb = (vp[2:, 1:-1, 1:-1] + vp[:-2, 1:-1, 1:-1] + vp[1:-1, 2:, 1:-1] + vp[1:-1, :-2, 1:-1]
+          + vp[1:-1, 1:-1, 2:] + vp[1:-1, 1:-1, :-2])
+    return sigma * c - (nb - 6.0 * c) / (h * h)
+
+
+# ---------------------------------------------------------------------------
+# Particular solution, difference potential, trace (eqs. rhs:particular_solution,
+# rhs:difference_potentials; Definition 2.5; trace operators)
+# ---------------------------------------------------------------------------
+def particular_solution(f, sets, h, sigma):
+    """G f: AP with q = f on M^+, 0 on M^-; restricted to N^+ (zero elsewhere)."""
+    q = np.where(sets["Mp"], f, 0.0)
+    return np.where(sets["Np"], aux_solve(q, h, sigma), 0.0)
+
+
+def gamma_density_grid(v_gamma, gamma_idx, N):
+    """A density on gamma extended by zero to the whole grid."""
+    g = np.zeros(N ** 3)
+    g[gamma_idx] = v_gamma
+    return g.reshape(N, N, N)
+
+
+def difference_potential(vgrid, sets, h, sigma):
+    """P_{N+gamma} v_gamma: AP with q = 0 on M^+, L[v_gamma] on M^-; on N^+."""
+    q = np.where(sets["Mm"], apply_L(vgrid, h, sigma), 0.0)
+    return np.where(sets["Np"], aux_solve(q, h, sigma), 0.0)
+
+
+# ---------------------------------------------------------------------------
+# DPM setup: gamma geometry, basis, BEP matrix (eq. BEP_recast), QR
+# ---------------------------------------------------------------------------
+class DPMSetup:
+    """Everything of Steps 1-2 that depends only on (geometry, grid, K, beta, sigma)."""
+
+    def __init__(self, geom, N, lo, hi, K, beta, sigma, build_bep=True):
+        self.geom, self.N, self.lo, self.hi = geom, N, lo, hi
+        self.K, self.beta, self.sigma = K, beta, sigma
+        self.h = grid_spacing(N, lo, hi)
+        self.sets = point_sets(inside_mask(geom, N, lo, hi))
+        self.labels = labels_from_sets(self.sets)
+        flat_gamma = self.sets["gamma"].reshape(-1)
+        self.gamma_idx = np.flatnonzero(flat_gamma)                 # ascending
+        self.gin_idx = np.flatnonzero(self.sets["gin"].reshape(-1))
+        self.gex_idx = np.flatnonzero(self.sets["gex"].reshape(-1))
+        # positions of gamma_in inside the gamma list
+        self.gin_pos = np.searchsorted(self.gamma_idx, self.gin_idx)
+        X, Y, Z = mesh(N, lo, hi)
+        self.P = np.stack([X.reshape(-1)[self.gamma_idx], Y.reshape(-1)[self.gamma_idx],
+                           Z.reshape(-1)[self.gamma_idx]], axis=1)
+        self.xf, self.d, self.normal = foot_point(geom, self.P)
+        self.phi = boundary_basis(geom, self.xf, K)                    # |gamma| x (K+1)^2
+        self.nsh = (K + 1) ** 2
+        self.ncol = (beta + 1) * self.nsh
+        if build_bep:
+            self.A = self.bep_matrix()
+            self.Q, self.R = np.linalg.qr(self.A)
+
+    def basis_densities(self) -> np.ndarray:
+        """Columns psi_k on gamma: phi_nu, then beta * (d^2/2) phi_nu (eq. extension_operator_recast)."""
+        cols = [self.phi]
+        if self.beta:
+            cols.append(0.5 * self.d[:, None] ** 2 * self.phi)
+        return np.concatenate(cols, axis=1)
+
+    def i_minus_p_gin(self, v_gamma) -> np.ndarray:
+        """Tr_{gamma_in} (v_gamma - P_{N+gamma} v_gamma)."""
+        vg = gamma_density_grid(v_gamma, self.gamma_idx, self.N)
+        Pv = difference_potential(vg, self.sets, self.h, self.sigma)
+        return v_gamma[self.gin_pos] - Pv.reshape(-1)[self.gin_idx]
+
+    def bep_matrix(self) -> np.ndarray:
+        """|gamma_in| x ncol matrix of eq. BEP_recast, one AP per column (Step 2)."""
+        Psi = self.basis_densities()
+        return np.stack([self.i_minus_p_gin(Psi[:, k]) for k in range(self.ncol)], axis=1)
+
+    def lstsq(self, b) -> np.ndarray:
+        """C = R^{-1} Q^T b with the precomputed QR (Steps 2 and 5)."""
+        from scipy.linalg import solve_triangular
+        return solve_triangular(self.R, self.Q.T @ b)
+
+    def extend(self, C, neumann=None) -> np.ndarray:
+        """u_gamma = sum C0 phi + d g_N + beta (d^2/2) sum C2 phi (eq. extension_operator)."""
+        u = self.phi @ C[: self.nsh]
+        if self.beta:
+            u = u + 0.5 * self.d ** 2 * (self.phi @ C[self.nsh:])
+        if neumann is not None:
+            u = u + self.d * neumann
+        return u
+
+    def gamma_grid(self, v_gamma):
+        return gamma_density_grid(v_gamma, self.gamma_idx, self.N)
+
+
+def dpm_elliptic_solve(setup: DPMSetup, f, neumann=None):
+    """Solve (sigma - Lap) u = f in Omega with du/dn = neumann on Gamma.
+
+    Step 4a: particular solution; Step 5: BEP least squares + extension;
+    Steps 6-7: Green's formula u = P u_gamma + G f on N^+ (eq.
+    generalized_greens_formula).  Returns (u on N^+, C, u_gamma)."""
+    s = setup
+    G = particular_solution(f, s.sets, s.h, s.sigma)
+    b = G.reshape(-1)[s.gin_idx]
+    if neumann is not None:
+        b = b - s.i_minus_p_gin(s.d * neumann)
+    C = s.lstsq(b)
+    ug = s.extend(C, neumann)
+    u = G + difference_potential(s.gamma_grid(ug), s.sets, s.h, s.sigma)
+    return u, C, ug
+
+
+# ---------------------------------------------------------------------------
+# PKS discretisation (eqs. discrete_chemotaxis .. slope_limiter, cfl_condition)
+# ---------------------------------------------------------------------------
+def minmod(*xs):
+    """eq. slope_limiter: min if all > 0, max if all < 0, else 0."""
+    X = np.stack(np.broadcast_arrays(*xs))
+    allpos = np.all(X > 0, axis=0)
+    allneg = np.all(X < 0, axis=0)
+    return np.where(allpos, X.min(axis=0), np.where(allneg, X.max(axis=0), 0.0))
+
+
+def _shift(a, ax, s, fill=0.0):
+    """b[p] = a[p + s e_ax] (fill outside the grid)."""
+    out = np.full_like(a, fill)
+    src = [slice(None)] * 3
+    dst = [slice(None)] * 3
+    if s > 0:
+        src[ax] = slice(s, None)
+        dst[ax] = slice(None, -s)
+    else:
+        src[ax] = slice(None, s)
+        dst[ax] = slice(-s, None)
+    out[tuple(dst)] = a[tuple(src)]
+    return out
+
+
+def limited_slopes(rho, Np, h, ax):
+    """minmod slope of rho along axis ax at every node of N^+; 0 where one of
+    the two neighbours is not in N^+ (reading of the paper's silence)."""
+    rp, rm = _shift(rho, ax, 1), _shift(rho, ax, -1)
+    ok = Np & _shift(Np, ax, 1, False) & _shift(Np, ax, -1, False)
+    s = minmod(2.0 * (rp - rho) / h, (rp - rm) / (2.0 * h), 2.0 * (rho - rm) / h)
+    return np.where(ok, s, 0.0)
+
+
+def convective_term(rho, c, sets, h, chi):
+    """g of eq. discrete_convective_term on M^+ (0 elsewhere).
+
+    Face gradients by eq. c-central-difference; face densities upwinded by eq.
+    upwind_approximation from the piecewise-linear reconstruction with minmod
+    slopes (eq. truncated_taylor_expansion)."""
+    Np, Mp = sets["Np"], sets["Mp"]
+    g = np.zeros_like(rho)
+    for ax in range(3):
+        s = limited_slopes(rho, Np, h, ax)
+        rE = rho + 0.5 * h * s          # reconstruction at x_{j+1/2} - 0
+        rW = rho - 0.5 * h * s          # reconstruction at x_{j-1/2} + 0
+        gp = (_shift(c, ax, 1) - c) / h                 # grad c at j+1/2
+        gm = (c - _shift(c, ax, -1)) / h                # grad c at j-1/2
+        rho_p = np.where(gp > 0, rE, _shift(rW, ax, 1))
+        rho_m = np.where(gm > 0, _shift(rE, ax, -1), rW)
+        g += (chi * rho_p * gp - chi * rho_m * gm) / h
+    return np.where(Mp, g, 0.0)
+
+
+def max_face_gradients(c, sets, h):
+    """max over M^+ of |grad_h c| at the j+-1/2 faces, per axis (eq. cfl_condition)."""
+    Mp = sets["Mp"]
+    out = []
+    for ax in range(3):
+        gp = np.abs(_shift(c, ax, 1) - c) / h
+        gm = np.abs(c - _shift(c, ax, -1)) / h
+        out.append(float(np.max(np.where(Mp, np.maximum(gp, gm), 0.0))))
+    return out
+
+
+def cfl_dt(c, sets, h, chi):
+    """min over axes of h / (6 chi max|grad c|) (eq. cfl_condition)."""
+    m = max_face_gradients(c, sets, h)
+    return min(h / (6.0 * chi * g) if g > 0 else math.inf for g in m)
+
+
+def pks_rhs(rho, c, sets, h, chi, dt):
+    """f for both equations of eq. discrete_chemotaxis on M^+ (alpha = gamma_rho = gamma_c = 1)."""
+    g = convective_term(rho, c, sets, h, chi)
+    Mp = sets["Mp"]
+    f_rho = np.where(Mp, rho - dt * g, 0.0)
+    f_c = np.where(Mp, (1.0 - dt) * c + dt * rho, 0.0)
+    return f_rho, f_c
+
+
+def diagnostics(rho, c, sets, h, N, lo, hi):
+    """Mass h^3 sum rho, max rho (eq. sd-norm:max), min rho / min c on N^+,
+    second moment (eq. sd-norm:second-moment) and free energy (eq. sd-norm:free-energy)."""
+    Mp, Np = sets["Mp"], sets["Np"]
+    X, Y, Z = mesh(N, lo, hi)
+    h3 = h ** 3
+    r = np.where(Mp, rho, 0.0)
+    mass = h3 * np.sum(r)
+    m2 = h3 * np.sum(np.where(Mp, (X * X + Y * Y + Z * Z) * rho, 0.0))
+    rlogr = np.where(rho > 0, rho * np.log(np.where(rho > 0, rho, 1.0)), 0.0)
+    grad2 = np.zeros_like(c)
+    for ax in range(3):
+        grad2 += (_shift(c, ax, 1) - _shift(c, ax, -1)) ** 2
+    dens = rlogr - rho * c + 0.5 * c * c + grad2 / (8.0 * h * h)
+    F = h3 * np.sum(np.where(Mp, dens, 0.0))
+    return dict(mass=mass, max_rho=float(np.max(np.where(Mp, rho, -np.inf))),
+                min_rho=float(np.min(np.where(Np, rho, np.inf))),
+                min_c=float(np.min(np.where(Np, c, np.inf))), m2=m2, free_energy=F)
+
+
+class PKSState:
+    """Oracle of the time loop, Steps 3-7, for the PKS model on one domain."""
+
+    def __init__(self, geom, N, lo, hi, K, beta, chi, dt_max, rho0=None, c0=None,
+                 dt_mode="fixed", clamp=True, rho=None, c=None):
+        self.geom, self.N, self.lo, self.hi = geom, N, lo, hi
+        self.K, self.beta, self.chi, self.dt_max = K, beta, chi, dt_max
+        self.dt_mode, self.clamp = dt_mode, clamp
+        self.h = grid_spacing(N, lo, hi)
+        self.setup = None
+        self.dt = None
+        self.t = 0.0
+        base = DPMSetup(geom, N, lo, hi, K, beta, 1.0 / dt_max, build_bep=False)
+        self.sets = base.sets
+        self._geo = base
+        if rho is None:
+            rho, c = self.initial_state(rho0, c0)
+        self.rho = np.asarray(rho, dtype=np.float64)
+        self.c = np.asarray(c, dtype=np.float64)
+
+    def initial_state(self, rho0, c0):
+        """rho^0, c^0 at the nodes of M^+ and at the foot points of gamma_ex
+        (2-term extension with zero Neumann data, Remark 2.1)."""
+        X, Y, Z = mesh(self.N, self.lo, self.hi)
+        rho = np.where(self.sets["Mp"], rho0(X, Y, Z), 0.0)
+        c = np.where(self.sets["Mp"], c0(X, Y, Z), 0.0)
+        g = self._geo
+        ex = g.labels.reshape(-1)[g.gamma_idx] & LBL_GEX > 0
+        xf = g.xf[ex]
+        rho.reshape(-1)[g.gamma_idx[ex]] = rho0(xf[:, 0], xf[:, 1], xf[:, 2])
+        c.reshape(-1)[g.gamma_idx[ex]] = c0(xf[:, 0], xf[:, 1], xf[:, 2])
+        return rho, c
+
+    def choose_dt(self):
+        """Step 3: fixed mode uses dt_max; cfl mode dt = min(dt_prev, dt_cfl, dt_max)."""
+        if self.dt_mode == "fixed":
+            return self.dt_max
+        cand = min(self.dt_max, cfl_dt(self.c, self.sets, self.h, self.chi))
+        return cand if self.dt is None else min(self.dt, cand)
+
+    def step(self):
+        dt = self.choose_dt()
+        if self.setup is None or dt != self.dt:           # Step 2 / Step 4b
+            self.setup = DPMSetup(self.geom, self.N, self.lo, self.hi, self.K, self.beta, 1.0 / dt)
+        self.dt = dt
+        s = self.setup
+        f_rho, f_c = pks_rhs(self.rho, self.c, self.sets, self.h, self.chi, dt)   # Step 4a
+        out = []
+        for f in (f_rho, f_c):
+            q = f / dt                                   # L_{h,dt} = dt (sigma - Lap_h)
+            G = particular_solution(q, s.sets, s.h, s.sigma)
+            C = s.lstsq(G.reshape(-1)[s.gin_idx])        # Step 5
+            ug = s.extend(C)
+            if self.clamp:
+                ug = np.maximum(ug, 0.0)
+            u = G + difference_potential(s.gamma_grid(ug), s.sets, s.h, s.sigma)   # Steps 6-7
+            out.append(u)
+        self.rho, self.c = out
+        self.t += dt
+        return dt

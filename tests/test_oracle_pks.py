@@ -1,0 +1,168 @@
+"""Pins of the oracle's PKS discretisation (eqs. discrete_chemotaxis ..
+slope_limiter, the flux split of the positivity proof, eq. cfl_condition)."""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import dpm_oracle as O
+from paper_1811_03557_gb300.workloads import (Geometry, Gaussian, TEST_A_C0, TEST_A_RHO0,
+                                              random_field)
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_minmod_golden_cases():
+    rows = np.loadtxt(os.path.join(GOLD, "minmod_cases.txt"))
+    got = O.minmod(rows[:, 0], rows[:, 1], rows[:, 2])
+    assert np.array_equal(got, rows[:, 3])
+
+
+def test_paper_parameters_match_workloads():
+    p = json.load(open(os.path.join(GOLD, "paper_parameters.json")))
+    assert TEST_A_RHO0.amp == p["test_A"]["rho0"]["amp"] and TEST_A_RHO0.alpha == p["test_A"]["rho0"]["alpha"]
+    assert TEST_A_C0.amp == p["test_A"]["c0"]["amp"] and TEST_A_C0.alpha == p["test_A"]["c0"]["alpha"]
+
+
+def _setup(N=20, lo=-1.3, hi=1.3):
+    g = Geometry.sphere(1.0)
+    return g, O.point_sets(O.inside_mask(g, N, lo, hi)), O.grid_spacing(N, lo, hi), O.mesh(N, lo, hi)
+
+
+@pytest.mark.parametrize("ax", [0, 1, 2])
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_linear_fields_give_closed_form_flux(ax, sign):
+    """rho = a + b x_ax, c = s*k x_ax: exact slopes, g = chi * (s k) * b away from gamma."""
+    g, sets, h, XYZ = _setup()
+    x = XYZ[ax]
+    a, b, k, chi = 5.0, 1.5, 2.0, 0.7
+    rho = np.where(sets["Np"], a + b * x, 0.0)
+    c = np.where(sets["Np"], sign * k * x, 0.0)
+    gterm = O.convective_term(rho, c, sets, h, chi)
+    # nodes whose x_ax-neighbours j-1, j, j+1 are all in M^+ have exact slopes on both faces
+    deep = sets["Mp"].copy()
+    for s in (1, -1, 2, -2):
+        deep &= O._shift(sets["Mp"], ax, s, False)
+    assert deep.sum() > 50
+    assert np.allclose(gterm[deep], chi * sign * k * b, rtol=1e-12, atol=1e-9)
+
+
+def _face_split(rho, c, sets, h, chi, dt):
+    """f_rho = F^E+F^W+F^N+F^S+F^U+F^D node by node (positivity proof, flux split)."""
+    N = rho.shape[0]
+    Np = sets["Np"]
+
+    def slope(p, ax):
+        e = np.eye(3, dtype=int)[ax]
+        pp, pm = tuple(np.add(p, e)), tuple(np.subtract(p, e))
+        if not (Np[p] and Np[pp] and Np[pm]):
+            return 0.0
+        return float(O.minmod(np.array(2 * (rho[pp] - rho[p]) / h), np.array((rho[pp] - rho[pm]) / (2 * h)),
+                              np.array(2 * (rho[p] - rho[pm]) / h)))
+
+    f = np.zeros_like(rho)
+    for p in itertools.product(range(2, N - 2), repeat=3):
+        if not sets["Mp"][p]:
+            continue
+        tot = 0.0
+        for ax in range(3):
+            e = np.eye(3, dtype=int)[ax]
+            pp, pm = tuple(np.add(p, e)), tuple(np.subtract(p, e))
+            sE = slope(p, ax)
+            rE, rW = rho[p] + h / 2 * sE, rho[p] - h / 2 * sE
+            gcp, gcm = (c[pp] - c[p]) / h, (c[p] - c[pm]) / h
+            face_p = rE if gcp > 0 else rho[pp] - h / 2 * slope(pp, ax)
+            face_m = (rho[pm] + h / 2 * slope(pm, ax)) if gcm > 0 else rW
+            FE = rE / 6 - dt * chi * gcp / h * face_p
+            FW = rW / 6 + dt * chi * gcm / h * face_m
+            tot += FE + FW
+        f[p] = tot
+    return f
+
+
+def test_flux_split_identity():
+    g, sets, h, _ = _setup(N=14, lo=-1.45, hi=1.45)
+    rho = np.where(sets["Np"], random_field(20, sets["Np"].shape, 0.0, 3.0), 0.0)
+    c = np.where(sets["Np"], random_field(21, sets["Np"].shape, 0.0, 2.0), 0.0)
+    dt, chi = 0.003, 1.0
+    f_rho, _ = O.pks_rhs(rho, c, sets, h, chi, dt)
+    f_split = _face_split(rho, c, sets, h, chi, dt)
+    assert np.allclose(f_rho, f_split, atol=1e-12)
+
+
+def test_cfl_dt_gives_nonnegative_rhs():
+    g, sets, h, _ = _setup(N=18)
+    for seed in range(4):
+        rho = np.where(sets["Np"], random_field(30 + seed, sets["Np"].shape, 0.0, 5.0), 0.0)
+        c = np.where(sets["Np"], random_field(40 + seed, sets["Np"].shape, 0.0, 50.0), 0.0)
+        dt = O.cfl_dt(c, sets, h, 1.0)
+        f_rho, f_c = O.pks_rhs(rho, c, sets, h, 1.0, dt)
+        assert f_rho[sets["Mp"]].min() >= -1e-12 * rho.max()
+        assert f_c[sets["Mp"]].min() >= 0.0
+        # 2x the CFL step is allowed to go negative for some seeds; 1x never
+        assert dt > 0
+
+
+def test_interior_fluxes_telescope():
+    """Sum over M^+ of h^3 g = boundary fluxes; with c flat near gamma it is 0."""
+    g, sets, h, (X, Y, Z) = _setup(N=22)
+    r = np.sqrt(X * X + Y * Y + Z * Z)
+    c = np.where(sets["Np"], np.maximum(0.0, 0.5 - r) ** 2, 0.0)
+    rho = np.where(sets["Np"], 1.0 + random_field(50, X.shape, 0, 1), 0.0)
+    gterm = O.convective_term(rho, c, sets, h, 1.0)
+    assert abs(gterm[sets["Mp"]].sum()) < 1e-10 * np.abs(gterm).sum()
+
+
+def test_diagnostics_closed_forms():
+    g, sets, h, (X, Y, Z) = _setup(N=16)
+    N = 16
+    rho = np.where(sets["Np"], 2.0, 0.0)
+    c = np.where(sets["Np"], 0.0, 0.0)
+    d = O.diagnostics(rho, c, sets, h, N, -1.3, 1.3)
+    nMp = sets["Mp"].sum()
+    assert d["mass"] == pytest.approx(2.0 * nMp * h ** 3)
+    assert d["max_rho"] == 2.0
+    # free energy of a constant density with c = 0: rho log rho per cell
+    assert d["free_energy"] == pytest.approx(nMp * h ** 3 * 2.0 * np.log(2.0))
+    assert d["m2"] == pytest.approx(h ** 3 * 2.0 * np.sum((X * X + Y * Y + Z * Z)[sets["Mp"]]))
+
+
+@pytest.fixture(scope="module")
+def pks_run():
+    st = O.PKSState(Geometry.sphere(1.0), 24, -1.25, 1.25, K=4, beta=1, chi=1.0, dt_max=1e-3,
+                    rho0=TEST_A_RHO0, c0=TEST_A_C0, dt_mode="cfl")
+    hist = [O.diagnostics(st.rho, st.c, st.sets, st.h, st.N, st.lo, st.hi)]
+    for _ in range(4):
+        st.step()
+        hist.append(O.diagnostics(st.rho, st.c, st.sets, st.h, st.N, st.lo, st.hi))
+    return st, hist
+
+
+def test_pks_positivity_under_cfl(pks_run):
+    st, hist = pks_run
+    assert all(hd["min_rho"] >= -1e-9 * hd["max_rho"] for hd in hist)
+    assert all(hd["min_c"] >= -1e-9 for hd in hist)
+
+
+def test_pks_free_energy_decreases(pks_run):
+    st, hist = pks_run
+    F = [hd["free_energy"] for hd in hist]
+    assert all(b <= a + 1e-9 * abs(a) for a, b in zip(F, F[1:])), F
+
+
+def test_pks_mass_approximately_conserved(pks_run):
+    st, hist = pks_run
+    m = [hd["mass"] for hd in hist]
+    assert max(abs(x - m[0]) for x in m) / m[0] < 0.05
+
+
+def test_pks_solution_keeps_cube_symmetry(pks_run):
+    st, _ = pks_run
+    for arr in (st.rho, st.c):
+        scale = np.abs(arr).max()
+        for perm in [(1, 0, 2), (2, 1, 0)]:
+            assert np.allclose(arr, arr.transpose(perm), atol=1e-9 * scale)
+        for ax in range(3):
+            assert np.allclose(arr, np.flip(arr, axis=ax), atol=1e-9 * scale)
