@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Benchmark of the DPM hot path on GB300.
+
+Workload (default): the N=128 PKS workload -- unit sphere in [-1.25, 1.25]^3,
+N = 128 interior nodes per axis, spherical harmonics to K = 8 (beta = 1, 162
+BEP columns), dt = h^2/4, off-centre Gaussian data (1200 e^{-120|x-x0|^2},
+600 e^{-60|x-x0|^2}, x0 = (0.3, 0, 0)).  One bench step is one PKS time step
+of the main algorithm with the BEP rebuilt (Steps 3, 4a, 4b, 5, 6, 7): the
+flux, 162 BEP-column APs + 2 particular APs in one batch, the FP64 QR, the
+least squares, the extensions, 2 Green's-formula APs and the diagnostics.
+
+metric: aux-solve grid-points/s = (APs per step) * N^3 / (seconds per step).
+
+--impl reference times the CPU oracle (the only implementation the paper
+gives is a description; the oracle restates it) on a bounded sample of the
+same step's AP solves.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1811_03557_gb300.workloads import WORKLOADS  # noqa: E402
+
+METRIC = "aux-solve grid-pts/s"
+UNIT = "grid-pts/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="pks_sphere_N128_K8")
+    ap.add_argument("--precision", choices=["fp32", "tc32", "fp64"], default="fp32")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="bound on the oracle's CPU-baseline sample")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl)
+                          if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+def oracle_sample(w, seconds, log=None):
+    """Time the oracle's BEP-column AP solves (difference potential of a basis
+    density, traced on gamma_in) of the workload for about `seconds`."""
+    from oracle import dpm_oracle as O
+    s = O.DPMSetup(w.geom, w.N, w.lo, w.hi, w.K, w.beta, 1.0 / w.dt, build_bep=False)
+    Psi = s.basis_densities()
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        s.i_minus_p_gin(Psi[:, n % Psi.shape[1]])
+        n += 1
+        el = time.perf_counter() - t0
+        if (el >= seconds and n >= 2) or n >= Psi.shape[1]:
+            break
+    return n, el
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            return int(max(i.get("num_threads", 1) for i in info))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def solves_per_step(w):
+    return w.ncol + 4
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = WORKLOADS[args.workload]
+    per = []
+    sample_s = max(1.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for i in range(args.warmup + args.steps):
+        n, el = oracle_sample(w, sample_s)
+        if i >= args.warmup:
+            per.append((n, el))
+    tot_n = sum(n for n, _ in per)
+    tot_t = sum(t for _, t in per)
+    value = tot_n * w.N ** 3 / tot_t
+    ms_per_step = tot_t / len(per) * 1e3
+    cores = blas_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "N": w.N, "K": w.K, "ncol": w.ncol,
+                   "step": f"bounded sample of the step's AP solves (~{sample_s:.0f} s of oracle work)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{tot_n} BEP-column AP solves at N={w.N} over {len(per)} steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    from paper_1811_03557_gb300 import abi
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w = WORKLOADS[args.workload]
+    prec = {"fp32": abi.DPM_PREC_FP32, "tc32": abi.DPM_PREC_TC32, "fp64": abi.DPM_PREC_FP64}[args.precision]
+    tdt = torch.float64 if prec == abi.DPM_PREC_FP64 else torch.float32
+    ctx = abi.dpm_ctx_create(local)
+    # replicas: every rank advances its own independent copy of the workload.
+    # dt = min(dt_prev, CFL bound, h^2/4) (Step 3; h^2/4 alone violates the CFL
+    # bound of this data), and the BEP is rebuilt on every step (Step 4b).
+    params = abi.pks_params(w.geom, w.N, w.lo, w.hi, 1.0, w.dt, w.K, w.beta, prec,
+                            dt_mode=1, rebuild=1, clamp=1)
+    stream = torch.cuda.current_stream()
+    pks = abi.dpm_pks_create(ctx, params, w.rho0, w.c0, stream=stream)
+    N = w.N
+    for _ in range(args.warmup):
+        abi.dpm_pks_step(pks, 1, want_stats=False, stream=stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    abi.dpm_profile_reset()
+    abi.dpm_profile_enable(True)
+    l0 = abi.dpm_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        abi.dpm_pks_step(pks, 1, want_stats=False, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    abi.dpm_profile_enable(False)
+    launches = abi.dpm_launch_count() - l0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    spp = solves_per_step(w)
+    value = world * spp * N ** 3 / (ms_max / 1e3)
+
+    # per-kernel device time recorded by the library on the launching stream
+    kinds = ["pass_k_fwd", "pass_j", "pass_i", "pass_k_inv", "lsq_householder_qr", "tc_"]
+    prof = {}
+    for k in kinds:
+        tot, n = abi.dpm_profile_read(k)
+        if n:
+            prof[k] = {"ms_total": tot, "launches": n, "ms_per_launch": tot / n}
+    abi.dpm_profile_reset()
+
+    st = abi.dpm_pks_step(pks, 1, want_stats=True, stream=stream)   # sanity after timing
+    finite = bool(np.isfinite(st.mass) and st.min_rho >= -1e-6 * st.max_rho)
+
+    roof = roofline(w, prec, prof, spp)
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(abi, torch, pks, w, tdt, spp, args, stream)
+
+    cpu = None
+    if rank == 0:
+        n, el = oracle_sample(w, args.cpu_seconds)
+        cpu = {"value": n * N ** 3 / el, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+               "sample": f"{n} BEP-column AP solves at N={N} (numpy FP64 dense DST-I), {el:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "tc32": "f32 (3xTF32 tensor)", "fp64": "f64"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": w.name, "N": N, "K": w.K, "ncol": w.ncol, "solves_per_step": spp,
+                       "step": "PKS step with BEP rebuild (Steps 3-7 incl. 4b), CFL dt <= h^2/4",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": f"inputs larger than L2 ({spp * N ** 3 * 4 / 1e9:.2f} GB batch per step)"},
+            "clocks": clk, "gpu_launches": int(launches), "roofline": roof, "kernels": prof,
+            "e2e": e2e, "cpu_baseline": cpu, "sanity": {"finite": bool(finite), "mass": st.mass},
+        }
+        print(json.dumps(line), flush=True)
+    abi.dpm_pks_destroy(pks)
+    abi.dpm_ctx_destroy(ctx)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def roofline(w, prec, prof, spp):
+    """Roofline of the dominant AP-pass kernel (largest device time)."""
+    peaks, src = measured_peaks()
+    passes = {k: v for k, v in prof.items() if k.startswith("pass") or k.startswith("tc_")}
+    if not passes:
+        return None
+    name, rec = max(passes.items(), key=lambda kv: kv[1]["ms_total"])
+    N = w.N
+    # right-hand sides per launch: every step runs one batch of (ncol + 2) and one of 2
+    batches = [(w.ncol + 2), 2]
+    rhs_per_launch = sum(batches) / len(batches)
+    points = rhs_per_launch * N ** 3
+    if prec in (0, 1):  # SIMT: fused-multiply-add bound
+        H = N // 2
+        passes_per_kind = {"pass_i": 2, "pass_j": 1, "pass_k_fwd": 1, "pass_k_inv": 1}
+        nt = passes_per_kind.get(name, 1)
+        flops = points * nt * (2.0 * H + 1.0)          # folded transform: N/2 FMAs + 1 add per point
+        ach = flops / (rec["ms_per_launch"] / 1e3) / 1e12
+        sm_max = peaks.get("sm_max_mhz", 2070.0)
+        lanes = 128 if prec == 0 else 2                  # FP32 lanes / FP64 units per SM
+        peak = 152 * lanes * 2 * sm_max * 1e6 / 1e12
+        return {"bound": "alu", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_source": f"152 SMs x {lanes} lanes x 2 flop x {sm_max:.0f} MHz (derived)"}
+    bytes_per = points * 8.0                              # read + write one FP32 cube per point
+    ach = bytes_per / (rec["ms_per_launch"] / 1e3) / 1e9
+    peak = peaks.get("hbm_gbs", 6800.0)
+    return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak, "traffic": None, "peak_source": f"hbm_gbs ({src})"}
+
+
+def run_e2e(abi, torch, pks, w, tdt, spp, args, stream):
+    """Same metric through the public API with host buffers: each step copies
+    the state (rho, c) host->device, steps, and copies it device->host."""
+    N = w.N
+    rho_h = torch.empty((N, N, N), dtype=tdt).pin_memory()
+    c_h = torch.empty_like(rho_h).pin_memory()
+    rho_d = torch.empty((N, N, N), dtype=tdt, device="cuda")
+    c_d = torch.empty_like(rho_d)
+    abi.dpm_pks_get_state(pks, rho_d, c_d, stream=stream)
+    rho_h.copy_(rho_d)
+    c_h.copy_(c_d)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    K = max(1, min(args.steps, 5))
+    e0.record(stream)
+    for _ in range(K):
+        rho_d.copy_(rho_h, non_blocking=True)
+        c_d.copy_(c_h, non_blocking=True)
+        abi.dpm_pks_set_state(pks, rho_d, c_d, stream=stream)
+        abi.dpm_pks_step(pks, 1, want_stats=False, stream=stream)
+        abi.dpm_pks_get_state(pks, rho_d, c_d, stream=stream)
+        rho_h.copy_(rho_d, non_blocking=True)
+        c_h.copy_(c_d, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    nb = 2 * N ** 3 * rho_h.element_size()
+    return {"value": spp * N ** 3 / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": nb,
+            "d2h_bytes_per_step": nb, "ms_per_step": ms}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

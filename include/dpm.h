@@ -1,0 +1,243 @@
+/*
+ * dpm.h -- C ABI of the GB300 (sm_103a) Difference Potentials Method library.
+ *
+ * The library implements the data-parallel hot path of the Difference
+ * Potentials Method (DPM) for the 3D Patlak-Keller-Segel (PKS) chemotaxis
+ * system of Epshteyn & Xia, "Efficient Numerical Algorithms based on
+ * Difference Potentials for Chemotaxis Systems in 3D" (arXiv:1811.03557).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every function returns int: DPM_OK (0) or a negative DPM_E* code.  On an
+ *    error dpm_last_error() returns a message (thread-local, valid until the
+ *    next call on the same thread).  No C++ exception crosses this boundary.
+ *  - Grid: the auxiliary domain is the cube [lo, hi]^3 with N interior nodes
+ *    per axis, x_j = lo + j*h, j = 1..N, h = (hi - lo)/(N + 1).  The nodes
+ *    j = 0 and j = N+1 are the Dirichlet layer N^0 \ M^0 of the auxiliary
+ *    problem and are never stored.
+ *  - Arrays over the grid are C-ordered u[i][j][k] (i = x, j = y, k = z, k
+ *    contiguous), linear index (i*N + j)*N + k, N^3 elements.
+ *  - "device" pointers are CUDA device memory (or managed memory) owned by
+ *    the caller; "host" pointers are ordinary host memory.  Handles
+ *    (dpm_ctx, dpm_bep, dpm_pks) own their internal device workspaces and free
+ *    them in the matching destroy call.
+ *  - All device work is enqueued on the caller's stream; a call returns once
+ *    the work is enqueued unless its comment says it synchronises (calls that
+ *    return counts or statistics to host memory synchronise the stream).
+ *  - A handle may be used by one host thread at a time.  Work on one handle
+ *    issued to two streams without ordering between them races.
+ */
+#ifndef DPM_H_
+#define DPM_H_
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define DPM_OK            0
+#define DPM_EINVAL       -1   /* invalid argument, size or geometry          */
+#define DPM_ENOMEM       -2   /* device allocation failed                     */
+#define DPM_ETIMEOUT     -3   /* a bounded device wait gave up                */
+#define DPM_ENUMERIC     -4   /* non-finite value or singular factorisation  */
+#define DPM_EUNSUPPORTED -5   /* valid request this build cannot serve       */
+#define DPM_ECUDA        -6   /* a CUDA runtime call failed                   */
+
+/* ---- arithmetic of the auxiliary-problem (AP) solve -------------------- */
+#define DPM_PREC_FP32 0  /* FP32 SIMT folded DST-I, FP32 storage            */
+#define DPM_PREC_FP64 1  /* FP64 SIMT DST-I, FP64 storage (comparator path) */
+#define DPM_PREC_TC32 2  /* tcgen05 3xTF32 DST-I contractions, FP32 storage  */
+
+/* ---- node label bits (one uint8 per node of M^0, Definition 2.1) ------- */
+#define DPM_LBL_MPLUS 1  /* node of M^+ (strict interior of Omega)           */
+#define DPM_LBL_GIN   2  /* node of gamma_in  = M^+ intersect gamma          */
+#define DPM_LBL_GEX   4  /* node of gamma_ex  = M^- intersect gamma          */
+#define DPM_LBL_SHELL 8  /* node of M^- where L[v_gamma] of a density on
+                            gamma can be nonzero (gamma_ex and M^- neighbours
+                            of gamma): the support of the right-hand side of
+                            a difference potential, eq. rhs:difference_potentials */
+
+typedef struct dpm_ctx dpm_ctx;
+typedef struct dpm_bep dpm_bep;
+typedef struct dpm_pks dpm_pks;
+
+/* Domain Omega.  kind 0: sphere |x - center| < axes[0] (axes[1], axes[2]
+ * ignored); kind 1: ellipsoid sum ((x_i - center_i)/axes_i)^2 < 1.
+ * Membership is decided in IEEE double with the fixed order
+ * ((tx*tx + ty*ty) + tz*tz) < 1, t_i = (x_i - c_i)/a_i, so that the integer
+ * point sets are reproducible bit for bit. */
+typedef struct {
+    int kind;
+    double center[3];
+    double axes[3];
+} dpm_geom;
+
+/* amp * exp(-alpha * ((x-x0)^2 + (y-y0)^2 + zscale*(z-z0)^2)): the form of the
+ * paper's initial conditions (Section 4, Tests (A) and (B); Remark 2.3 (i)). */
+typedef struct {
+    double amp, alpha;
+    double center[3];
+    double zscale;
+} dpm_gaussian;
+
+typedef struct {
+    int N;
+    double lo, hi, h, sigma;
+    int K, beta, ncol, precision;
+    int64_t n_mplus, n_gin, n_gex, n_gamma, n_shell;
+} dpm_bep_info;
+
+typedef struct {
+    dpm_geom geom;
+    int N;
+    double lo, hi;
+    double chi;       /* chemotactic sensitivity (alpha = gamma_rho = gamma_c = 1) */
+    double dt_max;    /* time step, or its upper bound in CFL mode              */
+    int K, beta;      /* spherical-harmonic degree, extension terms - 2          */
+    int precision;    /* DPM_PREC_*                                             */
+    int dt_mode;      /* 0: dt = dt_max every step; 1: dt = min(dt_prev,
+                         h/(6 chi max|grad_h c|), dt_max) (Step 3)              */
+    int rebuild;      /* 0: rebuild the BEP only when dt decreases (Step 4b);
+                         1: rebuild it on every step                           */
+    int clamp;        /* 1: u_gamma <- max(u_gamma, 0) after the extension
+                         (Theorem 2.4, condition 3)                             */
+} dpm_pks_params;
+
+typedef struct {
+    double t, dt;
+    int64_t step;
+    int rebuilt;            /* the BEP was (re)assembled in this step         */
+    double mass;            /* h^3 sum_{M+} rho                                */
+    double max_rho;         /* eq. sd-norm:max                                 */
+    double min_rho, min_c;  /* minima over N^+                                 */
+    double m2;              /* second moment, eq. sd-norm:second-moment         */
+    double free_energy;     /* eq. sd-norm:free-energy                          */
+} dpm_pks_stats;
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *dpm_last_error(void);
+
+/* Create a context on CUDA device `device` (made current on the calling
+ * thread).  The context holds scratch space shared by calls made through it. */
+int dpm_ctx_create(int device, dpm_ctx **out);
+int dpm_ctx_destroy(dpm_ctx *ctx);
+
+/*
+ * Node classification, Definition 2.1 (point sets M^+, M^-, N^+, N^-,
+ * gamma = N^+ ^ N^-, gamma_in = M^+ ^ gamma, gamma_ex = M^- ^ gamma).
+ *   labels   device uint8[N^3]: DPM_LBL_* bits per node (may be NULL).
+ *   gin_idx  device int32[gin_cap]: ascending linear indices of gamma_in (may
+ *            be NULL: count only).  gex_idx likewise for gamma_ex.
+ *   n_gin, n_gex  host int64 out: the set sizes (this call synchronises).
+ * Errors: DPM_EINVAL if N < 6, lo >= hi, a non-positive axis, Omega has no
+ * node, a node of M^+ lies within 2 nodes of a cube face (then N^+ or the
+ * potential's right-hand side would reach the Dirichlet layer), or a
+ * capacity is smaller than the set.  Integer outputs are bit-exact with the
+ * CPU oracle's.
+ */
+int dpm_classify(dpm_ctx *ctx, const dpm_geom *geom, int N, double lo, double hi,
+                 uint8_t *labels, int32_t *gin_idx, int64_t gin_cap,
+                 int32_t *gex_idx, int64_t gex_cap, int64_t *n_gin, int64_t *n_gex,
+                 cudaStream_t stream);
+
+/*
+ * Batched Auxiliary Problem solve, Definition 2.4 with the shifted operator:
+ *   (sigma - Lap_h) u_b = q_b on M^0,  u_b = 0 on N^0 \ M^0,   b = 0..B-1,
+ * Lap_h the 7-point Laplacian (eq. stencil:7-point), diagonalised by the 3D
+ * DST-I with eigenvalues sigma + (4/h^2) sum_axes sin^2(pi a/(2(N+1))).
+ * (The paper's L_{h,dt} = I - dt Lap_h equals dt (sigma - Lap_h), sigma = 1/dt.)
+ *   q, u  device arrays [B][N][N][N]: float for DPM_PREC_FP32/TC32, double for
+ *         DPM_PREC_FP64.  u may equal q (in place); otherwise they must not
+ *         overlap.
+ * Requires 2 <= N <= 256, h > 0, sigma >= 0, B >= 1.  DPM_PREC_TC32 requires
+ * N to be a multiple of 32 (DPM_EUNSUPPORTED otherwise).  Scratch: the
+ * context's workspace, grown on demand.
+ */
+int dpm_aux_solve_batched(dpm_ctx *ctx, int N, double h, double sigma, int B,
+                          const void *q, void *u, int precision, cudaStream_t stream);
+
+/*
+ * Steps 1-2 of the main algorithm: classify the grid, project every node of
+ * gamma on Gamma (foot point, signed distance d > 0 outside Omega along the
+ * outward normal; Definition 2.6), evaluate the real orthonormal spherical
+ * harmonics phi_nu, nu = l^2+l+m < (K+1)^2, at the foot point's polar and
+ * azimuthal angles about the centre (eq. spectral_approximation_sd), assemble
+ * the |gamma_in| x ncol BEP matrix of eq. BEP_recast,
+ *   A[:, k] = Tr_{gamma_in} (I - P_{N+gamma}) psi_k,
+ *   psi_k = phi_k (k < (K+1)^2),  psi_k = (d^2/2) phi_{k-(K+1)^2} (beta = 1),
+ * ncol = (beta+1)(K+1)^2, with one AP per column solved in one batch, and
+ * factor it by Householder QR in FP64 (kept resident with R^{-1} Q^T).
+ * K in [0, 16], beta in {0, 1}; sigma > 0.  Synchronises the stream.
+ */
+int dpm_bep_build(dpm_ctx *ctx, const dpm_geom *geom, int N, double lo, double hi,
+                  double sigma, int K, int beta, int precision, dpm_bep **out,
+                  cudaStream_t stream);
+int dpm_bep_get_info(const dpm_bep *bep, dpm_bep_info *info);
+/* Copy the BEP matrix to device double[n_gin * ncol], column-major. */
+int dpm_bep_matrix(const dpm_bep *bep, double *A, cudaStream_t stream);
+/* Copy the gamma geometry: ascending linear indices (int32[n_gamma]), foot
+ * points and unit outward normals (double[n_gamma][3]) and signed distances
+ * (double[n_gamma]).  Any pointer may be NULL.  All device pointers. */
+int dpm_bep_gamma_geometry(const dpm_bep *bep, int32_t *gamma_idx, double *foot,
+                           double *normal, double *dist, cudaStream_t stream);
+int dpm_bep_destroy(dpm_bep *bep);
+
+/*
+ * Elliptic DPM solve of (sigma - Lap) u = f in Omega, du/dn = g_N on Gamma:
+ * particular solution G f (eq. rhs:particular_solution), least squares of
+ * the BEP for the spectral coefficients (Step 5, using the resident QR),
+ * extension u_gamma = sum C0 phi + d g_N + beta (d^2/2) sum C2 phi
+ * (eq. extension_operator), and the discrete generalised Green's formula
+ * u = P_{N+gamma} u_gamma + G f on N^+ (eq. generalized_greens_formula).
+ *   f        device [N^3] (float, or double for DPM_PREC_FP64), used on M^+.
+ *   neumann  device double[n_gamma] g_N at the foot point of each node of
+ *            gamma (ascending order), or NULL for zero Neumann data.
+ *   u        device [N^3] out: the solution on N^+, 0 elsewhere.
+ *   coeffs   device double[ncol] out (C0 then C2), or NULL.
+ */
+int dpm_solve(dpm_bep *bep, const void *f, const double *neumann, void *u,
+              double *coeffs, cudaStream_t stream);
+
+/*
+ * PKS time stepping (Steps 3-7 of the main algorithm) on one domain.
+ * create: builds the point sets and gamma geometry and sets rho^0, c^0 to the
+ * given Gaussians at the nodes of M^+ and at the foot points of gamma_ex
+ * (Remark 2.1, 2-term extension with zero Neumann data).  Synchronises.
+ * set_state/get_state: device [N^3] arrays (float, or double for
+ * DPM_PREC_FP64) holding the values on N^+ (other nodes ignored / zeroed).
+ * step: advances nsteps steps; each step chooses dt (Step 3), forms the
+ * upwind minmod flux and the IMEX right-hand sides (eqs. discrete_chemotaxis
+ * to slope_limiter), rebuilds the BEP when dt_mode/rebuild ask for it (Step
+ * 4b), solves the particular problems, the least squares and the extensions
+ * (Steps 4a-5) and applies Green's formula (Steps 6-7) for rho and c.
+ * If stats is not NULL the call synchronises and writes the statistics of
+ * the last step (host struct).  DPM_ENUMERIC if a value became non-finite.
+ */
+int dpm_pks_create(dpm_ctx *ctx, const dpm_pks_params *params, const dpm_gaussian *rho0,
+                   const dpm_gaussian *c0, dpm_pks **out, cudaStream_t stream);
+int dpm_pks_set_state(dpm_pks *pks, const void *rho, const void *c, cudaStream_t stream);
+int dpm_pks_step(dpm_pks *pks, int nsteps, dpm_pks_stats *stats, cudaStream_t stream);
+int dpm_pks_get_state(dpm_pks *pks, void *rho, void *c, cudaStream_t stream);
+int dpm_pks_destroy(dpm_pks *pks);
+
+/* ---- diagnostics (no counterpart in the paper) -------------------------
+ * dpm_launch_count: number of CUDA kernels this library has launched in this
+ * process (all threads), for checking that work ran on the GPU.
+ * dpm_profile_enable(1): from now on each kernel launch of the library is
+ * bracketed by CUDA events recorded on the stream it is launched on (adds a
+ * little host overhead); 0 stops recording.  dpm_profile_read: synchronises
+ * on the recorded events and returns, for kernels whose name contains
+ * `name` (NULL or "" = all), the summed device time in ms and the number of
+ * launches.  dpm_profile_reset drops all records. */
+int64_t dpm_launch_count(void);
+int dpm_profile_enable(int on);
+int dpm_profile_read(const char *name, double *total_ms, int64_t *launches);
+int dpm_profile_reset(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DPM_H_ */

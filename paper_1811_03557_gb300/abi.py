@@ -1,0 +1,269 @@
+"""ctypes binding of libdpm (include/dpm.h), same names as the C ABI.
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+Array arguments are torch tensors on the GPU (their data_ptr() is passed) or
+None; ``stream`` is a torch.cuda.Stream, a raw cudaStream_t integer, or None
+for torch's current stream.  A nonzero status raises DPMError with the
+library's message.  There is no fallback: if libdpm.so is missing or a call
+fails, the error propagates.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdpm.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "dpm.h")
+
+DPM_OK, DPM_EINVAL, DPM_ENOMEM, DPM_ETIMEOUT, DPM_ENUMERIC, DPM_EUNSUPPORTED, DPM_ECUDA = (
+    0, -1, -2, -3, -4, -5, -6)
+DPM_PREC_FP32, DPM_PREC_FP64, DPM_PREC_TC32 = 0, 1, 2
+DPM_LBL_MPLUS, DPM_LBL_GIN, DPM_LBL_GEX, DPM_LBL_SHELL = 1, 2, 4, 8
+
+
+class DPMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libdpm error {code}: {msg}")
+        self.code = code
+
+
+class dpm_geom(C.Structure):
+    _fields_ = [("kind", C.c_int), ("center", C.c_double * 3), ("axes", C.c_double * 3)]
+
+
+class dpm_gaussian(C.Structure):
+    _fields_ = [("amp", C.c_double), ("alpha", C.c_double), ("center", C.c_double * 3),
+                ("zscale", C.c_double)]
+
+
+class dpm_bep_info(C.Structure):
+    _fields_ = [("N", C.c_int), ("lo", C.c_double), ("hi", C.c_double), ("h", C.c_double),
+                ("sigma", C.c_double), ("K", C.c_int), ("beta", C.c_int), ("ncol", C.c_int),
+                ("precision", C.c_int), ("n_mplus", C.c_int64), ("n_gin", C.c_int64),
+                ("n_gex", C.c_int64), ("n_gamma", C.c_int64), ("n_shell", C.c_int64)]
+
+
+class dpm_pks_params(C.Structure):
+    _fields_ = [("geom", dpm_geom), ("N", C.c_int), ("lo", C.c_double), ("hi", C.c_double),
+                ("chi", C.c_double), ("dt_max", C.c_double), ("K", C.c_int), ("beta", C.c_int),
+                ("precision", C.c_int), ("dt_mode", C.c_int), ("rebuild", C.c_int),
+                ("clamp", C.c_int)]
+
+
+class dpm_pks_stats(C.Structure):
+    _fields_ = [("t", C.c_double), ("dt", C.c_double), ("step", C.c_int64), ("rebuilt", C.c_int),
+                ("mass", C.c_double), ("max_rho", C.c_double), ("min_rho", C.c_double),
+                ("min_c", C.c_double), ("m2", C.c_double), ("free_energy", C.c_double)]
+
+
+_P = C.c_void_p
+_SIGS = {
+    "dpm_last_error": (C.c_char_p, []),
+    "dpm_ctx_create": (C.c_int, [C.c_int, C.POINTER(C.c_void_p)]),
+    "dpm_ctx_destroy": (C.c_int, [_P]),
+    "dpm_classify": (C.c_int, [_P, C.POINTER(dpm_geom), C.c_int, C.c_double, C.c_double, _P, _P,
+                               C.c_int64, _P, C.c_int64, C.POINTER(C.c_int64),
+                               C.POINTER(C.c_int64), _P]),
+    "dpm_aux_solve_batched": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.c_int, _P, _P,
+                                        C.c_int, _P]),
+    "dpm_bep_build": (C.c_int, [_P, C.POINTER(dpm_geom), C.c_int, C.c_double, C.c_double,
+                                C.c_double, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p), _P]),
+    "dpm_bep_get_info": (C.c_int, [_P, C.POINTER(dpm_bep_info)]),
+    "dpm_bep_matrix": (C.c_int, [_P, _P, _P]),
+    "dpm_bep_gamma_geometry": (C.c_int, [_P, _P, _P, _P, _P, _P]),
+    "dpm_bep_destroy": (C.c_int, [_P]),
+    "dpm_solve": (C.c_int, [_P, _P, _P, _P, _P, _P]),
+    "dpm_pks_create": (C.c_int, [_P, C.POINTER(dpm_pks_params), C.POINTER(dpm_gaussian),
+                                 C.POINTER(dpm_gaussian), C.POINTER(C.c_void_p), _P]),
+    "dpm_pks_set_state": (C.c_int, [_P, _P, _P, _P]),
+    "dpm_pks_step": (C.c_int, [_P, C.c_int, C.POINTER(dpm_pks_stats), _P]),
+    "dpm_pks_get_state": (C.c_int, [_P, _P, _P, _P]),
+    "dpm_pks_destroy": (C.c_int, [_P]),
+    "dpm_launch_count": (C.c_int64, []),
+    "dpm_profile_enable": (C.c_int, [C.c_int]),
+    "dpm_profile_read": (C.c_int, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "dpm_profile_reset": (C.c_int, []),
+}
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libdpm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_1811_03557_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/dpm.h."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(dpm_[a-z_0-9]+)\s*\(", txt)))
+
+
+def _check(rc: int):
+    if rc != DPM_OK:
+        raise DPMError(rc, lib().dpm_last_error().decode(errors="replace"))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_geom(geom) -> dpm_geom:
+    """From an object with kind/center/axes (e.g. workloads.Geometry)."""
+    g = dpm_geom()
+    g.kind = int(geom.kind)
+    for i in range(3):
+        g.center[i] = float(geom.center[i])
+        g.axes[i] = float(geom.axes[i])
+    return g
+
+
+def make_gaussian(gs) -> dpm_gaussian:
+    g = dpm_gaussian()
+    g.amp, g.alpha, g.zscale = float(gs.amp), float(gs.alpha), float(gs.zscale)
+    for i in range(3):
+        g.center[i] = float(gs.center[i])
+    return g
+
+
+# ---- entry points ------------------------------------------------------------
+def dpm_last_error() -> str:
+    return lib().dpm_last_error().decode(errors="replace")
+
+
+def dpm_ctx_create(device: int = 0):
+    h = C.c_void_p()
+    _check(lib().dpm_ctx_create(device, C.byref(h)))
+    return h
+
+
+def dpm_ctx_destroy(ctx):
+    _check(lib().dpm_ctx_destroy(ctx))
+
+
+def dpm_classify(ctx, geom, N, lo, hi, labels=None, gin_idx=None, gex_idx=None, stream=None):
+    """Returns (n_gin, n_gex).  labels: uint8 tensor [N^3]; gin_idx/gex_idx: int32 tensors."""
+    ng, ne = C.c_int64(), C.c_int64()
+    g = make_geom(geom) if not isinstance(geom, dpm_geom) else geom
+    _check(lib().dpm_classify(ctx, C.byref(g), N, lo, hi, _ptr(labels), _ptr(gin_idx),
+                              0 if gin_idx is None else gin_idx.numel(), _ptr(gex_idx),
+                              0 if gex_idx is None else gex_idx.numel(), C.byref(ng),
+                              C.byref(ne), _stream(stream)))
+    return ng.value, ne.value
+
+
+def dpm_aux_solve_batched(ctx, N, h, sigma, B, q, u, precision=DPM_PREC_FP32, stream=None):
+    _check(lib().dpm_aux_solve_batched(ctx, N, h, sigma, B, _ptr(q), _ptr(u), precision,
+                                       _stream(stream)))
+
+
+def dpm_bep_build(ctx, geom, N, lo, hi, sigma, K, beta=1, precision=DPM_PREC_FP32, stream=None):
+    h = C.c_void_p()
+    g = make_geom(geom) if not isinstance(geom, dpm_geom) else geom
+    _check(lib().dpm_bep_build(ctx, C.byref(g), N, lo, hi, sigma, K, beta, precision,
+                               C.byref(h), _stream(stream)))
+    return h
+
+
+def dpm_bep_get_info(bep) -> dpm_bep_info:
+    info = dpm_bep_info()
+    _check(lib().dpm_bep_get_info(bep, C.byref(info)))
+    return info
+
+
+def dpm_bep_matrix(bep, A, stream=None):
+    _check(lib().dpm_bep_matrix(bep, _ptr(A), _stream(stream)))
+
+
+def dpm_bep_gamma_geometry(bep, gamma_idx=None, foot=None, normal=None, dist=None, stream=None):
+    _check(lib().dpm_bep_gamma_geometry(bep, _ptr(gamma_idx), _ptr(foot), _ptr(normal),
+                                        _ptr(dist), _stream(stream)))
+
+
+def dpm_bep_destroy(bep):
+    _check(lib().dpm_bep_destroy(bep))
+
+
+def dpm_solve(bep, f, u, neumann=None, coeffs=None, stream=None):
+    _check(lib().dpm_solve(bep, _ptr(f), _ptr(neumann), _ptr(u), _ptr(coeffs), _stream(stream)))
+
+
+def dpm_pks_create(ctx, params: dpm_pks_params, rho0, c0, stream=None):
+    h = C.c_void_p()
+    g0 = make_gaussian(rho0) if not isinstance(rho0, dpm_gaussian) else rho0
+    g1 = make_gaussian(c0) if not isinstance(c0, dpm_gaussian) else c0
+    _check(lib().dpm_pks_create(ctx, C.byref(params), C.byref(g0), C.byref(g1), C.byref(h),
+                                _stream(stream)))
+    return h
+
+
+def dpm_pks_set_state(pks, rho, c, stream=None):
+    _check(lib().dpm_pks_set_state(pks, _ptr(rho), _ptr(c), _stream(stream)))
+
+
+def dpm_pks_step(pks, nsteps=1, want_stats=True, stream=None):
+    st = dpm_pks_stats()
+    _check(lib().dpm_pks_step(pks, nsteps, C.byref(st) if want_stats else None, _stream(stream)))
+    return st if want_stats else None
+
+
+def dpm_pks_get_state(pks, rho, c, stream=None):
+    _check(lib().dpm_pks_get_state(pks, _ptr(rho), _ptr(c), _stream(stream)))
+
+
+def dpm_pks_destroy(pks):
+    _check(lib().dpm_pks_destroy(pks))
+
+
+def pks_params(geom, N, lo, hi, chi, dt_max, K, beta=1, precision=DPM_PREC_FP32, dt_mode=0,
+               rebuild=0, clamp=1) -> dpm_pks_params:
+    p = dpm_pks_params()
+    p.geom = make_geom(geom)
+    p.N, p.lo, p.hi, p.chi, p.dt_max = N, lo, hi, chi, dt_max
+    p.K, p.beta, p.precision, p.dt_mode, p.rebuild, p.clamp = K, beta, precision, dt_mode, rebuild, clamp
+    return p
+
+
+def dpm_launch_count() -> int:
+    return int(lib().dpm_launch_count())
+
+
+def dpm_profile_enable(on: bool = True):
+    _check(lib().dpm_profile_enable(1 if on else 0))
+
+
+def dpm_profile_read(name: str | None = None):
+    """(total device ms, launches) of the recorded kernels whose name contains `name`."""
+    ms, n = C.c_double(), C.c_int64()
+    _check(lib().dpm_profile_read(name.encode() if name else None, C.byref(ms), C.byref(n)))
+    return ms.value, n.value
+
+
+def dpm_profile_reset():
+    _check(lib().dpm_profile_reset())

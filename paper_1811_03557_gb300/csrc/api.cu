@@ -1,0 +1,617 @@
+// C ABI of libdpm (include/dpm.h): argument checking, handle lifetime, and
+// the sequencing of the kernels for the DPM steps.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "dpm_internal.cuh"
+
+namespace dpm {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+// ---- launch counter and event profiler --------------------------------------
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+struct ProfRec {
+    const char *name;
+    cudaEvent_t a, b;
+};
+std::mutex g_pmu;
+std::vector<ProfRec> g_recs;
+std::vector<cudaEvent_t> g_pool;
+std::atomic<bool> g_prof{false};
+
+cudaEvent_t pool_event() {
+    if (!g_pool.empty()) {
+        cudaEvent_t e = g_pool.back();
+        g_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+}  // namespace
+
+int prof_begin(const char *name, cudaStream_t s) {
+    if (!g_prof.load(std::memory_order_relaxed)) return -1;
+    std::lock_guard<std::mutex> lk(g_pmu);
+    cudaEvent_t a = pool_event(), b = pool_event();
+    if (!a || !b) return -1;
+    cudaEventRecord(a, s);
+    g_recs.push_back({name, a, b});
+    return (int)g_recs.size() - 1;
+}
+
+void prof_end(int rec, cudaStream_t s) {
+    if (rec < 0) return;
+    std::lock_guard<std::mutex> lk(g_pmu);
+    if (rec < (int)g_recs.size()) cudaEventRecord(g_recs[rec].b, s);
+}
+
+template <class T>
+int pks_flux(int, double, double, double, const uint8_t *, const T *, const T *, T *, T *,
+             cudaStream_t);
+template <class T> int pks_cfl(int, const uint8_t *, const T *, unsigned int *, cudaStream_t);
+template <class T>
+int pks_diag(int, double, double, const uint8_t *, const T *, const T *, double *, double *,
+             cudaStream_t);
+int pks_diag_blocks(int N);
+template <class T>
+int pks_init(const GridIndex &, const GammaGeom &, const dpm_gaussian &, const dpm_gaussian &,
+             T *, T *, cudaStream_t);
+template <class T> int mask_copy(int, const uint8_t *, const T *, T *, cudaStream_t);
+
+namespace {
+
+size_t elem_size(int prec) { return prec == DPM_PREC_FP64 ? sizeof(double) : sizeof(float); }
+
+bool prec_ok(int prec) {
+    return prec == DPM_PREC_FP32 || prec == DPM_PREC_FP64 || prec == DPM_PREC_TC32;
+}
+
+// Run B right-hand sides through the AP solver in chunks that fit the
+// workspace (`work`, grown on demand up to kWorkCap bytes).
+constexpr size_t kWorkCap = size_t(8) << 30;
+
+template <class T>
+int run_ap(int prec, ApParams p, const std::vector<ApRhs<T>> &rhs, DevBuf &work, DevBuf &desc,
+           cudaStream_t s) {
+    const int B = (int)rhs.size();
+    if (B == 0) return DPM_OK;
+    const size_t cube = (size_t)p.N * p.N * p.N * sizeof(T);
+    size_t cb = std::max<size_t>(1, std::min<size_t>(B, kWorkCap / cube));
+    DPM_RET(work.reserve(cb * cube));
+    DPM_RET(desc.reserve(sizeof(ApRhs<T>) * B));
+    DPM_CUDA(cudaMemcpyAsync(desc.p, rhs.data(), sizeof(ApRhs<T>) * B, cudaMemcpyHostToDevice, s));
+    // The copy above is from pageable memory: it has been staged when it
+    // returns, so `rhs` may go out of scope afterwards.
+    for (int b0 = 0; b0 < B; b0 += (int)cb) {
+        ApParams q = p;
+        q.B = std::min<int>((int)cb, B - b0);
+        const ApRhs<T> *d = desc.as<ApRhs<T>>() + b0;
+        if (prec == DPM_PREC_TC32) {
+            if constexpr (sizeof(T) == 4) {
+                DPM_RET(ap_solve_tc(q, d, work.as<float>(), s));
+            } else {
+                set_error("tensor-core solve is FP32-storage only");
+                return DPM_EINVAL;
+            }
+        } else {
+            DPM_RET(ap_solve_simt<T>(q, d, work.as<T>(), s));
+        }
+    }
+    return DPM_OK;
+}
+
+template <class T>
+__global__ void k_neumann_rhs(int m, const T *trace0, const T *dgn, const int *gin_pos,
+                              const T *trace1, T *b) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= m) return;
+    // b = Tr G f - Tr_{gamma_in} (I - P)(d g_N)
+    b[r] = trace0[r] - (dgn[gin_pos[r]] - trace1[r]);
+}
+
+}  // namespace
+}  // namespace dpm
+
+using namespace dpm;
+
+// ---------------------------------------------------------------------------
+struct dpm_bep {
+    dpm_ctx *ctx = nullptr;
+    dpm_geom geom{};
+    int N = 0, K = 0, beta = 0, ncol = 0, prec = 0;
+    double lo = 0, hi = 0, sigma = 0;
+    GridIndex gi;
+    GammaGeom gg;
+    DevBuf psi;     // T[ncol][n_gamma]
+    DevBuf psi_in;  // double[ncol][n_gin]
+    DevBuf trace;   // T[ncol + 4][n_gin]
+    DevBuf dens;    // T[4][n_gamma]
+    DevBuf coef;    // double[4][ncol]
+    DevBuf zero;    // double[ncol] zeros
+    DevBuf desc;
+    DevBuf work;
+    LsqFactor lsq;
+    bool factored = false;
+};
+
+struct dpm_pks {
+    dpm_ctx *ctx = nullptr;
+    dpm_pks_params prm{};
+    dpm_bep bep;
+    DevBuf rho, c, frho, fc;
+    DevBuf gmax;       // uint32[3]
+    DevBuf diag_part;  // double[nblk][6]
+    DevBuf diag_out;   // double[6]
+    double t = 0, dt_prev = 0;
+    int64_t step = 0;
+    int last_rebuilt = 0;
+};
+
+extern "C" const char *dpm_last_error(void) { return g_err; }
+
+extern "C" int64_t dpm_launch_count(void) { return (int64_t)g_launches.load(); }
+
+extern "C" int dpm_profile_enable(int on) {
+    g_prof.store(on != 0);
+    return DPM_OK;
+}
+
+extern "C" int dpm_profile_read(const char *name, double *total_ms, int64_t *launches) {
+    std::lock_guard<std::mutex> lk(g_pmu);
+    double tot = 0.0;
+    int64_t n = 0;
+    for (auto &r : g_recs) {
+        if (name && name[0] && !strstr(r.name, name)) continue;
+        DPM_CUDA(cudaEventSynchronize(r.b));
+        float ms = 0.f;
+        DPM_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+        tot += ms;
+        ++n;
+    }
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = n;
+    return DPM_OK;
+}
+
+extern "C" int dpm_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(g_pmu);
+    for (auto &r : g_recs) {
+        cudaEventSynchronize(r.b);
+        g_pool.push_back(r.a);
+        g_pool.push_back(r.b);
+    }
+    g_recs.clear();
+    return DPM_OK;
+}
+
+extern "C" int dpm_ctx_create(int device, dpm_ctx **out) {
+    if (!out) { set_error("out is NULL"); return DPM_EINVAL; }
+    *out = nullptr;
+    int n = 0;
+    DPM_CUDA(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) { set_error("device %d not present (%d devices)", device, n); return DPM_EINVAL; }
+    DPM_CUDA(cudaSetDevice(device));
+    dpm_ctx *c = new (std::nothrow) dpm_ctx();
+    if (!c) { set_error("out of host memory"); return DPM_ENOMEM; }
+    c->device = device;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    *out = c;
+    return DPM_OK;
+}
+
+extern "C" int dpm_ctx_destroy(dpm_ctx *ctx) {
+    delete ctx;
+    return DPM_OK;
+}
+
+extern "C" int dpm_classify(dpm_ctx *ctx, const dpm_geom *geom, int N, double lo, double hi,
+                            uint8_t *labels, int32_t *gin_idx, int64_t gin_cap, int32_t *gex_idx,
+                            int64_t gex_cap, int64_t *n_gin, int64_t *n_gex, cudaStream_t s) {
+    if (!ctx || !geom) { set_error("ctx/geom is NULL"); return DPM_EINVAL; }
+    GridIndex gi;
+    DPM_RET(build_grid_index(*geom, N, lo, hi, gi, s));
+    if (n_gin) *n_gin = gi.n_gin;
+    if (n_gex) *n_gex = gi.n_gex;
+    if (gin_idx && gin_cap < gi.n_gin) { set_error("gin_cap %lld < |gamma_in| %lld", (long long)gin_cap, (long long)gi.n_gin); return DPM_EINVAL; }
+    if (gex_idx && gex_cap < gi.n_gex) { set_error("gex_cap %lld < |gamma_ex| %lld", (long long)gex_cap, (long long)gi.n_gex); return DPM_EINVAL; }
+    size_t n3 = (size_t)N * N * N;
+    if (labels) DPM_CUDA(cudaMemcpyAsync(labels, gi.labels.p, n3, cudaMemcpyDeviceToDevice, s));
+    if (gin_idx && gi.n_gin)
+        DPM_CUDA(cudaMemcpyAsync(gin_idx, gi.gin.p, sizeof(int) * gi.n_gin, cudaMemcpyDeviceToDevice, s));
+    if (gex_idx && gi.n_gex)
+        DPM_CUDA(cudaMemcpyAsync(gex_idx, gi.gex.p, sizeof(int) * gi.n_gex, cudaMemcpyDeviceToDevice, s));
+    DPM_CUDA(cudaStreamSynchronize(s));  // gi's buffers are freed on return
+    return DPM_OK;
+}
+
+extern "C" int dpm_aux_solve_batched(dpm_ctx *ctx, int N, double h, double sigma, int B,
+                                     const void *q, void *u, int precision, cudaStream_t s) {
+    if (!ctx || !q || !u) { set_error("ctx/q/u is NULL"); return DPM_EINVAL; }
+    if (!prec_ok(precision)) { set_error("unknown precision %d", precision); return DPM_EINVAL; }
+    if (N < 2 || N > 256 || B < 1 || !(h > 0) || !(sigma >= 0)) {
+        set_error("aux solve: need 2<=N<=256, B>=1, h>0, sigma>=0 (N=%d B=%d h=%g sigma=%g)", N, B, h, sigma);
+        return DPM_EINVAL;
+    }
+    if (precision == DPM_PREC_TC32 && !tc_supported(N)) {
+        set_error("tensor-core solve does not support N=%d", N);
+        return DPM_EUNSUPPORTED;
+    }
+    ApParams p;
+    p.N = N;
+    p.h = h;
+    p.sigma = sigma;
+    p.mask_f = 0;
+    p.mask_out = 0;
+    size_t n3 = (size_t)N * N * N;
+    if (precision == DPM_PREC_FP64) {
+        std::vector<ApRhs<double>> r(B);
+        for (int b = 0; b < B; ++b)
+            r[b] = {static_cast<const double *>(q) + b * n3, nullptr,
+                    static_cast<double *>(u) + b * n3, nullptr, 0, 0};
+        return run_ap<double>(precision, p, r, ctx->work, ctx->rhs_desc, s);
+    }
+    std::vector<ApRhs<float>> r(B);
+    for (int b = 0; b < B; ++b)
+        r[b] = {static_cast<const float *>(q) + b * n3, nullptr, static_cast<float *>(u) + b * n3,
+                nullptr, 0, 0};
+    return run_ap<float>(precision, p, r, ctx->work, ctx->rhs_desc, s);
+}
+
+// ---------------------------------------------------------------------------
+// BEP
+// ---------------------------------------------------------------------------
+namespace {
+
+template <class T> int bep_setup(dpm_bep *b, cudaStream_t s) {
+    DPM_RET(build_gamma_geom(b->geom, b->gi, b->K, b->gg, s));
+    const int64_t ng = b->gi.n_gamma, m = b->gi.n_gin;
+    DPM_RET(b->psi.alloc(sizeof(T) * b->ncol * ng));
+    DPM_RET(b->psi_in.alloc(sizeof(double) * b->ncol * m));
+    DPM_RET(make_basis_densities<T>(b->gg, b->gi, b->beta, b->psi.as<T>(), b->psi_in.as<double>(), s));
+    DPM_RET(b->trace.alloc(sizeof(T) * (b->ncol + 4) * m));
+    DPM_RET(b->dens.alloc(sizeof(T) * 4 * ng));
+    DPM_RET(b->coef.alloc(sizeof(double) * 4 * b->ncol));
+    DPM_RET(b->zero.alloc(sizeof(double) * b->ncol));
+    DPM_CUDA(cudaMemsetAsync(b->zero.p, 0, sizeof(double) * b->ncol, s));
+    b->lsq.m = (int)m;
+    b->lsq.n = b->ncol;
+    DPM_RET(b->lsq.A.alloc(sizeof(double) * m * b->ncol));
+    if (m < b->ncol) {
+        set_error("|gamma_in| = %lld is smaller than the %d BEP columns: refine the grid or lower K",
+                  (long long)m, b->ncol);
+        return DPM_EINVAL;
+    }
+    return DPM_OK;
+}
+
+ApParams base_params(const dpm_bep *b, double sigma) {
+    ApParams p;
+    p.N = b->N;
+    p.h = b->gi.h;
+    p.sigma = sigma;
+    ap_params_from_index(p, b->gi);
+    return p;
+}
+
+// Columns of eq. BEP_recast plus `extra` right-hand sides in the same batch.
+template <class T>
+int bep_assemble(dpm_bep *b, double sigma, std::vector<ApRhs<T>> extra, double fscale,
+                 cudaStream_t s) {
+    const int64_t ng = b->gi.n_gamma, m = b->gi.n_gin;
+    std::vector<ApRhs<T>> rhs;
+    rhs.reserve(b->ncol + extra.size());
+    for (int k = 0; k < b->ncol; ++k)
+        rhs.push_back({nullptr, b->psi.as<T>() + k * ng, nullptr, b->trace.as<T>() + k * m, 0, 0});
+    for (auto &e : extra) rhs.push_back(e);
+    ApParams p = base_params(b, sigma);
+    p.fscale = fscale;
+    DPM_RET(run_ap<T>(b->prec, p, rhs, b->work, b->desc, s));
+    DPM_RET(assemble_bep<T>(b->psi_in.as<double>(), b->trace.as<T>(), b->lsq.A.as<double>(), m,
+                            b->ncol, nullptr, s));
+    DPM_RET(lsq_factor(b->lsq, nullptr, s));
+    b->sigma = sigma;
+    b->factored = true;
+    return DPM_OK;
+}
+
+template <class T>
+int bep_solve(dpm_bep *b, const void *fv, const double *neumann, void *uv, double *coeffs,
+              cudaStream_t s) {
+    const T *f = static_cast<const T *>(fv);
+    T *u = static_cast<T *>(uv);
+    const int64_t ng = b->gi.n_gamma, m = b->gi.n_gin;
+    T *tr0 = b->trace.as<T>() + (int64_t)b->ncol * m;
+    T *tr1 = tr0 + m;
+    T *bvec = tr1 + m;
+    T *dens0 = b->dens.as<T>(), *dens1 = dens0 + ng;
+    double *C = b->coef.as<double>();
+    std::vector<ApRhs<T>> rhs;
+    rhs.push_back({f, nullptr, nullptr, tr0, 0, 0});
+    if (neumann) {
+        // density d*g_N (the known term of the extension)
+        DPM_RET(extend_density<T>(b->gg, ng, 0, b->zero.as<double>(), 0, neumann, dens1, (int)ng, 1, 0, s));
+        rhs.push_back({nullptr, dens1, nullptr, tr1, 0, 0});
+    }
+    ApParams p = base_params(b, b->sigma);
+    DPM_RET(run_ap<T>(b->prec, p, rhs, b->work, b->desc, s));
+    const T *bb = tr0;
+    if (neumann) {
+        k_neumann_rhs<T><<<(unsigned)((m + 255) / 256), 256, 0, s>>>((int)m, tr0, dens1,
+                                                                    b->gi.gin_pos.as<int>(), tr1, bvec);
+        DPM_LAUNCHED();
+        bb = bvec;
+    }
+    DPM_RET(lsq_apply<T>(b->lsq, bb, (int)m, C, 1, s));
+    DPM_RET(extend_density<T>(b->gg, ng, b->beta, C, b->ncol, neumann, dens0, (int)ng, 1, 0, s));
+    std::vector<ApRhs<T>> rhs2;
+    rhs2.push_back({f, dens0, u, nullptr, 0, 0});
+    DPM_RET(run_ap<T>(b->prec, p, rhs2, b->work, b->desc, s));
+    if (coeffs) DPM_CUDA(cudaMemcpyAsync(coeffs, C, sizeof(double) * b->ncol, cudaMemcpyDeviceToDevice, s));
+    return DPM_OK;
+}
+
+int bep_init(dpm_bep *b, dpm_ctx *ctx, const dpm_geom *geom, int N, double lo, double hi, int K,
+             int beta, int precision, cudaStream_t s) {
+    if (!ctx || !geom) { set_error("ctx/geom is NULL"); return DPM_EINVAL; }
+    if (!prec_ok(precision)) { set_error("unknown precision %d", precision); return DPM_EINVAL; }
+    if (beta != 0 && beta != 1) { set_error("beta must be 0 or 1"); return DPM_EINVAL; }
+    if (N > 256) { set_error("N=%d > 256 not supported by the AP solver", N); return DPM_EINVAL; }
+    if (precision == DPM_PREC_TC32 && !tc_supported(N)) {
+        set_error("tensor-core solve does not support N=%d", N);
+        return DPM_EUNSUPPORTED;
+    }
+    b->ctx = ctx;
+    b->geom = *geom;
+    b->N = N; b->lo = lo; b->hi = hi; b->K = K; b->beta = beta; b->prec = precision;
+    b->ncol = (beta + 1) * (K + 1) * (K + 1);
+    DPM_RET(build_grid_index(*geom, N, lo, hi, b->gi, s));
+    if (precision == DPM_PREC_FP64) return bep_setup<double>(b, s);
+    return bep_setup<float>(b, s);
+}
+
+}  // namespace
+
+extern "C" int dpm_bep_build(dpm_ctx *ctx, const dpm_geom *geom, int N, double lo, double hi,
+                             double sigma, int K, int beta, int precision, dpm_bep **out,
+                             cudaStream_t s) {
+    if (!out) { set_error("out is NULL"); return DPM_EINVAL; }
+    *out = nullptr;
+    if (!(sigma > 0)) { set_error("sigma must be positive"); return DPM_EINVAL; }
+    dpm_bep *b = new (std::nothrow) dpm_bep();
+    if (!b) { set_error("out of host memory"); return DPM_ENOMEM; }
+    int r = bep_init(b, ctx, geom, N, lo, hi, K, beta, precision, s);
+    if (r == DPM_OK) {
+        if (precision == DPM_PREC_FP64) r = bep_assemble<double>(b, sigma, {}, 1.0, s);
+        else r = bep_assemble<float>(b, sigma, {}, 1.0, s);
+    }
+    if (r == DPM_OK) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { set_error("BEP build: %s", cudaGetErrorString(e)); r = DPM_ECUDA; }
+    }
+    if (r != DPM_OK) { delete b; return r; }
+    *out = b;
+    return DPM_OK;
+}
+
+extern "C" int dpm_bep_get_info(const dpm_bep *b, dpm_bep_info *info) {
+    if (!b || !info) { set_error("bep/info is NULL"); return DPM_EINVAL; }
+    info->N = b->N; info->lo = b->lo; info->hi = b->hi; info->h = b->gi.h; info->sigma = b->sigma;
+    info->K = b->K; info->beta = b->beta; info->ncol = b->ncol; info->precision = b->prec;
+    info->n_mplus = b->gi.n_mplus; info->n_gin = b->gi.n_gin; info->n_gex = b->gi.n_gex;
+    info->n_gamma = b->gi.n_gamma; info->n_shell = b->gi.n_shell;
+    return DPM_OK;
+}
+
+extern "C" int dpm_bep_matrix(const dpm_bep *b, double *A, cudaStream_t s) {
+    if (!b || !A) { set_error("bep/A is NULL"); return DPM_EINVAL; }
+    const double *A0 = b->lsq.work.as<double>();  // unfactored copy
+    DPM_CUDA(cudaMemcpyAsync(A, A0, sizeof(double) * b->gi.n_gin * b->ncol, cudaMemcpyDeviceToDevice, s));
+    return DPM_OK;
+}
+
+extern "C" int dpm_bep_gamma_geometry(const dpm_bep *b, int32_t *gamma_idx, double *foot,
+                                      double *normal, double *dist, cudaStream_t s) {
+    if (!b) { set_error("bep is NULL"); return DPM_EINVAL; }
+    int64_t n = b->gi.n_gamma;
+    if (gamma_idx) DPM_CUDA(cudaMemcpyAsync(gamma_idx, b->gi.gamma.p, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
+    if (foot) DPM_CUDA(cudaMemcpyAsync(foot, b->gg.foot.p, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
+    if (normal) DPM_CUDA(cudaMemcpyAsync(normal, b->gg.normal.p, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
+    if (dist) DPM_CUDA(cudaMemcpyAsync(dist, b->gg.dist.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    return DPM_OK;
+}
+
+extern "C" int dpm_bep_destroy(dpm_bep *b) {
+    delete b;
+    return DPM_OK;
+}
+
+extern "C" int dpm_solve(dpm_bep *b, const void *f, const double *neumann, void *u, double *coeffs,
+                         cudaStream_t s) {
+    if (!b || !f || !u) { set_error("bep/f/u is NULL"); return DPM_EINVAL; }
+    if (b->prec == DPM_PREC_FP64) return bep_solve<double>(b, f, neumann, u, coeffs, s);
+    return bep_solve<float>(b, f, neumann, u, coeffs, s);
+}
+
+// ---------------------------------------------------------------------------
+// PKS
+// ---------------------------------------------------------------------------
+namespace {
+
+template <class T> int pks_alloc(dpm_pks *k, cudaStream_t s) {
+    size_t n3 = (size_t)k->prm.N * k->prm.N * k->prm.N;
+    DPM_RET(k->rho.alloc(sizeof(T) * n3));
+    DPM_RET(k->c.alloc(sizeof(T) * n3));
+    DPM_RET(k->frho.alloc(sizeof(T) * n3));
+    DPM_RET(k->fc.alloc(sizeof(T) * n3));
+    DPM_RET(k->gmax.alloc(sizeof(unsigned int) * 4));
+    DPM_RET(k->diag_part.alloc(sizeof(double) * 6 * pks_diag_blocks(k->prm.N)));
+    DPM_RET(k->diag_out.alloc(sizeof(double) * 8));
+    DPM_CUDA(cudaMemsetAsync(k->diag_out.p, 0, sizeof(double) * 8, s));
+    return DPM_OK;
+}
+
+template <class T> int pks_step_one(dpm_pks *k, cudaStream_t s) {
+    dpm_bep *b = &k->bep;
+    const dpm_pks_params &P = k->prm;
+    const int N = P.N;
+    const double h = b->gi.h;
+    double dt = P.dt_max;
+    if (P.dt_mode == 1) {
+        unsigned int gm[3];
+        DPM_RET(pks_cfl<T>(N, b->gi.labels.as<uint8_t>(), k->c.as<T>(), k->gmax.as<unsigned int>(), s));
+        DPM_CUDA(cudaMemcpyAsync(gm, k->gmax.p, sizeof(gm), cudaMemcpyDeviceToHost, s));
+        DPM_CUDA(cudaStreamSynchronize(s));
+        for (int ax = 0; ax < 3; ++ax) {
+            float g;
+            memcpy(&g, &gm[ax], sizeof(g));
+            double gmaxv = (double)g / h;  // max |grad_h c| along ax
+            if (gmaxv > 0) dt = std::min(dt, h / (6.0 * P.chi * gmaxv));
+        }
+        if (k->step > 0) dt = std::min(dt, k->dt_prev);
+    }
+    if (!(dt > 0) || !std::isfinite(dt)) { set_error("time step is not positive/finite (dt=%g)", dt); return DPM_ENUMERIC; }
+    const bool rebuild = !b->factored || P.rebuild || dt < k->dt_prev;
+    const double sigma = 1.0 / dt;
+    const int64_t m = b->gi.n_gin, ng = b->gi.n_gamma;
+    T *frho = k->frho.as<T>(), *fc = k->fc.as<T>();
+    DPM_RET(pks_flux<T>(N, h, P.chi, dt, b->gi.labels.as<uint8_t>(), k->rho.as<T>(), k->c.as<T>(),
+                        frho, fc, s));
+    T *tr0 = b->trace.as<T>() + (int64_t)b->ncol * m;
+    T *tr1 = tr0 + m;
+    std::vector<ApRhs<T>> part = {{frho, nullptr, nullptr, tr0, 0, 0},
+                                  {fc, nullptr, nullptr, tr1, 0, 0}};
+    if (rebuild) {
+        DPM_RET(bep_assemble<T>(b, sigma, part, sigma, s));
+    } else {
+        ApParams p = base_params(b, sigma);
+        p.fscale = sigma;  // L_{h,dt} u = f  <=>  (1/dt - Lap_h) u = f/dt
+        DPM_RET(run_ap<T>(b->prec, p, part, b->work, b->desc, s));
+    }
+    double *C = b->coef.as<double>();
+    DPM_RET(lsq_apply<T>(b->lsq, tr0, (int)m, C, 2, s));
+    T *dens = b->dens.as<T>();
+    DPM_RET(extend_density<T>(b->gg, ng, b->beta, C, b->ncol, nullptr, dens, (int)ng, 2, P.clamp, s));
+    std::vector<ApRhs<T>> green = {{frho, dens, k->rho.as<T>(), nullptr, 0, 0},
+                                   {fc, dens + ng, k->c.as<T>(), nullptr, 0, 0}};
+    ApParams p = base_params(b, sigma);
+    p.fscale = sigma;
+    DPM_RET(run_ap<T>(b->prec, p, green, b->work, b->desc, s));
+    DPM_RET(pks_diag<T>(N, b->gi.lo, h, b->gi.labels.as<uint8_t>(), k->rho.as<T>(), k->c.as<T>(),
+                        k->diag_part.as<double>(), k->diag_out.as<double>(), s));
+    k->t += dt;
+    k->dt_prev = dt;
+    k->step += 1;
+    k->last_rebuilt = rebuild ? 1 : 0;
+    return DPM_OK;
+}
+
+}  // namespace
+
+extern "C" int dpm_pks_create(dpm_ctx *ctx, const dpm_pks_params *prm, const dpm_gaussian *rho0,
+                              const dpm_gaussian *c0, dpm_pks **out, cudaStream_t s) {
+    if (!out || !prm) { set_error("out/params is NULL"); return DPM_EINVAL; }
+    *out = nullptr;
+    if (!(prm->dt_max > 0) || !(prm->chi >= 0) || (prm->dt_mode != 0 && prm->dt_mode != 1)) {
+        set_error("PKS params: need dt_max > 0, chi >= 0, dt_mode in {0,1}");
+        return DPM_EINVAL;
+    }
+    dpm_pks *k = new (std::nothrow) dpm_pks();
+    if (!k) { set_error("out of host memory"); return DPM_ENOMEM; }
+    k->ctx = ctx;
+    k->prm = *prm;
+    int r = bep_init(&k->bep, ctx, &prm->geom, prm->N, prm->lo, prm->hi, prm->K, prm->beta,
+                     prm->precision, s);
+    if (r == DPM_OK) {
+        dpm_gaussian z{};
+        const dpm_gaussian &g0 = rho0 ? *rho0 : z, &g1 = c0 ? *c0 : z;
+        if (prm->precision == DPM_PREC_FP64) {
+            r = pks_alloc<double>(k, s);
+            if (r == DPM_OK) r = pks_init<double>(k->bep.gi, k->bep.gg, g0, g1, k->rho.as<double>(), k->c.as<double>(), s);
+        } else {
+            r = pks_alloc<float>(k, s);
+            if (r == DPM_OK) r = pks_init<float>(k->bep.gi, k->bep.gg, g0, g1, k->rho.as<float>(), k->c.as<float>(), s);
+        }
+    }
+    if (r == DPM_OK) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { set_error("PKS create: %s", cudaGetErrorString(e)); r = DPM_ECUDA; }
+    }
+    if (r != DPM_OK) { delete k; return r; }
+    *out = k;
+    return DPM_OK;
+}
+
+extern "C" int dpm_pks_set_state(dpm_pks *k, const void *rho, const void *c, cudaStream_t s) {
+    if (!k || !rho || !c) { set_error("pks/rho/c is NULL"); return DPM_EINVAL; }
+    const uint8_t *lab = k->bep.gi.labels.as<uint8_t>();
+    if (k->prm.precision == DPM_PREC_FP64) {
+        DPM_RET(mask_copy<double>(k->prm.N, lab, static_cast<const double *>(rho), k->rho.as<double>(), s));
+        DPM_RET(mask_copy<double>(k->prm.N, lab, static_cast<const double *>(c), k->c.as<double>(), s));
+    } else {
+        DPM_RET(mask_copy<float>(k->prm.N, lab, static_cast<const float *>(rho), k->rho.as<float>(), s));
+        DPM_RET(mask_copy<float>(k->prm.N, lab, static_cast<const float *>(c), k->c.as<float>(), s));
+    }
+    return DPM_OK;
+}
+
+extern "C" int dpm_pks_step(dpm_pks *k, int nsteps, dpm_pks_stats *stats, cudaStream_t s) {
+    if (!k || nsteps < 0) { set_error("pks is NULL or nsteps < 0"); return DPM_EINVAL; }
+    for (int i = 0; i < nsteps; ++i) {
+        if (k->prm.precision == DPM_PREC_FP64) DPM_RET(pks_step_one<double>(k, s));
+        else DPM_RET(pks_step_one<float>(k, s));
+    }
+    if (stats) {
+        double d[6];
+        DPM_CUDA(cudaMemcpyAsync(d, k->diag_out.p, sizeof(d), cudaMemcpyDeviceToHost, s));
+        DPM_CUDA(cudaStreamSynchronize(s));
+        stats->t = k->t;
+        stats->dt = k->dt_prev;
+        stats->step = k->step;
+        stats->rebuilt = k->last_rebuilt;
+        stats->mass = d[0];
+        stats->max_rho = d[1];
+        stats->min_rho = d[2];
+        stats->min_c = d[3];
+        stats->m2 = d[4];
+        stats->free_energy = d[5];
+        if (!std::isfinite(d[0]) || !std::isfinite(d[5])) {
+            set_error("PKS state became non-finite at step %lld", (long long)k->step);
+            return DPM_ENUMERIC;
+        }
+    }
+    return DPM_OK;
+}
+
+extern "C" int dpm_pks_get_state(dpm_pks *k, void *rho, void *c, cudaStream_t s) {
+    if (!k) { set_error("pks is NULL"); return DPM_EINVAL; }
+    size_t n3 = (size_t)k->prm.N * k->prm.N * k->prm.N * elem_size(k->prm.precision);
+    if (rho) DPM_CUDA(cudaMemcpyAsync(rho, k->rho.p, n3, cudaMemcpyDeviceToDevice, s));
+    if (c) DPM_CUDA(cudaMemcpyAsync(c, k->c.p, n3, cudaMemcpyDeviceToDevice, s));
+    return DPM_OK;
+}
+
+extern "C" int dpm_pks_destroy(dpm_pks *k) {
+    delete k;
+    return DPM_OK;
+}

@@ -1,0 +1,201 @@
+// Internal declarations shared by the CUDA translation units of libdpm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/dpm.h"
+
+namespace dpm {
+
+void set_error(const char *fmt, ...);
+const char *cuda_err(cudaError_t e);
+
+#define DPM_CUDA(call)                                                                  \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            dpm::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),      \
+                           __FILE__, __LINE__);                                         \
+            return e_ == cudaErrorMemoryAllocation ? DPM_ENOMEM : DPM_ECUDA;            \
+        }                                                                               \
+    } while (0)
+
+// Kernel-launch bookkeeping: every launch is followed by DPM_LAUNCHED() (it
+// counts the launch and checks the launch error).  A launch whose device time
+// should be attributable sits inside a DPM_PROF("name", stream) scope, which
+// records CUDA events around it while profiling is enabled.
+void count_launch();
+int prof_begin(const char *name, cudaStream_t s);   // -1 when profiling is off
+void prof_end(int rec, cudaStream_t s);
+
+#define DPM_LAUNCHED()              \
+    do {                            \
+        dpm::count_launch();        \
+        DPM_CUDA(cudaGetLastError()); \
+    } while (0)
+
+struct ProfScope {
+    int rec;
+    cudaStream_t s;
+    ProfScope(const char *name, cudaStream_t st) : rec(prof_begin(name, st)), s(st) {}
+    ~ProfScope() { prof_end(rec, s); }
+};
+#define DPM_PROF(name, stream) dpm::ProfScope prof_scope_##__LINE__(name, stream)
+
+#define DPM_RET(expr)                        \
+    do {                                     \
+        int r_ = (expr);                     \
+        if (r_ != DPM_OK) return r_;         \
+    } while (0)
+
+// Owning device buffer.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    int alloc(size_t n) {  // exact size; contents undefined
+        if (n == bytes && p) return DPM_OK;
+        release();
+        if (n == 0) return DPM_OK;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            set_error("cudaMalloc(%zu bytes) failed: %s", n, cudaGetErrorString(e));
+            return DPM_ENOMEM;
+        }
+        bytes = n;
+        return DPM_OK;
+    }
+    int reserve(size_t n) {  // at least n bytes
+        if (n <= bytes && p) return DPM_OK;
+        return alloc(n);
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// ---------------------------------------------------------------------------
+// Point sets and the index structures built from them (Definition 2.1).
+// ---------------------------------------------------------------------------
+struct GridIndex {
+    int N = 0;
+    double lo = 0, hi = 0, h = 0;
+    int64_t n_mplus = 0, n_gin = 0, n_gex = 0, n_gamma = 0, n_shell = 0;
+    DevBuf labels;     // uint8[N^3]
+    DevBuf gin;        // int32[n_gin]   ascending linear indices of gamma_in
+    DevBuf gex;        // int32[n_gex]
+    DevBuf gamma;      // int32[n_gamma] ascending (union of the two)
+    DevBuf shell;      // int32[n_shell] ascending, nodes with DPM_LBL_SHELL
+    DevBuf shell_nb;   // int32[n_shell][8]: gamma positions of (self,-x,+x,-y,+y,-z,+z), -1 if none
+    DevBuf rp_gin;     // int32[N^2+1]: gamma_in entries of grid row r=(i*N+j)
+    DevBuf rp_shell;   // int32[N^2+1]
+    DevBuf gin_pos;    // int32[n_gin]: position of each gamma_in node in `gamma`
+    DevBuf gex_pos;    // int32[n_gex]
+};
+
+// Classify and build every list.  Synchronises `s` (the sizes come back to
+// the host).  Returns DPM_EINVAL on a geometry the library rejects.
+int build_grid_index(const dpm_geom &g, int N, double lo, double hi, GridIndex &gi,
+                     cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Gamma geometry and spherical harmonics (Definition 2.6, eq. spectral_approximation_sd)
+// ---------------------------------------------------------------------------
+struct GammaGeom {
+    int K = 0, nsh = 0;
+    DevBuf foot;     // double[n_gamma][3]
+    DevBuf normal;   // double[n_gamma][3]
+    DevBuf dist;     // double[n_gamma]
+    DevBuf phi;      // double[n_gamma][nsh] real orthonormal SH at the foot point
+};
+int build_gamma_geom(const dpm_geom &g, const GridIndex &gi, int K, GammaGeom &gg,
+                     cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Auxiliary-problem solver (Definition 2.4)
+// ---------------------------------------------------------------------------
+template <class T> struct ApRhs {
+    const T *f;      // dense N^3 source (scaled by fscale), or null
+    const T *dens;   // density on gamma [n_gamma] (potential part), or null
+    T *out_dense;    // dense N^3 output, or null
+    T *out_trace;    // trace on gamma_in [n_gin], or null
+    int cond;        // 1: skipped unless *cond_flag != 0
+    int pad_;
+};
+
+struct ApParams {
+    int N = 0, B = 0;
+    double h = 0, sigma = 0, fscale = 1;
+    const double *sigma_dev = nullptr;   // overrides sigma when set
+    const double *fscale_dev = nullptr;  // overrides fscale when set
+    const int *cond_flag = nullptr;      // see ApRhs::cond
+    int mask_f = 1;    // 1: f is applied on M^+ only (else everywhere)
+    int mask_out = 1;  // 1: out_dense is zero off N^+ (else the raw AP solution)
+    // index data (required when mask_f/mask_out or any dens/out_trace is used)
+    const uint8_t *labels = nullptr;
+    const int *shell = nullptr, *shell_nb = nullptr, *rp_shell = nullptr;
+    const int *gin = nullptr, *rp_gin = nullptr;
+};
+
+// Fills the index members of p from gi.
+void ap_params_from_index(ApParams &p, const GridIndex &gi);
+
+// work: B*N^3 elements of T.  rhs: device array of B descriptors.
+template <class T>
+int ap_solve_simt(const ApParams &p, const ApRhs<T> *rhs_dev, T *work, cudaStream_t s);
+int ap_solve_tc(const ApParams &p, const ApRhs<float> *rhs_dev, float *work, cudaStream_t s);
+bool tc_supported(int N);
+
+// DST-I fold tables (device, per N and type), built on first use.
+template <class T> const T *dst_fold_table(int N);
+
+// ---------------------------------------------------------------------------
+// FP64 least squares (Householder QR, resident R^{-1} Q^T)
+// ---------------------------------------------------------------------------
+struct LsqFactor {
+    int m = 0, n = 0;
+    DevBuf A;      // double[m*n] column-major; overwritten by the QR
+    DevBuf tau;    // double[n]
+    DevBuf X;      // double[n*m] row-major: X = R^{-1} Q1^T
+    DevBuf work;   // scratch
+};
+// Factor A (already in f.A, m x n col-major) and form X.
+int lsq_factor(LsqFactor &f, const int *cond_flag, cudaStream_t s);
+// C[r][0..n) = X b[r] for nr right-hand sides (b: [nr][m] in T, C: [nr][n] double)
+template <class T>
+int lsq_apply(const LsqFactor &f, const T *b, int ldb, double *C, int nr, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// BEP assembly helpers
+// ---------------------------------------------------------------------------
+// psi[k][g] (T) for k < ncol: phi or (d^2/2) phi.  Also psi_in (double) at gamma_in.
+template <class T>
+int make_basis_densities(const GammaGeom &gg, const GridIndex &gi, int beta, T *psi,
+                         double *psi_in, cudaStream_t s);
+// A[k*m + r] = psi_in[k*m + r] - trace[k*m + r]
+template <class T>
+int assemble_bep(const double *psi_in, const T *trace, double *A, int64_t m, int ncol,
+                 const int *cond_flag, cudaStream_t s);
+// u_gamma[r][g] = sum phi C0 + d*gN + beta (d^2/2) sum phi C2 (+ clamp)
+template <class T>
+int extend_density(const GammaGeom &gg, int64_t n_gamma, int beta, const double *C, int ldc,
+                   const double *neumann, T *dens, int ldd, int nr, int clamp, cudaStream_t s);
+
+}  // namespace dpm
+
+struct dpm_ctx {
+    int device = 0;
+    int num_sms = 0;
+    dpm::DevBuf work;      // AP workspace
+    dpm::DevBuf rhs_desc;  // descriptor scratch
+    dpm::DevBuf scratch;   // small scalars
+};

@@ -1,0 +1,490 @@
+// SIMT auxiliary-problem solver (Definition 2.4): (sigma - Lap_h) u = q on
+// M^0, u = 0 on N^0 \ M^0, by the 3D DST-I,
+//   u = (2/(N+1))^3 S_x S_y S_z [ (S_x S_y S_z q) / lambda ],
+//   S[a][m] = sin(pi a m/(N+1)),
+//   lambda_abc = sigma + (4/h^2)(s_a + s_b + s_c), s_a = sin^2(pi a/(2(N+1))).
+//
+// Five passes over a [B][N][N][N] workspace, each a per-tile dense transform
+// along one axis staged in shared memory:
+//   1. k (contiguous) forward, with the right-hand side built in the tile:
+//      q = fscale*f on M^+ (eq. rhs:particular_solution) plus L[v_gamma] on
+//      the M^- shell (eq. rhs:difference_potentials) from a density on gamma;
+//   2. j forward;  3. i forward, times (2/(N+1))^3/lambda, i inverse;
+//   4. j inverse;  5. k inverse, with the restriction to N^+ and the trace on
+//      gamma_in (Tr operators of Section 2) fused into the store.
+//
+// Each 1D transform uses the symmetry S[a][N+1-m] = (-1)^(a+1) S[a][m]:
+// folding x_m +- x_{N+1-m} first halves the multiply-adds (odd a read the
+// sums, even a the differences; for odd N the middle node joins odd a only).
+// N+1 = 33, 129, 257 have no radix-2 structure beyond this fold, so the rest
+// of each transform is a dense product with the folded sine table.
+#include <map>
+#include <math.h>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "dpm_internal.cuh"
+
+namespace dpm {
+
+// ---------------------------------------------------------------------------
+// Folded sine tables: SE[m'][a'] = S[2a'+1][m'+1] (odd a, sums), with an extra
+// row m' = H for the middle node when N is odd; SO[m'][a'] = S[2a'+2][m'+1]
+// (even a, differences).  a' padded to a multiple of 4 with zeros.
+// ---------------------------------------------------------------------------
+struct FoldDims {
+    int H, NE, NO, NEp, NOp, rowsE;
+    __host__ __device__ FoldDims(int N) {
+        H = N / 2;
+        NE = (N + 1) / 2;
+        NO = N / 2;
+        NEp = (NE + 3) & ~3;
+        NOp = (NO + 3) & ~3;
+        rowsE = H + (N & 1);
+    }
+    __host__ __device__ size_t offO() const { return (size_t)rowsE * NEp; }
+    __host__ __device__ size_t offW() const { return offO() + (size_t)H * NOp; }
+    // followed by N weights sin^2(pi (n+1)/(2(N+1)))
+    __host__ __device__ size_t total(int N) const { return offW() + (size_t)N; }
+};
+
+static double sin_pi_frac(long long num, long long den) {
+    // sin(pi num/den) with the argument reduced exactly modulo 2 den
+    long long r = num % (2 * den);
+    return sin(M_PI * (double)r / (double)den);
+}
+
+template <class T> const T *dst_fold_table(int N) {
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, void *> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_pair(dev, N);
+    auto it = cache.find(key);
+    if (it != cache.end()) return static_cast<const T *>(it->second);
+    FoldDims fd(N);
+    std::vector<T> h(fd.total(N), (T)0);
+    for (int mp = 0; mp < fd.rowsE; ++mp)
+        for (int ap = 0; ap < fd.NE; ++ap)
+            h[(size_t)mp * fd.NEp + ap] = (T)sin_pi_frac((long long)(2 * ap + 1) * (mp + 1), N + 1);
+    for (int mp = 0; mp < fd.H; ++mp)
+        for (int ap = 0; ap < fd.NO; ++ap)
+            h[fd.offO() + (size_t)mp * fd.NOp + ap] =
+                (T)sin_pi_frac((long long)(2 * ap + 2) * (mp + 1), N + 1);
+    for (int n = 0; n < N; ++n) {
+        double sn = sin(M_PI * (double)(n + 1) / (2.0 * (N + 1)));
+        h[fd.offW() + n] = (T)(sn * sn);
+    }
+    void *d = nullptr;
+    if (cudaMalloc(&d, h.size() * sizeof(T)) != cudaSuccess) return nullptr;
+    if (cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(d);
+        return nullptr;
+    }
+    cache[key] = d;
+    return static_cast<const T *>(d);
+}
+template const float *dst_fold_table<float>(int);
+template const double *dst_fold_table<double>(int);
+
+namespace {
+
+constexpr int kC = 32;         // columns (or rows) per tile
+constexpr int kThreads = 256;
+
+template <class T> struct V4 { T v[4]; };
+
+__device__ __forceinline__ V4<float> ld4(const float *p) {
+    float4 a = *reinterpret_cast<const float4 *>(p);
+    return {{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ V4<double> ld4(const double *p) {
+    double2 a = *reinterpret_cast<const double2 *>(p);
+    double2 b = *reinterpret_cast<const double2 *>(p + 2);
+    return {{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ V4<float> ldg4(const float *p) {
+    float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+    return {{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ V4<double> ldg4(const double *p) {
+    double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+    double2 b = __ldg(reinterpret_cast<const double2 *>(p + 2));
+    return {{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ void st4(float *p, const float *v) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double *p, const double *v) {
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2 *>(p + 2) = make_double2(v[2], v[3]);
+}
+
+// Column-major tile: x[m][c] (m = transform index, kC columns, row stride kC).
+// out[a][c] = sum_m S[a][m] x[m][c].  x is folded in place.
+template <class T>
+__device__ void tile_transform_cm(T *x, T *out, int N, const T *tab) {
+    FoldDims fd(N);
+    for (int idx = threadIdx.x; idx < fd.H * kC; idx += blockDim.x) {
+        int mp = idx / kC, c = idx % kC;
+        T a = x[mp * kC + c], b = x[(N - 1 - mp) * kC + c];
+        x[mp * kC + c] = a + b;
+        x[(N - 1 - mp) * kC + c] = a - b;
+    }
+    __syncthreads();
+    const int nabE = fd.NEp / 4, nabO = fd.NOp / 4;
+    const int ntask = (nabE + nabO) * (kC / 4);
+    for (int t = threadIdx.x; t < ntask; t += blockDim.x) {
+        int cb = t % (kC / 4), ab = t / (kC / 4);
+        bool even = ab < nabE;  // output a0 even <=> a odd <=> folded sums
+        int abp = even ? ab : ab - nabE;
+        const T *S = even ? tab + 4 * abp : tab + fd.offO() + 4 * abp;
+        int ld = even ? fd.NEp : fd.NOp;
+        T acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
+        for (int mp = 0; mp < fd.H; ++mp) {
+            int row = even ? mp : N - 1 - mp;
+            V4<T> xv = ld4(x + row * kC + 4 * cb);
+            V4<T> sv = ldg4(S + (size_t)mp * ld);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(sv.v[i], xv.v[j], acc[i][j]);
+        }
+        if (even && (N & 1)) {
+            V4<T> xv = ld4(x + fd.H * kC + 4 * cb);
+            V4<T> sv = ldg4(S + (size_t)fd.H * ld);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(sv.v[i], xv.v[j], acc[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int a0 = even ? 2 * (4 * abp + i) : 2 * (4 * abp + i) + 1;
+            if (a0 < N) st4(out + a0 * kC + 4 * cb, acc[i]);
+        }
+    }
+    __syncthreads();
+}
+
+// Row-major tile: x[r][m] (kC rows, row stride ld = N + 1).
+// out[r][a] = sum_m S[a][m] x[r][m].  x is folded in place.
+template <class T>
+__device__ void tile_transform_rm(T *x, T *out, int N, int ld, const T *tab) {
+    FoldDims fd(N);
+    for (int idx = threadIdx.x; idx < fd.H * kC; idx += blockDim.x) {
+        int r = idx / fd.H, mp = idx % fd.H;
+        T a = x[r * ld + mp], b = x[r * ld + N - 1 - mp];
+        x[r * ld + mp] = a + b;
+        x[r * ld + N - 1 - mp] = a - b;
+    }
+    __syncthreads();
+    const int nabE = fd.NEp / 4, nabO = fd.NOp / 4;
+    const int ntask = (nabE + nabO) * (kC / 4);
+    for (int t = threadIdx.x; t < ntask; t += blockDim.x) {
+        int rb = t % (kC / 4), ab = t / (kC / 4);
+        bool even = ab < nabE;
+        int abp = even ? ab : ab - nabE;
+        const T *S = even ? tab + 4 * abp : tab + fd.offO() + 4 * abp;
+        int lds = even ? fd.NEp : fd.NOp;
+        T acc[4][4];  // [row][a]
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
+        const T *xr = x + 4 * rb * ld;
+        for (int mp = 0; mp < fd.H; ++mp) {
+            int col = even ? mp : N - 1 - mp;
+            V4<T> sv = ldg4(S + (size_t)mp * lds);
+            T xv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) xv[i] = xr[i * ld + col];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(xv[i], sv.v[j], acc[i][j]);
+        }
+        if (even && (N & 1)) {
+            V4<T> sv = ldg4(S + (size_t)fd.H * lds);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                T xm = xr[i * ld + fd.H];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(xm, sv.v[j], acc[i][j]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int a0 = even ? 2 * (4 * abp + j) : 2 * (4 * abp + j) + 1;
+            if (a0 < N) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) out[(4 * rb + i) * ld + a0] = acc[i][j];
+            }
+        }
+    }
+    __syncthreads();
+}
+
+template <class T>
+__device__ __forceinline__ bool rhs_skipped(const ApRhs<T> &r, const int *flag) {
+    return r.cond && flag && *flag == 0;
+}
+
+struct PassArgs {
+    int N, B;
+    double h, sigma, fscale;
+    const double *sigma_dev, *fscale_dev;
+    const int *cond_flag;
+    int mask_f, mask_out;
+    const uint8_t *labels;
+    const int *shell, *shell_nb, *rp_shell, *gin, *rp_gin;
+};
+
+// Pass 1: right-hand side + forward transform along k.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_pass_k_fwd(PassArgs a, const ApRhs<T> *rhs, T *work,
+                                                         const T *tab) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = a.N, ld = N + 1;
+    const int b = blockIdx.y;
+    ApRhs<T> r = rhs[b];
+    if (rhs_skipped(r, a.cond_flag)) return;
+    T *x = reinterpret_cast<T *>(smem_raw);
+    T *out = x + kC * ld;
+    const int64_t nrows = (int64_t)N * N;
+    const int64_t R0 = (int64_t)blockIdx.x * kC;
+    const double sig = a.sigma_dev ? *a.sigma_dev : a.sigma;
+    const T fs = (T)(a.fscale_dev ? *a.fscale_dev : a.fscale);
+    for (int idx = threadIdx.x; idx < kC * N; idx += blockDim.x) {
+        int rr = idx / N, k = idx % N;
+        int64_t R = R0 + rr;
+        T v = (T)0;
+        if (R < nrows && r.f) {
+            int64_t p = R * N + k;
+            v = fs * r.f[p];
+            if (a.mask_f && !(a.labels[p] & DPM_LBL_MPLUS)) v = (T)0;
+        }
+        x[rr * ld + k] = v;
+    }
+    __syncthreads();
+    if (r.dens) {
+        const T cdiag = (T)(sig + 6.0 / (a.h * a.h));
+        const T coff = (T)(1.0 / (a.h * a.h));
+        int64_t Rend = R0 + kC < nrows ? R0 + kC : nrows;
+        int e0 = a.rp_shell[R0], e1 = a.rp_shell[Rend];
+        for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+            int p = a.shell[e];
+            const int *nb = a.shell_nb + 8 * (size_t)e;
+            T s = (T)0;
+#pragma unroll
+            for (int t = 1; t < 7; ++t) {
+                int g = nb[t];
+                if (g >= 0) s += r.dens[g];
+            }
+            T self = nb[0] >= 0 ? r.dens[nb[0]] : (T)0;
+            int rr = (int)(p / N - R0), k = p % N;
+            x[rr * ld + k] += cdiag * self - coff * s;
+        }
+        __syncthreads();
+    }
+    tile_transform_rm<T>(x, out, N, ld, tab);
+    T *w = work + (size_t)b * nrows * N;
+    for (int idx = threadIdx.x; idx < kC * N; idx += blockDim.x) {
+        int rr = idx / N, k = idx % N;
+        int64_t R = R0 + rr;
+        if (R < nrows) w[R * N + k] = out[rr * ld + k];
+    }
+}
+
+// Passes 2 and 4: transform along j for tiles [j][kc..kc+32) at fixed i.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_pass_j(PassArgs a, const ApRhs<T> *rhs, T *work,
+                                                     const T *tab) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = a.N;
+    const int b = blockIdx.y;
+    if (rhs_skipped(rhs[b], a.cond_flag)) return;
+    const int nkc = (N + kC - 1) / kC;
+    const int i = blockIdx.x / nkc, kc = (blockIdx.x % nkc) * kC;
+    T *x = reinterpret_cast<T *>(smem_raw);
+    T *out = x + N * kC;
+    T *w = work + (size_t)b * N * N * N + (size_t)i * N * N;
+    for (int idx = threadIdx.x; idx < N * kC; idx += blockDim.x) {
+        int j = idx / kC, c = idx % kC;
+        x[j * kC + c] = (kc + c < N) ? w[(size_t)j * N + kc + c] : (T)0;
+    }
+    __syncthreads();
+    tile_transform_cm<T>(x, out, N, tab);
+    for (int idx = threadIdx.x; idx < N * kC; idx += blockDim.x) {
+        int j = idx / kC, c = idx % kC;
+        if (kc + c < N) w[(size_t)j * N + kc + c] = out[j * kC + c];
+    }
+}
+
+// Pass 3: along i, forward, scale/lambda, inverse; tiles [i][kc..kc+32) at fixed j.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_pass_i(PassArgs a, const ApRhs<T> *rhs, T *work,
+                                                     const T *tab) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = a.N;
+    const int b = blockIdx.y;
+    if (rhs_skipped(rhs[b], a.cond_flag)) return;
+    const int nkc = (N + kC - 1) / kC;
+    const int j = blockIdx.x / nkc, kc = (blockIdx.x % nkc) * kC;
+    T *x = reinterpret_cast<T *>(smem_raw);
+    T *out = x + N * kC;
+    T *wt = out + N * kC;  // N weights (4/h^2) sin^2(pi (n+1)/(2(N+1)))
+    T *w = work + (size_t)b * N * N * N + (size_t)j * N;
+    const size_t si = (size_t)N * N;
+    const double sig = a.sigma_dev ? *a.sigma_dev : a.sigma;
+    const T w4 = (T)(4.0 / (a.h * a.h));
+    const T *s2 = tab + FoldDims(N).offW();
+    for (int n = threadIdx.x; n < N; n += blockDim.x) wt[n] = w4 * s2[n];
+    for (int idx = threadIdx.x; idx < N * kC; idx += blockDim.x) {
+        int i = idx / kC, c = idx % kC;
+        x[i * kC + c] = (kc + c < N) ? w[(size_t)i * si + kc + c] : (T)0;
+    }
+    __syncthreads();
+    tile_transform_cm<T>(x, out, N, tab);
+    const double sc = 2.0 / (N + 1);
+    const T scale = (T)(sc * sc * sc);
+    const T sgT = (T)sig;
+    for (int idx = threadIdx.x; idx < N * kC; idx += blockDim.x) {
+        int ai = idx / kC, c = idx % kC;
+        int kk = kc + c < N ? kc + c : N - 1;
+        T lam = sgT + (wt[ai] + wt[j] + wt[kk]);
+        x[ai * kC + c] = out[ai * kC + c] * (scale / lam);
+    }
+    __syncthreads();
+    tile_transform_cm<T>(x, out, N, tab);
+    for (int idx = threadIdx.x; idx < N * kC; idx += blockDim.x) {
+        int i = idx / kC, c = idx % kC;
+        if (kc + c < N) w[(size_t)i * si + kc + c] = out[i * kC + c];
+    }
+}
+
+// Pass 5: inverse along k, then the dense output (masked to N^+) and/or the
+// trace on gamma_in.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_pass_k_inv(PassArgs a, const ApRhs<T> *rhs,
+                                                         const T *work, const T *tab) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = a.N, ld = N + 1;
+    const int b = blockIdx.y;
+    ApRhs<T> r = rhs[b];
+    if (rhs_skipped(r, a.cond_flag)) return;
+    T *x = reinterpret_cast<T *>(smem_raw);
+    T *out = x + kC * ld;
+    const int64_t nrows = (int64_t)N * N;
+    const int64_t R0 = (int64_t)blockIdx.x * kC;
+    const T *w = work + (size_t)b * nrows * N;
+    for (int idx = threadIdx.x; idx < kC * N; idx += blockDim.x) {
+        int rr = idx / N, k = idx % N;
+        int64_t R = R0 + rr;
+        x[rr * ld + k] = R < nrows ? w[R * N + k] : (T)0;
+    }
+    __syncthreads();
+    tile_transform_rm<T>(x, out, N, ld, tab);
+    if (r.out_dense) {
+        for (int idx = threadIdx.x; idx < kC * N; idx += blockDim.x) {
+            int rr = idx / N, k = idx % N;
+            int64_t R = R0 + rr;
+            if (R < nrows) {
+                int64_t p = R * N + k;
+                T v = out[rr * ld + k];
+                if (a.mask_out && !(a.labels[p] & (DPM_LBL_MPLUS | DPM_LBL_GEX))) v = (T)0;
+                r.out_dense[p] = v;
+            }
+        }
+    }
+    if (r.out_trace) {
+        int64_t Rend = R0 + kC < nrows ? R0 + kC : nrows;
+        int e0 = a.rp_gin[R0], e1 = a.rp_gin[Rend];
+        for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+            int p = a.gin[e];
+            int rr = (int)(p / N - R0), k = p % N;
+            r.out_trace[e] = out[rr * ld + k];
+        }
+    }
+}
+
+template <class T> size_t smem_rows(int N) { return 2 * (size_t)kC * (N + 1) * sizeof(T); }
+template <class T> size_t smem_cols(int N) { return (2 * (size_t)N * kC + N) * sizeof(T); }
+
+template <class T> int set_smem_limits(int N) {
+    static int configured[2] = {0, 0};
+    int slot = sizeof(T) == 8;
+    size_t need = smem_rows<T>(N) > smem_cols<T>(N) ? smem_rows<T>(N) : smem_cols<T>(N);
+    if ((size_t)configured[slot] >= need) return DPM_OK;
+    int v = 227 * 1024;
+    DPM_CUDA(cudaFuncSetAttribute(k_pass_k_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+    DPM_CUDA(cudaFuncSetAttribute(k_pass_j<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+    DPM_CUDA(cudaFuncSetAttribute(k_pass_i<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+    DPM_CUDA(cudaFuncSetAttribute(k_pass_k_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+    configured[slot] = v;
+    return DPM_OK;
+}
+
+}  // namespace
+
+void ap_params_from_index(ApParams &p, const GridIndex &gi) {
+    p.labels = gi.labels.as<uint8_t>();
+    p.shell = gi.shell.as<int>();
+    p.shell_nb = gi.shell_nb.as<int>();
+    p.rp_shell = gi.rp_shell.as<int>();
+    p.gin = gi.gin.as<int>();
+    p.rp_gin = gi.rp_gin.as<int>();
+}
+
+template <class T>
+int ap_solve_simt(const ApParams &p, const ApRhs<T> *rhs_dev, T *work, cudaStream_t s) {
+    const int N = p.N;
+    if (N < 2 || N > 256) { set_error("AP solve: N=%d outside [2, 256]", N); return DPM_EINVAL; }
+    if (p.B < 1 || p.B > 65535) { set_error("AP solve: B=%d outside [1, 65535]", p.B); return DPM_EINVAL; }
+    const T *tab = dst_fold_table<T>(N);
+    if (!tab) { set_error("AP solve: could not create the DST table"); return DPM_ENOMEM; }
+    DPM_RET(set_smem_limits<T>(N));
+    PassArgs a{N, p.B, p.h, p.sigma, p.fscale, p.sigma_dev, p.fscale_dev, p.cond_flag, p.mask_f,
+               p.mask_out, p.labels, p.shell, p.shell_nb, p.rp_shell, p.gin, p.rp_gin};
+    const int64_t nrows = (int64_t)N * N;
+    dim3 grow((unsigned)((nrows + kC - 1) / kC), p.B);
+    dim3 gcol((unsigned)(N * ((N + kC - 1) / kC)), p.B);
+    const bool f64 = sizeof(T) == 8;
+    {
+        DPM_PROF(f64 ? "ap_simt64_pass_k_fwd" : "ap_simt32_pass_k_fwd", s);
+        k_pass_k_fwd<T><<<grow, kThreads, smem_rows<T>(N), s>>>(a, rhs_dev, work, tab);
+        DPM_LAUNCHED();
+    }
+    {
+        DPM_PROF(f64 ? "ap_simt64_pass_j" : "ap_simt32_pass_j", s);
+        k_pass_j<T><<<gcol, kThreads, smem_cols<T>(N), s>>>(a, rhs_dev, work, tab);
+        DPM_LAUNCHED();
+    }
+    {
+        DPM_PROF(f64 ? "ap_simt64_pass_i" : "ap_simt32_pass_i", s);
+        k_pass_i<T><<<gcol, kThreads, smem_cols<T>(N), s>>>(a, rhs_dev, work, tab);
+        DPM_LAUNCHED();
+    }
+    {
+        DPM_PROF(f64 ? "ap_simt64_pass_j" : "ap_simt32_pass_j", s);
+        k_pass_j<T><<<gcol, kThreads, smem_cols<T>(N), s>>>(a, rhs_dev, work, tab);
+        DPM_LAUNCHED();
+    }
+    {
+        DPM_PROF(f64 ? "ap_simt64_pass_k_inv" : "ap_simt32_pass_k_inv", s);
+        k_pass_k_inv<T><<<grow, kThreads, smem_rows<T>(N), s>>>(a, rhs_dev, work, tab);
+        DPM_LAUNCHED();
+    }
+    return DPM_OK;
+}
+
+template int ap_solve_simt<float>(const ApParams &, const ApRhs<float> *, float *, cudaStream_t);
+template int ap_solve_simt<double>(const ApParams &, const ApRhs<double> *, double *, cudaStream_t);
+
+}  // namespace dpm

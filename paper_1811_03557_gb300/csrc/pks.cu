@@ -1,0 +1,365 @@
+// PKS step kernels and the BEP assembly / extension helpers.
+//
+//  * k_flux: the convective term g of eq. discrete_convective_term on M^+,
+//    with face gradients of c by eq. c-central-difference, face densities
+//    upwinded (eq. upwind_approximation) from the piecewise-linear
+//    reconstruction (eq. truncated_taylor_expansion) with minmod slopes
+//    (eq. slope_limiter); a slope whose stencil leaves N^+ is 0.  Then the
+//    IMEX right-hand sides of eq. discrete_chemotaxis (alpha = gamma_rho =
+//    gamma_c = 1): f_rho = rho - dt g, f_c = (1 - dt) c + dt rho.
+//  * k_cfl: max over M^+ of |grad_h c| at the j +- 1/2 faces per axis
+//    (eq. cfl_condition).
+//  * k_diag: mass, max/min, second moment (eq. sd-norm:second-moment) and
+//    free energy (eq. sd-norm:free-energy), per-block FP64 partial sums
+//    reduced in a fixed order.
+//  * extension: u_gamma = sum C0 phi + beta (d^2/2) sum C2 phi + d g_N
+//    (eqs. extension_operator, extension_operator_recast), one warp per node
+//    of gamma with a shuffle reduction over the harmonics.
+#include <math.h>
+
+#include "dpm_internal.cuh"
+
+namespace dpm {
+namespace {
+
+__device__ __forceinline__ bool in_np(uint8_t l) { return l & (DPM_LBL_MPLUS | DPM_LBL_GEX); }
+
+template <class T> __device__ __forceinline__ T minmod3(T a, T b, T c) {
+    if (a > 0 && b > 0 && c > 0) return fmin(a, fmin(b, c));
+    if (a < 0 && b < 0 && c < 0) return fmax(a, fmax(b, c));
+    return (T)0;
+}
+
+// slope of rho at node q along stride st (0 when q or a neighbour is off N^+)
+template <class T>
+__device__ __forceinline__ T slope_at(const T *rho, const uint8_t *lab, int64_t q, int64_t st,
+                                      int coord, int N, T inv_h) {
+    if (coord < 1 || coord > N - 2) return (T)0;
+    if (!in_np(lab[q]) || !in_np(lab[q + st]) || !in_np(lab[q - st])) return (T)0;
+    T r0 = rho[q], rp = rho[q + st], rm = rho[q - st];
+    return minmod3<T>((T)2 * (rp - r0) * inv_h, (rp - rm) * ((T)0.5 * inv_h),
+                      (T)2 * (r0 - rm) * inv_h);
+}
+
+template <class T>
+__global__ void k_flux(int N, T h, T chi, double dt_d, const uint8_t *lab, const T *rho,
+                       const T *c, T *f_rho, T *f_c) {
+    const int64_t n3 = (int64_t)N * N * N;
+    const T dt = (T)dt_d, inv_h = (T)1 / h, half_h = (T)0.5 * h;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n3;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        if (!(lab[p] & DPM_LBL_MPLUS)) {
+            f_rho[p] = (T)0;
+            f_c[p] = (T)0;
+            continue;
+        }
+        int coord[3] = {(int)(p / ((int64_t)N * N)), (int)((p / N) % N), (int)(p % N)};
+        int64_t st[3] = {(int64_t)N * N, (int64_t)N, 1};
+        T r0 = rho[p], c0 = c[p];
+        T g = (T)0;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            int64_t s = st[ax];
+            int cc = coord[ax];
+            // M^+ is >= 2 nodes from the faces, so p +- s and p +- 2s exist
+            T sp = slope_at<T>(rho, lab, p, s, cc, N, inv_h);
+            T sL = slope_at<T>(rho, lab, p - s, s, cc - 1, N, inv_h);
+            T sR = slope_at<T>(rho, lab, p + s, s, cc + 1, N, inv_h);
+            T gp = (c[p + s] - c0) * inv_h;  // grad c at j+1/2
+            T gm = (c0 - c[p - s]) * inv_h;  // grad c at j-1/2
+            T east = r0 + half_h * sp, west = r0 - half_h * sp;
+            T rho_p = gp > 0 ? east : rho[p + s] - half_h * sR;
+            T rho_m = gm > 0 ? rho[p - s] + half_h * sL : west;
+            g += (chi * rho_p * gp - chi * rho_m * gm) * inv_h;
+        }
+        f_rho[p] = r0 - dt * g;
+        f_c[p] = ((T)1 - dt) * c0 + dt * r0;
+    }
+}
+
+// gmax[ax] = max |c(p+e) - c(p)|, |c(p) - c(p-e)| over M^+ (as float bits).
+template <class T>
+__global__ void k_cfl(int N, const uint8_t *lab, const T *c, unsigned int *gmax) {
+    const int64_t n3 = (int64_t)N * N * N;
+    float m[3] = {0.f, 0.f, 0.f};
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n3;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        if (!(lab[p] & DPM_LBL_MPLUS)) continue;
+        int64_t st[3] = {(int64_t)N * N, (int64_t)N, 1};
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            float a = fabsf((float)(c[p + st[ax]] - c[p]));
+            float b = fabsf((float)(c[p] - c[p - st[ax]]));
+            m[ax] = fmaxf(m[ax], fmaxf(a, b));
+        }
+    }
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        float v = m[ax];
+        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(gmax + ax, __float_as_uint(v));
+    }
+}
+
+constexpr int kDiagThreads = 256;
+constexpr int kDiag = 6;  // mass, max rho, min rho, min c, m2, free energy
+
+template <class T>
+__global__ void k_diag(int N, double lo, double h, const uint8_t *lab, const T *rho, const T *c,
+                       double *part) {
+    const int64_t n3 = (int64_t)N * N * N;
+    double v[kDiag] = {0.0, -INFINITY, INFINITY, INFINITY, 0.0, 0.0};
+    const T inv8h2 = (T)(1.0 / (8.0 * h * h));
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n3;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        uint8_t l = lab[p];
+        if (!in_np(l)) continue;
+        T r = rho[p], cc = c[p];
+        v[2] = fmin(v[2], (double)r);
+        v[3] = fmin(v[3], (double)cc);
+        if (!(l & DPM_LBL_MPLUS)) continue;
+        int i = (int)(p / ((int64_t)N * N)), j = (int)((p / N) % N), k = (int)(p % N);
+        double x = lo + (double)(i + 1) * h, y = lo + (double)(j + 1) * h,
+               z = lo + (double)(k + 1) * h;
+        v[0] += (double)r;
+        v[1] = fmax(v[1], (double)r);
+        v[4] += (x * x + y * y + z * z) * (double)r;
+        int64_t st[3] = {(int64_t)N * N, (int64_t)N, 1};
+        T g2 = (T)0;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            T d = c[p + st[ax]] - c[p - st[ax]];
+            g2 += d * d;
+        }
+        T rlr = r > (T)0 ? r * log(r) : (T)0;
+        v[5] += (double)(rlr - r * cc + (T)0.5 * cc * cc + g2 * inv8h2);
+    }
+    __shared__ double sh[kDiag][kDiagThreads / 32];
+#pragma unroll
+    for (int q = 0; q < kDiag; ++q) {
+        double x = v[q];
+        for (int o = 16; o > 0; o >>= 1) {
+            double y = __shfl_xor_sync(0xffffffffu, x, o);
+            x = (q == 1) ? fmax(x, y) : (q == 2 || q == 3) ? fmin(x, y) : x + y;
+        }
+        if ((threadIdx.x & 31) == 0) sh[q][threadIdx.x >> 5] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < kDiag) {
+        int q = threadIdx.x;
+        double x = sh[q][0];
+        for (int w = 1; w < kDiagThreads / 32; ++w)
+            x = (q == 1) ? fmax(x, sh[q][w]) : (q == 2 || q == 3) ? fmin(x, sh[q][w]) : x + sh[q][w];
+        part[blockIdx.x * kDiag + q] = x;
+    }
+}
+
+__global__ void k_diag_final(int nblk, double h, const double *part, double *out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double v[kDiag] = {0.0, -INFINITY, INFINITY, INFINITY, 0.0, 0.0};
+    for (int b = 0; b < nblk; ++b) {
+        const double *pp = part + b * kDiag;
+        v[0] += pp[0];
+        v[1] = fmax(v[1], pp[1]);
+        v[2] = fmin(v[2], pp[2]);
+        v[3] = fmin(v[3], pp[3]);
+        v[4] += pp[4];
+        v[5] += pp[5];
+    }
+    double h3 = h * h * h;
+    out[0] = h3 * v[0];
+    out[1] = v[1];
+    out[2] = v[2];
+    out[3] = v[3];
+    out[4] = h3 * v[4];
+    out[5] = h3 * v[5];
+}
+
+__device__ __forceinline__ double gauss(const dpm_gaussian &g, double x, double y, double z) {
+    double dx = x - g.center[0], dy = y - g.center[1], dz = z - g.center[2];
+    return g.amp * exp(-g.alpha * (dx * dx + dy * dy + g.zscale * dz * dz));
+}
+
+template <class T>
+__global__ void k_init_nodes(int N, double lo, double h, const uint8_t *lab, dpm_gaussian g0,
+                             dpm_gaussian g1, T *rho, T *c) {
+    const int64_t n3 = (int64_t)N * N * N;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n3;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        T a = (T)0, b = (T)0;
+        if (lab[p] & DPM_LBL_MPLUS) {
+            int i = (int)(p / ((int64_t)N * N)), j = (int)((p / N) % N), k = (int)(p % N);
+            double x = lo + (double)(i + 1) * h, y = lo + (double)(j + 1) * h,
+                   z = lo + (double)(k + 1) * h;
+            a = (T)gauss(g0, x, y, z);
+            b = (T)gauss(g1, x, y, z);
+        }
+        rho[p] = a;
+        c[p] = b;
+    }
+}
+
+template <class T>
+__global__ void k_init_gex(int n, const int *gex, const int *gex_pos, const double *foot,
+                           dpm_gaussian g0, dpm_gaussian g1, T *rho, T *c) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    int p = gex[e], g = gex_pos[e];
+    const double *x = foot + 3 * (size_t)g;
+    rho[p] = (T)gauss(g0, x[0], x[1], x[2]);
+    c[p] = (T)gauss(g1, x[0], x[1], x[2]);
+}
+
+template <class T>
+__global__ void k_mask_copy(int64_t n3, const uint8_t *lab, const T *src, T *dst) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n3;
+         p += (int64_t)gridDim.x * blockDim.x)
+        dst[p] = in_np(lab[p]) ? src[p] : (T)0;
+}
+
+template <class T>
+__global__ void k_assemble(int64_t total, const double *psi_in, const T *trace, double *A) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x)
+        A[i] = psi_in[i] - (double)trace[i];
+}
+
+// One warp per node of gamma: u[q][g] = sum_nu C0 phi + beta d^2/2 sum_nu C2 phi + d gN.
+template <class T>
+__global__ void k_extend(int n, int nsh, int beta, const double *phi, const double *dist,
+                         const double *C, int ldc, const double *neumann, T *dens, int ldd,
+                         int nr, int clamp) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const double *ph = phi + (size_t)warp * nsh;
+    double d = dist[warp];
+    for (int q = 0; q < nr; ++q) {
+        const double *cq = C + (size_t)q * ldc;
+        double s0 = 0.0, s2 = 0.0;
+        for (int nu = lane; nu < nsh; nu += 32) {
+            double f = ph[nu];
+            s0 += cq[nu] * f;
+            if (beta) s2 += cq[nsh + nu] * f;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        if (lane == 0) {
+            double u = s0 + 0.5 * d * d * s2;
+            if (neumann) u += d * neumann[warp];
+            if (clamp && u < 0.0) u = 0.0;
+            dens[(size_t)q * ldd + warp] = (T)u;
+        }
+    }
+}
+
+int blocks_for(int64_t n, int t) {
+    int64_t b = (n + t - 1) / t;
+    return (int)(b > 152 * 32 ? 152 * 32 : (b < 1 ? 1 : b));
+}
+
+}  // namespace
+
+template <class T>
+int assemble_bep(const double *psi_in, const T *trace, double *A, int64_t m, int ncol,
+                 const int *cond_flag, cudaStream_t s) {
+    (void)cond_flag;
+    int64_t total = m * ncol;
+    k_assemble<T><<<blocks_for(total, 256), 256, 0, s>>>(total, psi_in, trace, A);
+    DPM_LAUNCHED();
+    return DPM_OK;
+}
+template int assemble_bep<float>(const double *, const float *, double *, int64_t, int, const int *,
+                                 cudaStream_t);
+template int assemble_bep<double>(const double *, const double *, double *, int64_t, int,
+                                  const int *, cudaStream_t);
+
+template <class T>
+int extend_density(const GammaGeom &gg, int64_t n_gamma, int beta, const double *C, int ldc,
+                   const double *neumann, T *dens, int ldd, int nr, int clamp, cudaStream_t s) {
+    int64_t threads = n_gamma * 32;
+    k_extend<T><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+        (int)n_gamma, gg.nsh, beta, gg.phi.as<double>(), gg.dist.as<double>(), C, ldc, neumann,
+        dens, ldd, nr, clamp);
+    DPM_LAUNCHED();
+    return DPM_OK;
+}
+template int extend_density<float>(const GammaGeom &, int64_t, int, const double *, int,
+                                   const double *, float *, int, int, int, cudaStream_t);
+template int extend_density<double>(const GammaGeom &, int64_t, int, const double *, int,
+                                    const double *, double *, int, int, int, cudaStream_t);
+
+// ---- PKS helpers used by the API layer ------------------------------------
+template <class T>
+int pks_flux(int N, double h, double chi, double dt, const uint8_t *lab, const T *rho, const T *c,
+             T *f_rho, T *f_c, cudaStream_t s) {
+    int64_t n3 = (int64_t)N * N * N;
+    k_flux<T><<<blocks_for(n3, 256), 256, 0, s>>>(N, (T)h, (T)chi, dt, lab, rho, c, f_rho, f_c);
+    DPM_LAUNCHED();
+    return DPM_OK;
+}
+template int pks_flux<float>(int, double, double, double, const uint8_t *, const float *,
+                             const float *, float *, float *, cudaStream_t);
+template int pks_flux<double>(int, double, double, double, const uint8_t *, const double *,
+                              const double *, double *, double *, cudaStream_t);
+
+template <class T>
+int pks_cfl(int N, const uint8_t *lab, const T *c, unsigned int *gmax, cudaStream_t s) {
+    int64_t n3 = (int64_t)N * N * N;
+    DPM_CUDA(cudaMemsetAsync(gmax, 0, 3 * sizeof(unsigned int), s));
+    k_cfl<T><<<blocks_for(n3, 256), 256, 0, s>>>(N, lab, c, gmax);
+    DPM_LAUNCHED();
+    return DPM_OK;
+}
+template int pks_cfl<float>(int, const uint8_t *, const float *, unsigned int *, cudaStream_t);
+template int pks_cfl<double>(int, const uint8_t *, const double *, unsigned int *, cudaStream_t);
+
+int pks_diag_blocks(int N) { return blocks_for((int64_t)N * N * N, kDiagThreads); }
+
+template <class T>
+int pks_diag(int N, double lo, double h, const uint8_t *lab, const T *rho, const T *c,
+             double *part, double *out, cudaStream_t s) {
+    int nb = pks_diag_blocks(N);
+    k_diag<T><<<nb, kDiagThreads, 0, s>>>(N, lo, h, lab, rho, c, part);
+    DPM_LAUNCHED();
+    k_diag_final<<<1, 32, 0, s>>>(nb, h, part, out);
+    DPM_LAUNCHED();
+    return DPM_OK;
+}
+template int pks_diag<float>(int, double, double, const uint8_t *, const float *, const float *,
+                             double *, double *, cudaStream_t);
+template int pks_diag<double>(int, double, double, const uint8_t *, const double *,
+                              const double *, double *, double *, cudaStream_t);
+
+template <class T>
+int pks_init(const GridIndex &gi, const GammaGeom &gg, const dpm_gaussian &g0,
+             const dpm_gaussian &g1, T *rho, T *c, cudaStream_t s) {
+    int64_t n3 = (int64_t)gi.N * gi.N * gi.N;
+    k_init_nodes<T><<<blocks_for(n3, 256), 256, 0, s>>>(gi.N, gi.lo, gi.h, gi.labels.as<uint8_t>(),
+                                                        g0, g1, rho, c);
+    DPM_LAUNCHED();
+    if (gi.n_gex > 0) {
+        k_init_gex<T><<<(unsigned)((gi.n_gex + 255) / 256), 256, 0, s>>>(
+            (int)gi.n_gex, gi.gex.as<int>(), gi.gex_pos.as<int>(), gg.foot.as<double>(), g0, g1,
+            rho, c);
+        DPM_LAUNCHED();
+    }
+    return DPM_OK;
+}
+template int pks_init<float>(const GridIndex &, const GammaGeom &, const dpm_gaussian &,
+                             const dpm_gaussian &, float *, float *, cudaStream_t);
+template int pks_init<double>(const GridIndex &, const GammaGeom &, const dpm_gaussian &,
+                              const dpm_gaussian &, double *, double *, cudaStream_t);
+
+template <class T>
+int mask_copy(int N, const uint8_t *lab, const T *src, T *dst, cudaStream_t s) {
+    int64_t n3 = (int64_t)N * N * N;
+    k_mask_copy<T><<<blocks_for(n3, 256), 256, 0, s>>>(n3, lab, src, dst);
+    DPM_LAUNCHED();
+    return DPM_OK;
+}
+template int mask_copy<float>(int, const uint8_t *, const float *, float *, cudaStream_t);
+template int mask_copy<double>(int, const uint8_t *, const double *, double *, cudaStream_t);
+
+}  // namespace dpm

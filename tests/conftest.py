@@ -11,3 +11,18 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long CPU test")
+
+
+@pytest.fixture(scope="session")
+def ctx():
+    """A libdpm context on cuda:0 (GPU tests only)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1811_03557_gb300 import abi, build
+    if not os.path.exists(abi.LIB_PATH):
+        build.build()
+    torch.cuda.init()
+    h = abi.dpm_ctx_create(0)
+    yield h
+    abi.dpm_ctx_destroy(h)
