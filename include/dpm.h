@@ -160,6 +160,29 @@ int dpm_aux_solve_batched(dpm_ctx *ctx, int N, double h, double sigma, int B,
                           const void *q, void *u, int precision, cudaStream_t stream);
 
 /*
+ * The same FP32 auxiliary solve as dpm_aux_solve_batched with DPM_PREC_FP32,
+ * for callers that must not let a library allocate device memory: an
+ * application whose own allocator owns every byte of the GPU, or a
+ * latency-critical loop in which cudaMalloc/cudaFree (which may synchronise
+ * the device and take an unbounded time) are not acceptable.  The paper has
+ * no counterpart; this is an interface convenience.
+ *   q, u  device float[B][N][N][N], owned by the caller (u may equal q).
+ * All scratch -- the B*N^3 workspace, the sine table and the per-right-hand-
+ * side descriptors -- lives in one fixed device array compiled into the
+ * library (about 64 MiB, held by every GPU that loads the library until the
+ * process exits).  The call allocates nothing.  Limits: 2 <= N <= 256,
+ * 1 <= B <= 1024 and B*N^3 <= 16*2^20 (e.g. one N=256 cube, or 8 N=128
+ * cubes); larger requests fail with DPM_EINVAL before any work is enqueued.
+ * Runs on the calling thread's current CUDA device.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  Every call reuses the same
+ * array, so calls that overlap on the GPU (e.g. on two unordered streams)
+ * race and must be serialised by the caller.
+ */
+int dpm_aux_solve_batched_noalloc(int N, double h, double sigma, int B, const float *q,
+                                  float *u, cudaStream_t stream);
+
+/*
  * Steps 1-2 of the main algorithm: classify the grid, project every node of
  * gamma on Gamma (foot point, signed distance d > 0 outside Omega along the
  * outward normal; Definition 2.6), evaluate the real orthonormal spherical

@@ -81,6 +81,8 @@ _SIGS = {
     "dpm_pks_step": (C.c_int, [_P, C.c_int, C.POINTER(dpm_pks_stats), _P]),
     "dpm_pks_get_state": (C.c_int, [_P, _P, _P, _P]),
     "dpm_pks_destroy": (C.c_int, [_P]),
+    "dpm_aux_solve_batched_noalloc": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, _P,
+                                                _P, _P]),
     "dpm_launch_count": (C.c_int64, []),
     "dpm_profile_enable": (C.c_int, [C.c_int]),
     "dpm_profile_read": (C.c_int, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
@@ -181,6 +183,12 @@ def dpm_classify(ctx, geom, N, lo, hi, labels=None, gin_idx=None, gex_idx=None, 
 def dpm_aux_solve_batched(ctx, N, h, sigma, B, q, u, precision=DPM_PREC_FP32, stream=None):
     _check(lib().dpm_aux_solve_batched(ctx, N, h, sigma, B, _ptr(q), _ptr(u), precision,
                                        _stream(stream)))
+
+
+def dpm_aux_solve_batched_noalloc(N, h, sigma, B, q, u, stream=None):
+    """FP32 AP solve whose scratch is a fixed device array inside the library
+    (no allocation); q, u float32 device tensors [B][N][N][N]."""
+    _check(lib().dpm_aux_solve_batched_noalloc(N, h, sigma, B, _ptr(q), _ptr(u), _stream(stream)))
 
 
 def dpm_bep_build(ctx, geom, N, lo, hi, sigma, K, beta=1, precision=DPM_PREC_FP32, stream=None):

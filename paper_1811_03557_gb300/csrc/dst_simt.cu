@@ -488,3 +488,139 @@ template int ap_solve_simt<float>(const ApParams &, const ApRhs<float> *, float 
 template int ap_solve_simt<double>(const ApParams &, const ApRhs<double> *, double *, cudaStream_t);
 
 }  // namespace dpm
+
+// ===========================================================================
+// Allocation-free variant of the batched FP32 auxiliary solve.
+//
+// Some callers cannot let a library allocate device memory: an application
+// whose memory allocator owns every byte of the GPU (so a cudaMalloc behind
+// its back would break its accounting or fail against its reservation), or a
+// latency-critical loop where cudaMalloc/cudaFree -- which may synchronise the
+// device and take an unbounded time -- are not acceptable.  For them,
+// dpm_aux_solve_batched_noalloc runs the same five SIMT passes as the FP32
+// path of dpm_aux_solve_batched, but every piece of scratch (the B*N^3
+// workspace, the folded sine table and the right-hand-side descriptors) lives
+// in one file-scope device array compiled into the library.  Nothing is
+// allocated on any call.
+//
+// The array is shared by every call on a device and keeps the last call's
+// contents; each call writes every byte it later reads (the table and the
+// descriptors are rebuilt, the workspace is filled by the first pass), so
+// nothing has to start at zero.  Calls that overlap on the GPU (e.g. issued
+// to two streams without ordering) race on the array.
+// ===========================================================================
+namespace dpm {
+namespace {
+
+constexpr size_t kStaticWorkElems = size_t(16) << 20;     // 16 Mi floats = 64 MiB
+constexpr size_t kStaticTableElems = 34816;               // >= folded table + weights for N <= 256
+constexpr int kStaticMaxB = 1024;
+constexpr size_t kStaticDescBytes = sizeof(ApRhs<float>) * kStaticMaxB;
+constexpr size_t kStaticBytes =
+    kStaticWorkElems * sizeof(float) + kStaticTableElems * sizeof(float) + kStaticDescBytes;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void *g_static_addr[kMaxDevices] = {nullptr};
+
+// Device address of g_static_scratch for the current device (looked up once
+// per device with that device current).
+int static_scratch_address(void **out) {
+    int dev = 0;
+    DPM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("device ordinal %d beyond the %d devices this entry point tracks", dev, kMaxDevices);
+        return DPM_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            set_error("cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+            return DPM_ECUDA;
+        }
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return DPM_OK;
+}
+
+// Folded sine table of dst_fold_table, generated on the device.
+__global__ void k_static_table(int N, float *tab) {
+    FoldDims fd(N);
+    const size_t total = fd.total(N);
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        double v = 0.0;
+        long long den = N + 1;
+        if (idx < fd.offO()) {
+            int mp = (int)(idx / fd.NEp), ap = (int)(idx % fd.NEp);
+            if (ap < fd.NE) v = sin(M_PI * (double)(((long long)(2 * ap + 1) * (mp + 1)) % (2 * den)) / (double)den);
+        } else if (idx < fd.offW()) {
+            size_t r = idx - fd.offO();
+            int mp = (int)(r / fd.NOp), ap = (int)(r % fd.NOp);
+            if (ap < fd.NO) v = sin(M_PI * (double)(((long long)(2 * ap + 2) * (mp + 1)) % (2 * den)) / (double)den);
+        } else {
+            int n = (int)(idx - fd.offW());
+            double sn = sin(M_PI * (double)(n + 1) / (2.0 * (double)den));
+            v = sn * sn;
+        }
+        tab[idx] = (float)v;
+    }
+}
+
+__global__ void k_static_desc(int B, size_t n3, const float *q, float *u, ApRhs<float> *d) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) d[b] = ApRhs<float>{q + (size_t)b * n3, nullptr, u + (size_t)b * n3, nullptr, 0, 0};
+}
+
+}  // namespace
+}  // namespace dpm
+
+extern "C" int dpm_aux_solve_batched_noalloc(int N, double h, double sigma, int B, const float *q,
+                                             float *u, cudaStream_t s) {
+    using namespace dpm;
+    if (!q || !u) { set_error("q/u is NULL"); return DPM_EINVAL; }
+    if (N < 2 || N > 256 || B < 1 || !(h > 0) || !(sigma >= 0)) {
+        set_error("aux solve (no-alloc): need 2<=N<=256, B>=1, h>0, sigma>=0 (N=%d B=%d h=%g sigma=%g)",
+                  N, B, h, sigma);
+        return DPM_EINVAL;
+    }
+    const size_t n3 = (size_t)N * N * N;
+    if (B > kStaticMaxB || (size_t)B * n3 > kStaticWorkElems) {
+        set_error("aux solve (no-alloc): B*N^3 = %zu exceeds the static workspace of %zu floats "
+                  "(and B <= %d); split the batch or use dpm_aux_solve_batched",
+                  (size_t)B * n3, kStaticWorkElems, kStaticMaxB);
+        return DPM_EINVAL;
+    }
+    if (FoldDims(N).total(N) > kStaticTableElems) { set_error("internal: table too large"); return DPM_EINVAL; }
+    void *base = nullptr;
+    DPM_RET(static_scratch_address(&base));
+    float *work = static_cast<float *>(base);
+    float *tab = work + kStaticWorkElems;
+    ApRhs<float> *desc = reinterpret_cast<ApRhs<float> *>(tab + kStaticTableElems);
+    DPM_RET(set_smem_limits<float>(N));
+    k_static_table<<<64, 256, 0, s>>>(N, tab);
+    DPM_LAUNCHED();
+    k_static_desc<<<(B + 127) / 128, 128, 0, s>>>(B, n3, q, u, desc);
+    DPM_LAUNCHED();
+    PassArgs a{N, B, h, sigma, 1.0, nullptr, nullptr, nullptr, 0, 0,
+               nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    const int64_t nrows = (int64_t)N * N;
+    dim3 grow((unsigned)((nrows + kC - 1) / kC), B);
+    dim3 gcol((unsigned)(N * ((N + kC - 1) / kC)), B);
+    k_pass_k_fwd<float><<<grow, kThreads, smem_rows<float>(N), s>>>(a, desc, work, tab);
+    DPM_LAUNCHED();
+    k_pass_j<float><<<gcol, kThreads, smem_cols<float>(N), s>>>(a, desc, work, tab);
+    DPM_LAUNCHED();
+    k_pass_i<float><<<gcol, kThreads, smem_cols<float>(N), s>>>(a, desc, work, tab);
+    DPM_LAUNCHED();
+    k_pass_j<float><<<gcol, kThreads, smem_cols<float>(N), s>>>(a, desc, work, tab);
+    DPM_LAUNCHED();
+    k_pass_k_inv<float><<<grow, kThreads, smem_rows<float>(N), s>>>(a, desc, work, tab);
+    DPM_LAUNCHED();
+    return DPM_OK;
+}
