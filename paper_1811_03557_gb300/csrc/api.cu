@@ -409,6 +409,7 @@ extern "C" int dpm_bep_build(dpm_ctx *ctx, const dpm_geom *geom, int N, double l
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { set_error("BEP build: %s", cudaGetErrorString(e)); r = DPM_ECUDA; }
     }
+    if (r == DPM_OK && precision == DPM_PREC_TC32) r = tc_status_check();
     if (r != DPM_OK) { delete b; return r; }
     *out = b;
     return DPM_OK;
@@ -595,6 +596,7 @@ extern "C" int dpm_pks_step(dpm_pks *k, int nsteps, dpm_pks_stats *stats, cudaSt
         stats->min_c = d[3];
         stats->m2 = d[4];
         stats->free_energy = d[5];
+        if (k->prm.precision == DPM_PREC_TC32) DPM_RET(tc_status_check());
         if (!std::isfinite(d[0]) || !std::isfinite(d[5])) {
             set_error("PKS state became non-finite at step %lld", (long long)k->step);
             return DPM_ENUMERIC;

@@ -154,6 +154,9 @@ template <class T>
 int ap_solve_simt(const ApParams &p, const ApRhs<T> *rhs_dev, T *work, cudaStream_t s);
 int ap_solve_tc(const ApParams &p, const ApRhs<float> *rhs_dev, float *work, cudaStream_t s);
 bool tc_supported(int N);
+// DPM_ETIMEOUT if a bounded MMA wait of the tensor-core kernels expired
+// since the last check (synchronous; call where the stream is synchronised).
+int tc_status_check();
 
 // DST-I fold tables (device, per N and type), built on first use.
 template <class T> const T *dst_fold_table(int N);
