@@ -165,13 +165,15 @@ template <class T> const T *dst_fold_table(int N);
 // FP64 least squares (Householder QR, resident R^{-1} Q^T)
 // ---------------------------------------------------------------------------
 struct LsqFactor {
+    enum Method { kCholeskyQR = 0, kHouseholder = 1 };
     int m = 0, n = 0;
-    DevBuf A;      // double[m*n] column-major; overwritten by the QR
-    DevBuf tau;    // double[n]
-    DevBuf X;      // double[n*m] row-major: X = R^{-1} Q1^T
-    DevBuf work;   // scratch
+    int method = kCholeskyQR;
+    DevBuf A;      // double[m*n] column-major (Householder overwrites it)
+    DevBuf tau;    // double[n] Householder scalars
+    DevBuf X;      // scratch of the Gram / Cholesky factorisation
+    DevBuf work;   // A copy, R, solve scratch
 };
-// Factor A (already in f.A, m x n col-major) and form X.
+// Factor A (already in f.A, m x n col-major): R with R^T R = A^T A.
 int lsq_factor(LsqFactor &f, const int *cond_flag, cudaStream_t s);
 // C[r][0..n) = X b[r] for nr right-hand sides (b: [nr][m] in T, C: [nr][n] double)
 template <class T>

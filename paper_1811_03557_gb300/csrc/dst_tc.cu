@@ -224,62 +224,79 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
         const ApRhs<float> r = rhs[b];
         float *wplane = work + ((size_t)b * kN + i) * kN * kN;
         // ---- phase A: rows of the plane -> folded, split operands ----------
+        // The difference-potential part of q lives on the sparse M^- shell:
+        // stage it as an fp32 plane in the operand region first.
+        const bool has_dens = !INV && r.dens != nullptr;
+        float *stage = reinterpret_cast<float *>(S.A(0));  // 128 x 128 fp32 = 64 KB
+        if (has_dens) {
+            float4 *st4 = reinterpret_cast<float4 *>(stage);
+            for (int q = t; q < kN * kN / 4; q += kThreads) st4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            __syncthreads();
+            const int e0 = a.rp_shell[(int64_t)i * kN], e1 = a.rp_shell[(int64_t)(i + 1) * kN];
+            for (int e = e0 + t; e < e1; e += kThreads) {
+                const int pnode = a.shell[e];
+                const int* nb = a.shell_nb + 8 * (size_t)e;
+                float sacc = 0.f;
+#pragma unroll
+                for (int q = 1; q < 7; ++q)
+                    if (nb[q] >= 0) sacc += r.dens[nb[q]];
+                const float self = nb[0] >= 0 ? r.dens[nb[0]] : 0.f;
+                stage[pnode - i * kN * kN] = cdiag * self - coff * sacc;
+            }
+            __syncthreads();
+        }
+        // all 32 rows of this warp in flight at once (lane owns k = 4 lane .. 4 lane + 3)
+        float x[32][4];
+#pragma unroll
         for (int rr = 0; rr < 32; ++rr) {
             const int row = warp * 32 + rr;
-            float x[4] = {0.f, 0.f, 0.f, 0.f};
             if (INV) {
-                float4 v = *reinterpret_cast<const float4 *>(wplane + row * kN + 4 * lane);
-                x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+                const float4 v = *reinterpret_cast<const float4 *>(wplane + row * kN + 4 * lane);
+                x[rr][0] = v.x; x[rr][1] = v.y; x[rr][2] = v.z; x[rr][3] = v.w;
             } else {
-                const int64_t R = (int64_t)i * kN + row;
-                const int64_t p0 = R * kN + 4 * lane;
+                x[rr][0] = x[rr][1] = x[rr][2] = x[rr][3] = 0.f;
+                const int64_t p0 = ((int64_t)i * kN + row) * kN + 4 * lane;
                 if (r.f) {
-                    float4 v = *reinterpret_cast<const float4 *>(r.f + p0);
-                    x[0] = fs * v.x; x[1] = fs * v.y; x[2] = fs * v.z; x[3] = fs * v.w;
+                    const float4 v = *reinterpret_cast<const float4 *>(r.f + p0);
+                    x[rr][0] = fs * v.x; x[rr][1] = fs * v.y; x[rr][2] = fs * v.z; x[rr][3] = fs * v.w;
                     if (a.mask_f) {
-                        uint32_t lb = *reinterpret_cast<const uint32_t *>(a.labels + p0);
+                        const uint32_t lb = *reinterpret_cast<const uint32_t *>(a.labels + p0);
 #pragma unroll
                         for (int u = 0; u < 4; ++u)
-                            if (!((lb >> (8 * u)) & DPM_LBL_MPLUS)) x[u] = 0.f;
+                            if (!((lb >> (8 * u)) & DPM_LBL_MPLUS)) x[rr][u] = 0.f;
                     }
                 }
-                if (r.dens) {
-                    const int e0 = a.rp_shell[R], e1 = a.rp_shell[R + 1];
-                    for (int e = e0; e < e1; ++e) {
-                        const int k = (int)(a.shell[e] - R * kN);
-                        if ((k >> 2) == lane) {
-                            const int *nb = a.shell_nb + 8 * (size_t)e;
-                            float s = 0.f;
-#pragma unroll
-                            for (int q = 1; q < 7; ++q)
-                                if (nb[q] >= 0) s += r.dens[nb[q]];
-                            const float self = nb[0] >= 0 ? r.dens[nb[0]] : 0.f;
-                            x[k & 3] += cdiag * self - coff * s;
-                        }
-                    }
+                if (has_dens) {
+                    const float4 v = *reinterpret_cast<const float4 *>(stage + row * kN + 4 * lane);
+                    x[rr][0] += v.x; x[rr][1] += v.y; x[rr][2] += v.z; x[rr][3] += v.w;
                 }
             }
+        }
+        if (has_dens) __syncthreads();  // staged plane fully read before operands overwrite it
+#pragma unroll
+        for (int rr = 0; rr < 32; ++rr) {
+            const int row = warp * 32 + rr;
             float y[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) y[u] = __shfl_xor_sync(0xffffffffu, x[u], 31);
+            for (int u = 0; u < 4; ++u) y[u] = __shfl_xor_sync(0xffffffffu, x[rr][u], 31);
             float v[4];
             if (lane < 16) {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) v[u] = x[u] + y[3 - u];       // m' = 4 lane + u
+                for (int u = 0; u < 4; ++u) v[u] = x[rr][u] + y[3 - u];     // m' = 4 lane + u
             } else {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) v[u] = y[u] - x[3 - u];       // m' = 4 (31-lane) + u
+                for (int u = 0; u < 4; ++u) v[u] = y[u] - x[rr][3 - u];     // m' = 4 (31-lane) + u
             }
             float m = fmaxf(fmaxf(fabsf(v[0]), fabsf(v[1])), fmaxf(fabsf(v[2]), fabsf(v[3])));
             m = half_max(m);
             float inv;
-            const float s = pow2_scale(m, &inv);
+            const float sc = pow2_scale(m, &inv);
             const int L = row < kH ? 2 * row : 2 * (kN - 1 - row) + 1;
             if (lane < 16) {
-                put4(S.A(0), S.A(1), L, 4 * lane, v, s);
+                put4(S.A(0), S.A(1), L, 4 * lane, v, sc);
                 if (lane == 0) S.sE()[L] = inv;
             } else {
-                put4(S.A(2), S.A(3), L, 4 * (31 - lane), v, s);
+                put4(S.A(2), S.A(3), L, 4 * (31 - lane), v, sc);
                 if (lane == 16) S.sO()[L] = inv;
             }
         }
@@ -453,7 +470,7 @@ k_tc_pencil(TcArgs a, const ApRhs<float> *rhs, float *work) {
         }
         const float wjc = S.w()[jb] + S.w()[t] + sig;
 #pragma unroll
-        for (int am = 0; am < kN; ++am) z[am] *= nscale / (wjc + S.w()[am]);
+        for (int am = 0; am < kN; ++am) z[am] *= __fdividef(nscale, wjc + S.w()[am]);
 #pragma unroll
         for (int mp = 0; mp < kH; ++mp) {
             const float lo_ = z[mp], hi_ = z[kN - 1 - mp];

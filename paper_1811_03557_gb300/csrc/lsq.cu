@@ -1,13 +1,18 @@
 // FP64 least squares for the spectral coefficients of the BEP (eq. BEP_recast,
 // Steps 2 and 5 of the main algorithm).
 //
-// Factor (once per BEP): Householder QR of A (m x n, column-major, m >> n),
-// one reflector per column, H_j = I - tau_j v_j v_j^T, keeping R and a copy
-// of A.  Solve (every step): the normal equations through the QR factor,
-// R^T R C = A^T b (the "semi-normal equations"), followed by one step of
-// iterative refinement on the residual r = b - A C.  Both steps are FP64
-// GEMVs spread over all SMs plus n x n triangular solves in one CTA, so the
-// per-step cost does not depend on forming Q.
+// Factor (once per BEP, Step 2 / 4b): the R factor of the QR decomposition of
+// A (m x n, column-major, m >> n).  Two ways are built:
+//   * CholeskyQR (default): R^T R = A^T A with G = A^T A formed by one FP64
+//     SYRK over all SMs (fixed-order partial sums, deterministic) and R the
+//     Cholesky factor of G (one CTA, in shared memory for n <= 168);
+//   * Householder QR, one reflector H_j = I - tau_j v_j v_j^T per column
+//     (three dependent launches per column; kept as the reference method).
+// Solve (every step): R^T R C = A^T b with the original A (the semi-normal
+// equations), then one step of iterative refinement on r = b - A C.  With
+// kappa(A)^2 * eps_64 << 1 the refined C agrees with a backward-stable QR
+// solve; the FP64 work per step is two GEMVs over all SMs plus n x n
+// triangular solves in one CTA, and Q is never formed.
 #include <math.h>
 
 #include "dpm_internal.cuh"
@@ -147,24 +152,111 @@ __global__ void k_trisolve(int n, const double *R, const double *y, double *C, i
     for (int i = threadIdx.x; i < n; i += blockDim.x) cq[i] = accumulate ? cq[i] + z[i] : z[i];
 }
 
+// G partial sums: part[chunk][i][j] = sum over the chunk's rows of A[r][i] A[r][j]
+// for the 64 x 64 tile (bi, bj) with bj >= bi (upper tiles only).
+constexpr int kGT = 64, kGR = 16;
+__global__ void k_syrk_part(int m, int n, const double *A, int rows_per, double *part) {
+    __shared__ double As[kGR][kGT + 1], Bs[kGR][kGT + 1];
+    const int nb = (n + kGT - 1) / kGT;
+    // decode the upper tile index
+    int tile = blockIdx.x, bi = 0;
+    while (tile >= nb - bi) { tile -= nb - bi; ++bi; }
+    const int bj = bi + tile;
+    const int chunk = blockIdx.y;
+    const int r0 = chunk * rows_per, r1 = min(m, r0 + rows_per);
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 16 x 16 threads, 4 x 4 each
+    double acc[4][4] = {};
+    for (int rs = r0; rs < r1; rs += kGR) {
+        for (int q = threadIdx.x; q < kGR * kGT; q += blockDim.x) {
+            const int rr = q % kGR, cc = q / kGR;
+            const int r = rs + rr;
+            const int ci = bi * kGT + cc, cj = bj * kGT + cc;
+            As[rr][cc] = (r < r1 && ci < n) ? A[(size_t)ci * m + r] : 0.0;
+            Bs[rr][cc] = (r < r1 && cj < n) ? A[(size_t)cj * m + r] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int rr = 0; rr < kGR; ++rr) {
+            double a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = As[rr][ty * 4 + u];
+                b[u] = Bs[rr][tx * 4 + u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+    double *P = part + (size_t)chunk * n * n;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int i = bi * kGT + ty * 4 + u, j = bj * kGT + tx * 4 + v;
+            if (i < n && j < n) P[(size_t)i * n + j] = acc[u][v];
+        }
+}
+
+// G[i][j] = sum_chunk part[chunk][i][j] in chunk order, for j >= i.
+__global__ void k_syrk_reduce(int n, int nchunks, const double *part, double *G) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * n) return;
+    const int i = idx / n, j = idx % n;
+    if (j < i) return;
+    const int bi = i / kGT, bj = j / kGT;  // only upper tiles were written
+    if (bj < bi) return;
+    double s = 0.0;
+    for (int c = 0; c < nchunks; ++c) s += part[(size_t)c * n * n + idx];
+    G[idx] = s;
+}
+
+// Cholesky G = L L^T (upper triangle of G given) in one CTA; R = L^T row-major.
+// Scratch W (n x n) is shared memory when it fits, else global.
+__global__ void k_cholesky(int n, const double *G, double *R, double *Wg, int use_smem,
+                           int *status) {
+    extern __shared__ double Ws[];
+    double *W = use_smem ? Ws : Wg;
+    const int t = threadIdx.x, T = blockDim.x;
+    for (int idx = t; idx < n * n; idx += T) {
+        const int i = idx / n, j = idx % n;
+        W[idx] = j >= i ? G[(size_t)i * n + j] : G[(size_t)j * n + i];
+    }
+    __syncthreads();
+    __shared__ double dj;
+    for (int j = 0; j < n; ++j) {
+        if (t == 0) {
+            double d = W[(size_t)j * n + j];
+            if (!(d > 0.0) || !isfinite(d)) { status[0] = 1; d = 1.0; }
+            d = sqrt(d);
+            W[(size_t)j * n + j] = d;
+            dj = d;
+        }
+        __syncthreads();
+        const double inv = 1.0 / dj;
+        for (int i = j + 1 + t; i < n; i += T) W[(size_t)i * n + j] *= inv;
+        __syncthreads();
+        const int w = n - j - 1;
+        for (int idx = t; idx < w * w; idx += T) {
+            const int i = j + 1 + idx / w, k = j + 1 + idx % w;
+            if (k <= i) W[(size_t)i * n + k] -= W[(size_t)i * n + j] * W[(size_t)k * n + j];
+        }
+        __syncthreads();
+    }
+    for (int idx = t; idx < n * n; idx += T) {
+        const int i = idx / n, k = idx % n;
+        R[idx] = k >= i ? W[(size_t)k * n + i] : 0.0;  // R[i][k] = L[k][i]
+    }
+}
+
 }  // namespace
 
-int lsq_factor(LsqFactor &f, const int *cond_flag, cudaStream_t s) {
-    (void)cond_flag;
+static int householder_factor(LsqFactor &f, double *A0, double *w, double *rdiag, double *R,
+                              int *status, cudaStream_t s) {
     const int m = f.m, n = f.n;
-    if (m < n || n < 1) { set_error("least squares: need m >= n >= 1 (m=%d n=%d)", m, n); return DPM_EINVAL; }
-    // layout of f.work: [A0 m*n][w n][rdiag n][R n*n][status (64 B)][y 4*n][res 4*m]
-    size_t need = sizeof(double) * ((size_t)m * n + 2 * (size_t)n + (size_t)n * n) + 64 +
-                  sizeof(double) * 4 * ((size_t)n + (size_t)m);
-    DPM_RET(f.work.reserve(need));
     DPM_RET(f.tau.reserve(sizeof(double) * n));
-    double *A0 = f.work.as<double>();
-    double *w = A0 + (size_t)m * n;
-    double *rdiag = w + n;
-    double *R = rdiag + n;
-    int *status = reinterpret_cast<int *>(R + (size_t)n * n);
-    DPM_CUDA(cudaMemcpyAsync(A0, f.A.p, sizeof(double) * m * n, cudaMemcpyDeviceToDevice, s));
-    DPM_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
     double *A = f.A.as<double>();
     DPM_PROF("lsq_householder_qr", s);
     for (int j = 0; j < n; ++j) {
@@ -189,10 +281,67 @@ int lsq_factor(LsqFactor &f, const int *cond_flag, cudaStream_t s) {
     }
     k_extract_r<<<(n * n + 255) / 256, 256, 0, s>>>(m, n, A, rdiag, R);
     DPM_LAUNCHED();
+    (void)A0;
+    return DPM_OK;
+}
+
+static int cholesky_factor(LsqFactor &f, const double *A0, double *R, int *status,
+                           cudaStream_t s) {
+    const int m = f.m, n = f.n;
+    const int nb = (n + kGT - 1) / kGT;
+    const int ntiles = nb * (nb + 1) / 2;
+    int chunks = (4 * 152 + ntiles - 1) / ntiles;
+    const int maxc = (m + kGR - 1) / kGR;
+    if (chunks > maxc) chunks = maxc;
+    if (chunks < 1) chunks = 1;
+    const int rows_per = ((m + chunks - 1) / chunks + kGR - 1) / kGR * kGR;
+    chunks = (m + rows_per - 1) / rows_per;
+    // scratch in f.X: partials [chunks][n][n], G [n][n], W [n][n]
+    const size_t nn = (size_t)n * n;
+    DPM_RET(f.X.reserve(sizeof(double) * (nn * (size_t)chunks + 2 * nn)));
+    double *part = f.X.as<double>(), *G = part + nn * chunks, *W = G + nn;
+    {
+        DPM_PROF("lsq_gram_syrk", s);
+        k_syrk_part<<<dim3(ntiles, chunks), 256, 0, s>>>(m, n, A0, rows_per, part);
+        DPM_LAUNCHED();
+        k_syrk_reduce<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(n, chunks, part, G);
+        DPM_LAUNCHED();
+    }
+    const size_t smem = nn * sizeof(double);
+    const int use_smem = smem <= 200 * 1024 ? 1 : 0;
+    if (use_smem) DPM_CUDA(cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+        DPM_PROF("lsq_cholesky", s);
+        k_cholesky<<<1, 1024, use_smem ? smem : 0, s>>>(n, G, R, W, use_smem, status);
+        DPM_LAUNCHED();
+    }
+    return DPM_OK;
+}
+
+int lsq_factor(LsqFactor &f, const int *cond_flag, cudaStream_t s) {
+    (void)cond_flag;
+    const int m = f.m, n = f.n;
+    if (m < n || n < 1) { set_error("least squares: need m >= n >= 1 (m=%d n=%d)", m, n); return DPM_EINVAL; }
+    // layout of f.work: [A0 m*n][w n][rdiag n][R n*n][status (64 B)][y 4*n][res 4*m]
+    size_t need = sizeof(double) * ((size_t)m * n + 2 * (size_t)n + (size_t)n * n) + 64 +
+                  sizeof(double) * 4 * ((size_t)n + (size_t)m);
+    DPM_RET(f.work.reserve(need));
+    double *A0 = f.work.as<double>();
+    double *w = A0 + (size_t)m * n;
+    double *rdiag = w + n;
+    double *R = rdiag + n;
+    int *status = reinterpret_cast<int *>(R + (size_t)n * n);
+    DPM_CUDA(cudaMemcpyAsync(A0, f.A.p, sizeof(double) * m * n, cudaMemcpyDeviceToDevice, s));
+    DPM_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
+    if (f.method == LsqFactor::kHouseholder) {
+        DPM_RET(householder_factor(f, A0, w, rdiag, R, status, s));
+    } else {
+        DPM_RET(cholesky_factor(f, A0, R, status, s));
+    }
     int h_status = 0;
     DPM_CUDA(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s));
     DPM_CUDA(cudaStreamSynchronize(s));
-    if (h_status) { set_error("BEP matrix is rank deficient (a zero Householder column)"); return DPM_ENUMERIC; }
+    if (h_status) { set_error("BEP matrix is rank deficient (a zero pivot in the factorisation)"); return DPM_ENUMERIC; }
     return DPM_OK;
 }
 
