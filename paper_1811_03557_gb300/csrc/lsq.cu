@@ -117,41 +117,6 @@ __global__ void k_resid(int m, int n, const double *A0, const T *b, int ldb, con
     res[(size_t)q * m + r] = s;
 }
 
-// Solve R^T z = y then R x = z (R row-major upper triangular); C[q] (+)= x.
-__global__ void k_trisolve(int n, const double *R, const double *y, double *C, int accumulate,
-                           int *status) {
-    extern __shared__ double z[];
-    int q = blockIdx.x;
-    const double *yq = y + (size_t)q * n;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) z[i] = yq[i];
-    __syncthreads();
-    // forward: R^T z = y  (column i of R^T is row i of R)
-    for (int i = 0; i < n; ++i) {
-        if (threadIdx.x == 0) {
-            double d = R[(size_t)i * n + i];
-            if (d == 0.0) { status[0] = 1; d = 1.0; }
-            z[i] /= d;
-        }
-        __syncthreads();
-        double zi = z[i];
-        for (int k = i + 1 + threadIdx.x; k < n; k += blockDim.x) z[k] -= R[(size_t)i * n + k] * zi;
-        __syncthreads();
-    }
-    // backward: R x = z
-    for (int i = n - 1; i >= 0; --i) {
-        if (threadIdx.x == 0) {
-            double d = R[(size_t)i * n + i];
-            z[i] /= (d == 0.0 ? 1.0 : d);
-        }
-        __syncthreads();
-        double zi = z[i];
-        for (int k = threadIdx.x; k < i; k += blockDim.x) z[k] -= R[(size_t)k * n + i] * zi;
-        __syncthreads();
-    }
-    double *cq = C + (size_t)q * n;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) cq[i] = accumulate ? cq[i] + z[i] : z[i];
-}
-
 // G partial sums: part[chunk][i][j] = sum over the chunk's rows of A[r][i] A[r][j]
 // for the 64 x 64 tile (bi, bj) with bj >= bi (upper tiles only).
 constexpr int kGT = 64, kGR = 16;
@@ -251,6 +216,54 @@ __global__ void k_cholesky(int n, const double *G, double *R, double *Wg, int us
     }
 }
 
+// Rinv = R^{-1} (upper triangular, row-major): one warp per column j solves
+// R x = e_j by back substitution; x lives in shared memory.
+__global__ void k_rinv(int n, const double *R, double *Rinv, int *status) {
+    extern __shared__ double xs[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (j >= n) return;
+    double *x = xs + (size_t)warp * n;
+    for (int i = lane; i < n; i += 32) x[i] = 0.0;
+    __syncwarp();
+    for (int i = j; i >= 0; --i) {
+        double s = 0.0;
+        for (int k = i + 1 + lane; k <= j; k += 32) s += R[(size_t)i * n + k] * x[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            const double d = R[(size_t)i * n + i];
+            if (d == 0.0) status[0] = 1;
+            x[i] = ((i == j ? 1.0 : 0.0) - s) / (d == 0.0 ? 1.0 : d);
+        }
+        __syncwarp();
+    }
+    for (int i = lane; i < n; i += 32) Rinv[(size_t)i * n + j] = i <= j ? x[i] : 0.0;
+}
+
+// out[q][i] (+)= sum_k M[i][k] y[q][k] (TRANS = 0) or sum_k M[k][i] y[q][k]
+// (TRANS = 1), M upper triangular n x n.  One warp per output element.
+template <int TRANS>
+__global__ void k_trimv(int n, const double *M, const double *y, double *out, int nr,
+                        int accumulate) {
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (gw >= n * nr) return;
+    const int q = gw / n, i = gw % n;
+    const double *yq = y + (size_t)q * n;
+    double s = 0.0;
+    if (TRANS == 0) {
+        for (int k = i + lane; k < n; k += 32) s += M[(size_t)i * n + k] * yq[k];
+    } else {
+        for (int k = lane; k <= i; k += 32) s += M[(size_t)k * n + i] * yq[k];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        double *o2 = out + (size_t)q * n + i;
+        *o2 = accumulate ? *o2 + s : s;
+    }
+}
+
 }  // namespace
 
 static int householder_factor(LsqFactor &f, double *A0, double *w, double *rdiag, double *R,
@@ -323,8 +336,10 @@ int lsq_factor(LsqFactor &f, const int *cond_flag, cudaStream_t s) {
     const int m = f.m, n = f.n;
     if (m < n || n < 1) { set_error("least squares: need m >= n >= 1 (m=%d n=%d)", m, n); return DPM_EINVAL; }
     // layout of f.work: [A0 m*n][w n][rdiag n][R n*n][status (64 B)][y 4*n][res 4*m]
+    //                   [z 4*n][Rinv n*n]
     size_t need = sizeof(double) * ((size_t)m * n + 2 * (size_t)n + (size_t)n * n) + 64 +
-                  sizeof(double) * 4 * ((size_t)n + (size_t)m);
+                  sizeof(double) * 4 * ((size_t)n + (size_t)m) + sizeof(double) * 4 * (size_t)n +
+                  sizeof(double) * (size_t)n * n;
     DPM_RET(f.work.reserve(need));
     double *A0 = f.work.as<double>();
     double *w = A0 + (size_t)m * n;
@@ -337,6 +352,14 @@ int lsq_factor(LsqFactor &f, const int *cond_flag, cudaStream_t s) {
         DPM_RET(householder_factor(f, A0, w, rdiag, R, status, s));
     } else {
         DPM_RET(cholesky_factor(f, A0, R, status, s));
+    }
+    {
+        double *Rinv = reinterpret_cast<double *>(reinterpret_cast<char *>(R + (size_t)n * n) + 64) +
+                       4 * ((size_t)n + (size_t)m) + 4 * (size_t)n;
+        DPM_PROF("lsq_rinv", s);
+        const int warps = 4;
+        k_rinv<<<(n + warps - 1) / warps, 32 * warps, sizeof(double) * warps * n, s>>>(n, R, Rinv, status);
+        DPM_LAUNCHED();
     }
     int h_status = 0;
     DPM_CUDA(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -355,18 +378,27 @@ int lsq_apply(const LsqFactor &f, const T *b, int ldb, double *C, int nr, cudaSt
     // scratch after the factor: y[nr][n], res[nr][m]
     size_t base = sizeof(double) * ((size_t)m * n + 2 * (size_t)n + (size_t)n * n) + 64;
     double *y = reinterpret_cast<double *>(static_cast<char *>(f.work.p) + base);
-    double *res = y + (size_t)nr * n;
-    size_t tri_smem = sizeof(double) * n;
+    double *res = y + 4 * (size_t)n;
+    double *z = res + 4 * (size_t)m;
+    const double *Rinv = z + 4 * (size_t)n;
+    (void)status;
+    const int mv_blocks = (n * nr * 32 + 255) / 256;
+    DPM_PROF("lsq_solve", s);
+    // C = R^{-1} R^{-T} A^T b
     k_atb<T><<<dim3(n, nr), kT, 0, s>>>(m, n, A0, b, ldb, y, nr);
     DPM_LAUNCHED();
-    k_trisolve<<<nr, 256, tri_smem, s>>>(n, R, y, C, 0, status);
+    k_trimv<1><<<mv_blocks, 256, 0, s>>>(n, Rinv, y, z, nr, 0);
     DPM_LAUNCHED();
-    // one step of iterative refinement
+    k_trimv<0><<<mv_blocks, 256, 0, s>>>(n, Rinv, z, C, nr, 0);
+    DPM_LAUNCHED();
+    // one step of iterative refinement: C += R^{-1} R^{-T} A^T (b - A C)
     k_resid<T><<<dim3((m + 255) / 256, nr), 256, 0, s>>>(m, n, A0, b, ldb, C, res, nr);
     DPM_LAUNCHED();
     k_atb<double><<<dim3(n, nr), kT, 0, s>>>(m, n, A0, res, m, y, nr);
     DPM_LAUNCHED();
-    k_trisolve<<<nr, 256, tri_smem, s>>>(n, R, y, C, 1, status);
+    k_trimv<1><<<mv_blocks, 256, 0, s>>>(n, Rinv, y, z, nr, 0);
+    DPM_LAUNCHED();
+    k_trimv<0><<<mv_blocks, 256, 0, s>>>(n, Rinv, z, C, nr, 1);
     DPM_LAUNCHED();
     return DPM_OK;
 }

@@ -154,10 +154,14 @@ __global__ void k_diag(int N, double lo, double h, const uint8_t *lab, const T *
     }
 }
 
+// Final reduction of the per-block partials: each thread folds a strided set of
+// blocks in increasing order, then a fixed pairwise tree (deterministic).
 __global__ void k_diag_final(int nblk, double h, const double *part, double *out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    constexpr int T = 256;
+    __shared__ double sh[kDiag][T];
+    const int t = threadIdx.x;
     double v[kDiag] = {0.0, -INFINITY, INFINITY, INFINITY, 0.0, 0.0};
-    for (int b = 0; b < nblk; ++b) {
+    for (int b = t; b < nblk; b += T) {
         const double *pp = part + b * kDiag;
         v[0] += pp[0];
         v[1] = fmax(v[1], pp[1]);
@@ -166,13 +170,29 @@ __global__ void k_diag_final(int nblk, double h, const double *part, double *out
         v[4] += pp[4];
         v[5] += pp[5];
     }
-    double h3 = h * h * h;
-    out[0] = h3 * v[0];
-    out[1] = v[1];
-    out[2] = v[2];
-    out[3] = v[3];
-    out[4] = h3 * v[4];
-    out[5] = h3 * v[5];
+#pragma unroll
+    for (int q = 0; q < kDiag; ++q) sh[q][t] = v[q];
+    __syncthreads();
+    for (int w = T / 2; w > 0; w >>= 1) {
+        if (t < w) {
+            sh[0][t] += sh[0][t + w];
+            sh[1][t] = fmax(sh[1][t], sh[1][t + w]);
+            sh[2][t] = fmin(sh[2][t], sh[2][t + w]);
+            sh[3][t] = fmin(sh[3][t], sh[3][t + w]);
+            sh[4][t] += sh[4][t + w];
+            sh[5][t] += sh[5][t + w];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        double h3 = h * h * h;
+        out[0] = h3 * sh[0][0];
+        out[1] = sh[1][0];
+        out[2] = sh[2][0];
+        out[3] = sh[3][0];
+        out[4] = h3 * sh[4][0];
+        out[5] = h3 * sh[5][0];
+    }
 }
 
 __device__ __forceinline__ double gauss(const dpm_gaussian &g, double x, double y, double z) {
@@ -323,7 +343,7 @@ int pks_diag(int N, double lo, double h, const uint8_t *lab, const T *rho, const
     int nb = pks_diag_blocks(N);
     k_diag<T><<<nb, kDiagThreads, 0, s>>>(N, lo, h, lab, rho, c, part);
     DPM_LAUNCHED();
-    k_diag_final<<<1, 32, 0, s>>>(nb, h, part, out);
+    k_diag_final<<<1, 256, 0, s>>>(nb, h, part, out);
     DPM_LAUNCHED();
     return DPM_OK;
 }
