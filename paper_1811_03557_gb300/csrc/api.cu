@@ -98,7 +98,10 @@ int run_ap(int prec, ApParams p, const std::vector<ApRhs<T>> &rhs, DevBuf &work,
     if (B == 0) return DPM_OK;
     const size_t cube = (size_t)p.N * p.N * p.N * sizeof(T);
     size_t cb = std::max<size_t>(1, std::min<size_t>(B, kWorkCap / cube));
-    DPM_RET(work.reserve(cb * cube));
+    size_t extra = 0;  // tensor-core solver: staged shell right-hand sides after the cubes
+    if (prec == DPM_PREC_TC32) extra = tc_scratch_elems(p, (int)cb) * sizeof(float);
+    DPM_RET(work.reserve(cb * cube + extra));
+    if (prec == DPM_PREC_TC32) p.scratch = reinterpret_cast<float *>(static_cast<char *>(work.p) + cb * cube);
     DPM_RET(desc.reserve(sizeof(ApRhs<T>) * B));
     DPM_CUDA(cudaMemcpyAsync(desc.p, rhs.data(), sizeof(ApRhs<T>) * B, cudaMemcpyHostToDevice, s));
     // The copy above is from pageable memory: it has been staged when it

@@ -144,6 +144,8 @@ struct ApParams {
     const uint8_t *labels = nullptr;
     const int *shell = nullptr, *shell_nb = nullptr, *rp_shell = nullptr;
     const int *gin = nullptr, *rp_gin = nullptr;
+    int64_t n_shell = 0;       // shell size (the tensor-core solver stages L[v] on it)
+    float *scratch = nullptr;  // tensor-core solver: B * n_shell floats
 };
 
 // Fills the index members of p from gi.
@@ -153,6 +155,8 @@ void ap_params_from_index(ApParams &p, const GridIndex &gi);
 template <class T>
 int ap_solve_simt(const ApParams &p, const ApRhs<T> *rhs_dev, T *work, cudaStream_t s);
 int ap_solve_tc(const ApParams &p, const ApRhs<float> *rhs_dev, float *work, cudaStream_t s);
+// floats of ApParams::scratch the tensor-core solver needs for B right-hand sides
+size_t tc_scratch_elems(const ApParams &p, int B);
 bool tc_supported(int N);
 // DPM_ETIMEOUT if a bounded MMA wait of the tensor-core kernels expired
 // since the last check (synchronous; call where the stream is synchronised).

@@ -440,6 +440,7 @@ void ap_params_from_index(ApParams &p, const GridIndex &gi) {
     p.rp_shell = gi.rp_shell.as<int>();
     p.gin = gi.gin.as<int>();
     p.rp_gin = gi.rp_gin.as<int>();
+    p.n_shell = gi.n_shell;
 }
 
 template <class T>

@@ -65,6 +65,8 @@ struct TcArgs {
     const int *shell, *shell_nb, *rp_shell, *gin, *rp_gin;
     const uint4 *bops;   // 32 KB pre-split, pre-swizzled sine blocks
     const float *s2;     // sin^2(pi (n+1)/(2(N+1))), n < 128
+    const float *qsh;    // staged L[v] on the shell, [B][n_shell]
+    int64_t n_shell;
 };
 
 __device__ __forceinline__ float pow2_scale(float m, float *inv) {
@@ -80,6 +82,15 @@ __device__ __forceinline__ float pow2_scale(float m, float *inv) {
 __device__ __forceinline__ void split2(float v, __half &hi, __half &lo) {
     hi = __float2half_rn(v);
     lo = __float2half_rn(v - __half2float(hi));
+}
+
+// hi/lo split of two values at once, packed as f16x2 (first value in the low half).
+__device__ __forceinline__ void split_pack(float a, float b, uint32_t &hi, uint32_t &lo) {
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
 struct Smem {
@@ -127,35 +138,49 @@ __device__ void tc_epilogue(const Smem &S) {
 }
 
 // One folded 128-point transform: D[:,0:64) = E * SE^T, D[:,64:128) = O * SO^T,
-// each as hi*hi + hi*lo + lo*hi (issued by one thread), then commit.
+// each as hi*hi + hi*lo + lo*hi (issued by one thread), then commit.  The A
+// tiles are K-major (rows of 64 K) or, with MN = true, MN-major (atoms of
+// 64 rows x 8 K placed at (kgroup * 2 + matom) * 1024 B).
+template <bool MN>
 __device__ __forceinline__ void issue_transform(const Smem &S, uint32_t tm) {
-    const uint32_t id = tc::idesc_f16_f32(kN, kH);
+    const uint32_t id = tc::idesc_f16_f32(kN, kH, MN);
     const uint32_t a0 = tc::smem_u32(S.A(0)), b0 = tc::smem_u32(S.Bt(0));
 #pragma unroll
     for (int part = 0; part < 2; ++part) {  // 0: sums (E), 1: differences (O)
         const uint32_t ahi = a0 + (2 * part) * kATile, alo = ahi + kATile;
         const uint32_t bhi = b0 + (2 * part) * kBTile, blo = bhi + kBTile;
         const uint32_t d = tm + part * kH;
+        auto ad = [](uint32_t base, int kk) {
+            return MN ? tc::sdesc_mn128(base + kk * 4096, 1024, 2048) : tc::sdesc_k128(base + kk * 32);
+        };
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
-            tc::mma_f16(d, tc::sdesc_k128(ahi + kk * 32), tc::sdesc_k128(bhi + kk * 32), id, kk > 0);
+            tc::mma_f16(d, ad(ahi, kk), tc::sdesc_k128(bhi + kk * 32), id, kk > 0);
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
-            tc::mma_f16(d, tc::sdesc_k128(ahi + kk * 32), tc::sdesc_k128(blo + kk * 32), id, 1);
+            tc::mma_f16(d, ad(ahi, kk), tc::sdesc_k128(blo + kk * 32), id, 1);
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
-            tc::mma_f16(d, tc::sdesc_k128(alo + kk * 32), tc::sdesc_k128(bhi + kk * 32), id, 1);
+            tc::mma_f16(d, ad(alo, kk), tc::sdesc_k128(bhi + kk * 32), id, 1);
     }
     tc::mma_commit(S.bar());
 }
 
+// Byte offset of element (m, k) in an MN-major 128-row tile (see issue_transform).
+__device__ __forceinline__ uint32_t mn_off(int m, int k) {
+    const int row = k & 7;
+    return (uint32_t)((((k >> 3) * 2 + (m >> 6)) << 10) + row * 128 + ((((m & 63) >> 3) ^ row) << 4) +
+                      (m & 7) * 2);
+}
+
 // Operands written -> MMA issued -> completion observed by every thread.
+template <bool MN = false>
 __device__ __forceinline__ bool run_transform(const Smem &S, uint32_t tm, uint32_t &phase) {
     tc::fence_async_smem();
     tc::tc_fence_before_sync();
     __syncthreads();
     tc::tc_fence_after_sync();
-    if (threadIdx.x == 0) issue_transform(S, tm);
+    if (threadIdx.x == 0) issue_transform<MN>(S, tm);
     bool ok = tc::mbar_wait(S.bar(), phase, kWaitIters);
     phase ^= 1u;
     tc::tc_fence_after_sync();
@@ -167,15 +192,10 @@ __device__ __forceinline__ bool run_transform(const Smem &S, uint32_t tm, uint32
 // (k0 % 4 == 0) into the pair of tiles (hi, lo).
 __device__ __forceinline__ void put4(unsigned char *thi, unsigned char *tlo, int row, int k0,
                                      const float *v, float s) {
-    __half h[4], l[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) split2(v[u] * s, h[u], l[u]);
-    uint32_t off = tc::sw128_chunk(row, k0 >> 3) + (k0 & 7) * 2;
     uint2 ph, pl;
-    ph.x = (uint32_t)__half_as_ushort(h[0]) | ((uint32_t)__half_as_ushort(h[1]) << 16);
-    ph.y = (uint32_t)__half_as_ushort(h[2]) | ((uint32_t)__half_as_ushort(h[3]) << 16);
-    pl.x = (uint32_t)__half_as_ushort(l[0]) | ((uint32_t)__half_as_ushort(l[1]) << 16);
-    pl.y = (uint32_t)__half_as_ushort(l[2]) | ((uint32_t)__half_as_ushort(l[3]) << 16);
+    split_pack(v[0] * s, v[1] * s, ph.x, pl.x);
+    split_pack(v[2] * s, v[3] * s, ph.y, pl.y);
+    const uint32_t off = tc::sw128_chunk(row, k0 >> 3) + (k0 & 7) * 2;
     *reinterpret_cast<uint2 *>(thi + off) = ph;
     *reinterpret_cast<uint2 *>(tlo + off) = pl;
 }
@@ -185,14 +205,8 @@ __device__ __forceinline__ void put8(unsigned char *thi, unsigned char *tlo, int
                                      const float *v, float s) {
     uint32_t hw[4], lw[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        __half h0, l0, h1, l1;
-        split2(v[2 * u] * s, h0, l0);
-        split2(v[2 * u + 1] * s, h1, l1);
-        hw[u] = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
-        lw[u] = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
-    }
-    uint32_t off = tc::sw128_chunk(row, k0 >> 3);
+    for (int u = 0; u < 4; ++u) split_pack(v[2 * u] * s, v[2 * u + 1] * s, hw[u], lw[u]);
+    const uint32_t off = tc::sw128_chunk(row, k0 >> 3);
     *reinterpret_cast<uint4 *>(thi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
     *reinterpret_cast<uint4 *>(tlo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
 }
@@ -204,78 +218,149 @@ __device__ __forceinline__ float half_max(float v) {  // max over a 16-lane half
 }
 
 // ---------------------------------------------------------------------------
-// Plane pass.  INV = false: q built from f / the gamma density, forward k then
-// j, result Z[i][b][c] back to the workspace.  INV = true: reads Z, inverse
-// along c -> k then b -> j, writes u (masked) and/or the gamma_in trace.
+// Plane pass.  One CTA per SM, 8 warps, persistent over items (rhs b, plane i).
+// The plane's input (f, or Z for the inverse pass) is brought into shared
+// memory by one bulk copy (TMA) issued as soon as the previous item has read
+// its buffer, so it streams in while that item is in its MMAs and epilogues.
+// INV = false: q = fscale f (on M^+ when masked) + L[v_gamma] on the shell
+//   (staged values from k_shell_rhs), forward along k then j, Z[i][b][c] out.
+// INV = true: reads Z, along c -> k then b -> j, writes u (masked to N^+)
+//   and/or the trace on gamma_in.
 // ---------------------------------------------------------------------------
+constexpr int kPlaneThreads = 256;
+constexpr int kRawBytes = kN * kN * 4;                   // one fp32 plane
+constexpr int kPlaneSmem = kRawBytes + kSmemUsed + 1024;
+
+// q on the shell for every right-hand side that has a density:
+// qsh[b][e] = (sigma + 6/h^2) v(self) - (1/h^2) sum of v over the 6 neighbours.
+__global__ void k_shell_rhs(int n_shell, float cdiag, float coff, const ApRhs<float> *rhs,
+                            const int *shell_nb, float *qsh) {
+    const int b = blockIdx.y;
+    const ApRhs<float> r = rhs[b];
+    if (!r.dens) return;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_shell; e += gridDim.x * blockDim.x) {
+        const int *nb = shell_nb + 8 * (size_t)e;
+        float sacc = 0.f;
+#pragma unroll
+        for (int q = 1; q < 7; ++q)
+            if (nb[q] >= 0) sacc += r.dens[nb[q]];
+        const float self = nb[0] >= 0 ? r.dens[nb[0]] : 0.f;
+        qsh[(size_t)b * n_shell + e] = cdiag * self - coff * sacc;
+    }
+}
+
 template <bool INV>
-__global__ void __launch_bounds__(kThreads, 2)
+__device__ __forceinline__ const float *plane_src(const ApRhs<float> &r, const float *work, int b,
+                                                  int i) {
+    if (INV) return work + ((size_t)b * kN + i) * kN * kN;
+    return r.f ? r.f + (size_t)i * kN * kN : nullptr;
+}
+
+template <bool INV>
+__global__ void __launch_bounds__(kPlaneThreads, 1)
 k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
-    const Smem S = smem_base();
-    tc_prologue(S, a);
-    const uint32_t tm = *S.tslot();
+    extern __shared__ __align__(1024) unsigned char sm_raw[];
+    unsigned char *base = sm_raw + ((1024u - (tc::smem_u32(sm_raw) & 1023u)) & 1023u);
+    float *raw = reinterpret_cast<float *>(base);
+    const Smem S{base + kRawBytes};
+    uint64_t *bar_ld = S.bar() + 1;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    uint32_t phase = 0;
+    // prologue: sine blocks, barriers, TMEM
+    {
+        uint4 *dst = reinterpret_cast<uint4 *>(S.Bt(0));
+        for (int q = t; q < 4 * kBTile / 16; q += kPlaneThreads) dst[q] = a.bops[q];
+        if (t == 0) {
+            tc::mbar_init(S.bar(), 1);
+            tc::mbar_init(bar_ld, 1);
+            tc::fence_mbar_init();
+        }
+        if (warp == 0) {
+            tc::tmem_alloc(S.tslot(), kTmemCols);
+            tc::tmem_relinquish();
+        }
+        tc::fence_async_smem();
+        tc::tc_fence_before_sync();
+        __syncthreads();
+        tc::tc_fence_after_sync();
+    }
+    const uint32_t tm = *S.tslot();
+    uint32_t phase = 0, ld_phase = 0;
     const int nitems = a.B * kN;
     const float fs = (float)a.fscale;
-    const float cdiag = (float)(a.sigma + 6.0 / (a.h * a.h)), coff = (float)(1.0 / (a.h * a.h));
-    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int q4 = warp & 3, half = warp >> 2;  // TMEM lane quarter, column half
+    const int L = 32 * q4 + lane;                // TMEM lane (row of D) of this thread
+    const uint32_t lane_addr = tm + ((uint32_t)(32 * q4) << 16);
+    // first input in flight
+    int item = blockIdx.x;
+    if (t == 0 && item < nitems) {
+        const float *src = plane_src<INV>(rhs[item / kN], work, item / kN, item % kN);
+        if (src) {
+            tc::mbar_arrive_expect_tx(bar_ld, kRawBytes);
+            tc::bulk_g2s(raw, src, kRawBytes, bar_ld);
+        }
+    }
+    bool ok = true;
+    for (; item < nitems && ok; item += gridDim.x) {
         const int b = item / kN, i = item % kN;
         const ApRhs<float> r = rhs[b];
-        float *wplane = work + ((size_t)b * kN + i) * kN * kN;
-        // ---- phase A: rows of the plane -> folded, split operands ----------
-        // The difference-potential part of q lives on the sparse M^- shell:
-        // stage it as an fp32 plane in the operand region first.
-        const bool has_dens = !INV && r.dens != nullptr;
-        float *stage = reinterpret_cast<float *>(S.A(0));  // 128 x 128 fp32 = 64 KB
-        if (has_dens) {
-            float4 *st4 = reinterpret_cast<float4 *>(stage);
-            for (int q = t; q < kN * kN / 4; q += kThreads) st4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-            __syncthreads();
-            const int e0 = a.rp_shell[(int64_t)i * kN], e1 = a.rp_shell[(int64_t)(i + 1) * kN];
-            for (int e = e0 + t; e < e1; e += kThreads) {
-                const int pnode = a.shell[e];
-                const int* nb = a.shell_nb + 8 * (size_t)e;
-                float sacc = 0.f;
-#pragma unroll
-                for (int q = 1; q < 7; ++q)
-                    if (nb[q] >= 0) sacc += r.dens[nb[q]];
-                const float self = nb[0] >= 0 ? r.dens[nb[0]] : 0.f;
-                stage[pnode - i * kN * kN] = cdiag * self - coff * sacc;
-            }
-            __syncthreads();
-        }
-        // all 32 rows of this warp in flight at once (lane owns k = 4 lane .. 4 lane + 3)
-        float x[32][4];
-#pragma unroll
-        for (int rr = 0; rr < 32; ++rr) {
-            const int row = warp * 32 + rr;
-            if (INV) {
-                const float4 v = *reinterpret_cast<const float4 *>(wplane + row * kN + 4 * lane);
-                x[rr][0] = v.x; x[rr][1] = v.y; x[rr][2] = v.z; x[rr][3] = v.w;
-            } else {
-                x[rr][0] = x[rr][1] = x[rr][2] = x[rr][3] = 0.f;
-                const int64_t p0 = ((int64_t)i * kN + row) * kN + 4 * lane;
-                if (r.f) {
-                    const float4 v = *reinterpret_cast<const float4 *>(r.f + p0);
-                    x[rr][0] = fs * v.x; x[rr][1] = fs * v.y; x[rr][2] = fs * v.z; x[rr][3] = fs * v.w;
+        // ---- input plane in smem ----------------------------------------------
+        if (plane_src<INV>(r, work, b, i)) {
+            const bool got = tc::mbar_wait(bar_ld, ld_phase, kWaitIters);
+            ld_phase ^= 1u;
+            if (!got) atomicExch(&g_tc_status, 1);
+            if (!__syncthreads_and(got ? 1 : 0)) break;
+            if (!INV && (a.mask_f || fs != 1.f)) {
+                // scale f and keep it on M^+ only
+                const uint8_t *lab = a.labels + (size_t)i * kN * kN;
+                for (int q = t; q < kN * kN / 4; q += kPlaneThreads) {
+                    float4 v = reinterpret_cast<float4 *>(raw)[q];
+                    v.x *= fs; v.y *= fs; v.z *= fs; v.w *= fs;
                     if (a.mask_f) {
-                        const uint32_t lb = *reinterpret_cast<const uint32_t *>(a.labels + p0);
-#pragma unroll
-                        for (int u = 0; u < 4; ++u)
-                            if (!((lb >> (8 * u)) & DPM_LBL_MPLUS)) x[rr][u] = 0.f;
+                        const uint32_t lb = reinterpret_cast<const uint32_t *>(lab)[q];
+                        if (!(lb & DPM_LBL_MPLUS)) v.x = 0.f;
+                        if (!((lb >> 8) & DPM_LBL_MPLUS)) v.y = 0.f;
+                        if (!((lb >> 16) & DPM_LBL_MPLUS)) v.z = 0.f;
+                        if (!((lb >> 24) & DPM_LBL_MPLUS)) v.w = 0.f;
                     }
+                    reinterpret_cast<float4 *>(raw)[q] = v;
                 }
-                if (has_dens) {
-                    const float4 v = *reinterpret_cast<const float4 *>(stage + row * kN + 4 * lane);
-                    x[rr][0] += v.x; x[rr][1] += v.y; x[rr][2] += v.z; x[rr][3] += v.w;
+                __syncthreads();
+            }
+        } else if (!INV) {
+            float4 *r4 = reinterpret_cast<float4 *>(raw);
+            for (int q = t; q < kN * kN / 4; q += kPlaneThreads) r4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            __syncthreads();
+        }
+        if (!INV && r.dens) {
+            const int e0 = a.rp_shell[(int64_t)i * kN], e1 = a.rp_shell[(int64_t)(i + 1) * kN];
+            const float *qs = a.qsh + (size_t)b * a.n_shell;
+            const int off = i * kN * kN;
+            for (int e = e0 + t; e < e1; e += kPlaneThreads) raw[a.shell[e] - off] += qs[e];
+            __syncthreads();
+        }
+        // ---- phase A: rows -> folded, split operands (warp: 16 rows) ------------
+        float x[16][4];
+#pragma unroll
+        for (int rr = 0; rr < 16; ++rr) {
+            const float4 v = reinterpret_cast<const float4 *>(raw)[(warp * 16 + rr) * (kN / 4) + lane];
+            x[rr][0] = v.x; x[rr][1] = v.y; x[rr][2] = v.z; x[rr][3] = v.w;
+        }
+        // raw is free: start the next item's input (async proxy after generic reads)
+        __syncthreads();
+        if (t == 0) {
+            const int nx = item + gridDim.x;
+            if (nx < nitems) {
+                const float *src = plane_src<INV>(rhs[nx / kN], work, nx / kN, nx % kN);
+                if (src) {
+                    tc::fence_async_smem();
+                    tc::mbar_arrive_expect_tx(bar_ld, kRawBytes);
+                    tc::bulk_g2s(raw, src, kRawBytes, bar_ld);
                 }
             }
         }
-        if (has_dens) __syncthreads();  // staged plane fully read before operands overwrite it
 #pragma unroll
-        for (int rr = 0; rr < 32; ++rr) {
-            const int row = warp * 32 + rr;
+        for (int rr = 0; rr < 16; ++rr) {
+            const int row = warp * 16 + rr;
             float y[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) y[u] = __shfl_xor_sync(0xffffffffu, x[rr][u], 31);
@@ -291,122 +376,121 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
             m = half_max(m);
             float inv;
             const float sc = pow2_scale(m, &inv);
-            const int L = row < kH ? 2 * row : 2 * (kN - 1 - row) + 1;
+            const int LL = row < kH ? 2 * row : 2 * (kN - 1 - row) + 1;
             if (lane < 16) {
-                put4(S.A(0), S.A(1), L, 4 * lane, v, sc);
-                if (lane == 0) S.sE()[L] = inv;
+                put4(S.A(0), S.A(1), LL, 4 * lane, v, sc);
+                if (lane == 0) S.sE()[LL] = inv;
             } else {
-                put4(S.A(2), S.A(3), L, 4 * (31 - lane), v, sc);
-                if (lane == 16) S.sO()[L] = inv;
+                put4(S.A(2), S.A(3), LL, 4 * (31 - lane), v, sc);
+                if (lane == 16) S.sO()[LL] = inv;
             }
         }
-        if (!run_transform(S, tm, phase)) break;
-        // ---- phase C: D1 (row L = plane row r(L)) -> fold over rows -> A2 ---
-        const int L = t;
-        const uint32_t lane_addr = tm + ((uint32_t)(warp * 32) << 16);
+        if (!run_transform(S, tm, phase)) { ok = false; break; }
+        // ---- phase C: fold over rows (lanes L, L^1), A2 in MN-major layout --------
+        // This thread: columns c0 = 32 half + 16 cc of the sums (c = 2 col) and of
+        // the differences (c = 2 col + 1) -> folded values for c = 2 c0 .. 2 c0 + 31.
         const float iE = S.sE()[L] * (1.f / kSScale), iO = S.sO()[L] * (1.f / kSScale);
-        // tile maximum of the folded values
+        float f2[2][32];
         float mx = 0.f;
 #pragma unroll
-        for (int c0 = 0; c0 < 2 * kH; c0 += 16) {
-            float d[16];
-            tc::tmem_ld16(lane_addr + c0, d);
+        for (int cc = 0; cc < 2; ++cc) {
+            const int c0 = 32 * half + 16 * cc;
+            float de[16], dd[16];
+            tc::tmem_ld16(lane_addr + c0, de);
+            tc::tmem_ld16(lane_addr + kH + c0, dd);
             tc::tmem_wait_ld();
-            const float sc = c0 < kH ? iE : iO;
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
-                const float own = d[u] * sc;
-                const float par = __shfl_xor_sync(0xffffffffu, own, 1);
-                const float f2 = (L & 1) ? (par - own) : (own + par);
-                mx = fmaxf(mx, fabsf(f2));
+                const float oe = de[u] * iE, od = dd[u] * iO;
+                const float pe = __shfl_xor_sync(0xffffffffu, oe, 1);
+                const float pd = __shfl_xor_sync(0xffffffffu, od, 1);
+                f2[cc][2 * u] = (L & 1) ? (pe - oe) : (oe + pe);
+                f2[cc][2 * u + 1] = (L & 1) ? (pd - od) : (od + pd);
+                mx = fmaxf(mx, fmaxf(fabsf(f2[cc][2 * u]), fabsf(f2[cc][2 * u + 1])));
             }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if (lane == 0) S.red()[warp] = mx;
         __syncthreads();
-        mx = fmaxf(fmaxf(S.red()[0], S.red()[1]), fmaxf(S.red()[2], S.red()[3]));
+        mx = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) mx = fmaxf(mx, S.red()[w]);
         float inv2;
         const float s2 = pow2_scale(mx, &inv2);
         {
             const int p = L >> 1;
             unsigned char *thi = S.A((L & 1) ? 2 : 0), *tlo = S.A((L & 1) ? 3 : 1);
-            const uint32_t koff = (uint32_t)(p & 7) * 2;
 #pragma unroll
-            for (int c0 = 0; c0 < 2 * kH; c0 += 16) {
-                float d[16];
-                tc::tmem_ld16(lane_addr + c0, d);
-                tc::tmem_wait_ld();
-                const float sc = c0 < kH ? iE : iO;
+            for (int cc = 0; cc < 2; ++cc) {
+                const int c0 = 32 * half + 16 * cc;
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const float own = d[u] * sc;
-                    const float par = __shfl_xor_sync(0xffffffffu, own, 1);
-                    const float f2 = ((L & 1) ? (par - own) : (own + par)) * s2;
-                    // output index of the first transform: c = 2(c0+u) (sums), 2(c0+u-64)+1 (diffs)
-                    const int c = c0 < kH ? 2 * (c0 + u) : 2 * (c0 + u - kH) + 1;
-                    __half hi, lo;
-                    split2(f2, hi, lo);
-                    const uint32_t off = tc::sw128_chunk(c, p >> 3) + koff;
-                    *reinterpret_cast<__half *>(thi + off) = hi;
-                    *reinterpret_cast<__half *>(tlo + off) = lo;
+                for (int q8 = 0; q8 < 4; ++q8) {
+                    uint32_t hw[4], lw[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        split_pack(f2[cc][8 * q8 + 2 * u] * s2, f2[cc][8 * q8 + 2 * u + 1] * s2, hw[u], lw[u]);
+                    const uint32_t off = mn_off(2 * c0 + 8 * q8, p);
+                    *reinterpret_cast<uint4 *>(thi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    *reinterpret_cast<uint4 *>(tlo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                 }
             }
         }
-        if (!run_transform(S, tm, phase)) break;
-        // ---- phase E: D2 (row = c, columns = second-transform output) --------
+        if (!run_transform<true>(S, tm, phase)) { ok = false; break; }
+        // ---- phase E: D2 (row = c = L), half 0: sums part, half 1: differences --
         const float iout = inv2 * (1.f / kSScale);
         if (!INV) {
-            // Z[i][bmode][c], bmode = 2 col (sums) or 2 col + 1 (diffs)
+            float *wplane = work + ((size_t)b * kN + i) * kN * kN;
 #pragma unroll
-            for (int c0 = 0; c0 < 2 * kH; c0 += 16) {
+            for (int c0 = 0; c0 < kH; c0 += 16) {
                 float d[16];
-                tc::tmem_ld16(lane_addr + c0, d);
+                tc::tmem_ld16(lane_addr + kH * half + c0, d);
                 tc::tmem_wait_ld();
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int bm = c0 < kH ? 2 * (c0 + u) : 2 * (c0 + u - kH) + 1;
-                    wplane[bm * kN + t] = d[u] * iout;
-                }
+                for (int u = 0; u < 16; ++u) wplane[(2 * (c0 + u) + half) * kN + L] = d[u] * iout;
             }
         } else {
-            // u[i][j][k]: thread = k, column -> j
             float *stage = reinterpret_cast<float *>(S.A(0));  // 128 x 128 fp32 = 64 KB
             const int64_t pbase = (int64_t)i * kN * kN;
 #pragma unroll
-            for (int c0 = 0; c0 < 2 * kH; c0 += 16) {
+            for (int c0 = 0; c0 < kH; c0 += 16) {
                 float d[16];
-                tc::tmem_ld16(lane_addr + c0, d);
+                tc::tmem_ld16(lane_addr + kH * half + c0, d);
                 tc::tmem_wait_ld();
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {
-                    const int j = c0 < kH ? 2 * (c0 + u) : 2 * (c0 + u - kH) + 1;
-                    float val = d[u] * iout;
+                    const int j = 2 * (c0 + u) + half;
+                    const float val = d[u] * iout;
                     if (r.out_dense) {
-                        const int64_t p = pbase + (int64_t)j * kN + t;
+                        const int64_t pp = pbase + (int64_t)j * kN + L;
                         float o = val;
-                        if (a.mask_out && !(a.labels[p] & (DPM_LBL_MPLUS | DPM_LBL_GEX))) o = 0.f;
-                        r.out_dense[p] = o;
+                        if (a.mask_out && !(a.labels[pp] & (DPM_LBL_MPLUS | DPM_LBL_GEX))) o = 0.f;
+                        r.out_dense[pp] = o;
                     }
-                    if (r.out_trace) stage[j * kN + t] = val;
+                    if (r.out_trace) stage[j * kN + L] = val;
                 }
             }
             if (r.out_trace) {
                 __syncthreads();
                 const int e0 = a.rp_gin[(int64_t)i * kN], e1 = a.rp_gin[(int64_t)(i + 1) * kN];
-                for (int e = e0 + t; e < e1; e += kThreads) {
-                    const int p = a.gin[e];
-                    const int j = (p / kN) % kN, k = p % kN;
-                    r.out_trace[e] = stage[j * kN + k];
+                for (int e = e0 + t; e < e1; e += kPlaneThreads) {
+                    const int pg = a.gin[e];
+                    r.out_trace[e] = stage[((pg / kN) % kN) * kN + pg % kN];
                 }
             }
         }
-        // everyone is done with TMEM and the operand/staging smem of this item
         tc::tc_fence_before_sync();
         __syncthreads();
         tc::tc_fence_after_sync();
     }
-    tc_epilogue(S);
+    // a bulk copy issued for an item this CTA did not reach must land before exit
+    if (!ok) {
+        tc::mbar_wait(bar_ld, ld_phase, kWaitIters);
+    }
+    tc::tc_fence_before_sync();
+    __syncthreads();
+    tc::tc_fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tm, kTmemCols);
 }
 
 // ---------------------------------------------------------------------------
@@ -549,8 +633,8 @@ const uint4 *tc_sine_blocks() {
 int tc_configure() {
     static bool done = false;
     if (done) return DPM_OK;
-    DPM_CUDA(cudaFuncSetAttribute(k_tc_plane<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-    DPM_CUDA(cudaFuncSetAttribute(k_tc_plane<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    DPM_CUDA(cudaFuncSetAttribute(k_tc_plane<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPlaneSmem));
+    DPM_CUDA(cudaFuncSetAttribute(k_tc_plane<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPlaneSmem));
     DPM_CUDA(cudaFuncSetAttribute(k_tc_pencil, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
     done = true;
     return DPM_OK;
@@ -559,6 +643,8 @@ int tc_configure() {
 }  // namespace
 
 bool tc_supported(int N) { return N == kN; }
+
+size_t tc_scratch_elems(const ApParams &p, int B) { return (size_t)B * (size_t)p.n_shell; }
 
 int tc_status_check() {
     int st = 0;
@@ -592,22 +678,29 @@ int ap_solve_tc(const ApParams &p, const ApRhs<float> *rhs_dev, float *work, cud
     const int H = kN / 2, NEp = (H + 3) & ~3;
     const size_t offW = (size_t)H * NEp + (size_t)H * NEp;
     TcArgs a{p.B, p.h, p.sigma, p.fscale, p.mask_f, p.mask_out, p.labels, p.shell, p.shell_nb,
-             p.rp_shell, p.gin, p.rp_gin, bops, tab + offW};
+             p.rp_shell, p.gin, p.rp_gin, bops, tab + offW, p.scratch, p.n_shell};
     const int nitems = p.B * kN;
-    const int grid = std::min(nitems, 2 * sms);
+    if (p.n_shell > 0 && p.shell_nb) {
+        if (!p.scratch) { set_error("tensor-core AP solve: shell scratch missing"); return DPM_EINVAL; }
+        DPM_PROF("tc_shell_rhs", s);
+        const float cdiag = (float)(p.sigma + 6.0 / (p.h * p.h)), coff = (float)(1.0 / (p.h * p.h));
+        dim3 g((unsigned)std::min<int64_t>((p.n_shell + 255) / 256, 256), p.B);
+        k_shell_rhs<<<g, 256, 0, s>>>((int)p.n_shell, cdiag, coff, rhs_dev, p.shell_nb, p.scratch);
+        DPM_LAUNCHED();
+    }
     {
         DPM_PROF("tc_plane_fwd", s);
-        k_tc_plane<false><<<grid, kThreads, kSmemBytes, s>>>(a, rhs_dev, work);
+        k_tc_plane<false><<<std::min(nitems, sms), kPlaneThreads, kPlaneSmem, s>>>(a, rhs_dev, work);
         DPM_LAUNCHED();
     }
     {
         DPM_PROF("tc_pencil", s);
-        k_tc_pencil<<<grid, kThreads, kSmemBytes, s>>>(a, rhs_dev, work);
+        k_tc_pencil<<<std::min(nitems, 2 * sms), kThreads, kSmemBytes, s>>>(a, rhs_dev, work);
         DPM_LAUNCHED();
     }
     {
         DPM_PROF("tc_plane_inv", s);
-        k_tc_plane<true><<<grid, kThreads, kSmemBytes, s>>>(a, rhs_dev, work);
+        k_tc_plane<true><<<std::min(nitems, sms), kPlaneThreads, kPlaneSmem, s>>>(a, rhs_dev, work);
         DPM_LAUNCHED();
     }
     return DPM_OK;

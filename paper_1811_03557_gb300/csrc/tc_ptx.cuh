@@ -40,6 +40,26 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
     return false;
 }
 
+// Arrive on `bar` once and add `bytes` to the transaction count the current
+// phase waits for (the bulk copies below complete against it).
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// ---- bulk copy (TMA, non-tensor) -------------------------------------------------
+// global -> shared, `bytes` a multiple of 16, both addresses 16-byte aligned;
+// completion is signalled on `bar` as transaction bytes.
+__device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst_smem)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // ---- fences -----------------------------------------------------------------
 // generic-proxy shared-memory writes -> visible to the tensor core (async proxy)
 __device__ __forceinline__ void fence_async_smem() {
@@ -83,12 +103,27 @@ __device__ __forceinline__ uint64_t sdesc_k128(uint32_t saddr) {
     return d;
 }
 
+// Shared-memory matrix descriptor, MN-major operand (M contiguous) with the
+// 128-byte swizzle: atoms of 64 M-elements (128 B) x 8 K-rows (1024 B);
+// LBO = byte stride between atoms along M, SBO = byte stride between 8-row
+// groups along K (both verified on sm_103a with distinct-valued operands).
+__device__ __forceinline__ uint64_t sdesc_mn128(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
 // Instruction descriptor of kind::f16: A, B f16, D f32, both K-major,
 // shape M x N.  Bits: [4,6) D format (1 = f32), [7,10) A format (0 = f16),
 // [10,13) B format (0 = f16), 15/16 A/B major (0 = K), [17,23) N>>3,
 // [24,29) M>>4.
-__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
-    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N, bool a_mn_major = false) {
+    return (1u << 4) | (a_mn_major ? (1u << 15) : 0u) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
 }
 
 // D[tmem] (+)= A[smem] * B[smem]^T ; accumulate when `acc` != 0.
