@@ -338,15 +338,31 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
             for (int e = e0 + t; e < e1; e += kPlaneThreads) raw[a.shell[e] - off] += qs[e];
             __syncthreads();
         }
-        // ---- phase A: rows -> folded, split operands (warp: 16 rows) ------------
-        float x[16][4];
+        // ---- phase A: rows -> folded, split operands ---------------------------
+        // warp: 16 rows, two per step; lanes 0-15 take row 2s, lanes 16-31 row
+        // 2s+1, lane l' = l mod 16 holding x[4l'..4l'+3] and x[124-4l'..127-4l'],
+        // so the fold (sums e, differences o at m' = 4l'+u) is thread-local.
+        const int lp = lane & 15, rsel = lane >> 4;
+        float xa[8][4], xb[8][4];
+        float amax = 0.f;
 #pragma unroll
-        for (int rr = 0; rr < 16; ++rr) {
-            const float4 v = reinterpret_cast<const float4 *>(raw)[(warp * 16 + rr) * (kN / 4) + lane];
-            x[rr][0] = v.x; x[rr][1] = v.y; x[rr][2] = v.z; x[rr][3] = v.w;
+        for (int st = 0; st < 8; ++st) {
+            const int row = warp * 16 + 2 * st + rsel;
+            const float4 v1 = reinterpret_cast<const float4 *>(raw)[row * (kN / 4) + lp];
+            const float4 v2 = reinterpret_cast<const float4 *>(raw)[row * (kN / 4) + 31 - lp];
+            xa[st][0] = v1.x; xa[st][1] = v1.y; xa[st][2] = v1.z; xa[st][3] = v1.w;
+            xb[st][0] = v2.x; xb[st][1] = v2.y; xb[st][2] = v2.z; xb[st][3] = v2.w;
+            amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v1.x), fabsf(v1.y)), fmaxf(fabsf(v1.z), fabsf(v1.w))));
+            amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v2.x), fabsf(v2.y)), fmaxf(fabsf(v2.z), fabsf(v2.w))));
         }
-        // raw is free: start the next item's input (async proxy after generic reads)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        if (lane == 0) S.red()[warp] = amax;
+        // raw is free once every warp is here: start the next item's input
         __syncthreads();
+        amax = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) amax = fmaxf(amax, S.red()[w]);
         if (t == 0) {
             const int nx = item + gridDim.x;
             if (nx < nitems) {
@@ -358,38 +374,27 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
                 }
             }
         }
+        // one scale for the tile: |e|, |o| <= 2 max|x| -> scaled values < 2^14
+        float iA;
+        const float sA = pow2_scale(2.f * amax, &iA);
 #pragma unroll
-        for (int rr = 0; rr < 16; ++rr) {
-            const int row = warp * 16 + rr;
-            float y[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) y[u] = __shfl_xor_sync(0xffffffffu, x[rr][u], 31);
-            float v[4];
-            if (lane < 16) {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) v[u] = x[rr][u] + y[3 - u];     // m' = 4 lane + u
-            } else {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) v[u] = y[u] - x[rr][3 - u];     // m' = 4 (31-lane) + u
-            }
-            float m = fmaxf(fmaxf(fabsf(v[0]), fabsf(v[1])), fmaxf(fabsf(v[2]), fabsf(v[3])));
-            m = half_max(m);
-            float inv;
-            const float sc = pow2_scale(m, &inv);
+        for (int st = 0; st < 8; ++st) {
+            const int row = warp * 16 + 2 * st + rsel;
             const int LL = row < kH ? 2 * row : 2 * (kN - 1 - row) + 1;
-            if (lane < 16) {
-                put4(S.A(0), S.A(1), LL, 4 * lane, v, sc);
-                if (lane == 0) S.sE()[LL] = inv;
-            } else {
-                put4(S.A(2), S.A(3), LL, 4 * (31 - lane), v, sc);
-                if (lane == 16) S.sO()[LL] = inv;
+            float e[4], o[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                e[u] = xa[st][u] + xb[st][3 - u];
+                o[u] = xa[st][u] - xb[st][3 - u];
             }
+            put4(S.A(0), S.A(1), LL, 4 * lp, e, sA);
+            put4(S.A(2), S.A(3), LL, 4 * lp, o, sA);
         }
         if (!run_transform(S, tm, phase)) { ok = false; break; }
         // ---- phase C: fold over rows (lanes L, L^1), A2 in MN-major layout --------
         // This thread: columns c0 = 32 half + 16 cc of the sums (c = 2 col) and of
         // the differences (c = 2 col + 1) -> folded values for c = 2 c0 .. 2 c0 + 31.
-        const float iE = S.sE()[L] * (1.f / kSScale), iO = S.sO()[L] * (1.f / kSScale);
+        const float iE = iA * (1.f / kSScale), iO = iE;
         float f2[2][32];
         float mx = 0.f;
 #pragma unroll
