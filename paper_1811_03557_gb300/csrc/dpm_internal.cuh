@@ -169,9 +169,10 @@ template <class T> const T *dst_fold_table(int N);
 // FP64 least squares (Householder QR, resident R^{-1} Q^T)
 // ---------------------------------------------------------------------------
 struct LsqFactor {
-    enum Method { kCholeskyQR = 0, kHouseholder = 1 };
+    enum Method { kMixed = 0, kCholeskyQR = 1, kHouseholder = 2 };
     int m = 0, n = 0;
-    int method = kCholeskyQR;
+    int method = kMixed;
+    bool equilibrated = false;
     DevBuf A;      // double[m*n] column-major (Householder overwrites it)
     DevBuf tau;    // double[n] Householder scalars
     DevBuf X;      // scratch of the Gram / Cholesky factorisation

@@ -93,7 +93,8 @@ __global__ void k_extract_r(int m, int n, const double *A, const double *rdiag, 
 
 // y[q][c] = sum_r A0[r][c] b[q][r]  (b in T, row stride ldb)
 template <class T>
-__global__ void k_atb(int m, int n, const double *A0, const T *b, int ldb, double *y, int nr) {
+__global__ void k_atb(int m, int n, const double *A0, const T *b, int ldb, double *y, int nr,
+                      const double *colscale) {
     __shared__ double sh[32];
     int c = blockIdx.x, q = blockIdx.y;
     const double *a = A0 + (size_t)c * m;
@@ -101,7 +102,7 @@ __global__ void k_atb(int m, int n, const double *A0, const T *b, int ldb, doubl
     double s = 0.0;
     for (int r = threadIdx.x; r < m; r += blockDim.x) s += a[r] * (double)bq[r];
     s = block_sum(s, sh);
-    if (threadIdx.x == 0) y[(size_t)q * n + c] = s;
+    if (threadIdx.x == 0) y[(size_t)q * n + c] = colscale ? s * colscale[c] : s;
 }
 
 // res[q][r] = b[q][r] - sum_c A0[r][c] C[q][c]
@@ -178,6 +179,105 @@ __global__ void k_syrk_reduce(int n, int nchunks, const double *part, double *G)
     G[idx] = s;
 }
 
+// d[j] = 1 / ||A[:, j]||_2 (column equilibration; FP64)
+__global__ void k_colscale(int m, const double *A, double *d) {
+    __shared__ double sh[32];
+    const int j = blockIdx.x;
+    const double *a = A + (size_t)j * m;
+    double s = 0.0;
+    for (int r = threadIdx.x; r < m; r += blockDim.x) s += a[r] * a[r];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) d[j] = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
+}
+
+// FP32 Gram partials of the equilibrated matrix A D (upper 64 x 64 tiles),
+// part[chunk][i][j] in float; the chunk sums are added in FP64 by k_syrk_reduce32.
+__global__ void k_syrk32_part(int m, int n, const double *A, const double *d, int rows_per,
+                              float *part) {
+    __shared__ float As[kGR][kGT + 1], Bs[kGR][kGT + 1];
+    const int nb = (n + kGT - 1) / kGT;
+    int tile = blockIdx.x, bi = 0;
+    while (tile >= nb - bi) { tile -= nb - bi; ++bi; }
+    const int bj = bi + tile;
+    const int chunk = blockIdx.y;
+    const int r0 = chunk * rows_per, r1 = min(m, r0 + rows_per);
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    float acc[4][4] = {};
+    for (int rs = r0; rs < r1; rs += kGR) {
+        for (int q = threadIdx.x; q < kGR * kGT; q += blockDim.x) {
+            const int rr = q % kGR, cc = q / kGR;
+            const int r = rs + rr;
+            const int ci = bi * kGT + cc, cj = bj * kGT + cc;
+            As[rr][cc] = (r < r1 && ci < n) ? (float)(A[(size_t)ci * m + r] * d[ci]) : 0.f;
+            Bs[rr][cc] = (r < r1 && cj < n) ? (float)(A[(size_t)cj * m + r] * d[cj]) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int rr = 0; rr < kGR; ++rr) {
+            float a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = As[rr][ty * 4 + u];
+                b[u] = Bs[rr][tx * 4 + u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+    float *P = part + (size_t)chunk * n * n;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int i = bi * kGT + ty * 4 + u, j = bj * kGT + tx * 4 + v;
+            if (i < n && j < n) P[(size_t)i * n + j] = acc[u][v];
+        }
+}
+
+__global__ void k_syrk_reduce32(int n, int nchunks, const float *part, double *G) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * n) return;
+    const int i = idx / n, j = idx % n;
+    if (j < i) return;
+    double s = 0.0;
+    for (int c = 0; c < nchunks; ++c) s += (double)part[(size_t)c * n * n + idx];
+    G[idx] = s;
+}
+
+// FP32 Cholesky of the (well-conditioned, equilibrated) Gram matrix in one
+// CTA, one barrier per column: step j reads the pivot W[j][j], writes row j of
+// R = L^T (R[j][i] = W[i][j] / sqrt(W[j][j])) and applies the rank-1 update
+// W[i][k] -= W[i][j] W[k][j] / W[j][j] to the trailing lower triangle.
+__global__ void k_cholesky32(int n, const double *G, double *R, int *status) {
+    extern __shared__ float W32[];
+    const int t = threadIdx.x, T = blockDim.x;
+    for (int idx = t; idx < n * n; idx += T) {
+        const int i = idx / n, j = idx % n;
+        W32[idx] = (float)(j >= i ? G[(size_t)i * n + j] : G[(size_t)j * n + i]);
+        R[idx] = 0.0;
+    }
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+        float piv = W32[j * n + j];
+        if (!(piv > 0.f) || !isfinite(piv)) {
+            if (t == 0) status[0] = 1;
+            piv = 1.f;
+        }
+        const float rs = rsqrtf(piv), ip = 1.f / piv;
+        for (int i = j + t; i < n; i += T) R[(size_t)j * n + i] = (double)(W32[i * n + j] * rs);
+        // 32 x 32 thread grid over the trailing triangle (blockDim.x == 1024)
+        const int tx = t & 31, ty = t >> 5;
+        for (int i = j + 1 + ty; i < n; i += 32) {
+            const float wij = W32[i * n + j] * ip;
+            for (int k = j + 1 + tx; k <= i; k += 32) W32[i * n + k] -= wij * W32[k * n + j];
+        }
+        __syncthreads();
+    }
+}
+
 // Cholesky G = L L^T (upper triangle of G given) in one CTA; R = L^T row-major.
 // Scratch W (n x n) is shared memory when it fits, else global.
 __global__ void k_cholesky(int n, const double *G, double *R, double *Wg, int use_smem,
@@ -245,7 +345,7 @@ __global__ void k_rinv(int n, const double *R, double *Rinv, int *status) {
 // (TRANS = 1), M upper triangular n x n.  One warp per output element.
 template <int TRANS>
 __global__ void k_trimv(int n, const double *M, const double *y, double *out, int nr,
-                        int accumulate) {
+                        int accumulate, const double *outscale) {
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (gw >= n * nr) return;
     const int q = gw / n, i = gw % n;
@@ -259,6 +359,7 @@ __global__ void k_trimv(int n, const double *M, const double *y, double *out, in
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {
+        if (outscale) s *= outscale[i];
         double *o2 = out + (size_t)q * n + i;
         *o2 = accumulate ? *o2 + s : s;
     }
@@ -331,15 +432,53 @@ static int cholesky_factor(LsqFactor &f, const double *A0, double *R, int *statu
     return DPM_OK;
 }
 
+// Mixed precision: column equilibration d (FP64), Gram of A D with FP32
+// products (chunk sums in FP64), FP32 Cholesky; the refinement of every solve
+// is FP64 against the original A (the factor only preconditions it).
+static int mixed_factor(LsqFactor &f, const double *A0, double *R, double *dscale, int *status,
+                        cudaStream_t s) {
+    const int m = f.m, n = f.n;
+    const int nb = (n + kGT - 1) / kGT;
+    const int ntiles = nb * (nb + 1) / 2;
+    int chunks = (4 * 152 + ntiles - 1) / ntiles;
+    const int maxc = (m + kGR - 1) / kGR;
+    if (chunks > maxc) chunks = maxc;
+    if (chunks < 1) chunks = 1;
+    const int rows_per = ((m + chunks - 1) / chunks + kGR - 1) / kGR * kGR;
+    chunks = (m + rows_per - 1) / rows_per;
+    const size_t nn = (size_t)n * n;
+    DPM_RET(f.X.reserve(sizeof(float) * nn * (size_t)chunks + sizeof(double) * nn + 16));
+    float *part = f.X.as<float>();
+    double *G = reinterpret_cast<double *>(part + nn * chunks + (nn * chunks & 1));
+    {
+        DPM_PROF("lsq_gram_syrk", s);
+        k_colscale<<<n, kT, 0, s>>>(m, A0, dscale);
+        DPM_LAUNCHED();
+        k_syrk32_part<<<dim3(ntiles, chunks), 256, 0, s>>>(m, n, A0, dscale, rows_per, part);
+        DPM_LAUNCHED();
+        k_syrk_reduce32<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(n, chunks, part, G);
+        DPM_LAUNCHED();
+    }
+    const size_t smem = nn * sizeof(float);
+    if (smem > 220 * 1024) { set_error("least squares: %d columns exceed the in-smem Cholesky", n); return DPM_EUNSUPPORTED; }
+    DPM_CUDA(cudaFuncSetAttribute(k_cholesky32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+        DPM_PROF("lsq_cholesky", s);
+        k_cholesky32<<<1, 1024, smem, s>>>(n, G, R, status);
+        DPM_LAUNCHED();
+    }
+    return DPM_OK;
+}
+
 int lsq_factor(LsqFactor &f, const int *cond_flag, cudaStream_t s) {
     (void)cond_flag;
     const int m = f.m, n = f.n;
     if (m < n || n < 1) { set_error("least squares: need m >= n >= 1 (m=%d n=%d)", m, n); return DPM_EINVAL; }
     // layout of f.work: [A0 m*n][w n][rdiag n][R n*n][status (64 B)][y 4*n][res 4*m]
-    //                   [z 4*n][Rinv n*n]
+    //                   [z 4*n][Rinv n*n][colscale n]
     size_t need = sizeof(double) * ((size_t)m * n + 2 * (size_t)n + (size_t)n * n) + 64 +
                   sizeof(double) * 4 * ((size_t)n + (size_t)m) + sizeof(double) * 4 * (size_t)n +
-                  sizeof(double) * (size_t)n * n;
+                  sizeof(double) * (size_t)n * n + sizeof(double) * (size_t)n;
     DPM_RET(f.work.reserve(need));
     double *A0 = f.work.as<double>();
     double *w = A0 + (size_t)m * n;
@@ -348,14 +487,19 @@ int lsq_factor(LsqFactor &f, const int *cond_flag, cudaStream_t s) {
     int *status = reinterpret_cast<int *>(R + (size_t)n * n);
     DPM_CUDA(cudaMemcpyAsync(A0, f.A.p, sizeof(double) * m * n, cudaMemcpyDeviceToDevice, s));
     DPM_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
+    double *Rinv = reinterpret_cast<double *>(reinterpret_cast<char *>(R + (size_t)n * n) + 64) +
+                   4 * ((size_t)n + (size_t)m) + 4 * (size_t)n;
+    double *dscale = Rinv + (size_t)n * n;
+    f.equilibrated = false;
     if (f.method == LsqFactor::kHouseholder) {
         DPM_RET(householder_factor(f, A0, w, rdiag, R, status, s));
-    } else {
+    } else if (f.method == LsqFactor::kCholeskyQR) {
         DPM_RET(cholesky_factor(f, A0, R, status, s));
+    } else {
+        DPM_RET(mixed_factor(f, A0, R, dscale, status, s));
+        f.equilibrated = true;
     }
     {
-        double *Rinv = reinterpret_cast<double *>(reinterpret_cast<char *>(R + (size_t)n * n) + 64) +
-                       4 * ((size_t)n + (size_t)m) + 4 * (size_t)n;
         DPM_PROF("lsq_rinv", s);
         const int warps = 4;
         k_rinv<<<(n + warps - 1) / warps, 32 * warps, sizeof(double) * warps * n, s>>>(n, R, Rinv, status);
@@ -383,23 +527,27 @@ int lsq_apply(const LsqFactor &f, const T *b, int ldb, double *C, int nr, cudaSt
     const double *Rinv = z + 4 * (size_t)n;
     (void)status;
     const int mv_blocks = (n * nr * 32 + 255) / 256;
+    const double *dsc = f.equilibrated ? Rinv + (size_t)n * n : nullptr;
+    const int refine = f.equilibrated ? 3 : 1;
     DPM_PROF("lsq_solve", s);
-    // C = R^{-1} R^{-T} A^T b
-    k_atb<T><<<dim3(n, nr), kT, 0, s>>>(m, n, A0, b, ldb, y, nr);
+    // C = D R^{-1} R^{-T} D A^T b   (D = I unless the factor was equilibrated)
+    k_atb<T><<<dim3(n, nr), kT, 0, s>>>(m, n, A0, b, ldb, y, nr, dsc);
     DPM_LAUNCHED();
-    k_trimv<1><<<mv_blocks, 256, 0, s>>>(n, Rinv, y, z, nr, 0);
+    k_trimv<1><<<mv_blocks, 256, 0, s>>>(n, Rinv, y, z, nr, 0, nullptr);
     DPM_LAUNCHED();
-    k_trimv<0><<<mv_blocks, 256, 0, s>>>(n, Rinv, z, C, nr, 0);
+    k_trimv<0><<<mv_blocks, 256, 0, s>>>(n, Rinv, z, C, nr, 0, dsc);
     DPM_LAUNCHED();
-    // one step of iterative refinement: C += R^{-1} R^{-T} A^T (b - A C)
-    k_resid<T><<<dim3((m + 255) / 256, nr), 256, 0, s>>>(m, n, A0, b, ldb, C, res, nr);
-    DPM_LAUNCHED();
-    k_atb<double><<<dim3(n, nr), kT, 0, s>>>(m, n, A0, res, m, y, nr);
-    DPM_LAUNCHED();
-    k_trimv<1><<<mv_blocks, 256, 0, s>>>(n, Rinv, y, z, nr, 0);
-    DPM_LAUNCHED();
-    k_trimv<0><<<mv_blocks, 256, 0, s>>>(n, Rinv, z, C, nr, 1);
-    DPM_LAUNCHED();
+    // iterative refinement: C += D R^{-1} R^{-T} D A^T (b - A C), all in FP64
+    for (int it = 0; it < refine; ++it) {
+        k_resid<T><<<dim3((m + 255) / 256, nr), 256, 0, s>>>(m, n, A0, b, ldb, C, res, nr);
+        DPM_LAUNCHED();
+        k_atb<double><<<dim3(n, nr), kT, 0, s>>>(m, n, A0, res, m, y, nr, dsc);
+        DPM_LAUNCHED();
+        k_trimv<1><<<mv_blocks, 256, 0, s>>>(n, Rinv, y, z, nr, 0, nullptr);
+        DPM_LAUNCHED();
+        k_trimv<0><<<mv_blocks, 256, 0, s>>>(n, Rinv, z, C, nr, 1, dsc);
+        DPM_LAUNCHED();
+    }
     return DPM_OK;
 }
 
