@@ -1,0 +1,37 @@
+"""Profiling case: the BEP assembly of the N = 128, K = 8 sphere workload.
+
+Builds the BEP twice (the first build creates the per-device tables) through
+the C ABI; each build runs classification, the gamma geometry, one batched
+auxiliary solve of the 162 basis columns and the least-squares factorisation.
+Meant to be run under ncu with a kernel filter, e.g.
+
+    python -m paper_1811_03557_gb300.profile_case --precision tc32
+"""
+from __future__ import annotations
+
+import argparse
+
+
+def main():
+    import torch
+
+    from . import abi
+    from .workloads import WORKLOADS
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--precision", choices=["fp32", "tc32", "fp64"], default="tc32")
+    ap.add_argument("--builds", type=int, default=2)
+    args = ap.parse_args()
+    prec = {"fp32": abi.DPM_PREC_FP32, "tc32": abi.DPM_PREC_TC32, "fp64": abi.DPM_PREC_FP64}[args.precision]
+    w = WORKLOADS["pks_sphere_N128_K8"]
+    ctx = abi.dpm_ctx_create(0)
+    for _ in range(args.builds):
+        b = abi.dpm_bep_build(ctx, w.geom, w.N, w.lo, w.hi, 1.0 / w.dt, w.K, w.beta, prec)
+        abi.dpm_bep_destroy(b)
+    torch.cuda.synchronize()
+    abi.dpm_ctx_destroy(ctx)
+    print("profile case done")
+
+
+if __name__ == "__main__":
+    main()
