@@ -116,6 +116,7 @@ struct GammaGeom {
     DevBuf normal;   // double[n_gamma][3]
     DevBuf dist;     // double[n_gamma]
     DevBuf phi;      // double[n_gamma][nsh] real orthonormal SH at the foot point
+    DevBuf phi32;    // float copy of phi (FP32 paths' extension), built on demand
 };
 int build_gamma_geom(const dpm_geom &g, const GridIndex &gi, int K, GammaGeom &gg,
                      cudaStream_t s);

@@ -113,9 +113,16 @@ __global__ void k_resid(int m, int n, const double *A0, const T *b, int ldb, con
     int q = blockIdx.y;
     if (r >= m) return;
     const double *cq = C + (size_t)q * n;
-    double s = (double)b[(size_t)q * ldb + r];
-    for (int c = 0; c < n; ++c) s -= A0[(size_t)c * m + r] * cq[c];
-    res[(size_t)q * m + r] = s;
+    double s0 = (double)b[(size_t)q * ldb + r], s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int c = 0;
+    for (; c + 3 < n; c += 4) {
+        s0 -= A0[(size_t)c * m + r] * cq[c];
+        s1 -= A0[(size_t)(c + 1) * m + r] * cq[c + 1];
+        s2 -= A0[(size_t)(c + 2) * m + r] * cq[c + 2];
+        s3 -= A0[(size_t)(c + 3) * m + r] * cq[c + 3];
+    }
+    for (; c < n; ++c) s0 -= A0[(size_t)c * m + r] * cq[c];
+    res[(size_t)q * m + r] = (s0 + s1) + (s2 + s3);
 }
 
 // G partial sums: part[chunk][i][j] = sum over the chunk's rows of A[r][i] A[r][j]
@@ -247,34 +254,54 @@ __global__ void k_syrk_reduce32(int n, int nchunks, const float *part, double *G
     G[idx] = s;
 }
 
-// FP32 Cholesky of the (well-conditioned, equilibrated) Gram matrix in one
-// CTA, one barrier per column: step j reads the pivot W[j][j], writes row j of
-// R = L^T (R[j][i] = W[i][j] / sqrt(W[j][j])) and applies the rank-1 update
-// W[i][k] -= W[i][j] W[k][j] / W[j][j] to the trailing lower triangle.
-__global__ void k_cholesky32(int n, const double *G, double *R, int *status) {
-    extern __shared__ float W32[];
+// FP32 Cholesky of the (well-conditioned, equilibrated) Gram matrix G = L L^T
+// in one CTA, one barrier per column (step j writes column j of L and applies
+// the rank-1 update W[i][k] -= W[i][j] W[k][j] / W[j][j] to the trailing
+// lower triangle), then X = L^{-1} row by row with one warp per column set;
+// Rinv = R^{-1} = X^T is written in FP64.  It only preconditions the FP64
+// refinement of every solve, so FP32 suffices for this equilibrated matrix.
+__global__ void k_cholesky32(int n, const double *G, double *Rinv, int *status) {
+    extern __shared__ float sm32[];
+    float *W = sm32, *Ls = sm32 + (size_t)n * n;
     const int t = threadIdx.x, T = blockDim.x;
+    const int tx = t & 31, ty = t >> 5, nw = T >> 5;
     for (int idx = t; idx < n * n; idx += T) {
         const int i = idx / n, j = idx % n;
-        W32[idx] = (float)(j >= i ? G[(size_t)i * n + j] : G[(size_t)j * n + i]);
-        R[idx] = 0.0;
+        W[idx] = (float)(j >= i ? G[(size_t)i * n + j] : G[(size_t)j * n + i]);
+        Ls[idx] = 0.f;
     }
     __syncthreads();
     for (int j = 0; j < n; ++j) {
-        float piv = W32[j * n + j];
+        float piv = W[j * n + j];
         if (!(piv > 0.f) || !isfinite(piv)) {
             if (t == 0) status[0] = 1;
             piv = 1.f;
         }
         const float rs = rsqrtf(piv), ip = 1.f / piv;
-        for (int i = j + t; i < n; i += T) R[(size_t)j * n + i] = (double)(W32[i * n + j] * rs);
-        // 32 x 32 thread grid over the trailing triangle (blockDim.x == 1024)
-        const int tx = t & 31, ty = t >> 5;
-        for (int i = j + 1 + ty; i < n; i += 32) {
-            const float wij = W32[i * n + j] * ip;
-            for (int k = j + 1 + tx; k <= i; k += 32) W32[i * n + k] -= wij * W32[k * n + j];
+        for (int i = j + t; i < n; i += T) Ls[i * n + j] = W[i * n + j] * rs;
+        for (int i = j + 1 + ty; i < n; i += nw) {
+            const float wij = W[i * n + j] * ip;
+            for (int k = j + 1 + tx; k <= i; k += 32) W[i * n + k] -= wij * W[k * n + j];
         }
         __syncthreads();
+    }
+    // X = L^{-1} (lower) into W: X[i][c] = (delta_ic - sum_{c<=k<i} L[i][k] X[k][c]) / L[i][i]
+    for (int idx = t; idx < n * n; idx += T) W[idx] = 0.f;
+    __syncthreads();
+    for (int i = 0; i < n; ++i) {
+        const float dinv = 1.f / Ls[i * n + i];
+        for (int c = ty; c <= i; c += nw) {
+            float acc = 0.f;
+            for (int k = c + tx; k < i; k += 32) acc += Ls[i * n + k] * W[k * n + c];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (tx == 0) W[i * n + c] = ((i == c ? 1.f : 0.f) - acc) * dinv;
+        }
+        __syncthreads();
+    }
+    for (int idx = t; idx < n * n; idx += T) {
+        const int r = idx / n, c = idx % n;      // Rinv[r][c] = X[c][r]
+        Rinv[idx] = c >= r ? (double)W[c * n + r] : 0.0;
     }
 }
 
@@ -435,7 +462,7 @@ static int cholesky_factor(LsqFactor &f, const double *A0, double *R, int *statu
 // Mixed precision: column equilibration d (FP64), Gram of A D with FP32
 // products (chunk sums in FP64), FP32 Cholesky; the refinement of every solve
 // is FP64 against the original A (the factor only preconditions it).
-static int mixed_factor(LsqFactor &f, const double *A0, double *R, double *dscale, int *status,
+static int mixed_factor(LsqFactor &f, const double *A0, double *Rinv, double *dscale, int *status,
                         cudaStream_t s) {
     const int m = f.m, n = f.n;
     const int nb = (n + kGT - 1) / kGT;
@@ -452,19 +479,19 @@ static int mixed_factor(LsqFactor &f, const double *A0, double *R, double *dscal
     double *G = reinterpret_cast<double *>(part + nn * chunks + (nn * chunks & 1));
     {
         DPM_PROF("lsq_gram_syrk", s);
-        k_colscale<<<n, kT, 0, s>>>(m, A0, dscale);
+        k_colscale<<<n, 1024, 0, s>>>(m, A0, dscale);
         DPM_LAUNCHED();
         k_syrk32_part<<<dim3(ntiles, chunks), 256, 0, s>>>(m, n, A0, dscale, rows_per, part);
         DPM_LAUNCHED();
         k_syrk_reduce32<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(n, chunks, part, G);
         DPM_LAUNCHED();
     }
-    const size_t smem = nn * sizeof(float);
-    if (smem > 220 * 1024) { set_error("least squares: %d columns exceed the in-smem Cholesky", n); return DPM_EUNSUPPORTED; }
+    const size_t smem = 2 * nn * sizeof(float);
+    if (smem > 226 * 1024) { set_error("least squares: %d columns exceed the in-smem Cholesky", n); return DPM_EUNSUPPORTED; }
     DPM_CUDA(cudaFuncSetAttribute(k_cholesky32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     {
         DPM_PROF("lsq_cholesky", s);
-        k_cholesky32<<<1, 1024, smem, s>>>(n, G, R, status);
+        k_cholesky32<<<1, 1024, smem, s>>>(n, G, Rinv, status);
         DPM_LAUNCHED();
     }
     return DPM_OK;
@@ -496,10 +523,10 @@ int lsq_factor(LsqFactor &f, const int *cond_flag, cudaStream_t s) {
     } else if (f.method == LsqFactor::kCholeskyQR) {
         DPM_RET(cholesky_factor(f, A0, R, status, s));
     } else {
-        DPM_RET(mixed_factor(f, A0, R, dscale, status, s));
+        DPM_RET(mixed_factor(f, A0, Rinv, dscale, status, s));
         f.equilibrated = true;
     }
-    {
+    if (!f.equilibrated) {
         DPM_PROF("lsq_rinv", s);
         const int warps = 4;
         k_rinv<<<(n + warps - 1) / warps, 32 * warps, sizeof(double) * warps * n, s>>>(n, R, Rinv, status);
@@ -531,7 +558,7 @@ int lsq_apply(const LsqFactor &f, const T *b, int ldb, double *C, int nr, cudaSt
     const int refine = f.equilibrated ? 3 : 1;
     DPM_PROF("lsq_solve", s);
     // C = D R^{-1} R^{-T} D A^T b   (D = I unless the factor was equilibrated)
-    k_atb<T><<<dim3(n, nr), kT, 0, s>>>(m, n, A0, b, ldb, y, nr, dsc);
+    k_atb<T><<<dim3(n, nr), 1024, 0, s>>>(m, n, A0, b, ldb, y, nr, dsc);
     DPM_LAUNCHED();
     k_trimv<1><<<mv_blocks, 256, 0, s>>>(n, Rinv, y, z, nr, 0, nullptr);
     DPM_LAUNCHED();
@@ -541,7 +568,7 @@ int lsq_apply(const LsqFactor &f, const T *b, int ldb, double *C, int nr, cudaSt
     for (int it = 0; it < refine; ++it) {
         k_resid<T><<<dim3((m + 255) / 256, nr), 256, 0, s>>>(m, n, A0, b, ldb, C, res, nr);
         DPM_LAUNCHED();
-        k_atb<double><<<dim3(n, nr), kT, 0, s>>>(m, n, A0, res, m, y, nr, dsc);
+        k_atb<double><<<dim3(n, nr), 1024, 0, s>>>(m, n, A0, res, m, y, nr, dsc);
         DPM_LAUNCHED();
         k_trimv<1><<<mv_blocks, 256, 0, s>>>(n, Rinv, y, z, nr, 0, nullptr);
         DPM_LAUNCHED();

@@ -93,11 +93,18 @@ __global__ void k_cfl(int N, const uint8_t *lab, const T *c, unsigned int *gmax)
             m[ax] = fmaxf(m[ax], fmaxf(a, b));
         }
     }
+    __shared__ float shm[3][32];
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
         float v = m[ax];
         for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-        if ((threadIdx.x & 31) == 0) atomicMax(gmax + ax, __float_as_uint(v));
+        if ((threadIdx.x & 31) == 0) shm[ax][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        float v = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmaxf(v, shm[threadIdx.x][w]);
+        atomicMax(gmax + threadIdx.x, __float_as_uint(v));
     }
 }
 
@@ -244,29 +251,30 @@ __global__ void k_assemble(int64_t total, const double *psi_in, const T *trace, 
         A[i] = psi_in[i] - (double)trace[i];
 }
 
-// One warp per node of gamma: u[q][g] = sum_nu C0 phi + beta d^2/2 sum_nu C2 phi + d gN.
-template <class T>
-__global__ void k_extend(int n, int nsh, int beta, const double *phi, const double *dist,
+// One warp per node of gamma: u[q][g] = sum_nu C0 phi + beta d^2/2 sum_nu C2 phi + d gN,
+// accumulated in P (double for the FP64 path, float for the FP32 paths).
+template <class T, class P>
+__global__ void k_extend(int n, int nsh, int beta, const P *phi, const double *dist,
                          const double *C, int ldc, const double *neumann, T *dens, int ldd,
                          int nr, int clamp) {
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= n) return;
-    const double *ph = phi + (size_t)warp * nsh;
-    double d = dist[warp];
+    const P *ph = phi + (size_t)warp * nsh;
+    const double d = dist[warp];
     for (int q = 0; q < nr; ++q) {
         const double *cq = C + (size_t)q * ldc;
-        double s0 = 0.0, s2 = 0.0;
+        P s0 = (P)0, s2 = (P)0;
         for (int nu = lane; nu < nsh; nu += 32) {
-            double f = ph[nu];
-            s0 += cq[nu] * f;
-            if (beta) s2 += cq[nsh + nu] * f;
+            const P f = ph[nu];
+            s0 += (P)cq[nu] * f;
+            if (beta) s2 += (P)cq[nsh + nu] * f;
         }
         for (int o = 16; o > 0; o >>= 1) {
             s0 += __shfl_xor_sync(0xffffffffu, s0, o);
             s2 += __shfl_xor_sync(0xffffffffu, s2, o);
         }
         if (lane == 0) {
-            double u = s0 + 0.5 * d * d * s2;
+            double u = (double)s0 + 0.5 * d * d * (double)s2;
             if (neumann) u += d * neumann[warp];
             if (clamp && u < 0.0) u = 0.0;
             dens[(size_t)q * ldd + warp] = (T)u;
@@ -274,9 +282,21 @@ __global__ void k_extend(int n, int nsh, int beta, const double *phi, const doub
     }
 }
 
+__global__ void k_to_float(int64_t n, const double *src, float *dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
+}
+
 int blocks_for(int64_t n, int t) {
     int64_t b = (n + t - 1) / t;
     return (int)(b > 152 * 32 ? 152 * 32 : (b < 1 ? 1 : b));
+}
+
+// grid for the reductions over N^3 (a few nodes per thread, few partials)
+int reduce_blocks(int64_t n, int t) {
+    int64_t b = (n + t - 1) / t;
+    return (int)(b > 152 * 4 ? 152 * 4 : (b < 1 ? 1 : b));
 }
 
 }  // namespace
@@ -299,9 +319,22 @@ template <class T>
 int extend_density(const GammaGeom &gg, int64_t n_gamma, int beta, const double *C, int ldc,
                    const double *neumann, T *dens, int ldd, int nr, int clamp, cudaStream_t s) {
     int64_t threads = n_gamma * 32;
-    k_extend<T><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
-        (int)n_gamma, gg.nsh, beta, gg.phi.as<double>(), gg.dist.as<double>(), C, ldc, neumann,
-        dens, ldd, nr, clamp);
+    const unsigned blocks = (unsigned)((threads + 255) / 256);
+    if (sizeof(T) == 4) {
+        GammaGeom &g = const_cast<GammaGeom &>(gg);
+        const size_t elems = (size_t)n_gamma * gg.nsh;
+        if (g.phi32.bytes < elems * sizeof(float)) {
+            DPM_RET(g.phi32.alloc(elems * sizeof(float)));
+            k_to_float<<<blocks_for((int64_t)elems, 256), 256, 0, s>>>((int64_t)elems, gg.phi.as<double>(),
+                                                                         g.phi32.as<float>());
+            DPM_LAUNCHED();
+        }
+        k_extend<T, float><<<blocks, 256, 0, s>>>((int)n_gamma, gg.nsh, beta, g.phi32.as<float>(),
+                                                  gg.dist.as<double>(), C, ldc, neumann, dens, ldd, nr, clamp);
+    } else {
+        k_extend<T, double><<<blocks, 256, 0, s>>>((int)n_gamma, gg.nsh, beta, gg.phi.as<double>(),
+                                                   gg.dist.as<double>(), C, ldc, neumann, dens, ldd, nr, clamp);
+    }
     DPM_LAUNCHED();
     return DPM_OK;
 }
@@ -328,14 +361,14 @@ template <class T>
 int pks_cfl(int N, const uint8_t *lab, const T *c, unsigned int *gmax, cudaStream_t s) {
     int64_t n3 = (int64_t)N * N * N;
     DPM_CUDA(cudaMemsetAsync(gmax, 0, 3 * sizeof(unsigned int), s));
-    k_cfl<T><<<blocks_for(n3, 256), 256, 0, s>>>(N, lab, c, gmax);
+    k_cfl<T><<<reduce_blocks(n3, 256), 256, 0, s>>>(N, lab, c, gmax);
     DPM_LAUNCHED();
     return DPM_OK;
 }
 template int pks_cfl<float>(int, const uint8_t *, const float *, unsigned int *, cudaStream_t);
 template int pks_cfl<double>(int, const uint8_t *, const double *, unsigned int *, cudaStream_t);
 
-int pks_diag_blocks(int N) { return blocks_for((int64_t)N * N * N, kDiagThreads); }
+int pks_diag_blocks(int N) { return reduce_blocks((int64_t)N * N * N, kDiagThreads); }
 
 template <class T>
 int pks_diag(int N, double lo, double h, const uint8_t *lab, const T *rho, const T *c,
