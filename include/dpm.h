@@ -49,7 +49,8 @@ extern "C" {
 /* ---- arithmetic of the auxiliary-problem (AP) solve -------------------- */
 #define DPM_PREC_FP32 0  /* FP32 SIMT folded DST-I, FP32 storage            */
 #define DPM_PREC_FP64 1  /* FP64 SIMT DST-I, FP64 storage (comparator path) */
-#define DPM_PREC_TC32 2  /* tcgen05 3xTF32 DST-I contractions, FP32 storage  */
+#define DPM_PREC_TC32 2  /* tcgen05 DST-I contractions (3-term f16 split,
+                            FP32 accumulate), FP32 storage; N = 128 only    */
 
 /* ---- node label bits (one uint8 per node of M^0, Definition 2.1) ------- */
 #define DPM_LBL_MPLUS 1  /* node of M^+ (strict interior of Omega)           */
@@ -153,8 +154,8 @@ int dpm_classify(dpm_ctx *ctx, const dpm_geom *geom, int N, double lo, double hi
  *         DPM_PREC_FP64.  u may equal q (in place); otherwise they must not
  *         overlap.
  * Requires 2 <= N <= 256, h > 0, sigma >= 0, B >= 1.  DPM_PREC_TC32 requires
- * N to be a multiple of 32 (DPM_EUNSUPPORTED otherwise).  Scratch: the
- * context's workspace, grown on demand.
+ * N = 128 (DPM_EUNSUPPORTED otherwise).  Scratch: the context's workspace,
+ * grown on demand.
  */
 int dpm_aux_solve_batched(dpm_ctx *ctx, int N, double h, double sigma, int B,
                           const void *q, void *u, int precision, cudaStream_t stream);
@@ -192,7 +193,8 @@ int dpm_aux_solve_batched_noalloc(int N, double h, double sigma, int B, const fl
  *   A[:, k] = Tr_{gamma_in} (I - P_{N+gamma}) psi_k,
  *   psi_k = phi_k (k < (K+1)^2),  psi_k = (d^2/2) phi_{k-(K+1)^2} (beta = 1),
  * ncol = (beta+1)(K+1)^2, with one AP per column solved in one batch, and
- * factor it by Householder QR in FP64 (kept resident with R^{-1} Q^T).
+ * factor it for least squares (the R factor of its QR decomposition, kept
+ * resident with A; solves refine in FP64).
  * K in [0, 16], beta in {0, 1}; sigma > 0.  Synchronises the stream.
  */
 int dpm_bep_build(dpm_ctx *ctx, const dpm_geom *geom, int N, double lo, double hi,
