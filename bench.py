@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="bound on the oracle's CPU-baseline sample")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=1000,
+                    help="requests in the serving leg (0 skips it)")
+    ap.add_argument("--serving-rate", type=float, default=300.0, help="mean arrivals per second")
+    ap.add_argument("--serving-models", type=int, default=16)
     return ap.parse_args()
 
 
@@ -265,6 +269,10 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = run_e2e(abi, torch, pks, w, tdt, spp, args, stream)
 
+    serving = None
+    if rank == 0 and args.serving_requests > 0:
+        serving = run_serving(abi, torch, ctx, args)
+
     cpu = None
     if rank == 0:
         n, el = oracle_sample(w, args.cpu_seconds)
@@ -283,7 +291,8 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": f"inputs larger than L2 ({spp * N ** 3 * 4 / 1e9:.2f} GB batch per step)"},
             "clocks": clk, "gpu_launches": int(launches), "roofline": roof, "kernels": prof,
-            "e2e": e2e, "cpu_baseline": cpu, "sanity": {"finite": bool(finite), "mass": st.mass},
+            "e2e": e2e, "cpu_baseline": cpu, "serving": serving,
+            "sanity": {"finite": bool(finite), "mass": st.mass},
         }
         print(json.dumps(line), flush=True)
     abi.dpm_pks_destroy(pks)
@@ -368,6 +377,42 @@ def run_e2e(abi, torch, pks, w, tdt, spp, args, stream):
     nb = 2 * N ** 3 * rho_h.element_size()
     return {"value": spp * N ** 3 / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": nb,
             "d2h_bytes_per_step": nb, "ms_per_step": ms}
+
+
+def run_serving(abi, torch, ctx, args):
+    """Serving leg: a seeded Poisson stream of elliptic solves (and a few short
+    PKS runs) over a catalog of resident factorisations drawn from the serving
+    mix (N in {32, 64, 128, 256}, K in 4..12, sigma log-uniform in [1e2, 1e5],
+    spheres and ellipsoids with radius in [0.5, 1]).  Latency is arrival ->
+    solution back in host memory (copies included)."""
+    from paper_1811_03557_gb300.serving import LibraryBackend, ServingEngine
+    from paper_1811_03557_gb300.workloads import (pks_run_catalog, poly_gauss_rhs,
+                                                  serving_catalog, serving_stream)
+    cat = serving_catalog(0, args.serving_models)
+    pcat = pks_run_catalog(1, 4)
+    reqs = serving_stream(0, args.serving_requests, args.serving_rate, len(cat), len(pcat), 0.005)
+    pool = {}
+    for q in reqs:
+        if q.kind == "solve" and q.rhs_seed not in pool:
+            pool[q.rhs_seed] = torch.from_numpy(poly_gauss_rhs(q.rhs_seed, cat[q.model])).pin_memory()
+    slots, batch = 4, 8
+    be = LibraryBackend(ctx, slots, batch, max(m.N for m in cat))
+    eng = ServingEngine(be, cat, pcat, n_slots=slots, max_batch=batch, rhs=lambda s, m: pool[s])
+    t = time.perf_counter()
+    warm = eng.warm()
+    t_warm = time.perf_counter() - t
+    l0 = abi.dpm_launch_count()
+    rep = eng.run(reqs)
+    launches = abi.dpm_launch_count() - l0
+    eng.shutdown()
+    torch.cuda.synchronize()
+    out = {k: v for k, v in rep.as_dict().items() if k != "errors"}
+    out.update(requests=args.serving_requests, rate_hz=args.serving_rate, catalog=len(cat),
+               resident_after_warm=warm, warm_s=t_warm, slots=slots, max_batch=batch,
+               gpu_launches=int(launches), errors=rep.errors,
+               latency="arrival -> solution in pinned host memory (H2D and D2H included)",
+               precision="f32 storage (tcgen05 3-term f16 split at N=128, SIMT FP32 otherwise), FP64 least squares")
+    return out
 
 
 def main():

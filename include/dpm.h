@@ -227,6 +227,36 @@ int dpm_solve(dpm_bep *bep, const void *f, const double *neumann, void *u,
               double *coeffs, cudaStream_t stream);
 
 /*
+ * dpm_solve for nreq independent right-hand sides against one resident BEP
+ * (the batching primitive of a request loop): all particular solutions (and
+ * Neumann terms) in one batched AP, the least squares for all of them, the
+ * extensions, and all Green's-formula APs in a second batched AP.  Arguments
+ * are host arrays of nreq device pointers with the meaning of dpm_solve's
+ * (neumann[r] and coeffs[r] may be NULL; the arrays themselves may be NULL).
+ * Every request's result is computed by the same per-request arithmetic as
+ * dpm_solve, so it is identical whether solved alone or in a batch.
+ * 1 <= nreq <= 64.
+ */
+int dpm_solve_batched(dpm_bep *bep, int nreq, const void *const *f, const double *const *neumann,
+                      void *const *u, double *const *coeffs, cudaStream_t stream);
+
+/*
+ * Device bytes held by a BEP object (index lists, gamma geometry, columns,
+ * the factor, and the solve workspaces as currently sized).  Host-side
+ * query; no device work.
+ */
+int dpm_bep_device_bytes(const dpm_bep *bep, int64_t *bytes);
+
+/*
+ * Size every workspace a dpm_solve_batched call of up to max_nreq requests
+ * touches, so that such solves allocate nothing, and shrink the build
+ * workspace to that size (a later rebuild grows it again).  Synchronises the
+ * device (it may free memory).  Not part of the method: it serves request
+ * loops that keep many factorisations resident.  1 <= max_nreq <= 64.
+ */
+int dpm_bep_reserve(dpm_bep *bep, int max_nreq);
+
+/*
  * PKS time stepping (Steps 3-7 of the main algorithm) on one domain.
  * create: builds the point sets and gamma geometry and sets rho^0, c^0 to the
  * given Gaussians at the nodes of M^+ and at the foot points of gamma_ex
@@ -246,6 +276,9 @@ int dpm_pks_create(dpm_ctx *ctx, const dpm_pks_params *params, const dpm_gaussia
 int dpm_pks_set_state(dpm_pks *pks, const void *rho, const void *c, cudaStream_t stream);
 int dpm_pks_step(dpm_pks *pks, int nsteps, dpm_pks_stats *stats, cudaStream_t stream);
 int dpm_pks_get_state(dpm_pks *pks, void *rho, void *c, cudaStream_t stream);
+/* Device bytes held by a PKS run (its BEP, the two fields and scratch). */
+int dpm_pks_device_bytes(const dpm_pks *pks, int64_t *bytes);
+
 int dpm_pks_destroy(dpm_pks *pks);
 
 /* ---- diagnostics (no counterpart in the paper) -------------------------

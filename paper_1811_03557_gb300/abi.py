@@ -75,6 +75,10 @@ _SIGS = {
     "dpm_bep_gamma_geometry": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "dpm_bep_destroy": (C.c_int, [_P]),
     "dpm_solve": (C.c_int, [_P, _P, _P, _P, _P, _P]),
+    "dpm_solve_batched": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P]),
+    "dpm_bep_device_bytes": (C.c_int, [_P, C.POINTER(C.c_int64)]),
+    "dpm_bep_reserve": (C.c_int, [_P, C.c_int]),
+    "dpm_pks_device_bytes": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "dpm_pks_create": (C.c_int, [_P, C.POINTER(dpm_pks_params), C.POINTER(dpm_gaussian),
                                  C.POINTER(dpm_gaussian), C.POINTER(C.c_void_p), _P]),
     "dpm_pks_set_state": (C.c_int, [_P, _P, _P, _P]),
@@ -220,6 +224,33 @@ def dpm_bep_destroy(bep):
 
 def dpm_solve(bep, f, u, neumann=None, coeffs=None, stream=None):
     _check(lib().dpm_solve(bep, _ptr(f), _ptr(neumann), _ptr(u), _ptr(coeffs), _stream(stream)))
+
+
+def dpm_solve_batched(bep, fs, us, neumanns=None, coeffs=None, stream=None):
+    """Solve len(fs) requests against one BEP in one batch (lists of device tensors)."""
+    n = len(fs)
+    arr = C.c_void_p * n
+    fa = arr(*[_ptr(x) for x in fs])
+    ua = arr(*[_ptr(x) for x in us])
+    na = arr(*[_ptr(x) for x in neumanns]) if neumanns is not None else None
+    ca = arr(*[_ptr(x) for x in coeffs]) if coeffs is not None else None
+    _check(lib().dpm_solve_batched(bep, n, fa, na, ua, ca, _stream(stream)))
+
+
+def dpm_bep_device_bytes(bep) -> int:
+    v = C.c_int64(0)
+    _check(lib().dpm_bep_device_bytes(bep, C.byref(v)))
+    return int(v.value)
+
+
+def dpm_bep_reserve(bep, max_nreq: int):
+    _check(lib().dpm_bep_reserve(bep, int(max_nreq)))
+
+
+def dpm_pks_device_bytes(pks) -> int:
+    v = C.c_int64(0)
+    _check(lib().dpm_pks_device_bytes(pks, C.byref(v)))
+    return int(v.value)
 
 
 def dpm_pks_create(ctx, params: dpm_pks_params, rho0, c0, stream=None):

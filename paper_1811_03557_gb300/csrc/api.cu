@@ -155,6 +155,7 @@ struct dpm_bep {
     DevBuf desc;
     DevBuf work;
     LsqFactor lsq;
+    DevBuf btrace, bdens, bcoef;  // batched-solve buffers
     bool factored = false;
 };
 
@@ -374,6 +375,60 @@ int bep_solve(dpm_bep *b, const void *fv, const double *neumann, void *uv, doubl
     return DPM_OK;
 }
 
+template <class T>
+int bep_solve_batched(dpm_bep *b, int nreq, const void *const *fv, const double *const *neumann,
+                      void *const *uv, double *const *coeffs, cudaStream_t s) {
+    const int64_t ng = b->gi.n_gamma, m = b->gi.n_gin;
+    // per-batch buffers: traces [2*nreq][m], b vectors [nreq][m], densities [2*nreq][ng], C [nreq][ncol]
+    const size_t need_tr = sizeof(T) * (size_t)(3 * nreq) * m;
+    const size_t need_dn = sizeof(T) * (size_t)(2 * nreq) * ng;
+    const size_t need_c = sizeof(double) * (size_t)nreq * b->ncol;
+    DPM_RET(b->btrace.reserve(need_tr));
+    DPM_RET(b->bdens.reserve(need_dn));
+    DPM_RET(b->bcoef.reserve(need_c));
+    T *tr = b->btrace.as<T>();           // [r]: particular trace, [nreq + r]: Neumann trace
+    T *bv = tr + (size_t)2 * nreq * m;   // [r]: least-squares right-hand side
+    T *dn = b->bdens.as<T>();            // [r]: u_gamma, [nreq + r]: d g_N
+    double *C = b->bcoef.as<double>();
+    std::vector<ApRhs<T>> rhs;
+    for (int r = 0; r < nreq; ++r)
+        rhs.push_back({static_cast<const T *>(fv[r]), nullptr, nullptr, tr + (size_t)r * m, 0, 0});
+    for (int r = 0; r < nreq; ++r) {
+        if (neumann && neumann[r]) {
+            T *d1 = dn + (size_t)(nreq + r) * ng;
+            DPM_RET(extend_density<T>(b->gg, ng, 0, b->zero.as<double>(), 0, neumann[r], d1, (int)ng, 1, 0, s));
+            rhs.push_back({nullptr, d1, nullptr, tr + (size_t)(nreq + r) * m, 0, 0});
+        }
+    }
+    ApParams p = base_params(b, b->sigma);
+    DPM_RET(run_ap<T>(b->prec, p, rhs, b->work, b->desc, s));
+    for (int r = 0; r < nreq; ++r) {
+        T *dst = bv + (size_t)r * m;
+        if (neumann && neumann[r]) {
+            k_neumann_rhs<T><<<(unsigned)((m + 255) / 256), 256, 0, s>>>(
+                (int)m, tr + (size_t)r * m, dn + (size_t)(nreq + r) * ng, b->gi.gin_pos.as<int>(),
+                tr + (size_t)(nreq + r) * m, dst);
+            DPM_LAUNCHED();
+        } else {
+            DPM_CUDA(cudaMemcpyAsync(dst, tr + (size_t)r * m, sizeof(T) * m, cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    DPM_RET(lsq_apply<T>(b->lsq, bv, (int)m, C, nreq, s));
+    std::vector<ApRhs<T>> green;
+    for (int r = 0; r < nreq; ++r) {
+        T *d0 = dn + (size_t)r * ng;
+        DPM_RET(extend_density<T>(b->gg, ng, b->beta, C + (size_t)r * b->ncol, b->ncol,
+                                  neumann ? neumann[r] : nullptr, d0, (int)ng, 1, 0, s));
+        green.push_back({static_cast<const T *>(fv[r]), d0, static_cast<T *>(uv[r]), nullptr, 0, 0});
+    }
+    DPM_RET(run_ap<T>(b->prec, p, green, b->work, b->desc, s));
+    for (int r = 0; r < nreq; ++r)
+        if (coeffs && coeffs[r])
+            DPM_CUDA(cudaMemcpyAsync(coeffs[r], C + (size_t)r * b->ncol, sizeof(double) * b->ncol,
+                                     cudaMemcpyDeviceToDevice, s));
+    return DPM_OK;
+}
+
 int bep_init(dpm_bep *b, dpm_ctx *ctx, const dpm_geom *geom, int N, double lo, double hi, int K,
              int beta, int precision, cudaStream_t s) {
     if (!ctx || !geom) { set_error("ctx/geom is NULL"); return DPM_EINVAL; }
@@ -455,6 +510,70 @@ extern "C" int dpm_solve(dpm_bep *b, const void *f, const double *neumann, void 
     if (!b || !f || !u) { set_error("bep/f/u is NULL"); return DPM_EINVAL; }
     if (b->prec == DPM_PREC_FP64) return bep_solve<double>(b, f, neumann, u, coeffs, s);
     return bep_solve<float>(b, f, neumann, u, coeffs, s);
+}
+
+extern "C" int dpm_solve_batched(dpm_bep *b, int nreq, const void *const *f,
+                                 const double *const *neumann, void *const *u,
+                                 double *const *coeffs, cudaStream_t s) {
+    if (!b || !f || !u) { set_error("bep/f/u is NULL"); return DPM_EINVAL; }
+    if (nreq < 1 || nreq > kLsqMaxRhs) { set_error("nreq=%d outside [1, %d]", nreq, kLsqMaxRhs); return DPM_EINVAL; }
+    for (int r = 0; r < nreq; ++r)
+        if (!f[r] || !u[r]) { set_error("request %d: f/u is NULL", r); return DPM_EINVAL; }
+    if (b->prec == DPM_PREC_FP64) return bep_solve_batched<double>(b, nreq, f, neumann, u, coeffs, s);
+    return bep_solve_batched<float>(b, nreq, f, neumann, u, coeffs, s);
+}
+
+namespace {
+size_t bep_bytes(const dpm_bep &b) {
+    const GridIndex &g = b.gi;
+    const GammaGeom &q = b.gg;
+    const LsqFactor &l = b.lsq;
+    return g.labels.bytes + g.gin.bytes + g.gex.bytes + g.gamma.bytes + g.shell.bytes +
+           g.shell_nb.bytes + g.rp_gin.bytes + g.rp_shell.bytes + g.gin_pos.bytes + g.gex_pos.bytes +
+           q.foot.bytes + q.normal.bytes + q.dist.bytes + q.phi.bytes + q.phi32.bytes + l.A.bytes +
+           l.tau.bytes + l.X.bytes + l.work.bytes + b.psi.bytes + b.psi_in.bytes + b.trace.bytes +
+           b.dens.bytes + b.coef.bytes + b.zero.bytes + b.desc.bytes + b.work.bytes + b.btrace.bytes +
+           b.bdens.bytes + b.bcoef.bytes;
+}
+}  // namespace
+
+extern "C" int dpm_bep_device_bytes(const dpm_bep *b, int64_t *bytes) {
+    if (!b || !bytes) { set_error("bep/bytes is NULL"); return DPM_EINVAL; }
+    *bytes = (int64_t)bep_bytes(*b);
+    return DPM_OK;
+}
+
+extern "C" int dpm_bep_reserve(dpm_bep *b, int max_nreq) {
+    if (!b) { set_error("bep is NULL"); return DPM_EINVAL; }
+    if (max_nreq < 1 || max_nreq > kLsqMaxRhs) {
+        set_error("max_nreq=%d outside [1, %d]", max_nreq, kLsqMaxRhs);
+        return DPM_EINVAL;
+    }
+    DPM_CUDA(cudaSetDevice(b->ctx->device));
+    const size_t T = b->prec == DPM_PREC_FP64 ? sizeof(double) : sizeof(float);
+    const int64_t ng = b->gi.n_gamma, m = b->gi.n_gin;
+    const int B = 2 * max_nreq;  // particular + Neumann, or Green's formula
+    const size_t cube = (size_t)b->N * b->N * b->N * T;
+    const size_t cb = std::max<size_t>(1, std::min<size_t>(B, kWorkCap / cube));
+    size_t extra = 0;
+    if (b->prec == DPM_PREC_TC32) {
+        ApParams p = base_params(b, b->sigma);
+        extra = tc_scratch_elems(p, (int)cb) * sizeof(float);
+    }
+    // Every buffer a solve of up to max_nreq requests touches; the build
+    // workspace shrinks to that size (an exact re-allocation).
+    DPM_RET(b->work.alloc(cb * cube + extra));
+    DPM_RET(b->desc.reserve(sizeof(ApRhs<double>) * B));
+    DPM_RET(b->btrace.reserve(T * (size_t)(3 * max_nreq) * m));
+    DPM_RET(b->bdens.reserve(T * (size_t)(2 * max_nreq) * ng));
+    DPM_RET(b->bcoef.reserve(sizeof(double) * (size_t)max_nreq * b->ncol));
+    if (b->prec != DPM_PREC_FP64) {
+        // makes the FP32 extension table now rather than on the first solve
+        DPM_RET(extend_density<float>(b->gg, ng, 0, b->zero.as<double>(), 0, nullptr,
+                                      b->bdens.as<float>(), (int)ng, 1, 0, 0));
+    }
+    DPM_CUDA(cudaDeviceSynchronize());
+    return DPM_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -613,6 +732,13 @@ extern "C" int dpm_pks_get_state(dpm_pks *k, void *rho, void *c, cudaStream_t s)
     size_t n3 = (size_t)k->prm.N * k->prm.N * k->prm.N * elem_size(k->prm.precision);
     if (rho) DPM_CUDA(cudaMemcpyAsync(rho, k->rho.p, n3, cudaMemcpyDeviceToDevice, s));
     if (c) DPM_CUDA(cudaMemcpyAsync(c, k->c.p, n3, cudaMemcpyDeviceToDevice, s));
+    return DPM_OK;
+}
+
+extern "C" int dpm_pks_device_bytes(const dpm_pks *k, int64_t *bytes) {
+    if (!k || !bytes) { set_error("pks/bytes is NULL"); return DPM_EINVAL; }
+    *bytes = (int64_t)(bep_bytes(k->bep) + k->rho.bytes + k->c.bytes + k->frho.bytes + k->fc.bytes +
+                       k->gmax.bytes + k->diag_part.bytes + k->diag_out.bytes);
     return DPM_OK;
 }
 

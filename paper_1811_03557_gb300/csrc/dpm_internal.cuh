@@ -179,6 +179,7 @@ struct LsqFactor {
     DevBuf X;      // scratch of the Gram / Cholesky factorisation
     DevBuf work;   // A copy, R, solve scratch
 };
+constexpr int kLsqMaxRhs = 64;  // right-hand sides per lsq_apply call
 // Factor A (already in f.A, m x n col-major): R with R^T R = A^T A.
 int lsq_factor(LsqFactor &f, const int *cond_flag, cudaStream_t s);
 // C[r][0..n) = X b[r] for nr right-hand sides (b: [nr][m] in T, C: [nr][n] double)

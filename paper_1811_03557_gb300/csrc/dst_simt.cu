@@ -419,6 +419,8 @@ template <class T> size_t smem_cols(int N) { return (2 * (size_t)N * kC + N) * s
 
 template <class T> int set_smem_limits(int N) {
     static int configured[2] = {0, 0};
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
     int slot = sizeof(T) == 8;
     size_t need = smem_rows<T>(N) > smem_cols<T>(N) ? smem_rows<T>(N) : smem_cols<T>(N);
     if ((size_t)configured[slot] >= need) return DPM_OK;

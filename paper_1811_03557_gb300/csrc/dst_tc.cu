@@ -637,6 +637,8 @@ const uint4 *tc_sine_blocks() {
 
 int tc_configure() {
     static bool done = false;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
     if (done) return DPM_OK;
     DPM_CUDA(cudaFuncSetAttribute(k_tc_plane<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPlaneSmem));
     DPM_CUDA(cudaFuncSetAttribute(k_tc_plane<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPlaneSmem));

@@ -501,10 +501,11 @@ int lsq_factor(LsqFactor &f, const int *cond_flag, cudaStream_t s) {
     (void)cond_flag;
     const int m = f.m, n = f.n;
     if (m < n || n < 1) { set_error("least squares: need m >= n >= 1 (m=%d n=%d)", m, n); return DPM_EINVAL; }
-    // layout of f.work: [A0 m*n][w n][rdiag n][R n*n][status (64 B)][y 4*n][res 4*m]
-    //                   [z 4*n][Rinv n*n][colscale n]
+    // layout of f.work: [A0 m*n][w n][rdiag n][R n*n][status (64 B)][y R*n][res R*m]
+    //                   [z R*n][Rinv n*n][colscale n],  R = kLsqMaxRhs
+    const size_t RR = kLsqMaxRhs;
     size_t need = sizeof(double) * ((size_t)m * n + 2 * (size_t)n + (size_t)n * n) + 64 +
-                  sizeof(double) * 4 * ((size_t)n + (size_t)m) + sizeof(double) * 4 * (size_t)n +
+                  sizeof(double) * RR * ((size_t)n + (size_t)m) + sizeof(double) * RR * (size_t)n +
                   sizeof(double) * (size_t)n * n + sizeof(double) * (size_t)n;
     DPM_RET(f.work.reserve(need));
     double *A0 = f.work.as<double>();
@@ -515,7 +516,7 @@ int lsq_factor(LsqFactor &f, const int *cond_flag, cudaStream_t s) {
     DPM_CUDA(cudaMemcpyAsync(A0, f.A.p, sizeof(double) * m * n, cudaMemcpyDeviceToDevice, s));
     DPM_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
     double *Rinv = reinterpret_cast<double *>(reinterpret_cast<char *>(R + (size_t)n * n) + 64) +
-                   4 * ((size_t)n + (size_t)m) + 4 * (size_t)n;
+                   kLsqMaxRhs * ((size_t)n + (size_t)m) + kLsqMaxRhs * (size_t)n;
     double *dscale = Rinv + (size_t)n * n;
     f.equilibrated = false;
     if (f.method == LsqFactor::kHouseholder) {
@@ -545,13 +546,13 @@ int lsq_apply(const LsqFactor &f, const T *b, int ldb, double *C, int nr, cudaSt
     const double *A0 = f.work.as<double>();
     const double *R = A0 + (size_t)m * n + 2 * (size_t)n;
     int *status = reinterpret_cast<int *>(const_cast<double *>(R) + (size_t)n * n);
-    if (nr < 1 || nr > 4) { set_error("least squares: 1..4 right-hand sides per call"); return DPM_EINVAL; }
+    if (nr < 1 || nr > kLsqMaxRhs) { set_error("least squares: 1..%d right-hand sides per call", kLsqMaxRhs); return DPM_EINVAL; }
     // scratch after the factor: y[nr][n], res[nr][m]
     size_t base = sizeof(double) * ((size_t)m * n + 2 * (size_t)n + (size_t)n * n) + 64;
     double *y = reinterpret_cast<double *>(static_cast<char *>(f.work.p) + base);
-    double *res = y + 4 * (size_t)n;
-    double *z = res + 4 * (size_t)m;
-    const double *Rinv = z + 4 * (size_t)n;
+    double *res = y + kLsqMaxRhs * (size_t)n;
+    double *z = res + kLsqMaxRhs * (size_t)m;
+    const double *Rinv = z + kLsqMaxRhs * (size_t)n;
     (void)status;
     const int mv_blocks = (n * nr * 32 + 255) / 256;
     const double *dsc = f.equilibrated ? Rinv + (size_t)n * n : nullptr;

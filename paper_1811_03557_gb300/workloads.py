@@ -129,32 +129,133 @@ WORKLOADS = {
 }
 
 
-def serving_requests(seed: int, n: int, rate_hz: float = 2000.0):
-    """Poisson-arrival stream of elliptic-solve requests (shapes only)."""
+@dataclass(frozen=True)
+class ServingModel:
+    """One resident factorisation of the request stream: an elliptic problem
+    (sigma - Lap) u = f in the body `geom`, on an N^3 grid of the box
+    [lo, hi]^3, with degree-K harmonics on the boundary."""
+
+    geom: Geometry
+    N: int
+    lo: float
+    hi: float
+    K: int
+    sigma: float
+    beta: int = 1
+
+    @property
+    def ncol(self):
+        return (self.beta + 1) * (self.K + 1) ** 2
+
+
+@dataclass(frozen=True)
+class PksRunModel:
+    """A short PKS run: Test (A) data on the unit sphere, `steps` steps with the
+    CFL-limited step size (dt_max = h^2/4)."""
+
+    N: int
+    K: int
+    steps: int
+    lo: float = -1.25
+    hi: float = 1.25
+
+    @property
+    def geom(self):
+        return Geometry.sphere(1.0)
+
+    @property
+    def dt_max(self):
+        h = (self.hi - self.lo) / (self.N + 1)
+        return h * h / 4.0
+
+
+def serving_catalog(seed: int, n_models: int, Ns=(32, 64, 128, 256), K_range=(4, 12),
+                    sigma_range=(1e2, 1e5), radius_range=(0.5, 1.0)) -> list:
+    """n_models elliptic problems drawn from the serving mix: N uniform over Ns,
+    K uniform in K_range, sigma log-uniform in sigma_range, sphere or
+    ellipsoid (equal odds) with largest semi-axis uniform in radius_range; the
+    box is [-1.25 r, 1.25 r]^3."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n_models):
+        N = int(rng.choice(np.asarray(Ns)))
+        K = int(rng.integers(K_range[0], K_range[1] + 1))
+        sigma = float(10.0 ** rng.uniform(np.log10(sigma_range[0]), np.log10(sigma_range[1])))
+        r = float(rng.uniform(*radius_range))
+        if rng.integers(0, 2):
+            g = Geometry.ellipsoid(r, r * float(rng.uniform(0.7, 1.0)), r * float(rng.uniform(0.6, 1.0)))
+        else:
+            g = Geometry.sphere(r)
+        out.append(ServingModel(g, N, -1.25 * r, 1.25 * r, K, sigma))
+    return out
+
+
+def poly_gauss_coeffs(seed: int):
+    """Coefficients of a random polynomial of degree <= 3 (c[a, b, c] for
+    x^a y^b z^c, zero when a + b + c > 3) and a Gaussian width in [0.5, 3]."""
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(-1.0, 1.0, size=(4, 4, 4))
+    a, b, d = np.meshgrid(np.arange(4), np.arange(4), np.arange(4), indexing="ij")
+    c[a + b + d > 3] = 0.0
+    return c, float(rng.uniform(0.5, 3.0))
+
+
+def poly_gauss_rhs(seed: int, model, dtype=np.float32) -> np.ndarray:
+    """f = p(x/r, y/r, z/r) * exp(-w |x/r|^2) on the model's N^3 grid (r the
+    largest semi-axis), for the coefficients poly_gauss_coeffs(seed)."""
+    c, w = poly_gauss_coeffs(seed)
+    N = model.N
+    r = max(model.geom.axes)
+    h = (model.hi - model.lo) / (N + 1)
+    x = (model.lo + h * np.arange(1, N + 1) - 0.0) / r
+    cx, cy, cz = (np.asarray(model.geom.center, dtype=np.float64) / r)
+    X = np.stack([(x - cx) ** a * np.exp(-w * (x - cx) ** 2) for a in range(4)], axis=1)
+    Y = np.stack([(x - cy) ** a * np.exp(-w * (x - cy) ** 2) for a in range(4)], axis=1)
+    Z = np.stack([(x - cz) ** a * np.exp(-w * (x - cz) ** 2) for a in range(4)], axis=1)
+    # separable sum over (a, b, c): three small contractions, the last a matmul
+    T = np.einsum("abc,kc->abk", c, Z)
+    T = np.einsum("abk,jb->ajk", T, Y)
+    f = X @ T.reshape(4, N * N)
+    return f.reshape(N, N, N).astype(dtype)
+
+
+@dataclass(frozen=True)
+class ServingRequest:
+    """Arrival time (s from the start of the stream), what is asked, and the
+    seed of its right-hand side (elliptic) or the run (PKS)."""
+
+    t: float
+    kind: str          # "solve" or "pks"
+    model: int         # index into the elliptic catalog or the PKS catalog
+    rhs_seed: int
+
+
+def serving_stream(seed: int, n: int, rate_hz: float, n_models: int, n_pks_models: int = 0,
+                   pks_fraction: float = 0.0, rhs_pool: int = 2) -> list:
+    """Poisson arrivals at rate_hz; each request picks a catalog entry uniformly
+    and one of `rhs_pool` right-hand sides of that entry."""
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate_hz, size=n))
     out = []
     for i in range(n):
-        N = int(rng.choice([32, 64, 128, 256]))
-        K = int(rng.integers(4, 13))
-        sigma = float(10.0 ** rng.uniform(2.0, 5.0))
-        r = float(rng.uniform(0.5, 1.0))
-        ell = bool(rng.integers(0, 2))
-        if ell:
-            ax = (r, r * float(rng.uniform(0.7, 1.0)), r * float(rng.uniform(0.6, 1.0)))
+        if n_pks_models and rng.uniform() < pks_fraction:
+            out.append(ServingRequest(float(t[i]), "pks", int(rng.integers(0, n_pks_models)), 0))
         else:
-            ax = (r, r, r)
-        half = 1.25 * r * (N + 1) / max(N - 5, 1) if N > 8 else 1.5 * r
-        out.append(dict(t=float(t[i]), N=N, K=K, sigma=sigma,
-                        geom=Geometry(1 if ell else 0, (0.0, 0.0, 0.0), ax),
-                        lo=-half, hi=half,
-                        poly=rng.uniform(-1, 1, size=20).tolist(),
-                        gauss=float(rng.uniform(0.5, 3.0))))
+            m = int(rng.integers(0, n_models))
+            out.append(ServingRequest(float(t[i]), "solve", m, m * 1000 + int(rng.integers(0, rhs_pool))))
     return out
+
+
+def pks_run_catalog(seed: int, n_models: int, Ns=(32, 64, 128), K_range=(4, 8), steps=10) -> list:
+    rng = np.random.default_rng(seed)
+    return [PksRunModel(int(rng.choice(np.asarray(Ns))), int(rng.integers(K_range[0], K_range[1] + 1)),
+                        steps) for _ in range(n_models)]
 
 
 __all__ = [
     "Gaussian", "Geometry", "Workload", "WORKLOADS", "TEST_A_RHO0", "TEST_A_C0",
     "TEST_B_RHO0", "TEST_B_C0", "OFFC_RHO0", "OFFC_C0", "manufactured_u",
-    "manufactured_grad", "random_rhs", "random_field", "serving_requests",
+    "manufactured_grad", "random_rhs", "random_field", "ServingModel", "PksRunModel",
+    "serving_catalog", "poly_gauss_coeffs", "poly_gauss_rhs", "ServingRequest", "serving_stream",
+    "pks_run_catalog",
 ]
