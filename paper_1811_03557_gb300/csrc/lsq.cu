@@ -461,9 +461,11 @@ static int cholesky_factor(LsqFactor &f, const double *A0, double *R, int *statu
 
 // Mixed precision: column equilibration d (FP64), Gram of A D with FP32
 // products (chunk sums in FP64), FP32 Cholesky; the refinement of every solve
-// is FP64 against the original A (the factor only preconditions it).
-static int mixed_factor(LsqFactor &f, const double *A0, double *Rinv, double *dscale, int *status,
-                        cudaStream_t s) {
+// is FP64 against the original A (the factor only preconditions it).  Past
+// the in-shared-memory size (2 n^2 floats) the Cholesky of the same Gram runs
+// in FP64 from global memory and R^-1 is formed separately (*rinv_done = 0).
+static int mixed_factor(LsqFactor &f, const double *A0, double *R, double *Rinv, double *dscale,
+                        int *status, int *rinv_done, cudaStream_t s) {
     const int m = f.m, n = f.n;
     const int nb = (n + kGT - 1) / kGT;
     const int ntiles = nb * (nb + 1) / 2;
@@ -474,7 +476,10 @@ static int mixed_factor(LsqFactor &f, const double *A0, double *Rinv, double *ds
     const int rows_per = ((m + chunks - 1) / chunks + kGR - 1) / kGR * kGR;
     chunks = (m + rows_per - 1) / rows_per;
     const size_t nn = (size_t)n * n;
-    DPM_RET(f.X.reserve(sizeof(float) * nn * (size_t)chunks + sizeof(double) * nn + 16));
+    const size_t smem = 2 * nn * sizeof(float);
+    const bool in_smem = smem <= 226 * 1024;
+    // partials [chunks][n][n] floats, then G [n][n] (and W [n][n] for the FP64 Cholesky)
+    DPM_RET(f.X.reserve(sizeof(float) * nn * (size_t)chunks + sizeof(double) * nn * (in_smem ? 1 : 2) + 16));
     float *part = f.X.as<float>();
     double *G = reinterpret_cast<double *>(part + nn * chunks + (nn * chunks & 1));
     {
@@ -486,8 +491,14 @@ static int mixed_factor(LsqFactor &f, const double *A0, double *Rinv, double *ds
         k_syrk_reduce32<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(n, chunks, part, G);
         DPM_LAUNCHED();
     }
-    const size_t smem = 2 * nn * sizeof(float);
-    if (smem > 226 * 1024) { set_error("least squares: %d columns exceed the in-smem Cholesky", n); return DPM_EUNSUPPORTED; }
+    if (!in_smem) {
+        DPM_PROF("lsq_cholesky", s);
+        k_cholesky<<<1, 1024, 0, s>>>(n, G, R, G + nn, 0, status);
+        DPM_LAUNCHED();
+        *rinv_done = 0;
+        return DPM_OK;
+    }
+    *rinv_done = 1;
     DPM_CUDA(cudaFuncSetAttribute(k_cholesky32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     {
         DPM_PROF("lsq_cholesky", s);
@@ -519,15 +530,16 @@ int lsq_factor(LsqFactor &f, const int *cond_flag, cudaStream_t s) {
                    kLsqMaxRhs * ((size_t)n + (size_t)m) + kLsqMaxRhs * (size_t)n;
     double *dscale = Rinv + (size_t)n * n;
     f.equilibrated = false;
+    int rinv_done = 0;
     if (f.method == LsqFactor::kHouseholder) {
         DPM_RET(householder_factor(f, A0, w, rdiag, R, status, s));
     } else if (f.method == LsqFactor::kCholeskyQR) {
         DPM_RET(cholesky_factor(f, A0, R, status, s));
     } else {
-        DPM_RET(mixed_factor(f, A0, Rinv, dscale, status, s));
+        DPM_RET(mixed_factor(f, A0, R, Rinv, dscale, status, &rinv_done, s));
         f.equilibrated = true;
     }
-    if (!f.equilibrated) {
+    if (!rinv_done) {
         DPM_PROF("lsq_rinv", s);
         const int warps = 4;
         k_rinv<<<(n + warps - 1) / warps, 32 * warps, sizeof(double) * warps * n, s>>>(n, R, Rinv, status);

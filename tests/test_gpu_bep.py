@@ -115,3 +115,23 @@ def test_elliptic_solve_matches_oracle(ctx, prec, tol):
     X, Y, Z = O.mesh(w.N, w.lo, w.hi)
     assert np.max(np.abs(np.where(s.sets["Mp"], u - manufactured_u(X, Y, Z), 0))) < 1e-2
     b.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(abi.DPM_PREC_FP64, 1e-11), (abi.DPM_PREC_FP32, 1e-4)])
+@pytest.mark.parametrize("K", [9, 12])
+def test_elliptic_solve_many_harmonics(ctx, prec, tol, K):
+    """K = 9 and 12 (200 and 338 columns, past the in-shared-memory Cholesky):
+    the serving mix's upper range of harmonic degrees on an N=32 ellipsoid."""
+    geom, N, lo, hi, sigma = Geometry.ellipsoid(0.9, 0.75, 0.6), 32, -1.125, 1.125, 3.0e3
+    b = GpuBep(ctx, geom, N, lo, hi, sigma, K, 1, prec)
+    s = O.DPMSetup(geom, N, lo, hi, K, 1, sigma)
+    f, gn = manufactured_case(s, geom, N, lo, hi, sigma, s.xf, s.normal)
+    if prec == abi.DPM_PREC_FP32:
+        f = f.astype(np.float32).astype(np.float64)
+    u, C = b.solve(f, gn)
+    uo, Co, _ = O.dpm_elliptic_solve(s, f, gn)
+    Np = s.sets["Np"]
+    e = rel(u[Np], uo[Np])
+    print(f"elliptic K={K} prec={prec} rel err on N+ {e:.3e}")
+    assert e < tol
+    b.close()
