@@ -510,6 +510,7 @@ class ServingReport:
     evictions: int
     max_busy_slots: int
     peak_bytes: int
+    by_N: dict
     errors: list
 
     @staticmethod
@@ -525,6 +526,11 @@ class ServingReport:
         last = max((r.done for r in sol), default=first)
         span = max(last - first, 1e-9)
         solves = [e for e in eng.events if e[1] == "solve"]
+        by_N = {}
+        for r in sol:
+            by_N.setdefault(eng.models[r.model].spec.N, []).append(r.latency * 1e3)
+        by_N = {str(k): {"n": len(v), "p50_ms": pct(np.array(v), 50), "p99_ms": pct(np.array(v), 99)}
+                for k, v in sorted(by_N.items())}
         return ServingReport(
             n=len(rec), ok=sum(r.ok for r in rec), failed=sum(not r.ok for r in rec),
             elapsed_s=t_end, solve_p50_ms=pct(lat, 50), solve_p99_ms=pct(lat, 99),
@@ -535,7 +541,7 @@ class ServingReport:
             mean_batch=float(np.mean([e[2][1] for e in solves])) if solves else 0.0,
             builds=sum(1 for e in eng.events if e[1] == "build"),
             evictions=sum(1 for e in eng.events if e[1] == "evict"),
-            max_busy_slots=eng.busy_max, peak_bytes=eng.peak_bytes,
+            max_busy_slots=eng.busy_max, peak_bytes=eng.peak_bytes, by_N=by_N,
             errors=sorted({r.error for r in rec if not r.ok})[:5])
 
     def as_dict(self):
