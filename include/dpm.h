@@ -154,8 +154,9 @@ int dpm_classify(dpm_ctx *ctx, const dpm_geom *geom, int N, double lo, double hi
  *         DPM_PREC_FP64.  u may equal q (in place); otherwise they must not
  *         overlap.
  * Requires 2 <= N <= 256, h > 0, sigma >= 0, B >= 1.  DPM_PREC_TC32 requires
- * N = 128 (DPM_EUNSUPPORTED otherwise).  Scratch: the context's workspace,
- * grown on demand.
+ * N = 128 (DPM_EUNSUPPORTED otherwise) and a 16-byte aligned q (its planes
+ * are staged by bulk copies; DPM_EINVAL otherwise).  Scratch: the context's
+ * workspace, grown on demand.
  */
 int dpm_aux_solve_batched(dpm_ctx *ctx, int N, double h, double sigma, int B,
                           const void *q, void *u, int precision, cudaStream_t stream);

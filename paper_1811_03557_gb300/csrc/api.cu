@@ -100,6 +100,14 @@ int run_ap(int prec, ApParams p, const std::vector<ApRhs<T>> &rhs, DevBuf &work,
     size_t cb = std::max<size_t>(1, std::min<size_t>(B, kWorkCap / cube));
     size_t extra = 0;  // tensor-core solver: staged shell right-hand sides after the cubes
     if (prec == DPM_PREC_TC32) extra = tc_scratch_elems(p, (int)cb) * sizeof(float);
+    if (prec == DPM_PREC_TC32) {
+        // the tensor-core passes stage dense inputs with bulk copies (16-byte aligned)
+        for (const auto &r : rhs)
+            if (reinterpret_cast<uintptr_t>(r.f) & 15) {
+                set_error("tensor-core AP solve: f must be 16-byte aligned");
+                return DPM_EINVAL;
+            }
+    }
     DPM_RET(work.reserve(cb * cube + extra));
     if (prec == DPM_PREC_TC32) p.scratch = reinterpret_cast<float *>(static_cast<char *>(work.p) + cb * cube);
     DPM_RET(desc.reserve(sizeof(ApRhs<T>) * B));

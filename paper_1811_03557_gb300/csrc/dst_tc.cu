@@ -19,7 +19,8 @@
 // blocks are pre-split on the host, scaled by 2^12.
 //
 // CTA = 128 threads (4 warps = the 128 TMEM lanes), 2 CTAs per SM, persistent
-// over work items.  Every wait on the MMA-completion mbarrier is bounded; on
+// over work items; each item's input is staged by bulk copies (TMA) into the
+// operand tiles while the previous item writes its output.  Every wait on the MMA-completion mbarrier is bounded; on
 // expiry the kernel records an error in g_tc_status and stops.
 #include <algorithm>
 #include <map>
@@ -79,11 +80,6 @@ __device__ __forceinline__ float pow2_scale(float m, float *inv) {
     return ldexpf(1.f, 14 - e);
 }
 
-__device__ __forceinline__ void split2(float v, __half &hi, __half &lo) {
-    hi = __float2half_rn(v);
-    lo = __float2half_rn(v - __half2float(hi));
-}
-
 // hi/lo split of two values at once, packed as f16x2 (first value in the low half).
 __device__ __forceinline__ void split_pack(float a, float b, uint32_t &hi, uint32_t &lo) {
     const __half2 h = __floats2half2_rn(a, b);
@@ -98,7 +94,6 @@ struct Smem {
     __device__ unsigned char *A(int t) const { return base + kOffA + t * kATile; }
     __device__ unsigned char *Bt(int t) const { return base + kOffB + t * kBTile; }
     __device__ float *sE() const { return reinterpret_cast<float *>(base + kOffScale); }
-    __device__ float *sO() const { return reinterpret_cast<float *>(base + kOffScale) + kN; }
     __device__ float *w() const { return reinterpret_cast<float *>(base + kOffW); }
     __device__ float *red() const { return reinterpret_cast<float *>(base + kOffRed); }
     __device__ uint64_t *bar() const { return reinterpret_cast<uint64_t *>(base + kOffBar); }
@@ -115,9 +110,10 @@ __device__ __forceinline__ Smem smem_base() {
 __device__ void tc_prologue(const Smem &S, const TcArgs &a) {
     const int t = threadIdx.x;
     uint4 *dst = reinterpret_cast<uint4 *>(S.Bt(0));
-    for (int i = t; i < 4 * kBTile / 16; i += kThreads) dst[i] = a.bops[i];
+    for (int i = t; i < 4 * kBTile / 16; i += (int)blockDim.x) dst[i] = a.bops[i];
     if (t == 0) {
-        tc::mbar_init(S.bar(), 1);
+        tc::mbar_init(S.bar(), 1);      // MMA completion
+        tc::mbar_init(S.bar() + 1, 1);  // input bulk copies
         tc::fence_mbar_init();
     }
     if ((t >> 5) == 0) {
@@ -173,14 +169,22 @@ __device__ __forceinline__ uint32_t mn_off(int m, int k) {
                       (m & 7) * 2);
 }
 
+struct NoWork {
+    __device__ void operator()() const {}
+};
+
 // Operands written -> MMA issued -> completion observed by every thread.
-template <bool MN = false>
-__device__ __forceinline__ bool run_transform(const Smem &S, uint32_t tm, uint32_t &phase) {
+// `during` runs on every thread while the MMAs execute (it must not touch the
+// operand tiles or TMEM).
+template <bool MN = false, class F = NoWork>
+__device__ __forceinline__ bool run_transform(const Smem &S, uint32_t tm, uint32_t &phase,
+                                              F during = F()) {
     tc::fence_async_smem();
     tc::tc_fence_before_sync();
     __syncthreads();
     tc::tc_fence_after_sync();
     if (threadIdx.x == 0) issue_transform<MN>(S, tm);
+    during();
     bool ok = tc::mbar_wait(S.bar(), phase, kWaitIters);
     phase ^= 1u;
     tc::tc_fence_after_sync();
@@ -218,18 +222,27 @@ __device__ __forceinline__ float half_max(float v) {  // max over a 16-lane half
 }
 
 // ---------------------------------------------------------------------------
-// Plane pass.  One CTA per SM, 8 warps, persistent over items (rhs b, plane i).
-// The plane's input (f, or Z for the inverse pass) is brought into shared
-// memory by one bulk copy (TMA) issued as soon as the previous item has read
-// its buffer, so it streams in while that item is in its MMAs and epilogues.
+// Plane pass.  256 threads (warps w and w+4 share TMEM lanes 32(w%4)..+31 and
+// split the columns), two CTAs per SM,
+// persistent over items (rhs b, plane i).  The FP32 input plane (64 KB) is
+// staged in the operand region itself: it is read into registers before the
+// first operand tiles are written, and the bulk copy (TMA) of the next item's
+// plane is issued as soon as this item's second MMA has completed, so it
+// streams in during this item's output phase.  The other CTA on the SM runs
+// its MMAs and memory waits while this one computes, and the reverse.
 // INV = false: q = fscale f (on M^+ when masked) + L[v_gamma] on the shell
 //   (staged values from k_shell_rhs), forward along k then j, Z[i][b][c] out.
 // INV = true: reads Z, along c -> k then b -> j, writes u (masked to N^+)
 //   and/or the trace on gamma_in.
+// Operand scaling: the first transform's A rows (grid lines) get one
+// power-of-two scale each; the second transform's operand gets one scale from
+// the bound |A2| <= 256 max|x| (a 64-term fold of |x| <= max|x| with |S| <= 1,
+// then a sum of two rows), which keeps every f16 value below 2^14 without a
+// reduction over the tile.
 // ---------------------------------------------------------------------------
 constexpr int kPlaneThreads = 256;
-constexpr int kRawBytes = kN * kN * 4;                   // one fp32 plane
-constexpr int kPlaneSmem = kRawBytes + kSmemUsed + 1024;
+constexpr int kRawBytes = kN * kN * 4;                   // one fp32 plane = the four A tiles
+static_assert(kRawBytes == 4 * kATile, "the input plane is staged in the operand tiles");
 
 // q on the shell for every right-hand side that has a density:
 // qsh[b][e] = (sigma + 6/h^2) v(self) - (1/h^2) sum of v over the 6 neighbours.
@@ -257,58 +270,61 @@ __device__ __forceinline__ const float *plane_src(const ApRhs<float> &r, const f
 }
 
 template <bool INV>
-__global__ void __launch_bounds__(kPlaneThreads, 1)
+__global__ void __launch_bounds__(kPlaneThreads, 2)
 k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
-    extern __shared__ __align__(1024) unsigned char sm_raw[];
-    unsigned char *base = sm_raw + ((1024u - (tc::smem_u32(sm_raw) & 1023u)) & 1023u);
-    float *raw = reinterpret_cast<float *>(base);
-    const Smem S{base + kRawBytes};
+    const Smem S = smem_base();
+    tc_prologue(S, a);
+    float *raw = reinterpret_cast<float *>(S.A(0));
     uint64_t *bar_ld = S.bar() + 1;
-    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    // prologue: sine blocks, barriers, TMEM
-    {
-        uint4 *dst = reinterpret_cast<uint4 *>(S.Bt(0));
-        for (int q = t; q < 4 * kBTile / 16; q += kPlaneThreads) dst[q] = a.bops[q];
-        if (t == 0) {
-            tc::mbar_init(S.bar(), 1);
-            tc::mbar_init(bar_ld, 1);
-            tc::fence_mbar_init();
-        }
-        if (warp == 0) {
-            tc::tmem_alloc(S.tslot(), kTmemCols);
-            tc::tmem_relinquish();
-        }
-        tc::fence_async_smem();
-        tc::tc_fence_before_sync();
-        __syncthreads();
-        tc::tc_fence_after_sync();
-    }
+    float *rowinv = S.sE();  // inverse scale of each A row of the first transform
+    float *wmax = S.red();   // max |x| per warp
     const uint32_t tm = *S.tslot();
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int q4 = warp & 3, hc = warp >> 2;  // TMEM lane quarter, column half
+    const int L = 32 * q4 + lane;             // TMEM lane = row of D owned by this thread
+    const uint32_t lane_addr = tm + ((uint32_t)(32 * q4) << 16);
     uint32_t phase = 0, ld_phase = 0;
     const int nitems = a.B * kN;
     const float fs = (float)a.fscale;
-    const int q4 = warp & 3, half = warp >> 2;  // TMEM lane quarter, column half
-    const int L = 32 * q4 + lane;                // TMEM lane (row of D) of this thread
-    const uint32_t lane_addr = tm + ((uint32_t)(32 * q4) << 16);
-    // first input in flight
     int item = blockIdx.x;
-    if (t == 0 && item < nitems) {
+    bool inflight = false;  // a bulk copy into raw completes on bar_ld
+    if (item < nitems) {
         const float *src = plane_src<INV>(rhs[item / kN], work, item / kN, item % kN);
         if (src) {
-            tc::mbar_arrive_expect_tx(bar_ld, kRawBytes);
-            tc::bulk_g2s(raw, src, kRawBytes, bar_ld);
+            if (t == 0) {
+                tc::mbar_arrive_expect_tx(bar_ld, kRawBytes);
+                tc::bulk_g2s(raw, src, kRawBytes, bar_ld);
+            }
+            inflight = true;
         }
     }
     bool ok = true;
+    bool pre = false;  // raw was zeroed for this shell-only item during the last item
     for (; item < nitems && ok; item += gridDim.x) {
         const int b = item / kN, i = item % kN;
         const ApRhs<float> r = rhs[b];
+        const int nx = item + gridDim.x;
+        const float *nsrc = nullptr;
+        bool nsparse = false;  // next item: shell-only right-hand side (a BEP column)
+        if (nx < nitems) {
+            const ApRhs<float> &rn = rhs[nx / kN];
+            nsrc = plane_src<INV>(rn, work, nx / kN, nx % kN);
+            nsparse = !INV && !rn.f && rn.dens;
+        }
+        int ge0 = 0, ge1 = 0;  // gamma_in nodes of this plane (trace output)
+        if (INV && r.out_trace) {
+            ge0 = a.rp_gin[(int64_t)i * kN];
+            ge1 = a.rp_gin[(int64_t)(i + 1) * kN];
+        }
         // ---- input plane in smem ----------------------------------------------
-        if (plane_src<INV>(r, work, b, i)) {
+        if (inflight) {
             const bool got = tc::mbar_wait(bar_ld, ld_phase, kWaitIters);
-            ld_phase ^= 1u;
+            if (got) {
+                ld_phase ^= 1u;
+                inflight = false;
+            }
             if (!got) atomicExch(&g_tc_status, 1);
-            if (!__syncthreads_and(got ? 1 : 0)) break;
+            if (!__syncthreads_and(got ? 1 : 0)) { ok = false; break; }
             if (!INV && (a.mask_f || fs != 1.f)) {
                 // scale f and keep it on M^+ only
                 const uint8_t *lab = a.labels + (size_t)i * kN * kN;
@@ -326,7 +342,7 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
                 }
                 __syncthreads();
             }
-        } else if (!INV) {
+        } else if (!INV && !pre) {
             float4 *r4 = reinterpret_cast<float4 *>(raw);
             for (int q = t; q < kN * kN / 4; q += kPlaneThreads) r4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
             __syncthreads();
@@ -342,9 +358,9 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
         // warp: 16 rows, two per step; lanes 0-15 take row 2s, lanes 16-31 row
         // 2s+1, lane l' = l mod 16 holding x[4l'..4l'+3] and x[124-4l'..127-4l'],
         // so the fold (sums e, differences o at m' = 4l'+u) is thread-local.
+        // Rows j and 127-j go to A rows 2j and 2j+1 (adjacent TMEM lanes).
         const int lp = lane & 15, rsel = lane >> 4;
         float xa[8][4], xb[8][4];
-        float amax = 0.f;
 #pragma unroll
         for (int st = 0; st < 8; ++st) {
             const int row = warp * 16 + 2 * st + rsel;
@@ -352,89 +368,67 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
             const float4 v2 = reinterpret_cast<const float4 *>(raw)[row * (kN / 4) + 31 - lp];
             xa[st][0] = v1.x; xa[st][1] = v1.y; xa[st][2] = v1.z; xa[st][3] = v1.w;
             xb[st][0] = v2.x; xb[st][1] = v2.y; xb[st][2] = v2.z; xb[st][3] = v2.w;
-            amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v1.x), fabsf(v1.y)), fmaxf(fabsf(v1.z), fabsf(v1.w))));
-            amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v2.x), fabsf(v2.y)), fmaxf(fabsf(v2.z), fabsf(v2.w))));
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-        if (lane == 0) S.red()[warp] = amax;
-        // raw is free once every warp is here: start the next item's input
-        __syncthreads();
-        amax = 0.f;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) amax = fmaxf(amax, S.red()[w]);
-        if (t == 0) {
-            const int nx = item + gridDim.x;
-            if (nx < nitems) {
-                const float *src = plane_src<INV>(rhs[nx / kN], work, nx / kN, nx % kN);
-                if (src) {
-                    tc::fence_async_smem();
-                    tc::mbar_arrive_expect_tx(bar_ld, kRawBytes);
-                    tc::bulk_g2s(raw, src, kRawBytes, bar_ld);
-                }
-            }
-        }
-        // one scale for the tile: |e|, |o| <= 2 max|x| -> scaled values < 2^14
-        float iA;
-        const float sA = pow2_scale(2.f * amax, &iA);
+        __syncthreads();  // the plane is in registers: the tiles may overwrite it
+        float wm = 0.f;
 #pragma unroll
         for (int st = 0; st < 8; ++st) {
             const int row = warp * 16 + 2 * st + rsel;
             const int LL = row < kH ? 2 * row : 2 * (kN - 1 - row) + 1;
+            float rm = 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) rm = fmaxf(rm, fmaxf(fabsf(xa[st][u]), fabsf(xb[st][u])));
+            rm = half_max(rm);
+            float rinv;
+            const float sr = pow2_scale(2.f * rm, &rinv);  // |e|, |o| <= 2 max|x| of the row
             float e[4], o[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 e[u] = xa[st][u] + xb[st][3 - u];
                 o[u] = xa[st][u] - xb[st][3 - u];
             }
-            put4(S.A(0), S.A(1), LL, 4 * lp, e, sA);
-            put4(S.A(2), S.A(3), LL, 4 * lp, o, sA);
+            put4(S.A(0), S.A(1), LL, 4 * lp, e, sr);
+            put4(S.A(2), S.A(3), LL, 4 * lp, o, sr);
+            if (lp == 0) rowinv[LL] = rinv;
+            wm = fmaxf(wm, rm);
         }
+#pragma unroll
+        for (int q = 16; q > 0; q >>= 1) wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, q));
+        if (lane == 0) wmax[warp] = wm;
         if (!run_transform(S, tm, phase)) { ok = false; break; }
         // ---- phase C: fold over rows (lanes L, L^1), A2 in MN-major layout --------
-        // This thread: columns c0 = 32 half + 16 cc of the sums (c = 2 col) and of
-        // the differences (c = 2 col + 1) -> folded values for c = 2 c0 .. 2 c0 + 31.
-        const float iE = iA * (1.f / kSScale), iO = iE;
-        float f2[2][32];
-        float mx = 0.f;
+        // Columns [32 hc, 32 hc + 32) of the sums (modes 2c') and of the
+        // differences (modes 2c'+1) of this thread's row, 16 at a time.
+        float amax = 0.f;
 #pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-            const int c0 = 32 * half + 16 * cc;
-            float de[16], dd[16];
-            tc::tmem_ld16(lane_addr + c0, de);
-            tc::tmem_ld16(lane_addr + kH + c0, dd);
-            tc::tmem_wait_ld();
-#pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const float oe = de[u] * iE, od = dd[u] * iO;
-                const float pe = __shfl_xor_sync(0xffffffffu, oe, 1);
-                const float pd = __shfl_xor_sync(0xffffffffu, od, 1);
-                f2[cc][2 * u] = (L & 1) ? (pe - oe) : (oe + pe);
-                f2[cc][2 * u + 1] = (L & 1) ? (pd - od) : (od + pd);
-                mx = fmaxf(mx, fmaxf(fabsf(f2[cc][2 * u]), fabsf(f2[cc][2 * u + 1])));
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) S.red()[warp] = mx;
-        __syncthreads();
-        mx = 0.f;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) mx = fmaxf(mx, S.red()[w]);
+        for (int w = 0; w < kPlaneThreads / 32; ++w) amax = fmaxf(amax, wmax[w]);
         float inv2;
-        const float s2 = pow2_scale(mx, &inv2);
+        const float s2 = pow2_scale(256.f * amax, &inv2);
         {
+            const float iD = rowinv[L] * (1.f / kSScale);
             const int p = L >> 1;
             unsigned char *thi = S.A((L & 1) ? 2 : 0), *tlo = S.A((L & 1) ? 3 : 1);
 #pragma unroll
-            for (int cc = 0; cc < 2; ++cc) {
-                const int c0 = 32 * half + 16 * cc;
+            for (int c0 = 32 * hc; c0 < 32 * hc + 32; c0 += 16) {
+                float de[16], dd[16];
+                tc::tmem_ld16(lane_addr + c0, de);
+                tc::tmem_ld16(lane_addr + kH + c0, dd);
+                tc::tmem_wait_ld();
+                float f2[32];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const float oe = de[u] * iD, od = dd[u] * iD;
+                    const float pe = __shfl_xor_sync(0xffffffffu, oe, 1);
+                    const float pd = __shfl_xor_sync(0xffffffffu, od, 1);
+                    f2[2 * u] = (L & 1) ? (pe - oe) : (oe + pe);
+                    f2[2 * u + 1] = (L & 1) ? (pd - od) : (od + pd);
+                }
 #pragma unroll
                 for (int q8 = 0; q8 < 4; ++q8) {
                     uint32_t hw[4], lw[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u)
-                        split_pack(f2[cc][8 * q8 + 2 * u] * s2, f2[cc][8 * q8 + 2 * u + 1] * s2, hw[u], lw[u]);
+                        split_pack(f2[8 * q8 + 2 * u] * s2, f2[8 * q8 + 2 * u + 1] * s2, hw[u], lw[u]);
                     const uint32_t off = mn_off(2 * c0 + 8 * q8, p);
                     *reinterpret_cast<uint4 *>(thi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
                     *reinterpret_cast<uint4 *>(tlo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
@@ -442,29 +436,49 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
             }
         }
         if (!run_transform<true>(S, tm, phase)) { ok = false; break; }
-        // ---- phase E: D2 (row = c = L), half 0: sums part, half 1: differences --
+        // ---- the operand region is free: stage the next item's input -------------
+        const bool stage_trace = INV && r.out_trace;
+        if (!stage_trace && nsrc) {
+            if (t == 0) {
+                tc::mbar_arrive_expect_tx(bar_ld, kRawBytes);
+                tc::bulk_g2s(raw, nsrc, kRawBytes, bar_ld);
+            }
+            inflight = true;
+        } else if (nsparse) {
+            float4 *r4 = reinterpret_cast<float4 *>(raw);
+            for (int q = t; q < kN * kN / 4; q += kPlaneThreads) r4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        // ---- phase E: D2 (row = c = L); columns [0,64) even j-modes, [64,128) odd --
         const float iout = inv2 * (1.f / kSScale);
         if (!INV) {
             float *wplane = work + ((size_t)b * kN + i) * kN * kN;
 #pragma unroll
-            for (int c0 = 0; c0 < kH; c0 += 16) {
-                float d[16];
-                tc::tmem_ld16(lane_addr + kH * half + c0, d);
-                tc::tmem_wait_ld();
-#pragma unroll
-                for (int u = 0; u < 16; ++u) wplane[(2 * (c0 + u) + half) * kN + L] = d[u] * iout;
-            }
-        } else {
-            float *stage = reinterpret_cast<float *>(S.A(0));  // 128 x 128 fp32 = 64 KB
-            const int64_t pbase = (int64_t)i * kN * kN;
-#pragma unroll
-            for (int c0 = 0; c0 < kH; c0 += 16) {
-                float d[16];
-                tc::tmem_ld16(lane_addr + kH * half + c0, d);
+            for (int c0 = kH * hc; c0 < kH * hc + kH; c0 += 32) {
+                float d0[16], d1[16];
+                tc::tmem_ld16(lane_addr + c0, d0);
+                tc::tmem_ld16(lane_addr + c0 + 16, d1);
                 tc::tmem_wait_ld();
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {
-                    const int j = 2 * (c0 + u) + half;
+                    const int c = c0 + u, c1 = c0 + 16 + u;
+                    const int j0 = c < kH ? 2 * c : 2 * (c - kH) + 1;
+                    const int j1 = c1 < kH ? 2 * c1 : 2 * (c1 - kH) + 1;
+                    wplane[j0 * kN + L] = d0[u] * iout;
+                    wplane[j1 * kN + L] = d1[u] * iout;
+                }
+            }
+        } else {
+            float *stage = raw;  // 128 x 128 fp32 (the operand region, free again)
+            const int64_t pbase = (int64_t)i * kN * kN;
+#pragma unroll
+            for (int c0 = kH * hc; c0 < kH * hc + kH; c0 += 16) {
+                float d[16];
+                tc::tmem_ld16(lane_addr + c0, d);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int c = c0 + u;
+                    const int j = c < kH ? 2 * c : 2 * (c - kH) + 1;
                     const float val = d[u] * iout;
                     if (r.out_dense) {
                         const int64_t pp = pbase + (int64_t)j * kN + L;
@@ -477,26 +491,32 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
             }
             if (r.out_trace) {
                 __syncthreads();
-                const int e0 = a.rp_gin[(int64_t)i * kN], e1 = a.rp_gin[(int64_t)(i + 1) * kN];
-                for (int e = e0 + t; e < e1; e += kPlaneThreads) {
+                for (int e = ge0 + t; e < ge1; e += kPlaneThreads) {
                     const int pg = a.gin[e];
                     r.out_trace[e] = stage[((pg / kN) % kN) * kN + pg % kN];
+                }
+                // the staging writes precede the next bulk copy into the same bytes
+                tc::fence_async_smem();
+                __syncthreads();
+                if (nsrc) {
+                    if (t == 0) {
+                        tc::mbar_arrive_expect_tx(bar_ld, kRawBytes);
+                        tc::bulk_g2s(raw, nsrc, kRawBytes, bar_ld);
+                    }
+                    inflight = true;
                 }
             }
         }
         tc::tc_fence_before_sync();
         __syncthreads();
         tc::tc_fence_after_sync();
+        pre = nsparse;
     }
     // a bulk copy issued for an item this CTA did not reach must land before exit
-    if (!ok) {
-        tc::mbar_wait(bar_ld, ld_phase, kWaitIters);
-    }
-    tc::tc_fence_before_sync();
-    __syncthreads();
-    tc::tc_fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(tm, kTmemCols);
+    if (inflight) tc::mbar_wait(bar_ld, ld_phase, kWaitIters);
+    tc_epilogue(S);
 }
+
 
 // ---------------------------------------------------------------------------
 // Pencil pass along i for a fixed j-mode jb: forward, scale/lambda, inverse.
@@ -518,18 +538,47 @@ k_tc_pencil(TcArgs a, const ApRhs<float> *rhs, float *work) {
     const int nitems = a.B * kN;
     const size_t sN2 = (size_t)kN * kN;
     const uint32_t lane_addr = tm + ((uint32_t)(warp * 32) << 16);
+    // The item's column block Z[b][0..128)[jb][0..128) (128 rows of 512 B) is
+    // staged in the operand region by 128 bulk copies issued by warp 0 once the
+    // previous item's second MMA has completed.
+    float *raw = reinterpret_cast<float *>(S.A(0));
+    uint64_t *bar_ld = S.bar() + 1;
+    uint32_t ld_phase = 0;
+    const int lane = t & 31;
+    auto stage_block = [&](int it) {
+        const float *src = work + (size_t)(it / kN) * kN * sN2 + (size_t)(it % kN) * kN;
+        if (lane == 0) tc::mbar_arrive_expect_tx(bar_ld, kN * kN * 4);
+        __syncwarp();
+        for (int ii = lane; ii < kN; ii += 32)
+            tc::bulk_g2s(raw + ii * kN, src + (size_t)ii * sN2, kN * 4, bar_ld);
+    };
+    bool inflight = false;
+    if (blockIdx.x < nitems) {
+        if (warp == 0) stage_block(blockIdx.x);
+        inflight = true;
+    }
     for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
         const int b = item / kN, jb = item % kN;
         (void)rhs;
         float *base = work + (size_t)b * kN * sN2 + (size_t)jb * kN + t;
+        {
+            const bool got = tc::mbar_wait(bar_ld, ld_phase, kWaitIters);
+            if (got) {
+                ld_phase ^= 1u;
+                inflight = false;
+            }
+            if (!got) atomicExch(&g_tc_status, 1);
+            if (!__syncthreads_and(got ? 1 : 0)) break;
+        }
         // ---- phase A: fold along i, split, per-row (per-c) scale -----------
         float e[kH], o[kH];
 #pragma unroll
         for (int mp = 0; mp < kH; ++mp) {
-            const float x1 = base[(size_t)mp * sN2], x2 = base[(size_t)(kN - 1 - mp) * sN2];
+            const float x1 = raw[mp * kN + t], x2 = raw[(kN - 1 - mp) * kN + t];
             e[mp] = x1 + x2;
             o[mp] = x1 - x2;
         }
+        __syncthreads();  // the block is in registers: the tiles may overwrite it
         float me = 0.f, mo = 0.f;
 #pragma unroll
         for (int mp = 0; mp < kH; ++mp) {
@@ -580,6 +629,10 @@ k_tc_pencil(TcArgs a, const ApRhs<float> *rhs, float *work) {
             put8(S.A(2), S.A(3), t, k0, o + k0, so2);
         }
         if (!run_transform(S, tm, phase)) break;
+        if (item + (int)gridDim.x < nitems) {
+            if (warp == 0) stage_block(item + gridDim.x);
+            inflight = true;
+        }
         // ---- phase E: D3[c][i'] -> Z[i][jb][c] ---------------------------------
 #pragma unroll
         for (int c0 = 0; c0 < 2 * kH; c0 += 16) {
@@ -597,6 +650,8 @@ k_tc_pencil(TcArgs a, const ApRhs<float> *rhs, float *work) {
         __syncthreads();
         tc::tc_fence_after_sync();
     }
+    // copies issued for an item this CTA did not reach must land before exit
+    if (inflight) tc::mbar_wait(bar_ld, ld_phase, kWaitIters);
     tc_epilogue(S);
 }
 
@@ -640,8 +695,8 @@ int tc_configure() {
     static std::mutex mu;
     std::lock_guard<std::mutex> lk(mu);
     if (done) return DPM_OK;
-    DPM_CUDA(cudaFuncSetAttribute(k_tc_plane<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPlaneSmem));
-    DPM_CUDA(cudaFuncSetAttribute(k_tc_plane<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPlaneSmem));
+    DPM_CUDA(cudaFuncSetAttribute(k_tc_plane<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    DPM_CUDA(cudaFuncSetAttribute(k_tc_plane<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
     DPM_CUDA(cudaFuncSetAttribute(k_tc_pencil, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
     done = true;
     return DPM_OK;
@@ -697,7 +752,7 @@ int ap_solve_tc(const ApParams &p, const ApRhs<float> *rhs_dev, float *work, cud
     }
     {
         DPM_PROF("tc_plane_fwd", s);
-        k_tc_plane<false><<<std::min(nitems, sms), kPlaneThreads, kPlaneSmem, s>>>(a, rhs_dev, work);
+        k_tc_plane<false><<<std::min(nitems, 2 * sms), kPlaneThreads, kSmemBytes, s>>>(a, rhs_dev, work);
         DPM_LAUNCHED();
     }
     {
@@ -707,7 +762,7 @@ int ap_solve_tc(const ApParams &p, const ApRhs<float> *rhs_dev, float *work, cud
     }
     {
         DPM_PROF("tc_plane_inv", s);
-        k_tc_plane<true><<<std::min(nitems, sms), kPlaneThreads, kPlaneSmem, s>>>(a, rhs_dev, work);
+        k_tc_plane<true><<<std::min(nitems, 2 * sms), kPlaneThreads, kSmemBytes, s>>>(a, rhs_dev, work);
         DPM_LAUNCHED();
     }
     return DPM_OK;
