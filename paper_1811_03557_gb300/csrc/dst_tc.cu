@@ -18,10 +18,13 @@
 // hi*hi' + hi*lo' + lo*hi' (the dropped lo*lo' is ~2^-22 relative).  Sine
 // blocks are pre-split on the host, scaled by 2^12.
 //
-// CTA = 128 threads (4 warps = the 128 TMEM lanes), 2 CTAs per SM, persistent
-// over work items; each item's input is staged by bulk copies (TMA) into the
-// operand tiles while the previous item writes its output.  Every wait on the MMA-completion mbarrier is bounded; on
+// CTA = 256 threads (8 warps; warps w and w+4 share the TMEM lanes 32(w%4)..
+// and split the columns), 2 CTAs per SM at 128 registers, persistent over work
+// items; each item's input is staged by bulk copies (TMA) into the operand
+// tiles while the previous item writes its output.  Every wait on the MMA-completion mbarrier is bounded; on
 // expiry the kernel records an error in g_tc_status and stops.
+#include <cuda.h>
+
 #include <algorithm>
 #include <map>
 #include <math.h>
@@ -38,7 +41,6 @@ namespace {
 
 constexpr int kN = 128;             // grid points per axis handled by these kernels
 constexpr int kH = 64;              // fold length
-constexpr int kThreads = 128;
 constexpr uint32_t kTmemCols = 128; // D_E in columns [0,64), D_O in [64,128)
 constexpr float kSScale = 4096.f;   // sine blocks are stored times 2^12
 constexpr uint32_t kWaitIters = 1u << 26;
@@ -50,7 +52,8 @@ constexpr int kOffA = 0;                           // E_hi, E_lo, O_hi, O_lo
 constexpr int kOffB = 4 * kATile;                  // SE_hi, SE_lo, SO_hi, SO_lo
 constexpr int kOffScale = kOffB + 4 * kBTile;      // float sE[128], sO[128]
 constexpr int kOffW = kOffScale + 2 * kN * 4;      // float weights[128]
-constexpr int kOffRed = kOffW + kN * 4;            // float red[8]
+constexpr int kOffXch = kOffW + kN * 4;            // float xch[4][128] (pencil row maxima)
+constexpr int kOffRed = kOffXch + 4 * kN * 4;      // float red[16]
 constexpr int kOffBar = kOffRed + 64;              // mbarrier
 constexpr int kOffTmem = kOffBar + 16;             // TMEM base address
 constexpr int kSmemUsed = kOffTmem + 16;
@@ -95,6 +98,7 @@ struct Smem {
     __device__ unsigned char *Bt(int t) const { return base + kOffB + t * kBTile; }
     __device__ float *sE() const { return reinterpret_cast<float *>(base + kOffScale); }
     __device__ float *w() const { return reinterpret_cast<float *>(base + kOffW); }
+    __device__ float *xch() const { return reinterpret_cast<float *>(base + kOffXch); }
     __device__ float *red() const { return reinterpret_cast<float *>(base + kOffRed); }
     __device__ uint64_t *bar() const { return reinterpret_cast<uint64_t *>(base + kOffBar); }
     __device__ uint32_t *tslot() const { return reinterpret_cast<uint32_t *>(base + kOffTmem); }
@@ -520,47 +524,66 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
 
 // ---------------------------------------------------------------------------
 // Pencil pass along i for a fixed j-mode jb: forward, scale/lambda, inverse.
-// Thread t = c (the contiguous index), A rows = c, K = fold index over i / a.
+// 256 threads, two CTAs per SM.  Thread (c, h) = (t mod 128, t / 128): A row
+// and TMEM lane c (the contiguous index), fold indices m' in [32h, 32h+32) of
+// both transforms, and D columns [64h, 64h+64) (the even modes for h = 0, the
+// odd ones for h = 1).  The inverse transform folds modes a and 127-a, which
+// have opposite parity, so the spectral values pass through the operand
+// region (free once the first MMA has completed); per-row maxima of the two
+// halves meet in a small exchange area.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads, 2)
-k_tc_pencil(TcArgs a, const ApRhs<float> *rhs, float *work) {
+constexpr int kPencilThreads = 256;
+
+__global__ void __launch_bounds__(kPencilThreads, 2)
+k_tc_pencil(TcArgs a, const ApRhs<float> *rhs, float *work, const __grid_constant__ CUtensorMap zmap) {
     const Smem S = smem_base();
     tc_prologue(S, a);
     const uint32_t tm = *S.tslot();
-    const int t = threadIdx.x, warp = t >> 5;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int c = t & (kN - 1), h = t >> 7;
     uint32_t phase = 0;
     const float w4 = (float)(4.0 / (a.h * a.h));
-    for (int n = t; n < kN; n += kThreads) S.w()[n] = w4 * a.s2[n];
+    for (int n = t; n < kN; n += kPencilThreads) S.w()[n] = w4 * a.s2[n];
     __syncthreads();
     const float sig = (float)a.sigma;
     const double sc = 2.0 / (kN + 1);
     const float nscale = (float)(sc * sc * sc);
     const int nitems = a.B * kN;
     const size_t sN2 = (size_t)kN * kN;
-    const uint32_t lane_addr = tm + ((uint32_t)(warp * 32) << 16);
-    // The item's column block Z[b][0..128)[jb][0..128) (128 rows of 512 B) is
-    // staged in the operand region by 128 bulk copies issued by warp 0 once the
-    // previous item's second MMA has completed.
-    float *raw = reinterpret_cast<float *>(S.A(0));
+    const uint32_t lane_addr = tm + ((uint32_t)(32 * (warp & 3)) << 16);
+    float *raw = reinterpret_cast<float *>(S.A(0));  // staged block [i][c], later z[a][c]
+    float *xmax = S.xch();                           // [h][E/O][c] partial row maxima
     uint64_t *bar_ld = S.bar() + 1;
     uint32_t ld_phase = 0;
-    const int lane = t & 31;
+    // The item's column block Z[b][0..128)[jb][0..128) is staged in the operand
+    // region ([i][c], 64 KB) by one tensor copy (box 128 x 1 x 128 x 1 of the
+    // [b][i][j][c] workspace) issued once the previous item's second MMA has
+    // completed.
     auto stage_block = [&](int it) {
-        const float *src = work + (size_t)(it / kN) * kN * sN2 + (size_t)(it % kN) * kN;
-        if (lane == 0) tc::mbar_arrive_expect_tx(bar_ld, kN * kN * 4);
-        __syncwarp();
-        for (int ii = lane; ii < kN; ii += 32)
-            tc::bulk_g2s(raw + ii * kN, src + (size_t)ii * sN2, kN * 4, bar_ld);
+        if (lane == 0) {
+            tc::mbar_arrive_expect_tx(bar_ld, kN * kN * 4);
+            tc::tma_load_4d(raw, &zmap, 0, it % kN, 0, it / kN, bar_ld);
+        }
     };
     bool inflight = false;
     if (blockIdx.x < nitems) {
         if (warp == 0) stage_block(blockIdx.x);
         inflight = true;
     }
+    // max of |v| over this thread's half of a row: both halves via the exchange area
+    auto row_scales = [&](float me, float mo, float &ie, float &io, float &se, float &so) {
+        xmax[(2 * h) * kN + c] = me;
+        xmax[(2 * h + 1) * kN + c] = mo;
+        __syncthreads();
+        me = fmaxf(xmax[c], xmax[2 * kN + c]);
+        mo = fmaxf(xmax[kN + c], xmax[3 * kN + c]);
+        se = pow2_scale(me, &ie);
+        so = pow2_scale(mo, &io);
+    };
     for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
         const int b = item / kN, jb = item % kN;
         (void)rhs;
-        float *base = work + (size_t)b * kN * sN2 + (size_t)jb * kN + t;
+        float *base = work + (size_t)b * kN * sN2 + (size_t)jb * kN + c;
         {
             const bool got = tc::mbar_wait(bar_ld, ld_phase, kWaitIters);
             if (got) {
@@ -571,62 +594,58 @@ k_tc_pencil(TcArgs a, const ApRhs<float> *rhs, float *work) {
             if (!__syncthreads_and(got ? 1 : 0)) break;
         }
         // ---- phase A: fold along i, split, per-row (per-c) scale -----------
-        float e[kH], o[kH];
-#pragma unroll
-        for (int mp = 0; mp < kH; ++mp) {
-            const float x1 = raw[mp * kN + t], x2 = raw[(kN - 1 - mp) * kN + t];
-            e[mp] = x1 + x2;
-            o[mp] = x1 - x2;
-        }
-        __syncthreads();  // the block is in registers: the tiles may overwrite it
+        float e[32], o[32];
         float me = 0.f, mo = 0.f;
 #pragma unroll
-        for (int mp = 0; mp < kH; ++mp) {
-            me = fmaxf(me, fabsf(e[mp]));
-            mo = fmaxf(mo, fabsf(o[mp]));
+        for (int q = 0; q < 32; ++q) {
+            const int mp = 32 * h + q;
+            const float x1 = raw[mp * kN + c], x2 = raw[(kN - 1 - mp) * kN + c];
+            e[q] = x1 + x2;
+            o[q] = x1 - x2;
+            me = fmaxf(me, fabsf(e[q]));
+            mo = fmaxf(mo, fabsf(o[q]));
         }
-        float ie, io;
-        const float se = pow2_scale(me, &ie), so = pow2_scale(mo, &io);
+        float ie, io, se, so;
+        row_scales(me, mo, ie, io, se, so);  // its barrier also ends the reads of raw
 #pragma unroll
-        for (int k0 = 0; k0 < kH; k0 += 8) {
-            put8(S.A(0), S.A(1), t, k0, e + k0, se);
-            put8(S.A(2), S.A(3), t, k0, o + k0, so);
+        for (int k0 = 0; k0 < 32; k0 += 8) {
+            put8(S.A(0), S.A(1), c, 32 * h + k0, e + k0, se);
+            put8(S.A(2), S.A(3), c, 32 * h + k0, o + k0, so);
         }
         if (!run_transform(S, tm, phase)) break;
-        // ---- phase C: z[a] = D / lambda, fold over a, split -------------------
-        float z[kN];  // z[a], a = 0..127 (a = 2a' from sums, 2a'+1 from differences)
+        // ---- phase C: z[a] = D / lambda for this half's modes -> smem ------------
+        {
+            const float dsc = (h == 0 ? ie : io) * (1.f / kSScale);
+            const float wjc = S.w()[jb] + S.w()[c] + sig;
 #pragma unroll
-        for (int c0 = 0; c0 < 2 * kH; c0 += 16) {
-            float d[16];
-            tc::tmem_ld16(lane_addr + c0, d);
-            tc::tmem_wait_ld();
+            for (int c0 = 0; c0 < kH; c0 += 16) {
+                float d[16];
+                tc::tmem_ld16(lane_addr + kH * h + c0, d);
+                tc::tmem_wait_ld();
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const int am = c0 < kH ? 2 * (c0 + u) : 2 * (c0 + u - kH) + 1;
-                z[am] = d[u] * ((c0 < kH ? ie : io) * (1.f / kSScale));
+                for (int u = 0; u < 16; ++u) {
+                    const int am = 2 * (c0 + u) + h;  // mode index
+                    raw[am * kN + c] = d[u] * dsc * __fdividef(nscale, wjc + S.w()[am]);
+                }
             }
         }
-        const float wjc = S.w()[jb] + S.w()[t] + sig;
-#pragma unroll
-        for (int am = 0; am < kN; ++am) z[am] *= __fdividef(nscale, wjc + S.w()[am]);
-#pragma unroll
-        for (int mp = 0; mp < kH; ++mp) {
-            const float lo_ = z[mp], hi_ = z[kN - 1 - mp];
-            e[mp] = lo_ + hi_;
-            o[mp] = lo_ - hi_;
-        }
+        __syncthreads();
         me = 0.f;
         mo = 0.f;
 #pragma unroll
-        for (int mp = 0; mp < kH; ++mp) {
-            me = fmaxf(me, fabsf(e[mp]));
-            mo = fmaxf(mo, fabsf(o[mp]));
+        for (int q = 0; q < 32; ++q) {
+            const int mp = 32 * h + q;
+            const float lo_ = raw[mp * kN + c], hi_ = raw[(kN - 1 - mp) * kN + c];
+            e[q] = lo_ + hi_;
+            o[q] = lo_ - hi_;
+            me = fmaxf(me, fabsf(e[q]));
+            mo = fmaxf(mo, fabsf(o[q]));
         }
-        const float se2 = pow2_scale(me, &ie), so2 = pow2_scale(mo, &io);
+        row_scales(me, mo, ie, io, se, so);  // also ends the reads of z before the tiles
 #pragma unroll
-        for (int k0 = 0; k0 < kH; k0 += 8) {
-            put8(S.A(0), S.A(1), t, k0, e + k0, se2);
-            put8(S.A(2), S.A(3), t, k0, o + k0, so2);
+        for (int k0 = 0; k0 < 32; k0 += 8) {
+            put8(S.A(0), S.A(1), c, 32 * h + k0, e + k0, se);
+            put8(S.A(2), S.A(3), c, 32 * h + k0, o + k0, so);
         }
         if (!run_transform(S, tm, phase)) break;
         if (item + (int)gridDim.x < nitems) {
@@ -634,16 +653,19 @@ k_tc_pencil(TcArgs a, const ApRhs<float> *rhs, float *work) {
             inflight = true;
         }
         // ---- phase E: D3[c][i'] -> Z[i][jb][c] ---------------------------------
+        {
+            const float sc2 = (h == 0 ? ie : io) * (1.f / kSScale);
 #pragma unroll
-        for (int c0 = 0; c0 < 2 * kH; c0 += 16) {
-            float d[16];
-            tc::tmem_ld16(lane_addr + c0, d);
-            tc::tmem_wait_ld();
-            const float sc2 = (c0 < kH ? ie : io) * (1.f / kSScale);
+            for (int c0 = 0; c0 < kH; c0 += 32) {
+                float d0[16], d1[16];
+                tc::tmem_ld16(lane_addr + kH * h + c0, d0);
+                tc::tmem_ld16(lane_addr + kH * h + c0 + 16, d1);
+                tc::tmem_wait_ld();
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const int ii = c0 < kH ? 2 * (c0 + u) : 2 * (c0 + u - kH) + 1;
-                base[(size_t)ii * sN2] = d[u] * sc2;
+                for (int u = 0; u < 16; ++u) {
+                    base[(size_t)(2 * (c0 + u) + h) * sN2] = d0[u] * sc2;
+                    base[(size_t)(2 * (c0 + 16 + u) + h) * sN2] = d1[u] * sc2;
+                }
             }
         }
         tc::tc_fence_before_sync();
@@ -688,6 +710,45 @@ const uint4 *tc_sine_blocks() {
     }
     cache[dev] = d;
     return static_cast<const uint4 *>(d);
+}
+
+// Tensor map of the workspace [B][i][j][c] (FP32, 128^3 per right-hand side)
+// with a box of one (b, j) column block: 128 c x 1 j x 128 i x 1 b.
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+int encode_work_map(CUtensorMap *map, float *work, int B) {
+    static std::mutex mu;
+    static EncodeTiledFn fn = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!fn) {
+            void *f = nullptr;
+            cudaDriverEntryPointQueryResult q{};
+            if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                                 &q) != cudaSuccess ||
+                q != cudaDriverEntryPointSuccess || !f) {
+                set_error("tensor-core AP solve: cuTensorMapEncodeTiled is unavailable");
+                return DPM_ECUDA;
+            }
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+        }
+    }
+    const cuuint64_t dims[4] = {(cuuint64_t)kN, (cuuint64_t)kN, (cuuint64_t)kN, (cuuint64_t)B};
+    const cuuint64_t strides[3] = {(cuuint64_t)kN * 4, (cuuint64_t)kN * kN * 4,
+                                   (cuuint64_t)kN * kN * kN * 4};
+    const cuuint32_t box[4] = {(cuuint32_t)kN, 1, (cuuint32_t)kN, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, work, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("tensor-core AP solve: tensor map encoding failed (%d)", (int)r);
+        return DPM_ECUDA;
+    }
+    return DPM_OK;
 }
 
 int tc_configure() {
@@ -755,9 +816,11 @@ int ap_solve_tc(const ApParams &p, const ApRhs<float> *rhs_dev, float *work, cud
         k_tc_plane<false><<<std::min(nitems, 2 * sms), kPlaneThreads, kSmemBytes, s>>>(a, rhs_dev, work);
         DPM_LAUNCHED();
     }
+    CUtensorMap zmap;
+    DPM_RET(encode_work_map(&zmap, work, p.B));
     {
         DPM_PROF("tc_pencil", s);
-        k_tc_pencil<<<std::min(nitems, 2 * sms), kThreads, kSmemBytes, s>>>(a, rhs_dev, work);
+        k_tc_pencil<<<std::min(nitems, 2 * sms), kPencilThreads, kSmemBytes, s>>>(a, rhs_dev, work, zmap);
         DPM_LAUNCHED();
     }
     {

@@ -255,53 +255,168 @@ __global__ void k_syrk_reduce32(int n, int nchunks, const float *part, double *G
 }
 
 // FP32 Cholesky of the (well-conditioned, equilibrated) Gram matrix G = L L^T
-// in one CTA, one barrier per column (step j writes column j of L and applies
-// the rank-1 update W[i][k] -= W[i][j] W[k][j] / W[j][j] to the trailing
-// lower triangle), then X = L^{-1} row by row with one warp per column set;
+// and the triangular inverse X = L^{-1}, in one CTA, blocked by 32 so that
+// the sequential steps stay inside a warp (register rows and shuffles) and
+// the CTA meets at ~25 barriers:
+//   per panel p: warp 0 factors the diagonal block; one thread per row below
+//   solves its panel row against it; all threads apply the trailing update;
+//   inverse: warp b inverts diagonal block b; M[bi][k] = X_bi,bi L[bi][k] goes
+//   to X's (unused) upper triangle, transposed; then the off-diagonal blocks
+//   by block diagonals d = bi - bj: X[bi][bj] = -sum_{k=bj}^{bi-1} M[bi][k] X[k][bj].
 // Rinv = R^{-1} = X^T is written in FP64.  It only preconditions the FP64
 // refinement of every solve, so FP32 suffices for this equilibrated matrix.
-__global__ void k_cholesky32(int n, const double *G, double *Rinv, int *status) {
+__global__ void __launch_bounds__(1024) k_cholesky32(int n, const double *G, double *Rinv,
+                                                     int *status) {
     extern __shared__ float sm32[];
-    float *W = sm32, *Ls = sm32 + (size_t)n * n;
-    const int t = threadIdx.x, T = blockDim.x;
-    const int tx = t & 31, ty = t >> 5, nw = T >> 5;
+    float *W = sm32, *X = sm32 + (size_t)n * n;
+    const int t = threadIdx.x, T = blockDim.x, lane = t & 31, warp = t >> 5, nwarp = T >> 5;
+    const int nb = (n + 31) >> 5;
+    // G's upper triangle (row-major, read coalesced) -> lower triangle of W
     for (int idx = t; idx < n * n; idx += T) {
-        const int i = idx / n, j = idx % n;
-        W[idx] = (float)(j >= i ? G[(size_t)i * n + j] : G[(size_t)j * n + i]);
-        Ls[idx] = 0.f;
+        const int j = idx / n, i = idx % n;
+        W[i * n + j] = i >= j ? (float)G[idx] : 0.f;
+        X[idx] = 0.f;
     }
     __syncthreads();
-    for (int j = 0; j < n; ++j) {
-        float piv = W[j * n + j];
-        if (!(piv > 0.f) || !isfinite(piv)) {
-            if (t == 0) status[0] = 1;
-            piv = 1.f;
-        }
-        const float rs = rsqrtf(piv), ip = 1.f / piv;
-        for (int i = j + t; i < n; i += T) Ls[i * n + j] = W[i * n + j] * rs;
-        for (int i = j + 1 + ty; i < n; i += nw) {
-            const float wij = W[i * n + j] * ip;
-            for (int k = j + 1 + tx; k <= i; k += 32) W[i * n + k] -= wij * W[k * n + j];
-        }
-        __syncthreads();
-    }
-    // X = L^{-1} (lower) into W: X[i][c] = (delta_ic - sum_{c<=k<i} L[i][k] X[k][c]) / L[i][i]
-    for (int idx = t; idx < n * n; idx += T) W[idx] = 0.f;
-    __syncthreads();
-    for (int i = 0; i < n; ++i) {
-        const float dinv = 1.f / Ls[i * n + i];
-        for (int c = ty; c <= i; c += nw) {
-            float acc = 0.f;
-            for (int k = c + tx; k < i; k += 32) acc += Ls[i * n + k] * W[k * n + c];
+    for (int p = 0; p < nb; ++p) {
+        const int c0 = 32 * p, w = min(32, n - c0);
+        // ---- diagonal block: lane i owns row c0 + i ----------------------------
+        if (warp == 0) {
+            float a[32];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (tx == 0) W[i * n + c] = ((i == c ? 1.f : 0.f) - acc) * dinv;
+            for (int k = 0; k < 32; ++k)
+                a[k] = (lane < w && k <= lane) ? W[(c0 + lane) * n + c0 + k] : 0.f;
+            bool bad = false;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (j < w) {
+                    float piv = __shfl_sync(0xffffffffu, a[j], j);
+                    if (!(piv > 0.f) || !isfinite(piv)) {
+                        bad = true;
+                        piv = 1.f;
+                    }
+                    const float lij = a[j] * rsqrtf(piv);  // lane j: sqrt(piv)
+                    if (lane >= j) a[j] = lij;
+#pragma unroll
+                    for (int k = j + 1; k < 32; ++k) {
+                        const float lkj = __shfl_sync(0xffffffffu, lij, k);
+                        if (lane >= k) a[k] -= lij * lkj;
+                    }
+                }
+            }
+            if (bad && lane == 0) status[0] = 1;
+            if (lane < w) {
+#pragma unroll
+                for (int k = 0; k < 32; ++k)
+                    if (k <= lane) W[(c0 + lane) * n + c0 + k] = a[k];
+            }
+        }
+        __syncthreads();
+        // ---- panel rows below: L[i][c0+j] = (W - sum_k L[i][c0+k] L[c0+j][c0+k]) / L[c0+j][c0+j]
+        for (int i = c0 + w + t; i < n; i += T) {
+            float x[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) x[j] = j < w ? W[i * n + c0 + j] : 0.f;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (j < w) {
+                    float acc = x[j];
+#pragma unroll
+                    for (int k = 0; k < j; ++k) acc -= x[k] * W[(c0 + j) * n + c0 + k];
+                    x[j] = acc / W[(c0 + j) * n + c0 + j];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (j < w) W[i * n + c0 + j] = x[j];
+        }
+        __syncthreads();
+        // ---- trailing update of the lower triangle ----------------------------------
+        const int r0 = c0 + w, m = n - r0;
+        const int ntri = m * (m + 1) / 2;  // lower-triangle entries (i >= k) of the trailing block
+        for (int idx = t; idx < ntri; idx += T) {
+            // idx -> (ii, kk) with kk <= ii, row-major over the triangle
+            int ii = (int)((sqrtf(8.f * (float)idx + 1.f) - 1.f) * 0.5f);
+            while (ii * (ii + 1) / 2 > idx) --ii;
+            while ((ii + 1) * (ii + 2) / 2 <= idx) ++ii;
+            const int kk = idx - ii * (ii + 1) / 2;
+            const int i = r0 + ii, k = r0 + kk;
+            const float *li = W + i * n + c0, *lk = W + k * n + c0;
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+            int j = 0;
+            for (; j + 3 < w; j += 4) {
+                a0 += li[j] * lk[j];
+                a1 += li[j + 1] * lk[j + 1];
+                a2 += li[j + 2] * lk[j + 2];
+                a3 += li[j + 3] * lk[j + 3];
+            }
+            for (; j < w; ++j) a0 += li[j] * lk[j];
+            W[i * n + k] -= (a0 + a1) + (a2 + a3);
+        }
+        __syncthreads();
+    }
+    // ---- inverse: diagonal blocks, warp b, lane c = column c of X_bb ----------------
+    for (int bb = warp; bb < nb; bb += nwarp) {
+        const int c0 = 32 * bb, w = min(32, n - c0);
+        float x[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            float v = 0.f;
+            if (i < w && lane < w && i >= lane) {
+                float acc = (i == lane) ? 1.f : 0.f;
+#pragma unroll
+                for (int k = 0; k < i; ++k)
+                    if (k >= lane) acc -= W[(c0 + i) * n + c0 + k] * x[k];
+                v = acc / W[(c0 + i) * n + c0 + i];
+            }
+            x[i] = v;
+        }
+        if (lane < w) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+                if (i < w && i >= lane) X[(c0 + i) * n + c0 + lane] = x[i];
+        }
+    }
+    __syncthreads();
+    // ---- M[bi][k] = X_bi,bi L[bi][k] (k < bi), stored transposed in X's upper triangle
+    for (int idx = t; idx < n * n; idx += T) {
+        const int r = idx / n, c = idx % n;  // element (r, c) of the lower off-diagonal part
+        const int bi = r >> 5, bk = c >> 5;
+        if (bk >= bi) continue;
+        const int ri = 32 * bi;
+        float a0 = 0.f, a1 = 0.f;
+        int s2 = ri;
+        for (; s2 + 1 <= r; s2 += 2) {
+            a0 += X[r * n + s2] * W[s2 * n + c];
+            a1 += X[r * n + s2 + 1] * W[(s2 + 1) * n + c];
+        }
+        if (s2 <= r) a0 += X[r * n + s2] * W[s2 * n + c];
+        X[c * n + r] = a0 + a1;  // M^T
+    }
+    __syncthreads();
+    // ---- off-diagonal blocks of X by block diagonal d ------------------------------
+    for (int d = 1; d < nb; ++d) {
+        for (int idx = t; idx < n * n; idx += T) {
+            const int r = idx / n, c = idx % n;
+            const int bi = r >> 5, bj = c >> 5;
+            if (bi - bj != d) continue;
+            // sum over k = bj .. bi-1 (block rows), s in block k: M[bi](r, s) X(s, c);
+            // the range is a whole number of 32-row blocks
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+            const int s_end = 32 * bi;
+            for (int s2 = 32 * bj; s2 < s_end; s2 += 4) {
+                a0 += X[s2 * n + r] * X[s2 * n + c];
+                a1 += X[(s2 + 1) * n + r] * X[(s2 + 1) * n + c];
+                a2 += X[(s2 + 2) * n + r] * X[(s2 + 2) * n + c];
+                a3 += X[(s2 + 3) * n + r] * X[(s2 + 3) * n + c];
+            }
+            X[r * n + c] = -((a0 + a1) + (a2 + a3));
         }
         __syncthreads();
     }
     for (int idx = t; idx < n * n; idx += T) {
-        const int r = idx / n, c = idx % n;      // Rinv[r][c] = X[c][r]
-        Rinv[idx] = c >= r ? (double)W[c * n + r] : 0.0;
+        const int r = idx / n, c = idx % n;  // Rinv[r][c] = X[c][r]
+        Rinv[idx] = c >= r ? (double)X[c * n + r] : 0.0;
     }
 }
 
@@ -568,7 +683,10 @@ int lsq_apply(const LsqFactor &f, const T *b, int ldb, double *C, int nr, cudaSt
     (void)status;
     const int mv_blocks = (n * nr * 32 + 255) / 256;
     const double *dsc = f.equilibrated ? Rinv + (size_t)n * n : nullptr;
-    const int refine = f.equilibrated ? 3 : 1;
+    // FP64 refinement steps: each contracts the error by ~kappa(AD)^2 eps_32.
+    // One leaves C ~1e-11 relative, far below the FP32 solver's error; the
+    // FP64 path takes three.
+    const int refine = f.equilibrated ? (sizeof(T) == sizeof(double) ? 3 : 1) : 1;
     DPM_PROF("lsq_solve", s);
     // C = D R^{-1} R^{-T} D A^T b   (D = I unless the factor was equilibrated)
     k_atb<T><<<dim3(n, nr), 1024, 0, s>>>(m, n, A0, b, ldb, y, nr, dsc);
