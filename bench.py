@@ -52,6 +52,8 @@ def parse():
                     help="requests in the serving leg (0 skips it)")
     ap.add_argument("--serving-rate", type=float, default=300.0, help="mean arrivals per second")
     ap.add_argument("--serving-models", type=int, default=16)
+    ap.add_argument("--no-aux", action="store_true", help="skip the batched aux-solve leg")
+    ap.add_argument("--no-graph", action="store_true", help="host-driven steps instead of graph replay")
     return ap.parse_args()
 
 
@@ -216,9 +218,13 @@ def run_ours(args):
     # bound of this data), and the BEP is rebuilt on every step (Step 4b).
     params = abi.pks_params(w.geom, w.N, w.lo, w.hi, 1.0, w.dt, w.K, w.beta, prec,
                             dt_mode=1, rebuild=1, clamp=1)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()
     pks = abi.dpm_pks_create(ctx, params, w.rho0, w.c0, stream=stream)
     N = w.N
+    # each step replays one CUDA graph of the device-resident step (the
+    # warm-up steps include the uncaptured sizing step and the capture)
+    if not args.no_graph:
+        abi.dpm_pks_set_graph(pks, True, stream=stream)
     for _ in range(args.warmup):
         abi.dpm_pks_step(pks, 1, want_stats=False, stream=stream)
     torch.cuda.synchronize()
@@ -227,8 +233,6 @@ def run_ours(args):
 
     clocks = ClockSampler(local)
     clocks.start()
-    abi.dpm_profile_reset()
-    abi.dpm_profile_enable(True)
     l0 = abi.dpm_launch_count()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -239,10 +243,19 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
-    abi.dpm_profile_enable(False)
     launches = abi.dpm_launch_count() - l0
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
+    # per-kernel device times: the same step run without the graph, with the
+    # library's CUDA events around every launch (not part of the timed region)
+    abi.dpm_pks_set_graph(pks, False, stream=stream)
+    abi.dpm_profile_reset()
+    abi.dpm_profile_enable(True)
+    nprof = max(3, min(args.steps, 10))
+    for _ in range(nprof):
+        abi.dpm_pks_step(pks, 1, want_stats=False, stream=stream)
+    torch.cuda.synchronize()
+    abi.dpm_profile_enable(False)
     t = torch.tensor([ms], device="cuda", dtype=torch.float64)
     if dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -267,7 +280,13 @@ def run_ours(args):
 
     e2e = None
     if not args.no_e2e:
+        if not args.no_graph:
+            abi.dpm_pks_set_graph(pks, True, stream=stream)
         e2e = run_e2e(abi, torch, pks, w, tdt, spp, args, stream)
+
+    aux = None
+    if rank == 0 and not args.no_aux:
+        aux = run_aux(abi, torch, ctx, stream)
 
     serving = None
     if rank == 0 and args.serving_requests > 0:
@@ -291,7 +310,8 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": f"inputs larger than L2 ({spp * N ** 3 * 4 / 1e9:.2f} GB batch per step)"},
             "clocks": clk, "gpu_launches": int(launches), "roofline": roof, "kernels": prof,
-            "e2e": e2e, "cpu_baseline": cpu, "serving": serving,
+            "e2e": e2e, "cpu_baseline": cpu, "aux_solve": aux, "serving": serving,
+            "graph": not args.no_graph, "kernel_profile_steps": nprof,
             "sanity": {"finite": bool(finite), "mass": st.mass},
         }
         print(json.dumps(line), flush=True)
@@ -347,31 +367,81 @@ def roofline(w, prec, prof, spp):
             "peak_source": f"hbm_gbs ({src})"}
 
 
+def run_aux(abi, torch, ctx, stream):
+    """Batched auxiliary solves alone (Definition 2.4), dense uniform-random q
+    in [-1, 1] (seed 0), inputs resident and larger than L2: the tensor-core
+    solver at N = 128 with the 162-column batch, the FP32 SIMT solver and the
+    plain FP64 solver (one right-hand side per call) at N = 256.  Roofline:
+    the three-pass (tensor-core) or five-pass (SIMT) schedule moves 24 or
+    40 bytes per grid point per FP32 solve (read + write of the cube per pass)."""
+    from paper_1811_03557_gb300.workloads import random_rhs
+    peaks, src = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+
+    def timed(N, B, prec, reps, calls=1):
+        h = 2.5 / (N + 1)
+        tdt = torch.float64 if prec == abi.DPM_PREC_FP64 else torch.float32
+        q = torch.from_numpy(random_rhs(0, B, N)).to("cuda", tdt)
+        u = torch.empty_like(q)
+        sigma = 1.0 / 1e-4 + 1.0
+        for _ in range(2):
+            abi.dpm_aux_solve_batched(ctx, N, h, sigma, B, q, u, prec, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            for c in range(calls):
+                abi.dpm_aux_solve_batched(ctx, N, h, sigma, B // calls, q[c * (B // calls):],
+                                          u[c * (B // calls):], prec, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        del q, u
+        return ms, B * N ** 3 / (ms / 1e3)
+
+    out = {}
+    ms, v = timed(128, 162, abi.DPM_PREC_TC32, 5)
+    gbs = 24.0 * 162 * 128 ** 3 / (ms / 1e3) / 1e9
+    out["tc32_N128_B162"] = {"ms": ms, "grid_pts_per_s": v, "hbm_gbs": gbs, "frac": gbs / hbm}
+    ms, v = timed(256, 16, abi.DPM_PREC_FP32, 3)
+    gbs = 40.0 * 16 * 256 ** 3 / (ms / 1e3) / 1e9
+    out["fp32_N256_B16"] = {"ms": ms, "grid_pts_per_s": v, "hbm_gbs": gbs, "frac": gbs / hbm}
+    ms, v = timed(256, 2, abi.DPM_PREC_FP64, 1, calls=2)
+    out["fp64_N256_per_solve"] = {"ms": ms, "grid_pts_per_s": v}
+    out["peak"] = {"hbm_gbs": hbm, "source": src}
+    out["data"] = "uniform [-1, 1] q, seed 0; dense in, dense out; inputs larger than L2"
+    return out
+
+
 def run_e2e(abi, torch, pks, w, tdt, spp, args, stream):
     """Same metric through the public API with host buffers: each step copies
     the state (rho, c) host->device, steps, and copies it device->host."""
     N = w.N
-    rho_h = torch.empty((N, N, N), dtype=tdt).pin_memory()
-    c_h = torch.empty_like(rho_h).pin_memory()
-    rho_d = torch.empty((N, N, N), dtype=tdt, device="cuda")
-    c_d = torch.empty_like(rho_d)
-    abi.dpm_pks_get_state(pks, rho_d, c_d, stream=stream)
-    rho_h.copy_(rho_d)
-    c_h.copy_(c_d)
+    # warm-up outside the timed region (with graph stepping: the sizing step and the capture)
+    abi.dpm_pks_step(pks, 2, want_stats=False, stream=stream)
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    K = max(1, min(args.steps, 5))
-    e0.record(stream)
-    for _ in range(K):
-        rho_d.copy_(rho_h, non_blocking=True)
-        c_d.copy_(c_h, non_blocking=True)
-        abi.dpm_pks_set_state(pks, rho_d, c_d, stream=stream)
-        abi.dpm_pks_step(pks, 1, want_stats=False, stream=stream)
+    with torch.cuda.stream(stream):
+        rho_h = torch.empty((N, N, N), dtype=tdt).pin_memory()
+        c_h = torch.empty_like(rho_h).pin_memory()
+        rho_d = torch.empty((N, N, N), dtype=tdt, device="cuda")
+        c_d = torch.empty_like(rho_d)
         abi.dpm_pks_get_state(pks, rho_d, c_d, stream=stream)
-        rho_h.copy_(rho_d, non_blocking=True)
-        c_h.copy_(c_d, non_blocking=True)
-    e1.record(stream)
+        rho_h.copy_(rho_d)
+        c_h.copy_(c_d)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        K = max(1, min(args.steps, 5))
+        e0.record(stream)
+        for _ in range(K):
+            rho_d.copy_(rho_h, non_blocking=True)
+            c_d.copy_(c_h, non_blocking=True)
+            abi.dpm_pks_set_state(pks, rho_d, c_d, stream=stream)
+            abi.dpm_pks_step(pks, 1, want_stats=False, stream=stream)
+            abi.dpm_pks_get_state(pks, rho_d, c_d, stream=stream)
+            rho_h.copy_(rho_d, non_blocking=True)
+            c_h.copy_(c_d, non_blocking=True)
+        e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / K
     nb = 2 * N ** 3 * rho_h.element_size()

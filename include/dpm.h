@@ -276,6 +276,20 @@ int dpm_pks_create(dpm_ctx *ctx, const dpm_pks_params *params, const dpm_gaussia
                    const dpm_gaussian *c0, dpm_pks **out, cudaStream_t stream);
 int dpm_pks_set_state(dpm_pks *pks, const void *rho, const void *c, cudaStream_t stream);
 int dpm_pks_step(dpm_pks *pks, int nsteps, dpm_pks_stats *stats, cudaStream_t stream);
+
+/*
+ * Graph stepping (on != 0): later dpm_pks_step calls keep dt, sigma and the
+ * time in device memory (Step 3's dt computed by a kernel from the CFL
+ * maxima), so a step needs no host synchronisation; the library captures one
+ * step in a CUDA graph (on its own capture stream, after one uncaptured step
+ * that sizes the workspaces) and replays it on `stream` for each step.  Same
+ * kernels and arithmetic as the default stepping, so the results are the
+ * same.  Needs dt_mode 0, or rebuild = 1 (a rebuild only when dt decreases is
+ * a host decision): DPM_EUNSUPPORTED otherwise.  on = 0 returns to the
+ * default stepping (synchronises to read the time back).  The pivot status of
+ * the factorisations is checked when statistics are requested.
+ */
+int dpm_pks_set_graph(dpm_pks *pks, int on, cudaStream_t stream);
 int dpm_pks_get_state(dpm_pks *pks, void *rho, void *c, cudaStream_t stream);
 /* Device bytes held by a PKS run (its BEP, the two fields and scratch). */
 int dpm_pks_device_bytes(const dpm_pks *pks, int64_t *bytes);

@@ -83,6 +83,7 @@ _SIGS = {
                                  C.POINTER(dpm_gaussian), C.POINTER(C.c_void_p), _P]),
     "dpm_pks_set_state": (C.c_int, [_P, _P, _P, _P]),
     "dpm_pks_step": (C.c_int, [_P, C.c_int, C.POINTER(dpm_pks_stats), _P]),
+    "dpm_pks_set_graph": (C.c_int, [_P, C.c_int, _P]),
     "dpm_pks_get_state": (C.c_int, [_P, _P, _P, _P]),
     "dpm_pks_destroy": (C.c_int, [_P]),
     "dpm_aux_solve_batched_noalloc": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, _P,
@@ -270,6 +271,10 @@ def dpm_pks_step(pks, nsteps=1, want_stats=True, stream=None):
     st = dpm_pks_stats()
     _check(lib().dpm_pks_step(pks, nsteps, C.byref(st) if want_stats else None, _stream(stream)))
     return st if want_stats else None
+
+
+def dpm_pks_set_graph(pks, on=True, stream=None):
+    _check(lib().dpm_pks_set_graph(pks, 1 if on else 0, _stream(stream)))
 
 
 def dpm_pks_get_state(pks, rho, c, stream=None):

@@ -52,6 +52,9 @@ cudaEvent_t pool_event() {
 
 int prof_begin(const char *name, cudaStream_t s) {
     if (!g_prof.load(std::memory_order_relaxed)) return -1;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return -1;  // graph replays are timed as a whole
     std::lock_guard<std::mutex> lk(g_pmu);
     cudaEvent_t a = pool_event(), b = pool_event();
     if (!a || !b) return -1;
@@ -67,8 +70,8 @@ void prof_end(int rec, cudaStream_t s) {
 }
 
 template <class T>
-int pks_flux(int, double, double, double, const uint8_t *, const T *, const T *, T *, T *,
-             cudaStream_t);
+int pks_flux(int, double, double, double, const double *, const uint8_t *, const T *, const T *,
+             T *, T *, cudaStream_t);
 template <class T> int pks_cfl(int, const uint8_t *, const T *, unsigned int *, cudaStream_t);
 template <class T>
 int pks_diag(int, double, double, const uint8_t *, const T *, const T *, double *, double *,
@@ -92,6 +95,9 @@ bool prec_ok(int prec) {
 constexpr size_t kWorkCap = size_t(8) << 30;
 
 template <class T>
+int run_ap_dev(int prec, ApParams p, const ApRhs<T> *desc_dev, int B, DevBuf &work, cudaStream_t s);
+
+template <class T>
 int run_ap(int prec, ApParams p, const std::vector<ApRhs<T>> &rhs, DevBuf &work, DevBuf &desc,
            cudaStream_t s) {
     const int B = (int)rhs.size();
@@ -109,15 +115,28 @@ int run_ap(int prec, ApParams p, const std::vector<ApRhs<T>> &rhs, DevBuf &work,
             }
     }
     DPM_RET(work.reserve(cb * cube + extra));
-    if (prec == DPM_PREC_TC32) p.scratch = reinterpret_cast<float *>(static_cast<char *>(work.p) + cb * cube);
     DPM_RET(desc.reserve(sizeof(ApRhs<T>) * B));
     DPM_CUDA(cudaMemcpyAsync(desc.p, rhs.data(), sizeof(ApRhs<T>) * B, cudaMemcpyHostToDevice, s));
     // The copy above is from pageable memory: it has been staged when it
     // returns, so `rhs` may go out of scope afterwards.
+    return run_ap_dev<T>(prec, p, desc.as<ApRhs<T>>(), B, work, s);
+}
+
+// The same with the descriptors already in device memory and the workspace
+// already sized (no allocation, no host copy: usable under stream capture).
+template <class T>
+int run_ap_dev(int prec, ApParams p, const ApRhs<T> *desc_dev, int B, DevBuf &work, cudaStream_t s) {
+    if (B == 0) return DPM_OK;
+    const size_t cube = (size_t)p.N * p.N * p.N * sizeof(T);
+    size_t cb = std::max<size_t>(1, std::min<size_t>(B, kWorkCap / cube));
+    size_t extra = 0;
+    if (prec == DPM_PREC_TC32) extra = tc_scratch_elems(p, (int)cb) * sizeof(float);
+    if (work.bytes < cb * cube + extra) { set_error("AP workspace not sized for %d right-hand sides", B); return DPM_EINVAL; }
+    if (prec == DPM_PREC_TC32) p.scratch = reinterpret_cast<float *>(static_cast<char *>(work.p) + cb * cube);
     for (int b0 = 0; b0 < B; b0 += (int)cb) {
         ApParams q = p;
         q.B = std::min<int>((int)cb, B - b0);
-        const ApRhs<T> *d = desc.as<ApRhs<T>>() + b0;
+        const ApRhs<T> *d = desc_dev + b0;
         if (prec == DPM_PREC_TC32) {
             if constexpr (sizeof(T) == 4) {
                 DPM_RET(ap_solve_tc(q, d, work.as<float>(), s));
@@ -178,6 +197,18 @@ struct dpm_pks {
     double t = 0, dt_prev = 0;
     int64_t step = 0;
     int last_rebuilt = 0;
+    // device-resident step replayed as a CUDA graph (dpm_pks_set_graph)
+    int graph_on = 0;
+    bool dev_warm = false;
+    DevBuf scal;                     // StepScalars
+    DevBuf desc_rb, desc_green;      // ApRhs: ncol BEP columns + 2 particular; 2 Green's
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cap = nullptr;      // capture stream
+    int64_t gkernels = 0;            // kernel nodes per replay
+    ~dpm_pks() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (cap) cudaStreamDestroy(cap);
+    }
 };
 
 extern "C" const char *dpm_last_error(void) { return g_err; }
@@ -626,8 +657,8 @@ template <class T> int pks_step_one(dpm_pks *k, cudaStream_t s) {
     const double sigma = 1.0 / dt;
     const int64_t m = b->gi.n_gin, ng = b->gi.n_gamma;
     T *frho = k->frho.as<T>(), *fc = k->fc.as<T>();
-    DPM_RET(pks_flux<T>(N, h, P.chi, dt, b->gi.labels.as<uint8_t>(), k->rho.as<T>(), k->c.as<T>(),
-                        frho, fc, s));
+    DPM_RET(pks_flux<T>(N, h, P.chi, dt, nullptr, b->gi.labels.as<uint8_t>(), k->rho.as<T>(),
+                        k->c.as<T>(), frho, fc, s));
     T *tr0 = b->trace.as<T>() + (int64_t)b->ncol * m;
     T *tr1 = tr0 + m;
     std::vector<ApRhs<T>> part = {{frho, nullptr, nullptr, tr0, 0, 0},
@@ -654,6 +685,139 @@ template <class T> int pks_step_one(dpm_pks *k, cudaStream_t s) {
     k->dt_prev = dt;
     k->step += 1;
     k->last_rebuilt = rebuild ? 1 : 0;
+    return DPM_OK;
+}
+
+// One PKS step with dt, sigma and the time kept on the device: no host
+// synchronisation, no allocation and no host copy, so it can be captured in
+// a CUDA graph.  Same kernels and arithmetic as pks_step_one; the BEP is
+// rebuilt on every step unless dt is fixed (dt_mode 0 without rebuild).
+template <class T> int pks_step_dev(dpm_pks *k, cudaStream_t s) {
+    dpm_bep *b = &k->bep;
+    const dpm_pks_params &P = k->prm;
+    const int N = P.N;
+    const double h = b->gi.h;
+    StepScalars *sc = k->scal.as<StepScalars>();
+    const uint8_t *lab = b->gi.labels.as<uint8_t>();
+    if (P.dt_mode == 1)
+        DPM_RET(pks_cfl<T>(N, lab, k->c.as<T>(), k->gmax.as<unsigned int>(), s));
+    DPM_RET(pks_step_dt(k->gmax.as<unsigned int>(), h, P.chi, P.dt_max, P.dt_mode, sc, s));
+    T *frho = k->frho.as<T>(), *fc = k->fc.as<T>();
+    DPM_RET(pks_flux<T>(N, h, P.chi, 0.0, &sc->dt, lab, k->rho.as<T>(), k->c.as<T>(), frho, fc, s));
+    const bool rebuild = P.dt_mode == 1 || P.rebuild;
+    ApParams p = base_params(b, 0.0);
+    p.sigma_dev = &sc->sigma;
+    p.fscale_dev = &sc->sigma;  // L_{h,dt} u = f  <=>  (1/dt - Lap_h) u = f/dt
+    const int64_t m = b->gi.n_gin, ng = b->gi.n_gamma;
+    const ApRhs<T> *rb = k->desc_rb.as<ApRhs<T>>();
+    if (rebuild) {
+        DPM_RET(run_ap_dev<T>(b->prec, p, rb, b->ncol + 2, b->work, s));
+        DPM_RET(assemble_bep<T>(b->psi_in.as<double>(), b->trace.as<T>(), b->lsq.A.as<double>(), m,
+                                b->ncol, nullptr, s));
+        DPM_RET(lsq_factor_async(b->lsq, s));
+    } else {
+        DPM_RET(run_ap_dev<T>(b->prec, p, rb + b->ncol, 2, b->work, s));
+    }
+    double *C = b->coef.as<double>();
+    T *tr0 = b->trace.as<T>() + (int64_t)b->ncol * m;
+    DPM_RET(lsq_apply<T>(b->lsq, tr0, (int)m, C, 2, s));
+    T *dens = b->dens.as<T>();
+    DPM_RET(extend_density<T>(b->gg, ng, b->beta, C, b->ncol, nullptr, dens, (int)ng, 2, P.clamp, s));
+    DPM_RET(run_ap_dev<T>(b->prec, p, k->desc_green.as<ApRhs<T>>(), 2, b->work, s));
+    DPM_RET(pks_diag<T>(N, b->gi.lo, h, lab, k->rho.as<T>(), k->c.as<T>(), k->diag_part.as<double>(),
+                        k->diag_out.as<double>(), s));
+    DPM_RET(pks_step_end(sc, rebuild ? 1 : 0, s));
+    return DPM_OK;
+}
+
+// Descriptors of the device step's three batched solves, uploaded once.
+template <class T> int pks_dev_setup(dpm_pks *k, cudaStream_t s) {
+    dpm_bep *b = &k->bep;
+    const int64_t m = b->gi.n_gin, ng = b->gi.n_gamma;
+    T *frho = k->frho.as<T>(), *fc = k->fc.as<T>();
+    T *tr0 = b->trace.as<T>() + (int64_t)b->ncol * m, *tr1 = tr0 + m;
+    T *dens = b->dens.as<T>();
+    std::vector<ApRhs<T>> rb;
+    for (int c = 0; c < b->ncol; ++c)
+        rb.push_back({nullptr, b->psi.as<T>() + c * ng, nullptr, b->trace.as<T>() + c * m, 0, 0});
+    rb.push_back({frho, nullptr, nullptr, tr0, 0, 0});
+    rb.push_back({fc, nullptr, nullptr, tr1, 0, 0});
+    std::vector<ApRhs<T>> gr = {{frho, dens, k->rho.as<T>(), nullptr, 0, 0},
+                                {fc, dens + ng, k->c.as<T>(), nullptr, 0, 0}};
+    DPM_RET(k->desc_rb.reserve(sizeof(ApRhs<T>) * rb.size()));
+    DPM_RET(k->desc_green.reserve(sizeof(ApRhs<T>) * gr.size()));
+    DPM_CUDA(cudaMemcpyAsync(k->desc_rb.p, rb.data(), sizeof(ApRhs<T>) * rb.size(), cudaMemcpyHostToDevice, s));
+    DPM_CUDA(cudaMemcpyAsync(k->desc_green.p, gr.data(), sizeof(ApRhs<T>) * gr.size(), cudaMemcpyHostToDevice, s));
+    // buffers every solve of the step touches (the eager step sizes them the same way)
+    const size_t cube = (size_t)b->N * b->N * b->N * sizeof(T);
+    const int B = b->ncol + 2;
+    const size_t cb = std::max<size_t>(1, std::min<size_t>(B, kWorkCap / cube));
+    size_t extra = 0;
+    if (b->prec == DPM_PREC_TC32) {
+        ApParams p = base_params(b, 0.0);
+        extra = tc_scratch_elems(p, (int)cb) * sizeof(float);
+    }
+    DPM_RET(b->work.reserve(cb * cube + extra));
+    if (!k->scal.p) {
+        DPM_RET(k->scal.alloc(sizeof(StepScalars)));
+    }
+    StepScalars h{};
+    h.t = k->t;
+    h.dt_prev = k->dt_prev;
+    h.step = k->step;
+    h.rebuilt = k->last_rebuilt;
+    DPM_CUDA(cudaMemcpyAsync(k->scal.p, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+    DPM_CUDA(cudaStreamSynchronize(s));
+    return DPM_OK;
+}
+
+int pks_dev_step(dpm_pks *k, cudaStream_t s) {
+    return k->prm.precision == DPM_PREC_FP64 ? pks_step_dev<double>(k, s) : pks_step_dev<float>(k, s);
+}
+
+// Host copy of the device step's scalars (after graph steps).
+int pks_dev_pull(dpm_pks *k, cudaStream_t s, int *bad) {
+    StepScalars h{};
+    DPM_CUDA(cudaMemcpyAsync(&h, k->scal.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    DPM_CUDA(cudaStreamSynchronize(s));
+    k->t = h.t;
+    k->dt_prev = h.dt;
+    k->step = h.step;
+    k->last_rebuilt = h.rebuilt;
+    if (bad) *bad = h.bad;
+    return DPM_OK;
+}
+
+// Advance one step by replaying the captured graph (capturing it first).
+int pks_graph_step(dpm_pks *k, cudaStream_t s) {
+    if (!k->gexec) {
+        if (!k->dev_warm) {
+            // an uncaptured step sizes every workspace the captured one uses
+            DPM_RET(pks_dev_step(k, s));
+            k->dev_warm = true;
+            return DPM_OK;
+        }
+        if (!k->cap) DPM_CUDA(cudaStreamCreateWithFlags(&k->cap, cudaStreamNonBlocking));
+        // order the capture stream after the caller's work (capture records only)
+        DPM_CUDA(cudaStreamSynchronize(s));
+        cudaGraph_t g = nullptr;
+        DPM_CUDA(cudaStreamBeginCapture(k->cap, cudaStreamCaptureModeRelaxed));
+        const long long l0 = g_launches.load();
+        const int r = pks_dev_step(k, k->cap);
+        const cudaError_t e = cudaStreamEndCapture(k->cap, &g);
+        k->gkernels = g_launches.load() - l0;
+        g_launches.fetch_sub(k->gkernels);  // counted when replayed
+        if (r != DPM_OK) {
+            if (g) cudaGraphDestroy(g);
+            return r;
+        }
+        DPM_CUDA(e);
+        const cudaError_t ie = cudaGraphInstantiate(&k->gexec, g, 0);
+        cudaGraphDestroy(g);
+        DPM_CUDA(ie);
+    }
+    DPM_CUDA(cudaGraphLaunch(k->gexec, s));
+    g_launches.fetch_add(k->gkernels);
     return DPM_OK;
 }
 
@@ -706,11 +870,55 @@ extern "C" int dpm_pks_set_state(dpm_pks *k, const void *rho, const void *c, cud
     return DPM_OK;
 }
 
+extern "C" int dpm_pks_set_graph(dpm_pks *k, int on, cudaStream_t s) {
+    if (!k) { set_error("pks is NULL"); return DPM_EINVAL; }
+    const dpm_pks_params &P = k->prm;
+    if (on) {
+        if (P.dt_mode == 1 && !P.rebuild) {
+            set_error("graph steps need dt_mode 0 or rebuild = 1 (a rebuild only when dt decreases "
+                      "is a host decision)");
+            return DPM_EUNSUPPORTED;
+        }
+        if (k->graph_on) return DPM_OK;
+        DPM_CUDA(cudaSetDevice(k->ctx->device));
+        dpm_bep *b = &k->bep;
+        if (P.dt_mode == 0 && !P.rebuild && (!b->factored || b->sigma != 1.0 / P.dt_max)) {
+            // the fixed-dt step solves against the BEP of sigma = 1/dt_max
+            const double sg = 1.0 / P.dt_max;
+            if (P.precision == DPM_PREC_FP64) DPM_RET(bep_assemble<double>(b, sg, {}, sg, s));
+            else DPM_RET(bep_assemble<float>(b, sg, {}, sg, s));
+        }
+        if (P.precision == DPM_PREC_FP64) DPM_RET(pks_dev_setup<double>(k, s));
+        else DPM_RET(pks_dev_setup<float>(k, s));
+        k->graph_on = 1;
+        return DPM_OK;
+    }
+    if (!k->graph_on) return DPM_OK;
+    int bad = 0;
+    DPM_RET(pks_dev_pull(k, s, &bad));
+    if (k->gexec) {
+        cudaGraphExecDestroy(k->gexec);
+        k->gexec = nullptr;
+    }
+    k->graph_on = 0;
+    k->dev_warm = false;
+    k->bep.factored = true;
+    k->bep.sigma = 1.0 / k->dt_prev;
+    return DPM_OK;
+}
+
 extern "C" int dpm_pks_step(dpm_pks *k, int nsteps, dpm_pks_stats *stats, cudaStream_t s) {
     if (!k || nsteps < 0) { set_error("pks is NULL or nsteps < 0"); return DPM_EINVAL; }
     for (int i = 0; i < nsteps; ++i) {
-        if (k->prm.precision == DPM_PREC_FP64) DPM_RET(pks_step_one<double>(k, s));
+        if (k->graph_on) DPM_RET(pks_graph_step(k, s));
+        else if (k->prm.precision == DPM_PREC_FP64) DPM_RET(pks_step_one<double>(k, s));
         else DPM_RET(pks_step_one<float>(k, s));
+    }
+    if (stats && k->graph_on) {
+        int bad = 0;
+        DPM_RET(pks_dev_pull(k, s, &bad));
+        if (bad) { set_error("time step was not positive/finite on the device"); return DPM_ENUMERIC; }
+        if (k->last_rebuilt) DPM_RET(lsq_status(k->bep.lsq, s));
     }
     if (stats) {
         double d[6];

@@ -179,9 +179,23 @@ struct LsqFactor {
     DevBuf X;      // scratch of the Gram / Cholesky factorisation
     DevBuf work;   // A copy, R, solve scratch
 };
+// Scalars of the device-resident PKS step (Step 3's dt and the time).
+struct StepScalars {
+    double dt, sigma, t, dt_prev;
+    long long step;
+    int rebuilt, bad;  // bad: a non-positive / non-finite dt was replaced by dt_max
+};
+int pks_step_dt(const unsigned int *gmax, double h, double chi, double dt_max, int mode,
+                StepScalars *sc, cudaStream_t s);
+int pks_step_end(StepScalars *sc, int rebuilt, cudaStream_t s);
+
 constexpr int kLsqMaxRhs = 64;  // right-hand sides per lsq_apply call
 // Factor A (already in f.A, m x n col-major): R with R^T R = A^T A.
 int lsq_factor(LsqFactor &f, const int *cond_flag, cudaStream_t s);
+// The same without the host read of the pivot status (no synchronisation;
+// for stream capture): lsq_status reads it later.
+int lsq_factor_async(LsqFactor &f, cudaStream_t s);
+int lsq_status(const LsqFactor &f, cudaStream_t s);
 // C[r][0..n) = X b[r] for nr right-hand sides (b: [nr][m] in T, C: [nr][n] double)
 template <class T>
 int lsq_apply(const LsqFactor &f, const T *b, int ldb, double *C, int nr, cudaStream_t s);

@@ -71,6 +71,7 @@ struct TcArgs {
     const float *s2;     // sin^2(pi (n+1)/(2(N+1))), n < 128
     const float *qsh;    // staged L[v] on the shell, [B][n_shell]
     int64_t n_shell;
+    const double *sigma_dev, *fscale_dev;  // override sigma / fscale when set
 };
 
 __device__ __forceinline__ float pow2_scale(float m, float *inv) {
@@ -250,8 +251,10 @@ static_assert(kRawBytes == 4 * kATile, "the input plane is staged in the operand
 
 // q on the shell for every right-hand side that has a density:
 // qsh[b][e] = (sigma + 6/h^2) v(self) - (1/h^2) sum of v over the 6 neighbours.
-__global__ void k_shell_rhs(int n_shell, float cdiag, float coff, const ApRhs<float> *rhs,
-                            const int *shell_nb, float *qsh) {
+__global__ void k_shell_rhs(int n_shell, double h, double sigma, const double *sigma_dev,
+                            const ApRhs<float> *rhs, const int *shell_nb, float *qsh) {
+    const double sg = sigma_dev ? *sigma_dev : sigma;
+    const float cdiag = (float)(sg + 6.0 / (h * h)), coff = (float)(1.0 / (h * h));
     const int b = blockIdx.y;
     const ApRhs<float> r = rhs[b];
     if (!r.dens) return;
@@ -289,7 +292,7 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
     const uint32_t lane_addr = tm + ((uint32_t)(32 * q4) << 16);
     uint32_t phase = 0, ld_phase = 0;
     const int nitems = a.B * kN;
-    const float fs = (float)a.fscale;
+    const float fs = (float)(a.fscale_dev ? *a.fscale_dev : a.fscale);
     int item = blockIdx.x;
     bool inflight = false;  // a bulk copy into raw completes on bar_ld
     if (item < nitems) {
@@ -545,7 +548,7 @@ k_tc_pencil(TcArgs a, const ApRhs<float> *rhs, float *work, const __grid_constan
     const float w4 = (float)(4.0 / (a.h * a.h));
     for (int n = t; n < kN; n += kPencilThreads) S.w()[n] = w4 * a.s2[n];
     __syncthreads();
-    const float sig = (float)a.sigma;
+    const float sig = (float)(a.sigma_dev ? *a.sigma_dev : a.sigma);
     const double sc = 2.0 / (kN + 1);
     const float nscale = (float)(sc * sc * sc);
     const int nitems = a.B * kN;
@@ -786,8 +789,8 @@ int ap_solve_tc(const ApParams &p, const ApRhs<float> *rhs_dev, float *work, cud
         set_error("tensor-core AP solve supports N = %d only (got %d)", kN, p.N);
         return DPM_EUNSUPPORTED;
     }
-    if (p.sigma_dev || p.fscale_dev || p.cond_flag) {
-        set_error("tensor-core AP solve takes sigma/fscale by value");
+    if (p.cond_flag) {
+        set_error("tensor-core AP solve has no conditional right-hand sides");
         return DPM_EINVAL;
     }
     DPM_RET(tc_configure());
@@ -801,14 +804,15 @@ int ap_solve_tc(const ApParams &p, const ApRhs<float> *rhs_dev, float *work, cud
     const int H = kN / 2, NEp = (H + 3) & ~3;
     const size_t offW = (size_t)H * NEp + (size_t)H * NEp;
     TcArgs a{p.B, p.h, p.sigma, p.fscale, p.mask_f, p.mask_out, p.labels, p.shell, p.shell_nb,
-             p.rp_shell, p.gin, p.rp_gin, bops, tab + offW, p.scratch, p.n_shell};
+             p.rp_shell, p.gin, p.rp_gin, bops, tab + offW, p.scratch, p.n_shell,
+             p.sigma_dev, p.fscale_dev};
     const int nitems = p.B * kN;
     if (p.n_shell > 0 && p.shell_nb) {
         if (!p.scratch) { set_error("tensor-core AP solve: shell scratch missing"); return DPM_EINVAL; }
         DPM_PROF("tc_shell_rhs", s);
-        const float cdiag = (float)(p.sigma + 6.0 / (p.h * p.h)), coff = (float)(1.0 / (p.h * p.h));
         dim3 g((unsigned)std::min<int64_t>((p.n_shell + 255) / 256, 256), p.B);
-        k_shell_rhs<<<g, 256, 0, s>>>((int)p.n_shell, cdiag, coff, rhs_dev, p.shell_nb, p.scratch);
+        k_shell_rhs<<<g, 256, 0, s>>>((int)p.n_shell, p.h, p.sigma, p.sigma_dev, rhs_dev, p.shell_nb,
+                                      p.scratch);
         DPM_LAUNCHED();
     }
     {

@@ -623,8 +623,28 @@ static int mixed_factor(LsqFactor &f, const double *A0, double *R, double *Rinv,
     return DPM_OK;
 }
 
+static int lsq_factor_impl(LsqFactor &f, bool sync, cudaStream_t s);
+
 int lsq_factor(LsqFactor &f, const int *cond_flag, cudaStream_t s) {
     (void)cond_flag;
+    return lsq_factor_impl(f, true, s);
+}
+
+int lsq_factor_async(LsqFactor &f, cudaStream_t s) { return lsq_factor_impl(f, false, s); }
+
+int lsq_status(const LsqFactor &f, cudaStream_t s) {
+    const int m = f.m, n = f.n;
+    if (!f.work.p) return DPM_OK;
+    const int *status = reinterpret_cast<const int *>(f.work.as<double>() + (size_t)m * n + 2 * (size_t)n +
+                                                      (size_t)n * n);
+    int h_status = 0;
+    DPM_CUDA(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DPM_CUDA(cudaStreamSynchronize(s));
+    if (h_status) { set_error("BEP matrix is rank deficient (a zero pivot in the factorisation)"); return DPM_ENUMERIC; }
+    return DPM_OK;
+}
+
+static int lsq_factor_impl(LsqFactor &f, bool sync, cudaStream_t s) {
     const int m = f.m, n = f.n;
     if (m < n || n < 1) { set_error("least squares: need m >= n >= 1 (m=%d n=%d)", m, n); return DPM_EINVAL; }
     // layout of f.work: [A0 m*n][w n][rdiag n][R n*n][status (64 B)][y R*n][res R*m]
@@ -660,6 +680,8 @@ int lsq_factor(LsqFactor &f, const int *cond_flag, cudaStream_t s) {
         k_rinv<<<(n + warps - 1) / warps, 32 * warps, sizeof(double) * warps * n, s>>>(n, R, Rinv, status);
         DPM_LAUNCHED();
     }
+    if (!sync) return DPM_OK;
+    if (!sync) return DPM_OK;
     int h_status = 0;
     DPM_CUDA(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s));
     DPM_CUDA(cudaStreamSynchronize(s));

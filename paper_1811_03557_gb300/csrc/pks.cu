@@ -42,10 +42,10 @@ __device__ __forceinline__ T slope_at(const T *rho, const uint8_t *lab, int64_t 
 }
 
 template <class T>
-__global__ void k_flux(int N, T h, T chi, double dt_d, const uint8_t *lab, const T *rho,
-                       const T *c, T *f_rho, T *f_c) {
+__global__ void k_flux(int N, T h, T chi, double dt_d, const double *dt_dev, const uint8_t *lab,
+                       const T *rho, const T *c, T *f_rho, T *f_c) {
     const int64_t n3 = (int64_t)N * N * N;
-    const T dt = (T)dt_d, inv_h = (T)1 / h, half_h = (T)0.5 * h;
+    const T dt = (T)(dt_dev ? *dt_dev : dt_d), inv_h = (T)1 / h, half_h = (T)0.5 * h;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n3;
          p += (int64_t)gridDim.x * blockDim.x) {
         if (!(lab[p] & DPM_LBL_MPLUS)) {
@@ -345,17 +345,62 @@ template int extend_density<double>(const GammaGeom &, int64_t, int, const doubl
 
 // ---- PKS helpers used by the API layer ------------------------------------
 template <class T>
-int pks_flux(int N, double h, double chi, double dt, const uint8_t *lab, const T *rho, const T *c,
-             T *f_rho, T *f_c, cudaStream_t s) {
+int pks_flux(int N, double h, double chi, double dt, const double *dt_dev, const uint8_t *lab,
+             const T *rho, const T *c, T *f_rho, T *f_c, cudaStream_t s) {
     int64_t n3 = (int64_t)N * N * N;
-    k_flux<T><<<blocks_for(n3, 256), 256, 0, s>>>(N, (T)h, (T)chi, dt, lab, rho, c, f_rho, f_c);
+    k_flux<T><<<blocks_for(n3, 256), 256, 0, s>>>(N, (T)h, (T)chi, dt, dt_dev, lab, rho, c, f_rho,
+                                                  f_c);
     DPM_LAUNCHED();
     return DPM_OK;
 }
-template int pks_flux<float>(int, double, double, double, const uint8_t *, const float *,
-                             const float *, float *, float *, cudaStream_t);
-template int pks_flux<double>(int, double, double, double, const uint8_t *, const double *,
-                              const double *, double *, double *, cudaStream_t);
+template int pks_flux<float>(int, double, double, double, const double *, const uint8_t *,
+                             const float *, const float *, float *, float *, cudaStream_t);
+template int pks_flux<double>(int, double, double, double, const double *, const uint8_t *,
+                              const double *, const double *, double *, double *, cudaStream_t);
+
+// Step 3 on the device: dt = min(dt_max, CFL bound from the face-gradient
+// maxima, dt_prev) (dt_mode 1; dt_max alone in dt_mode 0), sigma = 1/dt.
+// The arithmetic is the host path's, in FP64.
+__global__ void k_step_dt(const unsigned int *gmax, double h, double chi, double dt_max, int mode,
+                          StepScalars *sc) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double dt = dt_max;
+    if (mode == 1) {
+        for (int ax = 0; ax < 3; ++ax) {
+            const float g = __uint_as_float(gmax[ax]);
+            const double gm = (double)g / h;
+            if (gm > 0) dt = fmin(dt, h / (6.0 * chi * gm));
+        }
+        if (sc->step > 0) dt = fmin(dt, sc->dt_prev);
+    }
+    if (!(dt > 0) || !isfinite(dt)) {
+        sc->bad = 1;
+        dt = dt_max;
+    }
+    sc->dt = dt;
+    sc->sigma = 1.0 / dt;
+}
+
+__global__ void k_step_end(StepScalars *sc, int rebuilt) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    sc->t += sc->dt;
+    sc->dt_prev = sc->dt;
+    sc->step += 1;
+    sc->rebuilt = rebuilt;
+}
+
+int pks_step_dt(const unsigned int *gmax, double h, double chi, double dt_max, int mode,
+                StepScalars *sc, cudaStream_t s) {
+    k_step_dt<<<1, 32, 0, s>>>(gmax, h, chi, dt_max, mode, sc);
+    DPM_LAUNCHED();
+    return DPM_OK;
+}
+
+int pks_step_end(StepScalars *sc, int rebuilt, cudaStream_t s) {
+    k_step_end<<<1, 32, 0, s>>>(sc, rebuilt);
+    DPM_LAUNCHED();
+    return DPM_OK;
+}
 
 template <class T>
 int pks_cfl(int N, const uint8_t *lab, const T *c, unsigned int *gmax, cudaStream_t s) {
