@@ -197,10 +197,20 @@ __global__ void k_colscale(int m, const double *A, double *d) {
     if (threadIdx.x == 0) d[j] = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
 }
 
+// Af = float(A D), column-major like A: the Gram products then read FP32
+// operands (FP64 arithmetic runs at a small fraction of the FP32 rate).
+__global__ void k_scale32(int m, const double *A, const double *d, float *Af) {
+    const int j = blockIdx.y;  // column
+    const double dj = d[j];
+    const double *a = A + (size_t)j * m;
+    float *o = Af + (size_t)j * m;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x)
+        o[r] = (float)(a[r] * dj);
+}
+
 // FP32 Gram partials of the equilibrated matrix A D (upper 64 x 64 tiles),
 // part[chunk][i][j] in float; the chunk sums are added in FP64 by k_syrk_reduce32.
-__global__ void k_syrk32_part(int m, int n, const double *A, const double *d, int rows_per,
-                              float *part) {
+__global__ void k_syrk32_part(int m, int n, const float *Af, int rows_per, float *part) {
     __shared__ float As[kGR][kGT + 1], Bs[kGR][kGT + 1];
     const int nb = (n + kGT - 1) / kGT;
     int tile = blockIdx.x, bi = 0;
@@ -215,8 +225,8 @@ __global__ void k_syrk32_part(int m, int n, const double *A, const double *d, in
             const int rr = q % kGR, cc = q / kGR;
             const int r = rs + rr;
             const int ci = bi * kGT + cc, cj = bj * kGT + cc;
-            As[rr][cc] = (r < r1 && ci < n) ? (float)(A[(size_t)ci * m + r] * d[ci]) : 0.f;
-            Bs[rr][cc] = (r < r1 && cj < n) ? (float)(A[(size_t)cj * m + r] * d[cj]) : 0.f;
+            As[rr][cc] = (r < r1 && ci < n) ? Af[(size_t)ci * m + r] : 0.f;
+            Bs[rr][cc] = (r < r1 && cj < n) ? Af[(size_t)cj * m + r] : 0.f;
         }
         __syncthreads();
 #pragma unroll
@@ -272,11 +282,11 @@ __global__ void __launch_bounds__(1024) k_cholesky32(int n, const double *G, dou
     const int t = threadIdx.x, T = blockDim.x, lane = t & 31, warp = t >> 5, nwarp = T >> 5;
     const int nb = (n + 31) >> 5;
     // G's upper triangle (row-major, read coalesced) -> lower triangle of W
-    for (int idx = t; idx < n * n; idx += T) {
-        const int j = idx / n, i = idx % n;
-        W[i * n + j] = i >= j ? (float)G[idx] : 0.f;
-        X[idx] = 0.f;
-    }
+    for (int j = warp; j < n; j += nwarp)
+        for (int i = lane; i < n; i += 32) {
+            W[i * n + j] = i >= j ? (float)G[(size_t)j * n + i] : 0.f;
+            X[j * n + i] = 0.f;
+        }
     __syncthreads();
     for (int p = 0; p < nb; ++p) {
         const int c0 = 32 * p, w = min(32, n - c0);
@@ -332,15 +342,10 @@ __global__ void __launch_bounds__(1024) k_cholesky32(int n, const double *G, dou
         }
         __syncthreads();
         // ---- trailing update of the lower triangle ----------------------------------
-        const int r0 = c0 + w, m = n - r0;
-        const int ntri = m * (m + 1) / 2;  // lower-triangle entries (i >= k) of the trailing block
-        for (int idx = t; idx < ntri; idx += T) {
-            // idx -> (ii, kk) with kk <= ii, row-major over the triangle
-            int ii = (int)((sqrtf(8.f * (float)idx + 1.f) - 1.f) * 0.5f);
-            while (ii * (ii + 1) / 2 > idx) --ii;
-            while ((ii + 1) * (ii + 2) / 2 <= idx) ++ii;
-            const int kk = idx - ii * (ii + 1) / 2;
-            const int i = r0 + ii, k = r0 + kk;
+        const int r0 = c0 + w;
+        // rows of the trailing lower triangle round-robin over the warps, columns over lanes
+        for (int i = r0 + warp; i < n; i += nwarp)
+            for (int k = r0 + lane; k <= i; k += 32) {
             const float *li = W + i * n + c0, *lk = W + k * n + c0;
             float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
             int j = 0;
@@ -379,10 +384,9 @@ __global__ void __launch_bounds__(1024) k_cholesky32(int n, const double *G, dou
     }
     __syncthreads();
     // ---- M[bi][k] = X_bi,bi L[bi][k] (k < bi), stored transposed in X's upper triangle
-    for (int idx = t; idx < n * n; idx += T) {
-        const int r = idx / n, c = idx % n;  // element (r, c) of the lower off-diagonal part
-        const int bi = r >> 5, bk = c >> 5;
-        if (bk >= bi) continue;
+    for (int r = 32 + warp; r < n; r += nwarp)
+        for (int c = lane; c < (r & ~31); c += 32) {  // (r, c) in the lower off-diagonal blocks
+        const int bi = r >> 5;
         const int ri = 32 * bi;
         float a0 = 0.f, a1 = 0.f;
         int s2 = ri;
@@ -396,10 +400,10 @@ __global__ void __launch_bounds__(1024) k_cholesky32(int n, const double *G, dou
     __syncthreads();
     // ---- off-diagonal blocks of X by block diagonal d ------------------------------
     for (int d = 1; d < nb; ++d) {
-        for (int idx = t; idx < n * n; idx += T) {
-            const int r = idx / n, c = idx % n;
-            const int bi = r >> 5, bj = c >> 5;
-            if (bi - bj != d) continue;
+        // rows r of block bi >= d, columns c of block bj = bi - d
+        for (int r = 32 * d + warp; r < n; r += nwarp) {
+            const int bi = r >> 5, bj = bi - d;
+            const int c = 32 * bj + lane;
             // sum over k = bj .. bi-1 (block rows), s in block k: M[bi](r, s) X(s, c);
             // the range is a whole number of 32-row blocks
             float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
@@ -414,10 +418,9 @@ __global__ void __launch_bounds__(1024) k_cholesky32(int n, const double *G, dou
         }
         __syncthreads();
     }
-    for (int idx = t; idx < n * n; idx += T) {
-        const int r = idx / n, c = idx % n;  // Rinv[r][c] = X[c][r]
-        Rinv[idx] = c >= r ? (double)X[c * n + r] : 0.0;
-    }
+    for (int r = warp; r < n; r += nwarp)
+        for (int c = lane; c < n; c += 32)  // Rinv[r][c] = X[c][r]
+            Rinv[(size_t)r * n + c] = c >= r ? (double)X[c * n + r] : 0.0;
 }
 
 // Cholesky G = L L^T (upper triangle of G given) in one CTA; R = L^T row-major.
@@ -593,15 +596,20 @@ static int mixed_factor(LsqFactor &f, const double *A0, double *R, double *Rinv,
     const size_t nn = (size_t)n * n;
     const size_t smem = 2 * nn * sizeof(float);
     const bool in_smem = smem <= 226 * 1024;
-    // partials [chunks][n][n] floats, then G [n][n] (and W [n][n] for the FP64 Cholesky)
-    DPM_RET(f.X.reserve(sizeof(float) * nn * (size_t)chunks + sizeof(double) * nn * (in_smem ? 1 : 2) + 16));
+    // partials [chunks][n][n] floats, then G [n][n] (and W [n][n] for the FP64
+    // Cholesky), then Af [n][m] floats
+    const size_t gbytes = sizeof(double) * nn * (in_smem ? 1 : 2);
+    DPM_RET(f.X.reserve(sizeof(float) * nn * (size_t)chunks + 16 + gbytes + sizeof(float) * (size_t)m * n));
     float *part = f.X.as<float>();
     double *G = reinterpret_cast<double *>(part + nn * chunks + (nn * chunks & 1));
+    float *Af = reinterpret_cast<float *>(reinterpret_cast<char *>(G) + gbytes);
     {
         DPM_PROF("lsq_gram_syrk", s);
         k_colscale<<<n, 1024, 0, s>>>(m, A0, dscale);
         DPM_LAUNCHED();
-        k_syrk32_part<<<dim3(ntiles, chunks), 256, 0, s>>>(m, n, A0, dscale, rows_per, part);
+        k_scale32<<<dim3(8, n), 256, 0, s>>>(m, A0, dscale, Af);
+        DPM_LAUNCHED();
+        k_syrk32_part<<<dim3(ntiles, chunks), 256, 0, s>>>(m, n, Af, rows_per, part);
         DPM_LAUNCHED();
         k_syrk_reduce32<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(n, chunks, part, G);
         DPM_LAUNCHED();
