@@ -251,10 +251,14 @@ static_assert(kRawBytes == 4 * kATile, "the input plane is staged in the operand
 
 // q on the shell for every right-hand side that has a density:
 // qsh[b][e] = (sigma + 6/h^2) v(self) - (1/h^2) sum of v over the 6 neighbours.
-__global__ void k_shell_rhs(int n_shell, double h, double sigma, const double *sigma_dev,
-                            const ApRhs<float> *rhs, const int *shell_nb, float *qsh) {
-    const double sg = sigma_dev ? *sigma_dev : sigma;
-    const float cdiag = (float)(sg + 6.0 / (h * h)), coff = (float)(1.0 / (h * h));
+__global__ void k_shell_rhs(int n_shell, double c6, float coff, double sigma,
+                            const double *sigma_dev, const ApRhs<float> *rhs, const int *shell_nb,
+                            float *qsh) {
+    // cdiag = sigma + 6/h^2 in FP64, rounded once (FP64 work kept out of the per-thread path)
+    __shared__ float cd;
+    if (threadIdx.x == 0) cd = (float)((sigma_dev ? *sigma_dev : sigma) + c6);
+    __syncthreads();
+    const float cdiag = cd;
     const int b = blockIdx.y;
     const ApRhs<float> r = rhs[b];
     if (!r.dens) return;
@@ -811,8 +815,8 @@ int ap_solve_tc(const ApParams &p, const ApRhs<float> *rhs_dev, float *work, cud
         if (!p.scratch) { set_error("tensor-core AP solve: shell scratch missing"); return DPM_EINVAL; }
         DPM_PROF("tc_shell_rhs", s);
         dim3 g((unsigned)std::min<int64_t>((p.n_shell + 255) / 256, 256), p.B);
-        k_shell_rhs<<<g, 256, 0, s>>>((int)p.n_shell, p.h, p.sigma, p.sigma_dev, rhs_dev, p.shell_nb,
-                                      p.scratch);
+        k_shell_rhs<<<g, 256, 0, s>>>((int)p.n_shell, 6.0 / (p.h * p.h), (float)(1.0 / (p.h * p.h)),
+                                      p.sigma, p.sigma_dev, rhs_dev, p.shell_nb, p.scratch);
         DPM_LAUNCHED();
     }
     {

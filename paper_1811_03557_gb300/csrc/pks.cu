@@ -256,18 +256,28 @@ __global__ void k_assemble(int64_t total, const double *psi_in, const T *trace, 
 template <class T, class P>
 __global__ void k_extend(int n, int nsh, int beta, const P *phi, const double *dist,
                          const double *C, int ldc, const double *neumann, T *dens, int ldd,
-                         int nr, int clamp) {
+                         int nr, int clamp, int cs_ok) {
+    // the coefficients in P, converted once per block (cs_ok: they fit in shared memory)
+    extern __shared__ unsigned char ext_sm[];
+    P *cs = reinterpret_cast<P *>(ext_sm);
+    const int ncu = (beta ? 2 : 1) * nsh;
+    if (cs_ok) {
+        for (int i = threadIdx.x; i < nr * ncu; i += blockDim.x)
+            cs[i] = (P)C[(size_t)(i / ncu) * ldc + i % ncu];
+        __syncthreads();
+    }
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= n) return;
     const P *ph = phi + (size_t)warp * nsh;
     const double d = dist[warp];
     for (int q = 0; q < nr; ++q) {
         const double *cq = C + (size_t)q * ldc;
+        const P *cp = cs + (size_t)q * ncu;
         P s0 = (P)0, s2 = (P)0;
         for (int nu = lane; nu < nsh; nu += 32) {
             const P f = ph[nu];
-            s0 += (P)cq[nu] * f;
-            if (beta) s2 += (P)cq[nsh + nu] * f;
+            s0 += (cs_ok ? cp[nu] : (P)cq[nu]) * f;
+            if (beta) s2 += (cs_ok ? cp[nsh + nu] : (P)cq[nsh + nu]) * f;
         }
         for (int o = 16; o > 0; o >>= 1) {
             s0 += __shfl_xor_sync(0xffffffffu, s0, o);
@@ -329,11 +339,15 @@ int extend_density(const GammaGeom &gg, int64_t n_gamma, int beta, const double 
                                                                          g.phi32.as<float>());
             DPM_LAUNCHED();
         }
-        k_extend<T, float><<<blocks, 256, 0, s>>>((int)n_gamma, gg.nsh, beta, g.phi32.as<float>(),
-                                                  gg.dist.as<double>(), C, ldc, neumann, dens, ldd, nr, clamp);
+        const size_t sm = sizeof(float) * (size_t)nr * (beta ? 2 : 1) * gg.nsh;
+        const int ok = sm <= 32 * 1024;
+        k_extend<T, float><<<blocks, 256, ok ? sm : 0, s>>>((int)n_gamma, gg.nsh, beta, g.phi32.as<float>(),
+                                                  gg.dist.as<double>(), C, ldc, neumann, dens, ldd, nr, clamp, ok);
     } else {
-        k_extend<T, double><<<blocks, 256, 0, s>>>((int)n_gamma, gg.nsh, beta, gg.phi.as<double>(),
-                                                   gg.dist.as<double>(), C, ldc, neumann, dens, ldd, nr, clamp);
+        const size_t sm = sizeof(double) * (size_t)nr * (beta ? 2 : 1) * gg.nsh;
+        const int ok = sm <= 32 * 1024;
+        k_extend<T, double><<<blocks, 256, ok ? sm : 0, s>>>((int)n_gamma, gg.nsh, beta, gg.phi.as<double>(),
+                                                   gg.dist.as<double>(), C, ldc, neumann, dens, ldd, nr, clamp, ok);
     }
     DPM_LAUNCHED();
     return DPM_OK;
