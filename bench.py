@@ -378,9 +378,10 @@ def run_aux(abi, torch, ctx, stream):
     """Batched auxiliary solves alone (Definition 2.4), dense uniform-random q
     in [-1, 1] (seed 0), inputs resident and larger than L2: the tensor-core
     solver at N = 128 with the 162-column batch, the FP32 SIMT solver and the
-    plain FP64 solver (one right-hand side per call) at N = 256.  Roofline:
-    the three-pass (tensor-core) or five-pass (SIMT) schedule moves 24 or
-    40 bytes per grid point per FP32 solve (read + write of the cube per pass)."""
+    plain FP64 solver (one right-hand side per call) at N = 256, and the N = 256
+    tensor-core solver.  Roofline: the three-pass (tensor-core, N = 128),
+    five-pass (SIMT) or assemble + six-pass + output (tensor-core, N = 256)
+    schedule moves 24, 40 or 64 bytes per grid point per FP32 solve."""
     from paper_1811_03557_gb300.workloads import random_rhs
     peaks, src = measured_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
@@ -410,6 +411,10 @@ def run_aux(abi, torch, ctx, stream):
     ms, v = timed(128, 162, abi.DPM_PREC_TC32, 5)
     gbs = 24.0 * 162 * 128 ** 3 / (ms / 1e3) / 1e9
     out["tc32_N128_B162"] = {"ms": ms, "grid_pts_per_s": v, "hbm_gbs": gbs, "frac": gbs / hbm}
+    ms, v = timed(256, 16, abi.DPM_PREC_TC32, 3)
+    # assemble (read f, write q), six out-of-place passes, masked output copy
+    gbs = 64.0 * 16 * 256 ** 3 / (ms / 1e3) / 1e9
+    out["tc32_N256_B16"] = {"ms": ms, "grid_pts_per_s": v, "hbm_gbs": gbs, "frac": gbs / hbm}
     ms, v = timed(256, 16, abi.DPM_PREC_FP32, 3)
     gbs = 40.0 * 16 * 256 ** 3 / (ms / 1e3) / 1e9
     out["fp32_N256_B16"] = {"ms": ms, "grid_pts_per_s": v, "hbm_gbs": gbs, "frac": gbs / hbm}

@@ -102,7 +102,7 @@ int run_ap(int prec, ApParams p, const std::vector<ApRhs<T>> &rhs, DevBuf &work,
            cudaStream_t s) {
     const int B = (int)rhs.size();
     if (B == 0) return DPM_OK;
-    const size_t cube = (size_t)p.N * p.N * p.N * sizeof(T);
+    const size_t cube = (size_t)p.N * p.N * p.N * sizeof(T) * ap_cubes_per_rhs(prec, p.N);
     size_t cb = std::max<size_t>(1, std::min<size_t>(B, kWorkCap / cube));
     size_t extra = 0;  // tensor-core solver: staged shell right-hand sides after the cubes
     if (prec == DPM_PREC_TC32) extra = tc_scratch_elems(p, (int)cb) * sizeof(float);
@@ -127,7 +127,7 @@ int run_ap(int prec, ApParams p, const std::vector<ApRhs<T>> &rhs, DevBuf &work,
 template <class T>
 int run_ap_dev(int prec, ApParams p, const ApRhs<T> *desc_dev, int B, DevBuf &work, cudaStream_t s) {
     if (B == 0) return DPM_OK;
-    const size_t cube = (size_t)p.N * p.N * p.N * sizeof(T);
+    const size_t cube = (size_t)p.N * p.N * p.N * sizeof(T) * ap_cubes_per_rhs(prec, p.N);
     size_t cb = std::max<size_t>(1, std::min<size_t>(B, kWorkCap / cube));
     size_t extra = 0;
     if (prec == DPM_PREC_TC32) extra = tc_scratch_elems(p, (int)cb) * sizeof(float);
@@ -592,7 +592,7 @@ extern "C" int dpm_bep_reserve(dpm_bep *b, int max_nreq) {
     const size_t T = b->prec == DPM_PREC_FP64 ? sizeof(double) : sizeof(float);
     const int64_t ng = b->gi.n_gamma, m = b->gi.n_gin;
     const int B = 2 * max_nreq;  // particular + Neumann, or Green's formula
-    const size_t cube = (size_t)b->N * b->N * b->N * T;
+    const size_t cube = (size_t)b->N * b->N * b->N * T * ap_cubes_per_rhs(b->prec, b->N);
     const size_t cb = std::max<size_t>(1, std::min<size_t>(B, kWorkCap / cube));
     size_t extra = 0;
     if (b->prec == DPM_PREC_TC32) {
@@ -749,7 +749,7 @@ template <class T> int pks_dev_setup(dpm_pks *k, cudaStream_t s) {
     DPM_CUDA(cudaMemcpyAsync(k->desc_rb.p, rb.data(), sizeof(ApRhs<T>) * rb.size(), cudaMemcpyHostToDevice, s));
     DPM_CUDA(cudaMemcpyAsync(k->desc_green.p, gr.data(), sizeof(ApRhs<T>) * gr.size(), cudaMemcpyHostToDevice, s));
     // buffers every solve of the step touches (the eager step sizes them the same way)
-    const size_t cube = (size_t)b->N * b->N * b->N * sizeof(T);
+    const size_t cube = (size_t)b->N * b->N * b->N * sizeof(T) * ap_cubes_per_rhs(b->prec, b->N);
     const int B = b->ncol + 2;
     const size_t cb = std::max<size_t>(1, std::min<size_t>(B, kWorkCap / cube));
     size_t extra = 0;

@@ -156,6 +156,11 @@ void ap_params_from_index(ApParams &p, const GridIndex &gi);
 template <class T>
 int ap_solve_simt(const ApParams &p, const ApRhs<T> *rhs_dev, T *work, cudaStream_t s);
 int ap_solve_tc(const ApParams &p, const ApRhs<float> *rhs_dev, float *work, cudaStream_t s);
+// N = 256: six out-of-place passes; work holds 2 B N^3 floats.
+int ap_solve_tc256(const ApParams &p, const ApRhs<float> *rhs_dev, float *work, cudaStream_t s);
+int tc256_status_check();
+// AP workspace cubes per right-hand side (the N = 256 tensor-core solver ping-pongs).
+inline size_t ap_cubes_per_rhs(int prec, int N) { return (prec == 2 && N == 256) ? 2 : 1; }
 // floats of ApParams::scratch the tensor-core solver needs for B right-hand sides
 size_t tc_scratch_elems(const ApParams &p, int B);
 bool tc_supported(int N);

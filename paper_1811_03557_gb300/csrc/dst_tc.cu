@@ -772,11 +772,14 @@ int tc_configure() {
 
 }  // namespace
 
-bool tc_supported(int N) { return N == kN; }
+bool tc_supported(int N) { return N == kN || N == 256; }
 
-size_t tc_scratch_elems(const ApParams &p, int B) { return (size_t)B * (size_t)p.n_shell; }
+size_t tc_scratch_elems(const ApParams &p, int B) {
+    return p.N == kN ? (size_t)B * (size_t)p.n_shell : 0;  // the N = 256 solver scatters in place
+}
 
 int tc_status_check() {
+    DPM_RET(tc256_status_check());
     int st = 0;
     DPM_CUDA(cudaMemcpyFromSymbol(&st, g_tc_status, sizeof(int)));
     if (st) {
@@ -790,9 +793,14 @@ int tc_status_check() {
 
 int ap_solve_tc(const ApParams &p, const ApRhs<float> *rhs_dev, float *work, cudaStream_t s) {
     if (!tc_supported(p.N)) {
-        set_error("tensor-core AP solve supports N = %d only (got %d)", kN, p.N);
+        set_error("tensor-core AP solve supports N = 128 and 256 only (got %d)", p.N);
         return DPM_EUNSUPPORTED;
     }
+    if (p.cond_flag) {
+        set_error("tensor-core AP solve has no conditional right-hand sides");
+        return DPM_EINVAL;
+    }
+    if (p.N == 256) return ap_solve_tc256(p, rhs_dev, work, s);
     if (p.cond_flag) {
         set_error("tensor-core AP solve has no conditional right-hand sides");
         return DPM_EINVAL;

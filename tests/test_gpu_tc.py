@@ -53,7 +53,7 @@ def test_tc_smooth_and_single_mode_inputs(ctx):
         assert rel(u[b], O.aux_solve(q[b].astype(np.float64), h, sigma)) < 1e-5
 
 
-def test_tc_rejects_other_sizes(ctx):
+def test_tc_rejects_other_sizes(ctx):  # N = 64 has no tensor-core solver
     q = torch.zeros(1, 64, 64, 64, device="cuda")
     with pytest.raises(abi.DPMError) as e:
         abi.dpm_aux_solve_batched(ctx, 64, 0.1, 1.0, 1, q, q, TC)
