@@ -420,6 +420,31 @@ def run_aux(abi, torch, ctx, stream):
     out["fp32_N256_B16"] = {"ms": ms, "grid_pts_per_s": v, "hbm_gbs": gbs, "frac": gbs / hbm}
     ms, v = timed(256, 2, abi.DPM_PREC_FP64, 1, calls=2)
     out["fp64_N256_per_solve"] = {"ms": ms, "grid_pts_per_s": v}
+    # the BEP batch workload: ellipsoid (1, 0.8, 0.6) in [-1.2, 1.2]^3, N = 256,
+    # K = 12 (338 columns in one batched solve), sigma = 1/dt + 1, dt = 1e-4
+    from paper_1811_03557_gb300.workloads import WORKLOADS
+    wb = WORKLOADS["bep_ellipsoid_N256_K12"]
+    for prec, key in ((abi.DPM_PREC_TC32, "bep_build_N256_K12_tc32"),):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bep = abi.dpm_bep_build(ctx, wb.geom, wb.N, wb.lo, wb.hi, wb.sigma, wb.K, wb.beta, prec, stream)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        abi.dpm_profile_reset()
+        abi.dpm_profile_enable(True)
+        bep2 = abi.dpm_bep_build(ctx, wb.geom, wb.N, wb.lo, wb.hi, wb.sigma, wb.K, wb.beta, prec, stream)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        abi.dpm_profile_enable(False)
+        ap_ms = sum(abi.dpm_profile_read(k)[0] for k in ("tc256_rhs", "tc256_k", "tc256_j", "tc256_i", "tc256_out"))
+        fac_ms = sum(abi.dpm_profile_read(k)[0] for k in ("lsq_gram_syrk", "lsq_cholesky"))
+        abi.dpm_profile_reset()
+        abi.dpm_bep_destroy(bep)
+        abi.dpm_bep_destroy(bep2)
+        ncol = wb.ncol
+        out[key] = {"build_ms": (t2 - t1) * 1e3, "first_build_ms": (t1 - t0) * 1e3, "ap_ms": ap_ms,
+                    "factor_ms": fac_ms, "ncol": ncol,
+                    "ap_grid_pts_per_s": ncol * wb.N ** 3 / (ap_ms / 1e3) if ap_ms > 0 else None}
     out["peak"] = {"hbm_gbs": hbm, "source": src}
     out["data"] = "uniform [-1, 1] q, seed 0; dense in, dense out; inputs larger than L2"
     return out

@@ -49,9 +49,9 @@ class LibraryBackend:
 
     Every slot owns a stream, device buffers for `max_batch` right-hand sides
     and solutions of up to max_N^3 values, and a pinned host buffer the
-    solutions come back to.  Storage is FP32: N = 128 problems use the
-    tensor-core solver (its only size), others the FP32 SIMT solver; the
-    least squares and the extension run in FP64 as in dpm_solve.
+    solutions come back to.  Storage is FP32: N = 128 and 256 problems use the
+    tensor-core solvers (their sizes), others the FP32 SIMT solver; the least
+    squares and the extension run in FP64 as in dpm_solve.
     """
 
     def __init__(self, ctx, n_slots: int, max_batch: int, max_N: int, device: int = 0,
@@ -73,7 +73,7 @@ class LibraryBackend:
     # -- sizes ----------------------------------------------------------------
     def precision(self, model) -> int:
         a = self.abi
-        return a.DPM_PREC_TC32 if (self.tc and model.N == 128) else a.DPM_PREC_FP32
+        return a.DPM_PREC_TC32 if (self.tc and model.N in (128, 256)) else a.DPM_PREC_FP32
 
     @staticmethod
     def estimate_bytes(model, max_batch: int, pks: bool = False) -> int:
@@ -85,8 +85,9 @@ class LibraryBackend:
         h = (model.hi - model.lo) / (N + 1)
         ng = int(2.0 * 4.0 * np.pi * (r / h) ** 2) + 1024   # |gamma| (two layers of the surface)
         m = ng // 2 + 512                                    # |gamma_in|
-        build_cubes = min(ncol + 4, (8 << 30) // cube)
-        b = build_cubes * cube + 2 * max_batch * cube        # AP workspace
+        per_rhs = 2 * cube if N == 256 else cube                 # the N = 256 TC solver ping-pongs
+        build_cubes = min(ncol + 4, (8 << 30) // per_rhs)
+        b = build_cubes * per_rhs + 2 * max_batch * per_rhs      # AP workspace
         b += N ** 3 + 16 * N * N + 64 * ng                   # labels, row pointers, index lists
         b += ng * nsh * 12 + ng * 56                         # harmonic tables, foot points, normals
         b += ncol * ng * 4 + ncol * m * 8 + (ncol + 4) * m * 4
