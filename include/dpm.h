@@ -50,7 +50,7 @@ extern "C" {
 #define DPM_PREC_FP32 0  /* FP32 SIMT folded DST-I, FP32 storage            */
 #define DPM_PREC_FP64 1  /* FP64 SIMT DST-I, FP64 storage (comparator path) */
 #define DPM_PREC_TC32 2  /* tcgen05 DST-I contractions (3-term f16 split,
-                            FP32 accumulate), FP32 storage; N = 128 only    */
+                            FP32 accumulate), FP32 storage; N = 128, 256    */
 
 /* ---- node label bits (one uint8 per node of M^0, Definition 2.1) ------- */
 #define DPM_LBL_MPLUS 1  /* node of M^+ (strict interior of Omega)           */
@@ -154,7 +154,7 @@ int dpm_classify(dpm_ctx *ctx, const dpm_geom *geom, int N, double lo, double hi
  *         DPM_PREC_FP64.  u may equal q (in place); otherwise they must not
  *         overlap.
  * Requires 2 <= N <= 256, h > 0, sigma >= 0, B >= 1.  DPM_PREC_TC32 requires
- * N = 128 (DPM_EUNSUPPORTED otherwise) and a 16-byte aligned q (its planes
+ * N = 128 or 256 (DPM_EUNSUPPORTED otherwise) and a 16-byte aligned q (its planes
  * are staged by bulk copies; DPM_EINVAL otherwise).  Scratch: the context's
  * workspace, grown on demand.
  */
