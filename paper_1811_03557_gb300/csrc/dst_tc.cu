@@ -297,9 +297,24 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
     uint32_t phase = 0, ld_phase = 0;
     const int nitems = a.B * kN;
     const float fs = (float)(a.fscale_dev ? *a.fscale_dev : a.fscale);
+    // An item whose plane needs no transform: forward without f and without shell
+    // nodes in plane i (the transform of zero is zero: the output plane is zeroed),
+    // inverse without dense output and without gamma_in nodes in plane i.
+    auto skippable = [&](int it) -> bool {
+        const ApRhs<float> &rr = rhs[it / kN];
+        const int ii = it % kN;
+        if (!INV) {
+            if (rr.f) return false;
+            if (!rr.dens) return true;
+            return a.rp_shell[(int64_t)ii * kN] == a.rp_shell[(int64_t)(ii + 1) * kN];
+        }
+        if (rr.out_dense) return false;
+        if (!rr.out_trace) return true;
+        return a.rp_gin[(int64_t)ii * kN] == a.rp_gin[(int64_t)(ii + 1) * kN];
+    };
     int item = blockIdx.x;
     bool inflight = false;  // a bulk copy into raw completes on bar_ld
-    if (item < nitems) {
+    if (item < nitems && !skippable(item)) {
         const float *src = plane_src<INV>(rhs[item / kN], work, item / kN, item % kN);
         if (src) {
             if (t == 0) {
@@ -317,10 +332,37 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
         const int nx = item + gridDim.x;
         const float *nsrc = nullptr;
         bool nsparse = false;  // next item: shell-only right-hand side (a BEP column)
-        if (nx < nitems) {
+        if (nx < nitems && !skippable(nx)) {
             const ApRhs<float> &rn = rhs[nx / kN];
             nsrc = plane_src<INV>(rn, work, nx / kN, nx % kN);
             nsparse = !INV && !rn.f && rn.dens;
+        }
+        // stage the next item's input in raw (free whenever this is called)
+        auto stage_next = [&]() {
+            if (nsrc) {
+                if (t == 0) {
+                    tc::mbar_arrive_expect_tx(bar_ld, kRawBytes);
+                    tc::bulk_g2s(raw, nsrc, kRawBytes, bar_ld);
+                }
+                inflight = true;
+            } else if (nsparse) {
+                float4 *r4 = reinterpret_cast<float4 *>(raw);
+                for (int q = t; q < kN * kN / 4; q += kPlaneThreads) r4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        };
+        if (skippable(item)) {
+            if (!INV) {
+                float4 *w4 = reinterpret_cast<float4 *>(work + ((size_t)b * kN + i) * kN * kN);
+                for (int q = t; q < kN * kN / 4; q += kPlaneThreads) w4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            tc::fence_async_smem();
+            __syncthreads();
+            stage_next();
+            tc::tc_fence_before_sync();
+            __syncthreads();
+            tc::tc_fence_after_sync();
+            pre = nsparse;
+            continue;
         }
         int ge0 = 0, ge1 = 0;  // gamma_in nodes of this plane (trace output)
         if (INV && r.out_trace) {
@@ -449,16 +491,7 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
         if (!run_transform<true>(S, tm, phase)) { ok = false; break; }
         // ---- the operand region is free: stage the next item's input -------------
         const bool stage_trace = INV && r.out_trace;
-        if (!stage_trace && nsrc) {
-            if (t == 0) {
-                tc::mbar_arrive_expect_tx(bar_ld, kRawBytes);
-                tc::bulk_g2s(raw, nsrc, kRawBytes, bar_ld);
-            }
-            inflight = true;
-        } else if (nsparse) {
-            float4 *r4 = reinterpret_cast<float4 *>(raw);
-            for (int q = t; q < kN * kN / 4; q += kPlaneThreads) r4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
+        if (!stage_trace) stage_next();
         // ---- phase E: D2 (row = c = L); columns [0,64) even j-modes, [64,128) odd --
         const float iout = inv2 * (1.f / kSScale);
         if (!INV) {
@@ -509,13 +542,7 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
                 // the staging writes precede the next bulk copy into the same bytes
                 tc::fence_async_smem();
                 __syncthreads();
-                if (nsrc) {
-                    if (t == 0) {
-                        tc::mbar_arrive_expect_tx(bar_ld, kRawBytes);
-                        tc::bulk_g2s(raw, nsrc, kRawBytes, bar_ld);
-                    }
-                    inflight = true;
-                }
+                stage_next();
             }
         }
         tc::tc_fence_before_sync();
