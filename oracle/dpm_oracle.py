@@ -78,9 +78,24 @@ def ellipsoid_form(geom, X, Y, Z):
 
 
 def inside_mask(geom, N, lo, hi) -> np.ndarray:
-    """Membership of each node of M^0 in the open domain Omega (F < 1)."""
+    """Membership of each node of M^0 in the open domain Omega: F < 1 for a
+    sphere or ellipsoid; for a spherical shell (kind 2, radii axes[0] > axes[1])
+    F < 1 for the outer sphere and F > 1 for the inner one."""
     x = node_coords(N, lo, hi)
-    return ellipsoid_form(geom, x[:, None, None], x[None, :, None], x[None, None, :]) < 1.0
+    X, Y, Z = x[:, None, None], x[None, :, None], x[None, None, :]
+    if geom.kind == 2:
+        c, (ro, ri, _) = geom.center, geom.axes
+        outer = ellipsoid_form(_Sph(c, ro), X, Y, Z) < 1.0
+        inner = ellipsoid_form(_Sph(c, ri), X, Y, Z) > 1.0
+        return outer & inner
+    return ellipsoid_form(geom, X, Y, Z) < 1.0
+
+
+class _Sph:
+    """A sphere as the (centre, axes) pair ellipsoid_form reads."""
+
+    def __init__(self, c, r):
+        self.kind, self.center, self.axes = 0, tuple(c), (r, r, r)
 
 
 def _stencil_union(S: np.ndarray) -> np.ndarray:
@@ -166,6 +181,13 @@ def foot_point(geom, P: np.ndarray, tol: float = 1e-15, maxit: int = 200):
     c = np.asarray(geom.center, dtype=np.float64)
     a = np.asarray(geom.axes, dtype=np.float64)
     q = P - c
+    if geom.kind == 2:
+        # spherical shell: the nearer of the two spheres; normal (x - c)/|x - c| and
+        # d = |x - c| - r on both (outward from the centre, also on the inner sphere)
+        rho = np.linalg.norm(q, axis=1)
+        n = q / rho[:, None]
+        r = np.where(np.abs(rho - a[0]) <= np.abs(rho - a[1]), a[0], a[1])
+        return c + r[:, None] * n, rho - r, n
     if geom.kind == 0:
         r = a[0]
         rho = np.linalg.norm(q, axis=1)
@@ -401,6 +423,135 @@ def dpm_elliptic_solve(setup: DPMSetup, f, neumann=None):
 
 
 # ---------------------------------------------------------------------------
+# Domain decomposition, Case 1 (Section 3): Omega_1 = ball |x - c| < r1,
+# Omega_2 = shell r1 < |x - c| < r2, each embedded in its own cubic box and
+# grid.  The interface Z (|x - c| = r1) carries three spherical-harmonic
+# series -- u, du/dnu, d2u/dnu2 with nu = (x - c)/|x - c| -- shared by both
+# sub-domains, which is how the interface conditions (continuity of u and of
+# its normal derivatives across Z) enter; Gamma (|x - c| = r2) carries u and
+# d2u/dn2 with du/dn the Neumann data (2-term extension of the single domain).
+# The reduced BEPs of both sub-domains (eqs. reduced_DD1_BEP1,
+# reduced_DD1_BEP2) are stacked into one least-squares problem.
+# ---------------------------------------------------------------------------
+class Shell:
+    """Spherical shell r_in < |x - c| < r_out (kind 2; axes = (r_out, r_in, 0))."""
+
+    def __init__(self, r_out, r_in, center=(0.0, 0.0, 0.0)):
+        self.kind, self.center, self.axes = 2, tuple(center), (r_out, r_in, 0.0)
+
+
+class DDSubdomain:
+    """Point sets and gamma geometry of one sub-domain; `surf` = 1 for the grid
+    boundary nodes whose foot point lies on Z, 0 for those on Gamma."""
+
+    def __init__(self, geom, N, lo, hi, r_z, K):
+        self.geom, self.N, self.lo, self.hi = geom, N, lo, hi
+        self.h = grid_spacing(N, lo, hi)
+        self.sets = point_sets(inside_mask(geom, N, lo, hi))
+        self.labels = labels_from_sets(self.sets)
+        self.gamma_idx = np.flatnonzero(self.sets["gamma"].reshape(-1))
+        self.gin_idx = np.flatnonzero(self.sets["gin"].reshape(-1))
+        self.gin_pos = np.searchsorted(self.gamma_idx, self.gin_idx)
+        X, Y, Z = mesh(N, lo, hi)
+        P = np.stack([X.reshape(-1)[self.gamma_idx], Y.reshape(-1)[self.gamma_idx],
+                      Z.reshape(-1)[self.gamma_idx]], axis=1)
+        self.xf, self.d, self.normal = foot_point(geom, P)
+        rf = np.linalg.norm(self.xf - np.asarray(geom.center), axis=1)
+        self.surf = (np.abs(rf - r_z) < 1e-9 * max(1.0, r_z)).astype(np.int64)
+        self.phi = boundary_basis(geom, self.xf, K)
+
+    def i_minus_p_gin(self, v_gamma, sigma):
+        """Tr_{gamma_in} (v_gamma - P v_gamma) on this sub-domain's grid."""
+        vg = gamma_density_grid(v_gamma, self.gamma_idx, self.N)
+        Pv = difference_potential(vg, self.sets, self.h, sigma)
+        return v_gamma[self.gin_pos] - Pv.reshape(-1)[self.gin_idx]
+
+
+class DDSetup:
+    """Steps 1-2 of the two-sub-domain method: both sub-domains, the column
+    densities of the shared Z series and the Gamma series, and the stacked
+    reduced BEP matrix with its QR decomposition."""
+
+    def __init__(self, center, r1, r2, N1, lo1, hi1, N2, lo2, hi2, KZ, KG, sigma, build_bep=True):
+        self.r1, self.r2, self.KZ, self.KG, self.sigma = r1, r2, KZ, KG, sigma
+        self.nz, self.ng = (KZ + 1) ** 2, (KG + 1) ** 2
+        self.ncol = 3 * self.nz + 2 * self.ng
+        K = max(KZ, KG)
+        self.sub = [DDSubdomain(_Sph(center, r1), N1, lo1, hi1, r1, KZ),
+                    DDSubdomain(Shell(r2, r1, center), N2, lo2, hi2, r1, K)]
+        if build_bep:
+            self.A = self.bep_matrix()
+            self.Q, self.R = np.linalg.qr(self.A)
+
+    def column_density(self, l, k):
+        """Density of unknown k on sub-domain l's grid boundary: Z columns
+        (3 terms x nz harmonics: phi, s phi, s^2/2 phi with s the signed distance
+        from Z along nu) on its Z nodes, Gamma columns (2 terms x ng: phi,
+        d^2/2 phi) on its Gamma nodes; zero on the other nodes."""
+        sd = self.sub[l]
+        out = np.zeros(len(sd.gamma_idx))
+        if k < 3 * self.nz:
+            t, nu = divmod(k, self.nz)
+            m = sd.surf == 1
+            fac = (np.ones_like(sd.d), sd.d, 0.5 * sd.d ** 2)[t]
+        else:
+            t, nu = divmod(k - 3 * self.nz, self.ng)
+            m = sd.surf == 0
+            fac = (np.ones_like(sd.d), 0.5 * sd.d ** 2)[t]
+        out[m] = fac[m] * sd.phi[m, nu]
+        return out
+
+    def bep_matrix(self):
+        """Rows gamma_in of Omega_1, then gamma_in of Omega_2 (Z and Gamma nodes);
+        one column per unknown coefficient."""
+        blocks = []
+        for l, sd in enumerate(self.sub):
+            cols = []
+            for k in range(self.ncol):
+                psi = self.column_density(l, k)
+                cols.append(sd.i_minus_p_gin(psi, self.sigma) if np.any(psi) else np.zeros(len(sd.gin_idx)))
+            blocks.append(np.stack(cols, axis=1))
+        return np.vstack(blocks)
+
+    def lstsq(self, b):
+        from scipy.linalg import solve_triangular
+        return solve_triangular(self.R, self.Q.T @ b)
+
+    def densities(self, C, neumann2=None):
+        """u on each grid boundary from the coefficients (+ d g_N on Gamma nodes)."""
+        out = []
+        for l, sd in enumerate(self.sub):
+            u = np.zeros(len(sd.gamma_idx))
+            for k in range(self.ncol):
+                u += C[k] * self.column_density(l, k)
+            if l == 1 and neumann2 is not None:
+                m = sd.surf == 0
+                u[m] += sd.d[m] * neumann2[m]
+            out.append(u)
+        return out
+
+
+def dd_elliptic_solve(setup: DDSetup, f1, f2, neumann2=None):
+    """(sigma - Lap) u = f in Omega = Omega_1 + Omega_2, du/dn = g_N on Gamma
+    (neumann2: values at the grid boundary nodes of Omega_2, used on its Gamma
+    nodes), by the coupled reduced BEPs, then Green's formula in each sub-domain.
+    Returns (u1 on N^+_1, u2 on N^+_2, C)."""
+    S1, S2 = setup.sub
+    G1 = particular_solution(f1, S1.sets, S1.h, setup.sigma)
+    G2 = particular_solution(f2, S2.sets, S2.h, setup.sigma)
+    b1 = G1.reshape(-1)[S1.gin_idx]
+    b2 = G2.reshape(-1)[S2.gin_idx]
+    if neumann2 is not None:
+        v = np.where(S2.surf == 0, S2.d * neumann2, 0.0)
+        b2 = b2 - S2.i_minus_p_gin(v, setup.sigma)
+    C = setup.lstsq(np.concatenate([b1, b2]))
+    ug1, ug2 = setup.densities(C, neumann2)
+    u1 = G1 + difference_potential(gamma_density_grid(ug1, S1.gamma_idx, S1.N), S1.sets, S1.h, setup.sigma)
+    u2 = G2 + difference_potential(gamma_density_grid(ug2, S2.gamma_idx, S2.N), S2.sets, S2.h, setup.sigma)
+    return u1, u2, C
+
+
+# ---------------------------------------------------------------------------
 # PKS discretisation (eqs. discrete_chemotaxis .. slope_limiter, cfl_condition)
 # ---------------------------------------------------------------------------
 def minmod(*xs):
@@ -561,3 +712,69 @@ class PKSState:
         self.rho, self.c = out
         self.t += dt
         return dt
+
+
+class DDPKSState:
+    """Oracle of the time loop (Steps 3-7) on the two sub-domains of Case 1:
+    each sub-domain keeps rho and c on its own grid; Step 3's dt is the
+    smaller CFL bound of the two grids (and dt_max, and dt_prev); the coupled
+    BEP is rebuilt whenever dt changes (Step 4b); every solve stacks the
+    particular-solution traces of both sub-domains into one least squares."""
+
+    def __init__(self, center, r1, r2, N1, lo1, hi1, N2, lo2, hi2, KZ, KG, chi, dt_max, rho0, c0,
+                 dt_mode="cfl", clamp=True):
+        self.args = (center, r1, r2, N1, lo1, hi1, N2, lo2, hi2, KZ, KG)
+        self.chi, self.dt_max, self.dt_mode, self.clamp = chi, dt_max, dt_mode, clamp
+        base = DDSetup(*self.args, 1.0 / dt_max, build_bep=False)
+        self.sub = base.sub
+        self.setup, self.dt, self.t = None, None, 0.0
+        self.rho, self.c = [], []
+        for sd in self.sub:
+            X, Y, Z = mesh(sd.N, sd.lo, sd.hi)
+            r = np.where(sd.sets["Mp"], rho0(X, Y, Z), 0.0)
+            c = np.where(sd.sets["Mp"], c0(X, Y, Z), 0.0)
+            ex = sd.labels.reshape(-1)[sd.gamma_idx] & LBL_GEX > 0
+            xf = sd.xf[ex]
+            r.reshape(-1)[sd.gamma_idx[ex]] = rho0(xf[:, 0], xf[:, 1], xf[:, 2])
+            c.reshape(-1)[sd.gamma_idx[ex]] = c0(xf[:, 0], xf[:, 1], xf[:, 2])
+            self.rho.append(r)
+            self.c.append(c)
+
+    def choose_dt(self):
+        if self.dt_mode == "fixed":
+            return self.dt_max
+        cand = min([self.dt_max] + [cfl_dt(c, sd.sets, sd.h, self.chi) for c, sd in zip(self.c, self.sub)])
+        return cand if self.dt is None else min(self.dt, cand)
+
+    def step(self):
+        dt = self.choose_dt()
+        if self.setup is None or dt != self.dt:
+            self.setup = DDSetup(*self.args, 1.0 / dt)
+        self.dt = dt
+        S = self.setup
+        rhs = [pks_rhs(r, c, sd.sets, sd.h, self.chi, dt) for r, c, sd in zip(self.rho, self.c, S.sub)]
+        new = []
+        for f in range(2):  # rho, c
+            G = [particular_solution(rhs[l][f] / dt, sd.sets, sd.h, S.sigma) for l, sd in enumerate(S.sub)]
+            b = np.concatenate([G[l].reshape(-1)[sd.gin_idx] for l, sd in enumerate(S.sub)])
+            C = S.lstsq(b)
+            dens = S.densities(C)
+            out = []
+            for l, sd in enumerate(S.sub):
+                ug = np.maximum(dens[l], 0.0) if self.clamp else dens[l]
+                out.append(G[l] + difference_potential(gamma_density_grid(ug, sd.gamma_idx, sd.N),
+                                                       sd.sets, sd.h, S.sigma))
+            new.append(out)
+        self.rho, self.c = new
+        self.t += dt
+        return dt
+
+    def diagnostics(self):
+        """diagnostics() of each sub-domain combined: sums of mass, second moment
+        and free energy; max / min over both."""
+        parts = [diagnostics(r, c, sd.sets, sd.h, sd.N, sd.lo, sd.hi)
+                 for r, c, sd in zip(self.rho, self.c, self.sub)]
+        return dict(mass=sum(p["mass"] for p in parts), max_rho=max(p["max_rho"] for p in parts),
+                    min_rho=min(p["min_rho"] for p in parts), min_c=min(p["min_c"] for p in parts),
+                    m2=sum(p["m2"] for p in parts), free_energy=sum(p["free_energy"] for p in parts))
+
