@@ -66,7 +66,9 @@ typedef struct dpm_bep dpm_bep;
 typedef struct dpm_pks dpm_pks;
 
 /* Domain Omega.  kind 0: sphere |x - center| < axes[0] (axes[1], axes[2]
- * ignored); kind 1: ellipsoid sum ((x_i - center_i)/axes_i)^2 < 1.
+ * ignored); kind 1: ellipsoid sum ((x_i - center_i)/axes_i)^2 < 1; kind 2:
+ * spherical shell axes[1] < |x - center| < axes[0] (the sub-domain of the
+ * domain decomposition; the forms of both spheres are tested as below).
  * Membership is decided in IEEE double with the fixed order
  * ((tx*tx + ty*ty) + tz*tz) < 1, t_i = (x_i - c_i)/a_i, so that the integer
  * point sets are reproducible bit for bit. */
@@ -309,6 +311,79 @@ int64_t dpm_launch_count(void);
 int dpm_profile_enable(int on);
 int dpm_profile_read(const char *name, double *total_ms, int64_t *launches);
 int dpm_profile_reset(void);
+
+/* ---- domain decomposition, Case 1 (Section 3) ---------------------------------
+ * Omega_1 = ball |x - center| < r1 on an N1^3 grid of [lo1, hi1]^3, Omega_2 =
+ * shell r1 < |x - center| < r2 on an N2^3 grid of [lo2, hi2]^3 (classified as
+ * dpm_geom kind 2 with axes = (r2, r1, -); its grid boundary splits into the
+ * nodes whose foot point lies on the interface Z (|x - c| = r1) and those on
+ * Gamma (|x - c| = r2)).  Unknowns: three real spherical-harmonic series of
+ * degree KZ on Z -- u, du/dnu, d2u/dnu2 with nu = (x - c)/|x - c| -- shared by
+ * both sub-domains (the interface conditions, eq. interface_condition), and
+ * two of degree KG on Gamma -- u, d2u/dn2 (du/dn is the Neumann data).  The
+ * reduced BEPs of both sub-domains (eqs. reduced_DD1_BEP1, reduced_DD1_BEP2)
+ * are stacked (rows: gamma_in of Omega_1, then of Omega_2; columns: the Z
+ * coefficients (3 (KZ+1)^2, term-major) then the Gamma ones (2 (KG+1)^2)) and
+ * solved in the least-squares sense; each sub-domain then applies Green's
+ * formula on its own grid.  precision applies per sub-domain; DPM_PREC_TC32
+ * falls back to DPM_PREC_FP32 on a grid whose N has no tensor-core solver. */
+typedef struct dpm_dd dpm_dd;
+typedef struct dpm_dd_pks dpm_dd_pks;
+
+typedef struct {
+    double center[3];
+    double r1, r2;        /* interface and outer radius, 0 < r1 < r2 */
+    int N1;
+    double lo1, hi1;      /* grid of the ball */
+    int N2;
+    double lo2, hi2;      /* grid of the shell */
+    int KZ, KG;           /* harmonic degrees on Z and Gamma, 0..16 */
+    int precision;
+} dpm_dd_params;
+
+typedef struct {
+    int N[2];
+    double h[2];
+    int precision[2];
+    int64_t n_mplus[2], n_gin[2], n_gamma[2];
+    int nz, ng, ncol;
+    double sigma;
+} dpm_dd_info;
+
+/* Steps 1-2 for both sub-domains at shift sigma (synchronises). */
+int dpm_dd_build(dpm_ctx *ctx, const dpm_dd_params *params, double sigma, dpm_dd **out,
+                 cudaStream_t stream);
+int dpm_dd_get_info(const dpm_dd *dd, dpm_dd_info *info);
+/* The stacked BEP matrix: device double[(n_gin[0] + n_gin[1]) * ncol], column-major. */
+int dpm_dd_matrix(dpm_dd *dd, double *A, cudaStream_t stream);
+/*
+ * (sigma - Lap) u = f on Omega_1 + Omega_2 with du/dn = g_N on Gamma: f1 / f2
+ * device [N1^3] / [N2^3] (float, or double for DPM_PREC_FP64) used on M^+ of
+ * each sub-domain; neumann2 device double[n_gamma[1]] (values at the grid
+ * boundary nodes of the shell, in ascending node order; only its Gamma nodes
+ * are read) or NULL for zero; u1 / u2 device outputs valid on N^+ of each
+ * sub-domain (zero elsewhere); coeffs device double[ncol] or NULL.
+ */
+int dpm_dd_solve(dpm_dd *dd, const void *f1, const void *f2, const double *neumann2, void *u1,
+                 void *u2, double *coeffs, cudaStream_t stream);
+int dpm_dd_destroy(dpm_dd *dd);
+
+/*
+ * PKS time stepping on the two sub-domains (Steps 3-7 with the coupled BEP;
+ * zero Neumann data on Gamma): dt = min(dt_max, the CFL bounds of both grids,
+ * dt_prev) in dt_mode 1 (dt_max in dt_mode 0); the stacked BEP is rebuilt
+ * when dt decreases or on every step with rebuild = 1; clamp: u_gamma >= 0.
+ * rho0/c0 set the state on M^+ of each sub-domain and at the foot points of its
+ * exterior grid-boundary nodes.  Statistics combine both sub-domains (sums of
+ * mass, second moment and free energy; max / min over both).
+ */
+int dpm_dd_pks_create(dpm_ctx *ctx, const dpm_dd_params *params, double chi, double dt_max,
+                      int dt_mode, int rebuild, int clamp, const dpm_gaussian *rho0,
+                      const dpm_gaussian *c0, dpm_dd_pks **out, cudaStream_t stream);
+int dpm_dd_pks_step(dpm_dd_pks *pks, int nsteps, dpm_pks_stats *stats, cudaStream_t stream);
+/* State of sub-domain l (0: ball, 1: shell) into device [N_l^3] arrays. */
+int dpm_dd_pks_get_state(dpm_dd_pks *pks, int l, void *rho, void *c, cudaStream_t stream);
+int dpm_dd_pks_destroy(dpm_dd_pks *pks);
 
 #ifdef __cplusplus
 }

@@ -58,6 +58,19 @@ class dpm_pks_stats(C.Structure):
                 ("min_c", C.c_double), ("m2", C.c_double), ("free_energy", C.c_double)]
 
 
+class dpm_dd_params(C.Structure):
+    _fields_ = [("center", C.c_double * 3), ("r1", C.c_double), ("r2", C.c_double),
+                ("N1", C.c_int), ("lo1", C.c_double), ("hi1", C.c_double),
+                ("N2", C.c_int), ("lo2", C.c_double), ("hi2", C.c_double),
+                ("KZ", C.c_int), ("KG", C.c_int), ("precision", C.c_int)]
+
+
+class dpm_dd_info(C.Structure):
+    _fields_ = [("N", C.c_int * 2), ("h", C.c_double * 2), ("precision", C.c_int * 2),
+                ("n_mplus", C.c_int64 * 2), ("n_gin", C.c_int64 * 2), ("n_gamma", C.c_int64 * 2),
+                ("nz", C.c_int), ("ng", C.c_int), ("ncol", C.c_int), ("sigma", C.c_double)]
+
+
 _P = C.c_void_p
 _SIGS = {
     "dpm_last_error": (C.c_char_p, []),
@@ -88,6 +101,17 @@ _SIGS = {
     "dpm_pks_destroy": (C.c_int, [_P]),
     "dpm_aux_solve_batched_noalloc": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, _P,
                                                 _P, _P]),
+    "dpm_dd_build": (C.c_int, [_P, C.POINTER(dpm_dd_params), C.c_double, C.POINTER(C.c_void_p), _P]),
+    "dpm_dd_get_info": (C.c_int, [_P, C.POINTER(dpm_dd_info)]),
+    "dpm_dd_matrix": (C.c_int, [_P, _P, _P]),
+    "dpm_dd_solve": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "dpm_dd_destroy": (C.c_int, [_P]),
+    "dpm_dd_pks_create": (C.c_int, [_P, C.POINTER(dpm_dd_params), C.c_double, C.c_double, C.c_int,
+                                    C.c_int, C.c_int, C.POINTER(dpm_gaussian), C.POINTER(dpm_gaussian),
+                                    C.POINTER(C.c_void_p), _P]),
+    "dpm_dd_pks_step": (C.c_int, [_P, C.c_int, C.POINTER(dpm_pks_stats), _P]),
+    "dpm_dd_pks_get_state": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "dpm_dd_pks_destroy": (C.c_int, [_P]),
     "dpm_launch_count": (C.c_int64, []),
     "dpm_profile_enable": (C.c_int, [C.c_int]),
     "dpm_profile_read": (C.c_int, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
@@ -292,6 +316,63 @@ def pks_params(geom, N, lo, hi, chi, dt_max, K, beta=1, precision=DPM_PREC_FP32,
     p.N, p.lo, p.hi, p.chi, p.dt_max = N, lo, hi, chi, dt_max
     p.K, p.beta, p.precision, p.dt_mode, p.rebuild, p.clamp = K, beta, precision, dt_mode, rebuild, clamp
     return p
+
+
+def dd_params(center, r1, r2, N1, lo1, hi1, N2, lo2, hi2, KZ, KG, precision=DPM_PREC_FP32) -> dpm_dd_params:
+    p = dpm_dd_params()
+    for t in range(3):
+        p.center[t] = center[t]
+    p.r1, p.r2, p.N1, p.lo1, p.hi1, p.N2, p.lo2, p.hi2 = r1, r2, N1, lo1, hi1, N2, lo2, hi2
+    p.KZ, p.KG, p.precision = KZ, KG, precision
+    return p
+
+
+def dpm_dd_build(ctx, params: dpm_dd_params, sigma, stream=None):
+    h = C.c_void_p()
+    _check(lib().dpm_dd_build(ctx, C.byref(params), sigma, C.byref(h), _stream(stream)))
+    return h
+
+
+def dpm_dd_get_info(dd) -> dpm_dd_info:
+    info = dpm_dd_info()
+    _check(lib().dpm_dd_get_info(dd, C.byref(info)))
+    return info
+
+
+def dpm_dd_matrix(dd, A, stream=None):
+    _check(lib().dpm_dd_matrix(dd, _ptr(A), _stream(stream)))
+
+
+def dpm_dd_solve(dd, f1, f2, u1, u2, neumann2=None, coeffs=None, stream=None):
+    _check(lib().dpm_dd_solve(dd, _ptr(f1), _ptr(f2), _ptr(neumann2), _ptr(u1), _ptr(u2), _ptr(coeffs),
+                              _stream(stream)))
+
+
+def dpm_dd_destroy(dd):
+    _check(lib().dpm_dd_destroy(dd))
+
+
+def dpm_dd_pks_create(ctx, params: dpm_dd_params, chi, dt_max, dt_mode, rebuild, clamp, rho0, c0,
+                      stream=None):
+    h = C.c_void_p()
+    g0, g1 = make_gaussian(rho0), make_gaussian(c0)
+    _check(lib().dpm_dd_pks_create(ctx, C.byref(params), chi, dt_max, dt_mode, rebuild, clamp, C.byref(g0),
+                                   C.byref(g1), C.byref(h), _stream(stream)))
+    return h
+
+
+def dpm_dd_pks_step(pks, nsteps=1, want_stats=True, stream=None):
+    st = dpm_pks_stats()
+    _check(lib().dpm_dd_pks_step(pks, nsteps, C.byref(st) if want_stats else None, _stream(stream)))
+    return st if want_stats else None
+
+
+def dpm_dd_pks_get_state(pks, l, rho, c, stream=None):
+    _check(lib().dpm_dd_pks_get_state(pks, l, _ptr(rho), _ptr(c), _stream(stream)))
+
+
+def dpm_dd_pks_destroy(pks):
+    _check(lib().dpm_dd_pks_destroy(pks))
 
 
 def dpm_launch_count() -> int:

@@ -962,3 +962,418 @@ extern "C" int dpm_pks_destroy(dpm_pks *k) {
     delete k;
     return DPM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Domain decomposition, Case 1 (Section 3): Omega_1 = ball |x - c| < r1 on its
+// own grid, Omega_2 = shell r1 < |x - c| < r2 on another; the series on Z are
+// shared by both sub-domains (interface conditions), the Gamma series belong to
+// Omega_2, and the reduced BEPs of both (eqs. reduced_DD1_BEP1,
+// reduced_DD1_BEP2) are stacked into one least-squares problem.
+// ---------------------------------------------------------------------------
+namespace {
+struct DDSub {
+    int N = 0, prec = 0, ncol_l = 0;
+    double lo = 0, hi = 0;
+    dpm_geom geom{};
+    GridIndex gi;
+    GammaGeom gg;
+    DevBuf surf, psi, psi_in, trace, dens, work, desc;
+    DevBuf rho, c, frho, fc, gmax, diag_part, diag_out;  // time-loop state
+};
+}  // namespace
+
+struct dpm_dd {
+    dpm_ctx *ctx = nullptr;
+    dpm_dd_params prm{};
+    DDSub sub[2];
+    int nz = 0, ng = 0, ncol = 0, storage = 0;  // storage: DPM_PREC_FP64 (double) or float
+    double sigma = 0;
+    bool factored = false;
+    LsqFactor lsq;
+    DevBuf coef, bvec;
+};
+
+struct dpm_dd_pks {
+    dpm_dd dd;
+    double chi = 0, dt_max = 0;
+    int dt_mode = 0, rebuild = 0, clamp = 1;
+    double t = 0, dt_prev = 0;
+    int64_t step = 0;
+    int last_rebuilt = 0;
+};
+
+namespace {
+
+int dd_sub_prec(int requested, int N) {
+    if (requested == DPM_PREC_TC32) return tc_supported(N) ? DPM_PREC_TC32 : DPM_PREC_FP32;
+    return requested;
+}
+
+ApParams dd_params(const DDSub &sd, double sigma) {
+    ApParams p;
+    p.N = sd.N;
+    p.h = sd.gi.h;
+    p.sigma = sigma;
+    ap_params_from_index(p, sd.gi);
+    return p;
+}
+
+template <class T> int dd_init(dpm_dd *d, dpm_ctx *ctx, const dpm_dd_params &P, cudaStream_t s) {
+    d->ctx = ctx;
+    d->prm = P;
+    d->storage = P.precision == DPM_PREC_FP64 ? DPM_PREC_FP64 : DPM_PREC_FP32;
+    d->nz = (P.KZ + 1) * (P.KZ + 1);
+    d->ng = (P.KG + 1) * (P.KG + 1);
+    d->ncol = 3 * d->nz + 2 * d->ng;
+    for (int l = 0; l < 2; ++l) {
+        DDSub &sd = d->sub[l];
+        sd.geom.kind = l == 0 ? 0 : 2;
+        for (int t = 0; t < 3; ++t) sd.geom.center[t] = P.center[t];
+        sd.geom.axes[0] = l == 0 ? P.r1 : P.r2;
+        sd.geom.axes[1] = l == 0 ? P.r1 : P.r1;
+        sd.geom.axes[2] = l == 0 ? P.r1 : 0.0;
+        sd.N = l == 0 ? P.N1 : P.N2;
+        sd.lo = l == 0 ? P.lo1 : P.lo2;
+        sd.hi = l == 0 ? P.hi1 : P.hi2;
+        sd.prec = dd_sub_prec(P.precision, sd.N);
+        DPM_RET(build_grid_index(sd.geom, sd.N, sd.lo, sd.hi, sd.gi, s));
+        const int K = l == 0 ? P.KZ : std::max(P.KZ, P.KG);
+        DPM_RET(build_gamma_geom(sd.geom, sd.gi, K, sd.gg, s));
+        const int64_t n = sd.gi.n_gamma, m = sd.gi.n_gin;
+        DPM_RET(sd.surf.alloc(std::max<int64_t>(n, 1)));
+        DPM_RET(dd_surface_flags(n, sd.gg.foot.as<double>(), P.center, l == 0 ? 2.0 * P.r1 : 0.5 * (P.r1 + P.r2),
+                                 sd.surf.as<uint8_t>(), s));
+        sd.ncol_l = l == 0 ? 3 * d->nz : d->ncol;
+        DPM_RET(sd.psi.alloc(sizeof(T) * sd.ncol_l * n));
+        DPM_RET(sd.psi_in.alloc(sizeof(double) * sd.ncol_l * m));
+        DPM_RET(dd_columns<T>(n, m, sd.gg.nsh, d->nz, d->ng, sd.ncol_l, sd.gg.phi.as<double>(),
+                              sd.gg.dist.as<double>(), sd.surf.as<uint8_t>(), sd.gi.gin_pos.as<int>(),
+                              sd.psi.as<T>(), sd.psi_in.as<double>(), s));
+        DPM_RET(sd.trace.alloc(sizeof(T) * (sd.ncol_l + 4) * m));
+        DPM_RET(sd.dens.alloc(sizeof(T) * 4 * n));
+    }
+    const int64_t m = d->sub[0].gi.n_gin + d->sub[1].gi.n_gin;
+    if (m < d->ncol) {
+        set_error("%lld BEP rows for %d unknowns: refine the grids or lower KZ/KG", (long long)m, d->ncol);
+        return DPM_EINVAL;
+    }
+    d->lsq.m = (int)m;
+    d->lsq.n = d->ncol;
+    DPM_RET(d->lsq.A.alloc(sizeof(double) * m * d->ncol));
+    DPM_RET(d->coef.alloc(sizeof(double) * 4 * d->ncol));
+    DPM_RET(d->bvec.alloc(sizeof(T) * 4 * m));
+    return DPM_OK;
+}
+
+// Batched solves of every column density of both sub-domains (plus `extra`
+// right-hand sides per sub-domain in the same batches), the stacked BEP and
+// its factorisation.
+template <class T>
+int dd_build_bep(dpm_dd *d, double sigma, const std::vector<ApRhs<T>> *extra, double fscale,
+                 cudaStream_t s) {
+    for (int l = 0; l < 2; ++l) {
+        DDSub &sd = d->sub[l];
+        const int64_t n = sd.gi.n_gamma, m = sd.gi.n_gin;
+        std::vector<ApRhs<T>> rhs;
+        for (int k = 0; k < sd.ncol_l; ++k)
+            rhs.push_back({nullptr, sd.psi.as<T>() + k * n, nullptr, sd.trace.as<T>() + k * m, 0, 0});
+        if (extra)
+            for (auto &e : extra[l]) rhs.push_back(e);
+        ApParams p = dd_params(sd, sigma);
+        p.fscale = fscale;
+        DPM_RET(run_ap<T>(sd.prec, p, rhs, sd.work, sd.desc, s));
+    }
+    DPM_RET(dd_assemble<T>(d->sub[0].gi.n_gin, d->sub[1].gi.n_gin, 3 * d->nz, d->ncol,
+                           d->sub[0].psi_in.as<double>(), d->sub[0].trace.as<T>(),
+                           d->sub[1].psi_in.as<double>(), d->sub[1].trace.as<T>(), d->lsq.A.as<double>(), s));
+    DPM_RET(lsq_factor(d->lsq, nullptr, s));
+    d->sigma = sigma;
+    d->factored = true;
+    return DPM_OK;
+}
+
+template <class T>
+int dd_solve(dpm_dd *d, const void *f1v, const void *f2v, const double *gn, void *u1v, void *u2v,
+             double *coeffs, cudaStream_t s) {
+    DDSub &a = d->sub[0], &b = d->sub[1];
+    const int64_t m1 = a.gi.n_gin, m2 = b.gi.n_gin, n1 = a.gi.n_gamma, n2 = b.gi.n_gamma;
+    const T *f[2] = {static_cast<const T *>(f1v), static_cast<const T *>(f2v)};
+    T *u[2] = {static_cast<T *>(u1v), static_cast<T *>(u2v)};
+    T *tr1 = a.trace.as<T>() + (int64_t)a.ncol_l * m1;
+    T *tr2 = b.trace.as<T>() + (int64_t)b.ncol_l * m2, *trv = tr2 + m2;
+    T *v = b.dens.as<T>() + n2;
+    if (gn) DPM_RET(dd_neumann_density<T>(n2, b.gg.dist.as<double>(), b.surf.as<uint8_t>(), gn, v, s));
+    {
+        std::vector<ApRhs<T>> r1 = {{f[0], nullptr, nullptr, tr1, 0, 0}};
+        DPM_RET(run_ap<T>(a.prec, dd_params(a, d->sigma), r1, a.work, a.desc, s));
+        std::vector<ApRhs<T>> r2 = {{f[1], nullptr, nullptr, tr2, 0, 0}};
+        if (gn) r2.push_back({nullptr, v, nullptr, trv, 0, 0});
+        DPM_RET(run_ap<T>(b.prec, dd_params(b, d->sigma), r2, b.work, b.desc, s));
+    }
+    T *bv = d->bvec.as<T>();
+    DPM_RET(dd_rhs<T>(m1, m2, tr1, tr2, gn ? v : nullptr, b.gi.gin_pos.as<int>(), trv, bv, s));
+    double *C = d->coef.as<double>();
+    DPM_RET(lsq_apply<T>(d->lsq, bv, (int)(m1 + m2), C, 1, s));
+    for (int l = 0; l < 2; ++l) {
+        DDSub &sd = d->sub[l];
+        T *dn = sd.dens.as<T>();
+        DPM_RET(dd_extend<T>(sd.gi.n_gamma, sd.gg.nsh, d->nz, d->ng, sd.gg.phi.as<double>(),
+                             sd.gg.dist.as<double>(), sd.surf.as<uint8_t>(), C, d->ncol,
+                             l == 1 ? gn : nullptr, dn, (int)sd.gi.n_gamma, 1, 0, s));
+        std::vector<ApRhs<T>> g = {{f[l], dn, u[l], nullptr, 0, 0}};
+        DPM_RET(run_ap<T>(sd.prec, dd_params(sd, d->sigma), g, sd.work, sd.desc, s));
+    }
+    (void)n1;
+    if (coeffs) DPM_CUDA(cudaMemcpyAsync(coeffs, C, sizeof(double) * d->ncol, cudaMemcpyDeviceToDevice, s));
+    return DPM_OK;
+}
+
+int dd_check(const dpm_dd_params *P) {
+    if (!P) { set_error("params is NULL"); return DPM_EINVAL; }
+    if (!(P->r1 > 0 && P->r2 > P->r1)) { set_error("need 0 < r1 < r2"); return DPM_EINVAL; }
+    if (P->KZ < 0 || P->KG < 0 || P->KZ > 16 || P->KG > 16) { set_error("KZ, KG in [0, 16]"); return DPM_EINVAL; }
+    if (!prec_ok(P->precision)) { set_error("unknown precision %d", P->precision); return DPM_EINVAL; }
+    if (P->N1 > 256 || P->N2 > 256) { set_error("N1, N2 <= 256"); return DPM_EINVAL; }
+    return DPM_OK;
+}
+
+}  // namespace
+
+extern "C" int dpm_dd_build(dpm_ctx *ctx, const dpm_dd_params *P, double sigma, dpm_dd **out,
+                            cudaStream_t s) {
+    if (!ctx || !out) { set_error("ctx/out is NULL"); return DPM_EINVAL; }
+    *out = nullptr;
+    DPM_RET(dd_check(P));
+    if (!(sigma >= 0)) { set_error("sigma must be >= 0"); return DPM_EINVAL; }
+    DPM_CUDA(cudaSetDevice(ctx->device));
+    dpm_dd *d = new (std::nothrow) dpm_dd();
+    if (!d) { set_error("out of host memory"); return DPM_ENOMEM; }
+    int r;
+    if (P->precision == DPM_PREC_FP64) {
+        r = dd_init<double>(d, ctx, *P, s);
+        if (r == DPM_OK) r = dd_build_bep<double>(d, sigma, nullptr, 1.0, s);
+    } else {
+        r = dd_init<float>(d, ctx, *P, s);
+        if (r == DPM_OK) r = dd_build_bep<float>(d, sigma, nullptr, 1.0, s);
+    }
+    if (r != DPM_OK) { delete d; return r; }
+    *out = d;
+    return DPM_OK;
+}
+
+extern "C" int dpm_dd_get_info(const dpm_dd *d, dpm_dd_info *info) {
+    if (!d || !info) { set_error("dd/info is NULL"); return DPM_EINVAL; }
+    for (int l = 0; l < 2; ++l) {
+        info->N[l] = d->sub[l].N;
+        info->h[l] = d->sub[l].gi.h;
+        info->precision[l] = d->sub[l].prec;
+        info->n_mplus[l] = d->sub[l].gi.n_mplus;
+        info->n_gin[l] = d->sub[l].gi.n_gin;
+        info->n_gamma[l] = d->sub[l].gi.n_gamma;
+    }
+    info->nz = d->nz;
+    info->ng = d->ng;
+    info->ncol = d->ncol;
+    info->sigma = d->sigma;
+    return DPM_OK;
+}
+
+extern "C" int dpm_dd_matrix(dpm_dd *d, double *A, cudaStream_t s) {
+    if (!d || !A) { set_error("dd/A is NULL"); return DPM_EINVAL; }
+    DPM_CUDA(cudaMemcpyAsync(A, d->lsq.A.p, sizeof(double) * (size_t)d->lsq.m * d->ncol,
+                             cudaMemcpyDeviceToDevice, s));
+    return DPM_OK;
+}
+
+extern "C" int dpm_dd_solve(dpm_dd *d, const void *f1, const void *f2, const double *neumann2,
+                            void *u1, void *u2, double *coeffs, cudaStream_t s) {
+    if (!d || !f1 || !f2 || !u1 || !u2) { set_error("dd/f/u is NULL"); return DPM_EINVAL; }
+    if (d->storage == DPM_PREC_FP64) return dd_solve<double>(d, f1, f2, neumann2, u1, u2, coeffs, s);
+    return dd_solve<float>(d, f1, f2, neumann2, u1, u2, coeffs, s);
+}
+
+extern "C" int dpm_dd_destroy(dpm_dd *d) {
+    delete d;
+    return DPM_OK;
+}
+
+// ---- time loop on the two sub-domains ------------------------------------------------
+namespace {
+
+template <class T> int dd_pks_alloc(dpm_dd_pks *k, const dpm_gaussian &g0, const dpm_gaussian &g1,
+                                    cudaStream_t s) {
+    for (int l = 0; l < 2; ++l) {
+        DDSub &sd = k->dd.sub[l];
+        const size_t n3 = (size_t)sd.N * sd.N * sd.N;
+        DPM_RET(sd.rho.alloc(sizeof(T) * n3));
+        DPM_RET(sd.c.alloc(sizeof(T) * n3));
+        DPM_RET(sd.frho.alloc(sizeof(T) * n3));
+        DPM_RET(sd.fc.alloc(sizeof(T) * n3));
+        DPM_RET(sd.gmax.alloc(sizeof(unsigned int) * 4));
+        DPM_RET(sd.diag_part.alloc(sizeof(double) * 6 * pks_diag_blocks(sd.N)));
+        DPM_RET(sd.diag_out.alloc(sizeof(double) * 8));
+        DPM_CUDA(cudaMemsetAsync(sd.diag_out.p, 0, sizeof(double) * 8, s));
+        DPM_RET(pks_init<T>(sd.gi, sd.gg, g0, g1, sd.rho.as<T>(), sd.c.as<T>(), s));
+    }
+    return DPM_OK;
+}
+
+// Steps 3-7 on both sub-domains: dt from the smaller CFL bound of the two grids,
+// the stacked BEP rebuilt when dt decreases (or always with rebuild = 1), one
+// least squares for the particular traces of both, extensions and Green's
+// formula per sub-domain.
+template <class T> int dd_pks_step(dpm_dd_pks *k, cudaStream_t s) {
+    dpm_dd *d = &k->dd;
+    double dt = k->dt_max;
+    if (k->dt_mode == 1) {
+        for (int l = 0; l < 2; ++l) {
+            DDSub &sd = d->sub[l];
+            DPM_RET(pks_cfl<T>(sd.N, sd.gi.labels.as<uint8_t>(), sd.c.as<T>(), sd.gmax.as<unsigned int>(), s));
+        }
+        unsigned int gm[2][3];
+        for (int l = 0; l < 2; ++l)
+            DPM_CUDA(cudaMemcpyAsync(gm[l], d->sub[l].gmax.p, sizeof(gm[l]), cudaMemcpyDeviceToHost, s));
+        DPM_CUDA(cudaStreamSynchronize(s));
+        for (int l = 0; l < 2; ++l) {
+            const double h = d->sub[l].gi.h;
+            for (int ax = 0; ax < 3; ++ax) {
+                float g;
+                memcpy(&g, &gm[l][ax], sizeof(g));
+                const double gmaxv = (double)g / h;
+                if (gmaxv > 0) dt = std::min(dt, h / (6.0 * k->chi * gmaxv));
+            }
+        }
+        if (k->step > 0) dt = std::min(dt, k->dt_prev);
+    }
+    if (!(dt > 0) || !std::isfinite(dt)) { set_error("time step is not positive/finite (dt=%g)", dt); return DPM_ENUMERIC; }
+    const bool rebuild = !d->factored || k->rebuild || dt < k->dt_prev;
+    const double sigma = 1.0 / dt;
+    std::vector<ApRhs<T>> part[2];
+    T *trp[2];
+    for (int l = 0; l < 2; ++l) {
+        DDSub &sd = d->sub[l];
+        const int64_t m = sd.gi.n_gin;
+        DPM_RET(pks_flux<T>(sd.N, sd.gi.h, k->chi, dt, nullptr, sd.gi.labels.as<uint8_t>(), sd.rho.as<T>(),
+                            sd.c.as<T>(), sd.frho.as<T>(), sd.fc.as<T>(), s));
+        trp[l] = sd.trace.as<T>() + (int64_t)sd.ncol_l * m;
+        part[l] = {{sd.frho.as<T>(), nullptr, nullptr, trp[l], 0, 0},
+                   {sd.fc.as<T>(), nullptr, nullptr, trp[l] + m, 0, 0}};
+    }
+    if (rebuild) {
+        DPM_RET(dd_build_bep<T>(d, sigma, part, sigma, s));
+    } else {
+        for (int l = 0; l < 2; ++l) {
+            ApParams p = dd_params(d->sub[l], sigma);
+            p.fscale = sigma;  // L_{h,dt} u = f  <=>  (1/dt - Lap_h) u = f/dt
+            DPM_RET(run_ap<T>(d->sub[l].prec, p, part[l], d->sub[l].work, d->sub[l].desc, s));
+        }
+    }
+    const int64_t m1 = d->sub[0].gi.n_gin, m2 = d->sub[1].gi.n_gin, m = m1 + m2;
+    T *bv = d->bvec.as<T>();
+    for (int f = 0; f < 2; ++f)
+        DPM_RET(dd_rhs<T>(m1, m2, trp[0] + f * m1, trp[1] + f * m2, nullptr, nullptr, nullptr, bv + f * m, s));
+    double *C = d->coef.as<double>();
+    DPM_RET(lsq_apply<T>(d->lsq, bv, (int)m, C, 2, s));
+    for (int l = 0; l < 2; ++l) {
+        DDSub &sd = d->sub[l];
+        const int64_t n = sd.gi.n_gamma;
+        T *dn = sd.dens.as<T>();
+        DPM_RET(dd_extend<T>(n, sd.gg.nsh, d->nz, d->ng, sd.gg.phi.as<double>(), sd.gg.dist.as<double>(),
+                             sd.surf.as<uint8_t>(), C, d->ncol, nullptr, dn, (int)n, 2, k->clamp, s));
+        std::vector<ApRhs<T>> g = {{sd.frho.as<T>(), dn, sd.rho.as<T>(), nullptr, 0, 0},
+                                   {sd.fc.as<T>(), dn + n, sd.c.as<T>(), nullptr, 0, 0}};
+        ApParams p = dd_params(sd, sigma);
+        p.fscale = sigma;
+        DPM_RET(run_ap<T>(sd.prec, p, g, sd.work, sd.desc, s));
+        DPM_RET(pks_diag<T>(sd.N, sd.gi.lo, sd.gi.h, sd.gi.labels.as<uint8_t>(), sd.rho.as<T>(), sd.c.as<T>(),
+                            sd.diag_part.as<double>(), sd.diag_out.as<double>(), s));
+    }
+    k->t += dt;
+    k->dt_prev = dt;
+    k->step += 1;
+    k->last_rebuilt = rebuild ? 1 : 0;
+    return DPM_OK;
+}
+
+}  // namespace
+
+extern "C" int dpm_dd_pks_create(dpm_ctx *ctx, const dpm_dd_params *P, double chi, double dt_max,
+                                 int dt_mode, int rebuild, int clamp, const dpm_gaussian *rho0,
+                                 const dpm_gaussian *c0, dpm_dd_pks **out, cudaStream_t s) {
+    if (!ctx || !out) { set_error("ctx/out is NULL"); return DPM_EINVAL; }
+    *out = nullptr;
+    DPM_RET(dd_check(P));
+    if (!(dt_max > 0) || !(chi >= 0) || (dt_mode != 0 && dt_mode != 1)) {
+        set_error("need dt_max > 0, chi >= 0, dt_mode in {0,1}");
+        return DPM_EINVAL;
+    }
+    DPM_CUDA(cudaSetDevice(ctx->device));
+    dpm_dd_pks *k = new (std::nothrow) dpm_dd_pks();
+    if (!k) { set_error("out of host memory"); return DPM_ENOMEM; }
+    k->chi = chi;
+    k->dt_max = dt_max;
+    k->dt_mode = dt_mode;
+    k->rebuild = rebuild;
+    k->clamp = clamp;
+    dpm_gaussian z{};
+    const dpm_gaussian &g0 = rho0 ? *rho0 : z, &g1 = c0 ? *c0 : z;
+    int r;
+    if (P->precision == DPM_PREC_FP64) {
+        r = dd_init<double>(&k->dd, ctx, *P, s);
+        if (r == DPM_OK) r = dd_pks_alloc<double>(k, g0, g1, s);
+    } else {
+        r = dd_init<float>(&k->dd, ctx, *P, s);
+        if (r == DPM_OK) r = dd_pks_alloc<float>(k, g0, g1, s);
+    }
+    if (r == DPM_OK) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { set_error("%s", cudaGetErrorString(e)); r = DPM_ECUDA; }
+    }
+    if (r != DPM_OK) { delete k; return r; }
+    *out = k;
+    return DPM_OK;
+}
+
+extern "C" int dpm_dd_pks_step(dpm_dd_pks *k, int nsteps, dpm_pks_stats *stats, cudaStream_t s) {
+    if (!k || nsteps < 0) { set_error("pks is NULL or nsteps < 0"); return DPM_EINVAL; }
+    for (int i = 0; i < nsteps; ++i) {
+        if (k->dd.storage == DPM_PREC_FP64) DPM_RET(dd_pks_step<double>(k, s));
+        else DPM_RET(dd_pks_step<float>(k, s));
+    }
+    if (stats) {
+        double d[2][6];
+        for (int l = 0; l < 2; ++l)
+            DPM_CUDA(cudaMemcpyAsync(d[l], k->dd.sub[l].diag_out.p, sizeof(d[l]), cudaMemcpyDeviceToHost, s));
+        DPM_CUDA(cudaStreamSynchronize(s));
+        stats->t = k->t;
+        stats->dt = k->dt_prev;
+        stats->step = k->step;
+        stats->rebuilt = k->last_rebuilt;
+        stats->mass = d[0][0] + d[1][0];
+        stats->max_rho = std::max(d[0][1], d[1][1]);
+        stats->min_rho = std::min(d[0][2], d[1][2]);
+        stats->min_c = std::min(d[0][3], d[1][3]);
+        stats->m2 = d[0][4] + d[1][4];
+        stats->free_energy = d[0][5] + d[1][5];
+        if (k->dd.prm.precision == DPM_PREC_TC32) DPM_RET(tc_status_check());
+        if (!std::isfinite(stats->mass) || !std::isfinite(stats->free_energy)) {
+            set_error("PKS state became non-finite at step %lld", (long long)k->step);
+            return DPM_ENUMERIC;
+        }
+    }
+    return DPM_OK;
+}
+
+extern "C" int dpm_dd_pks_get_state(dpm_dd_pks *k, int l, void *rho, void *c, cudaStream_t s) {
+    if (!k || l < 0 || l > 1) { set_error("pks is NULL or sub-domain index not 0/1"); return DPM_EINVAL; }
+    const DDSub &sd = k->dd.sub[l];
+    const size_t n3 = (size_t)sd.N * sd.N * sd.N * elem_size(k->dd.storage);
+    if (rho) DPM_CUDA(cudaMemcpyAsync(rho, sd.rho.p, n3, cudaMemcpyDeviceToDevice, s));
+    if (c) DPM_CUDA(cudaMemcpyAsync(c, sd.c.p, n3, cudaMemcpyDeviceToDevice, s));
+    return DPM_OK;
+}
+
+extern "C" int dpm_dd_pks_destroy(dpm_dd_pks *k) {
+    delete k;
+    return DPM_OK;
+}

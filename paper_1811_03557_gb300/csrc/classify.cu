@@ -21,8 +21,10 @@ constexpr int kThreads = 256;
 constexpr int kChunk = 4096;  // nodes per compaction block
 constexpr int kLists = 5;     // M+, gamma_in, gamma_ex, gamma, shell
 
+// kind 2 (spherical shell): inside iff the form of the outer sphere (radius ax)
+// is < 1 and that of the inner sphere (radius r_in) is > 1.
 __global__ void k_inside(int N, double lo, double h, double cx, double cy, double cz, double ax,
-                         double ay, double az, uint8_t *labels) {
+                         double ay, double az, int kind, double r_in, uint8_t *labels) {
     int64_t n3 = (int64_t)N * N * N;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n3;
          p += (int64_t)gridDim.x * blockDim.x) {
@@ -34,7 +36,15 @@ __global__ void k_inside(int N, double lo, double h, double cx, double cy, doubl
         double ty = __ddiv_rn(__dsub_rn(y, cy), ay);
         double tz = __ddiv_rn(__dsub_rn(z, cz), az);
         double s = __dadd_rn(__dadd_rn(__dmul_rn(tx, tx), __dmul_rn(ty, ty)), __dmul_rn(tz, tz));
-        labels[p] = (s < 1.0) ? (uint8_t)DPM_LBL_MPLUS : (uint8_t)0;
+        bool in = s < 1.0;
+        if (kind == 2) {
+            const double ux = __ddiv_rn(__dsub_rn(x, cx), r_in);
+            const double uy = __ddiv_rn(__dsub_rn(y, cy), r_in);
+            const double uz = __ddiv_rn(__dsub_rn(z, cz), r_in);
+            const double si = __dadd_rn(__dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy)), __dmul_rn(uz, uz));
+            in = in && si > 1.0;
+        }
+        labels[p] = in ? (uint8_t)DPM_LBL_MPLUS : (uint8_t)0;
     }
 }
 
@@ -226,10 +236,14 @@ int build_grid_index(const dpm_geom &g, int N, double lo, double hi, GridIndex &
                      cudaStream_t s) {
     if (N < 6 || N > 1024) { set_error("N=%d out of range [6,1024]", N); return DPM_EINVAL; }
     if (!(hi > lo)) { set_error("need lo < hi"); return DPM_EINVAL; }
-    if (g.kind != 0 && g.kind != 1) { set_error("geometry kind %d unknown", g.kind); return DPM_EINVAL; }
-    double ax = g.axes[0], ay = g.kind == 0 ? g.axes[0] : g.axes[1],
-           az = g.kind == 0 ? g.axes[0] : g.axes[2];
+    if (g.kind < 0 || g.kind > 2) { set_error("geometry kind %d unknown", g.kind); return DPM_EINVAL; }
+    double ax = g.axes[0], ay = g.kind == 1 ? g.axes[1] : g.axes[0],
+           az = g.kind == 1 ? g.axes[2] : g.axes[0];
     if (!(ax > 0 && ay > 0 && az > 0)) { set_error("axes must be positive"); return DPM_EINVAL; }
+    if (g.kind == 2 && !(g.axes[1] > 0 && g.axes[1] < g.axes[0])) {
+        set_error("shell radii: need 0 < inner (axes[1]) < outer (axes[0])");
+        return DPM_EINVAL;
+    }
     gi.N = N; gi.lo = lo; gi.hi = hi;
     gi.h = (hi - lo) / (double)(N + 1);
     int64_t n3 = (int64_t)N * N * N;
@@ -239,7 +253,7 @@ int build_grid_index(const dpm_geom &g, int N, double lo, double hi, GridIndex &
     DPM_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
     uint8_t *lab = gi.labels.as<uint8_t>();
     k_inside<<<grid_for(n3), kThreads, 0, s>>>(N, lo, gi.h, g.center[0], g.center[1], g.center[2],
-                                               ax, ay, az, lab);
+                                               ax, ay, az, g.kind, g.axes[1], lab);
     DPM_LAUNCHED();
     k_gamma<<<grid_for(n3), kThreads, 0, s>>>(N, lab, flag.as<int>());
     DPM_LAUNCHED();

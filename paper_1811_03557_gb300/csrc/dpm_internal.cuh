@@ -184,6 +184,29 @@ struct LsqFactor {
     DevBuf X;      // scratch of the Gram / Cholesky factorisation
     DevBuf work;   // A copy, R, solve scratch
 };
+// ---------------------------------------------------------------------------
+// Domain decomposition, Case 1 (Section 3): kernels in dd.cu
+// ---------------------------------------------------------------------------
+int dd_surface_flags(int64_t n, const double *foot, const double c[3], double r_mid, uint8_t *surf,
+                     cudaStream_t s);
+template <class T>
+int dd_columns(int64_t n, int64_t m, int nsh, int nz, int ng, int ncol_l, const double *phi,
+               const double *dist, const uint8_t *surf, const int *gin_pos, T *psi, double *psi_in,
+               cudaStream_t s);
+template <class T>
+int dd_assemble(int64_t m1, int64_t m2, int nzc, int ncol, const double *psi_in1, const T *tr1,
+                const double *psi_in2, const T *tr2, double *A, cudaStream_t s);
+template <class T>
+int dd_extend(int64_t n, int nsh, int nz, int ng, const double *phi, const double *dist,
+              const uint8_t *surf, const double *C, int ldc, const double *neumann, T *dens, int ldd,
+              int nr, int clamp, cudaStream_t s);
+template <class T>
+int dd_neumann_density(int64_t n, const double *dist, const uint8_t *surf, const double *gn, T *v,
+                       cudaStream_t s);
+template <class T>
+int dd_rhs(int64_t m1, int64_t m2, const T *tr_p1, const T *tr_p2, const T *v, const int *gin_pos2,
+           const T *tr_v2, T *b, cudaStream_t s);
+
 // Scalars of the device-resident PKS step (Step 3's dt and the time).
 struct StepScalars {
     double dt, sigma, t, dt_prev;

@@ -25,6 +25,18 @@ __constant__ double c_nlm[(kMaxK + 1) * (kMaxK + 1)];
 __device__ void project(int kind, const double c[3], const double a[3], const double p[3],
                         double xf[3], double nrm[3], double *dist) {
     double q[3] = {p[0] - c[0], p[1] - c[1], p[2] - c[2]};
+    if (kind == 2) {
+        // spherical shell (radii a[0] > a[1]): the nearer sphere; normal (p - c)/|p - c|
+        // and d = |p - c| - r on both spheres
+        double rho = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+        const double r = fabs(rho - a[0]) <= fabs(rho - a[1]) ? a[0] : a[1];
+        for (int t = 0; t < 3; ++t) {
+            nrm[t] = q[t] / rho;
+            xf[t] = c[t] + r * nrm[t];
+        }
+        *dist = rho - r;
+        return;
+    }
     if (kind == 0) {
         double rho = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
         for (int t = 0; t < 3; ++t) {
@@ -176,7 +188,7 @@ int build_gamma_geom(const dpm_geom &g, const GridIndex &gi, int K, GammaGeom &g
     DPM_RET(gg.dist.alloc(sizeof(double) * n));
     DPM_RET(gg.phi.alloc(sizeof(double) * gg.nsh * n));
     double ax = g.axes[0], ay = g.kind == 0 ? g.axes[0] : g.axes[1],
-           az = g.kind == 0 ? g.axes[0] : g.axes[2];
+           az = g.kind == 0 ? g.axes[0] : g.axes[2];  // kind 2: (r_out, r_in, -)
     int blocks = (int)((n + 127) / 128);
     k_gamma_geom<<<blocks, 128, 0, s>>>((int)n, gi.N, gi.lo, gi.h, g.kind, g.center[0], g.center[1],
                                         g.center[2], ax, ay, az, K, gi.gamma.as<int>(),

@@ -46,6 +46,10 @@ STRUCTS = {
     "dpm_bep_info": (abi.dpm_bep_info, ["N", "lo", "h", "sigma", "ncol", "n_mplus", "n_shell"]),
     "dpm_pks_params": (abi.dpm_pks_params, ["geom", "N", "lo", "chi", "dt_max", "K", "dt_mode", "clamp"]),
     "dpm_pks_stats": (abi.dpm_pks_stats, ["t", "dt", "step", "rebuilt", "mass", "free_energy"]),
+    "dpm_dd_params": (abi.dpm_dd_params, ["center", "r1", "r2", "N1", "lo1", "hi1", "N2", "lo2", "hi2",
+                                          "KZ", "KG", "precision"]),
+    "dpm_dd_info": (abi.dpm_dd_info, ["N", "h", "precision", "n_mplus", "n_gin", "n_gamma", "nz", "ng",
+                                      "ncol", "sigma"]),
 }
 
 
