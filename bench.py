@@ -288,6 +288,15 @@ def run_ours(args):
     if rank == 0 and not args.no_aux:
         aux = run_aux(abi, torch, ctx, stream)
 
+    sd_dd = None
+    if rank == 0 and not args.no_aux:
+        # the paper's only performance figure: Test (A) to t = 6e-5, single domain
+        # against the domain decomposition, R_S = T_SD / T_DD
+        from paper_1811_03557_gb300.experiments import sd_dd_speedup
+        sd_dd = sd_dd_speedup(ctx, 256, ((128, 128), (128, 64)), 6e-5)
+        sd_dd["paper_R_S"] = {"255 vs 127/127": 6.46, "255 vs 127/63": 9.26,
+                              "hardware": "32-core CPU node, FFTW3 + OpenMP"}
+
     serving = None
     if rank == 0 and args.serving_requests > 0:
         serving = run_serving(abi, torch, ctx, args)
@@ -310,7 +319,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": f"inputs larger than L2 ({spp * N ** 3 * 4 / 1e9:.2f} GB batch per step)"},
             "clocks": clk, "gpu_launches": int(launches), "roofline": roof, "kernels": prof,
-            "e2e": e2e, "cpu_baseline": cpu, "aux_solve": aux, "serving": serving,
+            "e2e": e2e, "cpu_baseline": cpu, "aux_solve": aux, "sd_dd_test_a": sd_dd, "serving": serving,
             "graph": not args.no_graph, "kernel_profile_steps": nprof,
             "sanity": {"finite": bool(finite), "mass": st.mass},
         }

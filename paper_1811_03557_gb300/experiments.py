@@ -34,7 +34,7 @@ def run_test_a(ctx, N: int = 128, K: int = 0, T: float = 6e-5, precision=None,
     from .workloads import TEST_A_C0, TEST_A_RHO0, Geometry
 
     if precision is None:
-        precision = abi.DPM_PREC_TC32 if N == 128 else abi.DPM_PREC_FP32
+        precision = abi.DPM_PREC_TC32 if N in (128, 256) else abi.DPM_PREC_FP32
     lo, hi, h = paper_geometry_a(N)
     prm = abi.pks_params(Geometry.sphere(0.5), N, lo, hi, 1.0, 0.5 * h * h, K, 1, precision,
                          dt_mode=1, rebuild=0, clamp=1)
@@ -66,6 +66,91 @@ def run_test_a(ctx, N: int = 128, K: int = 0, T: float = 6e-5, precision=None,
             "wall_s": wall, "series": series}
 
 
+def run_test_a_dd(ctx, N1: int = 128, N2: int = 64, K: int = 0, T: float = 6e-5, precision=None,
+                  r1: float = 0.25, r2: float = 0.5, record: bool = True, stream=None):
+    """Test (A) with the domain decomposition of Section 3 (Case 1): the ball
+    r < r1 on an N1 grid and the shell r1 < r < r2 on an N2 grid, each box
+    [-r - 2h, r + 2h]^3 with h = 2r/(N - 3); dt = min(dt_prev, CFL bounds of both
+    grids, 0.5 min(h1, h2)^2), rebuild of the coupled BEP when dt decreases."""
+    import torch
+
+    from . import abi
+    from .workloads import TEST_A_C0, TEST_A_RHO0
+
+    if precision is None:
+        precision = abi.DPM_PREC_TC32
+    lo1, hi1, h1 = paper_geometry_a(N1, r1)
+    lo2, hi2, h2 = paper_geometry_a(N2, r2)
+    P = abi.dd_params((0.0, 0.0, 0.0), r1, r2, N1, lo1, hi1, N2, lo2, hi2, K, K, precision)
+    h = min(h1, h2)
+    pk = abi.dpm_dd_pks_create(ctx, P, 1.0, 0.5 * h * h, 1, 0, 1, TEST_A_RHO0, TEST_A_C0, stream=stream)
+    series = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps = 0
+    try:
+        while True:
+            st = abi.dpm_dd_pks_step(pk, 1, record, stream=stream)
+            steps += 1
+            if record:
+                series.append({"step": int(st.step), "t": st.t, "dt": st.dt, "rebuilt": int(st.rebuilt),
+                               "max_rho": st.max_rho, "mass": st.mass, "m2": st.m2,
+                               "free_energy": st.free_energy})
+                if st.t >= T:
+                    break
+            elif abi.dpm_dd_pks_step(pk, 0, True, stream=stream).t >= T:
+                break
+        st = abi.dpm_dd_pks_step(pk, 0, True, stream=stream)
+        torch.cuda.synchronize()
+    finally:
+        abi.dpm_dd_pks_destroy(pk)
+    wall = time.perf_counter() - t0
+    last = {"t": st.t, "dt": st.dt, "step": int(st.step), "max_rho": st.max_rho, "mass": st.mass,
+            "m2": st.m2, "free_energy": st.free_energy}
+    return {"N1": N1, "N2": N2, "h1": h1, "h2": h2, "K": K, "T": T, "wall_s": wall, "last": last,
+            "series": series}
+
+
+def sd_dd_speedup(ctx, N_sd: int = 256, dd_grids=((128, 128), (128, 64)), T: float = 6e-5):
+    """Wall time of Test (A) to T on the single domain (N_sd) against the domain
+    decomposition (N1, N2) for each pair: R_S = T_SD / T_DD (the paper's ratio).
+    Both loops are host-driven (the CFL step is read back every step) and read
+    the time after every step, so both stop at the first step with t >= T."""
+    from . import abi
+
+    def sd_run():
+        lo, hi, h = paper_geometry_a(N_sd)
+        from .workloads import TEST_A_C0, TEST_A_RHO0, Geometry
+        import torch
+        prec = abi.DPM_PREC_TC32 if N_sd in (128, 256) else abi.DPM_PREC_FP32
+        prm = abi.pks_params(Geometry.sphere(0.5), N_sd, lo, hi, 1.0, 0.5 * h * h, 0, 1, prec,
+                             dt_mode=1, rebuild=0, clamp=1)
+        pk = abi.dpm_pks_create(ctx, prm, TEST_A_RHO0, TEST_A_C0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        steps = 0
+        while True:
+            abi.dpm_pks_step(pk, 1, False)
+            steps += 1
+            if abi.dpm_pks_step(pk, 0, True).t >= T:
+                break
+        st = abi.dpm_pks_step(pk, 0, True)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        abi.dpm_pks_destroy(pk)
+        return wall, {"t": st.t, "step": int(st.step), "max_rho": st.max_rho, "mass": st.mass}
+
+    sd_run()  # warm-up (tables, workspaces)
+    wall_sd, last_sd = sd_run()
+    out = {"T": T, "sd": {"N": N_sd, "wall_s": wall_sd, "last": last_sd}, "dd": []}
+    for N1, N2 in dd_grids:
+        run_test_a_dd(ctx, N1, N2, T=T, record=False)  # warm-up
+        r = run_test_a_dd(ctx, N1, N2, T=T, record=False)
+        out["dd"].append({"N1": N1, "N2": N2, "h1_over_h2": r["h1"] / r["h2"], "wall_s": r["wall_s"],
+                          "R_S": wall_sd / r["wall_s"], "last": r["last"]})
+    return out
+
+
 def main(argv=None):
     import argparse
 
@@ -77,8 +162,14 @@ def main(argv=None):
     ap.add_argument("--T", type=float, default=6e-5)
     ap.add_argument("--stop-jump", type=float, default=0.0)
     ap.add_argument("--out", default="")
+    ap.add_argument("--speedup", action="store_true",
+                    help="single domain (N) against the domain decomposition, R_S = T_SD/T_DD")
     a = ap.parse_args(argv)
     ctx = abi.dpm_ctx_create(0)
+    if a.speedup:
+        print(json.dumps(sd_dd_speedup(ctx, a.N, T=a.T)))
+        abi.dpm_ctx_destroy(ctx)
+        return
     res = run_test_a(ctx, a.N, a.K, a.T, stop_jump=a.stop_jump)
     abi.dpm_ctx_destroy(ctx)
     if a.out:
