@@ -18,10 +18,11 @@
 // hi*hi' + hi*lo' + lo*hi' (the dropped lo*lo' is ~2^-22 relative).  Sine
 // blocks are pre-split on the host, scaled by 2^12.
 //
-// CTA = 256 threads (8 warps; warps w and w+4 share the TMEM lanes 32(w%4)..
-// and split the columns), 2 CTAs per SM at 128 registers, persistent over work
-// items; each item's input is staged by bulk copies (TMA) into the operand
-// tiles while the previous item writes its output.  Every wait on the MMA-completion mbarrier is bounded; on
+// Plane passes: 256 threads (8 warps; warps w and w+4 share the TMEM lanes
+// 32(w%4).. and split the columns) at 128 registers; pencil: 128 threads (one
+// column per thread).  Two CTAs per SM, persistent over work items; each item's
+// input is staged by TMA into the operand tiles while the previous item writes
+// its output.  Every wait on the MMA-completion mbarrier is bounded; on
 // expiry the kernel records an error in g_tc_status and stops.
 #include <cuda.h>
 
@@ -558,23 +559,16 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
 
 // ---------------------------------------------------------------------------
 // Pencil pass along i for a fixed j-mode jb: forward, scale/lambda, inverse.
-// 256 threads, two CTAs per SM.  Thread (c, h) = (t mod 128, t / 128): A row
-// and TMEM lane c (the contiguous index), fold indices m' in [32h, 32h+32) of
-// both transforms, and D columns [64h, 64h+64) (the even modes for h = 0, the
-// odd ones for h = 1).  The inverse transform folds modes a and 127-a, which
-// have opposite parity, so the spectral values pass through the operand
-// region (free once the first MMA has completed); per-row maxima of the two
-// halves meet in a small exchange area.
+// Thread t = c (the contiguous index), A rows = c, K = fold index over i / a.
 // ---------------------------------------------------------------------------
-constexpr int kPencilThreads = 256;
+constexpr int kPencilThreads = 128;
 
 __global__ void __launch_bounds__(kPencilThreads, 2)
 k_tc_pencil(TcArgs a, const ApRhs<float> *rhs, float *work, const __grid_constant__ CUtensorMap zmap) {
     const Smem S = smem_base();
     tc_prologue(S, a);
     const uint32_t tm = *S.tslot();
-    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int c = t & (kN - 1), h = t >> 7;
+    const int t = threadIdx.x, warp = t >> 5;
     uint32_t phase = 0;
     const float w4 = (float)(4.0 / (a.h * a.h));
     for (int n = t; n < kN; n += kPencilThreads) S.w()[n] = w4 * a.s2[n];
@@ -584,15 +578,14 @@ k_tc_pencil(TcArgs a, const ApRhs<float> *rhs, float *work, const __grid_constan
     const float nscale = (float)(sc * sc * sc);
     const int nitems = a.B * kN;
     const size_t sN2 = (size_t)kN * kN;
-    const uint32_t lane_addr = tm + ((uint32_t)(32 * (warp & 3)) << 16);
-    float *raw = reinterpret_cast<float *>(S.A(0));  // staged block [i][c], later z[a][c]
-    float *xmax = S.xch();                           // [h][E/O][c] partial row maxima
+    const uint32_t lane_addr = tm + ((uint32_t)(warp * 32) << 16);
+    // The item's column block Z[b][0..128)[jb][0..128) (128 rows of 512 B) is
+    // staged in the operand region by one tensor copy (box 128 x 1 x 128 x 1 of
+    // the [b][i][j][c] workspace) once the previous item's second MMA has completed.
+    float *raw = reinterpret_cast<float *>(S.A(0));
     uint64_t *bar_ld = S.bar() + 1;
     uint32_t ld_phase = 0;
-    // The item's column block Z[b][0..128)[jb][0..128) is staged in the operand
-    // region ([i][c], 64 KB) by one tensor copy (box 128 x 1 x 128 x 1 of the
-    // [b][i][j][c] workspace) issued once the previous item's second MMA has
-    // completed.
+    const int lane = t & 31;
     auto stage_block = [&](int it) {
         if (lane == 0) {
             tc::mbar_arrive_expect_tx(bar_ld, kN * kN * 4);
@@ -604,20 +597,10 @@ k_tc_pencil(TcArgs a, const ApRhs<float> *rhs, float *work, const __grid_constan
         if (warp == 0) stage_block(blockIdx.x);
         inflight = true;
     }
-    // max of |v| over this thread's half of a row: both halves via the exchange area
-    auto row_scales = [&](float me, float mo, float &ie, float &io, float &se, float &so) {
-        xmax[(2 * h) * kN + c] = me;
-        xmax[(2 * h + 1) * kN + c] = mo;
-        __syncthreads();
-        me = fmaxf(xmax[c], xmax[2 * kN + c]);
-        mo = fmaxf(xmax[kN + c], xmax[3 * kN + c]);
-        se = pow2_scale(me, &ie);
-        so = pow2_scale(mo, &io);
-    };
     for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
         const int b = item / kN, jb = item % kN;
         (void)rhs;
-        float *base = work + (size_t)b * kN * sN2 + (size_t)jb * kN + c;
+        float *base = work + (size_t)b * kN * sN2 + (size_t)jb * kN + t;
         {
             const bool got = tc::mbar_wait(bar_ld, ld_phase, kWaitIters);
             if (got) {
@@ -628,58 +611,62 @@ k_tc_pencil(TcArgs a, const ApRhs<float> *rhs, float *work, const __grid_constan
             if (!__syncthreads_and(got ? 1 : 0)) break;
         }
         // ---- phase A: fold along i, split, per-row (per-c) scale -----------
-        float e[32], o[32];
+        float e[kH], o[kH];
+#pragma unroll
+        for (int mp = 0; mp < kH; ++mp) {
+            const float x1 = raw[mp * kN + t], x2 = raw[(kN - 1 - mp) * kN + t];
+            e[mp] = x1 + x2;
+            o[mp] = x1 - x2;
+        }
+        __syncthreads();  // the block is in registers: the tiles may overwrite it
         float me = 0.f, mo = 0.f;
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-            const int mp = 32 * h + q;
-            const float x1 = raw[mp * kN + c], x2 = raw[(kN - 1 - mp) * kN + c];
-            e[q] = x1 + x2;
-            o[q] = x1 - x2;
-            me = fmaxf(me, fabsf(e[q]));
-            mo = fmaxf(mo, fabsf(o[q]));
+        for (int mp = 0; mp < kH; ++mp) {
+            me = fmaxf(me, fabsf(e[mp]));
+            mo = fmaxf(mo, fabsf(o[mp]));
         }
-        float ie, io, se, so;
-        row_scales(me, mo, ie, io, se, so);  // its barrier also ends the reads of raw
+        float ie, io;
+        const float se = pow2_scale(me, &ie), so = pow2_scale(mo, &io);
 #pragma unroll
-        for (int k0 = 0; k0 < 32; k0 += 8) {
-            put8(S.A(0), S.A(1), c, 32 * h + k0, e + k0, se);
-            put8(S.A(2), S.A(3), c, 32 * h + k0, o + k0, so);
+        for (int k0 = 0; k0 < kH; k0 += 8) {
+            put8(S.A(0), S.A(1), t, k0, e + k0, se);
+            put8(S.A(2), S.A(3), t, k0, o + k0, so);
         }
         if (!run_transform(S, tm, phase)) break;
-        // ---- phase C: z[a] = D / lambda for this half's modes -> smem ------------
-        {
-            const float dsc = (h == 0 ? ie : io) * (1.f / kSScale);
-            const float wjc = S.w()[jb] + S.w()[c] + sig;
+        // ---- phase C: z[a] = D / lambda, fold over a, split -------------------
+        float z[kN];  // z[a], a = 0..127 (a = 2a' from sums, 2a'+1 from differences)
 #pragma unroll
-            for (int c0 = 0; c0 < kH; c0 += 16) {
-                float d[16];
-                tc::tmem_ld16(lane_addr + kH * h + c0, d);
-                tc::tmem_wait_ld();
+        for (int c0 = 0; c0 < 2 * kH; c0 += 16) {
+            float d[16];
+            tc::tmem_ld16(lane_addr + c0, d);
+            tc::tmem_wait_ld();
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int am = 2 * (c0 + u) + h;  // mode index
-                    raw[am * kN + c] = d[u] * dsc * __fdividef(nscale, wjc + S.w()[am]);
-                }
+            for (int u = 0; u < 16; ++u) {
+                const int am = c0 < kH ? 2 * (c0 + u) : 2 * (c0 + u - kH) + 1;
+                z[am] = d[u] * ((c0 < kH ? ie : io) * (1.f / kSScale));
             }
         }
-        __syncthreads();
+        const float wjc = S.w()[jb] + S.w()[t] + sig;
+#pragma unroll
+        for (int am = 0; am < kN; ++am) z[am] *= __fdividef(nscale, wjc + S.w()[am]);
+#pragma unroll
+        for (int mp = 0; mp < kH; ++mp) {
+            const float lo_ = z[mp], hi_ = z[kN - 1 - mp];
+            e[mp] = lo_ + hi_;
+            o[mp] = lo_ - hi_;
+        }
         me = 0.f;
         mo = 0.f;
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-            const int mp = 32 * h + q;
-            const float lo_ = raw[mp * kN + c], hi_ = raw[(kN - 1 - mp) * kN + c];
-            e[q] = lo_ + hi_;
-            o[q] = lo_ - hi_;
-            me = fmaxf(me, fabsf(e[q]));
-            mo = fmaxf(mo, fabsf(o[q]));
+        for (int mp = 0; mp < kH; ++mp) {
+            me = fmaxf(me, fabsf(e[mp]));
+            mo = fmaxf(mo, fabsf(o[mp]));
         }
-        row_scales(me, mo, ie, io, se, so);  // also ends the reads of z before the tiles
+        const float se2 = pow2_scale(me, &ie), so2 = pow2_scale(mo, &io);
 #pragma unroll
-        for (int k0 = 0; k0 < 32; k0 += 8) {
-            put8(S.A(0), S.A(1), c, 32 * h + k0, e + k0, se);
-            put8(S.A(2), S.A(3), c, 32 * h + k0, o + k0, so);
+        for (int k0 = 0; k0 < kH; k0 += 8) {
+            put8(S.A(0), S.A(1), t, k0, e + k0, se2);
+            put8(S.A(2), S.A(3), t, k0, o + k0, so2);
         }
         if (!run_transform(S, tm, phase)) break;
         if (item + (int)gridDim.x < nitems) {
@@ -687,19 +674,16 @@ k_tc_pencil(TcArgs a, const ApRhs<float> *rhs, float *work, const __grid_constan
             inflight = true;
         }
         // ---- phase E: D3[c][i'] -> Z[i][jb][c] ---------------------------------
-        {
-            const float sc2 = (h == 0 ? ie : io) * (1.f / kSScale);
 #pragma unroll
-            for (int c0 = 0; c0 < kH; c0 += 32) {
-                float d0[16], d1[16];
-                tc::tmem_ld16(lane_addr + kH * h + c0, d0);
-                tc::tmem_ld16(lane_addr + kH * h + c0 + 16, d1);
-                tc::tmem_wait_ld();
+        for (int c0 = 0; c0 < 2 * kH; c0 += 16) {
+            float d[16];
+            tc::tmem_ld16(lane_addr + c0, d);
+            tc::tmem_wait_ld();
+            const float sc2 = (c0 < kH ? ie : io) * (1.f / kSScale);
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    base[(size_t)(2 * (c0 + u) + h) * sN2] = d0[u] * sc2;
-                    base[(size_t)(2 * (c0 + 16 + u) + h) * sN2] = d1[u] * sc2;
-                }
+            for (int u = 0; u < 16; ++u) {
+                const int ii = c0 < kH ? 2 * (c0 + u) : 2 * (c0 + u - kH) + 1;
+                base[(size_t)ii * sN2] = d[u] * sc2;
             }
         }
         tc::tc_fence_before_sync();
