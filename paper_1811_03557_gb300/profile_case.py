@@ -1,4 +1,5 @@
-"""Profiling case: the BEP assembly of the N = 128, K = 8 sphere workload.
+"""Profiling cases: the BEP assembly of the N = 128, K = 8 sphere workload
+(default), or batched dense solves at N = 256 (--case aux256).
 
 Builds the BEP twice (the first build creates the per-device tables) through
 the C ABI; each build runs classification, the gamma geometry, one batched
@@ -21,7 +22,21 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--precision", choices=["fp32", "tc32", "fp64"], default="tc32")
     ap.add_argument("--builds", type=int, default=2)
+    ap.add_argument("--case", choices=["bep128", "aux256"], default="bep128",
+                    help="bep128: the BEP build above; aux256: two batched solves of 4 dense "
+                         "right-hand sides at N = 256 on the tensor-core solver")
     args = ap.parse_args()
+    if args.case == "aux256":
+        from .workloads import random_rhs
+        ctx = abi.dpm_ctx_create(0)
+        q = torch.from_numpy(random_rhs(0, 4, 256)).cuda()
+        u = torch.empty_like(q)
+        for _ in range(2):
+            abi.dpm_aux_solve_batched(ctx, 256, 2.4 / 257, 1e4 + 1.0, 4, q, u, abi.DPM_PREC_TC32)
+        torch.cuda.synchronize()
+        abi.dpm_ctx_destroy(ctx)
+        print("profile case done")
+        return
     prec = {"fp32": abi.DPM_PREC_FP32, "tc32": abi.DPM_PREC_TC32, "fp64": abi.DPM_PREC_FP64}[args.precision]
     w = WORKLOADS["pks_sphere_N128_K8"]
     ctx = abi.dpm_ctx_create(0)
