@@ -426,9 +426,11 @@ def run_aux(abi, torch, ctx, stream):
     out["tc32_N256_B16"] = {"ms": ms, "grid_pts_per_s": v, "hbm_gbs": gbs, "frac": gbs / hbm}
     ms, v = timed(256, 16, abi.DPM_PREC_FP32, 3)
     gbs = 40.0 * 16 * 256 ** 3 / (ms / 1e3) / 1e9
-    out["fp32_N256_B16"] = {"ms": ms, "grid_pts_per_s": v, "hbm_gbs": gbs, "frac": gbs / hbm}
+    out["fp32_N256_B16"] = {"ms": ms, "grid_pts_per_s": v, "hbm_gbs": gbs, "frac": gbs / hbm,
+                            "simt_tile": abi.dpm_simt_tile(256, abi.DPM_PREC_FP32, 16)}
     ms, v = timed(256, 2, abi.DPM_PREC_FP64, 1, calls=2)
-    out["fp64_N256_per_solve"] = {"ms": ms, "grid_pts_per_s": v}
+    out["fp64_N256_per_solve"] = {"ms": ms, "grid_pts_per_s": v,
+                                  "simt_tile": abi.dpm_simt_tile(256, abi.DPM_PREC_FP64, 1)}
     # the BEP batch workload: ellipsoid (1, 0.8, 0.6) in [-1.2, 1.2]^3, N = 256,
     # K = 12 (338 columns in one batched solve), sigma = 1/dt + 1, dt = 1e-4
     from paper_1811_03557_gb300.workloads import WORKLOADS

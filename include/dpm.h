@@ -187,6 +187,24 @@ int dpm_aux_solve_batched_noalloc(int N, double h, double sigma, int B, const fl
                                   float *u, cudaStream_t stream);
 
 /*
+ * Tile width of the SIMT (DPM_PREC_FP32 / DPM_PREC_FP64) solver.  Each of its
+ * five passes works on tiles of C grid lines (C = 16, 32 or 64; smaller tiles
+ * give more CTAs per SM, larger ones more reuse of each sine-table load).  The
+ * first solve on a device for a given N, precision and batch class (B <= 2,
+ * B <= 16, larger) times every width whose shared memory fits on a problem of
+ * that size with zero right-hand sides (same work as real data), keeps the
+ * fastest and synchronises the stream once to read the timers; a solve issued
+ * while its stream is being captured does not tune and uses the tuned width,
+ * else 32.  Every output is summed in the same order for each width, so the
+ * choice changes the run time only, never the result.  Environment: DPM_SIMT_TILE
+ * = 16|32|64 forces a width; DPM_AUTOTUNE=0 keeps 32.  The no-alloc solve
+ * always uses 32.
+ * dpm_simt_tile writes to *tile the width tuned on the current device for
+ * (N, precision, B), or 0 if none has been tuned yet.
+ */
+int dpm_simt_tile(int N, int precision, int B, int *tile);
+
+/*
  * Steps 1-2 of the main algorithm: classify the grid, project every node of
  * gamma on Gamma (foot point, signed distance d > 0 outside Omega along the
  * outward normal; Definition 2.6), evaluate the real orthonormal spherical

@@ -101,6 +101,7 @@ _SIGS = {
     "dpm_pks_destroy": (C.c_int, [_P]),
     "dpm_aux_solve_batched_noalloc": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, _P,
                                                 _P, _P]),
+    "dpm_simt_tile": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "dpm_dd_build": (C.c_int, [_P, C.POINTER(dpm_dd_params), C.c_double, C.POINTER(C.c_void_p), _P]),
     "dpm_dd_get_info": (C.c_int, [_P, C.POINTER(dpm_dd_info)]),
     "dpm_dd_matrix": (C.c_int, [_P, _P, _P]),
@@ -218,6 +219,14 @@ def dpm_aux_solve_batched_noalloc(N, h, sigma, B, q, u, stream=None):
     """FP32 AP solve whose scratch is a fixed device array inside the library
     (no allocation); q, u float32 device tensors [B][N][N][N]."""
     _check(lib().dpm_aux_solve_batched_noalloc(N, h, sigma, B, _ptr(q), _ptr(u), _stream(stream)))
+
+
+def dpm_simt_tile(N, precision=DPM_PREC_FP32, B=1):
+    """Tile width the SIMT solver tuned for (N, precision, B) on the current
+    device, 0 if none yet."""
+    t = C.c_int(0)
+    _check(lib().dpm_simt_tile(N, precision, B, C.byref(t)))
+    return t.value
 
 
 def dpm_bep_build(ctx, geom, N, lo, hi, sigma, K, beta=1, precision=DPM_PREC_FP32, stream=None):

@@ -155,6 +155,8 @@ void ap_params_from_index(ApParams &p, const GridIndex &gi);
 // work: B*N^3 elements of T.  rhs: device array of B descriptors.
 template <class T>
 int ap_solve_simt(const ApParams &p, const ApRhs<T> *rhs_dev, T *work, cudaStream_t s);
+// Tuned SIMT tile width for (N, FP64?, B) on the current device, 0 if none.
+int simt_tile_choice(int N, int f64, int B);
 int ap_solve_tc(const ApParams &p, const ApRhs<float> *rhs_dev, float *work, cudaStream_t s);
 // N = 256: six out-of-place passes; work holds 2 B N^3 floats.
 int ap_solve_tc256(const ApParams &p, const ApRhs<float> *rhs_dev, float *work, cudaStream_t s);

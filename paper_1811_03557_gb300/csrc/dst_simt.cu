@@ -21,6 +21,8 @@
 #include <map>
 #include <math.h>
 #include <mutex>
+#include <stdlib.h>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -91,7 +93,6 @@ template const double *dst_fold_table<double>(int);
 
 namespace {
 
-constexpr int kC = 32;         // columns (or rows) per tile
 constexpr int kThreads = 256;
 
 template <class T> struct V4 { T v[4]; };
@@ -122,22 +123,22 @@ __device__ __forceinline__ void st4(double *p, const double *v) {
     *reinterpret_cast<double2 *>(p + 2) = make_double2(v[2], v[3]);
 }
 
-// Column-major tile: x[m][c] (m = transform index, kC columns, row stride kC).
+// Column-major tile: x[m][c] (m = transform index, C columns, row stride C).
 // out[a][c] = sum_m S[a][m] x[m][c].  x is folded in place.
-template <class T>
+template <class T, int C = 32>
 __device__ void tile_transform_cm(T *x, T *out, int N, const T *tab) {
     FoldDims fd(N);
-    for (int idx = threadIdx.x; idx < fd.H * kC; idx += blockDim.x) {
-        int mp = idx / kC, c = idx % kC;
-        T a = x[mp * kC + c], b = x[(N - 1 - mp) * kC + c];
-        x[mp * kC + c] = a + b;
-        x[(N - 1 - mp) * kC + c] = a - b;
+    for (int idx = threadIdx.x; idx < fd.H * C; idx += blockDim.x) {
+        int mp = idx / C, c = idx % C;
+        T a = x[mp * C + c], b = x[(N - 1 - mp) * C + c];
+        x[mp * C + c] = a + b;
+        x[(N - 1 - mp) * C + c] = a - b;
     }
     __syncthreads();
     const int nabE = fd.NEp / 4, nabO = fd.NOp / 4;
-    const int ntask = (nabE + nabO) * (kC / 4);
+    const int ntask = (nabE + nabO) * (C / 4);
     for (int t = threadIdx.x; t < ntask; t += blockDim.x) {
-        int cb = t % (kC / 4), ab = t / (kC / 4);
+        int cb = t % (C / 4), ab = t / (C / 4);
         bool even = ab < nabE;  // output a0 even <=> a odd <=> folded sums
         int abp = even ? ab : ab - nabE;
         const T *S = even ? tab + 4 * abp : tab + fd.offO() + 4 * abp;
@@ -149,7 +150,7 @@ __device__ void tile_transform_cm(T *x, T *out, int N, const T *tab) {
             for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
         for (int mp = 0; mp < fd.H; ++mp) {
             int row = even ? mp : N - 1 - mp;
-            V4<T> xv = ld4(x + row * kC + 4 * cb);
+            V4<T> xv = ld4(x + row * C + 4 * cb);
             V4<T> sv = ldg4(S + (size_t)mp * ld);
 #pragma unroll
             for (int i = 0; i < 4; ++i)
@@ -157,7 +158,7 @@ __device__ void tile_transform_cm(T *x, T *out, int N, const T *tab) {
                 for (int j = 0; j < 4; ++j) acc[i][j] = fma(sv.v[i], xv.v[j], acc[i][j]);
         }
         if (even && (N & 1)) {
-            V4<T> xv = ld4(x + fd.H * kC + 4 * cb);
+            V4<T> xv = ld4(x + fd.H * C + 4 * cb);
             V4<T> sv = ldg4(S + (size_t)fd.H * ld);
 #pragma unroll
             for (int i = 0; i < 4; ++i)
@@ -167,18 +168,18 @@ __device__ void tile_transform_cm(T *x, T *out, int N, const T *tab) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             int a0 = even ? 2 * (4 * abp + i) : 2 * (4 * abp + i) + 1;
-            if (a0 < N) st4(out + a0 * kC + 4 * cb, acc[i]);
+            if (a0 < N) st4(out + a0 * C + 4 * cb, acc[i]);
         }
     }
     __syncthreads();
 }
 
-// Row-major tile: x[r][m] (kC rows, row stride ld = N + 1).
+// Row-major tile: x[r][m] (C rows, row stride ld = N + 1).
 // out[r][a] = sum_m S[a][m] x[r][m].  x is folded in place.
-template <class T>
+template <class T, int C = 32>
 __device__ void tile_transform_rm(T *x, T *out, int N, int ld, const T *tab) {
     FoldDims fd(N);
-    for (int idx = threadIdx.x; idx < fd.H * kC; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < fd.H * C; idx += blockDim.x) {
         int r = idx / fd.H, mp = idx % fd.H;
         T a = x[r * ld + mp], b = x[r * ld + N - 1 - mp];
         x[r * ld + mp] = a + b;
@@ -186,9 +187,9 @@ __device__ void tile_transform_rm(T *x, T *out, int N, int ld, const T *tab) {
     }
     __syncthreads();
     const int nabE = fd.NEp / 4, nabO = fd.NOp / 4;
-    const int ntask = (nabE + nabO) * (kC / 4);
+    const int ntask = (nabE + nabO) * (C / 4);
     for (int t = threadIdx.x; t < ntask; t += blockDim.x) {
-        int rb = t % (kC / 4), ab = t / (kC / 4);
+        int rb = t % (C / 4), ab = t / (C / 4);
         bool even = ab < nabE;
         int abp = even ? ab : ab - nabE;
         const T *S = even ? tab + 4 * abp : tab + fd.offO() + 4 * abp;
@@ -247,7 +248,7 @@ struct PassArgs {
 };
 
 // Pass 1: right-hand side + forward transform along k.
-template <class T>
+template <class T, int C = 32>
 __global__ void __launch_bounds__(kThreads) k_pass_k_fwd(PassArgs a, const ApRhs<T> *rhs, T *work,
                                                          const T *tab) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -256,12 +257,12 @@ __global__ void __launch_bounds__(kThreads) k_pass_k_fwd(PassArgs a, const ApRhs
     ApRhs<T> r = rhs[b];
     if (rhs_skipped(r, a.cond_flag)) return;
     T *x = reinterpret_cast<T *>(smem_raw);
-    T *out = x + kC * ld;
+    T *out = x + C * ld;
     const int64_t nrows = (int64_t)N * N;
-    const int64_t R0 = (int64_t)blockIdx.x * kC;
+    const int64_t R0 = (int64_t)blockIdx.x * C;
     const double sig = a.sigma_dev ? *a.sigma_dev : a.sigma;
     const T fs = (T)(a.fscale_dev ? *a.fscale_dev : a.fscale);
-    for (int idx = threadIdx.x; idx < kC * N; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < C * N; idx += blockDim.x) {
         int rr = idx / N, k = idx % N;
         int64_t R = R0 + rr;
         T v = (T)0;
@@ -276,7 +277,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_k_fwd(PassArgs a, const ApRhs
     if (r.dens) {
         const T cdiag = (T)(sig + 6.0 / (a.h * a.h));
         const T coff = (T)(1.0 / (a.h * a.h));
-        int64_t Rend = R0 + kC < nrows ? R0 + kC : nrows;
+        int64_t Rend = R0 + C < nrows ? R0 + C : nrows;
         int e0 = a.rp_shell[R0], e1 = a.rp_shell[Rend];
         for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
             int p = a.shell[e];
@@ -293,85 +294,85 @@ __global__ void __launch_bounds__(kThreads) k_pass_k_fwd(PassArgs a, const ApRhs
         }
         __syncthreads();
     }
-    tile_transform_rm<T>(x, out, N, ld, tab);
+    tile_transform_rm<T, C>(x, out, N, ld, tab);
     T *w = work + (size_t)b * nrows * N;
-    for (int idx = threadIdx.x; idx < kC * N; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < C * N; idx += blockDim.x) {
         int rr = idx / N, k = idx % N;
         int64_t R = R0 + rr;
         if (R < nrows) w[R * N + k] = out[rr * ld + k];
     }
 }
 
-// Passes 2 and 4: transform along j for tiles [j][kc..kc+32) at fixed i.
-template <class T>
+// Passes 2 and 4: transform along j for tiles [j][kc..kc+C) at fixed i.
+template <class T, int C = 32>
 __global__ void __launch_bounds__(kThreads) k_pass_j(PassArgs a, const ApRhs<T> *rhs, T *work,
                                                      const T *tab) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = a.N;
     const int b = blockIdx.y;
     if (rhs_skipped(rhs[b], a.cond_flag)) return;
-    const int nkc = (N + kC - 1) / kC;
-    const int i = blockIdx.x / nkc, kc = (blockIdx.x % nkc) * kC;
+    const int nkc = (N + C - 1) / C;
+    const int i = blockIdx.x / nkc, kc = (blockIdx.x % nkc) * C;
     T *x = reinterpret_cast<T *>(smem_raw);
-    T *out = x + N * kC;
+    T *out = x + N * C;
     T *w = work + (size_t)b * N * N * N + (size_t)i * N * N;
-    for (int idx = threadIdx.x; idx < N * kC; idx += blockDim.x) {
-        int j = idx / kC, c = idx % kC;
-        x[j * kC + c] = (kc + c < N) ? w[(size_t)j * N + kc + c] : (T)0;
+    for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
+        int j = idx / C, c = idx % C;
+        x[j * C + c] = (kc + c < N) ? w[(size_t)j * N + kc + c] : (T)0;
     }
     __syncthreads();
-    tile_transform_cm<T>(x, out, N, tab);
-    for (int idx = threadIdx.x; idx < N * kC; idx += blockDim.x) {
-        int j = idx / kC, c = idx % kC;
-        if (kc + c < N) w[(size_t)j * N + kc + c] = out[j * kC + c];
+    tile_transform_cm<T, C>(x, out, N, tab);
+    for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
+        int j = idx / C, c = idx % C;
+        if (kc + c < N) w[(size_t)j * N + kc + c] = out[j * C + c];
     }
 }
 
-// Pass 3: along i, forward, scale/lambda, inverse; tiles [i][kc..kc+32) at fixed j.
-template <class T>
+// Pass 3: along i, forward, scale/lambda, inverse; tiles [i][kc..kc+C) at fixed j.
+template <class T, int C = 32>
 __global__ void __launch_bounds__(kThreads) k_pass_i(PassArgs a, const ApRhs<T> *rhs, T *work,
                                                      const T *tab) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = a.N;
     const int b = blockIdx.y;
     if (rhs_skipped(rhs[b], a.cond_flag)) return;
-    const int nkc = (N + kC - 1) / kC;
-    const int j = blockIdx.x / nkc, kc = (blockIdx.x % nkc) * kC;
+    const int nkc = (N + C - 1) / C;
+    const int j = blockIdx.x / nkc, kc = (blockIdx.x % nkc) * C;
     T *x = reinterpret_cast<T *>(smem_raw);
-    T *out = x + N * kC;
-    T *wt = out + N * kC;  // N weights (4/h^2) sin^2(pi (n+1)/(2(N+1)))
+    T *out = x + N * C;
+    T *wt = out + N * C;  // N weights (4/h^2) sin^2(pi (n+1)/(2(N+1)))
     T *w = work + (size_t)b * N * N * N + (size_t)j * N;
     const size_t si = (size_t)N * N;
     const double sig = a.sigma_dev ? *a.sigma_dev : a.sigma;
     const T w4 = (T)(4.0 / (a.h * a.h));
     const T *s2 = tab + FoldDims(N).offW();
     for (int n = threadIdx.x; n < N; n += blockDim.x) wt[n] = w4 * s2[n];
-    for (int idx = threadIdx.x; idx < N * kC; idx += blockDim.x) {
-        int i = idx / kC, c = idx % kC;
-        x[i * kC + c] = (kc + c < N) ? w[(size_t)i * si + kc + c] : (T)0;
+    for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
+        int i = idx / C, c = idx % C;
+        x[i * C + c] = (kc + c < N) ? w[(size_t)i * si + kc + c] : (T)0;
     }
     __syncthreads();
-    tile_transform_cm<T>(x, out, N, tab);
+    tile_transform_cm<T, C>(x, out, N, tab);
     const double sc = 2.0 / (N + 1);
     const T scale = (T)(sc * sc * sc);
     const T sgT = (T)sig;
-    for (int idx = threadIdx.x; idx < N * kC; idx += blockDim.x) {
-        int ai = idx / kC, c = idx % kC;
+    for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
+        int ai = idx / C, c = idx % C;
         int kk = kc + c < N ? kc + c : N - 1;
         T lam = sgT + (wt[ai] + wt[j] + wt[kk]);
-        x[ai * kC + c] = out[ai * kC + c] * (scale / lam);
+        x[ai * C + c] = out[ai * C + c] * (scale / lam);
     }
     __syncthreads();
-    tile_transform_cm<T>(x, out, N, tab);
-    for (int idx = threadIdx.x; idx < N * kC; idx += blockDim.x) {
-        int i = idx / kC, c = idx % kC;
-        if (kc + c < N) w[(size_t)i * si + kc + c] = out[i * kC + c];
+    tile_transform_cm<T, C>(x, out, N, tab);
+    for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
+        int i = idx / C, c = idx % C;
+        if (kc + c < N) w[(size_t)i * si + kc + c] = out[i * C + c];
     }
 }
 
 // Pass 5: inverse along k, then the dense output (masked to N^+) and/or the
 // trace on gamma_in.
-template <class T>
+template <class T, int C = 32>
 __global__ void __launch_bounds__(kThreads) k_pass_k_inv(PassArgs a, const ApRhs<T> *rhs,
                                                          const T *work, const T *tab) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -380,19 +381,19 @@ __global__ void __launch_bounds__(kThreads) k_pass_k_inv(PassArgs a, const ApRhs
     ApRhs<T> r = rhs[b];
     if (rhs_skipped(r, a.cond_flag)) return;
     T *x = reinterpret_cast<T *>(smem_raw);
-    T *out = x + kC * ld;
+    T *out = x + C * ld;
     const int64_t nrows = (int64_t)N * N;
-    const int64_t R0 = (int64_t)blockIdx.x * kC;
+    const int64_t R0 = (int64_t)blockIdx.x * C;
     const T *w = work + (size_t)b * nrows * N;
-    for (int idx = threadIdx.x; idx < kC * N; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < C * N; idx += blockDim.x) {
         int rr = idx / N, k = idx % N;
         int64_t R = R0 + rr;
         x[rr * ld + k] = R < nrows ? w[R * N + k] : (T)0;
     }
     __syncthreads();
-    tile_transform_rm<T>(x, out, N, ld, tab);
+    tile_transform_rm<T, C>(x, out, N, ld, tab);
     if (r.out_dense) {
-        for (int idx = threadIdx.x; idx < kC * N; idx += blockDim.x) {
+        for (int idx = threadIdx.x; idx < C * N; idx += blockDim.x) {
             int rr = idx / N, k = idx % N;
             int64_t R = R0 + rr;
             if (R < nrows) {
@@ -404,7 +405,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_k_inv(PassArgs a, const ApRhs
         }
     }
     if (r.out_trace) {
-        int64_t Rend = R0 + kC < nrows ? R0 + kC : nrows;
+        int64_t Rend = R0 + C < nrows ? R0 + C : nrows;
         int e0 = a.rp_gin[R0], e1 = a.rp_gin[Rend];
         for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
             int p = a.gin[e];
@@ -414,22 +415,166 @@ __global__ void __launch_bounds__(kThreads) k_pass_k_inv(PassArgs a, const ApRhs
     }
 }
 
-template <class T> size_t smem_rows(int N) { return 2 * (size_t)kC * (N + 1) * sizeof(T); }
-template <class T> size_t smem_cols(int N) { return (2 * (size_t)N * kC + N) * sizeof(T); }
+template <class T, int C = 32> size_t smem_rows(int N) { return 2 * (size_t)C * (N + 1) * sizeof(T); }
+template <class T, int C = 32> size_t smem_cols(int N) { return (2 * (size_t)N * C + N) * sizeof(T); }
 
-template <class T> int set_smem_limits(int N) {
-    static int configured[2] = {0, 0};
+template <class T, int C = 32> int set_smem_limits(int N) {
+    static int configured = 0;
     static std::mutex mu;
     std::lock_guard<std::mutex> lk(mu);
-    int slot = sizeof(T) == 8;
-    size_t need = smem_rows<T>(N) > smem_cols<T>(N) ? smem_rows<T>(N) : smem_cols<T>(N);
-    if ((size_t)configured[slot] >= need) return DPM_OK;
+    size_t need = smem_rows<T, C>(N) > smem_cols<T, C>(N) ? smem_rows<T, C>(N) : smem_cols<T, C>(N);
+    if ((size_t)configured >= need) return DPM_OK;
     int v = 227 * 1024;
-    DPM_CUDA(cudaFuncSetAttribute(k_pass_k_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
-    DPM_CUDA(cudaFuncSetAttribute(k_pass_j<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
-    DPM_CUDA(cudaFuncSetAttribute(k_pass_i<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
-    DPM_CUDA(cudaFuncSetAttribute(k_pass_k_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
-    configured[slot] = v;
+    DPM_CUDA(cudaFuncSetAttribute(k_pass_k_fwd<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+    DPM_CUDA(cudaFuncSetAttribute(k_pass_j<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+    DPM_CUDA(cudaFuncSetAttribute(k_pass_i<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+    DPM_CUDA(cudaFuncSetAttribute(k_pass_k_inv<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+    configured = v;
+    return DPM_OK;
+}
+
+template <class T, int C> bool tile_fits(int N) {
+    return smem_rows<T, C>(N) <= 227 * 1024 && smem_cols<T, C>(N) <= 227 * 1024;
+}
+
+// The five passes with tile width C (columns or rows per CTA).
+template <class T, int C>
+int simt_passes(const PassArgs &a, const ApRhs<T> *rhs_dev, T *work, const T *tab, cudaStream_t s) {
+    const int N = a.N;
+    DPM_RET((set_smem_limits<T, C>(N)));
+    const int64_t nrows = (int64_t)N * N;
+    dim3 grow((unsigned)((nrows + C - 1) / C), a.B);
+    dim3 gcol((unsigned)(N * ((N + C - 1) / C)), a.B);
+    const bool f64 = sizeof(T) == 8;
+    {
+        DPM_PROF(f64 ? "ap_simt64_pass_k_fwd" : "ap_simt32_pass_k_fwd", s);
+        k_pass_k_fwd<T, C><<<grow, kThreads, smem_rows<T, C>(N), s>>>(a, rhs_dev, work, tab);
+        DPM_LAUNCHED();
+    }
+    {
+        DPM_PROF(f64 ? "ap_simt64_pass_j" : "ap_simt32_pass_j", s);
+        k_pass_j<T, C><<<gcol, kThreads, smem_cols<T, C>(N), s>>>(a, rhs_dev, work, tab);
+        DPM_LAUNCHED();
+    }
+    {
+        DPM_PROF(f64 ? "ap_simt64_pass_i" : "ap_simt32_pass_i", s);
+        k_pass_i<T, C><<<gcol, kThreads, smem_cols<T, C>(N), s>>>(a, rhs_dev, work, tab);
+        DPM_LAUNCHED();
+    }
+    {
+        DPM_PROF(f64 ? "ap_simt64_pass_j" : "ap_simt32_pass_j", s);
+        k_pass_j<T, C><<<gcol, kThreads, smem_cols<T, C>(N), s>>>(a, rhs_dev, work, tab);
+        DPM_LAUNCHED();
+    }
+    {
+        DPM_PROF(f64 ? "ap_simt64_pass_k_inv" : "ap_simt32_pass_k_inv", s);
+        k_pass_k_inv<T, C><<<grow, kThreads, smem_rows<T, C>(N), s>>>(a, rhs_dev, work, tab);
+        DPM_LAUNCHED();
+    }
+    return DPM_OK;
+}
+
+template <class T>
+int simt_dispatch(int C, const PassArgs &a, const ApRhs<T> *rhs_dev, T *work, const T *tab, cudaStream_t s) {
+    if (C == 16) return simt_passes<T, 16>(a, rhs_dev, work, tab, s);
+    if (C == 64) return simt_passes<T, 64>(a, rhs_dev, work, tab, s);
+    return simt_passes<T, 32>(a, rhs_dev, work, tab, s);
+}
+
+// ---- autotuner of the tile width ---------------------------------------------------
+// The first solve of each (N, precision, batch class) on a device times the
+// candidate widths on a workspace-only problem (every right-hand side zero, no
+// outputs: the passes do the same work as for real data) and keeps the fastest.
+// The per-output sums run in the same order for every width, so the choice
+// changes the time, not the result.  DPM_SIMT_TILE=16|32|64 forces a width;
+// DPM_AUTOTUNE=0 keeps 32.  A solve issued while its stream is being captured
+// uses the tuned width if there is one, else 32.
+struct TuneKey {
+    int dev, N, f64, bclass;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(dev, N, f64, bclass) < std::tie(o.dev, o.N, o.f64, o.bclass);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tuned;
+
+int batch_class(int B) { return B <= 2 ? 0 : (B <= 16 ? 1 : 2); }
+
+template <class T>
+int tuned_tile(const PassArgs &a0, T *work, const T *tab, cudaStream_t s, int *out) {
+    const char *force = getenv("DPM_SIMT_TILE");
+    if (force) {
+        const int c = atoi(force);
+        if ((c == 16 || c == 32 || c == 64) &&
+            (c == 16 ? tile_fits<T, 16>(a0.N) : c == 32 ? tile_fits<T, 32>(a0.N) : tile_fits<T, 64>(a0.N))) {
+            *out = c;
+            return DPM_OK;
+        }
+    }
+    *out = 32;
+    const char *en = getenv("DPM_AUTOTUNE");
+    if (en && en[0] == '0') return DPM_OK;
+    int dev = 0;
+    DPM_CUDA(cudaGetDevice(&dev));
+    const TuneKey key{dev, a0.N, (int)(sizeof(T) == 8), batch_class(a0.B)};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) { *out = it->second; return DPM_OK; }
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return DPM_OK;
+    // One tuning at a time: the zero descriptors below are shared.
+    static std::mutex run_mu;
+    static std::map<int, std::pair<void *, size_t>> zdesc;  // device -> (descriptors, bytes)
+    std::lock_guard<std::mutex> run_lk(run_mu);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) { *out = it->second; return DPM_OK; }
+    }
+    auto &zb = zdesc[dev];
+    const size_t need = sizeof(ApRhs<T>) * (size_t)a0.B;
+    if (zb.second < need) {
+        if (zb.first) DPM_CUDA(cudaFree(zb.first));
+        zb.first = nullptr;
+        zb.second = 0;
+        DPM_CUDA(cudaMalloc(&zb.first, need));
+        zb.second = need;
+    }
+    ApRhs<T> *zd = static_cast<ApRhs<T> *>(zb.first);
+    DPM_CUDA(cudaMemsetAsync(zd, 0, need, s));
+    PassArgs a = a0;
+    a.cond_flag = nullptr;
+    a.mask_f = a.mask_out = 0;
+    cudaEvent_t e0, e1;
+    DPM_CUDA(cudaEventCreate(&e0));
+    DPM_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bestC = 32;
+    const int cands[3] = {16, 32, 64};
+    int rc = DPM_OK;
+    for (int c : cands) {
+        const bool fits = c == 16 ? tile_fits<T, 16>(a.N) : c == 32 ? tile_fits<T, 32>(a.N) : tile_fits<T, 64>(a.N);
+        if (!fits) continue;
+        rc = simt_dispatch<T>(c, a, zd, work, tab, s);  // warm-up
+        if (rc == DPM_OK && cudaEventRecord(e0, s) != cudaSuccess) rc = DPM_ECUDA;
+        for (int r = 0; r < 2 && rc == DPM_OK; ++r) rc = simt_dispatch<T>(c, a, zd, work, tab, s);
+        if (rc == DPM_OK && cudaEventRecord(e1, s) != cudaSuccess) rc = DPM_ECUDA;
+        if (rc == DPM_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = DPM_ECUDA;
+        float ms = 0.f;
+        if (rc == DPM_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = DPM_ECUDA;
+        if (rc != DPM_OK) break;
+        if (ms < best) { best = ms; bestC = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != DPM_OK) { set_error("SIMT tile tuning failed"); return rc; }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[key] = bestC;
+    }
+    *out = bestC;
     return DPM_OK;
 }
 
@@ -452,39 +597,19 @@ int ap_solve_simt(const ApParams &p, const ApRhs<T> *rhs_dev, T *work, cudaStrea
     if (p.B < 1 || p.B > 65535) { set_error("AP solve: B=%d outside [1, 65535]", p.B); return DPM_EINVAL; }
     const T *tab = dst_fold_table<T>(N);
     if (!tab) { set_error("AP solve: could not create the DST table"); return DPM_ENOMEM; }
-    DPM_RET(set_smem_limits<T>(N));
     PassArgs a{N, p.B, p.h, p.sigma, p.fscale, p.sigma_dev, p.fscale_dev, p.cond_flag, p.mask_f,
                p.mask_out, p.labels, p.shell, p.shell_nb, p.rp_shell, p.gin, p.rp_gin};
-    const int64_t nrows = (int64_t)N * N;
-    dim3 grow((unsigned)((nrows + kC - 1) / kC), p.B);
-    dim3 gcol((unsigned)(N * ((N + kC - 1) / kC)), p.B);
-    const bool f64 = sizeof(T) == 8;
-    {
-        DPM_PROF(f64 ? "ap_simt64_pass_k_fwd" : "ap_simt32_pass_k_fwd", s);
-        k_pass_k_fwd<T><<<grow, kThreads, smem_rows<T>(N), s>>>(a, rhs_dev, work, tab);
-        DPM_LAUNCHED();
-    }
-    {
-        DPM_PROF(f64 ? "ap_simt64_pass_j" : "ap_simt32_pass_j", s);
-        k_pass_j<T><<<gcol, kThreads, smem_cols<T>(N), s>>>(a, rhs_dev, work, tab);
-        DPM_LAUNCHED();
-    }
-    {
-        DPM_PROF(f64 ? "ap_simt64_pass_i" : "ap_simt32_pass_i", s);
-        k_pass_i<T><<<gcol, kThreads, smem_cols<T>(N), s>>>(a, rhs_dev, work, tab);
-        DPM_LAUNCHED();
-    }
-    {
-        DPM_PROF(f64 ? "ap_simt64_pass_j" : "ap_simt32_pass_j", s);
-        k_pass_j<T><<<gcol, kThreads, smem_cols<T>(N), s>>>(a, rhs_dev, work, tab);
-        DPM_LAUNCHED();
-    }
-    {
-        DPM_PROF(f64 ? "ap_simt64_pass_k_inv" : "ap_simt32_pass_k_inv", s);
-        k_pass_k_inv<T><<<grow, kThreads, smem_rows<T>(N), s>>>(a, rhs_dev, work, tab);
-        DPM_LAUNCHED();
-    }
-    return DPM_OK;
+    int C = 32;
+    DPM_RET(tuned_tile<T>(a, work, tab, s, &C));
+    return simt_dispatch<T>(C, a, rhs_dev, work, tab, s);
+}
+
+int simt_tile_choice(int N, int f64, int B) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(TuneKey{dev, N, f64, batch_class(B)});
+    return it == g_tuned.end() ? 0 : it->second;
 }
 
 template int ap_solve_simt<float>(const ApParams &, const ApRhs<float> *, float *, cudaStream_t);
@@ -605,25 +730,22 @@ extern "C" int dpm_aux_solve_batched_noalloc(int N, double h, double sigma, int 
     float *work = static_cast<float *>(base);
     float *tab = work + kStaticWorkElems;
     ApRhs<float> *desc = reinterpret_cast<ApRhs<float> *>(tab + kStaticTableElems);
-    DPM_RET(set_smem_limits<float>(N));
     k_static_table<<<64, 256, 0, s>>>(N, tab);
     DPM_LAUNCHED();
     k_static_desc<<<(B + 127) / 128, 128, 0, s>>>(B, n3, q, u, desc);
     DPM_LAUNCHED();
     PassArgs a{N, B, h, sigma, 1.0, nullptr, nullptr, nullptr, 0, 0,
                nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    const int64_t nrows = (int64_t)N * N;
-    dim3 grow((unsigned)((nrows + kC - 1) / kC), B);
-    dim3 gcol((unsigned)(N * ((N + kC - 1) / kC)), B);
-    k_pass_k_fwd<float><<<grow, kThreads, smem_rows<float>(N), s>>>(a, desc, work, tab);
-    DPM_LAUNCHED();
-    k_pass_j<float><<<gcol, kThreads, smem_cols<float>(N), s>>>(a, desc, work, tab);
-    DPM_LAUNCHED();
-    k_pass_i<float><<<gcol, kThreads, smem_cols<float>(N), s>>>(a, desc, work, tab);
-    DPM_LAUNCHED();
-    k_pass_j<float><<<gcol, kThreads, smem_cols<float>(N), s>>>(a, desc, work, tab);
-    DPM_LAUNCHED();
-    k_pass_k_inv<float><<<grow, kThreads, smem_rows<float>(N), s>>>(a, desc, work, tab);
-    DPM_LAUNCHED();
+    return simt_passes<float, 32>(a, desc, work, tab, s);
+}
+
+extern "C" int dpm_simt_tile(int N, int precision, int B, int *tile) {
+    using namespace dpm;
+    if (!tile) { set_error("tile is NULL"); return DPM_EINVAL; }
+    if (precision != DPM_PREC_FP32 && precision != DPM_PREC_FP64) {
+        set_error("dpm_simt_tile: precision must be DPM_PREC_FP32 or DPM_PREC_FP64");
+        return DPM_EINVAL;
+    }
+    *tile = simt_tile_choice(N, precision == DPM_PREC_FP64, B < 1 ? 1 : B);
     return DPM_OK;
 }
