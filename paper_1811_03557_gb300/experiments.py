@@ -151,6 +151,111 @@ def sd_dd_speedup(ctx, N_sd: int = 256, dd_grids=((128, 128), (128, 64)), T: flo
     return out
 
 
+def _mplus_mask(ctx, geom, N, lo, hi):
+    import types
+
+    import torch
+
+    from . import abi
+    lab = torch.empty(N ** 3, dtype=torch.uint8, device="cuda")
+    g = geom if not isinstance(geom, tuple) else types.SimpleNamespace(kind=geom[0], center=geom[1],
+                                                                       axes=geom[2])
+    abi.dpm_classify(ctx, g, N, lo, hi, labels=lab)
+    return (lab & abi.DPM_LBL_MPLUS) != 0
+
+
+def run_time_convergence(ctx, N: int = 128, dd_grids=((128, 128), (128, 64)), taus=(16, 32, 64, 128, 256),
+                         tau_ref: int = 512, dT: float = 1e-7, T: float = 1e-6, precision=None):
+    """Convergence in time for Test (A) (Section 4): fixed meshes, dt = dT/tau,
+    rho and c at the final time T against the run with dt = dT/tau_ref, the
+    error E_t = max over M^+ (of each sub-domain) of the difference, and the
+    rate log2(E_t(tau)/E_t(2 tau)).  The single domain runs on an N grid, the
+    domain decomposition (ball r < 0.25, shell 0.25 < r < 0.5) on each (N1, N2)
+    pair.  FP64 throughout: the differences reach 1e-12 of the values."""
+    import math
+
+    import torch
+
+    from . import abi
+    from .workloads import TEST_A_C0, TEST_A_RHO0, Geometry
+
+    if precision is None:
+        precision = abi.DPM_PREC_FP64
+    tdt = torch.float64 if precision == abi.DPM_PREC_FP64 else torch.float32
+    all_taus = sorted(set(taus) | {tau_ref})
+
+    def nsteps(tau):
+        return int(round(T * tau / dT))
+
+    def sd_final(tau):
+        lo, hi, h = paper_geometry_a(N)
+        prm = abi.pks_params(Geometry.sphere(0.5), N, lo, hi, 1.0, dT / tau, 0, 1, precision,
+                             dt_mode=0, rebuild=0, clamp=1)
+        pk = abi.dpm_pks_create(ctx, prm, TEST_A_RHO0, TEST_A_C0)
+        try:
+            abi.dpm_pks_step(pk, nsteps(tau), False)
+            st = abi.dpm_pks_step(pk, 0, True)
+            rho = torch.empty(N ** 3, dtype=tdt, device="cuda")
+            c = torch.empty_like(rho)
+            abi.dpm_pks_get_state(pk, rho, c)
+            torch.cuda.synchronize()
+        finally:
+            abi.dpm_pks_destroy(pk)
+        return st.t, [(rho.double(), c.double())]
+
+    def dd_final(N1, N2):
+        def run(tau):
+            r1, r2 = 0.25, 0.5
+            lo1, hi1, _ = paper_geometry_a(N1, r1)
+            lo2, hi2, _ = paper_geometry_a(N2, r2)
+            P = abi.dd_params((0.0, 0.0, 0.0), r1, r2, N1, lo1, hi1, N2, lo2, hi2, 0, 0, precision)
+            pk = abi.dpm_dd_pks_create(ctx, P, 1.0, dT / tau, 0, 0, 1, TEST_A_RHO0, TEST_A_C0)
+            out = []
+            try:
+                abi.dpm_dd_pks_step(pk, nsteps(tau), False)
+                st = abi.dpm_dd_pks_step(pk, 0, True)
+                for l, Nl in enumerate((N1, N2)):
+                    rho = torch.empty(Nl ** 3, dtype=tdt, device="cuda")
+                    c = torch.empty_like(rho)
+                    abi.dpm_dd_pks_get_state(pk, l, rho, c)
+                    out.append((rho.double(), c.double()))
+                torch.cuda.synchronize()
+            finally:
+                abi.dpm_dd_pks_destroy(pk)
+            return st.t, out
+        return run
+
+    def study(run, masks):
+        finals = {tau: run(tau) for tau in all_taus}
+        ref = finals[tau_ref][1]
+        rows = []
+        for tau in sorted(taus):
+            t, fields = finals[tau]
+            row = {"tau": tau, "dt": dT / tau, "steps": nsteps(tau), "t": t}
+            for l, ((rho, c), (rr, cr), m) in enumerate(zip(fields, ref, masks)):
+                row[f"E_rho_{l}"] = float(torch.max(torch.where(m, (rho - rr).abs(), 0.0)))
+                row[f"E_c_{l}"] = float(torch.max(torch.where(m, (c - cr).abs(), 0.0)))
+            rows.append(row)
+        for a, b in zip(rows, rows[1:]):
+            for k in [k for k in a if k.startswith("E_")]:
+                if a[k] > 0 and b[k] > 0:
+                    b["rate_" + k[2:]] = math.log2(a[k] / b[k])
+        return rows
+
+    lo, hi, _ = paper_geometry_a(N)
+    out = {"dT": dT, "T": T, "tau_ref": tau_ref, "precision": precision,
+           "sd": {"N": N, "rows": study(sd_final, [_mplus_mask(ctx, Geometry.sphere(0.5), N, lo, hi)])},
+           "dd": []}
+    for N1, N2 in dd_grids:
+        lo1, hi1, h1 = paper_geometry_a(N1, 0.25)
+        lo2, hi2, h2 = paper_geometry_a(N2, 0.5)
+        masks = [_mplus_mask(ctx, Geometry.sphere(0.25), N1, lo1, hi1),
+                 _mplus_mask(ctx, (2, (0.0, 0.0, 0.0), (0.5, 0.25, 0.0)), N2, lo2, hi2)]
+        out["dd"].append({"N1": N1, "N2": N2, "h1_over_h2": h1 / h2,
+                          "rows": study(dd_final(N1, N2), masks)})
+    return out
+
+
 def main(argv=None):
     import argparse
 
@@ -164,8 +269,14 @@ def main(argv=None):
     ap.add_argument("--out", default="")
     ap.add_argument("--speedup", action="store_true",
                     help="single domain (N) against the domain decomposition, R_S = T_SD/T_DD")
+    ap.add_argument("--time-convergence", action="store_true",
+                    help="convergence in time at fixed meshes (N, DD 128/128 and 128/64), FP64")
     a = ap.parse_args(argv)
     ctx = abi.dpm_ctx_create(0)
+    if a.time_convergence:
+        print(json.dumps(run_time_convergence(ctx, a.N)))
+        abi.dpm_ctx_destroy(ctx)
+        return
     if a.speedup:
         print(json.dumps(sd_dd_speedup(ctx, a.N, T=a.T)))
         abi.dpm_ctx_destroy(ctx)

@@ -166,3 +166,58 @@ def test_pks_solution_keeps_cube_symmetry(pks_run):
             assert np.allclose(arr, arr.transpose(perm), atol=1e-9 * scale)
         for ax in range(3):
             assert np.allclose(arr, np.flip(arr, axis=ax), atol=1e-9 * scale)
+
+
+def _time_errors(taus, tau_ref, N=16, dT=1e-7, T=1e-6):
+    """Test (A) on a fixed N = 16 mesh of the paper's geometry (sphere r = 0.5 in
+    [-r - 2h, r + 2h]^3), dt = dT/tau: max over M^+ of rho and c at time T
+    against the dt = dT/tau_ref run (the convergence-in-time protocol of
+    Section 4)."""
+    h = 1.0 / (N - 3)
+    lo, hi = -0.5 - 2 * h, 0.5 + 2 * h
+
+    def final(tau):
+        st = O.PKSState(Geometry.sphere(0.5), N, lo, hi, 0, 1, 1.0, dT / tau, rho0=TEST_A_RHO0,
+                        c0=TEST_A_C0, dt_mode="fixed", clamp=True)
+        for _ in range(int(round(T * tau / dT))):
+            st.step()
+        assert abs(st.t - T) < 1e-12 * T * tau
+        return st
+
+    ref = final(tau_ref)
+    m = ref.sets["Mp"]
+    out = []
+    for tau in taus:
+        s = final(tau)
+        out.append((np.max(np.abs(np.where(m, s.rho - ref.rho, 0.0))),
+                    np.max(np.abs(np.where(m, s.c - ref.c, 0.0)))))
+    return np.array(out)
+
+
+def test_first_order_in_time():
+    """The IMEX step is first order in dt: with E(tau) ~ C (1/tau - 1/tau_ref),
+    the rate log2(E(tau)/E(2 tau)) is log2((1 - 1/32)/(1/2 - 1/32)) = 1.047 for
+    tau = 1 -> 2 and log2((1/2 - 1/32)/(1/4 - 1/32)) = 1.100 for 2 -> 4 (the same
+    rise of the apparent rate as the reference nears, seen in Section 4's
+    tables), for rho and for c."""
+    E = _time_errors((1, 2, 4), 32)
+    rates = np.log2(E[:-1] / E[1:])
+    want = np.array([np.log2((1 - 1 / 32) / (1 / 2 - 1 / 32)), np.log2((1 / 2 - 1 / 32) / (1 / 4 - 1 / 32))])
+    np.testing.assert_allclose(rates[:, 0], want, atol=0.03)
+    np.testing.assert_allclose(rates[:, 1], want, atol=0.03)
+    assert 1e-7 < E[0, 0] / TEST_A_RHO0.amp < 1e-3     # the error is resolved, not rounding
+
+
+def test_planted_dt_mistake_breaks_time_convergence(monkeypatch):
+    """A flux that takes its dt from the base step dT instead of the current dt
+    (a plausible mistake) is inconsistent: the errors stop falling with dt."""
+    orig = O.pks_rhs
+
+    def wrong(rho, c, sets, h, chi, dt):
+        f_rho, _ = orig(rho, c, sets, h, chi, 1e-7)
+        _, f_c = orig(rho, c, sets, h, chi, dt)
+        return f_rho, f_c
+
+    monkeypatch.setattr(O, "pks_rhs", wrong)
+    E = _time_errors((1, 2), 8)
+    assert E[1, 0] > 0.8 * E[0, 0]
