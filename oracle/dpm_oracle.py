@@ -88,6 +88,8 @@ def inside_mask(geom, N, lo, hi) -> np.ndarray:
         outer = ellipsoid_form(_Sph(c, ro), X, Y, Z) < 1.0
         inner = ellipsoid_form(_Sph(c, ri), X, Y, Z) > 1.0
         return outer & inner
+    if geom.kind in (3, 4):
+        return _two_sphere_inside(geom, X, Y, Z)
     return ellipsoid_form(geom, X, Y, Z) < 1.0
 
 
@@ -552,6 +554,218 @@ def dd_elliptic_solve(setup: DDSetup, f1, f2, neumann2=None):
 
 
 # ---------------------------------------------------------------------------
+# Domain decomposition, Case 2 (Section 3): the interface Z meets Gamma.
+# Omega is the sphere |x - c| < R; Z is the sphere |x - c_Z| = r_Z with
+# c_Z = c + (0, 0, z_off); Omega_1 = Omega inside Z (a lens around the north
+# pole when z_off = R), Omega_2 = Omega outside Z.  Each sub-domain has its own
+# cubic box and grid, described in a local frame: global x = origin + local x,
+# the box is [lo, hi]^3 in local coordinates, and its geometry's centres are
+# the global ones minus the origin.
+# Reading of the grid boundary split (gamma_l, zeta_l of Section 3): a node of
+# sub-domain l's grid boundary (Definition 2.1 on Omega_l) belongs to gamma_l
+# when it is a grid-boundary node of the whole sphere Omega on the same grid,
+# and to zeta_l when it is a grid-boundary node of the ball inside Z; a node in
+# both lies in the layer at the wedge Z n Gamma and carries two values (the
+# "extra layer" of the paper's angle window is this one grid layer).  A node in
+# neither (possible only for nodes exactly on a sphere) is given to the nearer
+# surface.  Its effective density is the mean of its values; every node of
+# gamma_l,in gives one BEP row per surface it belongs to (eq. reduced_DD2_BEP).
+# Basis: zonal harmonics about the z axis through each surface's centre,
+# Y_nu(theta) = sqrt((2 nu + 1)/(4 pi)) P_nu(cos theta), nu < M (Section 4 uses
+# zonal harmonics), M_Z per term of the 3-term series on Z (u, du/dnu,
+# d2u/dnu2, nu = (x - c_Z)/|x - c_Z|, shared by both sub-domains) and M_G per
+# term of the 2-term series on Gamma (u, d2u/dn2; du/dn the Neumann data).
+# ---------------------------------------------------------------------------
+def zonal_harmonics(M: int, cos_theta: np.ndarray) -> np.ndarray:
+    """sqrt((2 nu + 1)/(4 pi)) P_nu(x), nu = 0..M-1, by Bonnet's recurrence
+    (nu + 1) P_{nu+1} = (2 nu + 1) x P_nu - nu P_{nu-1}.  Shape (len(x), M)."""
+    x = np.asarray(cos_theta, dtype=np.float64)
+    P = np.zeros((len(x), max(M, 1)))
+    P[:, 0] = 1.0
+    if M > 1:
+        P[:, 1] = x
+    for nu in range(1, M - 1):
+        P[:, nu + 1] = ((2 * nu + 1) * x * P[:, nu] - nu * P[:, nu - 1]) / (nu + 1)
+    norm = np.sqrt((2 * np.arange(M) + 1) / (4 * math.pi))
+    return P[:, :M] * norm
+
+
+class Lens:
+    """Omega_1 of Case 2: |x - c| < R and |x - c_Z| < r_Z, c_Z = c + (0, 0, z_off)
+    (kind 3; axes = (R, r_Z, z_off))."""
+
+    def __init__(self, R, r_z, z_off, center=(0.0, 0.0, 0.0)):
+        self.kind, self.center, self.axes = 3, tuple(center), (R, r_z, z_off)
+
+
+class OutsideZ:
+    """Omega_2 of Case 2: |x - c| < R and |x - c_Z| > r_Z (kind 4; axes as Lens)."""
+
+    def __init__(self, R, r_z, z_off, center=(0.0, 0.0, 0.0)):
+        self.kind, self.center, self.axes = 4, tuple(center), (R, r_z, z_off)
+
+
+def _z_centre(geom):
+    c = geom.center
+    return (c[0], c[1], c[2] + geom.axes[2])
+
+
+def _two_sphere_inside(geom, X, Y, Z):
+    R, rz, _ = geom.axes
+    inO = ellipsoid_form(_Sph(geom.center, R), X, Y, Z) < 1.0
+    fz = ellipsoid_form(_Sph(_z_centre(geom), rz), X, Y, Z)
+    return inO & ((fz < 1.0) if geom.kind == 3 else (fz > 1.0))
+
+
+def _radial(P, c):
+    """|p - c| summed as (qx^2 + qy^2) + qz^2, and q = p - c."""
+    q = P - np.asarray(c, dtype=np.float64)
+    return np.sqrt((q[:, 0] * q[:, 0] + q[:, 1] * q[:, 1]) + q[:, 2] * q[:, 2]), q
+
+
+class DD2Subdomain:
+    """Point sets, the gamma_l / zeta_l split, distances, zonal harmonics and
+    the BEP rows of one sub-domain of Case 2."""
+
+    def __init__(self, geom, N, lo, hi, origin, MZ, MG):
+        self.geom, self.N, self.lo, self.hi = geom, N, lo, hi
+        self.origin = np.asarray(origin, dtype=np.float64)
+        self.h = grid_spacing(N, lo, hi)
+        X, Y, Z = mesh(N, lo, hi)
+        self.sets = point_sets(inside_mask(geom, N, lo, hi))
+        self.labels = labels_from_sets(self.sets)
+        self.gamma_idx = np.flatnonzero(self.sets["gamma"].reshape(-1))
+        self.gin_idx = np.flatnonzero(self.sets["gin"].reshape(-1))
+        self.gin_pos = np.searchsorted(self.gamma_idx, self.gin_idx)
+        R, rz, _ = geom.axes
+        c0, cz = geom.center, _z_centre(geom)
+        on_g = point_sets(inside_mask(_Sph(c0, R), N, lo, hi))["gamma"].reshape(-1)[self.gamma_idx]
+        on_z = point_sets(inside_mask(_Sph(cz, rz), N, lo, hi))["gamma"].reshape(-1)[self.gamma_idx]
+        P = np.stack([X.reshape(-1)[self.gamma_idx], Y.reshape(-1)[self.gamma_idx],
+                      Z.reshape(-1)[self.gamma_idx]], axis=1)
+        rg, qg = _radial(P, c0)
+        rzz, qz = _radial(P, cz)
+        self.dG, self.dZ = rg - R, rzz - rz
+        neither = ~on_g & ~on_z
+        near_g = np.abs(self.dG) <= np.abs(self.dZ)
+        self.on_g = on_g | (neither & near_g)
+        self.on_z = on_z | (neither & ~near_g)
+        cnt = self.on_g.astype(np.float64) + self.on_z.astype(np.float64)
+        self.wG, self.wZ = self.on_g / cnt, self.on_z / cnt
+        self.phiG = zonal_harmonics(MG, qg[:, 2] / rg)
+        self.phiZ = zonal_harmonics(MZ, qz[:, 2] / rzz)
+        self.footG = np.asarray(c0) + R * (qg / rg[:, None])
+        self.footZ = np.asarray(cz) + rz * (qz / rzz[:, None])
+        self.normalG = qg / rg[:, None]
+        # rows: gamma_in nodes in ascending order; a Gamma row before a Z row
+        rows = []
+        for i, e in enumerate(self.gin_pos):
+            if self.on_g[e]:
+                rows.append((i, e, 0))
+            if self.on_z[e]:
+                rows.append((i, e, 1))
+        self.rows = np.array(rows, dtype=np.int64).reshape(-1, 3)
+
+    def value(self, k, surf, MZ, MG):
+        """Value of unknown k's basis density at every node of gamma_l as the
+        given surface's series (1 = Z, 0 = Gamma) would give it."""
+        if k < 3 * MZ:
+            if surf == 0:
+                return np.zeros(len(self.gamma_idx))
+            t, nu = divmod(k, MZ)
+            fac = (np.ones_like(self.dZ), self.dZ, 0.5 * self.dZ ** 2)[t]
+            return fac * self.phiZ[:, nu]
+        if surf == 1:
+            return np.zeros(len(self.gamma_idx))
+        t, nu = divmod(k - 3 * MZ, MG)
+        fac = (np.ones_like(self.dG), 0.5 * self.dG ** 2)[t]
+        return fac * self.phiG[:, nu]
+
+    def rows_minus_potential(self, own, eff, sigma):
+        """Row values own(surface of row)[node] - Tr P_{N+gamma} eff at the row's node."""
+        Pv = difference_potential(gamma_density_grid(eff, self.gamma_idx, self.N), self.sets, self.h, sigma)
+        tr = Pv.reshape(-1)[self.gin_idx]
+        i, e, sf = self.rows[:, 0], self.rows[:, 1], self.rows[:, 2]
+        return np.where(sf == 1, own[1][e], own[0][e]) - tr[i]
+
+
+class DD2Setup:
+    """Steps 1-2 of Case 2: both sub-domains, the stacked reduced BEPs
+    (eq. reduced_DD2_BEP, l = 1, 2) over the shared Z and Gamma series, and the
+    QR decomposition."""
+
+    def __init__(self, center, R, r_z, z_off, N1, lo1, hi1, origin1, N2, lo2, hi2, origin2, MZ, MG, sigma,
+                 build_bep=True):
+        self.R, self.r_z, self.z_off, self.MZ, self.MG, self.sigma = R, r_z, z_off, MZ, MG, sigma
+        self.ncol = 3 * MZ + 2 * MG
+        # the sphere's centre in each sub-domain's local frame
+        c1 = np.asarray(center, dtype=np.float64) - np.asarray(origin1, dtype=np.float64)
+        c2 = np.asarray(center, dtype=np.float64) - np.asarray(origin2, dtype=np.float64)
+        self.sub = [DD2Subdomain(Lens(R, r_z, z_off, tuple(c1)), N1, lo1, hi1, origin1, MZ, MG),
+                    DD2Subdomain(OutsideZ(R, r_z, z_off, tuple(c2)), N2, lo2, hi2, origin2, MZ, MG)]
+        if build_bep:
+            self.A = self.bep_matrix()
+            self.Q, self.R_ = np.linalg.qr(self.A)
+
+    def column(self, l, k):
+        sd = self.sub[l]
+        vz = sd.value(k, 1, self.MZ, self.MG)
+        vg = sd.value(k, 0, self.MZ, self.MG)
+        return (vg, vz), sd.wG * vg + sd.wZ * vz
+
+    def bep_matrix(self):
+        blocks = []
+        for l, sd in enumerate(self.sub):
+            cols = []
+            for k in range(self.ncol):
+                own, eff = self.column(l, k)
+                cols.append(sd.rows_minus_potential(own, eff, self.sigma))
+            blocks.append(np.stack(cols, axis=1))
+        return np.vstack(blocks)
+
+    def lstsq(self, b):
+        from scipy.linalg import solve_triangular
+        return solve_triangular(self.R_, self.Q.T @ b)
+
+    def densities(self, C, neumann=None, clamp=False):
+        """Effective density of each sub-domain from the coefficients: the mean of
+        the Gamma series value (+ d g_N) and the Z series value at wedge nodes."""
+        out = []
+        for l, sd in enumerate(self.sub):
+            ug = np.zeros(len(sd.gamma_idx))
+            uz = np.zeros(len(sd.gamma_idx))
+            for k in range(self.ncol):
+                ug += C[k] * sd.value(k, 0, self.MZ, self.MG)
+                uz += C[k] * sd.value(k, 1, self.MZ, self.MG)
+            if neumann is not None:
+                ug = ug + sd.dG * neumann[l]
+            u = sd.wG * ug + sd.wZ * uz
+            out.append(np.maximum(u, 0.0) if clamp else u)
+        return out
+
+
+def dd2_elliptic_solve(setup: DD2Setup, f1, f2, neumann=None):
+    """(sigma - Lap) u = f on Omega_1 + Omega_2 with du/dn = g_N on Gamma
+    (neumann[l]: g_N at the Gamma foot points of sub-domain l's grid boundary
+    nodes), by the stacked BEPs of Case 2 and Green's formula per sub-domain.
+    Returns (u1, u2, C)."""
+    G, b = [], []
+    for l, (sd, f) in enumerate(zip(setup.sub, (f1, f2))):
+        g = particular_solution(f, sd.sets, sd.h, setup.sigma)
+        bl = g.reshape(-1)[sd.gin_idx][sd.rows[:, 0]]
+        if neumann is not None:
+            vg = sd.dG * neumann[l]
+            bl = bl - sd.rows_minus_potential((vg, np.zeros_like(vg)), sd.wG * vg, setup.sigma)
+        G.append(g)
+        b.append(bl)
+    C = setup.lstsq(np.concatenate(b))
+    dens = setup.densities(C, neumann)
+    us = [g + difference_potential(gamma_density_grid(u, sd.gamma_idx, sd.N), sd.sets, sd.h, setup.sigma)
+          for g, u, sd in zip(G, dens, setup.sub)]
+    return us[0], us[1], C
+
+
+# ---------------------------------------------------------------------------
 # PKS discretisation (eqs. discrete_chemotaxis .. slope_limiter, cfl_condition)
 # ---------------------------------------------------------------------------
 def minmod(*xs):
@@ -774,6 +988,77 @@ class DDPKSState:
         and free energy; max / min over both."""
         parts = [diagnostics(r, c, sd.sets, sd.h, sd.N, sd.lo, sd.hi)
                  for r, c, sd in zip(self.rho, self.c, self.sub)]
+        return dict(mass=sum(p["mass"] for p in parts), max_rho=max(p["max_rho"] for p in parts),
+                    min_rho=min(p["min_rho"] for p in parts), min_c=min(p["min_c"] for p in parts),
+                    m2=sum(p["m2"] for p in parts), free_energy=sum(p["free_energy"] for p in parts))
+
+
+class DD2PKSState:
+    """Oracle of the time loop (Steps 3-7) on the two sub-domains of Case 2:
+    rho and c on each sub-domain's grid (local frames), Step 3's dt from the
+    smaller CFL bound of the two grids, the stacked BEP rebuilt whenever dt
+    changes, one least squares for the particular traces of both sub-domains
+    (wedge rows duplicated), effective densities clamped at 0."""
+
+    def __init__(self, center, R, r_z, z_off, N1, lo1, hi1, origin1, N2, lo2, hi2, origin2, MZ, MG, chi,
+                 dt_max, rho0, c0, dt_mode="cfl", clamp=True):
+        self.args = (center, R, r_z, z_off, N1, lo1, hi1, origin1, N2, lo2, hi2, origin2, MZ, MG)
+        self.chi, self.dt_max, self.dt_mode, self.clamp = chi, dt_max, dt_mode, clamp
+        base = DD2Setup(*self.args, 1.0 / dt_max, build_bep=False)
+        self.sub = base.sub
+        self.setup, self.dt, self.t = None, None, 0.0
+        self.rho, self.c = [], []
+        for sd in self.sub:
+            X, Y, Z = mesh(sd.N, sd.lo, sd.hi)
+            o = sd.origin
+            X, Y, Z = X + o[0], Y + o[1], Z + o[2]
+            r = np.where(sd.sets["Mp"], rho0(X, Y, Z), 0.0)
+            c = np.where(sd.sets["Mp"], c0(X, Y, Z), 0.0)
+            # gamma_ex: the data at the foot point on the node's first surface
+            # (Gamma when it belongs to gamma_l, else Z)
+            ex = sd.labels.reshape(-1)[sd.gamma_idx] & LBL_GEX > 0
+            xf = np.where(sd.on_g[:, None], sd.footG, sd.footZ)[ex] + o
+            r.reshape(-1)[sd.gamma_idx[ex]] = rho0(xf[:, 0], xf[:, 1], xf[:, 2])
+            c.reshape(-1)[sd.gamma_idx[ex]] = c0(xf[:, 0], xf[:, 1], xf[:, 2])
+            self.rho.append(r)
+            self.c.append(c)
+
+    def choose_dt(self):
+        if self.dt_mode == "fixed":
+            return self.dt_max
+        cand = min([self.dt_max] + [cfl_dt(c, sd.sets, sd.h, self.chi) for c, sd in zip(self.c, self.sub)])
+        return cand if self.dt is None else min(self.dt, cand)
+
+    def step(self):
+        dt = self.choose_dt()
+        if self.setup is None or dt != self.dt:
+            self.setup = DD2Setup(*self.args, 1.0 / dt)
+        self.dt = dt
+        S = self.setup
+        rhs = [pks_rhs(r, c, sd.sets, sd.h, self.chi, dt) for r, c, sd in zip(self.rho, self.c, S.sub)]
+        new = []
+        for f in range(2):  # rho, c
+            G = [particular_solution(rhs[l][f] / dt, sd.sets, sd.h, S.sigma) for l, sd in enumerate(S.sub)]
+            b = np.concatenate([G[l].reshape(-1)[sd.gin_idx][sd.rows[:, 0]] for l, sd in enumerate(S.sub)])
+            C = S.lstsq(b)
+            dens = S.densities(C, clamp=self.clamp)
+            new.append([G[l] + difference_potential(gamma_density_grid(dens[l], sd.gamma_idx, sd.N), sd.sets,
+                                                    sd.h, S.sigma) for l, sd in enumerate(S.sub)])
+        self.rho, self.c = new
+        self.t += dt
+        return dt
+
+    def diagnostics(self):
+        """Sums over both sub-domains of mass, second moment (global
+        coordinates: local + origin) and free energy; max / min over both."""
+        parts = []
+        for r, c, sd in zip(self.rho, self.c, self.sub):
+            d = diagnostics(r, c, sd.sets, sd.h, sd.N, sd.lo, sd.hi)
+            X, Y, Z = mesh(sd.N, sd.lo, sd.hi)
+            o = sd.origin
+            X, Y, Z = X + o[0], Y + o[1], Z + o[2]
+            d["m2"] = sd.h ** 3 * np.sum(np.where(sd.sets["Mp"], (X * X + Y * Y + Z * Z) * r, 0.0))
+            parts.append(d)
         return dict(mass=sum(p["mass"] for p in parts), max_rho=max(p["max_rho"] for p in parts),
                     min_rho=min(p["min_rho"] for p in parts), min_c=min(p["min_c"] for p in parts),
                     m2=sum(p["m2"] for p in parts), free_energy=sum(p["free_energy"] for p in parts))

@@ -1,0 +1,205 @@
+"""Pins of the oracle's domain decomposition, Case 2 (Section 3: the interface
+Z meets Gamma): Omega = sphere r < 0.5, Z = the sphere of radius 0.25 about the
+north pole (the geometry of Section 4's Case 2 runs), Omega_1 = the lens inside
+Z, Omega_2 = the rest, each on its own grid and box.  Pinned: the zonal
+harmonics against the library Legendre polynomials and orthonormality; the
+lens/outside sets against brute force; the Gamma / Z split against the
+distances it implies; the coupled solve against an axisymmetric manufactured
+solution, with the single-domain error on the same grid as the yardstick and
+second-order refinement; two planted mistakes (a flipped Z normal, no wedge
+averaging); and the invariants of the coupled time loop."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dpm_oracle as O
+from paper_1811_03557_gb300.workloads import Gaussian, Geometry
+
+R, RZ = 0.5, 0.25
+SIGMA = 1001.0
+
+
+def u_exact(X, Y, Z):
+    return np.exp(Z) * np.cos(X * X + Y * Y)
+
+
+def lap_exact(X, Y, Z):
+    q = X * X + Y * Y
+    return np.exp(Z) * ((1 - 4 * q) * np.cos(q) - 4 * np.sin(q))
+
+
+def grad_exact(X, Y, Z):
+    q = X * X + Y * Y
+    e = np.exp(Z)
+    return np.stack([-2 * X * e * np.sin(q), -2 * Y * e * np.sin(q), e * np.cos(q)], axis=-1)
+
+
+def boxes(N1, N2):
+    h1, h2 = 2 * RZ / (N1 - 3), 2 * R / (N2 - 3)
+    return (-RZ - 2 * h1, RZ + 2 * h1, (0.0, 0.0, R)), (-R - 2 * h2, R + 2 * h2, (0.0, 0.0, 0.0))
+
+
+def setup(N1, N2, MZ, MG, build=True):
+    (lo1, hi1, o1), (lo2, hi2, o2) = boxes(N1, N2)
+    return O.DD2Setup((0.0, 0.0, 0.0), R, RZ, R, N1, lo1, hi1, o1, N2, lo2, hi2, o2, MZ, MG, SIGMA,
+                      build_bep=build)
+
+
+def global_mesh(sd):
+    X, Y, Z = O.mesh(sd.N, sd.lo, sd.hi)
+    o = sd.origin
+    return X + o[0], Y + o[1], Z + o[2]
+
+
+def solve_errors(S):
+    fs, gn = [], []
+    for sd in S.sub:
+        X, Y, Z = global_mesh(sd)
+        fs.append(SIGMA * u_exact(X, Y, Z) - lap_exact(X, Y, Z))
+        xf = sd.footG + sd.origin
+        gn.append(np.sum(grad_exact(xf[:, 0], xf[:, 1], xf[:, 2]) * sd.normalG, axis=1))
+    u1, u2, _ = O.dd2_elliptic_solve(S, fs[0], fs[1], gn)
+    errs = []
+    for sd, u in zip(S.sub, (u1, u2)):
+        X, Y, Z = global_mesh(sd)
+        errs.append(float(np.max(np.abs(np.where(sd.sets["Mp"], u - u_exact(X, Y, Z), 0.0)))))
+    return errs
+
+
+def test_zonal_harmonics_against_library_and_orthonormality():
+    from scipy.special import eval_legendre
+    x = np.linspace(-1, 1, 37)
+    Y = O.zonal_harmonics(40, x)
+    for nu in (0, 1, 2, 7, 39):
+        np.testing.assert_allclose(Y[:, nu], math.sqrt((2 * nu + 1) / (4 * math.pi)) * eval_legendre(nu, x),
+                                   rtol=1e-12, atol=1e-13)
+    xg, wg = np.polynomial.legendre.leggauss(60)
+    Yg = O.zonal_harmonics(40, xg)
+    G = 2 * math.pi * (Yg * wg[:, None]).T @ Yg          # integral over the sphere
+    np.testing.assert_allclose(G, np.eye(40), atol=1e-12)
+
+
+def test_lens_and_outside_sets_against_brute_force():
+    N = 24
+    lo, hi = -0.6, 0.6
+    lens, out = O.Lens(R, RZ, R), O.OutsideZ(R, RZ, R)
+    X, Y, Z = O.mesh(N, lo, hi)
+    r0 = np.sqrt(X * X + Y * Y + Z * Z)
+    rz = np.sqrt(X * X + Y * Y + (Z - R) ** 2)
+    safe = (np.abs(r0 - R) > 1e-9) & (np.abs(rz - RZ) > 1e-9)
+    ml, mo = O.inside_mask(lens, N, lo, hi), O.inside_mask(out, N, lo, hi)
+    assert np.array_equal(ml[safe], ((r0 < R) & (rz < RZ))[safe])
+    assert np.array_equal(mo[safe], ((r0 < R) & (rz > RZ))[safe])
+    assert not np.any(ml & mo)
+
+
+@pytest.mark.parametrize("N1,N2", [(20, 20), (28, 20)])
+def test_split_of_the_grid_boundary(N1, N2):
+    S = setup(N1, N2, 4, 6, build=False)
+    for sd in S.sub:
+        h = sd.h
+        assert np.all(sd.on_g | sd.on_z)
+        # a Gamma node is within one cell of Gamma, a Z node within one cell of Z
+        assert np.all(np.abs(sd.dG[sd.on_g]) <= h * (1 + 1e-12))
+        assert np.all(np.abs(sd.dZ[sd.on_z]) <= h * (1 + 1e-12))
+        # the wedge layer: nodes near both spheres, i.e. near the circle Z n Gamma
+        w = sd.on_g & sd.on_z
+        assert 0 < np.count_nonzero(w) < 0.3 * len(w)
+        P = np.stack([O.mesh(sd.N, sd.lo, sd.hi)[t].reshape(-1)[sd.gamma_idx] for t in range(3)], axis=1)
+        c = np.asarray(sd.geom.center)
+        # the circle Z n Gamma: height zc = (2 R^2 - rz^2)/(2 R) above c, radius sqrt(R^2 - zc^2)
+        zc = (2 * R * R - RZ * RZ) / (2 * R)
+        ring_r = math.sqrt(R * R - zc * zc)
+        rho = np.sqrt((P[w, 0] - c[0]) ** 2 + (P[w, 1] - c[1]) ** 2)
+        dist_ring = np.sqrt((rho - ring_r) ** 2 + (P[w, 2] - c[2] - zc) ** 2)
+        assert np.all(dist_ring <= 2 * h)
+        # rows: one per surface of each gamma_in node
+        gin_flags = sd.on_g[sd.gin_pos].astype(int) + sd.on_z[sd.gin_pos].astype(int)
+        assert len(sd.rows) == int(gin_flags.sum())
+
+
+def _sd_error(N, K=8):
+    h = 2 * R / (N - 3)
+    lo, hi = -R - 2 * h, R + 2 * h
+    s = O.DPMSetup(Geometry.sphere(R), N, lo, hi, K, 1, SIGMA)
+    X, Y, Z = O.mesh(N, lo, hi)
+    gn = np.sum(grad_exact(s.xf[:, 0], s.xf[:, 1], s.xf[:, 2]) * s.normal, axis=1)
+    u, _, _ = O.dpm_elliptic_solve(s, SIGMA * u_exact(X, Y, Z) - lap_exact(X, Y, Z), gn)
+    return float(np.max(np.abs(np.where(s.sets["Mp"], u - u_exact(X, Y, Z), 0.0))))
+
+
+def test_dd2_elliptic_accuracy_and_refinement():
+    """(sigma - Lap) u = f with u = e^z cos(x^2 + y^2), du/dn on Gamma: the
+    coupled solve is as accurate on Omega_2's grid as the single-domain solve on
+    the same grid, more accurate in the finer lens, and second order under
+    refinement of both grids (h ratio 17/33: error ratio (17/33)^2 = 0.27)."""
+    e1, e2 = solve_errors(setup(20, 20, 6, 10))
+    esd = _sd_error(20)
+    assert e2 <= 1.2 * esd and esd < 1e-4
+    assert e1 < e2
+    f1, f2 = solve_errors(setup(36, 36, 6, 10))
+    assert f1 < 0.4 * e1 and f2 < 0.5 * e2
+
+
+def test_dd2_bep_structure():
+    S = setup(20, 20, 4, 6)
+    m1 = len(S.sub[0].rows)
+    assert S.A.shape == (m1 + len(S.sub[1].rows), S.ncol)
+    # every unknown acts on both sub-domains (Z and Gamma both bound each of them)
+    assert np.all(np.max(np.abs(S.A[:m1]), axis=0) > 0)
+    assert np.all(np.max(np.abs(S.A[m1:]), axis=0) > 0)
+    sv = np.linalg.svd(S.A / np.linalg.norm(S.A, axis=0), compute_uv=False)
+    assert sv[-1] > 0 and sv[0] / sv[-1] < 1e6
+
+
+def test_planted_flipped_z_normal_is_caught(monkeypatch):
+    """Flip the sign of s in Omega_2's Z series (its outward normal on Z points to
+    c_Z, a plausible mistake): the coupled solve loses all accuracy."""
+    e = solve_errors(setup(20, 20, 6, 10))
+    orig = O.DD2Subdomain.value
+
+    def flipped(self, k, surf, MZ, MG):
+        v = orig(self, k, surf, MZ, MG)
+        return -v if (MZ <= k < 2 * MZ and self.geom.kind == 4) else v
+
+    monkeypatch.setattr(O.DD2Subdomain, "value", flipped)
+    g = solve_errors(setup(20, 20, 6, 10))
+    assert max(g) > 1000 * max(e)
+
+
+def test_planted_missing_wedge_average_is_caught(monkeypatch):
+    """Give wedge nodes their Gamma value alone instead of the mean of both
+    values (the averaging of Section 3's remark): the lens loses accuracy."""
+    e1, _ = solve_errors(setup(20, 20, 6, 10))
+    orig = O.DD2Subdomain.__init__
+
+    def no_mean(self, *a, **k):
+        orig(self, *a, **k)
+        both = self.on_g & self.on_z
+        self.wG = np.where(both, 1.0, self.wG)
+        self.wZ = np.where(both, 0.0, self.wZ)
+
+    monkeypatch.setattr(O.DD2Subdomain, "__init__", no_mean)
+    g1, _ = solve_errors(setup(20, 20, 6, 10))
+    assert g1 > 1.3 * e1
+
+
+def test_dd2_pks_invariants():
+    """Four steps of the coupled time loop from smooth data straddling Z
+    (rho0 = 200 exp(-20 |x - (0, 0, 0.25)|^2), c0 = 0): non-negative density,
+    decreasing free energy, growing second moment, mass conserved to 5e-3."""
+    (lo1, hi1, o1), (lo2, hi2, o2) = boxes(20, 20)
+    h = min(2 * RZ / 17, 2 * R / 17)
+    st = O.DD2PKSState((0.0, 0.0, 0.0), R, RZ, R, 20, lo1, hi1, o1, 20, lo2, hi2, o2, 6, 6, 1.0, 0.5 * h * h,
+                       Gaussian(200.0, 20.0, (0.0, 0.0, 0.25)), Gaussian(0.0, 1.0))
+    d0 = st.diagnostics()
+    prev = d0
+    for _ in range(4):
+        st.step()
+        d = st.diagnostics()
+        assert d["min_rho"] >= -1e-9 * d["max_rho"]
+        assert d["free_energy"] < prev["free_energy"]
+        assert d["m2"] > prev["m2"]
+        prev = d
+    assert abs(prev["mass"] - d0["mass"]) < 5e-3 * d0["mass"]
