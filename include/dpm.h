@@ -68,7 +68,10 @@ typedef struct dpm_pks dpm_pks;
 /* Domain Omega.  kind 0: sphere |x - center| < axes[0] (axes[1], axes[2]
  * ignored); kind 1: ellipsoid sum ((x_i - center_i)/axes_i)^2 < 1; kind 2:
  * spherical shell axes[1] < |x - center| < axes[0] (the sub-domain of the
- * domain decomposition; the forms of both spheres are tested as below).
+ * domain decomposition; the forms of both spheres are tested as below);
+ * kinds 3 and 4: the sphere |x - center| < axes[0] inside (3) or outside (4)
+ * the sphere of radius axes[1] about center + (0, 0, axes[2]) (the sub-domains
+ * of the domain decomposition whose interface meets Gamma).
  * Membership is decided in IEEE double with the fixed order
  * ((tx*tx + ty*ty) + tz*tz) < 1, t_i = (x_i - c_i)/a_i, so that the integer
  * point sets are reproducible bit for bit. */
@@ -402,6 +405,95 @@ int dpm_dd_pks_step(dpm_dd_pks *pks, int nsteps, dpm_pks_stats *stats, cudaStrea
 /* State of sub-domain l (0: ball, 1: shell) into device [N_l^3] arrays. */
 int dpm_dd_pks_get_state(dpm_dd_pks *pks, int l, void *rho, void *c, cudaStream_t stream);
 int dpm_dd_pks_destroy(dpm_dd_pks *pks);
+
+/* ---- domain decomposition, Case 2 (Section 3: the interface meets Gamma) -----
+ * Omega = sphere |x - center| < R; the interface Z is the sphere |x - c_Z| = rz,
+ * c_Z = center + (0, 0, zoff), with |R - rz| < |zoff| < R + rz so that Z cuts
+ * Gamma.  Omega_1 = Omega inside Z (classified as dpm_geom kind 3: axes = (R, rz,
+ * zoff)), Omega_2 = Omega outside Z (kind 4, same axes).  Sub-domain l has its
+ * own box, the cube origin_l + [lo_l, hi_l]^3 (global coordinates; the grid and
+ * every per-node output are in the local frame x - origin_l), N_l interior nodes
+ * per axis.
+ * Grid-boundary split (gamma_l and zeta_l, Section 3): a grid-boundary node of
+ * Omega_l (Definition 2.1 on Omega_l's own point sets) is a Gamma node when it is
+ * a grid-boundary node of the sphere Omega on the same grid, a Z node when it is
+ * one of the ball inside Z, both in the one-layer wedge where Z meets Gamma
+ * (a node in neither, possible only for a node exactly on a sphere, goes to the
+ * nearer surface).  A wedge node's density is the mean of its Gamma value and
+ * its Z value, and each node of gamma_in gives one BEP row per surface it
+ * belongs to (eq. reduced_DD2_BEP; rows: Omega_1's gamma_in nodes in ascending
+ * order, a Gamma row before a Z row, then Omega_2's).
+ * Unknowns: zonal harmonics Y_nu(theta) = sqrt((2 nu + 1)/(4 pi)) P_nu(cos theta),
+ * nu < M, theta the polar angle about each sphere's centre from +z: three series
+ * of MZ terms on Z (u, du/dnu, d2u/dnu2, nu = (x - c_Z)/|x - c_Z|, shared by both
+ * sub-domains) then two of MG terms on Gamma (u, d2u/dn2; du/dn is the Neumann
+ * data).  On Z the argument of P_nu is cos theta_Z mapped from the range that
+ * the part of Z inside Omega spans ([-1, c*] for zoff > 0, [c*, 1] otherwise, c*
+ * = (R^2 - zoff^2 - rz^2)/(2 zoff rz)) to [-1, 1]: the same polynomials of degree
+ * < MZ in cos theta_Z, in a basis that stays well conditioned on the partial
+ * sphere.  Columns: term-major, Z first.  The problem must be symmetric about
+ * the z axis through both centres for the zonal basis to represent it.  The
+ * least squares use the FP64 Gram of the column-equilibrated matrix.
+ * MZ in [1, 64], MG in [1, 1024]; N_l <= 256; precision as for Case 1. */
+typedef struct dpm_dd2 dpm_dd2;
+typedef struct dpm_dd2_pks dpm_dd2_pks;
+
+typedef struct {
+    double center[3];
+    double R, rz, zoff;
+    int N1;
+    double lo1, hi1, origin1[3];  /* Omega_1 (inside Z) */
+    int N2;
+    double lo2, hi2, origin2[3];  /* Omega_2 (outside Z) */
+    int MZ, MG;
+    int precision;
+} dpm_dd2_params;
+
+typedef struct {
+    int N[2];
+    double h[2];
+    int precision[2];
+    int64_t n_mplus[2], n_gin[2], n_gamma[2];
+    int64_t n_rows[2];            /* BEP rows of each sub-domain */
+    int64_t n_wedge[2];           /* grid-boundary nodes on both surfaces */
+    int ncol;
+    double sigma;
+} dpm_dd2_info;
+
+/* Steps 1-2 for both sub-domains at shift sigma (synchronises). */
+int dpm_dd2_build(dpm_ctx *ctx, const dpm_dd2_params *params, double sigma, dpm_dd2 **out,
+                  cudaStream_t stream);
+int dpm_dd2_get_info(const dpm_dd2 *dd, dpm_dd2_info *info);
+/* The stacked BEP matrix: device double[(n_rows[0] + n_rows[1]) * ncol], column-major. */
+int dpm_dd2_matrix(dpm_dd2 *dd, double *A, cudaStream_t stream);
+/* Grid boundary of sub-domain l: ascending linear node indices (int32[n_gamma]),
+ * surface flags (uint8: bit 0 Gamma, bit 1 Z) and the foot points on Gamma in
+ * the local frame (double[n_gamma][3]).  Any pointer may be NULL.  Device. */
+int dpm_dd2_gamma(dpm_dd2 *dd, int l, int32_t *gamma_idx, uint8_t *flags, double *foot_gamma,
+                  cudaStream_t stream);
+/*
+ * (sigma - Lap) u = f on Omega_1 + Omega_2 with du/dn = g_N on Gamma: f1 / f2
+ * device [N1^3] / [N2^3] (float, or double for DPM_PREC_FP64) used on M^+;
+ * neumann1 / neumann2 device double[n_gamma[l]]: g_N at the Gamma foot points of
+ * sub-domain l's grid-boundary nodes (read on its Gamma nodes), or NULL for zero;
+ * u1 / u2 device outputs valid on N^+ of each sub-domain; coeffs device
+ * double[ncol] or NULL.
+ */
+int dpm_dd2_solve(dpm_dd2 *dd, const void *f1, const void *f2, const double *neumann1,
+                  const double *neumann2, void *u1, void *u2, double *coeffs, cudaStream_t stream);
+int dpm_dd2_destroy(dpm_dd2 *dd);
+
+/* PKS time stepping on the two sub-domains of Case 2 (as dpm_dd_pks_*, zero
+ * Neumann data; rho0 / c0 in global coordinates; the gamma_ex nodes take the
+ * data at their foot point on Gamma, or on Z for Z-only nodes; the clamp
+ * u_gamma >= 0 acts on the effective densities; the second moment is taken in
+ * global coordinates). */
+int dpm_dd2_pks_create(dpm_ctx *ctx, const dpm_dd2_params *params, double chi, double dt_max,
+                       int dt_mode, int rebuild, int clamp, const dpm_gaussian *rho0,
+                       const dpm_gaussian *c0, dpm_dd2_pks **out, cudaStream_t stream);
+int dpm_dd2_pks_step(dpm_dd2_pks *pks, int nsteps, dpm_pks_stats *stats, cudaStream_t stream);
+int dpm_dd2_pks_get_state(dpm_dd2_pks *pks, int l, void *rho, void *c, cudaStream_t stream);
+int dpm_dd2_pks_destroy(dpm_dd2_pks *pks);
 
 #ifdef __cplusplus
 }

@@ -572,7 +572,9 @@ def dd_elliptic_solve(setup: DDSetup, f1, f2, neumann2=None):
 # gamma_l,in gives one BEP row per surface it belongs to (eq. reduced_DD2_BEP).
 # Basis: zonal harmonics about the z axis through each surface's centre,
 # Y_nu(theta) = sqrt((2 nu + 1)/(4 pi)) P_nu(cos theta), nu < M (Section 4 uses
-# zonal harmonics), M_Z per term of the 3-term series on Z (u, du/dnu,
+# zonal harmonics; on Z the cosine is first mapped from the range the part of Z
+# inside Omega spans to [-1, 1], the same polynomials in a basis that stays
+# well conditioned there), M_Z per term of the 3-term series on Z (u, du/dnu,
 # d2u/dnu2, nu = (x - c_Z)/|x - c_Z|, shared by both sub-domains) and M_G per
 # term of the 2-term series on Gamma (u, d2u/dn2; du/dn the Neumann data).
 # ---------------------------------------------------------------------------
@@ -652,11 +654,21 @@ class DD2Subdomain:
         self.on_z = on_z | (neither & ~near_g)
         cnt = self.on_g.astype(np.float64) + self.on_z.astype(np.float64)
         self.wG, self.wZ = self.on_g / cnt, self.on_z / cnt
-        self.phiG = zonal_harmonics(MG, qg[:, 2] / rg)
-        self.phiZ = zonal_harmonics(MZ, qz[:, 2] / rzz)
-        self.footG = np.asarray(c0) + R * (qg / rg[:, None])
-        self.footZ = np.asarray(cz) + rz * (qz / rzz[:, None])
-        self.normalG = qg / rg[:, None]
+        # a node at a sphere's centre carries no value of that sphere (cosine 1)
+        rg1, rz1 = np.where(rg > 0, rg, 1.0), np.where(rzz > 0, rzz, 1.0)
+        cos_g = np.where(rg > 0, qg[:, 2] / rg1, 1.0)
+        cos_z = np.where(rzz > 0, qz[:, 2] / rz1, 1.0)
+        self.phiG = zonal_harmonics(MG, cos_g)
+        # Z inside Omega spans cos theta_Z in [-1, c*] (z_off > 0; [c*, 1] otherwise),
+        # c* the cosine at the circle Z n Gamma; its series uses P_nu of cos theta_Z
+        # mapped from that range to [-1, 1] (the same polynomials of degree < MZ)
+        zoff = geom.axes[2]
+        cstar = (R * R - zoff * zoff - rz * rz) / (2.0 * zoff * rz)
+        a, b = (-1.0, cstar) if zoff > 0 else (cstar, 1.0)
+        self.phiZ = zonal_harmonics(MZ, (2.0 * cos_z - (a + b)) / (b - a))
+        self.footG = np.asarray(c0) + R * (qg / rg1[:, None])
+        self.footZ = np.asarray(cz) + rz * (qz / rz1[:, None])
+        self.normalG = qg / rg1[:, None]
         # rows: gamma_in nodes in ascending order; a Gamma row before a Z row
         rows = []
         for i, e in enumerate(self.gin_pos):

@@ -71,6 +71,20 @@ class dpm_dd_info(C.Structure):
                 ("nz", C.c_int), ("ng", C.c_int), ("ncol", C.c_int), ("sigma", C.c_double)]
 
 
+class dpm_dd2_params(C.Structure):
+    _fields_ = [("center", C.c_double * 3), ("R", C.c_double), ("rz", C.c_double), ("zoff", C.c_double),
+                ("N1", C.c_int), ("lo1", C.c_double), ("hi1", C.c_double), ("origin1", C.c_double * 3),
+                ("N2", C.c_int), ("lo2", C.c_double), ("hi2", C.c_double), ("origin2", C.c_double * 3),
+                ("MZ", C.c_int), ("MG", C.c_int), ("precision", C.c_int)]
+
+
+class dpm_dd2_info(C.Structure):
+    _fields_ = [("N", C.c_int * 2), ("h", C.c_double * 2), ("precision", C.c_int * 2),
+                ("n_mplus", C.c_int64 * 2), ("n_gin", C.c_int64 * 2), ("n_gamma", C.c_int64 * 2),
+                ("n_rows", C.c_int64 * 2), ("n_wedge", C.c_int64 * 2), ("ncol", C.c_int),
+                ("sigma", C.c_double)]
+
+
 _P = C.c_void_p
 _SIGS = {
     "dpm_last_error": (C.c_char_p, []),
@@ -113,6 +127,18 @@ _SIGS = {
     "dpm_dd_pks_step": (C.c_int, [_P, C.c_int, C.POINTER(dpm_pks_stats), _P]),
     "dpm_dd_pks_get_state": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "dpm_dd_pks_destroy": (C.c_int, [_P]),
+    "dpm_dd2_build": (C.c_int, [_P, C.POINTER(dpm_dd2_params), C.c_double, C.POINTER(C.c_void_p), _P]),
+    "dpm_dd2_get_info": (C.c_int, [_P, C.POINTER(dpm_dd2_info)]),
+    "dpm_dd2_matrix": (C.c_int, [_P, _P, _P]),
+    "dpm_dd2_gamma": (C.c_int, [_P, C.c_int, _P, _P, _P, _P]),
+    "dpm_dd2_solve": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "dpm_dd2_destroy": (C.c_int, [_P]),
+    "dpm_dd2_pks_create": (C.c_int, [_P, C.POINTER(dpm_dd2_params), C.c_double, C.c_double, C.c_int,
+                                     C.c_int, C.c_int, C.POINTER(dpm_gaussian), C.POINTER(dpm_gaussian),
+                                     C.POINTER(C.c_void_p), _P]),
+    "dpm_dd2_pks_step": (C.c_int, [_P, C.c_int, C.POINTER(dpm_pks_stats), _P]),
+    "dpm_dd2_pks_get_state": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "dpm_dd2_pks_destroy": (C.c_int, [_P]),
     "dpm_launch_count": (C.c_int64, []),
     "dpm_profile_enable": (C.c_int, [C.c_int]),
     "dpm_profile_read": (C.c_int, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
@@ -401,3 +427,67 @@ def dpm_profile_read(name: str | None = None):
 
 def dpm_profile_reset():
     _check(lib().dpm_profile_reset())
+
+
+# ---- domain decomposition, Case 2 (interface meeting Gamma) -------------------------
+def dd2_params(center, R, rz, zoff, N1, lo1, hi1, origin1, N2, lo2, hi2, origin2, MZ, MG,
+               precision=DPM_PREC_FP32) -> dpm_dd2_params:
+    p = dpm_dd2_params()
+    for t in range(3):
+        p.center[t], p.origin1[t], p.origin2[t] = center[t], origin1[t], origin2[t]
+    p.R, p.rz, p.zoff = R, rz, zoff
+    p.N1, p.lo1, p.hi1, p.N2, p.lo2, p.hi2 = N1, lo1, hi1, N2, lo2, hi2
+    p.MZ, p.MG, p.precision = MZ, MG, precision
+    return p
+
+
+def dpm_dd2_build(ctx, params: dpm_dd2_params, sigma, stream=None):
+    h = C.c_void_p()
+    _check(lib().dpm_dd2_build(ctx, C.byref(params), sigma, C.byref(h), _stream(stream)))
+    return h
+
+
+def dpm_dd2_get_info(dd) -> dpm_dd2_info:
+    info = dpm_dd2_info()
+    _check(lib().dpm_dd2_get_info(dd, C.byref(info)))
+    return info
+
+
+def dpm_dd2_matrix(dd, A, stream=None):
+    _check(lib().dpm_dd2_matrix(dd, _ptr(A), _stream(stream)))
+
+
+def dpm_dd2_gamma(dd, l, gamma_idx=None, flags=None, foot_gamma=None, stream=None):
+    _check(lib().dpm_dd2_gamma(dd, l, _ptr(gamma_idx), _ptr(flags), _ptr(foot_gamma), _stream(stream)))
+
+
+def dpm_dd2_solve(dd, f1, f2, u1, u2, neumann1=None, neumann2=None, coeffs=None, stream=None):
+    _check(lib().dpm_dd2_solve(dd, _ptr(f1), _ptr(f2), _ptr(neumann1), _ptr(neumann2), _ptr(u1), _ptr(u2),
+                               _ptr(coeffs), _stream(stream)))
+
+
+def dpm_dd2_destroy(dd):
+    _check(lib().dpm_dd2_destroy(dd))
+
+
+def dpm_dd2_pks_create(ctx, params: dpm_dd2_params, chi, dt_max, dt_mode, rebuild, clamp, rho0, c0,
+                       stream=None):
+    h = C.c_void_p()
+    g0, g1 = make_gaussian(rho0), make_gaussian(c0)
+    _check(lib().dpm_dd2_pks_create(ctx, C.byref(params), chi, dt_max, dt_mode, rebuild, clamp, C.byref(g0),
+                                    C.byref(g1), C.byref(h), _stream(stream)))
+    return h
+
+
+def dpm_dd2_pks_step(pks, nsteps=1, want_stats=True, stream=None):
+    st = dpm_pks_stats()
+    _check(lib().dpm_dd2_pks_step(pks, nsteps, C.byref(st) if want_stats else None, _stream(stream)))
+    return st if want_stats else None
+
+
+def dpm_dd2_pks_get_state(pks, l, rho, c, stream=None):
+    _check(lib().dpm_dd2_pks_get_state(pks, l, _ptr(rho), _ptr(c), _stream(stream)))
+
+
+def dpm_dd2_pks_destroy(pks):
+    _check(lib().dpm_dd2_pks_destroy(pks))

@@ -75,7 +75,7 @@ int pks_flux(int, double, double, double, const double *, const uint8_t *, const
 template <class T> int pks_cfl(int, const uint8_t *, const T *, unsigned int *, cudaStream_t);
 template <class T>
 int pks_diag(int, double, double, const uint8_t *, const T *, const T *, double *, double *,
-             cudaStream_t);
+             cudaStream_t, const double *origin = nullptr);
 int pks_diag_blocks(int N);
 template <class T>
 int pks_init(const GridIndex &, const GammaGeom &, const dpm_gaussian &, const dpm_gaussian &,
@@ -1374,6 +1374,514 @@ extern "C" int dpm_dd_pks_get_state(dpm_dd_pks *k, int l, void *rho, void *c, cu
 }
 
 extern "C" int dpm_dd_pks_destroy(dpm_dd_pks *k) {
+    delete k;
+    return DPM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Domain decomposition, Case 2 (Section 3): the interface Z (a sphere about
+// center + (0, 0, zoff)) meets Gamma.  Omega_1 = Omega inside Z, Omega_2 =
+// Omega outside Z, each on its own grid in its own frame; the grid boundary of
+// each splits into Gamma nodes, Z nodes and the wedge layer carrying both
+// (eq. reduced_DD2_BEP); the Z and Gamma zonal series are shared by both
+// sub-domains and the stacked reduced BEPs solved in the least-squares sense.
+// ---------------------------------------------------------------------------
+namespace {
+struct DD2Sub {
+    int N = 0, prec = 0;
+    double lo = 0, hi = 0, origin[3] = {0, 0, 0};
+    dpm_geom geom{};
+    GridIndex gi;
+    int64_t n_rows = 0, n_wedge = 0;
+    DevBuf flags, dG, dZ, cosG, cosZ, footG, footZ, YG, YZ;
+    DevBuf row_i, row_e, row_s;
+    DevBuf psi, own, trace, dens, vG, work, desc;
+    GammaGeom init_geom;                                   // foot points for the initial data
+    DevBuf rho, c, frho, fc, gmax, diag_part, diag_out;    // time-loop state
+};
+}  // namespace
+
+struct dpm_dd2 {
+    dpm_ctx *ctx = nullptr;
+    dpm_dd2_params prm{};
+    DD2Sub sub[2];
+    int ncol = 0, storage = 0;
+    double sigma = 0;
+    bool factored = false;
+    LsqFactor lsq;
+    DevBuf coef, bvec;
+};
+
+struct dpm_dd2_pks {
+    dpm_dd2 dd;
+    double chi = 0, dt_max = 0;
+    int dt_mode = 0, rebuild = 0, clamp = 1;
+    double t = 0, dt_prev = 0;
+    int64_t step = 0;
+    int last_rebuilt = 0;
+};
+
+namespace {
+
+ApParams dd2_ap(const DD2Sub &sd, double sigma) {
+    ApParams p;
+    p.N = sd.N;
+    p.h = sd.gi.h;
+    p.sigma = sigma;
+    ap_params_from_index(p, sd.gi);
+    return p;
+}
+
+int dd2_check(const dpm_dd2_params *P) {
+    if (!P) { set_error("params is NULL"); return DPM_EINVAL; }
+    if (!(P->R > 0 && P->rz > 0)) { set_error("need R > 0, rz > 0"); return DPM_EINVAL; }
+    const double az = std::fabs(P->zoff);
+    if (!(az > std::fabs(P->R - P->rz) && az < P->R + P->rz)) {
+        set_error("Case 2 needs |R - rz| < |zoff| < R + rz (Z must cut Gamma)");
+        return DPM_EINVAL;
+    }
+    if (P->MZ < 1 || P->MZ > 64 || P->MG < 1 || P->MG > 1024) {
+        set_error("MZ in [1, 64], MG in [1, 1024]");
+        return DPM_EINVAL;
+    }
+    if (!prec_ok(P->precision)) { set_error("unknown precision %d", P->precision); return DPM_EINVAL; }
+    if (P->N1 > 256 || P->N2 > 256) { set_error("N1, N2 <= 256"); return DPM_EINVAL; }
+    return DPM_OK;
+}
+
+template <class T> int dd2_init(dpm_dd2 *d, dpm_ctx *ctx, const dpm_dd2_params &P, cudaStream_t s) {
+    d->ctx = ctx;
+    d->prm = P;
+    d->storage = P.precision == DPM_PREC_FP64 ? DPM_PREC_FP64 : DPM_PREC_FP32;
+    const int MZ = P.MZ, MG = P.MG;
+    d->ncol = 3 * MZ + 2 * MG;
+    for (int l = 0; l < 2; ++l) {
+        DD2Sub &sd = d->sub[l];
+        const double *org = l == 0 ? P.origin1 : P.origin2;
+        for (int t = 0; t < 3; ++t) sd.origin[t] = org[t];
+        sd.geom.kind = l == 0 ? 3 : 4;
+        for (int t = 0; t < 3; ++t) sd.geom.center[t] = P.center[t] - org[t];
+        sd.geom.axes[0] = P.R;
+        sd.geom.axes[1] = P.rz;
+        sd.geom.axes[2] = P.zoff;
+        sd.N = l == 0 ? P.N1 : P.N2;
+        sd.lo = l == 0 ? P.lo1 : P.lo2;
+        sd.hi = l == 0 ? P.hi1 : P.hi2;
+        sd.prec = dd_sub_prec(P.precision, sd.N);
+        DPM_RET(build_grid_index(sd.geom, sd.N, sd.lo, sd.hi, sd.gi, s));
+        const int64_t n = sd.gi.n_gamma, g = sd.gi.n_gin;
+        const int64_t n3 = (int64_t)sd.N * sd.N * sd.N;
+        // the grid-boundary sets of the whole sphere and of the ball inside Z
+        const double c0[3] = {sd.geom.center[0], sd.geom.center[1], sd.geom.center[2]};
+        const double cz[3] = {c0[0], c0[1], c0[2] + P.zoff};
+        dpm_geom go{}, gb{};
+        go.kind = gb.kind = 0;
+        for (int t = 0; t < 3; ++t) {
+            go.center[t] = c0[t];
+            gb.center[t] = cz[t];
+            go.axes[t] = P.R;
+            gb.axes[t] = P.rz;
+        }
+        DevBuf lab_o, lab_b;
+        DPM_RET(lab_o.alloc(n3));
+        DPM_RET(lab_b.alloc(n3));
+        DPM_RET(classify_labels(go, sd.N, sd.lo, sd.hi, lab_o.as<uint8_t>(), s));
+        DPM_RET(classify_labels(gb, sd.N, sd.lo, sd.hi, lab_b.as<uint8_t>(), s));
+        const int64_t n1 = std::max<int64_t>(n, 1);
+        DPM_RET(sd.flags.alloc(n1));
+        DPM_RET(sd.dG.alloc(sizeof(double) * n1));
+        DPM_RET(sd.dZ.alloc(sizeof(double) * n1));
+        DPM_RET(sd.cosG.alloc(sizeof(double) * n1));
+        DPM_RET(sd.cosZ.alloc(sizeof(double) * n1));
+        DPM_RET(sd.footG.alloc(sizeof(double) * 3 * n1));
+        DPM_RET(sd.footZ.alloc(sizeof(double) * 3 * n1));
+        DPM_RET(dd2_split(sd.gi, lab_o.as<uint8_t>(), lab_b.as<uint8_t>(), c0, P.R, cz, P.rz,
+                          sd.flags.as<uint8_t>(), sd.dG.as<double>(), sd.dZ.as<double>(), sd.cosG.as<double>(),
+                          sd.cosZ.as<double>(), sd.footG.as<double>(), sd.footZ.as<double>(), s));
+        DPM_RET(sd.YG.alloc(sizeof(double) * MG * n1));
+        DPM_RET(sd.YZ.alloc(sizeof(double) * MZ * n1));
+        // Z inside Omega spans cos theta_Z in [-1, c*] (zoff > 0) or [c*, 1], c* the
+        // cosine at the circle Z n Gamma: (R^2 - zoff^2 - rz^2)/(2 zoff rz)
+        const double cstar = (P.R * P.R - P.zoff * P.zoff - P.rz * P.rz) / (2.0 * P.zoff * P.rz);
+        const double za = P.zoff > 0 ? -1.0 : cstar, zb = P.zoff > 0 ? cstar : 1.0;
+        DPM_RET(dd2_zonal(n, MG, sd.cosG.as<double>(), -1.0, 1.0, sd.YG.as<double>(), s));
+        DPM_RET(dd2_zonal(n, MZ, sd.cosZ.as<double>(), za, zb, sd.YZ.as<double>(), s));
+        // BEP rows: gamma_in nodes in ascending order, a Gamma row before a Z row
+        std::vector<uint8_t> hf(n);
+        std::vector<int> hpos(g);
+        if (n) DPM_CUDA(cudaMemcpyAsync(hf.data(), sd.flags.p, n, cudaMemcpyDeviceToHost, s));
+        if (g) DPM_CUDA(cudaMemcpyAsync(hpos.data(), sd.gi.gin_pos.p, sizeof(int) * g, cudaMemcpyDeviceToHost, s));
+        DPM_CUDA(cudaStreamSynchronize(s));
+        std::vector<int> ri, re;
+        std::vector<uint8_t> rs;
+        sd.n_wedge = 0;
+        for (int64_t e = 0; e < n; ++e) sd.n_wedge += hf[e] == 3;
+        for (int64_t i = 0; i < g; ++i) {
+            const int e = hpos[i];
+            if (hf[e] & 1) { ri.push_back((int)i); re.push_back(e); rs.push_back(0); }
+            if (hf[e] & 2) { ri.push_back((int)i); re.push_back(e); rs.push_back(1); }
+        }
+        sd.n_rows = (int64_t)ri.size();
+        const int64_t m1 = std::max<int64_t>(sd.n_rows, 1);
+        DPM_RET(sd.row_i.alloc(sizeof(int) * m1));
+        DPM_RET(sd.row_e.alloc(sizeof(int) * m1));
+        DPM_RET(sd.row_s.alloc(m1));
+        if (sd.n_rows) {
+            DPM_CUDA(cudaMemcpyAsync(sd.row_i.p, ri.data(), sizeof(int) * sd.n_rows, cudaMemcpyHostToDevice, s));
+            DPM_CUDA(cudaMemcpyAsync(sd.row_e.p, re.data(), sizeof(int) * sd.n_rows, cudaMemcpyHostToDevice, s));
+            DPM_CUDA(cudaMemcpyAsync(sd.row_s.p, rs.data(), sd.n_rows, cudaMemcpyHostToDevice, s));
+        }
+        DPM_RET(sd.psi.alloc(sizeof(T) * d->ncol * n1));
+        DPM_RET(sd.own.alloc(sizeof(double) * d->ncol * m1));
+        DPM_RET(dd2_columns<T>(n, sd.n_rows, MZ, MG, sd.flags.as<uint8_t>(), sd.dG.as<double>(), sd.dZ.as<double>(),
+                               sd.YG.as<double>(), sd.YZ.as<double>(), sd.row_e.as<int>(), sd.row_s.as<uint8_t>(),
+                               sd.psi.as<T>(), sd.own.as<double>(), s));
+        DPM_RET(sd.trace.alloc(sizeof(T) * (d->ncol + 4) * std::max<int64_t>(g, 1)));
+        DPM_RET(sd.dens.alloc(sizeof(T) * 4 * n1));
+        DPM_RET(sd.vG.alloc(sizeof(double) * n1));
+        DPM_CUDA(cudaStreamSynchronize(s));  // host vectors and label buffers go out of scope
+    }
+    const int64_t m = d->sub[0].n_rows + d->sub[1].n_rows;
+    if (m < d->ncol) {
+        set_error("%lld BEP rows for %d unknowns: refine the grids or lower MZ/MG", (long long)m, d->ncol);
+        return DPM_EINVAL;
+    }
+    d->lsq.m = (int)m;
+    d->lsq.n = d->ncol;
+    // the partial-sphere series make kappa^2 too large for the FP32 Gram
+    d->lsq.method = LsqFactor::kEquilibrated64;
+    DPM_RET(d->lsq.A.alloc(sizeof(double) * m * d->ncol));
+    DPM_RET(d->coef.alloc(sizeof(double) * 4 * d->ncol));
+    DPM_RET(d->bvec.alloc(sizeof(T) * 4 * m));
+    return DPM_OK;
+}
+
+template <class T>
+int dd2_build_bep(dpm_dd2 *d, double sigma, const std::vector<ApRhs<T>> *extra, double fscale, cudaStream_t s) {
+    for (int l = 0; l < 2; ++l) {
+        DD2Sub &sd = d->sub[l];
+        const int64_t n = sd.gi.n_gamma, g = sd.gi.n_gin;
+        std::vector<ApRhs<T>> rhs;
+        for (int k = 0; k < d->ncol; ++k)
+            rhs.push_back({nullptr, sd.psi.as<T>() + k * n, nullptr, sd.trace.as<T>() + k * g, 0, 0});
+        if (extra)
+            for (auto &e : extra[l]) rhs.push_back(e);
+        ApParams p = dd2_ap(sd, sigma);
+        p.fscale = fscale;
+        DPM_RET(run_ap<T>(sd.prec, p, rhs, sd.work, sd.desc, s));
+    }
+    const DD2Sub &a = d->sub[0], &b = d->sub[1];
+    DPM_RET(dd2_assemble<T>(a.n_rows, b.n_rows, d->ncol, a.own.as<double>(), a.trace.as<T>(), a.gi.n_gin,
+                            a.row_i.as<int>(), b.own.as<double>(), b.trace.as<T>(), b.gi.n_gin, b.row_i.as<int>(),
+                            d->lsq.A.as<double>(), s));
+    DPM_RET(lsq_factor(d->lsq, nullptr, s));
+    d->sigma = sigma;
+    d->factored = true;
+    return DPM_OK;
+}
+
+template <class T>
+int dd2_solve(dpm_dd2 *d, const void *f1v, const void *f2v, const double *gn1, const double *gn2, void *u1v,
+              void *u2v, double *coeffs, cudaStream_t s) {
+    const T *f[2] = {static_cast<const T *>(f1v), static_cast<const T *>(f2v)};
+    T *u[2] = {static_cast<T *>(u1v), static_cast<T *>(u2v)};
+    const double *gn[2] = {gn1, gn2};
+    T *bv = d->bvec.as<T>();
+    int64_t off = 0;
+    for (int l = 0; l < 2; ++l) {
+        DD2Sub &sd = d->sub[l];
+        const int64_t n = sd.gi.n_gamma, g = sd.gi.n_gin;
+        T *trp = sd.trace.as<T>() + (int64_t)d->ncol * g, *trv = trp + g;
+        T *veff = sd.dens.as<T>() + n;
+        std::vector<ApRhs<T>> r = {{f[l], nullptr, nullptr, trp, 0, 0}};
+        if (gn[l]) {
+            DPM_RET(dd2_neumann<T>(n, sd.flags.as<uint8_t>(), sd.dG.as<double>(), gn[l], sd.vG.as<double>(), veff, s));
+            r.push_back({nullptr, veff, nullptr, trv, 0, 0});
+        }
+        DPM_RET(run_ap<T>(sd.prec, dd2_ap(sd, d->sigma), r, sd.work, sd.desc, s));
+        DPM_RET(dd2_rhs<T>(sd.n_rows, sd.row_i.as<int>(), sd.row_e.as<int>(), sd.row_s.as<uint8_t>(), trp,
+                           gn[l] ? sd.vG.as<double>() : nullptr, trv, bv + off, s));
+        off += sd.n_rows;
+    }
+    double *C = d->coef.as<double>();
+    DPM_RET(lsq_apply<T>(d->lsq, bv, (int)off, C, 1, s));
+    for (int l = 0; l < 2; ++l) {
+        DD2Sub &sd = d->sub[l];
+        const int64_t n = sd.gi.n_gamma;
+        T *dn = sd.dens.as<T>();
+        DPM_RET(dd2_extend<T>(n, d->prm.MZ, d->prm.MG, sd.flags.as<uint8_t>(), sd.dG.as<double>(), sd.dZ.as<double>(),
+                              sd.YG.as<double>(), sd.YZ.as<double>(), C, d->ncol, gn[l], dn, (int)n, 1, 0, s));
+        std::vector<ApRhs<T>> gr = {{f[l], dn, u[l], nullptr, 0, 0}};
+        DPM_RET(run_ap<T>(sd.prec, dd2_ap(sd, d->sigma), gr, sd.work, sd.desc, s));
+    }
+    if (coeffs) DPM_CUDA(cudaMemcpyAsync(coeffs, C, sizeof(double) * d->ncol, cudaMemcpyDeviceToDevice, s));
+    return DPM_OK;
+}
+
+}  // namespace
+
+extern "C" int dpm_dd2_build(dpm_ctx *ctx, const dpm_dd2_params *P, double sigma, dpm_dd2 **out,
+                             cudaStream_t s) {
+    if (!ctx || !out) { set_error("ctx/out is NULL"); return DPM_EINVAL; }
+    *out = nullptr;
+    DPM_RET(dd2_check(P));
+    if (!(sigma > 0)) { set_error("sigma must be > 0"); return DPM_EINVAL; }
+    DPM_CUDA(cudaSetDevice(ctx->device));
+    dpm_dd2 *d = new (std::nothrow) dpm_dd2();
+    if (!d) { set_error("out of host memory"); return DPM_ENOMEM; }
+    int r;
+    if (P->precision == DPM_PREC_FP64) {
+        r = dd2_init<double>(d, ctx, *P, s);
+        if (r == DPM_OK) r = dd2_build_bep<double>(d, sigma, nullptr, 1.0, s);
+    } else {
+        r = dd2_init<float>(d, ctx, *P, s);
+        if (r == DPM_OK) r = dd2_build_bep<float>(d, sigma, nullptr, 1.0, s);
+    }
+    if (r == DPM_OK && P->precision == DPM_PREC_TC32) r = tc_status_check();
+    if (r != DPM_OK) { delete d; return r; }
+    *out = d;
+    return DPM_OK;
+}
+
+extern "C" int dpm_dd2_get_info(const dpm_dd2 *d, dpm_dd2_info *info) {
+    if (!d || !info) { set_error("dd/info is NULL"); return DPM_EINVAL; }
+    for (int l = 0; l < 2; ++l) {
+        const DD2Sub &sd = d->sub[l];
+        info->N[l] = sd.N;
+        info->h[l] = sd.gi.h;
+        info->precision[l] = sd.prec;
+        info->n_mplus[l] = sd.gi.n_mplus;
+        info->n_gin[l] = sd.gi.n_gin;
+        info->n_gamma[l] = sd.gi.n_gamma;
+        info->n_rows[l] = sd.n_rows;
+        info->n_wedge[l] = sd.n_wedge;
+    }
+    info->ncol = d->ncol;
+    info->sigma = d->sigma;
+    return DPM_OK;
+}
+
+extern "C" int dpm_dd2_matrix(dpm_dd2 *d, double *A, cudaStream_t s) {
+    if (!d || !A) { set_error("dd/A is NULL"); return DPM_EINVAL; }
+    const size_t bytes = sizeof(double) * (size_t)d->lsq.m * d->ncol;
+    DPM_CUDA(cudaMemcpyAsync(A, d->lsq.A.p, bytes, cudaMemcpyDeviceToDevice, s));
+    return DPM_OK;
+}
+
+extern "C" int dpm_dd2_gamma(dpm_dd2 *d, int l, int32_t *gamma_idx, uint8_t *flags, double *foot_gamma,
+                             cudaStream_t s) {
+    if (!d || l < 0 || l > 1) { set_error("dd is NULL or sub-domain index not 0/1"); return DPM_EINVAL; }
+    const DD2Sub &sd = d->sub[l];
+    const size_t n = (size_t)sd.gi.n_gamma;
+    if (gamma_idx) DPM_CUDA(cudaMemcpyAsync(gamma_idx, sd.gi.gamma.p, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
+    if (flags) DPM_CUDA(cudaMemcpyAsync(flags, sd.flags.p, n, cudaMemcpyDeviceToDevice, s));
+    if (foot_gamma)
+        DPM_CUDA(cudaMemcpyAsync(foot_gamma, sd.footG.p, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
+    return DPM_OK;
+}
+
+extern "C" int dpm_dd2_solve(dpm_dd2 *d, const void *f1, const void *f2, const double *neumann1,
+                             const double *neumann2, void *u1, void *u2, double *coeffs, cudaStream_t s) {
+    if (!d || !f1 || !f2 || !u1 || !u2) { set_error("dd/f/u is NULL"); return DPM_EINVAL; }
+    int r = d->storage == DPM_PREC_FP64 ? dd2_solve<double>(d, f1, f2, neumann1, neumann2, u1, u2, coeffs, s)
+                                        : dd2_solve<float>(d, f1, f2, neumann1, neumann2, u1, u2, coeffs, s);
+    if (r == DPM_OK && d->prm.precision == DPM_PREC_TC32) r = tc_status_check();
+    return r;
+}
+
+extern "C" int dpm_dd2_destroy(dpm_dd2 *d) {
+    delete d;
+    return DPM_OK;
+}
+
+// ---- time loop on the two sub-domains of Case 2 --------------------------------------
+namespace {
+
+template <class T> int dd2_pks_alloc(dpm_dd2_pks *k, const dpm_gaussian &g0, const dpm_gaussian &g1, cudaStream_t s) {
+    for (int l = 0; l < 2; ++l) {
+        DD2Sub &sd = k->dd.sub[l];
+        const size_t n3 = (size_t)sd.N * sd.N * sd.N;
+        DPM_RET(sd.rho.alloc(sizeof(T) * n3));
+        DPM_RET(sd.c.alloc(sizeof(T) * n3));
+        DPM_RET(sd.frho.alloc(sizeof(T) * n3));
+        DPM_RET(sd.fc.alloc(sizeof(T) * n3));
+        DPM_RET(sd.gmax.alloc(sizeof(unsigned int) * 4));
+        DPM_RET(sd.diag_part.alloc(sizeof(double) * 6 * pks_diag_blocks(sd.N)));
+        DPM_RET(sd.diag_out.alloc(sizeof(double) * 8));
+        DPM_CUDA(cudaMemsetAsync(sd.diag_out.p, 0, sizeof(double) * 8, s));
+        const int64_t n = sd.gi.n_gamma;
+        DPM_RET(sd.init_geom.foot.alloc(sizeof(double) * 3 * std::max<int64_t>(n, 1)));
+        DPM_RET(dd2_init_foot(n, sd.flags.as<uint8_t>(), sd.footG.as<double>(), sd.footZ.as<double>(),
+                              sd.init_geom.foot.as<double>(), s));
+        dpm_gaussian a = g0, b = g1;  // centres in the local frame
+        for (int t = 0; t < 3; ++t) {
+            a.center[t] -= sd.origin[t];
+            b.center[t] -= sd.origin[t];
+        }
+        DPM_RET(pks_init<T>(sd.gi, sd.init_geom, a, b, sd.rho.as<T>(), sd.c.as<T>(), s));
+    }
+    return DPM_OK;
+}
+
+template <class T> int dd2_pks_step(dpm_dd2_pks *k, cudaStream_t s) {
+    dpm_dd2 *d = &k->dd;
+    double dt = k->dt_max;
+    if (k->dt_mode == 1) {
+        for (int l = 0; l < 2; ++l) {
+            DD2Sub &sd = d->sub[l];
+            DPM_RET(pks_cfl<T>(sd.N, sd.gi.labels.as<uint8_t>(), sd.c.as<T>(), sd.gmax.as<unsigned int>(), s));
+        }
+        unsigned int gm[2][3];
+        for (int l = 0; l < 2; ++l)
+            DPM_CUDA(cudaMemcpyAsync(gm[l], d->sub[l].gmax.p, sizeof(gm[l]), cudaMemcpyDeviceToHost, s));
+        DPM_CUDA(cudaStreamSynchronize(s));
+        for (int l = 0; l < 2; ++l) {
+            const double h = d->sub[l].gi.h;
+            for (int ax = 0; ax < 3; ++ax) {
+                float g;
+                memcpy(&g, &gm[l][ax], sizeof(g));
+                const double gmaxv = (double)g / h;
+                if (gmaxv > 0) dt = std::min(dt, h / (6.0 * k->chi * gmaxv));
+            }
+        }
+        if (k->step > 0) dt = std::min(dt, k->dt_prev);
+    }
+    if (!(dt > 0) || !std::isfinite(dt)) { set_error("time step is not positive/finite (dt=%g)", dt); return DPM_ENUMERIC; }
+    const bool rebuild = !d->factored || k->rebuild || dt < k->dt_prev;
+    const double sigma = 1.0 / dt;
+    std::vector<ApRhs<T>> part[2];
+    T *trp[2];
+    for (int l = 0; l < 2; ++l) {
+        DD2Sub &sd = d->sub[l];
+        const int64_t g = sd.gi.n_gin;
+        DPM_RET(pks_flux<T>(sd.N, sd.gi.h, k->chi, dt, nullptr, sd.gi.labels.as<uint8_t>(), sd.rho.as<T>(),
+                            sd.c.as<T>(), sd.frho.as<T>(), sd.fc.as<T>(), s));
+        trp[l] = sd.trace.as<T>() + (int64_t)d->ncol * g;
+        part[l] = {{sd.frho.as<T>(), nullptr, nullptr, trp[l], 0, 0},
+                   {sd.fc.as<T>(), nullptr, nullptr, trp[l] + g, 0, 0}};
+    }
+    if (rebuild) {
+        DPM_RET(dd2_build_bep<T>(d, sigma, part, sigma, s));
+    } else {
+        for (int l = 0; l < 2; ++l) {
+            ApParams p = dd2_ap(d->sub[l], sigma);
+            p.fscale = sigma;  // L_{h,dt} u = f  <=>  (1/dt - Lap_h) u = f/dt
+            DPM_RET(run_ap<T>(d->sub[l].prec, p, part[l], d->sub[l].work, d->sub[l].desc, s));
+        }
+    }
+    const int64_t m = d->sub[0].n_rows + d->sub[1].n_rows;
+    T *bv = d->bvec.as<T>();
+    for (int f = 0; f < 2; ++f) {
+        int64_t off = 0;
+        for (int l = 0; l < 2; ++l) {
+            DD2Sub &sd = d->sub[l];
+            DPM_RET(dd2_rhs<T>(sd.n_rows, sd.row_i.as<int>(), sd.row_e.as<int>(), sd.row_s.as<uint8_t>(),
+                               trp[l] + f * sd.gi.n_gin, nullptr, nullptr, bv + f * m + off, s));
+            off += sd.n_rows;
+        }
+    }
+    double *C = d->coef.as<double>();
+    DPM_RET(lsq_apply<T>(d->lsq, bv, (int)m, C, 2, s));
+    for (int l = 0; l < 2; ++l) {
+        DD2Sub &sd = d->sub[l];
+        const int64_t n = sd.gi.n_gamma;
+        T *dn = sd.dens.as<T>();
+        DPM_RET(dd2_extend<T>(n, d->prm.MZ, d->prm.MG, sd.flags.as<uint8_t>(), sd.dG.as<double>(), sd.dZ.as<double>(),
+                              sd.YG.as<double>(), sd.YZ.as<double>(), C, d->ncol, nullptr, dn, (int)n, 2, k->clamp, s));
+        std::vector<ApRhs<T>> g = {{sd.frho.as<T>(), dn, sd.rho.as<T>(), nullptr, 0, 0},
+                                   {sd.fc.as<T>(), dn + n, sd.c.as<T>(), nullptr, 0, 0}};
+        ApParams p = dd2_ap(sd, sigma);
+        p.fscale = sigma;
+        DPM_RET(run_ap<T>(sd.prec, p, g, sd.work, sd.desc, s));
+        DPM_RET(pks_diag<T>(sd.N, sd.gi.lo, sd.gi.h, sd.gi.labels.as<uint8_t>(), sd.rho.as<T>(), sd.c.as<T>(),
+                            sd.diag_part.as<double>(), sd.diag_out.as<double>(), s, sd.origin));
+    }
+    k->t += dt;
+    k->dt_prev = dt;
+    k->step += 1;
+    k->last_rebuilt = rebuild ? 1 : 0;
+    return DPM_OK;
+}
+
+}  // namespace
+
+extern "C" int dpm_dd2_pks_create(dpm_ctx *ctx, const dpm_dd2_params *P, double chi, double dt_max, int dt_mode,
+                                  int rebuild, int clamp, const dpm_gaussian *rho0, const dpm_gaussian *c0,
+                                  dpm_dd2_pks **out, cudaStream_t s) {
+    if (!ctx || !out) { set_error("ctx/out is NULL"); return DPM_EINVAL; }
+    *out = nullptr;
+    DPM_RET(dd2_check(P));
+    if (!(dt_max > 0) || !(chi >= 0) || (dt_mode != 0 && dt_mode != 1)) {
+        set_error("need dt_max > 0, chi >= 0, dt_mode in {0,1}");
+        return DPM_EINVAL;
+    }
+    DPM_CUDA(cudaSetDevice(ctx->device));
+    dpm_dd2_pks *k = new (std::nothrow) dpm_dd2_pks();
+    if (!k) { set_error("out of host memory"); return DPM_ENOMEM; }
+    k->chi = chi;
+    k->dt_max = dt_max;
+    k->dt_mode = dt_mode;
+    k->rebuild = rebuild;
+    k->clamp = clamp;
+    dpm_gaussian z{};
+    const dpm_gaussian &g0 = rho0 ? *rho0 : z, &g1 = c0 ? *c0 : z;
+    int r;
+    if (P->precision == DPM_PREC_FP64) {
+        r = dd2_init<double>(&k->dd, ctx, *P, s);
+        if (r == DPM_OK) r = dd2_pks_alloc<double>(k, g0, g1, s);
+    } else {
+        r = dd2_init<float>(&k->dd, ctx, *P, s);
+        if (r == DPM_OK) r = dd2_pks_alloc<float>(k, g0, g1, s);
+    }
+    if (r == DPM_OK) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { set_error("%s", cudaGetErrorString(e)); r = DPM_ECUDA; }
+    }
+    if (r != DPM_OK) { delete k; return r; }
+    *out = k;
+    return DPM_OK;
+}
+
+extern "C" int dpm_dd2_pks_step(dpm_dd2_pks *k, int nsteps, dpm_pks_stats *stats, cudaStream_t s) {
+    if (!k || nsteps < 0) { set_error("pks is NULL or nsteps < 0"); return DPM_EINVAL; }
+    for (int i = 0; i < nsteps; ++i) {
+        if (k->dd.storage == DPM_PREC_FP64) DPM_RET(dd2_pks_step<double>(k, s));
+        else DPM_RET(dd2_pks_step<float>(k, s));
+    }
+    if (stats) {
+        double dg[2][6];
+        for (int l = 0; l < 2; ++l)
+            DPM_CUDA(cudaMemcpyAsync(dg[l], k->dd.sub[l].diag_out.p, sizeof(dg[l]), cudaMemcpyDeviceToHost, s));
+        DPM_CUDA(cudaStreamSynchronize(s));
+        stats->t = k->t;
+        stats->dt = k->dt_prev;
+        stats->step = k->step;
+        stats->rebuilt = k->last_rebuilt;
+        stats->mass = dg[0][0] + dg[1][0];
+        stats->max_rho = std::max(dg[0][1], dg[1][1]);
+        stats->min_rho = std::min(dg[0][2], dg[1][2]);
+        stats->min_c = std::min(dg[0][3], dg[1][3]);
+        stats->m2 = dg[0][4] + dg[1][4];
+        stats->free_energy = dg[0][5] + dg[1][5];
+        if (k->dd.prm.precision == DPM_PREC_TC32) DPM_RET(tc_status_check());
+        if (!std::isfinite(stats->mass) || !std::isfinite(stats->free_energy)) {
+            set_error("PKS state became non-finite at step %lld", (long long)k->step);
+            return DPM_ENUMERIC;
+        }
+    }
+    return DPM_OK;
+}
+
+extern "C" int dpm_dd2_pks_get_state(dpm_dd2_pks *k, int l, void *rho, void *c, cudaStream_t s) {
+    if (!k || l < 0 || l > 1) { set_error("pks is NULL or sub-domain index not 0/1"); return DPM_EINVAL; }
+    const DD2Sub &sd = k->dd.sub[l];
+    const size_t n3 = (size_t)sd.N * sd.N * sd.N * elem_size(k->dd.storage);
+    if (rho) DPM_CUDA(cudaMemcpyAsync(rho, sd.rho.p, n3, cudaMemcpyDeviceToDevice, s));
+    if (c) DPM_CUDA(cudaMemcpyAsync(c, sd.c.p, n3, cudaMemcpyDeviceToDevice, s));
+    return DPM_OK;
+}
+
+extern "C" int dpm_dd2_pks_destroy(dpm_dd2_pks *k) {
     delete k;
     return DPM_OK;
 }

@@ -22,9 +22,11 @@ constexpr int kChunk = 4096;  // nodes per compaction block
 constexpr int kLists = 5;     // M+, gamma_in, gamma_ex, gamma, shell
 
 // kind 2 (spherical shell): inside iff the form of the outer sphere (radius ax)
-// is < 1 and that of the inner sphere (radius r_in) is > 1.
+// is < 1 and that of the inner sphere (radius r_in) is > 1.  Kinds 3 / 4: the
+// form of the sphere of radius ax is < 1 and that of the sphere of radius r_in
+// about (cx, cy, cz + zoff) is < 1 (3) or > 1 (4).
 __global__ void k_inside(int N, double lo, double h, double cx, double cy, double cz, double ax,
-                         double ay, double az, int kind, double r_in, uint8_t *labels) {
+                         double ay, double az, int kind, double r_in, double zoff, uint8_t *labels) {
     int64_t n3 = (int64_t)N * N * N;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n3;
          p += (int64_t)gridDim.x * blockDim.x) {
@@ -37,12 +39,13 @@ __global__ void k_inside(int N, double lo, double h, double cx, double cy, doubl
         double tz = __ddiv_rn(__dsub_rn(z, cz), az);
         double s = __dadd_rn(__dadd_rn(__dmul_rn(tx, tx), __dmul_rn(ty, ty)), __dmul_rn(tz, tz));
         bool in = s < 1.0;
-        if (kind == 2) {
+        if (kind >= 2) {
+            const double czz = kind == 2 ? cz : __dadd_rn(cz, zoff);
             const double ux = __ddiv_rn(__dsub_rn(x, cx), r_in);
             const double uy = __ddiv_rn(__dsub_rn(y, cy), r_in);
-            const double uz = __ddiv_rn(__dsub_rn(z, cz), r_in);
+            const double uz = __ddiv_rn(__dsub_rn(z, czz), r_in);
             const double si = __dadd_rn(__dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy)), __dmul_rn(uz, uz));
-            in = in && si > 1.0;
+            in = in && (kind == 3 ? si < 1.0 : si > 1.0);
         }
         labels[p] = in ? (uint8_t)DPM_LBL_MPLUS : (uint8_t)0;
     }
@@ -232,11 +235,28 @@ int grid_for(int64_t n) {
 
 }  // namespace
 
+int classify_labels(const dpm_geom &g, int N, double lo, double hi, uint8_t *labels, cudaStream_t s) {
+    if (g.kind != 0 && g.kind != 1) { set_error("classify_labels: sphere or ellipsoid only"); return DPM_EINVAL; }
+    const double h = (hi - lo) / (double)(N + 1);
+    const double ax = g.axes[0], ay = g.kind == 1 ? g.axes[1] : g.axes[0], az = g.kind == 1 ? g.axes[2] : g.axes[0];
+    const int64_t n3 = (int64_t)N * N * N;
+    DevBuf flag;  // the margin check does not apply here
+    DPM_RET(flag.alloc(sizeof(int)));
+    k_inside<<<grid_for(n3), kThreads, 0, s>>>(N, lo, h, g.center[0], g.center[1], g.center[2], ax, ay, az,
+                                               g.kind, 0.0, 0.0, labels);
+    DPM_LAUNCHED();
+    k_gamma<<<grid_for(n3), kThreads, 0, s>>>(N, labels, flag.as<int>());
+    DPM_LAUNCHED();
+    DPM_CUDA(cudaStreamSynchronize(s));
+    return DPM_OK;
+}
+
 int build_grid_index(const dpm_geom &g, int N, double lo, double hi, GridIndex &gi,
                      cudaStream_t s) {
     if (N < 6 || N > 1024) { set_error("N=%d out of range [6,1024]", N); return DPM_EINVAL; }
     if (!(hi > lo)) { set_error("need lo < hi"); return DPM_EINVAL; }
-    if (g.kind < 0 || g.kind > 2) { set_error("geometry kind %d unknown", g.kind); return DPM_EINVAL; }
+    if (g.kind < 0 || g.kind > 4) { set_error("geometry kind %d unknown", g.kind); return DPM_EINVAL; }
+    if (g.kind >= 3 && !(g.axes[1] > 0)) { set_error("kinds 3/4: need axes[1] > 0"); return DPM_EINVAL; }
     double ax = g.axes[0], ay = g.kind == 1 ? g.axes[1] : g.axes[0],
            az = g.kind == 1 ? g.axes[2] : g.axes[0];
     if (!(ax > 0 && ay > 0 && az > 0)) { set_error("axes must be positive"); return DPM_EINVAL; }
@@ -253,7 +273,8 @@ int build_grid_index(const dpm_geom &g, int N, double lo, double hi, GridIndex &
     DPM_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
     uint8_t *lab = gi.labels.as<uint8_t>();
     k_inside<<<grid_for(n3), kThreads, 0, s>>>(N, lo, gi.h, g.center[0], g.center[1], g.center[2],
-                                               ax, ay, az, g.kind, g.axes[1], lab);
+                                               ax, ay, az, g.kind, g.axes[1], g.kind >= 3 ? g.axes[2] : 0.0,
+                                               lab);
     DPM_LAUNCHED();
     k_gamma<<<grid_for(n3), kThreads, 0, s>>>(N, lab, flag.as<int>());
     DPM_LAUNCHED();

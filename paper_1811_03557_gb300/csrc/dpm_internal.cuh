@@ -106,6 +106,10 @@ struct GridIndex {
 // the host).  Returns DPM_EINVAL on a geometry the library rejects.
 int build_grid_index(const dpm_geom &g, int N, double lo, double hi, GridIndex &gi,
                      cudaStream_t s);
+// Labels only (M^+, gamma_in, gamma_ex bits) of a sphere or ellipsoid on an
+// N^3 grid, without the margin check: the domain may leave the cube (used for
+// the Gamma / Z split of the domain decomposition).  Synchronises `s`.
+int classify_labels(const dpm_geom &g, int N, double lo, double hi, uint8_t *labels, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Gamma geometry and spherical harmonics (Definition 2.6, eq. spectral_approximation_sd)
@@ -177,7 +181,9 @@ template <class T> const T *dst_fold_table(int N);
 // FP64 least squares (Householder QR, resident R^{-1} Q^T)
 // ---------------------------------------------------------------------------
 struct LsqFactor {
-    enum Method { kMixed = 0, kCholeskyQR = 1, kHouseholder = 2 };
+    // kEquilibrated64: FP64 Gram of A, equilibrated (D G D), FP64 Cholesky: for
+    // matrices whose kappa^2 is beyond FP32 (kMixed) but whose column scales differ.
+    enum Method { kMixed = 0, kCholeskyQR = 1, kHouseholder = 2, kEquilibrated64 = 3 };
     int m = 0, n = 0;
     int method = kMixed;
     bool equilibrated = false;
@@ -208,6 +214,35 @@ int dd_neumann_density(int64_t n, const double *dist, const uint8_t *surf, const
 template <class T>
 int dd_rhs(int64_t m1, int64_t m2, const T *tr_p1, const T *tr_p2, const T *v, const int *gin_pos2,
            const T *tr_v2, T *b, cudaStream_t s);
+
+// Domain decomposition, Case 2 (dd2.cu): the Gamma / Z split of a grid
+// boundary (flags bit 0 Gamma, bit 1 Z), distances to both spheres, the cosines
+// of the polar angles, the foot points; zonal harmonics; column densities and
+// row values; the stacked BEP; right-hand sides; Neumann density; extension.
+int dd2_split(const GridIndex &gi, const uint8_t *lab_o, const uint8_t *lab_b, const double c0[3], double R,
+              const double cz[3], double rz, uint8_t *flags, double *dG, double *dZ, double *cosG,
+              double *cosZ, double *footG, double *footZ, cudaStream_t s);
+int dd2_zonal(int64_t n, int M, const double *x, double a, double b, double *Y, cudaStream_t s);
+template <class T>
+int dd2_columns(int64_t n, int64_t m, int MZ, int MG, const uint8_t *flags, const double *dG,
+                const double *dZ, const double *YG, const double *YZ, const int *row_e, const uint8_t *row_s,
+                T *psi, double *own, cudaStream_t s);
+template <class T>
+int dd2_assemble(int64_t m1, int64_t m2, int ncol, const double *own1, const T *tr1, int64_t g1,
+                 const int *ri1, const double *own2, const T *tr2, int64_t g2, const int *ri2, double *A,
+                 cudaStream_t s);
+template <class T>
+int dd2_rhs(int64_t m, const int *row_i, const int *row_e, const uint8_t *row_s, const T *trp,
+            const double *vG, const T *trv, T *b, cudaStream_t s);
+template <class T>
+int dd2_neumann(int64_t n, const uint8_t *flags, const double *dG, const double *gn, double *vG, T *veff,
+                cudaStream_t s);
+template <class T>
+int dd2_extend(int64_t n, int MZ, int MG, const uint8_t *flags, const double *dG, const double *dZ,
+               const double *YG, const double *YZ, const double *C, int ldc, const double *gn, T *dens,
+               int ldd, int nr, int clamp, cudaStream_t s);
+int dd2_init_foot(int64_t n, const uint8_t *flags, const double *footG, const double *footZ, double *foot,
+                  cudaStream_t s);
 
 // Scalars of the device-resident PKS step (Step 3's dt and the time).
 struct StepScalars {

@@ -179,6 +179,11 @@ int ensure_nlm() {
 int build_gamma_geom(const dpm_geom &g, const GridIndex &gi, int K, GammaGeom &gg,
                      cudaStream_t s) {
     if (K < 0 || K > kMaxK) { set_error("K=%d out of range [0,%d]", K, kMaxK); return DPM_EINVAL; }
+    if (g.kind < 0 || g.kind > 2) {
+        set_error("geometry kind %d: the single-domain and Case 1 paths take kinds 0-2 (kinds 3/4 are "
+                  "the sub-domains of dpm_dd2_*)", g.kind);
+        return DPM_EINVAL;
+    }
     DPM_RET(ensure_nlm());
     gg.K = K;
     gg.nsh = (K + 1) * (K + 1);

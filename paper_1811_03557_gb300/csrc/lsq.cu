@@ -15,6 +15,8 @@
 // triangular solves in one CTA, and Q is never formed.
 #include <math.h>
 
+#include <algorithm>
+
 #include "dpm_internal.cuh"
 
 namespace dpm {
@@ -544,8 +546,18 @@ static int householder_factor(LsqFactor &f, double *A0, double *w, double *rdiag
     return DPM_OK;
 }
 
+// G[i][j] *= d[i] d[j]: the Gram of A D from the Gram of A.
+__global__ void k_gscale(int n, double *G, const double *d) {
+    const size_t nn = (size_t)n * n;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nn; q += (size_t)gridDim.x * blockDim.x)
+        G[q] *= d[q / n] * d[q % n];
+}
+
+// FP64 Gram G = A^T A (tiles of partial sums reduced in FP64), then, with
+// dscale, the column equilibration D G D (R becomes the factor of A D), then
+// the FP64 Cholesky.
 static int cholesky_factor(LsqFactor &f, const double *A0, double *R, int *status,
-                           cudaStream_t s) {
+                           cudaStream_t s, double *dscale = nullptr) {
     const int m = f.m, n = f.n;
     const int nb = (n + kGT - 1) / kGT;
     const int ntiles = nb * (nb + 1) / 2;
@@ -565,6 +577,12 @@ static int cholesky_factor(LsqFactor &f, const double *A0, double *R, int *statu
         DPM_LAUNCHED();
         k_syrk_reduce<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(n, chunks, part, G);
         DPM_LAUNCHED();
+        if (dscale) {
+            k_colscale<<<n, 1024, 0, s>>>(m, A0, dscale);
+            DPM_LAUNCHED();
+            k_gscale<<<(unsigned)std::min<size_t>((nn + 255) / 256, 4096), 256, 0, s>>>(n, G, dscale);
+            DPM_LAUNCHED();
+        }
     }
     const size_t smem = nn * sizeof(double);
     const int use_smem = smem <= 200 * 1024 ? 1 : 0;
@@ -678,6 +696,9 @@ static int lsq_factor_impl(LsqFactor &f, bool sync, cudaStream_t s) {
         DPM_RET(householder_factor(f, A0, w, rdiag, R, status, s));
     } else if (f.method == LsqFactor::kCholeskyQR) {
         DPM_RET(cholesky_factor(f, A0, R, status, s));
+    } else if (f.method == LsqFactor::kEquilibrated64) {
+        DPM_RET(cholesky_factor(f, A0, R, status, s, dscale));
+        f.equilibrated = true;
     } else {
         DPM_RET(mixed_factor(f, A0, R, Rinv, dscale, status, &rinv_done, s));
         f.equilibrated = true;
@@ -688,7 +709,6 @@ static int lsq_factor_impl(LsqFactor &f, bool sync, cudaStream_t s) {
         k_rinv<<<(n + warps - 1) / warps, 32 * warps, sizeof(double) * warps * n, s>>>(n, R, Rinv, status);
         DPM_LAUNCHED();
     }
-    if (!sync) return DPM_OK;
     if (!sync) return DPM_OK;
     int h_status = 0;
     DPM_CUDA(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s));

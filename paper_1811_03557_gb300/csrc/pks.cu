@@ -113,7 +113,7 @@ constexpr int kDiag = 6;  // mass, max rho, min rho, min c, m2, free energy
 
 template <class T>
 __global__ void k_diag(int N, double lo, double h, const uint8_t *lab, const T *rho, const T *c,
-                       double *part) {
+                       double *part, double ox, double oy, double oz) {
     const int64_t n3 = (int64_t)N * N * N;
     double v[kDiag] = {0.0, -INFINITY, INFINITY, INFINITY, 0.0, 0.0};
     const T inv8h2 = (T)(1.0 / (8.0 * h * h));
@@ -126,8 +126,13 @@ __global__ void k_diag(int N, double lo, double h, const uint8_t *lab, const T *
         v[3] = fmin(v[3], (double)cc);
         if (!(l & DPM_LBL_MPLUS)) continue;
         int i = (int)(p / ((int64_t)N * N)), j = (int)((p / N) % N), k = (int)(p % N);
+        // global coordinates: the grid's local frame plus its origin (0 unless
+        // the grid belongs to a shifted sub-domain box)
         double x = lo + (double)(i + 1) * h, y = lo + (double)(j + 1) * h,
                z = lo + (double)(k + 1) * h;
+        x += ox;
+        y += oy;
+        z += oz;
         v[0] += (double)r;
         v[1] = fmax(v[1], (double)r);
         v[4] += (x * x + y * y + z * z) * (double)r;
@@ -431,18 +436,19 @@ int pks_diag_blocks(int N) { return reduce_blocks((int64_t)N * N * N, kDiagThrea
 
 template <class T>
 int pks_diag(int N, double lo, double h, const uint8_t *lab, const T *rho, const T *c,
-             double *part, double *out, cudaStream_t s) {
+             double *part, double *out, cudaStream_t s, const double *origin) {
     int nb = pks_diag_blocks(N);
-    k_diag<T><<<nb, kDiagThreads, 0, s>>>(N, lo, h, lab, rho, c, part);
+    const double ox = origin ? origin[0] : 0.0, oy = origin ? origin[1] : 0.0, oz = origin ? origin[2] : 0.0;
+    k_diag<T><<<nb, kDiagThreads, 0, s>>>(N, lo, h, lab, rho, c, part, ox, oy, oz);
     DPM_LAUNCHED();
     k_diag_final<<<1, 256, 0, s>>>(nb, h, part, out);
     DPM_LAUNCHED();
     return DPM_OK;
 }
 template int pks_diag<float>(int, double, double, const uint8_t *, const float *, const float *,
-                             double *, double *, cudaStream_t);
+                             double *, double *, cudaStream_t, const double *);
 template int pks_diag<double>(int, double, double, const uint8_t *, const double *,
-                              const double *, double *, double *, cudaStream_t);
+                              const double *, double *, double *, cudaStream_t, const double *);
 
 template <class T>
 int pks_init(const GridIndex &gi, const GammaGeom &gg, const dpm_gaussian &g0,

@@ -50,6 +50,10 @@ STRUCTS = {
                                           "KZ", "KG", "precision"]),
     "dpm_dd_info": (abi.dpm_dd_info, ["N", "h", "precision", "n_mplus", "n_gin", "n_gamma", "nz", "ng",
                                       "ncol", "sigma"]),
+    "dpm_dd2_params": (abi.dpm_dd2_params, ["center", "R", "rz", "zoff", "N1", "lo1", "hi1", "origin1", "N2",
+                                            "lo2", "hi2", "origin2", "MZ", "MG", "precision"]),
+    "dpm_dd2_info": (abi.dpm_dd2_info, ["N", "h", "precision", "n_mplus", "n_gin", "n_gamma", "n_rows",
+                                        "n_wedge", "ncol", "sigma"]),
 }
 
 
