@@ -45,6 +45,7 @@ constexpr int kH = 64;              // fold length
 constexpr uint32_t kTmemCols = 128; // D_E in columns [0,64), D_O in [64,128)
 constexpr float kSScale = 4096.f;   // sine blocks are stored times 2^12
 constexpr uint32_t kWaitIters = 1u << 26;
+constexpr double kRzBias = 5.0e-7;  // see the pencil pass's spectral scale
 
 // shared-memory layout (offsets from a 1024-aligned base)
 constexpr int kATile = kN * 128;                   // 128 rows x 64 f16 = 16 KB
@@ -140,7 +141,7 @@ __device__ void tc_epilogue(const Smem &S) {
 }
 
 // One folded 128-point transform: D[:,0:64) = E * SE^T, D[:,64:128) = O * SO^T,
-// each as hi*hi + hi*lo + lo*hi (issued by one thread), then commit.  The A
+// each as hi*lo + lo*hi + hi*hi (issued by one thread), then commit.  The A
 // tiles are K-major (rows of 64 K) or, with MN = true, MN-major (atoms of
 // 64 rows x 8 K placed at (kgroup * 2 + matom) * 1024 B).
 template <bool MN>
@@ -155,15 +156,18 @@ __device__ __forceinline__ void issue_transform(const Smem &S, uint32_t tm) {
         auto ad = [](uint32_t base, int kk) {
             return MN ? tc::sdesc_mn128(base + kk * 4096, 1024, 2048) : tc::sdesc_k128(base + kk * 32);
         };
+        // cross terms first: each accumulation step rounds the running sum toward
+        // zero, so only the main term's 4 steps act on the full-size sum (12 such
+        // steps left u about 2e-6 too small)
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
-            tc::mma_f16(d, ad(ahi, kk), tc::sdesc_k128(bhi + kk * 32), id, kk > 0);
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-            tc::mma_f16(d, ad(ahi, kk), tc::sdesc_k128(blo + kk * 32), id, 1);
+            tc::mma_f16(d, ad(ahi, kk), tc::sdesc_k128(blo + kk * 32), id, kk > 0);
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
             tc::mma_f16(d, ad(alo, kk), tc::sdesc_k128(bhi + kk * 32), id, 1);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+            tc::mma_f16(d, ad(ahi, kk), tc::sdesc_k128(bhi + kk * 32), id, 1);
     }
     tc::mma_commit(S.bar());
 }
@@ -574,8 +578,12 @@ k_tc_pencil(TcArgs a, const ApRhs<float> *rhs, float *work, const __grid_constan
     for (int n = t; n < kN; n += kPencilThreads) S.w()[n] = w4 * a.s2[n];
     __syncthreads();
     const float sig = (float)(a.sigma_dev ? *a.sigma_dev : a.sigma);
+    // (2/(N+1))^3, times 1 + kRzBias: the expected relative loss of the solve to
+    // the tensor cores' round-toward-zero accumulation (4 full-size steps per
+    // transform, 6 transforms; measured mean -4e-7 to -6e-7 on dense random and
+    // Gaussian data, -5e-7 taken), so that long time loops do not drift
     const double sc = 2.0 / (kN + 1);
-    const float nscale = (float)(sc * sc * sc);
+    const float nscale = (float)(sc * sc * sc * (1.0 + kRzBias));
     const int nitems = a.B * kN;
     const size_t sN2 = (size_t)kN * kN;
     const uint32_t lane_addr = tm + ((uint32_t)(warp * 32) << 16);

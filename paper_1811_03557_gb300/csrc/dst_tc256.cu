@@ -134,7 +134,11 @@ __device__ __forceinline__ float half_max(float v) {  // max over a 16-lane half
     return v;
 }
 
-// D[128 x 128] = A (128 x 128) * B^T as hi*hi + hi*lo + lo*hi, 8 K steps of 16.
+// D[128 x 128] = A (128 x 128) * B^T as hi*lo + lo*hi + hi*hi, 8 K steps of 16.
+// The small cross terms go first: every accumulation step of the tensor core
+// rounds the running sum toward zero, so the terms added while D is still small
+// cost nothing, and only the 8 steps of the main term shrink the full-size sum
+// (24 steps at full size left u about 5e-6 too small at N = 256).
 __device__ __forceinline__ void issue_part(const Sm &S, uint32_t tm) {
     const uint32_t id = tc::idesc_f16_f32(128, kH, false);
     const uint32_t a0 = tc::smem_u32(S.A(0)), b0 = tc::smem_u32(S.Bt(0));
@@ -142,11 +146,11 @@ __device__ __forceinline__ void issue_part(const Sm &S, uint32_t tm) {
         return tc::sdesc_k128(base + (2 * lohi + (kk >> 2)) * kTile + (kk & 3) * 32);
     };
 #pragma unroll
-    for (int kk = 0; kk < 8; ++kk) tc::mma_f16(tm, desc(a0, 0, kk), desc(b0, 0, kk), id, kk > 0);
-#pragma unroll
-    for (int kk = 0; kk < 8; ++kk) tc::mma_f16(tm, desc(a0, 0, kk), desc(b0, 1, kk), id, 1);
+    for (int kk = 0; kk < 8; ++kk) tc::mma_f16(tm, desc(a0, 0, kk), desc(b0, 1, kk), id, kk > 0);
 #pragma unroll
     for (int kk = 0; kk < 8; ++kk) tc::mma_f16(tm, desc(a0, 1, kk), desc(b0, 0, kk), id, 1);
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) tc::mma_f16(tm, desc(a0, 0, kk), desc(b0, 0, kk), id, 1);
     tc::mma_commit(S.bar());
 }
 
@@ -291,8 +295,12 @@ __global__ void __launch_bounds__(kThreads, 1) k256_cols(LineArgs a) {
     const int nitems = a.B * kN * 2;
     const size_t n3 = (size_t)kN * kN * kN;
     const size_t stride = AXIS == 1 ? (size_t)kN : (size_t)kN * kN;
+    // (2/(N+1))^3, times 1 + the expected relative loss of the solve to the tensor
+    // cores' round-toward-zero accumulation (8 full-size steps per transform, 6
+    // transforms; measured mean -1.1e-6 to -1.55e-6 on dense random and Gaussian
+    // data, -1.33e-6 taken), so that long time loops do not drift
     const double sc = 2.0 / (kN + 1);
-    const float nscale = (float)(sc * sc * sc);
+    const float nscale = (float)(sc * sc * sc * (1.0 + 1.33e-6));
     const float sig = (float)(a.sigma_dev ? *a.sigma_dev : a.sigma);
     for (int it = blockIdx.x >> 1; it < nitems; it += per) {
         const int b = it / (2 * kN), rem = it % (2 * kN);

@@ -546,12 +546,23 @@ static int householder_factor(LsqFactor &f, double *A0, double *w, double *rdiag
     return DPM_OK;
 }
 
-// G[i][j] *= d[i] d[j]: the Gram of A D from the Gram of A.
-__global__ void k_gscale(int n, double *G, const double *d) {
+// G[i][j] *= d[i] d[j]: the Gram of A D from the Gram of A, plus `shift` on the
+// diagonal (which is 1 after the scaling).
+__global__ void k_gscale(int n, double *G, const double *d, double shift) {
     const size_t nn = (size_t)n * n;
-    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nn; q += (size_t)gridDim.x * blockDim.x)
-        G[q] *= d[q / n] * d[q % n];
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nn; q += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = q / n, j = q % n;
+        G[q] = G[q] * (d[i] * d[j]) + (i == j ? shift : 0.0);
+    }
 }
+
+// Relative diagonal shift of the equilibrated FP64 Gram: directions of A D whose
+// singular value is below ~1e-6 of the largest (numerically rank-deficient
+// series, e.g. more harmonics than the grid boundary resolves) are damped
+// instead of breaking the Cholesky; the FP64 refinement of every solve removes
+// the shift's effect on all better-determined directions (contraction
+// shift / (sigma_i^2 + shift) per step).
+constexpr double kGramShift = 1e-12;
 
 // FP64 Gram G = A^T A (tiles of partial sums reduced in FP64), then, with
 // dscale, the column equilibration D G D (R becomes the factor of A D), then
@@ -580,7 +591,7 @@ static int cholesky_factor(LsqFactor &f, const double *A0, double *R, int *statu
         if (dscale) {
             k_colscale<<<n, 1024, 0, s>>>(m, A0, dscale);
             DPM_LAUNCHED();
-            k_gscale<<<(unsigned)std::min<size_t>((nn + 255) / 256, 4096), 256, 0, s>>>(n, G, dscale);
+            k_gscale<<<(unsigned)std::min<size_t>((nn + 255) / 256, 4096), 256, 0, s>>>(n, G, dscale, kGramShift);
             DPM_LAUNCHED();
         }
     }

@@ -151,6 +151,68 @@ def sd_dd_speedup(ctx, N_sd: int = 256, dd_grids=((128, 128), (128, 64)), T: flo
     return out
 
 
+def boxes_test_b(N1: int, N2: int, R: float = 0.5, r1: float = 0.25):
+    """Boxes of Case 2 for Test (B): the lens box centred on the north pole
+    (0, 0, R) with half-width r1 + 2 h1, h1 = 2 r1/(N1 - 3); the outer box
+    [-R - 2 h2, R + 2 h2]^3, h2 = 2 R/(N2 - 3)."""
+    h1, h2 = 2.0 * r1 / (N1 - 3), 2.0 * R / (N2 - 3)
+    return (-r1 - 2 * h1, r1 + 2 * h1, (0.0, 0.0, R), h1), (-R - 2 * h2, R + 2 * h2, (0.0, 0.0, 0.0), h2)
+
+
+def run_test_b_dd(ctx, N1: int = 128, N2: int = 128, MZ: int = 20, MG: int = 150, precision=None,
+                  stop_jump: float = 1000.0, T: float = 0.1, max_steps: int = 200000, record_every: int = 50,
+                  stream=None):
+    """Test (B) of Section 4 with the domain decomposition of Case 2: the sphere
+    r < 0.5 split by the sphere Z of radius 0.25 about the north pole into the
+    lens Omega_1 (N1 grid) and the rest (N2 grid); rho0 = 2000 exp(-100 |x -
+    (0, 0, 0.25)|^2), c0 = 0, chi = 1; MZ zonal terms per series on Z, MG on
+    Gamma (2-term extension there); dt = 0.5 min(h1, h2)^2 capped by the CFL
+    bound of both grids, the coupled BEP rebuilt whenever dt decreases; stop
+    once ||rho||_inf changes by more than stop_jump between two steps (the
+    paper's termination rule) or at time T."""
+    import torch
+
+    from . import abi
+    from .workloads import TEST_B_C0, TEST_B_RHO0
+
+    if precision is None:
+        precision = abi.DPM_PREC_TC32
+    (lo1, hi1, o1, h1), (lo2, hi2, o2, h2) = boxes_test_b(N1, N2)
+    P = abi.dd2_params((0.0, 0.0, 0.0), 0.5, 0.25, 0.5, N1, lo1, hi1, o1, N2, lo2, hi2, o2, MZ, MG, precision)
+    h = min(h1, h2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pk = abi.dpm_dd2_pks_create(ctx, P, 1.0, 0.5 * h * h, 1, 0, 1, TEST_B_RHO0, TEST_B_C0, stream=stream)
+    t_setup = time.perf_counter() - t0
+    series, prev, stopped, rebuilds = [], None, "T reached", 0
+    t0 = time.perf_counter()
+    try:
+        while True:
+            st = abi.dpm_dd2_pks_step(pk, 1, True, stream=stream)
+            rebuilds += int(st.rebuilt)
+            row = {"step": int(st.step), "t": st.t, "dt": st.dt, "rebuilt": int(st.rebuilt), "max_rho": st.max_rho,
+                   "min_rho": st.min_rho, "mass": st.mass, "m2": st.m2, "free_energy": st.free_energy}
+            jump = abs(st.max_rho - prev) if prev is not None else 0.0
+            if row["step"] % record_every == 0 or jump > stop_jump or st.t >= T:
+                series.append(row)
+            prev = st.max_rho
+            if stop_jump > 0 and jump > stop_jump:
+                stopped = "max density jump"
+                break
+            if st.t >= T:
+                break
+            if row["step"] >= max_steps:
+                stopped = "step limit"
+                break
+    finally:
+        torch.cuda.synchronize()
+        abi.dpm_dd2_pks_destroy(pk)
+    wall = time.perf_counter() - t0
+    return {"N1": N1, "N2": N2, "h1": h1, "h2": h2, "MZ": MZ, "MG": MG, "precision": precision,
+            "steps": series[-1]["step"] if series else 0, "rebuilds": rebuilds, "stopped": stopped,
+            "setup_s": t_setup, "wall_s": wall, "last": series[-1] if series else None, "series": series}
+
+
 def _mplus_mask(ctx, geom, N, lo, hi):
     import types
 
@@ -271,8 +333,19 @@ def main(argv=None):
                     help="single domain (N) against the domain decomposition, R_S = T_SD/T_DD")
     ap.add_argument("--time-convergence", action="store_true",
                     help="convergence in time at fixed meshes (N, DD 128/128 and 128/64), FP64")
+    ap.add_argument("--test-b", default="",
+                    help="Test (B) with the Case 2 decomposition: N1/N2/MZ/MG, e.g. 128/128/20/150")
     a = ap.parse_args(argv)
     ctx = abi.dpm_ctx_create(0)
+    if a.test_b:
+        N1, N2, MZ, MG = (int(v) for v in a.test_b.split("/"))
+        res = run_test_b_dd(ctx, N1, N2, MZ, MG, T=a.T)
+        abi.dpm_ctx_destroy(ctx)
+        if a.out:
+            with open(a.out, "w") as f:
+                json.dump(res, f)
+        print(json.dumps({k: v for k, v in res.items() if k != "series"}))
+        return
     if a.time_convergence:
         print(json.dumps(run_time_convergence(ctx, a.N)))
         abi.dpm_ctx_destroy(ctx)
