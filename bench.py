@@ -57,6 +57,20 @@ def parse():
     return ap.parse_args()
 
 
+def whole_job_rate(ms_local, units_per_rank, dist=None, device="cpu"):
+    """Replicas: every rank times the same K steps between barriers; the job's
+    step time is the slowest rank's, and the whole-job rate counts the units of
+    all ranks.  Returns (max ms per step over ranks, units per second)."""
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    world = 1
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        world = dist.get_world_size()
+    ms_max = float(t.item())
+    return ms_max, world * units_per_rank / (ms_max / 1e3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -256,12 +270,8 @@ def run_ours(args):
         abi.dpm_pks_step(pks, 1, want_stats=False, stream=stream)
     torch.cuda.synchronize()
     abi.dpm_profile_enable(False)
-    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
     spp = solves_per_step(w)
-    value = world * spp * N ** 3 / (ms_max / 1e3)
+    ms_max, value = whole_job_rate(ms, spp * N ** 3, dist, device="cuda")
 
     # per-kernel device time recorded by the library on the launching stream
     kinds = ["pass_k_fwd", "pass_j", "pass_i", "pass_k_inv", "lsq_householder_qr",
