@@ -7,8 +7,8 @@
 //
 //   assemble q (f on M^+ times fscale, plus L[v_gamma] on the shell) -> X
 //   k forward X -> Y;  j forward Y -> X;  i forward, times (2/(N+1))^3/lambda, X -> Y
-//   i inverse Y -> X;  j inverse X -> Y;  k inverse Y -> X
-//   restriction to N^+ and/or trace on gamma_in from X
+//   i inverse Y -> X;  j inverse X -> Y;  k inverse Y -> the outputs (restriction
+//   to N^+ and/or the trace on gamma_in, written from the pass's staged rows)
 //
 // A 256-point transform folds to 128 sums (odd 1-based modes) and 128
 // differences (even modes); each is a 128 x 128 x 128 contraction with the
@@ -86,6 +86,12 @@ struct LineArgs {
     float *out;
     const uint4 *bops;  // [parity][hi/lo][K half] tiles, pre-split and pre-swizzled
     const float *s2;    // sin^2(pi (n+1)/(2(N+1))), n < 256
+    // last k pass: write each right-hand side's result (dense, masked to N^+
+    // when asked, and/or its trace on gamma_in) instead of `out`
+    int final_out, mask_out;
+    const ApRhs<float> *rhs;
+    const uint8_t *labels;
+    const int *rp_gin, *gin;
 };
 
 __device__ __forceinline__ float pow2_scale(float m, float *inv) {
@@ -261,12 +267,44 @@ __global__ void __launch_bounds__(kThreads, 1) k256_rows(LineArgs a) {
         }
         __syncthreads();
         // ---- rows of the output: warp w writes rows w, w + 8, ... ------------------
-        for (int r = warp; r < 128; r += kThreads / 32) {
-            float *orow = a.out + tile0 + (size_t)r * kN;
+        if (!a.final_out) {
+            for (int r = warp; r < 128; r += kThreads / 32) {
+                float *orow = a.out + tile0 + (size_t)r * kN;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int ap = 32 * q + lane;
-                orow[2 * ap + parity] = stage[r * 128 + 32 * q + ((lane ^ r) & 31)];
+                for (int q = 0; q < 4; ++q) {
+                    const int ap = 32 * q + lane;
+                    orow[2 * ap + parity] = stage[r * 128 + 32 * q + ((lane ^ r) & 31)];
+                }
+            }
+        } else {
+            // the solve's result: this CTA's parity of every row, masked to N^+,
+            // and the gamma_in nodes of the tile whose k has this parity (the
+            // tile's rows are consecutive, so its nodes are one run of the
+            // sorted gamma_in list, taken in parallel)
+            const ApRhs<float> rb = a.rhs[b];
+            const uint8_t keep = DPM_LBL_MPLUS | DPM_LBL_GEX;
+            const int row0 = i * kN + 128 * jb;  // grid row (i, j) of the tile's first line
+            if (rb.out_dense) {
+                for (int r = warp; r < 128; r += kThreads / 32) {
+                    const size_t prow = (size_t)(row0 + r) * kN;  // linear index of node (i, j, 0)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int ap = 32 * q + lane, k = 2 * ap + parity;
+                        float v = stage[r * 128 + 32 * q + ((lane ^ r) & 31)];
+                        if (a.mask_out && !(a.labels[prow + k] & keep)) v = 0.f;
+                        rb.out_dense[prow + k] = v;
+                    }
+                }
+            }
+            if (rb.out_trace && a.rp_gin) {
+                const int e0 = a.rp_gin[row0], e1 = a.rp_gin[row0 + 128];
+                for (int e = e0 + t; e < e1; e += kThreads) {
+                    const int rel = a.gin[e] - row0 * kN;  // r * 256 + k
+                    const int r = rel >> 8, k = rel & (kN - 1);
+                    if ((k & 1) != parity) continue;
+                    const int ap = k >> 1;
+                    rb.out_trace[e] = stage[r * 128 + ((ap & ~31) | ((ap ^ r) & 31))];
+                }
             }
         }
         tc::tc_fence_before_sync();
@@ -400,39 +438,6 @@ __global__ void k256_shell(int n_shell, double c6, float coff, double sigma, con
     }
 }
 
-// Dense output (masked to N^+ when asked) from X[b].
-__global__ void k256_out(const ApRhs<float> *rhs, int mask_out, const uint8_t *lab, const float *X) {
-    const int b = blockIdx.y;
-    const ApRhs<float> r = rhs[b];
-    if (!r.out_dense) return;
-    const size_t n4 = (size_t)kN * kN * kN / 4;
-    const float4 *x = reinterpret_cast<const float4 *>(X + (size_t)b * kN * kN * kN);
-    float4 *o = reinterpret_cast<float4 *>(r.out_dense);
-    const uint8_t keep = DPM_LBL_MPLUS | DPM_LBL_GEX;
-    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n4; q += (size_t)gridDim.x * blockDim.x) {
-        float4 v = x[q];
-        if (mask_out) {
-            const uint32_t lb = reinterpret_cast<const uint32_t *>(lab)[q];
-            if (!(lb & keep)) v.x = 0.f;
-            if (!((lb >> 8) & keep)) v.y = 0.f;
-            if (!((lb >> 16) & keep)) v.z = 0.f;
-            if (!((lb >> 24) & keep)) v.w = 0.f;
-        }
-        o[q] = v;
-    }
-}
-
-// Trace on gamma_in from X[b]; rp_gin[N^2] is the number of gamma_in nodes.
-__global__ void k256_trace(const ApRhs<float> *rhs, const int *rp_gin, const int *gin, const float *X) {
-    const int b = blockIdx.y;
-    const ApRhs<float> r = rhs[b];
-    if (!r.out_trace) return;
-    const int n_gin = rp_gin[kN * kN];
-    const float *x = X + (size_t)b * kN * kN * kN;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_gin; e += gridDim.x * blockDim.x)
-        r.out_trace[e] = x[gin[e]];
-}
-
 // Host: pre-split, pre-swizzled folded sine blocks, [parity][hi/lo][K half] x 16 KB.
 const uint4 *tc256_sine_blocks() {
     static std::mutex mu;
@@ -522,10 +527,11 @@ int ap_solve_tc256(const ApParams &p, const ApRhs<float> *rhs_dev, float *work, 
             DPM_LAUNCHED();
         }
     }
-    LineArgs a{p.B, 0, p.h, p.sigma, p.sigma_dev, nullptr, nullptr, bops, s2};
-    auto rows = [&](const float *in, float *out) -> int {
-        a.in = in, a.out = out, a.lam = 0;
-        DPM_PROF("tc256_k", s);
+    LineArgs a{p.B, 0, p.h, p.sigma, p.sigma_dev, nullptr, nullptr, bops, s2,
+               0, p.mask_out, rhs_dev, p.labels, p.rp_gin, p.gin};
+    auto rows = [&](const float *in, float *out, int final_out) -> int {
+        a.in = in, a.out = out, a.lam = 0, a.final_out = final_out;
+        DPM_PROF(final_out ? "tc256_k_out" : "tc256_k", s);
         k256_rows<<<grid, kThreads, kSmemBytes, s>>>(a);
         DPM_LAUNCHED();
         return DPM_OK;
@@ -538,21 +544,12 @@ int ap_solve_tc256(const ApParams &p, const ApRhs<float> *rhs_dev, float *work, 
         DPM_LAUNCHED();
         return DPM_OK;
     };
-    DPM_RET(rows(X, Y));
+    DPM_RET(rows(X, Y, 0));
     DPM_RET(cols(1, 0, Y, X));
     DPM_RET(cols(2, 1, X, Y));
     DPM_RET(cols(2, 0, Y, X));
     DPM_RET(cols(1, 0, X, Y));
-    DPM_RET(rows(Y, X));
-    {
-        DPM_PROF("tc256_out", s);
-        k256_out<<<ge, 256, 0, s>>>(rhs_dev, p.mask_out, p.labels, X);
-        DPM_LAUNCHED();
-        if (p.gin && p.rp_gin) {
-            k256_trace<<<dim3(64, p.B), 256, 0, s>>>(rhs_dev, p.rp_gin, p.gin, X);
-            DPM_LAUNCHED();
-        }
-    }
+    DPM_RET(rows(Y, nullptr, 1));  // k inverse straight into the outputs
     return DPM_OK;
 }
 
