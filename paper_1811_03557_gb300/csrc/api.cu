@@ -991,6 +991,7 @@ struct dpm_dd {
     bool factored = false;
     LsqFactor lsq;
     DevBuf coef, bvec;
+    DevBuf gwork, gitems;  // grouped SIMT solves of both sub-domains
 };
 
 struct dpm_dd_pks {
@@ -1016,6 +1017,28 @@ ApParams dd_params(const DDSub &sd, double sigma) {
     p.sigma = sigma;
     ap_params_from_index(p, sd.gi);
     return p;
+}
+
+// The right-hand sides of the two sub-domains: one grouped set of SIMT launches
+// when both grids use the SIMT solver (their N may differ; DPM_DD_GROUP=0 turns
+// this off), else one batched solve per sub-domain.
+template <class T>
+int dd_run_pair(int prec0, const ApParams &p0, const std::vector<ApRhs<T>> &r0, DevBuf &w0, DevBuf &d0,
+                int prec1, const ApParams &p1, const std::vector<ApRhs<T>> &r1, DevBuf &w1, DevBuf &d1,
+                DevBuf &gw, DevBuf &gd, cudaStream_t s) {
+    const char *env = getenv("DPM_DD_GROUP");
+    const bool simt0 = prec0 == DPM_PREC_FP32 || prec0 == DPM_PREC_FP64;
+    const bool simt1 = prec1 == DPM_PREC_FP32 || prec1 == DPM_PREC_FP64;
+    if (!(simt0 && simt1) || (env && env[0] == '0') || r0.empty() || r1.empty()) {
+        DPM_RET(run_ap<T>(prec0, p0, r0, w0, d0, s));
+        return run_ap<T>(prec1, p1, r1, w1, d1, s);
+    }
+    std::vector<ApParams> probs = {p0, p1};
+    std::vector<ApRhs<T>> rhs(r0);
+    rhs.insert(rhs.end(), r1.begin(), r1.end());
+    std::vector<int> prob_of(r0.size(), 0);
+    prob_of.resize(rhs.size(), 1);
+    return ap_solve_simt_group<T>(probs, rhs, prob_of, gw, gd, s);
 }
 
 template <class T> int dd_init(dpm_dd *d, dpm_ctx *ctx, const dpm_dd_params &P, cudaStream_t s) {
@@ -1071,18 +1094,20 @@ template <class T> int dd_init(dpm_dd *d, dpm_ctx *ctx, const dpm_dd_params &P, 
 template <class T>
 int dd_build_bep(dpm_dd *d, double sigma, const std::vector<ApRhs<T>> *extra, double fscale,
                  cudaStream_t s) {
+    std::vector<ApRhs<T>> rhs[2];
+    ApParams prm[2];
     for (int l = 0; l < 2; ++l) {
         DDSub &sd = d->sub[l];
         const int64_t n = sd.gi.n_gamma, m = sd.gi.n_gin;
-        std::vector<ApRhs<T>> rhs;
         for (int k = 0; k < sd.ncol_l; ++k)
-            rhs.push_back({nullptr, sd.psi.as<T>() + k * n, nullptr, sd.trace.as<T>() + k * m, 0, 0});
+            rhs[l].push_back({nullptr, sd.psi.as<T>() + k * n, nullptr, sd.trace.as<T>() + k * m, 0, 0});
         if (extra)
-            for (auto &e : extra[l]) rhs.push_back(e);
-        ApParams p = dd_params(sd, sigma);
-        p.fscale = fscale;
-        DPM_RET(run_ap<T>(sd.prec, p, rhs, sd.work, sd.desc, s));
+            for (auto &e : extra[l]) rhs[l].push_back(e);
+        prm[l] = dd_params(sd, sigma);
+        prm[l].fscale = fscale;
     }
+    DPM_RET(dd_run_pair<T>(d->sub[0].prec, prm[0], rhs[0], d->sub[0].work, d->sub[0].desc, d->sub[1].prec, prm[1],
+                           rhs[1], d->sub[1].work, d->sub[1].desc, d->gwork, d->gitems, s));
     DPM_RET(dd_assemble<T>(d->sub[0].gi.n_gin, d->sub[1].gi.n_gin, 3 * d->nz, d->ncol,
                            d->sub[0].psi_in.as<double>(), d->sub[0].trace.as<T>(),
                            d->sub[1].psi_in.as<double>(), d->sub[1].trace.as<T>(), d->lsq.A.as<double>(), s));
@@ -1105,24 +1130,26 @@ int dd_solve(dpm_dd *d, const void *f1v, const void *f2v, const double *gn, void
     if (gn) DPM_RET(dd_neumann_density<T>(n2, b.gg.dist.as<double>(), b.surf.as<uint8_t>(), gn, v, s));
     {
         std::vector<ApRhs<T>> r1 = {{f[0], nullptr, nullptr, tr1, 0, 0}};
-        DPM_RET(run_ap<T>(a.prec, dd_params(a, d->sigma), r1, a.work, a.desc, s));
         std::vector<ApRhs<T>> r2 = {{f[1], nullptr, nullptr, tr2, 0, 0}};
         if (gn) r2.push_back({nullptr, v, nullptr, trv, 0, 0});
-        DPM_RET(run_ap<T>(b.prec, dd_params(b, d->sigma), r2, b.work, b.desc, s));
+        DPM_RET(dd_run_pair<T>(a.prec, dd_params(a, d->sigma), r1, a.work, a.desc, b.prec, dd_params(b, d->sigma),
+                               r2, b.work, b.desc, d->gwork, d->gitems, s));
     }
     T *bv = d->bvec.as<T>();
     DPM_RET(dd_rhs<T>(m1, m2, tr1, tr2, gn ? v : nullptr, b.gi.gin_pos.as<int>(), trv, bv, s));
     double *C = d->coef.as<double>();
     DPM_RET(lsq_apply<T>(d->lsq, bv, (int)(m1 + m2), C, 1, s));
+    std::vector<ApRhs<T>> g[2];
     for (int l = 0; l < 2; ++l) {
         DDSub &sd = d->sub[l];
         T *dn = sd.dens.as<T>();
         DPM_RET(dd_extend<T>(sd.gi.n_gamma, sd.gg.nsh, d->nz, d->ng, sd.gg.phi.as<double>(),
                              sd.gg.dist.as<double>(), sd.surf.as<uint8_t>(), C, d->ncol,
                              l == 1 ? gn : nullptr, dn, (int)sd.gi.n_gamma, 1, 0, s));
-        std::vector<ApRhs<T>> g = {{f[l], dn, u[l], nullptr, 0, 0}};
-        DPM_RET(run_ap<T>(sd.prec, dd_params(sd, d->sigma), g, sd.work, sd.desc, s));
+        g[l] = {{f[l], dn, u[l], nullptr, 0, 0}};
     }
+    DPM_RET(dd_run_pair<T>(a.prec, dd_params(a, d->sigma), g[0], a.work, a.desc, b.prec, dd_params(b, d->sigma),
+                           g[1], b.work, b.desc, d->gwork, d->gitems, s));
     (void)n1;
     if (coeffs) DPM_CUDA(cudaMemcpyAsync(coeffs, C, sizeof(double) * d->ncol, cudaMemcpyDeviceToDevice, s));
     return DPM_OK;
@@ -1262,11 +1289,10 @@ template <class T> int dd_pks_step(dpm_dd_pks *k, cudaStream_t s) {
     if (rebuild) {
         DPM_RET(dd_build_bep<T>(d, sigma, part, sigma, s));
     } else {
-        for (int l = 0; l < 2; ++l) {
-            ApParams p = dd_params(d->sub[l], sigma);
-            p.fscale = sigma;  // L_{h,dt} u = f  <=>  (1/dt - Lap_h) u = f/dt
-            DPM_RET(run_ap<T>(d->sub[l].prec, p, part[l], d->sub[l].work, d->sub[l].desc, s));
-        }
+        ApParams p0 = dd_params(d->sub[0], sigma), p1 = dd_params(d->sub[1], sigma);
+        p0.fscale = p1.fscale = sigma;  // L_{h,dt} u = f  <=>  (1/dt - Lap_h) u = f/dt
+        DPM_RET(dd_run_pair<T>(d->sub[0].prec, p0, part[0], d->sub[0].work, d->sub[0].desc, d->sub[1].prec, p1,
+                               part[1], d->sub[1].work, d->sub[1].desc, d->gwork, d->gitems, s));
     }
     const int64_t m1 = d->sub[0].gi.n_gin, m2 = d->sub[1].gi.n_gin, m = m1 + m2;
     T *bv = d->bvec.as<T>();
@@ -1274,17 +1300,23 @@ template <class T> int dd_pks_step(dpm_dd_pks *k, cudaStream_t s) {
         DPM_RET(dd_rhs<T>(m1, m2, trp[0] + f * m1, trp[1] + f * m2, nullptr, nullptr, nullptr, bv + f * m, s));
     double *C = d->coef.as<double>();
     DPM_RET(lsq_apply<T>(d->lsq, bv, (int)m, C, 2, s));
+    std::vector<ApRhs<T>> g[2];
+    ApParams pg[2];
     for (int l = 0; l < 2; ++l) {
         DDSub &sd = d->sub[l];
         const int64_t n = sd.gi.n_gamma;
         T *dn = sd.dens.as<T>();
         DPM_RET(dd_extend<T>(n, sd.gg.nsh, d->nz, d->ng, sd.gg.phi.as<double>(), sd.gg.dist.as<double>(),
                              sd.surf.as<uint8_t>(), C, d->ncol, nullptr, dn, (int)n, 2, k->clamp, s));
-        std::vector<ApRhs<T>> g = {{sd.frho.as<T>(), dn, sd.rho.as<T>(), nullptr, 0, 0},
-                                   {sd.fc.as<T>(), dn + n, sd.c.as<T>(), nullptr, 0, 0}};
-        ApParams p = dd_params(sd, sigma);
-        p.fscale = sigma;
-        DPM_RET(run_ap<T>(sd.prec, p, g, sd.work, sd.desc, s));
+        g[l] = {{sd.frho.as<T>(), dn, sd.rho.as<T>(), nullptr, 0, 0},
+                {sd.fc.as<T>(), dn + n, sd.c.as<T>(), nullptr, 0, 0}};
+        pg[l] = dd_params(sd, sigma);
+        pg[l].fscale = sigma;
+    }
+    DPM_RET(dd_run_pair<T>(d->sub[0].prec, pg[0], g[0], d->sub[0].work, d->sub[0].desc, d->sub[1].prec, pg[1],
+                           g[1], d->sub[1].work, d->sub[1].desc, d->gwork, d->gitems, s));
+    for (int l = 0; l < 2; ++l) {
+        DDSub &sd = d->sub[l];
         DPM_RET(pks_diag<T>(sd.N, sd.gi.lo, sd.gi.h, sd.gi.labels.as<uint8_t>(), sd.rho.as<T>(), sd.c.as<T>(),
                             sd.diag_part.as<double>(), sd.diag_out.as<double>(), s));
     }
@@ -1410,6 +1442,7 @@ struct dpm_dd2 {
     bool factored = false;
     LsqFactor lsq;
     DevBuf coef, bvec;
+    DevBuf gwork, gitems;  // grouped SIMT solves of both sub-domains
 };
 
 struct dpm_dd2_pks {
@@ -1558,18 +1591,20 @@ template <class T> int dd2_init(dpm_dd2 *d, dpm_ctx *ctx, const dpm_dd2_params &
 
 template <class T>
 int dd2_build_bep(dpm_dd2 *d, double sigma, const std::vector<ApRhs<T>> *extra, double fscale, cudaStream_t s) {
+    std::vector<ApRhs<T>> rhs[2];
+    ApParams prm[2];
     for (int l = 0; l < 2; ++l) {
         DD2Sub &sd = d->sub[l];
         const int64_t n = sd.gi.n_gamma, g = sd.gi.n_gin;
-        std::vector<ApRhs<T>> rhs;
         for (int k = 0; k < d->ncol; ++k)
-            rhs.push_back({nullptr, sd.psi.as<T>() + k * n, nullptr, sd.trace.as<T>() + k * g, 0, 0});
+            rhs[l].push_back({nullptr, sd.psi.as<T>() + k * n, nullptr, sd.trace.as<T>() + k * g, 0, 0});
         if (extra)
-            for (auto &e : extra[l]) rhs.push_back(e);
-        ApParams p = dd2_ap(sd, sigma);
-        p.fscale = fscale;
-        DPM_RET(run_ap<T>(sd.prec, p, rhs, sd.work, sd.desc, s));
+            for (auto &e : extra[l]) rhs[l].push_back(e);
+        prm[l] = dd2_ap(sd, sigma);
+        prm[l].fscale = fscale;
     }
+    DPM_RET(dd_run_pair<T>(d->sub[0].prec, prm[0], rhs[0], d->sub[0].work, d->sub[0].desc, d->sub[1].prec, prm[1],
+                           rhs[1], d->sub[1].work, d->sub[1].desc, d->gwork, d->gitems, s));
     const DD2Sub &a = d->sub[0], &b = d->sub[1];
     DPM_RET(dd2_assemble<T>(a.n_rows, b.n_rows, d->ncol, a.own.as<double>(), a.trace.as<T>(), a.gi.n_gin,
                             a.row_i.as<int>(), b.own.as<double>(), b.trace.as<T>(), b.gi.n_gin, b.row_i.as<int>(),
@@ -1763,11 +1798,10 @@ template <class T> int dd2_pks_step(dpm_dd2_pks *k, cudaStream_t s) {
     if (rebuild) {
         DPM_RET(dd2_build_bep<T>(d, sigma, part, sigma, s));
     } else {
-        for (int l = 0; l < 2; ++l) {
-            ApParams p = dd2_ap(d->sub[l], sigma);
-            p.fscale = sigma;  // L_{h,dt} u = f  <=>  (1/dt - Lap_h) u = f/dt
-            DPM_RET(run_ap<T>(d->sub[l].prec, p, part[l], d->sub[l].work, d->sub[l].desc, s));
-        }
+        ApParams p0 = dd2_ap(d->sub[0], sigma), p1 = dd2_ap(d->sub[1], sigma);
+        p0.fscale = p1.fscale = sigma;  // L_{h,dt} u = f  <=>  (1/dt - Lap_h) u = f/dt
+        DPM_RET(dd_run_pair<T>(d->sub[0].prec, p0, part[0], d->sub[0].work, d->sub[0].desc, d->sub[1].prec, p1,
+                               part[1], d->sub[1].work, d->sub[1].desc, d->gwork, d->gitems, s));
     }
     const int64_t m = d->sub[0].n_rows + d->sub[1].n_rows;
     T *bv = d->bvec.as<T>();
@@ -1782,17 +1816,23 @@ template <class T> int dd2_pks_step(dpm_dd2_pks *k, cudaStream_t s) {
     }
     double *C = d->coef.as<double>();
     DPM_RET(lsq_apply<T>(d->lsq, bv, (int)m, C, 2, s));
+    std::vector<ApRhs<T>> g[2];
+    ApParams pg[2];
     for (int l = 0; l < 2; ++l) {
         DD2Sub &sd = d->sub[l];
         const int64_t n = sd.gi.n_gamma;
         T *dn = sd.dens.as<T>();
         DPM_RET(dd2_extend<T>(n, d->prm.MZ, d->prm.MG, sd.flags.as<uint8_t>(), sd.dG.as<double>(), sd.dZ.as<double>(),
                               sd.YG.as<double>(), sd.YZ.as<double>(), C, d->ncol, nullptr, dn, (int)n, 2, k->clamp, s));
-        std::vector<ApRhs<T>> g = {{sd.frho.as<T>(), dn, sd.rho.as<T>(), nullptr, 0, 0},
-                                   {sd.fc.as<T>(), dn + n, sd.c.as<T>(), nullptr, 0, 0}};
-        ApParams p = dd2_ap(sd, sigma);
-        p.fscale = sigma;
-        DPM_RET(run_ap<T>(sd.prec, p, g, sd.work, sd.desc, s));
+        g[l] = {{sd.frho.as<T>(), dn, sd.rho.as<T>(), nullptr, 0, 0},
+                {sd.fc.as<T>(), dn + n, sd.c.as<T>(), nullptr, 0, 0}};
+        pg[l] = dd2_ap(sd, sigma);
+        pg[l].fscale = sigma;
+    }
+    DPM_RET(dd_run_pair<T>(d->sub[0].prec, pg[0], g[0], d->sub[0].work, d->sub[0].desc, d->sub[1].prec, pg[1],
+                           g[1], d->sub[1].work, d->sub[1].desc, d->gwork, d->gitems, s));
+    for (int l = 0; l < 2; ++l) {
+        DD2Sub &sd = d->sub[l];
         DPM_RET(pks_diag<T>(sd.N, sd.gi.lo, sd.gi.h, sd.gi.labels.as<uint8_t>(), sd.rho.as<T>(), sd.c.as<T>(),
                             sd.diag_part.as<double>(), sd.diag_out.as<double>(), s, sd.origin));
     }

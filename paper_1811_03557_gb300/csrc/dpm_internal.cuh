@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <vector>
 #include <stdint.h>
 #include <stddef.h>
 
@@ -159,6 +160,11 @@ void ap_params_from_index(ApParams &p, const GridIndex &gi);
 // work: B*N^3 elements of T.  rhs: device array of B descriptors.
 template <class T>
 int ap_solve_simt(const ApParams &p, const ApRhs<T> *rhs_dev, T *work, cudaStream_t s);
+// Right-hand sides of grids of different N (problem prob_of[b] for rhs[b]) in
+// one set of five SIMT launches; work / items_dev grown on demand.
+template <class T>
+int ap_solve_simt_group(const std::vector<ApParams> &probs, const std::vector<ApRhs<T>> &rhs,
+                        const std::vector<int> &prob_of, DevBuf &work, DevBuf &items_dev, cudaStream_t s);
 // Tuned SIMT tile width for (N, FP64?, B) on the current device, 0 if none.
 int simt_tile_choice(int N, int f64, int B);
 int ap_solve_tc(const ApParams &p, const ApRhs<float> *rhs_dev, float *work, cudaStream_t s);

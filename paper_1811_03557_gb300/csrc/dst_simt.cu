@@ -247,19 +247,21 @@ struct PassArgs {
     const int *shell, *shell_nb, *rp_shell, *gin, *rp_gin;
 };
 
+// Each pass is a device body over one tile of one right-hand side (its cube at
+// `cube`), run by a single-problem kernel (every right-hand side on one grid)
+// or by a grouped kernel (right-hand sides of grids of different N in one
+// launch, each with its own parameters).
 // Pass 1: right-hand side + forward transform along k.
-template <class T, int C = 32>
-__global__ void __launch_bounds__(kThreads) k_pass_k_fwd(PassArgs a, const ApRhs<T> *rhs, T *work,
-                                                         const T *tab) {
+template <class T, int C>
+__device__ __forceinline__ void body_k_fwd(const PassArgs &a, const ApRhs<T> &r, T *cube, const T *tab,
+                                           int tile) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = a.N, ld = N + 1;
-    const int b = blockIdx.y;
-    ApRhs<T> r = rhs[b];
     if (rhs_skipped(r, a.cond_flag)) return;
     T *x = reinterpret_cast<T *>(smem_raw);
     T *out = x + C * ld;
     const int64_t nrows = (int64_t)N * N;
-    const int64_t R0 = (int64_t)blockIdx.x * C;
+    const int64_t R0 = (int64_t)tile * C;
     const double sig = a.sigma_dev ? *a.sigma_dev : a.sigma;
     const T fs = (T)(a.fscale_dev ? *a.fscale_dev : a.fscale);
     for (int idx = threadIdx.x; idx < C * N; idx += blockDim.x) {
@@ -295,7 +297,7 @@ __global__ void __launch_bounds__(kThreads) k_pass_k_fwd(PassArgs a, const ApRhs
         __syncthreads();
     }
     tile_transform_rm<T, C>(x, out, N, ld, tab);
-    T *w = work + (size_t)b * nrows * N;
+    T *w = cube;
     for (int idx = threadIdx.x; idx < C * N; idx += blockDim.x) {
         int rr = idx / N, k = idx % N;
         int64_t R = R0 + rr;
@@ -304,18 +306,16 @@ __global__ void __launch_bounds__(kThreads) k_pass_k_fwd(PassArgs a, const ApRhs
 }
 
 // Passes 2 and 4: transform along j for tiles [j][kc..kc+C) at fixed i.
-template <class T, int C = 32>
-__global__ void __launch_bounds__(kThreads) k_pass_j(PassArgs a, const ApRhs<T> *rhs, T *work,
-                                                     const T *tab) {
+template <class T, int C>
+__device__ __forceinline__ void body_j(const PassArgs &a, const ApRhs<T> &r, T *cube, const T *tab, int tile) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = a.N;
-    const int b = blockIdx.y;
-    if (rhs_skipped(rhs[b], a.cond_flag)) return;
+    if (rhs_skipped(r, a.cond_flag)) return;
     const int nkc = (N + C - 1) / C;
-    const int i = blockIdx.x / nkc, kc = (blockIdx.x % nkc) * C;
+    const int i = tile / nkc, kc = (tile % nkc) * C;
     T *x = reinterpret_cast<T *>(smem_raw);
     T *out = x + N * C;
-    T *w = work + (size_t)b * N * N * N + (size_t)i * N * N;
+    T *w = cube + (size_t)i * N * N;
     for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
         int j = idx / C, c = idx % C;
         x[j * C + c] = (kc + c < N) ? w[(size_t)j * N + kc + c] : (T)0;
@@ -329,19 +329,17 @@ __global__ void __launch_bounds__(kThreads) k_pass_j(PassArgs a, const ApRhs<T> 
 }
 
 // Pass 3: along i, forward, scale/lambda, inverse; tiles [i][kc..kc+C) at fixed j.
-template <class T, int C = 32>
-__global__ void __launch_bounds__(kThreads) k_pass_i(PassArgs a, const ApRhs<T> *rhs, T *work,
-                                                     const T *tab) {
+template <class T, int C>
+__device__ __forceinline__ void body_i(const PassArgs &a, const ApRhs<T> &r, T *cube, const T *tab, int tile) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = a.N;
-    const int b = blockIdx.y;
-    if (rhs_skipped(rhs[b], a.cond_flag)) return;
+    if (rhs_skipped(r, a.cond_flag)) return;
     const int nkc = (N + C - 1) / C;
-    const int j = blockIdx.x / nkc, kc = (blockIdx.x % nkc) * C;
+    const int j = tile / nkc, kc = (tile % nkc) * C;
     T *x = reinterpret_cast<T *>(smem_raw);
     T *out = x + N * C;
     T *wt = out + N * C;  // N weights (4/h^2) sin^2(pi (n+1)/(2(N+1)))
-    T *w = work + (size_t)b * N * N * N + (size_t)j * N;
+    T *w = cube + (size_t)j * N;
     const size_t si = (size_t)N * N;
     const double sig = a.sigma_dev ? *a.sigma_dev : a.sigma;
     const T w4 = (T)(4.0 / (a.h * a.h));
@@ -372,19 +370,17 @@ __global__ void __launch_bounds__(kThreads) k_pass_i(PassArgs a, const ApRhs<T> 
 
 // Pass 5: inverse along k, then the dense output (masked to N^+) and/or the
 // trace on gamma_in.
-template <class T, int C = 32>
-__global__ void __launch_bounds__(kThreads) k_pass_k_inv(PassArgs a, const ApRhs<T> *rhs,
-                                                         const T *work, const T *tab) {
+template <class T, int C>
+__device__ __forceinline__ void body_k_inv(const PassArgs &a, const ApRhs<T> &r, const T *cube, const T *tab,
+                                           int tile) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = a.N, ld = N + 1;
-    const int b = blockIdx.y;
-    ApRhs<T> r = rhs[b];
     if (rhs_skipped(r, a.cond_flag)) return;
     T *x = reinterpret_cast<T *>(smem_raw);
     T *out = x + C * ld;
     const int64_t nrows = (int64_t)N * N;
-    const int64_t R0 = (int64_t)blockIdx.x * C;
-    const T *w = work + (size_t)b * nrows * N;
+    const int64_t R0 = (int64_t)tile * C;
+    const T *w = cube;
     for (int idx = threadIdx.x; idx < C * N; idx += blockDim.x) {
         int rr = idx / N, k = idx % N;
         int64_t R = R0 + rr;
@@ -413,6 +409,65 @@ __global__ void __launch_bounds__(kThreads) k_pass_k_inv(PassArgs a, const ApRhs
             r.out_trace[e] = out[rr * ld + k];
         }
     }
+}
+
+template <class T, int C = 32>
+__global__ void __launch_bounds__(kThreads) k_pass_k_fwd(PassArgs a, const ApRhs<T> *rhs, T *work,
+                                                         const T *tab) {
+    const int b = blockIdx.y;
+    body_k_fwd<T, C>(a, rhs[b], work + (size_t)b * a.N * a.N * a.N, tab, blockIdx.x);
+}
+template <class T, int C = 32>
+__global__ void __launch_bounds__(kThreads) k_pass_j(PassArgs a, const ApRhs<T> *rhs, T *work, const T *tab) {
+    const int b = blockIdx.y;
+    body_j<T, C>(a, rhs[b], work + (size_t)b * a.N * a.N * a.N, tab, blockIdx.x);
+}
+template <class T, int C = 32>
+__global__ void __launch_bounds__(kThreads) k_pass_i(PassArgs a, const ApRhs<T> *rhs, T *work, const T *tab) {
+    const int b = blockIdx.y;
+    body_i<T, C>(a, rhs[b], work + (size_t)b * a.N * a.N * a.N, tab, blockIdx.x);
+}
+template <class T, int C = 32>
+__global__ void __launch_bounds__(kThreads) k_pass_k_inv(PassArgs a, const ApRhs<T> *rhs, const T *work,
+                                                         const T *tab) {
+    const int b = blockIdx.y;
+    body_k_inv<T, C>(a, rhs[b], work + (size_t)b * a.N * a.N * a.N, tab, blockIdx.x);
+}
+
+// Grouped launches: item b carries its own grid's parameters, right-hand side,
+// cube and sine table; CTAs past the item's tile count return at once.
+template <class T> struct GroupItem {
+    PassArgs a;
+    ApRhs<T> r;
+    T *cube;
+    const T *tab;
+};
+template <int C> __host__ __device__ __forceinline__ int row_tiles(int N) { return (N * N + C - 1) / C; }
+template <int C> __host__ __device__ __forceinline__ int col_tiles(int N) { return N * ((N + C - 1) / C); }
+
+template <class T, int C>
+__global__ void __launch_bounds__(kThreads) kg_pass_k_fwd(const GroupItem<T> *items) {
+    const GroupItem<T> &g = items[blockIdx.y];
+    if ((int)blockIdx.x >= row_tiles<C>(g.a.N)) return;
+    body_k_fwd<T, C>(g.a, g.r, g.cube, g.tab, blockIdx.x);
+}
+template <class T, int C>
+__global__ void __launch_bounds__(kThreads) kg_pass_j(const GroupItem<T> *items) {
+    const GroupItem<T> &g = items[blockIdx.y];
+    if ((int)blockIdx.x >= col_tiles<C>(g.a.N)) return;
+    body_j<T, C>(g.a, g.r, g.cube, g.tab, blockIdx.x);
+}
+template <class T, int C>
+__global__ void __launch_bounds__(kThreads) kg_pass_i(const GroupItem<T> *items) {
+    const GroupItem<T> &g = items[blockIdx.y];
+    if ((int)blockIdx.x >= col_tiles<C>(g.a.N)) return;
+    body_i<T, C>(g.a, g.r, g.cube, g.tab, blockIdx.x);
+}
+template <class T, int C>
+__global__ void __launch_bounds__(kThreads) kg_pass_k_inv(const GroupItem<T> *items) {
+    const GroupItem<T> &g = items[blockIdx.y];
+    if ((int)blockIdx.x >= row_tiles<C>(g.a.N)) return;
+    body_k_inv<T, C>(g.a, g.r, g.cube, g.tab, blockIdx.x);
 }
 
 template <class T, int C = 32> size_t smem_rows(int N) { return 2 * (size_t)C * (N + 1) * sizeof(T); }
@@ -603,6 +658,119 @@ int ap_solve_simt(const ApParams &p, const ApRhs<T> *rhs_dev, T *work, cudaStrea
     DPM_RET(tuned_tile<T>(a, work, tab, s, &C));
     return simt_dispatch<T>(C, a, rhs_dev, work, tab, s);
 }
+
+namespace {
+template <class T, int C> int set_group_smem_limits() {
+    static bool done = false;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done) return DPM_OK;
+    const int v = 227 * 1024;
+    DPM_CUDA(cudaFuncSetAttribute(kg_pass_k_fwd<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+    DPM_CUDA(cudaFuncSetAttribute(kg_pass_j<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+    DPM_CUDA(cudaFuncSetAttribute(kg_pass_i<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+    DPM_CUDA(cudaFuncSetAttribute(kg_pass_k_inv<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+    done = true;
+    return DPM_OK;
+}
+
+template <class T, int C>
+int simt_group_passes(const GroupItem<T> *items, int B, int maxN, cudaStream_t s) {
+    if (!tile_fits<T, C>(maxN)) { set_error("grouped AP solve: N=%d tiles exceed shared memory", maxN); return DPM_EINVAL; }
+    DPM_RET((set_group_smem_limits<T, C>()));
+    const bool f64 = sizeof(T) == 8;
+    const dim3 grow((unsigned)row_tiles<C>(maxN), B), gcol((unsigned)col_tiles<C>(maxN), B);
+    const size_t sr = smem_rows<T, C>(maxN), sc = smem_cols<T, C>(maxN);
+    {
+        DPM_PROF(f64 ? "ap_simt64_pass_k_fwd" : "ap_simt32_pass_k_fwd", s);
+        kg_pass_k_fwd<T, C><<<grow, kThreads, sr, s>>>(items);
+        DPM_LAUNCHED();
+    }
+    {
+        DPM_PROF(f64 ? "ap_simt64_pass_j" : "ap_simt32_pass_j", s);
+        kg_pass_j<T, C><<<gcol, kThreads, sc, s>>>(items);
+        DPM_LAUNCHED();
+    }
+    {
+        DPM_PROF(f64 ? "ap_simt64_pass_i" : "ap_simt32_pass_i", s);
+        kg_pass_i<T, C><<<gcol, kThreads, sc, s>>>(items);
+        DPM_LAUNCHED();
+    }
+    {
+        DPM_PROF(f64 ? "ap_simt64_pass_j" : "ap_simt32_pass_j", s);
+        kg_pass_j<T, C><<<gcol, kThreads, sc, s>>>(items);
+        DPM_LAUNCHED();
+    }
+    {
+        DPM_PROF(f64 ? "ap_simt64_pass_k_inv" : "ap_simt32_pass_k_inv", s);
+        kg_pass_k_inv<T, C><<<grow, kThreads, sr, s>>>(items);
+        DPM_LAUNCHED();
+    }
+    return DPM_OK;
+}
+
+}  // namespace
+
+template <class T>
+int ap_solve_simt_group(const std::vector<ApParams> &probs, const std::vector<ApRhs<T>> &rhs,
+                        const std::vector<int> &prob_of, DevBuf &work, DevBuf &items_dev, cudaStream_t s) {
+    const size_t B = rhs.size();
+    if (B == 0) return DPM_OK;
+    if (prob_of.size() != B) { set_error("grouped AP solve: one problem index per right-hand side"); return DPM_EINVAL; }
+    int maxN = 0;
+    for (const ApParams &p : probs) {
+        if (p.N < 2 || p.N > 256) { set_error("grouped AP solve: N=%d outside [2, 256]", p.N); return DPM_EINVAL; }
+        maxN = std::max(maxN, p.N);
+    }
+    std::vector<const T *> tabs(probs.size());
+    for (size_t q = 0; q < probs.size(); ++q) {
+        tabs[q] = dst_fold_table<T>(probs[q].N);
+        if (!tabs[q]) { set_error("grouped AP solve: could not create the DST table"); return DPM_ENOMEM; }
+    }
+    // one launch set per chunk of right-hand sides whose cubes fit the workspace cap
+    constexpr size_t kCap = size_t(8) << 30;
+    std::vector<GroupItem<T>> items(B);
+    size_t b0 = 0;
+    while (b0 < B) {
+        size_t bytes = 0, b1 = b0;
+        while (b1 < B && b1 - b0 < 65535) {
+            const int pi = prob_of[b1];
+            if (pi < 0 || pi >= (int)probs.size()) { set_error("grouped AP solve: bad problem index"); return DPM_EINVAL; }
+            const size_t cube = (size_t)probs[pi].N * probs[pi].N * probs[pi].N * sizeof(T);
+            if (b1 > b0 && bytes + cube > kCap) break;
+            bytes += cube;
+            ++b1;
+        }
+        DPM_RET(work.reserve(bytes));
+        DPM_RET(items_dev.reserve(sizeof(GroupItem<T>) * (b1 - b0)));
+        size_t off = 0;
+        for (size_t b = b0; b < b1; ++b) {
+            const ApParams &p = probs[prob_of[b]];
+            GroupItem<T> &g = items[b - b0];
+            g.a = PassArgs{p.N, 1, p.h, p.sigma, p.fscale, p.sigma_dev, p.fscale_dev, p.cond_flag, p.mask_f,
+                           p.mask_out, p.labels, p.shell, p.shell_nb, p.rp_shell, p.gin, p.rp_gin};
+            g.r = rhs[b];
+            g.cube = reinterpret_cast<T *>(static_cast<char *>(work.p) + off);
+            g.tab = tabs[prob_of[b]];
+            off += (size_t)p.N * p.N * p.N * sizeof(T);
+        }
+        // pageable source: staged before the call returns, so `items` may be reused
+        DPM_CUDA(cudaMemcpyAsync(items_dev.p, items.data(), sizeof(GroupItem<T>) * (b1 - b0),
+                                 cudaMemcpyHostToDevice, s));
+        const auto *d = static_cast<const GroupItem<T> *>(items_dev.p);
+        // the tile width of the largest grid: 16 when its 32-wide tiles would leave
+        // one CTA per SM (N > 128), else 32 (the autotuner's choices at N = 256 / 128)
+        if (maxN > 128) DPM_RET((simt_group_passes<T, 16>(d, (int)(b1 - b0), maxN, s)));
+        else DPM_RET((simt_group_passes<T, 32>(d, (int)(b1 - b0), maxN, s)));
+        if (b1 < B) DPM_CUDA(cudaStreamSynchronize(s));  // the items / workspace are reused
+        b0 = b1;
+    }
+    return DPM_OK;
+}
+template int ap_solve_simt_group<float>(const std::vector<ApParams> &, const std::vector<ApRhs<float>> &,
+                                        const std::vector<int> &, DevBuf &, DevBuf &, cudaStream_t);
+template int ap_solve_simt_group<double>(const std::vector<ApParams> &, const std::vector<ApRhs<double>> &,
+                                         const std::vector<int> &, DevBuf &, DevBuf &, cudaStream_t);
 
 int simt_tile_choice(int N, int f64, int B) {
     int dev = 0;

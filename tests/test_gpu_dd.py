@@ -116,3 +116,61 @@ def test_dd_pks_steps_match_oracle(ctx, prec, mode, tol):
         r_g = rho.cpu().numpy().astype(np.float64).reshape(sd.N, sd.N, sd.N)
         assert rel(r_g[Np], st.rho[l][Np]) < tol
     abi.dpm_dd_pks_destroy(pk)
+
+
+@pytest.mark.parametrize("prec", [abi.DPM_PREC_FP64, abi.DPM_PREC_FP32])
+def test_grouped_launch_matches_separate_launches(ctx, prec):
+    """With both sub-domains on the SIMT solver (grids of different N), their
+    solves run as one grouped set of launches; the results are bit-identical to
+    one batched solve per sub-domain (DPM_DD_GROUP=0)."""
+    import os
+    N1, N2 = 24, 20
+    r1, r2 = 0.25, 0.5
+    h1, h2 = 2 * r1 / (N1 - 3), 2 * r2 / (N2 - 3)
+    P = abi.dd_params((0.0, 0.0, 0.0), r1, r2, N1, -r1 - 2 * h1, r1 + 2 * h1, N2, -r2 - 2 * h2, r2 + 2 * h2,
+                      1, 1, prec)
+    dt = torch.float64 if prec == abi.DPM_PREC_FP64 else torch.float32
+    states = []
+    for group in ("1", "0"):
+        os.environ["DPM_DD_GROUP"] = group
+        try:
+            pk = abi.dpm_dd_pks_create(ctx, P, 1.0, 0.5 * h1 * h1, 1, 0, 1, TEST_A_RHO0, TEST_A_C0)
+            abi.dpm_dd_pks_step(pk, 3, False)
+            out = []
+            for l, Nl in enumerate((N1, N2)):
+                rho = torch.empty(Nl ** 3, dtype=dt, device="cuda")
+                c = torch.empty_like(rho)
+                abi.dpm_dd_pks_get_state(pk, l, rho, c)
+                out += [rho, c]
+            torch.cuda.synchronize()
+            abi.dpm_dd_pks_destroy(pk)
+            states.append([t.cpu().numpy() for t in out])
+        finally:
+            del os.environ["DPM_DD_GROUP"]
+    for a, b in zip(*states):
+        assert np.array_equal(a, b)
+
+
+def test_grouped_launch_at_larger_grids(ctx):
+    """Grouped SIMT launches whose tiles need more than the default 48 KB of
+    shared memory (FP64, N1 = 96): bit-identical to separate launches."""
+    import os
+    N1, N2 = 96, 40
+    r1, r2 = 0.25, 0.5
+    h1, h2 = 2 * r1 / (N1 - 3), 2 * r2 / (N2 - 3)
+    P = abi.dd_params((0.0, 0.0, 0.0), r1, r2, N1, -r1 - 2 * h1, r1 + 2 * h1, N2, -r2 - 2 * h2, r2 + 2 * h2,
+                      0, 0, abi.DPM_PREC_FP64)
+    states = []
+    for group in ("1", "0"):
+        os.environ["DPM_DD_GROUP"] = group
+        try:
+            pk = abi.dpm_dd_pks_create(ctx, P, 1.0, 0.5 * h1 * h1, 1, 0, 1, TEST_A_RHO0, TEST_A_C0)
+            abi.dpm_dd_pks_step(pk, 2, False)
+            rho = torch.empty(N1 ** 3, dtype=torch.float64, device="cuda")
+            abi.dpm_dd_pks_get_state(pk, 0, rho, None)
+            torch.cuda.synchronize()
+            abi.dpm_dd_pks_destroy(pk)
+            states.append(rho.cpu().numpy())
+        finally:
+            del os.environ["DPM_DD_GROUP"]
+    assert np.array_equal(states[0], states[1])
