@@ -554,6 +554,189 @@ def dd_elliptic_solve(setup: DDSetup, f1, f2, neumann2=None):
 
 
 # ---------------------------------------------------------------------------
+# Domain decomposition into L concentric sub-domains, Case 1 generalised: the
+# ball |x - c| < rho_1 and the shells rho_l < |x - c| < rho_{l+1} (rho_L = R), each
+# on its own grid.  Interface Z_m (|x - c| = rho_m, m = 1..L-1) carries its own
+# three series (u, du/dnu, d2u/dnu2, nu = (x - c)/|x - c|, degree K_m) shared by
+# the two sub-domains it separates; Gamma carries the two series of the
+# outermost shell.  A shell's grid-boundary node belongs to the nearer of its
+# two spheres (the outer one on a tie), as in Case 1.  The reduced BEPs of all
+# sub-domains are stacked; each involves only the series of its own surfaces.
+# ---------------------------------------------------------------------------
+class MLSubdomain:
+    """Sub-domain l of the layered decomposition: point sets, the sphere index
+    of each grid-boundary node (m = 1..L; L is Gamma), its signed distance s
+    from that sphere along nu, and the harmonics of its direction."""
+
+    def __init__(self, l, center, radii, N, lo, hi, Kmax):
+        self.l, self.N, self.lo, self.hi = l, N, lo, hi
+        c = np.asarray(center, dtype=np.float64)
+        self.geom = _Sph(center, radii[0]) if l == 0 else Shell(radii[l], radii[l - 1], center)
+        self.h = grid_spacing(N, lo, hi)
+        self.sets = point_sets(inside_mask(self.geom, N, lo, hi))
+        self.labels = labels_from_sets(self.sets)
+        self.gamma_idx = np.flatnonzero(self.sets["gamma"].reshape(-1))
+        self.gin_idx = np.flatnonzero(self.sets["gin"].reshape(-1))
+        self.gin_pos = np.searchsorted(self.gamma_idx, self.gin_idx)
+        X, Y, Z = mesh(N, lo, hi)
+        P = np.stack([X.reshape(-1)[self.gamma_idx], Y.reshape(-1)[self.gamma_idx],
+                      Z.reshape(-1)[self.gamma_idx]], axis=1)
+        self.xf, _, self.normal = foot_point(self.geom, P)
+        rho = np.linalg.norm(P - c, axis=1)
+        if l == 0:
+            self.sphere = np.ones(len(P), dtype=np.int64)
+        else:
+            outer = np.abs(rho - radii[l]) <= np.abs(rho - radii[l - 1])
+            self.sphere = np.where(outer, l + 1, l)
+        self.s = rho - np.asarray(radii)[self.sphere - 1]
+        self.phi = boundary_basis(self.geom, self.xf, Kmax)
+
+    def i_minus_p_gin(self, v_gamma, sigma):
+        vg = gamma_density_grid(v_gamma, self.gamma_idx, self.N)
+        Pv = difference_potential(vg, self.sets, self.h, sigma)
+        return v_gamma[self.gin_pos] - Pv.reshape(-1)[self.gin_idx]
+
+
+class MLSetup:
+    """Steps 1-2 of the layered decomposition: the L sub-domains, the columns
+    (interface m: 3 (K_m + 1)^2, term-major; then Gamma: 2 (K_G + 1)^2), the
+    stacked reduced BEP matrix and its QR decomposition."""
+
+    def __init__(self, center, radii, grids, K, KG, sigma, build_bep=True):
+        # radii: rho_1 .. rho_{L-1}, R; grids: (N, lo, hi) per sub-domain; K: K_m per interface
+        self.L = len(radii)
+        self.radii, self.K, self.KG, self.sigma = list(radii), list(K), KG, sigma
+        self.n = [(k + 1) ** 2 for k in self.K] + [(KG + 1) ** 2]
+        self.terms = [3] * (self.L - 1) + [2]
+        self.off = np.concatenate([[0], np.cumsum([t * n for t, n in zip(self.terms, self.n)])]).astype(int)
+        self.ncol = int(self.off[-1])
+        Kmax = max(self.K + [KG])
+        self.sub = [MLSubdomain(l, center, radii, *grids[l], Kmax) for l in range(self.L)]
+        if build_bep:
+            self.A = self.bep_matrix()
+            self.Q, self.R = np.linalg.qr(self.A)
+
+    def column_sphere(self, k):
+        m = int(np.searchsorted(self.off, k, side="right"))  # 1-based sphere index
+        t, nu = divmod(k - self.off[m - 1], self.n[m - 1])
+        return m, t, nu
+
+    def column_density(self, l, k):
+        sd = self.sub[l]
+        m, t, nu = self.column_sphere(k)
+        on = sd.sphere == m
+        out = np.zeros(len(sd.gamma_idx))
+        if not np.any(on):
+            return out
+        s = sd.s[on]
+        fac = (np.ones_like(s), s, 0.5 * s * s)[t] if m < self.L else (np.ones_like(s), 0.5 * s * s)[t]
+        out[on] = fac * sd.phi[on, nu]
+        return out
+
+    def bep_matrix(self):
+        blocks = []
+        for l, sd in enumerate(self.sub):
+            cols = []
+            for k in range(self.ncol):
+                psi = self.column_density(l, k)
+                cols.append(sd.i_minus_p_gin(psi, self.sigma) if np.any(psi) else np.zeros(len(sd.gin_idx)))
+            blocks.append(np.stack(cols, axis=1))
+        return np.vstack(blocks)
+
+    def lstsq(self, b):
+        from scipy.linalg import solve_triangular
+        return solve_triangular(self.R, self.Q.T @ b)
+
+    def densities(self, C, neumann=None, clamp=False):
+        out = []
+        for l, sd in enumerate(self.sub):
+            u = np.zeros(len(sd.gamma_idx))
+            for k in range(self.ncol):
+                u += C[k] * self.column_density(l, k)
+            if l == self.L - 1 and neumann is not None:
+                g = sd.sphere == self.L
+                u[g] += sd.s[g] * neumann[g]
+            out.append(np.maximum(u, 0.0) if clamp else u)
+        return out
+
+
+def ml_elliptic_solve(setup: MLSetup, fs, neumann=None):
+    """(sigma - Lap) u = f on the union of the sub-domains, du/dn = g_N on Gamma
+    (neumann: values at the outermost sub-domain's grid-boundary nodes, read on
+    its Gamma nodes).  Returns ([u_l on N^+_l], C)."""
+    G, b = [], []
+    L = setup.L
+    for l, (sd, f) in enumerate(zip(setup.sub, fs)):
+        g = particular_solution(f, sd.sets, sd.h, setup.sigma)
+        bl = g.reshape(-1)[sd.gin_idx]
+        if l == L - 1 and neumann is not None:
+            v = np.where(sd.sphere == L, sd.s * neumann, 0.0)
+            bl = bl - sd.i_minus_p_gin(v, setup.sigma)
+        G.append(g)
+        b.append(bl)
+    C = setup.lstsq(np.concatenate(b))
+    dens = setup.densities(C, neumann)
+    us = [g + difference_potential(gamma_density_grid(u, sd.gamma_idx, sd.N), sd.sets, sd.h, setup.sigma)
+          for g, u, sd in zip(G, dens, setup.sub)]
+    return us, C
+
+
+class MLPKSState:
+    """Oracle of the time loop on the layered decomposition: dt from the smallest
+    CFL bound of all grids (and dt_max, dt_prev), the stacked BEP rebuilt when dt
+    changes, one least squares for the particular traces of all sub-domains."""
+
+    def __init__(self, center, radii, grids, K, KG, chi, dt_max, rho0, c0, dt_mode="cfl", clamp=True):
+        self.args = (center, radii, grids, K, KG)
+        self.chi, self.dt_max, self.dt_mode, self.clamp = chi, dt_max, dt_mode, clamp
+        base = MLSetup(*self.args, 1.0 / dt_max, build_bep=False)
+        self.sub = base.sub
+        self.setup, self.dt, self.t = None, None, 0.0
+        self.rho, self.c = [], []
+        for sd in self.sub:
+            X, Y, Z = mesh(sd.N, sd.lo, sd.hi)
+            r = np.where(sd.sets["Mp"], rho0(X, Y, Z), 0.0)
+            c = np.where(sd.sets["Mp"], c0(X, Y, Z), 0.0)
+            ex = sd.labels.reshape(-1)[sd.gamma_idx] & LBL_GEX > 0
+            xf = sd.xf[ex]
+            r.reshape(-1)[sd.gamma_idx[ex]] = rho0(xf[:, 0], xf[:, 1], xf[:, 2])
+            c.reshape(-1)[sd.gamma_idx[ex]] = c0(xf[:, 0], xf[:, 1], xf[:, 2])
+            self.rho.append(r)
+            self.c.append(c)
+
+    def choose_dt(self):
+        if self.dt_mode == "fixed":
+            return self.dt_max
+        cand = min([self.dt_max] + [cfl_dt(c, sd.sets, sd.h, self.chi) for c, sd in zip(self.c, self.sub)])
+        return cand if self.dt is None else min(self.dt, cand)
+
+    def step(self):
+        dt = self.choose_dt()
+        if self.setup is None or dt != self.dt:
+            self.setup = MLSetup(*self.args, 1.0 / dt)
+        self.dt = dt
+        S = self.setup
+        rhs = [pks_rhs(r, c, sd.sets, sd.h, self.chi, dt) for r, c, sd in zip(self.rho, self.c, S.sub)]
+        new = []
+        for f in range(2):  # rho, c
+            G = [particular_solution(rhs[l][f] / dt, sd.sets, sd.h, S.sigma) for l, sd in enumerate(S.sub)]
+            b = np.concatenate([G[l].reshape(-1)[sd.gin_idx] for l, sd in enumerate(S.sub)])
+            C = S.lstsq(b)
+            dens = S.densities(C, clamp=self.clamp)
+            new.append([G[l] + difference_potential(gamma_density_grid(dens[l], sd.gamma_idx, sd.N), sd.sets,
+                                                    sd.h, S.sigma) for l, sd in enumerate(S.sub)])
+        self.rho, self.c = new
+        self.t += dt
+        return dt
+
+    def diagnostics(self):
+        parts = [diagnostics(r, c, sd.sets, sd.h, sd.N, sd.lo, sd.hi) for r, c, sd in zip(self.rho, self.c, self.sub)]
+        return dict(mass=sum(p["mass"] for p in parts), max_rho=max(p["max_rho"] for p in parts),
+                    min_rho=min(p["min_rho"] for p in parts), min_c=min(p["min_c"] for p in parts),
+                    m2=sum(p["m2"] for p in parts), free_energy=sum(p["free_energy"] for p in parts))
+
+
+# ---------------------------------------------------------------------------
 # Domain decomposition, Case 2 (Section 3): the interface Z meets Gamma.
 # Omega is the sphere |x - c| < R; Z is the sphere |x - c_Z| = r_Z with
 # c_Z = c + (0, 0, z_off); Omega_1 = Omega inside Z (a lens around the north

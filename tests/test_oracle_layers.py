@@ -1,0 +1,116 @@
+"""Pins of the oracle's layered domain decomposition (Section 3's Case 1 with
+more than one interface: a ball and concentric shells, each on its own grid,
+coupled through the three shared series of every interface): with two layers it
+is Case 1 itself; with three and four the outermost layer is as accurate as the
+single-domain solve on the same grid; the stacked BEP is block-banded (each
+layer sees only its own two surfaces); a flipped interface normal is caught;
+the coupled time loop keeps its invariants."""
+import numpy as np
+import pytest
+
+from oracle import dpm_oracle as O
+from paper_1811_03557_gb300.workloads import (TEST_A_C0, TEST_A_RHO0, Gaussian, Geometry, manufactured_grad,
+                                              manufactured_u)
+
+SIGMA = 1001.0
+
+
+def grids(radii, Ns):
+    out = []
+    for r, N in zip(radii, Ns):
+        h = 2 * r / (N - 3)
+        out.append((N, -r - 2 * h, r + 2 * h))
+    return out
+
+
+def solve_errors(S):
+    fs = []
+    for sd in S.sub:
+        X, Y, Z = O.mesh(sd.N, sd.lo, sd.hi)
+        fs.append((SIGMA + 1) * manufactured_u(X, Y, Z))
+    sd = S.sub[-1]
+    gn = np.sum(manufactured_grad(sd.xf[:, 0], sd.xf[:, 1], sd.xf[:, 2]) * sd.normal, axis=1)
+    us, _ = O.ml_elliptic_solve(S, fs, gn)
+    errs = []
+    for sd, u in zip(S.sub, us):
+        X, Y, Z = O.mesh(sd.N, sd.lo, sd.hi)
+        errs.append(float(np.max(np.abs(np.where(sd.sets["Mp"], u - manufactured_u(X, Y, Z), 0.0)))))
+    return errs
+
+
+def sd_error(N, K=8):
+    h = 2.0 / (N - 3)
+    lo, hi = -1 - 2 * h, 1 + 2 * h
+    s = O.DPMSetup(Geometry.sphere(1.0), N, lo, hi, K, 1, SIGMA)
+    X, Y, Z = O.mesh(N, lo, hi)
+    gn = np.sum(manufactured_grad(s.xf[:, 0], s.xf[:, 1], s.xf[:, 2]) * s.normal, axis=1)
+    u, _, _ = O.dpm_elliptic_solve(s, (SIGMA + 1) * manufactured_u(X, Y, Z), gn)
+    return float(np.max(np.abs(np.where(s.sets["Mp"], u - manufactured_u(X, Y, Z), 0.0))))
+
+
+def test_two_layers_are_case_1():
+    radii, Ns = [0.5, 1.0], [20, 20]
+    S = O.MLSetup((0.0, 0.0, 0.0), radii, grids(radii, Ns), [4], 4, SIGMA)
+    (N1, lo1, hi1), (N2, lo2, hi2) = grids(radii, Ns)
+    D = O.DDSetup((0.0, 0.0, 0.0), 0.5, 1.0, N1, lo1, hi1, N2, lo2, hi2, 4, 4, SIGMA)
+    assert S.A.shape == D.A.shape
+    np.testing.assert_allclose(S.A, D.A, rtol=0, atol=1e-13 * np.max(np.abs(D.A)))
+
+
+@pytest.mark.parametrize("radii,Ns", [([0.4, 0.7, 1.0], [20, 24, 28]), ([0.3, 0.5, 0.75, 1.0], [20, 20, 24, 28])])
+def test_outer_layer_as_accurate_as_single_domain(radii, Ns):
+    errs = solve_errors(O.MLSetup((0.0, 0.0, 0.0), radii, grids(radii, Ns), [8] * (len(radii) - 1), 8, SIGMA))
+    esd = sd_error(Ns[-1])
+    assert errs[-1] <= 1.05 * esd and esd < 1e-4
+    assert all(e < errs[-1] for e in errs[:-1])
+
+
+def test_bep_is_block_banded():
+    radii, Ns = [0.4, 0.7, 1.0], [20, 20, 24]
+    S = O.MLSetup((0.0, 0.0, 0.0), radii, grids(radii, Ns), [3, 3], 3, SIGMA)
+    rows = np.cumsum([0] + [len(sd.gin_idx) for sd in S.sub])
+    for l in range(S.L):
+        block = S.A[rows[l]:rows[l + 1]]
+        # sphere m's columns act on the layers it bounds: l = m - 1 and l = m (Gamma: the last)
+        for m in range(1, S.L + 1):
+            cols = slice(S.off[m - 1], S.off[m])
+            touches = l in ((m - 1, m) if m < S.L else (S.L - 1,))
+            assert (np.max(np.abs(block[:, cols])) > 0) == touches, (l, m)
+
+
+def test_planted_interface_flip_is_caught(monkeypatch):
+    """Flip the sign of s in interface 2's series on the outer layer's nodes (a
+    mistaken orientation of nu on one side): the coupled solve loses accuracy."""
+    radii, Ns = [0.4, 0.7, 1.0], [20, 24, 28]
+    K = [6, 6]
+    e = solve_errors(O.MLSetup((0.0, 0.0, 0.0), radii, grids(radii, Ns), K, 6, SIGMA))
+    orig = O.MLSetup.column_density
+
+    def flipped(self, l, k):
+        out = orig(self, l, k)
+        m, t, _ = self.column_sphere(k)
+        return -out if (m == 2 and t == 1 and l == 2) else out
+
+    monkeypatch.setattr(O.MLSetup, "column_density", flipped)
+    g = solve_errors(O.MLSetup((0.0, 0.0, 0.0), radii, grids(radii, Ns), K, 6, SIGMA))
+    assert max(g) > 20 * max(e)
+
+
+def test_layered_pks_invariants():
+    radii, Ns = [0.2, 0.35, 0.5], [20, 20, 20]
+    g = grids(radii, Ns)
+    h = min((hi - lo) / (N + 1) for N, lo, hi in g)
+    st = O.MLPKSState((0.0, 0.0, 0.0), radii, g, [0, 0], 0, 1.0, 0.5 * h * h,
+                      Gaussian(200.0, 20.0), Gaussian(100.0, 10.0))
+    d0 = st.diagnostics()
+    prev = None
+    for _ in range(4):
+        st.step()
+        d = st.diagnostics()
+        assert d["min_rho"] >= -1e-9 * d["max_rho"]
+        # from the first step on (the initial gamma_ex values are the data at the
+        # foot points, not an extension, so the first gradient term jumps)
+        if prev is not None:
+            assert d["free_energy"] < prev["free_energy"]
+        prev = d
+    assert abs(prev["mass"] - d0["mass"]) < 5e-3 * d0["mass"]
