@@ -495,6 +495,72 @@ int dpm_dd2_pks_step(dpm_dd2_pks *pks, int nsteps, dpm_pks_stats *stats, cudaStr
 int dpm_dd2_pks_get_state(dpm_dd2_pks *pks, int l, void *rho, void *c, cudaStream_t stream);
 int dpm_dd2_pks_destroy(dpm_dd2_pks *pks);
 
+/* ---- layered domain decomposition (Section 3's Case 1 with more interfaces) ----
+ * L sub-domains (2 <= L <= 16): the ball |x - center| < radii[0] and the shells
+ * radii[l-1] < |x - center| < radii[l], l = 1..L-1, radii[L-1] = R the outer
+ * boundary Gamma; sub-domain l on its own N[l]^3 grid of [lo[l], hi[l]]^3.
+ * Sphere m = 1..L-1 (|x - c| = radii[m-1]) is an interface: three real SH series
+ * of degree K[m-1] -- u, du/dnu, d2u/dnu2 with nu = (x - c)/|x - c| -- shared by
+ * the two sub-domains it separates; Gamma carries two of degree KG (u, d2u/dn2;
+ * du/dn the Neumann data).  A shell's grid-boundary node belongs to the nearer of
+ * its two spheres (the outer on a tie).  Columns: sphere by sphere, term-major;
+ * rows: gamma_in of sub-domain 0, 1, ..., L-1 (each block involves only the
+ * columns of its own spheres).  With L = 2 this is Case 1 (dpm_dd_*).
+ * Sub-domains whose grids use the SIMT solver run their batched solves as one
+ * grouped set of launches (DPM_DD_GROUP=0: one batch each); a tensor-core grid
+ * (N = 128 or 256 with DPM_PREC_TC32) runs its own.  K, KG in [0, 16]. */
+#define DPM_ML_MAX 16
+typedef struct dpm_ml dpm_ml;
+typedef struct dpm_ml_pks dpm_ml_pks;
+
+typedef struct {
+    double center[3];
+    int L;
+    double radii[DPM_ML_MAX];
+    int N[DPM_ML_MAX];
+    double lo[DPM_ML_MAX], hi[DPM_ML_MAX];
+    int K[DPM_ML_MAX];  /* per interface: the first L - 1 entries */
+    int KG;
+    int precision;
+} dpm_ml_params;
+
+typedef struct {
+    int L;
+    int N[DPM_ML_MAX];
+    double h[DPM_ML_MAX];
+    int precision[DPM_ML_MAX];
+    int64_t n_mplus[DPM_ML_MAX], n_gin[DPM_ML_MAX], n_gamma[DPM_ML_MAX];
+    int ncol;
+    double sigma;
+} dpm_ml_info;
+
+/* Steps 1-2 for all sub-domains at shift sigma (synchronises). */
+int dpm_ml_build(dpm_ctx *ctx, const dpm_ml_params *params, double sigma, dpm_ml **out, cudaStream_t stream);
+int dpm_ml_get_info(const dpm_ml *ml, dpm_ml_info *info);
+/* The stacked BEP matrix: device double[(sum n_gin) * ncol], column-major. */
+int dpm_ml_matrix(dpm_ml *ml, double *A, cudaStream_t stream);
+/*
+ * (sigma - Lap) u = f on the union of the sub-domains, du/dn = g_N on Gamma:
+ * f[l] device [N[l]^3] (float, or double for DPM_PREC_FP64) used on M^+ of
+ * sub-domain l; neumann device double[n_gamma[L-1]] (values at the outermost
+ * sub-domain's grid-boundary nodes in ascending node order, read on its Gamma
+ * nodes) or NULL; u[l] device outputs valid on N^+ of each sub-domain; coeffs
+ * device double[ncol] or NULL.  f and u are host arrays of L device pointers.
+ */
+int dpm_ml_solve(dpm_ml *ml, const void *const *f, const double *neumann, void *const *u, double *coeffs,
+                 cudaStream_t stream);
+int dpm_ml_destroy(dpm_ml *ml);
+
+/* PKS time stepping on the L sub-domains (as dpm_dd_pks_*: dt from the CFL bounds
+ * of all grids in dt_mode 1, dt_max in dt_mode 0; the stacked BEP rebuilt when dt
+ * decreases or always with rebuild = 1; statistics summed / extremised over all). */
+int dpm_ml_pks_create(dpm_ctx *ctx, const dpm_ml_params *params, double chi, double dt_max, int dt_mode,
+                      int rebuild, int clamp, const dpm_gaussian *rho0, const dpm_gaussian *c0, dpm_ml_pks **out,
+                      cudaStream_t stream);
+int dpm_ml_pks_step(dpm_ml_pks *pks, int nsteps, dpm_pks_stats *stats, cudaStream_t stream);
+int dpm_ml_pks_get_state(dpm_ml_pks *pks, int l, void *rho, void *c, cudaStream_t stream);
+int dpm_ml_pks_destroy(dpm_ml_pks *pks);
+
 #ifdef __cplusplus
 }
 #endif

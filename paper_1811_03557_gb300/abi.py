@@ -85,6 +85,22 @@ class dpm_dd2_info(C.Structure):
                 ("sigma", C.c_double)]
 
 
+DPM_ML_MAX = 16
+
+
+class dpm_ml_params(C.Structure):
+    _fields_ = [("center", C.c_double * 3), ("L", C.c_int), ("radii", C.c_double * DPM_ML_MAX),
+                ("N", C.c_int * DPM_ML_MAX), ("lo", C.c_double * DPM_ML_MAX), ("hi", C.c_double * DPM_ML_MAX),
+                ("K", C.c_int * DPM_ML_MAX), ("KG", C.c_int), ("precision", C.c_int)]
+
+
+class dpm_ml_info(C.Structure):
+    _fields_ = [("L", C.c_int), ("N", C.c_int * DPM_ML_MAX), ("h", C.c_double * DPM_ML_MAX),
+                ("precision", C.c_int * DPM_ML_MAX), ("n_mplus", C.c_int64 * DPM_ML_MAX),
+                ("n_gin", C.c_int64 * DPM_ML_MAX), ("n_gamma", C.c_int64 * DPM_ML_MAX), ("ncol", C.c_int),
+                ("sigma", C.c_double)]
+
+
 _P = C.c_void_p
 _SIGS = {
     "dpm_last_error": (C.c_char_p, []),
@@ -139,6 +155,17 @@ _SIGS = {
     "dpm_dd2_pks_step": (C.c_int, [_P, C.c_int, C.POINTER(dpm_pks_stats), _P]),
     "dpm_dd2_pks_get_state": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "dpm_dd2_pks_destroy": (C.c_int, [_P]),
+    "dpm_ml_build": (C.c_int, [_P, C.POINTER(dpm_ml_params), C.c_double, C.POINTER(C.c_void_p), _P]),
+    "dpm_ml_get_info": (C.c_int, [_P, C.POINTER(dpm_ml_info)]),
+    "dpm_ml_matrix": (C.c_int, [_P, _P, _P]),
+    "dpm_ml_solve": (C.c_int, [_P, C.POINTER(C.c_void_p), _P, C.POINTER(C.c_void_p), _P, _P]),
+    "dpm_ml_destroy": (C.c_int, [_P]),
+    "dpm_ml_pks_create": (C.c_int, [_P, C.POINTER(dpm_ml_params), C.c_double, C.c_double, C.c_int, C.c_int,
+                                    C.c_int, C.POINTER(dpm_gaussian), C.POINTER(dpm_gaussian),
+                                    C.POINTER(C.c_void_p), _P]),
+    "dpm_ml_pks_step": (C.c_int, [_P, C.c_int, C.POINTER(dpm_pks_stats), _P]),
+    "dpm_ml_pks_get_state": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "dpm_ml_pks_destroy": (C.c_int, [_P]),
     "dpm_launch_count": (C.c_int64, []),
     "dpm_profile_enable": (C.c_int, [C.c_int]),
     "dpm_profile_read": (C.c_int, [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
@@ -491,3 +518,71 @@ def dpm_dd2_pks_get_state(pks, l, rho, c, stream=None):
 
 def dpm_dd2_pks_destroy(pks):
     _check(lib().dpm_dd2_pks_destroy(pks))
+
+
+# ---- layered domain decomposition (ball + concentric shells) ------------------------
+def ml_params(center, radii, grids, K, KG, precision=DPM_PREC_FP32) -> dpm_ml_params:
+    """radii: rho_1 .. rho_{L-1}, R; grids: (N, lo, hi) per sub-domain; K: degree per interface."""
+    p = dpm_ml_params()
+    L = len(radii)
+    if not 2 <= L <= DPM_ML_MAX or len(grids) != L or len(K) != L - 1:
+        raise ValueError("need 2 <= L <= 16 radii, L grids and L - 1 interface degrees")
+    for t in range(3):
+        p.center[t] = center[t]
+    p.L = L
+    for l in range(L):
+        p.radii[l] = radii[l]
+        p.N[l], p.lo[l], p.hi[l] = grids[l]
+    for m, k in enumerate(K):
+        p.K[m] = k
+    p.KG, p.precision = KG, precision
+    return p
+
+
+def dpm_ml_build(ctx, params: dpm_ml_params, sigma, stream=None):
+    h = C.c_void_p()
+    _check(lib().dpm_ml_build(ctx, C.byref(params), sigma, C.byref(h), _stream(stream)))
+    return h
+
+
+def dpm_ml_get_info(ml) -> dpm_ml_info:
+    info = dpm_ml_info()
+    _check(lib().dpm_ml_get_info(ml, C.byref(info)))
+    return info
+
+
+def dpm_ml_matrix(ml, A, stream=None):
+    _check(lib().dpm_ml_matrix(ml, _ptr(A), _stream(stream)))
+
+
+def dpm_ml_solve(ml, fs, us, neumann=None, coeffs=None, stream=None):
+    """fs, us: lists of device tensors, one per sub-domain."""
+    fa = (C.c_void_p * len(fs))(*[_ptr(f) for f in fs])
+    ua = (C.c_void_p * len(us))(*[_ptr(u) for u in us])
+    _check(lib().dpm_ml_solve(ml, fa, _ptr(neumann), ua, _ptr(coeffs), _stream(stream)))
+
+
+def dpm_ml_destroy(ml):
+    _check(lib().dpm_ml_destroy(ml))
+
+
+def dpm_ml_pks_create(ctx, params: dpm_ml_params, chi, dt_max, dt_mode, rebuild, clamp, rho0, c0, stream=None):
+    h = C.c_void_p()
+    g0, g1 = make_gaussian(rho0), make_gaussian(c0)
+    _check(lib().dpm_ml_pks_create(ctx, C.byref(params), chi, dt_max, dt_mode, rebuild, clamp, C.byref(g0),
+                                   C.byref(g1), C.byref(h), _stream(stream)))
+    return h
+
+
+def dpm_ml_pks_step(pks, nsteps=1, want_stats=True, stream=None):
+    st = dpm_pks_stats()
+    _check(lib().dpm_ml_pks_step(pks, nsteps, C.byref(st) if want_stats else None, _stream(stream)))
+    return st if want_stats else None
+
+
+def dpm_ml_pks_get_state(pks, l, rho, c, stream=None):
+    _check(lib().dpm_ml_pks_get_state(pks, l, _ptr(rho), _ptr(c), _stream(stream)))
+
+
+def dpm_ml_pks_destroy(pks):
+    _check(lib().dpm_ml_pks_destroy(pks))

@@ -1925,3 +1925,477 @@ extern "C" int dpm_dd2_pks_destroy(dpm_dd2_pks *k) {
     delete k;
     return DPM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Layered domain decomposition: the ball and L - 1 concentric shells, each on
+// its own grid; one shared 3-term series per interface, the 2-term series on
+// Gamma; the stacked (block-banded) reduced BEPs in one least squares.
+// ---------------------------------------------------------------------------
+namespace {
+struct MLSub {
+    int N = 0, prec = 0, ncl = 0;
+    double lo = 0, hi = 0;
+    dpm_geom geom{};
+    GridIndex gi;
+    GammaGeom gg;
+    DevBuf sphere, cols, psi, psi_in, trace, dens, work, desc;
+    DevBuf rho, c, frho, fc, gmax, diag_part, diag_out;
+};
+}  // namespace
+
+struct dpm_ml {
+    dpm_ctx *ctx = nullptr;
+    dpm_ml_params prm{};
+    MLSub sub[DPM_ML_MAX];
+    int L = 0;
+    MlColumns cm{};
+    int ncol = 0, storage = 0;
+    double sigma = 0;
+    bool factored = false;
+    LsqFactor lsq;
+    DevBuf coef, bvec, gwork, gitems;
+};
+
+struct dpm_ml_pks {
+    dpm_ml ml;
+    double chi = 0, dt_max = 0;
+    int dt_mode = 0, rebuild = 0, clamp = 1;
+    double t = 0, dt_prev = 0;
+    int64_t step = 0;
+    int last_rebuilt = 0;
+};
+
+namespace {
+
+int ml_check(const dpm_ml_params *P) {
+    if (!P) { set_error("params is NULL"); return DPM_EINVAL; }
+    if (P->L < 2 || P->L > DPM_ML_MAX) { set_error("L must be in [2, %d]", DPM_ML_MAX); return DPM_EINVAL; }
+    for (int l = 0; l < P->L; ++l) {
+        if (!(P->radii[l] > (l ? P->radii[l - 1] : 0.0))) { set_error("radii must increase from > 0"); return DPM_EINVAL; }
+        if (P->N[l] < 6 || P->N[l] > 256) { set_error("N[%d] = %d outside [6, 256]", l, P->N[l]); return DPM_EINVAL; }
+        if (l < P->L - 1 && (P->K[l] < 0 || P->K[l] > 16)) { set_error("K in [0, 16]"); return DPM_EINVAL; }
+    }
+    if (P->KG < 0 || P->KG > 16) { set_error("KG in [0, 16]"); return DPM_EINVAL; }
+    if (!prec_ok(P->precision)) { set_error("unknown precision %d", P->precision); return DPM_EINVAL; }
+    return DPM_OK;
+}
+
+ApParams ml_ap(const MLSub &sd, double sigma) {
+    ApParams p;
+    p.N = sd.N;
+    p.h = sd.gi.h;
+    p.sigma = sigma;
+    ap_params_from_index(p, sd.gi);
+    return p;
+}
+
+// One batched solve per sub-domain, the SIMT grids' right-hand sides in one
+// grouped set of launches (DPM_DD_GROUP=0: one batch each).
+template <class T>
+int ml_run(dpm_ml *d, const std::vector<ApParams> &prm, const std::vector<std::vector<ApRhs<T>>> &rhs, cudaStream_t s) {
+    const char *env = getenv("DPM_DD_GROUP");
+    const bool group = !(env && env[0] == '0');
+    std::vector<ApParams> gp;
+    std::vector<ApRhs<T>> gr;
+    std::vector<int> gof;
+    for (size_t l = 0; l < d->L; ++l) {
+        MLSub &sd = d->sub[l];
+        if (rhs[l].empty()) continue;
+        const bool simt = sd.prec == DPM_PREC_FP32 || sd.prec == DPM_PREC_FP64;
+        if (group && simt) {
+            gp.push_back(prm[l]);
+            gr.insert(gr.end(), rhs[l].begin(), rhs[l].end());
+            gof.resize(gr.size(), (int)gp.size() - 1);
+        } else {
+            DPM_RET(run_ap<T>(sd.prec, prm[l], rhs[l], sd.work, sd.desc, s));
+        }
+    }
+    if (!gr.empty()) DPM_RET(ap_solve_simt_group<T>(gp, gr, gof, d->gwork, d->gitems, s));
+    return DPM_OK;
+}
+
+template <class T> int ml_init(dpm_ml *d, dpm_ctx *ctx, const dpm_ml_params &P, cudaStream_t s) {
+    d->ctx = ctx;
+    d->prm = P;
+    d->storage = P.precision == DPM_PREC_FP64 ? DPM_PREC_FP64 : DPM_PREC_FP32;
+    const int L = P.L;
+    MlColumns &cm = d->cm;
+    cm.L = L;
+    cm.off[0] = 0;
+    int Kmax = P.KG;
+    for (int m = 1; m <= L; ++m) {
+        const int K = m < L ? P.K[m - 1] : P.KG;
+        Kmax = std::max(Kmax, K);
+        cm.n[m - 1] = (K + 1) * (K + 1);
+        cm.off[m] = cm.off[m - 1] + (m < L ? 3 : 2) * cm.n[m - 1];
+    }
+    d->ncol = cm.off[L];
+    d->L = L;
+    int64_t mtot = 0;
+    for (int l = 0; l < L; ++l) {
+        MLSub &sd = d->sub[l];
+        sd.geom.kind = l == 0 ? 0 : 2;
+        for (int t = 0; t < 3; ++t) sd.geom.center[t] = P.center[t];
+        sd.geom.axes[0] = P.radii[l];
+        sd.geom.axes[1] = l == 0 ? P.radii[0] : P.radii[l - 1];
+        sd.geom.axes[2] = l == 0 ? P.radii[0] : 0.0;
+        sd.N = P.N[l];
+        sd.lo = P.lo[l];
+        sd.hi = P.hi[l];
+        sd.prec = dd_sub_prec(P.precision, sd.N);
+        DPM_RET(build_grid_index(sd.geom, sd.N, sd.lo, sd.hi, sd.gi, s));
+        DPM_RET(build_gamma_geom(sd.geom, sd.gi, Kmax, sd.gg, s));
+        const int64_t n = sd.gi.n_gamma, m = sd.gi.n_gin;
+        DPM_RET(sd.sphere.alloc(std::max<int64_t>(n, 1)));
+        const double rmid = l == 0 ? 2.0 * P.radii[0] : 0.5 * (P.radii[l - 1] + P.radii[l]);
+        DPM_RET(ml_sphere_flags(n, sd.gg.foot.as<double>(), P.center, rmid, l, l == 0 ? 1 : 0, sd.sphere.as<uint8_t>(), s));
+        // the columns of this sub-domain's spheres: 1 for the ball, l and l + 1 for shell l
+        std::vector<int> cols;
+        const int m0 = l == 0 ? 1 : l, m1 = l + 1;
+        for (int q = m0; q <= m1; ++q)
+            for (int k = cm.off[q - 1]; k < cm.off[q]; ++k) cols.push_back(k);
+        sd.ncl = (int)cols.size();
+        DPM_RET(sd.cols.alloc(sizeof(int) * sd.ncl));
+        DPM_CUDA(cudaMemcpyAsync(sd.cols.p, cols.data(), sizeof(int) * sd.ncl, cudaMemcpyHostToDevice, s));
+        DPM_RET(sd.psi.alloc(sizeof(T) * sd.ncl * std::max<int64_t>(n, 1)));
+        DPM_RET(sd.psi_in.alloc(sizeof(double) * sd.ncl * std::max<int64_t>(m, 1)));
+        DPM_RET(ml_columns<T>(n, m, sd.gg.nsh, cm, sd.ncl, sd.cols.as<int>(), sd.sphere.as<uint8_t>(),
+                              sd.gg.dist.as<double>(), sd.gg.phi.as<double>(), sd.gi.gin_pos.as<int>(), sd.psi.as<T>(),
+                              sd.psi_in.as<double>(), s));
+        DPM_RET(sd.trace.alloc(sizeof(T) * (sd.ncl + 4) * std::max<int64_t>(m, 1)));
+        DPM_RET(sd.dens.alloc(sizeof(T) * 4 * std::max<int64_t>(n, 1)));
+        DPM_CUDA(cudaStreamSynchronize(s));  // `cols` goes out of scope
+        mtot += m;
+    }
+    if (mtot < d->ncol) {
+        set_error("%lld BEP rows for %d unknowns: refine the grids or lower K", (long long)mtot, d->ncol);
+        return DPM_EINVAL;
+    }
+    d->lsq.m = (int)mtot;
+    d->lsq.n = d->ncol;
+    DPM_RET(d->lsq.A.alloc(sizeof(double) * mtot * d->ncol));
+    DPM_RET(d->coef.alloc(sizeof(double) * 4 * d->ncol));
+    DPM_RET(d->bvec.alloc(sizeof(T) * 4 * mtot));
+    return DPM_OK;
+}
+
+template <class T>
+int ml_build_bep(dpm_ml *d, double sigma, const std::vector<std::vector<ApRhs<T>>> *extra, double fscale, cudaStream_t s) {
+    const int L = (int)d->L;
+    std::vector<ApParams> prm(L);
+    std::vector<std::vector<ApRhs<T>>> rhs(L);
+    for (int l = 0; l < L; ++l) {
+        MLSub &sd = d->sub[l];
+        const int64_t n = sd.gi.n_gamma, m = sd.gi.n_gin;
+        for (int j = 0; j < sd.ncl; ++j)
+            rhs[l].push_back({nullptr, sd.psi.as<T>() + j * n, nullptr, sd.trace.as<T>() + j * m, 0, 0});
+        if (extra)
+            for (auto &e : (*extra)[l]) rhs[l].push_back(e);
+        prm[l] = ml_ap(sd, sigma);
+        prm[l].fscale = fscale;
+    }
+    DPM_RET(ml_run<T>(d, prm, rhs, s));
+    const int64_t mtot = d->lsq.m;
+    DPM_CUDA(cudaMemsetAsync(d->lsq.A.p, 0, sizeof(double) * mtot * d->ncol, s));
+    int64_t row0 = 0;
+    for (int l = 0; l < L; ++l) {
+        MLSub &sd = d->sub[l];
+        DPM_RET(ml_assemble<T>(sd.gi.n_gin, sd.ncl, mtot, row0, sd.cols.as<int>(), sd.psi_in.as<double>(),
+                               sd.trace.as<T>(), d->lsq.A.as<double>(), s));
+        row0 += sd.gi.n_gin;
+    }
+    DPM_RET(lsq_factor(d->lsq, nullptr, s));
+    d->sigma = sigma;
+    d->factored = true;
+    return DPM_OK;
+}
+
+template <class T>
+int ml_solve(dpm_ml *d, const void *const *fv, const double *gn, void *const *uv, double *coeffs, cudaStream_t s) {
+    const int L = (int)d->L;
+    std::vector<ApParams> prm(L);
+    std::vector<std::vector<ApRhs<T>>> rhs(L);
+    MLSub &last = d->sub[L - 1];
+    T *v = last.dens.as<T>() + last.gi.n_gamma;
+    if (gn) DPM_RET(ml_neumann<T>(last.gi.n_gamma, L, last.sphere.as<uint8_t>(), last.gg.dist.as<double>(), gn, v, s));
+    for (int l = 0; l < L; ++l) {
+        MLSub &sd = d->sub[l];
+        const int64_t m = sd.gi.n_gin;
+        T *trp = sd.trace.as<T>() + (int64_t)sd.ncl * m;
+        rhs[l].push_back({static_cast<const T *>(fv[l]), nullptr, nullptr, trp, 0, 0});
+        if (l == L - 1 && gn) rhs[l].push_back({nullptr, v, nullptr, trp + m, 0, 0});
+        prm[l] = ml_ap(sd, d->sigma);
+    }
+    DPM_RET(ml_run<T>(d, prm, rhs, s));
+    T *bv = d->bvec.as<T>();
+    int64_t row0 = 0;
+    for (int l = 0; l < L; ++l) {
+        MLSub &sd = d->sub[l];
+        const int64_t m = sd.gi.n_gin;
+        T *trp = sd.trace.as<T>() + (int64_t)sd.ncl * m;
+        const bool nm = l == L - 1 && gn;
+        DPM_RET(ml_rhs<T>(m, trp, nm ? v : nullptr, sd.gi.gin_pos.as<int>(), trp + m, bv + row0, s));
+        row0 += m;
+    }
+    double *C = d->coef.as<double>();
+    DPM_RET(lsq_apply<T>(d->lsq, bv, (int)row0, C, 1, s));
+    for (int l = 0; l < L; ++l) {
+        MLSub &sd = d->sub[l];
+        const int64_t n = sd.gi.n_gamma;
+        DPM_RET(ml_extend<T>(n, sd.gg.nsh, d->cm, sd.sphere.as<uint8_t>(), sd.gg.dist.as<double>(), sd.gg.phi.as<double>(),
+                             C, d->ncol, l == L - 1 ? gn : nullptr, sd.dens.as<T>(), (int)n, 1, 0, s));
+        rhs[l] = {{static_cast<const T *>(fv[l]), sd.dens.as<T>(), static_cast<T *>(uv[l]), nullptr, 0, 0}};
+    }
+    DPM_RET(ml_run<T>(d, prm, rhs, s));
+    if (coeffs) DPM_CUDA(cudaMemcpyAsync(coeffs, C, sizeof(double) * d->ncol, cudaMemcpyDeviceToDevice, s));
+    return DPM_OK;
+}
+
+}  // namespace
+
+extern "C" int dpm_ml_build(dpm_ctx *ctx, const dpm_ml_params *P, double sigma, dpm_ml **out, cudaStream_t s) {
+    if (!ctx || !out) { set_error("ctx/out is NULL"); return DPM_EINVAL; }
+    *out = nullptr;
+    DPM_RET(ml_check(P));
+    if (!(sigma > 0)) { set_error("sigma must be > 0"); return DPM_EINVAL; }
+    DPM_CUDA(cudaSetDevice(ctx->device));
+    dpm_ml *d = new (std::nothrow) dpm_ml();
+    if (!d) { set_error("out of host memory"); return DPM_ENOMEM; }
+    int r;
+    if (P->precision == DPM_PREC_FP64) {
+        r = ml_init<double>(d, ctx, *P, s);
+        if (r == DPM_OK) r = ml_build_bep<double>(d, sigma, nullptr, 1.0, s);
+    } else {
+        r = ml_init<float>(d, ctx, *P, s);
+        if (r == DPM_OK) r = ml_build_bep<float>(d, sigma, nullptr, 1.0, s);
+    }
+    if (r == DPM_OK && P->precision == DPM_PREC_TC32) r = tc_status_check();
+    if (r != DPM_OK) { delete d; return r; }
+    *out = d;
+    return DPM_OK;
+}
+
+extern "C" int dpm_ml_get_info(const dpm_ml *d, dpm_ml_info *info) {
+    if (!d || !info) { set_error("ml/info is NULL"); return DPM_EINVAL; }
+    *info = dpm_ml_info{};
+    info->L = (int)d->L;
+    for (size_t l = 0; l < d->L; ++l) {
+        const MLSub &sd = d->sub[l];
+        info->N[l] = sd.N;
+        info->h[l] = sd.gi.h;
+        info->precision[l] = sd.prec;
+        info->n_mplus[l] = sd.gi.n_mplus;
+        info->n_gin[l] = sd.gi.n_gin;
+        info->n_gamma[l] = sd.gi.n_gamma;
+    }
+    info->ncol = d->ncol;
+    info->sigma = d->sigma;
+    return DPM_OK;
+}
+
+extern "C" int dpm_ml_matrix(dpm_ml *d, double *A, cudaStream_t s) {
+    if (!d || !A) { set_error("ml/A is NULL"); return DPM_EINVAL; }
+    DPM_CUDA(cudaMemcpyAsync(A, d->lsq.A.p, sizeof(double) * (size_t)d->lsq.m * d->ncol, cudaMemcpyDeviceToDevice, s));
+    return DPM_OK;
+}
+
+extern "C" int dpm_ml_solve(dpm_ml *d, const void *const *f, const double *neumann, void *const *u, double *coeffs,
+                            cudaStream_t s) {
+    if (!d || !f || !u) { set_error("ml/f/u is NULL"); return DPM_EINVAL; }
+    for (size_t l = 0; l < d->L; ++l)
+        if (!f[l] || !u[l]) { set_error("f[%zu]/u[%zu] is NULL", l, l); return DPM_EINVAL; }
+    int r = d->storage == DPM_PREC_FP64 ? ml_solve<double>(d, f, neumann, u, coeffs, s)
+                                        : ml_solve<float>(d, f, neumann, u, coeffs, s);
+    if (r == DPM_OK && d->prm.precision == DPM_PREC_TC32) r = tc_status_check();
+    return r;
+}
+
+extern "C" int dpm_ml_destroy(dpm_ml *d) {
+    delete d;
+    return DPM_OK;
+}
+
+namespace {
+
+template <class T> int ml_pks_alloc(dpm_ml_pks *k, const dpm_gaussian &g0, const dpm_gaussian &g1, cudaStream_t s) {
+    for (int l = 0; l < k->ml.L; ++l) {
+        MLSub &sd = k->ml.sub[l];
+        const size_t n3 = (size_t)sd.N * sd.N * sd.N;
+        DPM_RET(sd.rho.alloc(sizeof(T) * n3));
+        DPM_RET(sd.c.alloc(sizeof(T) * n3));
+        DPM_RET(sd.frho.alloc(sizeof(T) * n3));
+        DPM_RET(sd.fc.alloc(sizeof(T) * n3));
+        DPM_RET(sd.gmax.alloc(sizeof(unsigned int) * 4));
+        DPM_RET(sd.diag_part.alloc(sizeof(double) * 6 * pks_diag_blocks(sd.N)));
+        DPM_RET(sd.diag_out.alloc(sizeof(double) * 8));
+        DPM_CUDA(cudaMemsetAsync(sd.diag_out.p, 0, sizeof(double) * 8, s));
+        DPM_RET(pks_init<T>(sd.gi, sd.gg, g0, g1, sd.rho.as<T>(), sd.c.as<T>(), s));
+    }
+    return DPM_OK;
+}
+
+template <class T> int ml_pks_step(dpm_ml_pks *k, cudaStream_t s) {
+    dpm_ml *d = &k->ml;
+    const int L = (int)d->L;
+    double dt = k->dt_max;
+    if (k->dt_mode == 1) {
+        std::vector<unsigned int> gm(3 * L);
+        for (int l = 0; l < L; ++l) {
+            MLSub &sd = d->sub[l];
+            DPM_RET(pks_cfl<T>(sd.N, sd.gi.labels.as<uint8_t>(), sd.c.as<T>(), sd.gmax.as<unsigned int>(), s));
+            DPM_CUDA(cudaMemcpyAsync(gm.data() + 3 * l, sd.gmax.p, 3 * sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+        }
+        DPM_CUDA(cudaStreamSynchronize(s));
+        for (int l = 0; l < L; ++l) {
+            const double h = d->sub[l].gi.h;
+            for (int ax = 0; ax < 3; ++ax) {
+                float g;
+                memcpy(&g, &gm[3 * l + ax], sizeof(g));
+                const double gmaxv = (double)g / h;
+                if (gmaxv > 0) dt = std::min(dt, h / (6.0 * k->chi * gmaxv));
+            }
+        }
+        if (k->step > 0) dt = std::min(dt, k->dt_prev);
+    }
+    if (!(dt > 0) || !std::isfinite(dt)) { set_error("time step is not positive/finite (dt=%g)", dt); return DPM_ENUMERIC; }
+    const bool rebuild = !d->factored || k->rebuild || dt < k->dt_prev;
+    const double sigma = 1.0 / dt;
+    std::vector<std::vector<ApRhs<T>>> part(L);
+    std::vector<ApParams> prm(L);
+    std::vector<T *> trp(L);
+    for (int l = 0; l < L; ++l) {
+        MLSub &sd = d->sub[l];
+        const int64_t m = sd.gi.n_gin;
+        DPM_RET(pks_flux<T>(sd.N, sd.gi.h, k->chi, dt, nullptr, sd.gi.labels.as<uint8_t>(), sd.rho.as<T>(), sd.c.as<T>(),
+                            sd.frho.as<T>(), sd.fc.as<T>(), s));
+        trp[l] = sd.trace.as<T>() + (int64_t)sd.ncl * m;
+        part[l] = {{sd.frho.as<T>(), nullptr, nullptr, trp[l], 0, 0}, {sd.fc.as<T>(), nullptr, nullptr, trp[l] + m, 0, 0}};
+        prm[l] = ml_ap(sd, sigma);
+        prm[l].fscale = sigma;  // L_{h,dt} u = f  <=>  (1/dt - Lap_h) u = f/dt
+    }
+    if (rebuild) DPM_RET(ml_build_bep<T>(d, sigma, &part, sigma, s));
+    else DPM_RET(ml_run<T>(d, prm, part, s));
+    const int64_t mtot = d->lsq.m;
+    T *bv = d->bvec.as<T>();
+    for (int f = 0; f < 2; ++f) {
+        int64_t row0 = 0;
+        for (int l = 0; l < L; ++l) {
+            MLSub &sd = d->sub[l];
+            const int64_t m = sd.gi.n_gin;
+            DPM_RET(ml_rhs<T>(m, trp[l] + f * m, nullptr, nullptr, nullptr, bv + f * mtot + row0, s));
+            row0 += m;
+        }
+    }
+    double *C = d->coef.as<double>();
+    DPM_RET(lsq_apply<T>(d->lsq, bv, (int)mtot, C, 2, s));
+    std::vector<std::vector<ApRhs<T>>> g(L);
+    for (int l = 0; l < L; ++l) {
+        MLSub &sd = d->sub[l];
+        const int64_t n = sd.gi.n_gamma;
+        T *dn = sd.dens.as<T>();
+        DPM_RET(ml_extend<T>(n, sd.gg.nsh, d->cm, sd.sphere.as<uint8_t>(), sd.gg.dist.as<double>(), sd.gg.phi.as<double>(),
+                             C, d->ncol, nullptr, dn, (int)n, 2, k->clamp, s));
+        g[l] = {{sd.frho.as<T>(), dn, sd.rho.as<T>(), nullptr, 0, 0}, {sd.fc.as<T>(), dn + n, sd.c.as<T>(), nullptr, 0, 0}};
+    }
+    DPM_RET(ml_run<T>(d, prm, g, s));
+    for (int l = 0; l < L; ++l) {
+        MLSub &sd = d->sub[l];
+        DPM_RET(pks_diag<T>(sd.N, sd.gi.lo, sd.gi.h, sd.gi.labels.as<uint8_t>(), sd.rho.as<T>(), sd.c.as<T>(),
+                            sd.diag_part.as<double>(), sd.diag_out.as<double>(), s));
+    }
+    k->t += dt;
+    k->dt_prev = dt;
+    k->step += 1;
+    k->last_rebuilt = rebuild ? 1 : 0;
+    return DPM_OK;
+}
+
+}  // namespace
+
+extern "C" int dpm_ml_pks_create(dpm_ctx *ctx, const dpm_ml_params *P, double chi, double dt_max, int dt_mode, int rebuild,
+                                 int clamp, const dpm_gaussian *rho0, const dpm_gaussian *c0, dpm_ml_pks **out,
+                                 cudaStream_t s) {
+    if (!ctx || !out) { set_error("ctx/out is NULL"); return DPM_EINVAL; }
+    *out = nullptr;
+    DPM_RET(ml_check(P));
+    if (!(dt_max > 0) || !(chi >= 0) || (dt_mode != 0 && dt_mode != 1)) {
+        set_error("need dt_max > 0, chi >= 0, dt_mode in {0,1}");
+        return DPM_EINVAL;
+    }
+    DPM_CUDA(cudaSetDevice(ctx->device));
+    dpm_ml_pks *k = new (std::nothrow) dpm_ml_pks();
+    if (!k) { set_error("out of host memory"); return DPM_ENOMEM; }
+    k->chi = chi;
+    k->dt_max = dt_max;
+    k->dt_mode = dt_mode;
+    k->rebuild = rebuild;
+    k->clamp = clamp;
+    dpm_gaussian z{};
+    const dpm_gaussian &g0 = rho0 ? *rho0 : z, &g1 = c0 ? *c0 : z;
+    int r;
+    if (P->precision == DPM_PREC_FP64) {
+        r = ml_init<double>(&k->ml, ctx, *P, s);
+        if (r == DPM_OK) r = ml_pks_alloc<double>(k, g0, g1, s);
+    } else {
+        r = ml_init<float>(&k->ml, ctx, *P, s);
+        if (r == DPM_OK) r = ml_pks_alloc<float>(k, g0, g1, s);
+    }
+    if (r == DPM_OK) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { set_error("%s", cudaGetErrorString(e)); r = DPM_ECUDA; }
+    }
+    if (r != DPM_OK) { delete k; return r; }
+    *out = k;
+    return DPM_OK;
+}
+
+extern "C" int dpm_ml_pks_step(dpm_ml_pks *k, int nsteps, dpm_pks_stats *stats, cudaStream_t s) {
+    if (!k || nsteps < 0) { set_error("pks is NULL or nsteps < 0"); return DPM_EINVAL; }
+    for (int i = 0; i < nsteps; ++i) {
+        if (k->ml.storage == DPM_PREC_FP64) DPM_RET(ml_pks_step<double>(k, s));
+        else DPM_RET(ml_pks_step<float>(k, s));
+    }
+    if (stats) {
+        const int L = (int)k->ml.L;
+        std::vector<double> dg(6 * L);
+        for (int l = 0; l < L; ++l)
+            DPM_CUDA(cudaMemcpyAsync(dg.data() + 6 * l, k->ml.sub[l].diag_out.p, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        DPM_CUDA(cudaStreamSynchronize(s));
+        *stats = dpm_pks_stats{};
+        stats->t = k->t;
+        stats->dt = k->dt_prev;
+        stats->step = k->step;
+        stats->rebuilt = k->last_rebuilt;
+        stats->max_rho = -INFINITY;
+        stats->min_rho = INFINITY;
+        stats->min_c = INFINITY;
+        for (int l = 0; l < L; ++l) {
+            stats->mass += dg[6 * l];
+            stats->max_rho = std::max(stats->max_rho, dg[6 * l + 1]);
+            stats->min_rho = std::min(stats->min_rho, dg[6 * l + 2]);
+            stats->min_c = std::min(stats->min_c, dg[6 * l + 3]);
+            stats->m2 += dg[6 * l + 4];
+            stats->free_energy += dg[6 * l + 5];
+        }
+        if (k->ml.prm.precision == DPM_PREC_TC32) DPM_RET(tc_status_check());
+        if (!std::isfinite(stats->mass) || !std::isfinite(stats->free_energy)) {
+            set_error("PKS state became non-finite at step %lld", (long long)k->step);
+            return DPM_ENUMERIC;
+        }
+    }
+    return DPM_OK;
+}
+
+extern "C" int dpm_ml_pks_get_state(dpm_ml_pks *k, int l, void *rho, void *c, cudaStream_t s) {
+    if (!k || l < 0 || l >= (int)k->ml.L) { set_error("pks is NULL or sub-domain index out of range"); return DPM_EINVAL; }
+    const MLSub &sd = k->ml.sub[l];
+    const size_t n3 = (size_t)sd.N * sd.N * sd.N * elem_size(k->ml.storage);
+    if (rho) DPM_CUDA(cudaMemcpyAsync(rho, sd.rho.p, n3, cudaMemcpyDeviceToDevice, s));
+    if (c) DPM_CUDA(cudaMemcpyAsync(c, sd.c.p, n3, cudaMemcpyDeviceToDevice, s));
+    return DPM_OK;
+}
+
+extern "C" int dpm_ml_pks_destroy(dpm_ml_pks *k) {
+    delete k;
+    return DPM_OK;
+}

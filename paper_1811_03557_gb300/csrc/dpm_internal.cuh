@@ -250,6 +250,30 @@ int dd2_extend(int64_t n, int MZ, int MG, const uint8_t *flags, const double *dG
 int dd2_init_foot(int64_t n, const uint8_t *flags, const double *footG, const double *footZ, double *foot,
                   cudaStream_t s);
 
+// Layered domain decomposition (ddml.cu): the column layout by sphere
+// (1..L, L = Gamma): columns [off[m-1], off[m]) of n[m-1] harmonics per term.
+constexpr int kMlMax = 16;
+struct MlColumns {
+    int L;
+    int off[kMlMax + 1];
+    int n[kMlMax];
+};
+int ml_sphere_flags(int64_t n, const double *foot, const double c[3], double r_mid, int m_in, int ball,
+                    uint8_t *sphere, cudaStream_t s);
+template <class T>
+int ml_columns(int64_t n, int64_t m, int nsh, const MlColumns &cm, int ncl, const int *cols, const uint8_t *sphere,
+               const double *dist, const double *phi, const int *gin_pos, T *psi, double *psi_in, cudaStream_t s);
+template <class T>
+int ml_assemble(int64_t m, int ncl, int64_t mtot, int64_t row0, const int *cols, const double *psi_in, const T *trace,
+                double *A, cudaStream_t s);
+template <class T>
+int ml_extend(int64_t n, int nsh, const MlColumns &cm, const uint8_t *sphere, const double *dist, const double *phi,
+              const double *C, int ldc, const double *gn, T *dens, int ldd, int nr, int clamp, cudaStream_t s);
+template <class T>
+int ml_neumann(int64_t n, int L, const uint8_t *sphere, const double *dist, const double *gn, T *v, cudaStream_t s);
+template <class T>
+int ml_rhs(int64_t m, const T *trp, const T *v, const int *gin_pos, const T *trv, T *b, cudaStream_t s);
+
 // Scalars of the device-resident PKS step (Step 3's dt and the time).
 struct StepScalars {
     double dt, sigma, t, dt_prev;

@@ -54,6 +54,9 @@ STRUCTS = {
                                             "lo2", "hi2", "origin2", "MZ", "MG", "precision"]),
     "dpm_dd2_info": (abi.dpm_dd2_info, ["N", "h", "precision", "n_mplus", "n_gin", "n_gamma", "n_rows",
                                         "n_wedge", "ncol", "sigma"]),
+    "dpm_ml_params": (abi.dpm_ml_params, ["center", "L", "radii", "N", "lo", "hi", "K", "KG", "precision"]),
+    "dpm_ml_info": (abi.dpm_ml_info, ["L", "N", "h", "precision", "n_mplus", "n_gin", "n_gamma", "ncol",
+                                      "sigma"]),
 }
 
 

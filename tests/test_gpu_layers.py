@@ -1,0 +1,163 @@
+"""GPU parity of the layered domain decomposition (a ball and concentric
+shells, each on its own grid, coupled through one shared 3-term series per
+interface) through dpm_ml_*: the stacked BEP matrix, the coupled elliptic solve
+with Neumann data and the coupled time loop against the oracle; grouped and
+separate launches bit-identical; two layers give Case 1's matrix."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import dpm_oracle as O
+from paper_1811_03557_gb300 import abi
+from paper_1811_03557_gb300.workloads import Gaussian, manufactured_grad, manufactured_u
+
+pytestmark = pytest.mark.gpu
+
+SIGMA = 1001.0
+TOL = {abi.DPM_PREC_FP64: 1e-11, abi.DPM_PREC_FP32: 1e-5}
+RADII, NS = [0.4, 0.7, 1.0], [20, 24, 28]
+
+
+def grids(radii, Ns):
+    out = []
+    for r, N in zip(radii, Ns):
+        h = 2 * r / (N - 3)
+        out.append((N, -r - 2 * h, r + 2 * h))
+    return out
+
+
+def gpu_matrix(ml):
+    info = abi.dpm_ml_get_info(ml)
+    m = sum(info.n_gin[l] for l in range(info.L))
+    A = torch.empty(m * info.ncol, dtype=torch.float64, device="cuda")
+    abi.dpm_ml_matrix(ml, A)
+    torch.cuda.synchronize()
+    return A.cpu().numpy().reshape(info.ncol, m).T
+
+
+@pytest.mark.parametrize("prec,tol", [(abi.DPM_PREC_FP64, 1e-12), (abi.DPM_PREC_FP32, 2e-5)])
+def test_bep_matrix_matches_oracle(ctx, prec, tol):
+    K, KG = [3, 4], 3
+    S = O.MLSetup((0.0, 0.0, 0.0), RADII, grids(RADII, NS), K, KG, SIGMA)
+    ml = abi.dpm_ml_build(ctx, abi.ml_params((0.0, 0.0, 0.0), RADII, grids(RADII, NS), K, KG, prec), SIGMA)
+    try:
+        A = gpu_matrix(ml)
+    finally:
+        abi.dpm_ml_destroy(ml)
+    assert A.shape == S.A.shape
+    scale = np.max(np.abs(S.A), axis=0)
+    err = np.max(np.abs(A - S.A), axis=0) / scale
+    assert np.max(err) < tol, np.max(err)
+    # block structure: exact zeros off each layer's own spheres
+    rows = np.cumsum([0] + [len(sd.gin_idx) for sd in S.sub])
+    for l in range(S.L):
+        for m in range(1, S.L + 1):
+            touches = l in ((m - 1, m) if m < S.L else (S.L - 1,))
+            if not touches:
+                assert not np.any(A[rows[l]:rows[l + 1], S.off[m - 1]:S.off[m]])
+
+
+def test_two_layers_give_case_1(ctx):
+    radii, Ns = [0.5, 1.0], [20, 20]
+    g = grids(radii, Ns)
+    ml = abi.dpm_ml_build(ctx, abi.ml_params((0.0, 0.0, 0.0), radii, g, [4], 4, abi.DPM_PREC_FP64), SIGMA)
+    d = abi.dpm_dd_build(ctx, abi.dd_params((0.0, 0.0, 0.0), 0.5, 1.0, g[0][0], g[0][1], g[0][2], g[1][0], g[1][1],
+                                            g[1][2], 4, 4, abi.DPM_PREC_FP64), SIGMA)
+    try:
+        A = gpu_matrix(ml)
+        info = abi.dpm_dd_get_info(d)
+        m = info.n_gin[0] + info.n_gin[1]
+        B = torch.empty(m * info.ncol, dtype=torch.float64, device="cuda")
+        abi.dpm_dd_matrix(d, B)
+        torch.cuda.synchronize()
+        B = B.cpu().numpy().reshape(info.ncol, m).T
+    finally:
+        abi.dpm_ml_destroy(ml)
+        abi.dpm_dd_destroy(d)
+    np.testing.assert_allclose(A, B, rtol=0, atol=1e-13 * np.max(np.abs(B)))
+
+
+@pytest.mark.parametrize("prec", [abi.DPM_PREC_FP64, abi.DPM_PREC_FP32])
+def test_elliptic_solve_matches_oracle(ctx, prec):
+    K, KG = [6, 6], 6
+    S = O.MLSetup((0.0, 0.0, 0.0), RADII, grids(RADII, NS), K, KG, SIGMA)
+    fs = []
+    for sd in S.sub:
+        X, Y, Z = O.mesh(sd.N, sd.lo, sd.hi)
+        f = (SIGMA + 1) * manufactured_u(X, Y, Z)
+        fs.append(f.astype(np.float32).astype(np.float64) if prec == abi.DPM_PREC_FP32 else f)
+    sd = S.sub[-1]
+    gn = np.sum(manufactured_grad(sd.xf[:, 0], sd.xf[:, 1], sd.xf[:, 2]) * sd.normal, axis=1)
+    us, _ = O.ml_elliptic_solve(S, fs, gn)
+    dt = torch.float64 if prec == abi.DPM_PREC_FP64 else torch.float32
+    ml = abi.dpm_ml_build(ctx, abi.ml_params((0.0, 0.0, 0.0), RADII, grids(RADII, NS), K, KG, prec), SIGMA)
+    try:
+        fd = [torch.from_numpy(f).to("cuda", dt).contiguous() for f in fs]
+        ud = [torch.empty_like(f) for f in fd]
+        abi.dpm_ml_solve(ml, fd, ud, neumann=torch.from_numpy(gn).cuda())
+        torch.cuda.synchronize()
+    finally:
+        abi.dpm_ml_destroy(ml)
+    for sd, ref, got in zip(S.sub, us, ud):
+        g = got.cpu().numpy().astype(np.float64)
+        m = sd.sets["Np"]
+        rel = np.max(np.abs(np.where(m, g - ref, 0))) / np.max(np.abs(np.where(m, ref, 0)))
+        assert rel < TOL[prec], rel
+
+
+@pytest.mark.parametrize("prec,tol", [(abi.DPM_PREC_FP64, 1e-10), (abi.DPM_PREC_FP32, 1e-4)])
+def test_time_loop_matches_oracle(ctx, prec, tol):
+    radii, Ns = [0.2, 0.35, 0.5], [20, 24, 28]
+    g = grids(radii, Ns)
+    h = min((hi - lo) / (N + 1) for N, lo, hi in g)
+    rho0, c0 = Gaussian(200.0, 20.0), Gaussian(100.0, 10.0)
+    st = O.MLPKSState((0.0, 0.0, 0.0), radii, g, [2, 2], 2, 1.0, 0.5 * h * h, rho0, c0, dt_mode="fixed")
+    pk = abi.dpm_ml_pks_create(ctx, abi.ml_params((0.0, 0.0, 0.0), radii, g, [2, 2], 2, prec), 1.0, 0.5 * h * h,
+                               0, 0, 1, rho0, c0)
+    try:
+        for _ in range(3):
+            st.step()
+            s = abi.dpm_ml_pks_step(pk, 1, True)
+            d = st.diagnostics()
+            for key in ("mass", "max_rho", "m2", "free_energy"):
+                assert abs(getattr(s, key) - d[key]) <= tol * abs(d[key]), (key, getattr(s, key), d[key])
+        dt = torch.float64 if prec == abi.DPM_PREC_FP64 else torch.float32
+        for l, sd in enumerate(st.sub):
+            rho = torch.empty(sd.N ** 3, dtype=dt, device="cuda")
+            c = torch.empty_like(rho)
+            abi.dpm_ml_pks_get_state(pk, l, rho, c)
+            torch.cuda.synchronize()
+            m = sd.sets["Np"].reshape(-1)
+            for got, ref in ((rho, st.rho[l]), (c, st.c[l])):
+                gg = got.cpu().numpy().astype(np.float64)
+                r = ref.reshape(-1)
+                assert np.max(np.abs(gg[m] - r[m])) <= tol * np.max(np.abs(r[m]))
+    finally:
+        abi.dpm_ml_pks_destroy(pk)
+
+
+def test_grouped_launch_matches_separate(ctx):
+    radii, Ns = [0.2, 0.35, 0.5], [20, 32, 44]
+    g = grids(radii, Ns)
+    h = min((hi - lo) / (N + 1) for N, lo, hi in g)
+    P = abi.ml_params((0.0, 0.0, 0.0), radii, g, [1, 1], 1, abi.DPM_PREC_FP32)
+    states = []
+    for group in ("1", "0"):
+        os.environ["DPM_DD_GROUP"] = group
+        try:
+            pk = abi.dpm_ml_pks_create(ctx, P, 1.0, 0.5 * h * h, 1, 0, 1, Gaussian(200.0, 20.0), Gaussian(100.0, 10.0))
+            abi.dpm_ml_pks_step(pk, 3, False)
+            out = []
+            for l, N in enumerate(Ns):
+                rho = torch.empty(N ** 3, device="cuda")
+                abi.dpm_ml_pks_get_state(pk, l, rho, None)
+                out.append(rho)
+            torch.cuda.synchronize()
+            abi.dpm_ml_pks_destroy(pk)
+            states.append([t.cpu().numpy() for t in out])
+        finally:
+            del os.environ["DPM_DD_GROUP"]
+    for a, b in zip(*states):
+        assert np.array_equal(a, b)
