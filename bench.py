@@ -306,6 +306,13 @@ def run_ours(args):
         sd_dd = sd_dd_speedup(ctx, 256, ((128, 128), (128, 64)), 6e-5)
         sd_dd["paper_R_S"] = {"255 vs 127/127": 6.46, "255 vs 127/63": 9.26,
                               "hardware": "32-core CPU node, FFTW3 + OpenMP"}
+    layers = None
+    if rank == 0 and not args.no_aux:
+        # the uneven-box layered decomposition: ball N = 192 + 7 shells of seeded
+        # N in [48, 128], every SIMT grid's solves in one grouped set of launches
+        from paper_1811_03557_gb300.experiments import run_layers_uneven
+        layers = run_layers_uneven(ctx, steps=200)
+        layers["grid_pts_per_s"] = layers["grid_pts_per_step"] / (layers["ms_per_step"] / 1e3)
 
     serving = None
     if rank == 0 and args.serving_requests > 0:
@@ -329,7 +336,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": f"inputs larger than L2 ({spp * N ** 3 * 4 / 1e9:.2f} GB batch per step)"},
             "clocks": clk, "gpu_launches": int(launches), "roofline": roof, "kernels": prof,
-            "e2e": e2e, "cpu_baseline": cpu, "aux_solve": aux, "sd_dd_test_a": sd_dd, "serving": serving,
+            "e2e": e2e, "cpu_baseline": cpu, "aux_solve": aux, "sd_dd_test_a": sd_dd, "layers_uneven": layers, "serving": serving,
             "graph": not args.no_graph, "kernel_profile_steps": nprof,
             "sanity": {"finite": bool(finite), "mass": st.mass},
         }

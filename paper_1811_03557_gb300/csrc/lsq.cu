@@ -716,8 +716,14 @@ static int lsq_factor_impl(LsqFactor &f, bool sync, cudaStream_t s) {
     }
     if (!rinv_done) {
         DPM_PROF("lsq_rinv", s);
-        const int warps = 4;
-        k_rinv<<<(n + warps - 1) / warps, 32 * warps, sizeof(double) * warps * n, s>>>(n, R, Rinv, status);
+        // one warp per column of R^-1, each with an n-vector in shared memory
+        const size_t per = sizeof(double) * (size_t)n;
+        const int warps = (int)std::max<size_t>(1, std::min<size_t>(4, (200 * 1024) / per));
+        const size_t smem = per * warps;
+        if (smem > 227 * 1024) { set_error("least squares: n = %d too large for R^-1", n); return DPM_EINVAL; }
+        if (smem > 48 * 1024)
+            DPM_CUDA(cudaFuncSetAttribute(k_rinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_rinv<<<(n + warps - 1) / warps, 32 * warps, smem, s>>>(n, R, Rinv, status);
         DPM_LAUNCHED();
     }
     if (!sync) return DPM_OK;

@@ -213,6 +213,74 @@ def run_test_b_dd(ctx, N1: int = 128, N2: int = 128, MZ: int = 20, MG: int = 150
             "setup_s": t_setup, "wall_s": wall, "last": series[-1] if series else None, "series": series}
 
 
+def layered_uneven_config(seed: int = 0, n_shells: int = 7, r_ball: float = 0.4, R: float = 1.0):
+    """The uneven-box layered workload: a fine inner ball r < 0.4 on a 192^3 grid
+    and n_shells concentric shells of equal thickness out to R = 1, shell grids
+    N ~ U{48..128}, interface degrees K ~ U{6..10} (seeded), Gamma degree 8; each
+    box [-r - 2.5h, r + 2.5h]^3 around its outer sphere, h = 2r/(N - 4) (half a
+    cell more than two layers of margin, so that no node rounds onto the sphere
+    within two layers of a face)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    radii = [r_ball] + [r_ball + (R - r_ball) * l / n_shells for l in range(1, n_shells + 1)]
+    Ns = [192] + [int(v) for v in rng.integers(48, 129, size=n_shells)]
+    Ks = [int(v) for v in rng.integers(6, 11, size=n_shells)]
+    grids = []
+    for r, N in zip(radii, Ns):
+        h = 2.0 * r / (N - 4)
+        grids.append((N, -r - 2.5 * h, r + 2.5 * h))
+    return radii, grids, Ks, 8
+
+
+def run_layers_uneven(ctx, steps: int = 200, seed: int = 0, precision=None, group: bool = True, stream=None):
+    """PKS steps of Test (A)'s data on the uneven-box layered decomposition
+    (ball + 7 shells of different N, all sub-domain solves of the SIMT grids in
+    one grouped set of launches per batch).  dt: 0.9 x the CFL bound of the
+    initial c on the finest grid (max |grad c0| = 5000 e^{-1/2}), fixed, so the
+    stacked BEP is built once.  Returns the sizes, the build time and the time
+    per step."""
+    import os
+
+    import torch
+
+    from . import abi
+    from .workloads import TEST_A_C0, TEST_A_RHO0
+
+    if precision is None:
+        precision = abi.DPM_PREC_FP32
+    radii, grids, Ks, KG = layered_uneven_config(seed)
+    hmin = min((hi - lo) / (N + 1) for N, lo, hi in grids)
+    gmax = 5000.0 * 2.718281828459045 ** -0.5
+    dt = 0.9 * hmin / (6.0 * gmax)
+    old = os.environ.get("DPM_DD_GROUP")
+    os.environ["DPM_DD_GROUP"] = "1" if group else "0"
+    try:
+        P = abi.ml_params((0.0, 0.0, 0.0), radii, grids, Ks, KG, precision)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pk = abi.dpm_ml_pks_create(ctx, P, 1.0, dt, 0, 0, 1, TEST_A_RHO0, TEST_A_C0, stream=stream)
+        abi.dpm_ml_pks_step(pk, 1, False, stream=stream)  # Steps 1-2 (the stacked BEP) + the first step
+        torch.cuda.synchronize()
+        t_build = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        abi.dpm_ml_pks_step(pk, steps, False, stream=stream)
+        torch.cuda.synchronize()
+        t_steps = time.perf_counter() - t0
+        st = abi.dpm_ml_pks_step(pk, 0, True, stream=stream)
+        info = None
+        abi.dpm_ml_pks_destroy(pk)
+    finally:
+        if old is None:
+            del os.environ["DPM_DD_GROUP"]
+        else:
+            os.environ["DPM_DD_GROUP"] = old
+    grid_pts = sum(N ** 3 for N, _, _ in grids)
+    return {"radii": radii, "N": [g[0] for g in grids], "K": Ks, "KG": KG, "dt": dt, "steps": steps,
+            "grouped": group, "first_step_with_build_s": t_build, "ms_per_step": 1e3 * t_steps / steps,
+            "aps_per_step": 4 * len(grids), "grid_pts_per_step": 4 * grid_pts,
+            "last": {"t": st.t, "max_rho": st.max_rho, "mass": st.mass, "free_energy": st.free_energy}}
+
+
 def _mplus_mask(ctx, geom, N, lo, hi):
     import types
 
@@ -333,10 +401,17 @@ def main(argv=None):
                     help="single domain (N) against the domain decomposition, R_S = T_SD/T_DD")
     ap.add_argument("--time-convergence", action="store_true",
                     help="convergence in time at fixed meshes (N, DD 128/128 and 128/64), FP64")
+    ap.add_argument("--layers", action="store_true",
+                    help="the uneven-box layered decomposition (ball N=192 + 7 shells), grouped vs separate")
     ap.add_argument("--test-b", default="",
                     help="Test (B) with the Case 2 decomposition: N1/N2/MZ/MG, e.g. 128/128/20/150")
     a = ap.parse_args(argv)
     ctx = abi.dpm_ctx_create(0)
+    if a.layers:
+        out = [run_layers_uneven(ctx, group=g) for g in (True, False)]
+        abi.dpm_ctx_destroy(ctx)
+        print(json.dumps(out))
+        return
     if a.test_b:
         N1, N2, MZ, MG = (int(v) for v in a.test_b.split("/"))
         res = run_test_b_dd(ctx, N1, N2, MZ, MG, T=a.T)
