@@ -13,7 +13,7 @@ auxiliary problem is the dense 3D DST-I written out with the explicit sine
 matrix (a library matmul per axis), the point sets are the literal set unions
 of Definition 2.1, and so on.
 
-Readings where the paper is silent or ambiguous (all listed in the design doc):
+Readings where the paper is silent or ambiguous:
   * grid: N interior nodes per axis of the cube [lo, hi]^3, x_j = lo + j*h,
     j = 1..N, h = (hi - lo)/(N + 1); the Dirichlet ghost layer j = 0, N+1 is
     the set N^0 \\ M^0.
@@ -31,7 +31,7 @@ Readings where the paper is silent or ambiguous (all listed in the design doc):
 Parity pins: every function here is checked by tests/test_oracle_*.py against
 closed forms, brute force, library routines or the paper's theorems.  The
 ellipsoid foot point is pinned by its optimality conditions and the sphere
-limit only ("parity unpinned" beyond Newton convergence, see DESIGN.md).
+limit only ("parity unpinned" beyond Newton convergence).
 """
 from __future__ import annotations
 
