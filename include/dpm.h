@@ -43,7 +43,7 @@ extern "C" {
 #define DPM_ENOMEM       -2   /* device allocation failed                     */
 #define DPM_ETIMEOUT     -3   /* a bounded device wait gave up                */
 #define DPM_ENUMERIC     -4   /* non-finite value or singular factorisation  */
-#define DPM_EUNSUPPORTED -5   /* valid request this build cannot serve       */
+#define DPM_EUNSUPPORTED -5   /* valid request the library does not serve    */
 #define DPM_ECUDA        -6   /* a CUDA runtime call failed                   */
 
 /* ---- arithmetic of the auxiliary-problem (AP) solve -------------------- */
