@@ -331,19 +331,53 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
     }
     bool ok = true;
     bool pre = false;  // raw was zeroed for this shell-only item during the last item
+    // forward pass: the next item's shell values (linear node index within the
+    // plane, value) are loaded into registers during this item's output phase, up
+    // to kPre per thread, so their global-memory latency is hidden
+    constexpr int kPre = 4;
+    int pidx[kPre], pcnt = 0, pe0 = 0, pe1 = 0;  // pe0, pe1: the prefetched item's shell range
+    float pval[kPre];
+    bool pref = false;  // pidx / pval hold this item's first kPre * kPlaneThreads entries
     for (; item < nitems && ok; item += gridDim.x) {
         const int b = item / kN, i = item % kN;
         const ApRhs<float> r = rhs[b];
         const int nx = item + gridDim.x;
         const float *nsrc = nullptr;
         bool nsparse = false;  // next item: shell-only right-hand side (a BEP column)
+        int n_e0 = 0, n_e1 = 0;
+        const float *n_qs = nullptr;
         if (nx < nitems && !skippable(nx)) {
             const ApRhs<float> &rn = rhs[nx / kN];
             nsrc = plane_src<INV>(rn, work, nx / kN, nx % kN);
             nsparse = !INV && !rn.f && rn.dens;
+            if (!INV && rn.dens) {
+                n_e0 = a.rp_shell[(int64_t)(nx % kN) * kN];
+                n_e1 = a.rp_shell[(int64_t)(nx % kN + 1) * kN];
+                n_qs = a.qsh + (size_t)(nx / kN) * a.n_shell;
+            }
         }
+        const bool have_pref = pref;
+        pref = false;
+        auto prefetch_next = [&]() {
+            if (INV || !n_qs) return;
+            const int off = (nx % kN) * kN * kN;
+            pcnt = 0;
+            pe0 = n_e0;
+            pe1 = n_e1;
+#pragma unroll
+            for (int q = 0; q < kPre; ++q) {
+                const int e = n_e0 + t + q * kPlaneThreads;
+                if (e < n_e1) {
+                    pidx[q] = a.shell[e] - off;
+                    pval[q] = n_qs[e];
+                    pcnt = q + 1;
+                }
+            }
+            pref = true;
+        };
         // stage the next item's input in raw (free whenever this is called)
         auto stage_next = [&]() {
+            prefetch_next();
             if (nsrc) {
                 if (t == 0) {
                     tc::mbar_arrive_expect_tx(bar_ld, kRawBytes);
@@ -406,10 +440,18 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
             __syncthreads();
         }
         if (!INV && r.dens) {
-            const int e0 = a.rp_shell[(int64_t)i * kN], e1 = a.rp_shell[(int64_t)(i + 1) * kN];
+            const int e0 = have_pref ? pe0 : a.rp_shell[(int64_t)i * kN];
+            const int e1 = have_pref ? pe1 : a.rp_shell[(int64_t)(i + 1) * kN];
             const float *qs = a.qsh + (size_t)b * a.n_shell;
             const int off = i * kN * kN;
-            for (int e = e0 + t; e < e1; e += kPlaneThreads) raw[a.shell[e] - off] += qs[e];
+            int e = e0 + t;
+            if (have_pref) {
+#pragma unroll
+                for (int q = 0; q < kPre; ++q)
+                    if (q < pcnt) raw[pidx[q]] += pval[q];
+                e += kPre * kPlaneThreads;
+            }
+            for (; e < e1; e += kPlaneThreads) raw[a.shell[e] - off] += qs[e];
             __syncthreads();
         }
         // ---- phase A: rows -> folded, split operands ---------------------------
@@ -519,6 +561,15 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
         } else {
             float *stage = raw;  // 128 x 128 fp32 (the operand region, free again)
             const int64_t pbase = (int64_t)i * kN * kN;
+            // the first kPre * kPlaneThreads gamma_in nodes of the plane: their
+            // positions are loaded now, so the gather below does not wait on them
+            if (r.out_trace) {
+#pragma unroll
+                for (int q = 0; q < kPre; ++q) {
+                    const int e = ge0 + t + q * kPlaneThreads;
+                    if (e < ge1) pidx[q] = a.gin[e];
+                }
+            }
 #pragma unroll
             for (int c0 = kH * hc; c0 < kH * hc + kH; c0 += 16) {
                 float d[16];
@@ -540,7 +591,12 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
             }
             if (r.out_trace) {
                 __syncthreads();
-                for (int e = ge0 + t; e < ge1; e += kPlaneThreads) {
+#pragma unroll
+                for (int q = 0; q < kPre; ++q) {
+                    const int e = ge0 + t + q * kPlaneThreads;
+                    if (e < ge1) r.out_trace[e] = stage[((pidx[q] / kN) % kN) * kN + pidx[q] % kN];
+                }
+                for (int e = ge0 + t + kPre * kPlaneThreads; e < ge1; e += kPlaneThreads) {
                     const int pg = a.gin[e];
                     r.out_trace[e] = stage[((pg / kN) % kN) * kN + pg % kN];
                 }
