@@ -391,9 +391,9 @@ def roofline(w, prec, prof, spp):
     # measured DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one
     # ncu capture of the 162-column BEP batch, per right-hand side; scaled to the
     # step's average launch (traffic grows with the number of right-hand sides)
-    measured_per_rhs = {"tc_plane_fwd": (0.037402e9 + 1.297699e9) / 162,
-                        "tc_pencil": (1.359100e9 + 1.297976e9) / 162,
-                        "tc_plane_inv": (1.107182e9 + 0.020088e9) / 162}
+    measured_per_rhs = {"tc_plane_fwd": (0.037332e9 + 1.297840e9) / 162,
+                        "tc_pencil": (1.359097e9 + 1.297749e9) / 162,
+                        "tc_plane_inv": (1.106946e9 + 0.019860e9) / 162}
     traffic = measured_per_rhs[name] * rhs_per_launch if name in measured_per_rhs else None
     return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s",
             "frac": ach / peak, "traffic": traffic, "bytes_per_launch": bytes_per,
