@@ -193,6 +193,7 @@ struct LsqFactor {
     int m = 0, n = 0;
     int method = kMixed;
     bool equilibrated = false;
+    bool rinv32 = false;  // R^{-1} stored in FP32 (the in-shared-memory mixed factor)
     DevBuf A;      // double[m*n] column-major (Householder overwrites it)
     DevBuf tau;    // double[n] Householder scalars
     DevBuf X;      // scratch of the Gram / Cholesky factorisation

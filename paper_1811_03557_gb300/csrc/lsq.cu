@@ -94,37 +94,104 @@ __global__ void k_extract_r(int m, int n, const double *A, const double *rdiag, 
 }
 
 // y[q][c] = sum_r A0[r][c] b[q][r]  (b in T, row stride ldb)
-template <class T>
-__global__ void k_atb(int m, int n, const double *A0, const T *b, int ldb, double *y, int nr,
-                      const double *colscale) {
-    __shared__ double sh[32];
-    int c = blockIdx.x, q = blockIdx.y;
+// part[sl][q][c] = sum over the rows of slice sl of A0[r][c] b[q][r]: one CTA
+// per (column, row slice, group of up to kAtbQ right-hand sides), so that the
+// FP64 work (which runs at a small fraction of the FP32 rate) spreads evenly
+// over all SMs; kAtbU rows per thread in flight, fixed-order block sums.  The
+// slices are added (in slice order) where y is consumed (k_trimv).
+constexpr int kAtbQ = 4, kAtbU = 4, kAtbT = 256, kAtbMaxSlices = 16;
+__global__ void __launch_bounds__(kAtbT) k_atb(int m, int n, const double *__restrict__ A0,
+                                               const double *__restrict__ b, int ldb,
+                                               double *__restrict__ part, int nr, int rows_per) {
+    __shared__ double sh[kAtbQ][kAtbT / 32];
+    const int c = blockIdx.x, sl = blockIdx.y, q0 = blockIdx.z * kAtbQ, nq = min(kAtbQ, nr - q0);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int r_begin = sl * rows_per, r_end = min(m, r_begin + rows_per);
     const double *a = A0 + (size_t)c * m;
-    const T *bq = b + (size_t)q * ldb;
-    double s = 0.0;
-    for (int r = threadIdx.x; r < m; r += blockDim.x) s += a[r] * (double)bq[r];
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) y[(size_t)q * n + c] = colscale ? s * colscale[c] : s;
+    double acc[kAtbQ] = {};
+    for (int r0 = r_begin + t; r0 < r_end; r0 += kAtbU * kAtbT) {
+        double av[kAtbU];
+#pragma unroll
+        for (int u = 0; u < kAtbU; ++u) {
+            const int r = r0 + u * kAtbT;
+            av[u] = r < r_end ? a[r] : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < kAtbQ; ++q) {
+            if (q < nq) {
+                const double *bq = b + (size_t)(q0 + q) * ldb;
+#pragma unroll
+                for (int u = 0; u < kAtbU; ++u) {
+                    const int r = r0 + u * kAtbT;
+                    if (r < r_end) acc[q] = fma(av[u], bq[r], acc[q]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kAtbQ; ++q) {
+        double v = acc[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[q][warp] = v;
+    }
+    __syncthreads();
+    if (t < nq) {
+        double v = 0.0;
+#pragma unroll
+        for (int w = 0; w < kAtbT / 32; ++w) v += sh[t][w];
+        part[((size_t)sl * nr + q0 + t) * n + c] = v;
+    }
 }
 
-// res[q][r] = b[q][r] - sum_c A0[r][c] C[q][c]
+// out[q][r] = (double) b[q][r] (the FP32 right-hand sides, converted once)
+__global__ void k_to_double(int m, int nr, const float *__restrict__ b, int ldb, double *__restrict__ out) {
+    const size_t total = (size_t)m * nr;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x)
+        out[e] = (double)b[(e / m) * ldb + e % m];
+}
+
+// res[q][r] = b[q][r] - sum_c A0[r][c] C[q][c].  A CTA takes 32 rows (the
+// lanes) and up to kAtbQ right-hand sides; its 8 warps take the columns
+// c = w, w + 8, ... and the 8 partial sums are added in warp order.
+constexpr int kResW = 8;
 template <class T>
-__global__ void k_resid(int m, int n, const double *A0, const T *b, int ldb, const double *C,
-                        double *res, int nr) {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    int q = blockIdx.y;
-    if (r >= m) return;
-    const double *cq = C + (size_t)q * n;
-    double s0 = (double)b[(size_t)q * ldb + r], s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int c = 0;
-    for (; c + 3 < n; c += 4) {
-        s0 -= A0[(size_t)c * m + r] * cq[c];
-        s1 -= A0[(size_t)(c + 1) * m + r] * cq[c + 1];
-        s2 -= A0[(size_t)(c + 2) * m + r] * cq[c + 2];
-        s3 -= A0[(size_t)(c + 3) * m + r] * cq[c + 3];
+__global__ void __launch_bounds__(32 * kResW) k_resid(int m, int n, const double *A0, const T *b, int ldb,
+                                                      const double *C, double *res, int nr) {
+    __shared__ double sh[kResW][kAtbQ][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = blockIdx.x * 32 + lane;
+    const int q0 = blockIdx.y * kAtbQ, nq = min(kAtbQ, nr - q0);
+    double s[kAtbQ] = {};
+    if (r < m) {
+        int c = warp;
+        for (; c + 3 * kResW < n; c += 4 * kResW) {
+            double av[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) av[u] = A0[(size_t)(c + u * kResW) * m + r];
+#pragma unroll
+            for (int q = 0; q < kAtbQ; ++q)
+                if (q < nq) {
+                    const double *cq = C + (size_t)(q0 + q) * n;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) s[q] = fma(av[u], cq[c + u * kResW], s[q]);
+                }
+        }
+        for (; c < n; c += kResW) {
+            const double av = A0[(size_t)c * m + r];
+#pragma unroll
+            for (int q = 0; q < kAtbQ; ++q)
+                if (q < nq) s[q] = fma(av, C[(size_t)(q0 + q) * n + c], s[q]);
+        }
     }
-    for (; c < n; ++c) s0 -= A0[(size_t)c * m + r] * cq[c];
-    res[(size_t)q * m + r] = (s0 + s1) + (s2 + s3);
+#pragma unroll
+    for (int q = 0; q < kAtbQ; ++q) sh[warp][q][lane] = s[q];
+    __syncthreads();
+    if (warp < nq && r < m) {
+        double v = 0.0;
+#pragma unroll
+        for (int w = 0; w < kResW; ++w) v += sh[w][warp][lane];
+        res[(size_t)(q0 + warp) * m + r] = (double)b[(size_t)(q0 + warp) * ldb + r] - v;
+    }
 }
 
 // G partial sums: part[chunk][i][j] = sum over the chunk's rows of A[r][i] A[r][j]
@@ -175,17 +242,40 @@ __global__ void k_syrk_part(int m, int n, const double *A, int rows_per, double 
         }
 }
 
-// G[i][j] = sum_chunk part[chunk][i][j] in chunk order, for j >= i.
-__global__ void k_syrk_reduce(int n, int nchunks, const double *part, double *G) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n * n) return;
+// G[i][j] = sum over chunks of part[chunk][i][j], for j >= i.  A CTA takes 32
+// consecutive elements (the lanes); warp w sums the chunks w, w + 8, ... in
+// order and the 8 warp sums are added in warp order (fixed, deterministic).
+constexpr int kRedW = 8;
+template <class P, class O>
+__global__ void __launch_bounds__(32 * kRedW) k_syrk_reduce(int n, int nchunks, const P *part, O *G) {
+    __shared__ double sh[kRedW][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int idx = blockIdx.x * 32 + lane;
     const int i = idx / n, j = idx % n;
-    if (j < i) return;
-    const int bi = i / kGT, bj = j / kGT;  // only upper tiles were written
-    if (bj < bi) return;
+    const bool on = idx < n * n && j >= i;  // upper triangle: only upper tiles were written
     double s = 0.0;
-    for (int c = 0; c < nchunks; ++c) s += part[(size_t)c * n * n + idx];
-    G[idx] = s;
+    if (on) {
+        const size_t nn = (size_t)n * n;
+        int c = warp;
+        for (; c + 3 * kRedW < nchunks; c += 4 * kRedW) {
+            double v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = (double)part[(size_t)(c + u * kRedW) * nn + idx];
+            s += v[0];
+            s += v[1];
+            s += v[2];
+            s += v[3];
+        }
+        for (; c < nchunks; c += kRedW) s += (double)part[(size_t)c * nn + idx];
+    }
+    sh[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0 && on) {
+        double v = 0.0;
+#pragma unroll
+        for (int w = 0; w < kRedW; ++w) v += sh[w][lane];
+        G[idx] = (O)v;
+    }
 }
 
 // d[j] = 1 / ||A[:, j]||_2 (column equilibration; FP64)
@@ -193,25 +283,53 @@ __global__ void k_colscale(int m, const double *A, double *d) {
     __shared__ double sh[32];
     const int j = blockIdx.x;
     const double *a = A + (size_t)j * m;
+    const int T_ = blockDim.x;
     double s = 0.0;
-    for (int r = threadIdx.x; r < m; r += blockDim.x) s += a[r] * a[r];
+    for (int r0 = threadIdx.x; r0 < m; r0 += kAtbU * T_) {
+        double av[kAtbU];
+#pragma unroll
+        for (int u = 0; u < kAtbU; ++u) av[u] = r0 + u * T_ < m ? a[r0 + u * T_] : 0.0;
+#pragma unroll
+        for (int u = 0; u < kAtbU; ++u) s = fma(av[u], av[u], s);
+    }
     s = block_sum(s, sh);
     if (threadIdx.x == 0) d[j] = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
 }
 
 // Af = float(A D), column-major like A: the Gram products then read FP32
 // operands (FP64 arithmetic runs at a small fraction of the FP32 rate).
-__global__ void k_scale32(int m, const double *A, const double *d, float *Af) {
+__global__ void k_scale32(int m, const double *__restrict__ A, const double *__restrict__ d,
+                          float *__restrict__ Af) {
     const int j = blockIdx.y;  // column
     const double dj = d[j];
     const double *a = A + (size_t)j * m;
     float *o = Af + (size_t)j * m;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x)
-        o[r] = (float)(a[r] * dj);
+    const int stride = gridDim.x * blockDim.x;
+    for (int r0 = blockIdx.x * blockDim.x + threadIdx.x; r0 < m; r0 += kAtbU * stride) {
+        double av[kAtbU];
+#pragma unroll
+        for (int u = 0; u < kAtbU; ++u) av[u] = r0 + u * stride < m ? a[r0 + u * stride] : 0.0;
+#pragma unroll
+        for (int u = 0; u < kAtbU; ++u)
+            if (r0 + u * stride < m) o[r0 + u * stride] = (float)(av[u] * dj);
+    }
 }
 
-// FP32 Gram partials of the equilibrated matrix A D (upper 64 x 64 tiles),
-// part[chunk][i][j] in float; the chunk sums are added in FP64 by k_syrk_reduce32.
+// Af = float(A), column-major like A (the Gram products read FP32 operands)
+__global__ void k_to_float(size_t total, const double *__restrict__ A, float *__restrict__ Af) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t e0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e0 < total; e0 += kAtbU * stride) {
+        double v[kAtbU];
+#pragma unroll
+        for (int u = 0; u < kAtbU; ++u) v[u] = e0 + u * stride < total ? A[e0 + u * stride] : 0.0;
+#pragma unroll
+        for (int u = 0; u < kAtbU; ++u)
+            if (e0 + u * stride < total) Af[e0 + u * stride] = (float)v[u];
+    }
+}
+
+// FP32 Gram partials of the FP32 copy of A (or of A D; upper 64 x 64 tiles),
+// part[chunk][i][j] in float; the chunk sums are added in FP64 by k_syrk_reduce.
 __global__ void k_syrk32_part(int m, int n, const float *Af, int rows_per, float *part) {
     __shared__ float As[kGR][kGT + 1], Bs[kGR][kGT + 1];
     const int nb = (n + kGT - 1) / kGT;
@@ -256,173 +374,290 @@ __global__ void k_syrk32_part(int m, int n, const float *Af, int rows_per, float
         }
 }
 
-__global__ void k_syrk_reduce32(int n, int nchunks, const float *part, double *G) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n * n) return;
-    const int i = idx / n, j = idx % n;
-    if (j < i) return;
-    double s = 0.0;
-    for (int c = 0; c < nchunks; ++c) s += (double)part[(size_t)c * n * n + idx];
-    G[idx] = s;
+// FP32 Cholesky of the (well-conditioned, equilibrated) Gram matrix G = L L^T
+// and the triangular inverse X = L^{-1}, in one CTA of kCholT threads, blocked
+// by 32.  W (the factor) and X are n x ld floats in shared memory; the row
+// stride ld = 4 (mod 8) keeps 16-byte rows and spreads a warp's float4 loads
+// of 8 different rows over all banks.
+//   per panel p: warp 0 factors the 32 x 32 diagonal block in registers (lane
+//   = row, shuffles) and mirrors it into the block's upper triangle, so that
+//   column j of L_pp is a contiguous row; the rows below solve against it by
+//   right-looking substitution (one thread per row, float4 reads of the
+//   mirror); the trailing lower triangle is updated in 4 x 4 register tiles
+//   (float4 reads of the two panel rows, 16 FMAs per pair of loads).
+//   inverse: warp b inverts diagonal block b (lane = column, right-looking);
+//   M[bi][k] = X_bi,bi L[bi][k] goes to X's (unused) upper triangle,
+//   transposed; then the off-diagonal blocks by block diagonals d = bi - bj:
+//   X[bi][bj] = -sum_{k=bj}^{bi-1} M[bi][k] X[k][bj], both in 4 x 4 tiles.
+// Rinv = R^{-1} = X^T is written in FP32 (it only preconditions the FP64
+// refinement of every solve, so FP32 suffices for this equilibrated matrix);
+// G, the upper triangle of the Gram, is read in FP32.
+// Entries of W above the diagonal outside the current diagonal block and of
+// the padding columns are scratch (tiles straddling the diagonal write them).
+constexpr int kCholT = 384;
+__host__ __device__ constexpr int chol_ld(int n) {
+    return ((n + 3) & ~3) + ((((n + 3) & ~3) & 7) ? 0 : 4);
+}
+__host__ __device__ constexpr size_t chol_smem(int n) {
+    return sizeof(float) * (2 * (size_t)n * chol_ld(n) + (size_t)n + 3 + 64);
 }
 
-// FP32 Cholesky of the (well-conditioned, equilibrated) Gram matrix G = L L^T
-// and the triangular inverse X = L^{-1}, in one CTA, blocked by 32 so that
-// the sequential steps stay inside a warp (register rows and shuffles) and
-// the CTA meets at ~25 barriers:
-//   per panel p: warp 0 factors the diagonal block; one thread per row below
-//   solves its panel row against it; all threads apply the trailing update;
-//   inverse: warp b inverts diagonal block b; M[bi][k] = X_bi,bi L[bi][k] goes
-//   to X's (unused) upper triangle, transposed; then the off-diagonal blocks
-//   by block diagonals d = bi - bj: X[bi][bj] = -sum_{k=bj}^{bi-1} M[bi][k] X[k][bj].
-// Rinv = R^{-1} = X^T is written in FP64.  It only preconditions the FP64
-// refinement of every solve, so FP32 suffices for this equilibrated matrix.
-__global__ void __launch_bounds__(1024) k_cholesky32(int n, const double *G, double *Rinv,
-                                                     int *status) {
-    extern __shared__ float sm32[];
-    float *W = sm32, *X = sm32 + (size_t)n * n;
-    const int t = threadIdx.x, T = blockDim.x, lane = t & 31, warp = t >> 5, nwarp = T >> 5;
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+
+// (I, K) with 0 <= K <= I from the index I (I + 1) / 2 + K of a lower-triangular tile
+__device__ __forceinline__ void tri_decode(int tt, int &I, int &K) {
+    int i = (int)((sqrtf(8.f * (float)tt + 1.f) - 1.f) * 0.5f);
+    while ((i + 1) * (i + 2) / 2 <= tt) ++i;
+    while (i * (i + 1) / 2 > tt) --i;
+    I = i;
+    K = tt - i * (i + 1) / 2;
+}
+
+// With dscale: G is the Gram of A itself; the kernel equilibrates it first,
+// d_j = 1 / sqrt(G_jj) rounded to FP32 (dscale[j] = that value in FP64),
+// and factors D G D.
+__global__ void __launch_bounds__(kCholT) k_cholesky32(int n, const float *G, float *Rinv, int *status,
+                                                       double *dscale) {
+    extern __shared__ __align__(16) float sm32[];
+    const int ld = chol_ld(n);
+    float *W = sm32, *X = sm32 + (size_t)n * ld, *dinv = X + (size_t)n * ld;
+    float *colb = dinv + n + ((4 - (n & 3)) & 3);  // 2 x 32 floats, 16-byte aligned
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    constexpr int NW = kCholT / 32;
     const int nb = (n + 31) >> 5;
-    // G's upper triangle (row-major, read coalesced) -> lower triangle of W
-    for (int j = warp; j < n; j += nwarp)
-        for (int i = lane; i < n; i += 32) {
-            W[i * n + j] = i >= j ? (float)G[(size_t)j * n + i] : 0.f;
-            X[j * n + i] = 0.f;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    // ---- load: G's upper triangle, row j (read coalesced) -> column j of W's
+    // lower triangle; the rest of W and all of X zero
+    for (int q = t; q < n * ld / 4; q += kCholT) {
+        reinterpret_cast<float4 *>(W)[q] = z4;
+        reinterpret_cast<float4 *>(X)[q] = z4;
+    }
+    if (dscale) {
+        for (int i = t; i < n; i += kCholT) {
+            const float g = G[(size_t)i * n + i];
+            const float d = g > 0.f ? 1.f / sqrtf(g) : 1.f;
+            dinv[i] = d;  // the factor's reciprocals overwrite it below
+            dscale[i] = (double)d;
         }
+    }
+    __syncthreads();
+    // 4 rows of G per warp and pass, all 24 loads of a lane in flight (n <= 192)
+    for (int j0 = 4 * warp; j0 < n; j0 += 4 * NW) {
+        float v[4][6];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                const int j = j0 + r, i = 32 * c + lane;
+                v[r][c] = (j < n && i < n && i >= j) ? G[(size_t)j * n + i] : 0.f;
+            }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int j = j0 + r;
+            if (j >= n) break;
+            const float dj = dscale ? dinv[j] : 1.f;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                const int i = 32 * c + lane;
+                if (i < n && i >= j) W[i * ld + j] = dscale ? v[r][c] * dinv[i] * dj : v[r][c];
+            }
+        }
+    }
     __syncthreads();
     for (int p = 0; p < nb; ++p) {
         const int c0 = 32 * p, w = min(32, n - c0);
-        // ---- diagonal block: lane i owns row c0 + i ----------------------------
+        // ---- diagonal block (warp 0); rows/columns past w are an identity pad.
+        // Step j: lane i holds row i of the block (a) and column i of its
+        // inverse X_pp (x); l[:, j] goes through colb and is read back as
+        // broadcast float4 loads, once for both updates:
+        //   a[k] -= l[i][j] l[k][j] (k > j)   and   x[k] -= l[k][j] x[j] (k > j),
+        // after x[j] *= 1 / l[j][j].  Entries above the diagonal of a lane's
+        // row of a are scratch (updated but never read); x stays zero above.
         if (warp == 0) {
-            float a[32];
+            float a[32], x[32];
 #pragma unroll
-            for (int k = 0; k < 32; ++k)
-                a[k] = (lane < w && k <= lane) ? W[(c0 + lane) * n + c0 + k] : 0.f;
+            for (int k = 0; k < 32; ++k) {
+                a[k] = lane < w ? ((k <= lane) ? W[(c0 + lane) * ld + c0 + k] : 0.f) : (k == lane ? 1.f : 0.f);
+                x[k] = k == lane ? 1.f : 0.f;
+            }
             bool bad = false;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-                if (j < w) {
-                    float piv = __shfl_sync(0xffffffffu, a[j], j);
-                    if (!(piv > 0.f) || !isfinite(piv)) {
-                        bad = true;
-                        piv = 1.f;
-                    }
-                    const float lij = a[j] * rsqrtf(piv);  // lane j: sqrt(piv)
-                    if (lane >= j) a[j] = lij;
+                float piv = __shfl_sync(0xffffffffu, a[j], j);
+                if (!(piv > 0.f) || !isfinite(piv)) {
+                    bad = true;
+                    piv = 1.f;
+                }
+                const float rs = rsqrtf(piv);  // 1 / l[j][j]
+                const float lij = a[j] * rs;   // lane j: sqrt(piv)
+                a[j] = lij;
+                float *cb = colb + 32 * (j & 1);  // two buffers: one __syncwarp per step
+                cb[lane] = lij;
+                __syncwarp();
+                x[j] *= rs;
 #pragma unroll
-                    for (int k = j + 1; k < 32; ++k) {
-                        const float lkj = __shfl_sync(0xffffffffu, lij, k);
-                        if (lane >= k) a[k] -= lij * lkj;
-                    }
+                for (int q = (j + 1) / 4; q < 8; ++q) {
+                    const float4 l = ld4(cb + 4 * q);
+                    const float lv[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (4 * q + e > j) {
+                            a[4 * q + e] = fmaf(-lij, lv[e], a[4 * q + e]);
+                            x[4 * q + e] = fmaf(-lv[e], x[j], x[4 * q + e]);
+                        }
                 }
             }
             if (bad && lane == 0) status[0] = 1;
             if (lane < w) {
 #pragma unroll
                 for (int k = 0; k < 32; ++k)
-                    if (k <= lane) W[(c0 + lane) * n + c0 + k] = a[k];
+                    if (k < w) {
+                        if (k <= lane) W[(c0 + lane) * ld + c0 + k] = a[k];  // L[lane][k]
+                        if (k >= lane) X[(c0 + k) * ld + c0 + lane] = x[k];  // X_pp[k][lane]
+                    }
             }
         }
         __syncthreads();
-        // ---- panel rows below: L[i][c0+j] = (W - sum_k L[i][c0+k] L[c0+j][c0+k]) / L[c0+j][c0+j]
-        for (int i = c0 + w + t; i < n; i += T) {
-            float x[32];
-#pragma unroll
-            for (int j = 0; j < 32; ++j) x[j] = j < w ? W[i * n + c0 + j] : 0.f;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                if (j < w) {
-                    float acc = x[j];
-#pragma unroll
-                    for (int k = 0; k < j; ++k) acc -= x[k] * W[(c0 + j) * n + c0 + k];
-                    x[j] = acc / W[(c0 + j) * n + c0 + j];
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-                if (j < w) W[i * n + c0 + j] = x[j];
-        }
-        __syncthreads();
-        // ---- trailing update of the lower triangle ----------------------------------
         const int r0 = c0 + w;
-        // rows of the trailing lower triangle round-robin over the warps, columns over lanes
-        for (int i = r0 + warp; i < n; i += nwarp)
-            for (int k = r0 + lane; k <= i; k += 32) {
-            const float *li = W + i * n + c0, *lk = W + k * n + c0;
-            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-            int j = 0;
-            for (; j + 3 < w; j += 4) {
-                a0 += li[j] * lk[j];
-                a1 += li[j + 1] * lk[j + 1];
-                a2 += li[j + 2] * lk[j + 2];
-                a3 += li[j + 3] * lk[j + 3];
+        if (r0 >= n) break;  // w == 32 below: the panel is a full block
+        // ---- rows below: L[i][c0 + j] = sum_k a[k] X_pp[j][k], a = row i of the
+        // panel.  Four threads per row, thread g taking j = g, g + 4, ...; the
+        // result goes to PT[j][i] = X[c0 + j][i] (X's upper triangle, free
+        // until the inverse) and is copied back into W during the trailing update.
+        {
+            for (int e = t; e < 4 * (n - r0); e += kCholT) {
+                const int i = r0 + (e >> 2), g = e & 3;
+                float acc[8] = {};
+#pragma unroll 2
+                for (int q = 0; q < 8; ++q) {
+                    const float4 av = ld4(W + i * ld + c0 + 4 * q);
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) {
+                        const float4 xv = ld4(X + (c0 + g + 4 * jj) * ld + c0 + 4 * q);
+                        acc[jj] = fmaf(av.x, xv.x, fmaf(av.y, xv.y, fmaf(av.z, xv.z, fmaf(av.w, xv.w, acc[jj]))));
+                    }
+                }
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) X[(c0 + g + 4 * jj) * ld + i] = acc[jj];
             }
-            for (; j < w; ++j) a0 += li[j] * lk[j];
-            W[i * n + k] -= (a0 + a1) + (a2 + a3);
+        }
+        __syncthreads();
+        // ---- trailing lower triangle, 4 x 4 tiles: W[i][k] -= sum_j L[i][c0+j] L[k][c0+j],
+        // the panel read from PT (rows i0..i0+3 and k0..k0+3 are float4s of a PT row)
+        {
+            const int nt = (n - r0 + 3) >> 2;
+            const float *PT = X + c0 * ld;
+            // the panel back into W's lower triangle (columns c0.., not touched below)
+            for (int e = t; e < 32 * (n - r0); e += kCholT) {
+                const int j = e / (n - r0), i = r0 + e % (n - r0);
+                W[i * ld + c0 + j] = PT[j * ld + i];
+            }
+            for (int tt = t; tt < nt * (nt + 1) / 2; tt += kCholT) {
+                int I, K;
+                tri_decode(tt, I, K);
+                const int i0 = r0 + 4 * I, k0 = r0 + 4 * K;
+                float acc[4][4] = {};
+#pragma unroll 8
+                for (int j = 0; j < 32; ++j) {
+                    const float4 li = ld4(PT + j * ld + i0), lk = ld4(PT + j * ld + k0);
+                    const float lv[4] = {li.x, li.y, li.z, li.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        acc[u][0] = fmaf(lv[u], lk.x, acc[u][0]);
+                        acc[u][1] = fmaf(lv[u], lk.y, acc[u][1]);
+                        acc[u][2] = fmaf(lv[u], lk.z, acc[u][2]);
+                        acc[u][3] = fmaf(lv[u], lk.w, acc[u][3]);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (i0 + u < n) {
+                        float4 *o = reinterpret_cast<float4 *>(W + (i0 + u) * ld + k0);
+                        float4 v = *o;
+                        v.x -= acc[u][0]; v.y -= acc[u][1]; v.z -= acc[u][2]; v.w -= acc[u][3];
+                        *o = v;
+                    }
+            }
         }
         __syncthreads();
     }
-    // ---- inverse: diagonal blocks, warp b, lane c = column c of X_bb ----------------
-    for (int bb = warp; bb < nb; bb += nwarp) {
-        const int c0 = 32 * bb, w = min(32, n - c0);
-        float x[32];
+    // ---- M = X_bb L[bi][:bi] for the rows of blocks bi >= 1, stored as
+    // M^T in X's upper triangle: X[c][r] = sum_{s in block bi} X[r][s] L[s][c]
+    {
+        // tiles: per block bi >= 1, (rows of bi)/4 x (32 bi)/4, enumerated by block
+        int base = 0;
+        for (int bi = 1; bi < nb; ++bi) {
+            const int rb = 32 * bi, wb = min(32, n - rb), nrt = (wb + 3) >> 2, nct = 8 * bi;
+            const int cnt = nrt * nct;
+            for (int tt = t - base; tt < cnt; tt += kCholT) {
+                if (tt < 0) continue;
+                const int r0 = rb + 4 * (tt / nct), cc = 4 * (tt % nct);
+                float acc[4][4] = {};
+                for (int q = 0; q < (wb + 3) >> 2; ++q) {
+                    const int s0 = rb + 4 * q;
+                    float4 xr[4], ls[4];
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            float v = 0.f;
-            if (i < w && lane < w && i >= lane) {
-                float acc = (i == lane) ? 1.f : 0.f;
+                    for (int u = 0; u < 4; ++u) {
+                        xr[u] = r0 + u < n ? ld4(X + (r0 + u) * ld + s0) : z4;   // X[r][s0..s0+3]
+                        ls[u] = s0 + u < n ? ld4(W + (s0 + u) * ld + cc) : z4;   // L[s0+u][cc..cc+3]
+                    }
 #pragma unroll
-                for (int k = 0; k < i; ++k)
-                    if (k >= lane) acc -= W[(c0 + i) * n + c0 + k] * x[k];
-                v = acc / W[(c0 + i) * n + c0 + i];
+                    for (int u = 0; u < 4; ++u) {
+                        const float xs[4] = {xr[u].x, xr[u].y, xr[u].z, xr[u].w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            acc[u][0] = fmaf(xs[e], ls[e].x, acc[u][0]);
+                            acc[u][1] = fmaf(xs[e], ls[e].y, acc[u][1]);
+                            acc[u][2] = fmaf(xs[e], ls[e].z, acc[u][2]);
+                            acc[u][3] = fmaf(xs[e], ls[e].w, acc[u][3]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    *reinterpret_cast<float4 *>(X + (cc + v) * ld + r0) =
+                        make_float4(acc[0][v], acc[1][v], acc[2][v], acc[3][v]);
             }
-            x[i] = v;
-        }
-        if (lane < w) {
-#pragma unroll
-            for (int i = 0; i < 32; ++i)
-                if (i < w && i >= lane) X[(c0 + i) * n + c0 + lane] = x[i];
+            base += cnt;
         }
     }
     __syncthreads();
-    // ---- M[bi][k] = X_bi,bi L[bi][k] (k < bi), stored transposed in X's upper triangle
-    for (int r = 32 + warp; r < n; r += nwarp)
-        for (int c = lane; c < (r & ~31); c += 32) {  // (r, c) in the lower off-diagonal blocks
-        const int bi = r >> 5;
-        const int ri = 32 * bi;
-        float a0 = 0.f, a1 = 0.f;
-        int s2 = ri;
-        for (; s2 + 1 <= r; s2 += 2) {
-            a0 += X[r * n + s2] * W[s2 * n + c];
-            a1 += X[r * n + s2 + 1] * W[(s2 + 1) * n + c];
-        }
-        if (s2 <= r) a0 += X[r * n + s2] * W[s2 * n + c];
-        X[c * n + r] = a0 + a1;  // M^T
-    }
-    __syncthreads();
-    // ---- off-diagonal blocks of X by block diagonal d ------------------------------
+    // ---- off-diagonal blocks of X by block diagonal d:
+    // X[r][c] = -sum_{s in [32 bj, 32 bi)} M^T[s][r] X[s][c]
     for (int d = 1; d < nb; ++d) {
-        // rows r of block bi >= d, columns c of block bj = bi - d
-        for (int r = 32 * d + warp; r < n; r += nwarp) {
-            const int bi = r >> 5, bj = bi - d;
-            const int c = 32 * bj + lane;
-            // sum over k = bj .. bi-1 (block rows), s in block k: M[bi](r, s) X(s, c);
-            // the range is a whole number of 32-row blocks
-            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-            const int s_end = 32 * bi;
-            for (int s2 = 32 * bj; s2 < s_end; s2 += 4) {
-                a0 += X[s2 * n + r] * X[s2 * n + c];
-                a1 += X[(s2 + 1) * n + r] * X[(s2 + 1) * n + c];
-                a2 += X[(s2 + 2) * n + r] * X[(s2 + 2) * n + c];
-                a3 += X[(s2 + 3) * n + r] * X[(s2 + 3) * n + c];
+        int base = 0;
+        for (int bj = 0; bj + d < nb; ++bj) {
+            const int bi = bj + d, rb = 32 * bi, wb = min(32, n - rb), nrt = (wb + 3) >> 2;
+            const int cnt = nrt * 8;
+            for (int tt = t - base; tt < cnt; tt += kCholT) {
+                if (tt < 0) continue;
+                const int r0 = rb + 4 * (tt >> 3), cc = 32 * bj + 4 * (tt & 7);
+                float acc[4][4] = {};
+                for (int s = 32 * bj; s < rb; ++s) {
+                    const float4 m = ld4(X + s * ld + r0);  // M^T[s][r0..r0+3]
+                    const float4 x = ld4(X + s * ld + cc);  // X[s][cc..cc+3]
+                    const float mv[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        acc[u][0] = fmaf(mv[u], x.x, acc[u][0]);
+                        acc[u][1] = fmaf(mv[u], x.y, acc[u][1]);
+                        acc[u][2] = fmaf(mv[u], x.z, acc[u][2]);
+                        acc[u][3] = fmaf(mv[u], x.w, acc[u][3]);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (r0 + u < n)
+                        *reinterpret_cast<float4 *>(X + (r0 + u) * ld + cc) =
+                            make_float4(-acc[u][0], -acc[u][1], -acc[u][2], -acc[u][3]);
             }
-            X[r * n + c] = -((a0 + a1) + (a2 + a3));
+            base += cnt;
         }
         __syncthreads();
     }
-    for (int r = warp; r < n; r += nwarp)
+    for (int r = warp; r < n; r += NW)
         for (int c = lane; c < n; c += 32)  // Rinv[r][c] = X[c][r]
-            Rinv[(size_t)r * n + c] = c >= r ? (double)X[c * n + r] : 0.0;
+            Rinv[(size_t)r * n + c] = c >= r ? X[c * ld + r] : 0.f;
 }
 
 // Cholesky G = L L^T (upper triangle of G given) in one CTA; R = L^T row-major.
@@ -490,18 +725,26 @@ __global__ void k_rinv(int n, const double *R, double *Rinv, int *status) {
 
 // out[q][i] (+)= sum_k M[i][k] y[q][k] (TRANS = 0) or sum_k M[k][i] y[q][k]
 // (TRANS = 1), M upper triangular n x n.  One warp per output element.
-template <int TRANS>
-__global__ void k_trimv(int n, const double *M, const double *y, double *out, int nr,
-                        int accumulate, const double *outscale) {
+// With yparts > 1 (TRANS = 1), y holds the row-slice partial sums of A^T b,
+// y[sl][q][k], added here in slice order and scaled by yscale[k] (if given).
+template <int TRANS, class MT>
+__global__ void k_trimv(int n, const MT *M, const double *y, double *out, int nr,
+                        int accumulate, const double *outscale, int yparts = 1,
+                        const double *yscale = nullptr) {
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (gw >= n * nr) return;
     const int q = gw / n, i = gw % n;
     const double *yq = y + (size_t)q * n;
     double s = 0.0;
     if (TRANS == 0) {
-        for (int k = i + lane; k < n; k += 32) s += M[(size_t)i * n + k] * yq[k];
+        for (int k = i + lane; k < n; k += 32) s += (double)M[(size_t)i * n + k] * yq[k];
     } else {
-        for (int k = lane; k <= i; k += 32) s += M[(size_t)k * n + i] * yq[k];
+        for (int k = lane; k <= i; k += 32) {
+            double yk = yq[k];
+            for (int sl = 1; sl < yparts; ++sl) yk += yq[(size_t)sl * nr * n + k];
+            if (yscale) yk *= yscale[k];
+            s += (double)M[(size_t)k * n + i] * yk;
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -586,7 +829,7 @@ static int cholesky_factor(LsqFactor &f, const double *A0, double *R, int *statu
         DPM_PROF("lsq_gram_syrk", s);
         k_syrk_part<<<dim3(ntiles, chunks), 256, 0, s>>>(m, n, A0, rows_per, part);
         DPM_LAUNCHED();
-        k_syrk_reduce<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(n, chunks, part, G);
+        k_syrk_reduce<double, double><<<(unsigned)((nn + 31) / 32), 32 * kRedW, 0, s>>>(n, chunks, part, G);
         DPM_LAUNCHED();
         if (dscale) {
             k_colscale<<<n, 1024, 0, s>>>(m, A0, dscale);
@@ -606,10 +849,11 @@ static int cholesky_factor(LsqFactor &f, const double *A0, double *R, int *statu
     return DPM_OK;
 }
 
-// Mixed precision: column equilibration d (FP64), Gram of A D with FP32
-// products (chunk sums in FP64), FP32 Cholesky; the refinement of every solve
-// is FP64 against the original A (the factor only preconditions it).  Past
-// the in-shared-memory size (2 n^2 floats) the Cholesky of the same Gram runs
+// Mixed precision: Gram of an FP32 copy of A with FP32 products (chunk sums
+// in FP64), column equilibration d_j = 1 / sqrt(G_jj) and FP32 Cholesky of
+// D G D in one CTA; the refinement of every solve is FP64 against the
+// original A (the factor only preconditions it).  Past the in-shared-memory
+// size the Gram is that of A D (d from FP64 column norms), its Cholesky runs
 // in FP64 from global memory and R^-1 is formed separately (*rinv_done = 0).
 static int mixed_factor(LsqFactor &f, const double *A0, double *R, double *Rinv, double *dscale,
                         int *status, int *rinv_done, cudaStream_t s) {
@@ -623,8 +867,8 @@ static int mixed_factor(LsqFactor &f, const double *A0, double *R, double *Rinv,
     const int rows_per = ((m + chunks - 1) / chunks + kGR - 1) / kGR * kGR;
     chunks = (m + rows_per - 1) / rows_per;
     const size_t nn = (size_t)n * n;
-    const size_t smem = 2 * nn * sizeof(float);
-    const bool in_smem = smem <= 226 * 1024;
+    const size_t smem = chol_smem(n);
+    const bool in_smem = smem <= 227 * 1024;
     // partials [chunks][n][n] floats, then G [n][n] (and W [n][n] for the FP64
     // Cholesky), then Af [n][m] floats
     const size_t gbytes = sizeof(double) * nn * (in_smem ? 1 : 2);
@@ -634,13 +878,23 @@ static int mixed_factor(LsqFactor &f, const double *A0, double *R, double *Rinv,
     float *Af = reinterpret_cast<float *>(reinterpret_cast<char *>(G) + gbytes);
     {
         DPM_PROF("lsq_gram_syrk", s);
-        k_colscale<<<n, 1024, 0, s>>>(m, A0, dscale);
-        DPM_LAUNCHED();
-        k_scale32<<<dim3(8, n), 256, 0, s>>>(m, A0, dscale, Af);
-        DPM_LAUNCHED();
+        if (in_smem) {
+            // Gram of float(A); the Cholesky kernel equilibrates it by its diagonal
+            k_to_float<<<4 * 152, 256, 0, s>>>((size_t)m * n, A0, Af);
+            DPM_LAUNCHED();
+        } else {
+            k_colscale<<<n, 1024, 0, s>>>(m, A0, dscale);
+            DPM_LAUNCHED();
+            k_scale32<<<dim3(8, n), 256, 0, s>>>(m, A0, dscale, Af);
+            DPM_LAUNCHED();
+        }
         k_syrk32_part<<<dim3(ntiles, chunks), 256, 0, s>>>(m, n, Af, rows_per, part);
         DPM_LAUNCHED();
-        k_syrk_reduce32<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(n, chunks, part, G);
+        if (in_smem)  // the FP32 Cholesky reads the Gram in FP32 (summed in FP64, rounded once)
+            k_syrk_reduce<float, float><<<(unsigned)((nn + 31) / 32), 32 * kRedW, 0, s>>>(
+                n, chunks, part, reinterpret_cast<float *>(G));
+        else
+            k_syrk_reduce<float, double><<<(unsigned)((nn + 31) / 32), 32 * kRedW, 0, s>>>(n, chunks, part, G);
         DPM_LAUNCHED();
     }
     if (!in_smem) {
@@ -651,10 +905,12 @@ static int mixed_factor(LsqFactor &f, const double *A0, double *R, double *Rinv,
         return DPM_OK;
     }
     *rinv_done = 1;
+    f.rinv32 = true;
     DPM_CUDA(cudaFuncSetAttribute(k_cholesky32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     {
         DPM_PROF("lsq_cholesky", s);
-        k_cholesky32<<<1, 1024, smem, s>>>(n, G, Rinv, status);
+        k_cholesky32<<<1, kCholT, smem, s>>>(n, reinterpret_cast<const float *>(G),
+                                             reinterpret_cast<float *>(Rinv), status, dscale);
         DPM_LAUNCHED();
     }
     return DPM_OK;
@@ -685,11 +941,13 @@ static int lsq_factor_impl(LsqFactor &f, bool sync, cudaStream_t s) {
     const int m = f.m, n = f.n;
     if (m < n || n < 1) { set_error("least squares: need m >= n >= 1 (m=%d n=%d)", m, n); return DPM_EINVAL; }
     // layout of f.work: [A0 m*n][w n][rdiag n][R n*n][status (64 B)][y R*n][res R*m]
-    //                   [z R*n][Rinv n*n][colscale n],  R = kLsqMaxRhs
+    //                   [z R*n][Rinv n*n][colscale n][A^T b slices kAtbMaxSlices*R*n],
+    //                   R = kLsqMaxRhs
     const size_t RR = kLsqMaxRhs;
     size_t need = sizeof(double) * ((size_t)m * n + 2 * (size_t)n + (size_t)n * n) + 64 +
                   sizeof(double) * RR * ((size_t)n + (size_t)m) + sizeof(double) * RR * (size_t)n +
-                  sizeof(double) * (size_t)n * n + sizeof(double) * (size_t)n;
+                  sizeof(double) * (size_t)n * n + sizeof(double) * (size_t)n +
+                  sizeof(double) * kAtbMaxSlices * RR * (size_t)n;
     DPM_RET(f.work.reserve(need));
     double *A0 = f.work.as<double>();
     double *w = A0 + (size_t)m * n;
@@ -702,6 +960,7 @@ static int lsq_factor_impl(LsqFactor &f, bool sync, cudaStream_t s) {
                    kLsqMaxRhs * ((size_t)n + (size_t)m) + kLsqMaxRhs * (size_t)n;
     double *dscale = Rinv + (size_t)n * n;
     f.equilibrated = false;
+    f.rinv32 = false;
     int rinv_done = 0;
     if (f.method == LsqFactor::kHouseholder) {
         DPM_RET(householder_factor(f, A0, w, rdiag, R, status, s));
@@ -755,24 +1014,55 @@ int lsq_apply(const LsqFactor &f, const T *b, int ldb, double *C, int nr, cudaSt
     // FP64 path takes three.
     const int refine = f.equilibrated ? (sizeof(T) == sizeof(double) ? 3 : 1) : 1;
     DPM_PROF("lsq_solve", s);
+    // A^T b by row slices: about six CTAs per SM in all, at most kAtbMaxSlices
+    const unsigned qg = (unsigned)((nr + kAtbQ - 1) / kAtbQ);
+    int S = (int)std::min<long>(kAtbMaxSlices, std::max<long>(1, (6L * 152 + (long)n * qg - 1) / ((long)n * qg)));
+    const int rows_per = (m + S - 1) / S;
+    S = (m + rows_per - 1) / rows_per;
+    double *ypart = const_cast<double *>(Rinv) + (size_t)n * n + n;
+    const double *bd;
+    int ldbd;
+    if constexpr (sizeof(T) == sizeof(float)) {
+        // the FP32 right-hand sides in FP64 once (res is free until the refinement)
+        k_to_double<<<(unsigned)std::min<size_t>(((size_t)m * nr + 255) / 256, 4 * 152), 256, 0, s>>>(
+            m, nr, reinterpret_cast<const float *>(b), ldb, res);
+        DPM_LAUNCHED();
+        bd = res;
+        ldbd = m;
+    } else {
+        bd = reinterpret_cast<const double *>(b);
+        ldbd = ldb;
+    }
+    // out (+)= R^{-1} or R^{-T} times y, R^{-1} in FP32 or FP64
+    auto trimv = [&](bool trans, const double *yin, double *out, int accumulate, const double *outscale,
+                     int yparts, const double *yscale) -> int {
+        const float *M32 = reinterpret_cast<const float *>(Rinv);
+        if (trans && f.rinv32)
+            k_trimv<1, float><<<mv_blocks, 256, 0, s>>>(n, M32, yin, out, nr, accumulate, outscale, yparts, yscale);
+        else if (trans)
+            k_trimv<1, double><<<mv_blocks, 256, 0, s>>>(n, Rinv, yin, out, nr, accumulate, outscale, yparts, yscale);
+        else if (f.rinv32)
+            k_trimv<0, float><<<mv_blocks, 256, 0, s>>>(n, M32, yin, out, nr, accumulate, outscale);
+        else
+            k_trimv<0, double><<<mv_blocks, 256, 0, s>>>(n, Rinv, yin, out, nr, accumulate, outscale);
+        DPM_LAUNCHED();
+        return DPM_OK;
+    };
     // C = D R^{-1} R^{-T} D A^T b   (D = I unless the factor was equilibrated)
-    k_atb<T><<<dim3(n, nr), 1024, 0, s>>>(m, n, A0, b, ldb, y, nr, dsc);
+    k_atb<<<dim3(n, S, qg), kAtbT, 0, s>>>(m, n, A0, bd, ldbd, ypart, nr, rows_per);
     DPM_LAUNCHED();
-    k_trimv<1><<<mv_blocks, 256, 0, s>>>(n, Rinv, y, z, nr, 0, nullptr);
-    DPM_LAUNCHED();
-    k_trimv<0><<<mv_blocks, 256, 0, s>>>(n, Rinv, z, C, nr, 0, dsc);
-    DPM_LAUNCHED();
+    DPM_RET(trimv(true, ypart, z, 0, nullptr, S, dsc));
+    DPM_RET(trimv(false, z, C, 0, dsc, 1, nullptr));
     // iterative refinement: C += D R^{-1} R^{-T} D A^T (b - A C), all in FP64
     for (int it = 0; it < refine; ++it) {
-        k_resid<T><<<dim3((m + 255) / 256, nr), 256, 0, s>>>(m, n, A0, b, ldb, C, res, nr);
+        k_resid<T><<<dim3((m + 31) / 32, qg), 32 * kResW, 0, s>>>(m, n, A0, b, ldb, C, res, nr);
         DPM_LAUNCHED();
-        k_atb<double><<<dim3(n, nr), 1024, 0, s>>>(m, n, A0, res, m, y, nr, dsc);
+        k_atb<<<dim3(n, S, qg), kAtbT, 0, s>>>(m, n, A0, res, m, ypart, nr, rows_per);
         DPM_LAUNCHED();
-        k_trimv<1><<<mv_blocks, 256, 0, s>>>(n, Rinv, y, z, nr, 0, nullptr);
-        DPM_LAUNCHED();
-        k_trimv<0><<<mv_blocks, 256, 0, s>>>(n, Rinv, z, C, nr, 1, dsc);
-        DPM_LAUNCHED();
+        DPM_RET(trimv(true, ypart, z, 0, nullptr, S, dsc));
+        DPM_RET(trimv(false, z, C, 1, dsc, 1, nullptr));
     }
+    (void)y;
     return DPM_OK;
 }
 
