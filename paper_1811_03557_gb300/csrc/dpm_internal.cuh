@@ -194,6 +194,7 @@ struct LsqFactor {
     int method = kMixed;
     bool equilibrated = false;
     bool rinv32 = false;  // R^{-1} stored in FP32 (the in-shared-memory mixed factor)
+    const float *A32 = nullptr;  // FP32 copy of A kept by that factor (in X), else null
     DevBuf A;      // double[m*n] column-major (Householder overwrites it)
     DevBuf tau;    // double[n] Householder scalars
     DevBuf X;      // scratch of the Gram / Cholesky factorisation

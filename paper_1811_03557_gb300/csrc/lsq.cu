@@ -143,6 +143,53 @@ __global__ void __launch_bounds__(kAtbT) k_atb(int m, int n, const double *__res
     }
 }
 
+// The same products from the FP32 copy of A and FP32 right-hand sides (or
+// residuals): FP32 products and per-thread sums, FP64 block sums.  Used for
+// A^T b and A^T r on the mixed-precision path, where only the residual needs
+// FP64 (the preconditioner's own error is larger than these roundings).
+__global__ void __launch_bounds__(kAtbT) k_atb32(int m, int n, const float *__restrict__ A32,
+                                                 const float *__restrict__ b, int ldb,
+                                                 double *__restrict__ part, int nr, int rows_per) {
+    __shared__ double sh[kAtbQ][kAtbT / 32];
+    const int c = blockIdx.x, sl = blockIdx.y, q0 = blockIdx.z * kAtbQ, nq = min(kAtbQ, nr - q0);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int r_begin = sl * rows_per, r_end = min(m, r_begin + rows_per);
+    const float *a = A32 + (size_t)c * m;
+    float acc[kAtbQ] = {};
+    for (int r0 = r_begin + t; r0 < r_end; r0 += kAtbU * kAtbT) {
+        float av[kAtbU];
+#pragma unroll
+        for (int u = 0; u < kAtbU; ++u) {
+            const int r = r0 + u * kAtbT;
+            av[u] = r < r_end ? a[r] : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < kAtbQ; ++q) {
+            if (q < nq) {
+                const float *bq = b + (size_t)(q0 + q) * ldb;
+#pragma unroll
+                for (int u = 0; u < kAtbU; ++u) {
+                    const int r = r0 + u * kAtbT;
+                    if (r < r_end) acc[q] = fmaf(av[u], bq[r], acc[q]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kAtbQ; ++q) {
+        double v = (double)acc[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[q][warp] = v;
+    }
+    __syncthreads();
+    if (t < nq) {
+        double v = 0.0;
+#pragma unroll
+        for (int w = 0; w < kAtbT / 32; ++w) v += sh[t][w];
+        part[((size_t)sl * nr + q0 + t) * n + c] = v;
+    }
+}
+
 // out[q][r] = (double) b[q][r] (the FP32 right-hand sides, converted once)
 __global__ void k_to_double(int m, int nr, const float *__restrict__ b, int ldb, double *__restrict__ out) {
     const size_t total = (size_t)m * nr;
@@ -154,9 +201,9 @@ __global__ void k_to_double(int m, int nr, const float *__restrict__ b, int ldb,
 // lanes) and up to kAtbQ right-hand sides; its 8 warps take the columns
 // c = w, w + 8, ... and the 8 partial sums are added in warp order.
 constexpr int kResW = 8;
-template <class T>
+template <class T, class R>
 __global__ void __launch_bounds__(32 * kResW) k_resid(int m, int n, const double *A0, const T *b, int ldb,
-                                                      const double *C, double *res, int nr) {
+                                                      const double *C, R *res, int nr) {
     __shared__ double sh[kResW][kAtbQ][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r = blockIdx.x * 32 + lane;
@@ -190,7 +237,7 @@ __global__ void __launch_bounds__(32 * kResW) k_resid(int m, int n, const double
         double v = 0.0;
 #pragma unroll
         for (int w = 0; w < kResW; ++w) v += sh[w][warp][lane];
-        res[(size_t)(q0 + warp) * m + r] = (double)b[(size_t)(q0 + warp) * ldb + r] - v;
+        res[(size_t)(q0 + warp) * m + r] = (R)((double)b[(size_t)(q0 + warp) * ldb + r] - v);
     }
 }
 
@@ -906,6 +953,7 @@ static int mixed_factor(LsqFactor &f, const double *A0, double *R, double *Rinv,
     }
     *rinv_done = 1;
     f.rinv32 = true;
+    f.A32 = Af;
     DPM_CUDA(cudaFuncSetAttribute(k_cholesky32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     {
         DPM_PROF("lsq_cholesky", s);
@@ -961,6 +1009,7 @@ static int lsq_factor_impl(LsqFactor &f, bool sync, cudaStream_t s) {
     double *dscale = Rinv + (size_t)n * n;
     f.equilibrated = false;
     f.rinv32 = false;
+    f.A32 = nullptr;
     int rinv_done = 0;
     if (f.method == LsqFactor::kHouseholder) {
         DPM_RET(householder_factor(f, A0, w, rdiag, R, status, s));
@@ -1020,19 +1069,26 @@ int lsq_apply(const LsqFactor &f, const T *b, int ldb, double *C, int nr, cudaSt
     const int rows_per = (m + S - 1) / S;
     S = (m + rows_per - 1) / rows_per;
     double *ypart = const_cast<double *>(Rinv) + (size_t)n * n + n;
-    const double *bd;
-    int ldbd;
-    if constexpr (sizeof(T) == sizeof(float)) {
-        // the FP32 right-hand sides in FP64 once (res is free until the refinement)
-        k_to_double<<<(unsigned)std::min<size_t>(((size_t)m * nr + 255) / 256, 4 * 152), 256, 0, s>>>(
-            m, nr, reinterpret_cast<const float *>(b), ldb, res);
-        DPM_LAUNCHED();
-        bd = res;
-        ldbd = m;
-    } else {
-        bd = reinterpret_cast<const double *>(b);
-        ldbd = ldb;
+    // FP32 right-hand sides with the factor's FP32 copy of A: the products with
+    // A^T in FP32 (FP64 sums), only the residual in FP64; it is stored in FP32
+    // in res's space
+    const bool fast32 = sizeof(T) == sizeof(float) && f.A32 != nullptr;
+    const double *bd = nullptr;
+    int ldbd = 0;
+    if (!fast32) {
+        if constexpr (sizeof(T) == sizeof(float)) {
+            // the FP32 right-hand sides in FP64 once (res is free until the refinement)
+            k_to_double<<<(unsigned)std::min<size_t>(((size_t)m * nr + 255) / 256, 4 * 152), 256, 0, s>>>(
+                m, nr, reinterpret_cast<const float *>(b), ldb, res);
+            DPM_LAUNCHED();
+            bd = res;
+            ldbd = m;
+        } else {
+            bd = reinterpret_cast<const double *>(b);
+            ldbd = ldb;
+        }
     }
+    float *res32 = reinterpret_cast<float *>(res);
     // out (+)= R^{-1} or R^{-T} times y, R^{-1} in FP32 or FP64
     auto trimv = [&](bool trans, const double *yin, double *out, int accumulate, const double *outscale,
                      int yparts, const double *yscale) -> int {
@@ -1049,15 +1105,25 @@ int lsq_apply(const LsqFactor &f, const T *b, int ldb, double *C, int nr, cudaSt
         return DPM_OK;
     };
     // C = D R^{-1} R^{-T} D A^T b   (D = I unless the factor was equilibrated)
-    k_atb<<<dim3(n, S, qg), kAtbT, 0, s>>>(m, n, A0, bd, ldbd, ypart, nr, rows_per);
+    if (fast32)
+        k_atb32<<<dim3(n, S, qg), kAtbT, 0, s>>>(m, n, f.A32, reinterpret_cast<const float *>(b), ldb, ypart,
+                                                 nr, rows_per);
+    else
+        k_atb<<<dim3(n, S, qg), kAtbT, 0, s>>>(m, n, A0, bd, ldbd, ypart, nr, rows_per);
     DPM_LAUNCHED();
     DPM_RET(trimv(true, ypart, z, 0, nullptr, S, dsc));
     DPM_RET(trimv(false, z, C, 0, dsc, 1, nullptr));
-    // iterative refinement: C += D R^{-1} R^{-T} D A^T (b - A C), all in FP64
+    // iterative refinement: C += D R^{-1} R^{-T} D A^T (b - A C), the residual in FP64
     for (int it = 0; it < refine; ++it) {
-        k_resid<T><<<dim3((m + 31) / 32, qg), 32 * kResW, 0, s>>>(m, n, A0, b, ldb, C, res, nr);
-        DPM_LAUNCHED();
-        k_atb<<<dim3(n, S, qg), kAtbT, 0, s>>>(m, n, A0, res, m, ypart, nr, rows_per);
+        if (fast32) {
+            k_resid<T, float><<<dim3((m + 31) / 32, qg), 32 * kResW, 0, s>>>(m, n, A0, b, ldb, C, res32, nr);
+            DPM_LAUNCHED();
+            k_atb32<<<dim3(n, S, qg), kAtbT, 0, s>>>(m, n, f.A32, res32, m, ypart, nr, rows_per);
+        } else {
+            k_resid<T, double><<<dim3((m + 31) / 32, qg), 32 * kResW, 0, s>>>(m, n, A0, b, ldb, C, res, nr);
+            DPM_LAUNCHED();
+            k_atb<<<dim3(n, S, qg), kAtbT, 0, s>>>(m, n, A0, res, m, ypart, nr, rows_per);
+        }
         DPM_LAUNCHED();
         DPM_RET(trimv(true, ypart, z, 0, nullptr, S, dsc));
         DPM_RET(trimv(false, z, C, 1, dsc, 1, nullptr));
