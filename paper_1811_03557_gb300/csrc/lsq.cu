@@ -377,37 +377,52 @@ __global__ void k_to_float(size_t total, const double *__restrict__ A, float *__
 
 // FP32 Gram partials of the FP32 copy of A (or of A D; upper 64 x 64 tiles),
 // part[chunk][i][j] in float; the chunk sums are added in FP64 by k_syrk_reduce.
-__global__ void k_syrk32_part(int m, int n, const float *Af, int rows_per, float *part) {
-    __shared__ float As[kGR][kGT + 1], Bs[kGR][kGT + 1];
+// 16 x 16 threads with 4 x 4 outputs each; per step 16 rows of the two column
+// blocks in shared memory, stored with the float4 group of column c XORed by
+// the row (rr) so that the transposing stores spread over the banks and each
+// thread reads its 4 columns as one float4; the next step's rows are loaded
+// into registers while this one is multiplied.
+__device__ __forceinline__ int gram_sw(int rr, int cc) { return rr * kGT + ((((cc >> 2) ^ rr) & 15) << 2) + (cc & 3); }
+__global__ void __launch_bounds__(256) k_syrk32_part(int m, int n, const float *Af, int rows_per, float *part) {
+    __shared__ __align__(16) float As[kGR * kGT], Bs[kGR * kGT];
     const int nb = (n + kGT - 1) / kGT;
     int tile = blockIdx.x, bi = 0;
     while (tile >= nb - bi) { tile -= nb - bi; ++bi; }
     const int bj = bi + tile;
     const int chunk = blockIdx.y;
     const int r0 = chunk * rows_per, r1 = min(m, r0 + rows_per);
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    float acc[4][4] = {};
-    for (int rs = r0; rs < r1; rs += kGR) {
-        for (int q = threadIdx.x; q < kGR * kGT; q += blockDim.x) {
-            const int rr = q % kGR, cc = q / kGR;
-            const int r = rs + rr;
+    const int t = threadIdx.x, tx = t % 16, ty = t / 16;
+    // this thread's 4 elements of each block per step: q = t + 256 e, row q % 16, column q / 16
+    float pa[4], pb[4];
+    auto fetch = [&](int rs) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int q = t + 256 * e, rr = q % kGR, cc = q / kGR, r = rs + rr;
             const int ci = bi * kGT + cc, cj = bj * kGT + cc;
-            As[rr][cc] = (r < r1 && ci < n) ? Af[(size_t)ci * m + r] : 0.f;
-            Bs[rr][cc] = (r < r1 && cj < n) ? Af[(size_t)cj * m + r] : 0.f;
+            pa[e] = (r < r1 && ci < n) ? Af[(size_t)ci * m + r] : 0.f;
+            pb[e] = (r < r1 && cj < n) ? Af[(size_t)cj * m + r] : 0.f;
+        }
+    };
+    float acc[4][4] = {};
+    if (r0 < r1) fetch(r0);
+    for (int rs = r0; rs < r1; rs += kGR) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int q = t + 256 * e;
+            As[gram_sw(q % kGR, q / kGR)] = pa[e];
+            Bs[gram_sw(q % kGR, q / kGR)] = pb[e];
         }
         __syncthreads();
+        if (rs + kGR < r1) fetch(rs + kGR);
 #pragma unroll
         for (int rr = 0; rr < kGR; ++rr) {
-            float a[4], b[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                a[u] = As[rr][ty * 4 + u];
-                b[u] = Bs[rr][tx * 4 + u];
-            }
+            const float4 a = *reinterpret_cast<const float4 *>(&As[rr * kGT + (((ty ^ rr) & 15) << 2)]);
+            const float4 b = *reinterpret_cast<const float4 *>(&Bs[rr * kGT + (((tx ^ rr) & 15) << 2)]);
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
         }
         __syncthreads();
     }
