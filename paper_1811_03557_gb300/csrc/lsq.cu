@@ -1,18 +1,19 @@
-// FP64 least squares for the spectral coefficients of the BEP (eq. BEP_recast,
-// Steps 2 and 5 of the main algorithm).
+// Least squares for the spectral coefficients of the BEP (eq. BEP_recast,
+// Steps 2 and 5 of the main algorithm), refined to FP64 accuracy.
 //
-// Factor (once per BEP, Step 2 / 4b): the R factor of the QR decomposition of
-// A (m x n, column-major, m >> n).  Two ways are built:
-//   * CholeskyQR (default): R^T R = A^T A with G = A^T A formed by one FP64
-//     SYRK over all SMs (fixed-order partial sums, deterministic) and R the
-//     Cholesky factor of G (one CTA, in shared memory for n <= 168);
+// Factor (once per BEP, Step 2 / 4b): an upper-triangular R with R^T R =
+// A^T A (up to column equilibration D), A m x n column-major, m >> n:
+//   * mixed precision (the FP32 paths): Gram of an FP32 copy of A over all
+//     SMs (chunk sums in FP64, fixed order), equilibrated by its diagonal and
+//     factored in FP32 in one CTA, R^{-1} kept in FP32 (n <= 168);
+//   * CholeskyQR in FP64 (FP64 SYRK, FP64 Cholesky; optionally equilibrated
+//     with a small diagonal shift);
 //   * Householder QR, one reflector H_j = I - tau_j v_j v_j^T per column
 //     (three dependent launches per column; kept as the reference method).
-// Solve (every step): R^T R C = A^T b with the original A (the semi-normal
-// equations), then one step of iterative refinement on r = b - A C.  With
-// kappa(A)^2 * eps_64 << 1 the refined C agrees with a backward-stable QR
-// solve; the FP64 work per step is two GEMVs over all SMs plus n x n
-// triangular solves in one CTA, and Q is never formed.
+// Solve (every step): C = D R^{-1} R^{-T} D A^T b (the semi-normal equations
+// with the original A), then iterative refinement on r = b - A C, the
+// residual always in FP64.  With the factor as a preconditioner the refined C
+// agrees with a backward-stable QR solve; Q is never formed.
 #include <math.h>
 
 #include <algorithm>
