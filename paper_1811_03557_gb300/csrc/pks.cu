@@ -13,9 +13,12 @@
 //    free energy (eq. sd-norm:free-energy), per-block FP64 partial sums
 //    reduced in a fixed order.
 //  * extension: u_gamma = sum C0 phi + beta (d^2/2) sum C2 phi + d g_N
-//    (eqs. extension_operator, extension_operator_recast), one warp per node
-//    of gamma with a shuffle reduction over the harmonics.
+//    (eqs. extension_operator, extension_operator_recast): FP32 paths one
+//    thread per node of gamma over a transposed FP32 table, the FP64 path one
+//    warp per node with a shuffle reduction over the harmonics.
 #include <math.h>
+
+#include <algorithm>
 
 #include "dpm_internal.cuh"
 
@@ -23,6 +26,15 @@ namespace dpm {
 namespace {
 
 __device__ __forceinline__ bool in_np(uint8_t l) { return l & (DPM_LBL_MPLUS | DPM_LBL_GEX); }
+
+// (i, j, k) of node p = (i N + j) N + k in 32-bit arithmetic (N^3 < 2^32; a
+// 64-bit division costs about ten times as many instructions)
+__device__ __forceinline__ void node_ijk(int64_t p, int N, int &i, int &j, int &k) {
+    const unsigned q = (unsigned)p, n = (unsigned)N, ij = q / n, ii = ij / n;
+    k = (int)(q - ij * n);
+    j = (int)(ij - ii * n);
+    i = (int)ii;
+}
 
 template <class T> __device__ __forceinline__ T minmod3(T a, T b, T c) {
     if (a > 0 && b > 0 && c > 0) return fmin(a, fmin(b, c));
@@ -53,7 +65,8 @@ __global__ void k_flux(int N, T h, T chi, double dt_d, const double *dt_dev, con
             f_c[p] = (T)0;
             continue;
         }
-        int coord[3] = {(int)(p / ((int64_t)N * N)), (int)((p / N) % N), (int)(p % N)};
+        int coord[3];
+        node_ijk(p, N, coord[0], coord[1], coord[2]);
         int64_t st[3] = {(int64_t)N * N, (int64_t)N, 1};
         T r0 = rho[p], c0 = c[p];
         T g = (T)0;
@@ -111,31 +124,32 @@ __global__ void k_cfl(int N, const uint8_t *lab, const T *c, unsigned int *gmax)
 constexpr int kDiagThreads = 256;
 constexpr int kDiag = 6;  // mass, max rho, min rho, min c, m2, free energy
 
+// Per-thread partials in T (a thread folds ~14 nodes of the 128^3 grid, so
+// FP32 sums lose ~1e-7 on the FP32 paths and the FP64 pipe, 1/64 of the FP32
+// rate here, is left to the block and final sums).
 template <class T>
 __global__ void k_diag(int N, double lo, double h, const uint8_t *lab, const T *rho, const T *c,
                        double *part, double ox, double oy, double oz) {
     const int64_t n3 = (int64_t)N * N * N;
-    double v[kDiag] = {0.0, -INFINITY, INFINITY, INFINITY, 0.0, 0.0};
-    const T inv8h2 = (T)(1.0 / (8.0 * h * h));
+    T a[kDiag] = {(T)0, (T)-INFINITY, (T)INFINITY, (T)INFINITY, (T)0, (T)0};
+    const T inv8h2 = (T)(1.0 / (8.0 * h * h)), ht = (T)h;
+    const T x0 = (T)(lo + ox), y0 = (T)(lo + oy), z0 = (T)(lo + oz);
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n3;
          p += (int64_t)gridDim.x * blockDim.x) {
         uint8_t l = lab[p];
         if (!in_np(l)) continue;
         T r = rho[p], cc = c[p];
-        v[2] = fmin(v[2], (double)r);
-        v[3] = fmin(v[3], (double)cc);
+        a[2] = fmin(a[2], r);
+        a[3] = fmin(a[3], cc);
         if (!(l & DPM_LBL_MPLUS)) continue;
-        int i = (int)(p / ((int64_t)N * N)), j = (int)((p / N) % N), k = (int)(p % N);
+        int i, j, k;
+        node_ijk(p, N, i, j, k);
         // global coordinates: the grid's local frame plus its origin (0 unless
         // the grid belongs to a shifted sub-domain box)
-        double x = lo + (double)(i + 1) * h, y = lo + (double)(j + 1) * h,
-               z = lo + (double)(k + 1) * h;
-        x += ox;
-        y += oy;
-        z += oz;
-        v[0] += (double)r;
-        v[1] = fmax(v[1], (double)r);
-        v[4] += (x * x + y * y + z * z) * (double)r;
+        const T x = x0 + (T)(i + 1) * ht, y = y0 + (T)(j + 1) * ht, z = z0 + (T)(k + 1) * ht;
+        a[0] += r;
+        a[1] = fmax(a[1], r);
+        a[4] += (x * x + y * y + z * z) * r;
         int64_t st[3] = {(int64_t)N * N, (int64_t)N, 1};
         T g2 = (T)0;
 #pragma unroll
@@ -144,8 +158,11 @@ __global__ void k_diag(int N, double lo, double h, const uint8_t *lab, const T *
             g2 += d * d;
         }
         T rlr = r > (T)0 ? r * log(r) : (T)0;
-        v[5] += (double)(rlr - r * cc + (T)0.5 * cc * cc + g2 * inv8h2);
+        a[5] += rlr - r * cc + (T)0.5 * cc * cc + g2 * inv8h2;
     }
+    double v[kDiag];
+#pragma unroll
+    for (int q = 0; q < kDiag; ++q) v[q] = (double)a[q];
     __shared__ double sh[kDiag][kDiagThreads / 32];
 #pragma unroll
     for (int q = 0; q < kDiag; ++q) {
@@ -220,7 +237,8 @@ __global__ void k_init_nodes(int N, double lo, double h, const uint8_t *lab, dpm
          p += (int64_t)gridDim.x * blockDim.x) {
         T a = (T)0, b = (T)0;
         if (lab[p] & DPM_LBL_MPLUS) {
-            int i = (int)(p / ((int64_t)N * N)), j = (int)((p / N) % N), k = (int)(p % N);
+            int i, j, k;
+            node_ijk(p, N, i, j, k);
             double x = lo + (double)(i + 1) * h, y = lo + (double)(j + 1) * h,
                    z = lo + (double)(k + 1) * h;
             a = (T)gauss(g0, x, y, z);
@@ -257,7 +275,7 @@ __global__ void k_assemble(int64_t total, const double *psi_in, const T *trace, 
 }
 
 // One warp per node of gamma: u[q][g] = sum_nu C0 phi + beta d^2/2 sum_nu C2 phi + d gN,
-// accumulated in P (double for the FP64 path, float for the FP32 paths).
+// accumulated in P (the FP64 path: P = double).
 template <class T, class P>
 __global__ void k_extend(int n, int nsh, int beta, const P *phi, const double *dist,
                          const double *C, int ldc, const double *neumann, T *dens, int ldd,
@@ -297,10 +315,55 @@ __global__ void k_extend(int n, int nsh, int beta, const P *phi, const double *d
     }
 }
 
-__global__ void k_to_float(int64_t n, const double *src, float *dst) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = (float)src[i];
+// FP32 paths: one thread per node of gamma, the harmonics in order (the FP32
+// table is stored transposed, [nu][node], so the loads are coalesced), up to
+// kExtQ right-hand sides per pass over the table; the coefficients converted
+// to FP32 once per block into shared memory.
+constexpr int kExtQ = 4;
+template <class T>
+__global__ void k_extend32(int n, int nsh, int beta, const float *__restrict__ phit,
+                           const double *__restrict__ dist, const double *__restrict__ C, int ldc,
+                           const double *__restrict__ neumann, T *dens, int ldd, int nr, int clamp) {
+    extern __shared__ float cs32[];
+    const int ncu = (beta ? 2 : 1) * nsh;
+    for (int i = threadIdx.x; i < nr * ncu; i += blockDim.x) cs32[i] = (float)C[(size_t)(i / ncu) * ldc + i % ncu];
+    __syncthreads();
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const double d = dist[g];
+    for (int q0 = 0; q0 < nr; q0 += kExtQ) {
+        const int nq = min(kExtQ, nr - q0);
+        float s0[kExtQ] = {}, s2[kExtQ] = {};
+#pragma unroll 8
+        for (int nu = 0; nu < nsh; ++nu) {
+            const float f = phit[(size_t)nu * n + g];
+#pragma unroll
+            for (int q = 0; q < kExtQ; ++q)
+                if (q < nq) {
+                    const float *cp = cs32 + (size_t)(q0 + q) * ncu;
+                    s0[q] = fmaf(cp[nu], f, s0[q]);
+                    if (beta) s2[q] = fmaf(cp[nsh + nu], f, s2[q]);
+                }
+        }
+#pragma unroll
+        for (int q = 0; q < kExtQ; ++q)
+            if (q < nq) {
+                double u = (double)s0[q] + 0.5 * d * d * (double)s2[q];
+                if (neumann) u += d * neumann[g];
+                if (clamp && u < 0.0) u = 0.0;
+                dens[(size_t)(q0 + q) * ldd + g] = (T)u;
+            }
+    }
+}
+
+// phit[nu][g] = float(phi[g][nu])
+__global__ void k_phi32t(int n, int nsh, const double *phi, float *phit) {
+    const int64_t total = (int64_t)n * nsh;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t nu = e / n, g = e - nu * n;
+        phit[e] = (float)phi[g * nsh + nu];
+    }
 }
 
 int blocks_for(int64_t n, int t) {
@@ -320,6 +383,7 @@ template <class T>
 int assemble_bep(const double *psi_in, const T *trace, double *A, int64_t m, int ncol,
                  const int *cond_flag, cudaStream_t s) {
     (void)cond_flag;
+    DPM_PROF("assemble", s);
     int64_t total = m * ncol;
     k_assemble<T><<<blocks_for(total, 256), 256, 0, s>>>(total, psi_in, trace, A);
     DPM_LAUNCHED();
@@ -333,6 +397,7 @@ template int assemble_bep<double>(const double *, const double *, double *, int6
 template <class T>
 int extend_density(const GammaGeom &gg, int64_t n_gamma, int beta, const double *C, int ldc,
                    const double *neumann, T *dens, int ldd, int nr, int clamp, cudaStream_t s) {
+    DPM_PROF("extend", s);
     int64_t threads = n_gamma * 32;
     const unsigned blocks = (unsigned)((threads + 255) / 256);
     if (sizeof(T) == 4) {
@@ -340,14 +405,20 @@ int extend_density(const GammaGeom &gg, int64_t n_gamma, int beta, const double 
         const size_t elems = (size_t)n_gamma * gg.nsh;
         if (g.phi32.bytes < elems * sizeof(float)) {
             DPM_RET(g.phi32.alloc(elems * sizeof(float)));
-            k_to_float<<<blocks_for((int64_t)elems, 256), 256, 0, s>>>((int64_t)elems, gg.phi.as<double>(),
-                                                                         g.phi32.as<float>());
+            k_phi32t<<<blocks_for((int64_t)elems, 256), 256, 0, s>>>((int)n_gamma, gg.nsh, gg.phi.as<double>(),
+                                                                      g.phi32.as<float>());
             DPM_LAUNCHED();
         }
-        const size_t sm = sizeof(float) * (size_t)nr * (beta ? 2 : 1) * gg.nsh;
-        const int ok = sm <= 32 * 1024;
-        k_extend<T, float><<<blocks, 256, ok ? sm : 0, s>>>((int)n_gamma, gg.nsh, beta, g.phi32.as<float>(),
-                                                  gg.dist.as<double>(), C, ldc, neumann, dens, ldd, nr, clamp, ok);
+        // right-hand sides in groups whose FP32 coefficients fit in 48 KB of shared memory
+        const size_t per = sizeof(float) * (size_t)(beta ? 2 : 1) * gg.nsh;
+        const int grp = (int)std::max<size_t>(1, (48 * 1024) / per);
+        for (int q0 = 0; q0 < nr; q0 += grp) {
+            const int nq = std::min(grp, nr - q0);
+            k_extend32<T><<<(unsigned)((n_gamma + 127) / 128), 128, per * nq, s>>>(
+                (int)n_gamma, gg.nsh, beta, g.phi32.as<float>(), gg.dist.as<double>(), C + (size_t)q0 * ldc, ldc,
+                neumann, dens + (size_t)q0 * ldd, ldd, nq, clamp);
+            if (q0 + grp < nr) DPM_LAUNCHED();
+        }
     } else {
         const size_t sm = sizeof(double) * (size_t)nr * (beta ? 2 : 1) * gg.nsh;
         const int ok = sm <= 32 * 1024;
@@ -366,6 +437,7 @@ template int extend_density<double>(const GammaGeom &, int64_t, int, const doubl
 template <class T>
 int pks_flux(int N, double h, double chi, double dt, const double *dt_dev, const uint8_t *lab,
              const T *rho, const T *c, T *f_rho, T *f_c, cudaStream_t s) {
+    DPM_PROF("pks_flux", s);
     int64_t n3 = (int64_t)N * N * N;
     k_flux<T><<<blocks_for(n3, 256), 256, 0, s>>>(N, (T)h, (T)chi, dt, dt_dev, lab, rho, c, f_rho,
                                                   f_c);
@@ -423,6 +495,7 @@ int pks_step_end(StepScalars *sc, int rebuilt, cudaStream_t s) {
 
 template <class T>
 int pks_cfl(int N, const uint8_t *lab, const T *c, unsigned int *gmax, cudaStream_t s) {
+    DPM_PROF("pks_cfl", s);
     int64_t n3 = (int64_t)N * N * N;
     DPM_CUDA(cudaMemsetAsync(gmax, 0, 3 * sizeof(unsigned int), s));
     k_cfl<T><<<reduce_blocks(n3, 256), 256, 0, s>>>(N, lab, c, gmax);
@@ -437,6 +510,7 @@ int pks_diag_blocks(int N) { return reduce_blocks((int64_t)N * N * N, kDiagThrea
 template <class T>
 int pks_diag(int N, double lo, double h, const uint8_t *lab, const T *rho, const T *c,
              double *part, double *out, cudaStream_t s, const double *origin) {
+    DPM_PROF("pks_diag", s);
     int nb = pks_diag_blocks(N);
     const double ox = origin ? origin[0] : 0.0, oy = origin ? origin[1] : 0.0, oz = origin ? origin[2] : 0.0;
     k_diag<T><<<nb, kDiagThreads, 0, s>>>(N, lo, h, lab, rho, c, part, ox, oy, oz);
