@@ -160,18 +160,27 @@ __global__ void k_diag(int N, double lo, double h, const uint8_t *lab, const T *
         T rlr = r > (T)0 ? r * log(r) : (T)0;
         a[5] += rlr - r * cc + (T)0.5 * cc * cc + g2 * inv8h2;
     }
-    double v[kDiag];
-#pragma unroll
-    for (int q = 0; q < kDiag; ++q) v[q] = (double)a[q];
+    // warp reduction: max / min in T (exact), the three sums in FP64
     __shared__ double sh[kDiag][kDiagThreads / 32];
+    T mx = a[1], mn_r = a[2], mn_c = a[3];
+    double s_m = (double)a[0], s_2 = (double)a[4], s_f = (double)a[5];
 #pragma unroll
-    for (int q = 0; q < kDiag; ++q) {
-        double x = v[q];
-        for (int o = 16; o > 0; o >>= 1) {
-            double y = __shfl_xor_sync(0xffffffffu, x, o);
-            x = (q == 1) ? fmax(x, y) : (q == 2 || q == 3) ? fmin(x, y) : x + y;
-        }
-        if ((threadIdx.x & 31) == 0) sh[q][threadIdx.x >> 5] = x;
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        mn_r = fmin(mn_r, __shfl_xor_sync(0xffffffffu, mn_r, o));
+        mn_c = fmin(mn_c, __shfl_xor_sync(0xffffffffu, mn_c, o));
+        s_m += __shfl_xor_sync(0xffffffffu, s_m, o);
+        s_2 += __shfl_xor_sync(0xffffffffu, s_2, o);
+        s_f += __shfl_xor_sync(0xffffffffu, s_f, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        const int w = threadIdx.x >> 5;
+        sh[0][w] = s_m;
+        sh[1][w] = (double)mx;
+        sh[2][w] = (double)mn_r;
+        sh[3][w] = (double)mn_c;
+        sh[4][w] = s_2;
+        sh[5][w] = s_f;
     }
     __syncthreads();
     if (threadIdx.x < kDiag) {
