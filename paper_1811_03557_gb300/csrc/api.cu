@@ -174,6 +174,7 @@ struct dpm_bep {
     GridIndex gi;
     GammaGeom gg;
     DevBuf psi;     // T[ncol][n_gamma]
+    DevBuf shpre;   // float2[ncol][n_shell]: shell pairs of the basis columns (tensor cores, N = 128)
     DevBuf psi_in;  // double[ncol][n_gin]
     DevBuf trace;   // T[ncol + 4][n_gin]
     DevBuf dens;    // T[4][n_gamma]
@@ -358,14 +359,35 @@ ApParams base_params(const dpm_bep *b, double sigma) {
 }
 
 // Columns of eq. BEP_recast plus `extra` right-hand sides in the same batch.
+// Shell pairs of the basis columns for the tensor-core N = 128 solver (the
+// basis densities depend on the geometry only), computed on first use; null
+// where they do not apply (the solver then gathers q from the densities).
+template <class T>
+int bep_shell_pre(dpm_bep *b, const float2 **out, cudaStream_t s) {
+    *out = nullptr;
+    if constexpr (sizeof(T) == sizeof(float)) {
+        if (b->prec != DPM_PREC_TC32 || b->N != 128 || b->gi.n_shell <= 0) return DPM_OK;
+        if (!b->shpre.p) {
+            DPM_RET(b->shpre.alloc(sizeof(float2) * (size_t)b->ncol * b->gi.n_shell));
+            DPM_RET(tc_shell_pre(b->gi.n_shell, b->gi.shell_nb.as<int>(), b->psi.as<float>(), b->gi.n_gamma,
+                                 b->ncol, b->shpre.as<float2>(), s));
+        }
+        *out = b->shpre.as<float2>();
+    }
+    return DPM_OK;
+}
+
 template <class T>
 int bep_assemble(dpm_bep *b, double sigma, std::vector<ApRhs<T>> extra, double fscale,
                  cudaStream_t s) {
     const int64_t ng = b->gi.n_gamma, m = b->gi.n_gin;
     std::vector<ApRhs<T>> rhs;
     rhs.reserve(b->ncol + extra.size());
+    const float2 *pre = nullptr;
+    DPM_RET(bep_shell_pre<T>(b, &pre, s));
     for (int k = 0; k < b->ncol; ++k)
-        rhs.push_back({nullptr, b->psi.as<T>() + k * ng, nullptr, b->trace.as<T>() + k * m, 0, 0});
+        rhs.push_back({nullptr, b->psi.as<T>() + k * ng, nullptr, b->trace.as<T>() + k * m, 0, 0,
+                       pre ? pre + (size_t)k * b->gi.n_shell : nullptr});
     for (auto &e : extra) rhs.push_back(e);
     ApParams p = base_params(b, sigma);
     p.fscale = fscale;
@@ -570,7 +592,7 @@ size_t bep_bytes(const dpm_bep &b) {
     return g.labels.bytes + g.gin.bytes + g.gex.bytes + g.gamma.bytes + g.shell.bytes +
            g.shell_nb.bytes + g.rp_gin.bytes + g.rp_shell.bytes + g.gin_pos.bytes + g.gex_pos.bytes +
            q.foot.bytes + q.normal.bytes + q.dist.bytes + q.phi.bytes + q.phi32.bytes + l.A.bytes +
-           l.tau.bytes + l.X.bytes + l.work.bytes + b.psi.bytes + b.psi_in.bytes + b.trace.bytes +
+           l.tau.bytes + l.X.bytes + l.work.bytes + b.psi.bytes + b.shpre.bytes + b.psi_in.bytes + b.trace.bytes +
            b.dens.bytes + b.coef.bytes + b.zero.bytes + b.desc.bytes + b.work.bytes + b.btrace.bytes +
            b.bdens.bytes + b.bcoef.bytes;
 }
@@ -738,8 +760,11 @@ template <class T> int pks_dev_setup(dpm_pks *k, cudaStream_t s) {
     T *tr0 = b->trace.as<T>() + (int64_t)b->ncol * m, *tr1 = tr0 + m;
     T *dens = b->dens.as<T>();
     std::vector<ApRhs<T>> rb;
+    const float2 *pre = nullptr;
+    DPM_RET(bep_shell_pre<T>(b, &pre, s));
     for (int c = 0; c < b->ncol; ++c)
-        rb.push_back({nullptr, b->psi.as<T>() + c * ng, nullptr, b->trace.as<T>() + c * m, 0, 0});
+        rb.push_back({nullptr, b->psi.as<T>() + c * ng, nullptr, b->trace.as<T>() + c * m, 0, 0,
+                      pre ? pre + (size_t)c * b->gi.n_shell : nullptr});
     rb.push_back({frho, nullptr, nullptr, tr0, 0, 0});
     rb.push_back({fc, nullptr, nullptr, tr1, 0, 0});
     std::vector<ApRhs<T>> gr = {{frho, dens, k->rho.as<T>(), nullptr, 0, 0},

@@ -136,6 +136,10 @@ template <class T> struct ApRhs {
     T *out_trace;    // trace on gamma_in [n_gin], or null
     int cond;        // 1: skipped unless *cond_flag != 0
     int pad_;
+    // tensor-core N = 128 path, a density that does not change between solves:
+    // pre[e] = {v(self), sum of v over the 6 neighbours} on the shell, so the
+    // shell right-hand side is a streaming pass instead of a gather (null: from dens)
+    const float2 *pre = nullptr;
 };
 
 struct ApParams {
@@ -167,6 +171,9 @@ int ap_solve_simt_group(const std::vector<ApParams> &probs, const std::vector<Ap
                         const std::vector<int> &prob_of, DevBuf &work, DevBuf &items_dev, cudaStream_t s);
 // Tuned SIMT tile width for (N, FP64?, B) on the current device, 0 if none.
 int simt_tile_choice(int N, int f64, int B);
+// pre[c][e] for the ncol densities dens + c ng (see ApRhs::pre)
+int tc_shell_pre(int64_t n_shell, const int *shell_nb, const float *dens, int64_t ng, int ncol, float2 *pre,
+                 cudaStream_t s);
 int ap_solve_tc(const ApParams &p, const ApRhs<float> *rhs_dev, float *work, cudaStream_t s);
 // N = 256: six out-of-place passes; work holds 2 B N^3 floats.
 int ap_solve_tc256(const ApParams &p, const ApRhs<float> *rhs_dev, float *work, cudaStream_t s);

@@ -267,6 +267,13 @@ __global__ void k_shell_rhs(int n_shell, double c6, float coff, double sigma,
     const int b = blockIdx.y;
     const ApRhs<float> r = rhs[b];
     if (!r.dens) return;
+    if (r.pre) {  // the density's shell pairs are precomputed: a streaming pass
+        for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_shell; e += gridDim.x * blockDim.x) {
+            const float2 v = r.pre[e];
+            qsh[(size_t)b * n_shell + e] = cdiag * v.x - coff * v.y;
+        }
+        return;
+    }
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_shell; e += gridDim.x * blockDim.x) {
         const int *nb = shell_nb + 8 * (size_t)e;
         float sacc = 0.f;
@@ -275,6 +282,23 @@ __global__ void k_shell_rhs(int n_shell, double c6, float coff, double sigma,
             if (nb[q] >= 0) sacc += r.dens[nb[q]];
         const float self = nb[0] >= 0 ? r.dens[nb[0]] : 0.f;
         qsh[(size_t)b * n_shell + e] = cdiag * self - coff * sacc;
+    }
+}
+
+// pre[c][e] = {v_c(self), sum of v_c over the 6 neighbours} on the shell: the
+// sigma-independent parts of q for densities that stay fixed between solves
+// (the same neighbour order and FP32 sum as k_shell_rhs)
+__global__ void k_shell_pre(int n_shell, const int *shell_nb, const float *dens, int64_t ng, float2 *pre) {
+    const int c = blockIdx.y;
+    const float *d = dens + (size_t)c * ng;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_shell; e += gridDim.x * blockDim.x) {
+        const int *nb = shell_nb + 8 * (size_t)e;
+        float sacc = 0.f;
+#pragma unroll
+        for (int q = 1; q < 7; ++q)
+            if (nb[q] >= 0) sacc += d[nb[q]];
+        const float self = nb[0] >= 0 ? d[nb[0]] : 0.f;
+        pre[(size_t)c * n_shell + e] = make_float2(self, sacc);
     }
 }
 
@@ -863,6 +887,15 @@ int tc_status_check() {
         set_error("a tensor-core MMA wait expired (bounded wait)");
         return DPM_ETIMEOUT;
     }
+    return DPM_OK;
+}
+
+int tc_shell_pre(int64_t n_shell, const int *shell_nb, const float *dens, int64_t ng, int ncol, float2 *pre,
+                 cudaStream_t s) {
+    if (n_shell <= 0 || ncol <= 0) return DPM_OK;
+    dim3 g((unsigned)std::min<int64_t>((n_shell + 255) / 256, 256), (unsigned)ncol);
+    k_shell_pre<<<g, 256, 0, s>>>((int)n_shell, shell_nb, dens, ng, pre);
+    DPM_LAUNCHED();
     return DPM_OK;
 }
 
