@@ -545,7 +545,7 @@ extern "C" int dpm_bep_get_info(const dpm_bep *b, dpm_bep_info *info) {
 
 extern "C" int dpm_bep_matrix(const dpm_bep *b, double *A, cudaStream_t s) {
     if (!b || !A) { set_error("bep/A is NULL"); return DPM_EINVAL; }
-    const double *A0 = b->lsq.work.as<double>();  // unfactored copy
+    const double *A0 = lsq_matrix(b->lsq);  // unfactored
     DPM_CUDA(cudaMemcpyAsync(A, A0, sizeof(double) * b->gi.n_gin * b->ncol, cudaMemcpyDeviceToDevice, s));
     return DPM_OK;
 }

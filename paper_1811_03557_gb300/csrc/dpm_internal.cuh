@@ -205,8 +205,13 @@ struct LsqFactor {
     DevBuf A;      // double[m*n] column-major (Householder overwrites it)
     DevBuf tau;    // double[n] Householder scalars
     DevBuf X;      // scratch of the Gram / Cholesky factorisation
-    DevBuf work;   // A copy, R, solve scratch
+    DevBuf work;   // A copy (Householder only), R, solve scratch
 };
+// The unfactored A the solves read: a copy for Householder QR (which
+// overwrites A), A itself for the Cholesky-based methods.
+inline const double *lsq_matrix(const LsqFactor &f) {
+    return f.method == LsqFactor::kHouseholder ? f.work.as<double>() : f.A.as<double>();
+}
 // ---------------------------------------------------------------------------
 // Domain decomposition, Case 1 (Section 3): kernels in dd.cu
 // ---------------------------------------------------------------------------

@@ -1018,7 +1018,10 @@ static int lsq_factor_impl(LsqFactor &f, bool sync, cudaStream_t s) {
     double *rdiag = w + n;
     double *R = rdiag + n;
     int *status = reinterpret_cast<int *>(R + (size_t)n * n);
-    DPM_CUDA(cudaMemcpyAsync(A0, f.A.p, sizeof(double) * m * n, cudaMemcpyDeviceToDevice, s));
+    if (f.method == LsqFactor::kHouseholder)  // the reflectors overwrite f.A
+        DPM_CUDA(cudaMemcpyAsync(A0, f.A.p, sizeof(double) * m * n, cudaMemcpyDeviceToDevice, s));
+    else
+        A0 = f.A.as<double>();
     DPM_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
     double *Rinv = reinterpret_cast<double *>(reinterpret_cast<char *>(R + (size_t)n * n) + 64) +
                    kLsqMaxRhs * ((size_t)n + (size_t)m) + kLsqMaxRhs * (size_t)n;
@@ -1061,8 +1064,8 @@ static int lsq_factor_impl(LsqFactor &f, bool sync, cudaStream_t s) {
 template <class T>
 int lsq_apply(const LsqFactor &f, const T *b, int ldb, double *C, int nr, cudaStream_t s) {
     const int m = f.m, n = f.n;
-    const double *A0 = f.work.as<double>();
-    const double *R = A0 + (size_t)m * n + 2 * (size_t)n;
+    const double *R = f.work.as<double>() + (size_t)m * n + 2 * (size_t)n;
+    const double *A0 = lsq_matrix(f);
     int *status = reinterpret_cast<int *>(const_cast<double *>(R) + (size_t)n * n);
     if (nr < 1 || nr > kLsqMaxRhs) { set_error("least squares: 1..%d right-hand sides per call", kLsqMaxRhs); return DPM_EINVAL; }
     // scratch after the factor: y[nr][n], res[nr][m]
