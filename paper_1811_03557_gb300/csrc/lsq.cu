@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kAtbT) k_atb(int m, int n, const double *__res
 }
 
 // The same products from the FP32 copy of A and FP32 right-hand sides (or
-// residuals): FP32 products and per-thread sums, FP64 block sums.  Used for
+// residuals): FP32 products, per-thread and warp sums, FP64 block sums.  Used for
 // A^T b and A^T r on the mixed-precision path, where only the residual needs
 // FP64 (the preconditioner's own error is larger than these roundings).
 __global__ void __launch_bounds__(kAtbT) k_atb32(int m, int n, const float *__restrict__ A32,
@@ -176,11 +176,15 @@ __global__ void __launch_bounds__(kAtbT) k_atb32(int m, int n, const float *__re
             }
         }
     }
+    // warp sums in FP32 (the FP64 pipe runs at 1/64 of the FP32 rate), the
+    // block's 8 warp sums in FP64
 #pragma unroll
     for (int q = 0; q < kAtbQ; ++q) {
-        double v = (double)acc[q];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) sh[q][warp] = v;
+        if (q < nq) {
+            float v = acc[q];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) sh[q][warp] = (double)v;
+        }
     }
     __syncthreads();
     if (t < nq) {
@@ -818,6 +822,52 @@ __global__ void k_trimv(int n, const MT *M, const double *y, double *out, int nr
     }
 }
 
+// The mixed path's two triangular products in one CTA, in FP32 (they apply the
+// FP32 preconditioner to a correction that the FP64 residual refines; C
+// accumulates in FP64):
+//   y[q][k] = yscale[k] sum_sl part[sl][q][k],  z = R^{-T} y,
+//   C[q][i] (+)= outscale[i] (R^{-1} z)[q][i],
+// with R^{-1} (upper triangular, row-major, FP32) staged in shared memory.
+constexpr int kTriT = 1024;
+size_t trisolve_smem(int n, int nr) { return sizeof(float) * ((size_t)n * n + 2 * (size_t)nr * n); }
+__global__ void __launch_bounds__(kTriT) k_trisolve32(int n, int nr, const float *__restrict__ M,
+                                                      const double *__restrict__ part, int S,
+                                                      const double *__restrict__ yscale, double *C, int accumulate,
+                                                      const double *__restrict__ outscale) {
+    extern __shared__ float tsm[];
+    float *Ms = tsm, *ys = Ms + (size_t)n * n, *zs = ys + (size_t)nr * n;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (int e = t; e < n * n; e += kTriT) Ms[e] = M[e];
+    for (int e = t; e < nr * n; e += kTriT) {
+        const int q = e / n, k = e - q * n;
+        double v = 0.0;
+        for (int sl = 0; sl < S; ++sl) v += part[((size_t)sl * nr + q) * n + k];
+        if (yscale) v *= yscale[k];
+        ys[e] = (float)v;
+    }
+    __syncthreads();
+    for (int o = warp; o < nr * n; o += kTriT / 32) {  // z[q][i] = sum_{k <= i} M[k][i] y[q][k]
+        const int q = o / n, i = o - q * n;
+        float a = 0.f;
+        for (int k = lane; k <= i; k += 32) a = fmaf(Ms[k * n + i], ys[q * n + k], a);
+        for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+        if (lane == 0) zs[o] = a;
+    }
+    __syncthreads();
+    for (int o = warp; o < nr * n; o += kTriT / 32) {  // (R^{-1} z)[q][i] = sum_{k >= i} M[i][k] z[q][k]
+        const int q = o / n, i = o - q * n;
+        float a = 0.f;
+        for (int k = i + lane; k < n; k += 32) a = fmaf(Ms[i * n + k], zs[q * n + k], a);
+        for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+        if (lane == 0) {
+            double c = (double)a;
+            if (outscale) c *= outscale[i];
+            double *dst = C + (size_t)q * n + i;
+            *dst = accumulate ? *dst + c : c;
+        }
+    }
+}
+
 }  // namespace
 
 static int householder_factor(LsqFactor &f, double *A0, double *w, double *rdiag, double *R,
@@ -1130,8 +1180,22 @@ int lsq_apply(const LsqFactor &f, const T *b, int ldb, double *C, int nr, cudaSt
     else
         k_atb<<<dim3(n, S, qg), kAtbT, 0, s>>>(m, n, A0, bd, ldbd, ypart, nr, rows_per);
     DPM_LAUNCHED();
-    DPM_RET(trimv(true, ypart, z, 0, nullptr, S, dsc));
-    DPM_RET(trimv(false, z, C, 0, dsc, 1, nullptr));
+    // z = R^{-T} D y, C (+)= D R^{-1} z
+    const size_t tsm = trisolve_smem(n, nr);
+    const bool fused = fast32 && f.rinv32 && tsm <= 227 * 1024;
+    if (fused && tsm > 48 * 1024)
+        DPM_CUDA(cudaFuncSetAttribute(k_trisolve32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+    auto precondition = [&](int accumulate) -> int {
+        if (fused) {
+            k_trisolve32<<<1, kTriT, tsm, s>>>(n, nr, reinterpret_cast<const float *>(Rinv), ypart, S, dsc, C,
+                                               accumulate, dsc);
+            DPM_LAUNCHED();
+            return DPM_OK;
+        }
+        DPM_RET(trimv(true, ypart, z, 0, nullptr, S, dsc));
+        return trimv(false, z, C, accumulate, dsc, 1, nullptr);
+    };
+    DPM_RET(precondition(0));
     // iterative refinement: C += D R^{-1} R^{-T} D A^T (b - A C), the residual in FP64
     for (int it = 0; it < refine; ++it) {
         if (fast32) {
@@ -1144,8 +1208,7 @@ int lsq_apply(const LsqFactor &f, const T *b, int ldb, double *C, int nr, cudaSt
             k_atb<<<dim3(n, S, qg), kAtbT, 0, s>>>(m, n, A0, res, m, ypart, nr, rows_per);
         }
         DPM_LAUNCHED();
-        DPM_RET(trimv(true, ypart, z, 0, nullptr, S, dsc));
-        DPM_RET(trimv(false, z, C, 1, dsc, 1, nullptr));
+        DPM_RET(precondition(1));
     }
     (void)y;
     return DPM_OK;
