@@ -837,7 +837,15 @@ __global__ void __launch_bounds__(kTriT) k_trisolve32(int n, int nr, const float
     extern __shared__ float tsm[];
     float *Ms = tsm, *ys = Ms + (size_t)n * n, *zs = ys + (size_t)nr * n;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    for (int e = t; e < n * n; e += kTriT) Ms[e] = M[e];
+    const int nn = n * n;
+    for (int e0 = t; e0 < nn; e0 += 8 * kTriT) {  // 8 loads in flight per thread
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = e0 + u * kTriT < nn ? M[e0 + u * kTriT] : 0.f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (e0 + u * kTriT < nn) Ms[e0 + u * kTriT] = v[u];
+    }
     for (int e = t; e < nr * n; e += kTriT) {
         const int q = e / n, k = e - q * n;
         double v = 0.0;
