@@ -135,3 +135,25 @@ def test_elliptic_solve_many_harmonics(ctx, prec, tol, K):
     print(f"elliptic K={K} prec={prec} rel err on N+ {e:.3e}")
     assert e < tol
     b.close()
+
+
+@pytest.mark.parametrize("K,beta", [(0, 0), (2, 1), (6, 0), (7, 1), (8, 1), (12, 0)])
+def test_elliptic_solve_factor_sizes(ctx, K, beta):
+    """The FP32 path's least squares at n = 1, 18, 49, 128, 162 columns (the
+    one-CTA FP32 Cholesky: a single partial panel, partial last panels, full
+    panels) and n = 169 (just past it: the FP64 Cholesky from global memory),
+    on an N=32 ellipsoid against the oracle's Householder solve."""
+    geom, N, lo, hi, sigma = Geometry.ellipsoid(0.9, 0.75, 0.6), 32, -1.125, 1.125, 3.0e3
+    prec = abi.DPM_PREC_FP32
+    b = GpuBep(ctx, geom, N, lo, hi, sigma, K, beta, prec)
+    s = O.DPMSetup(geom, N, lo, hi, K, beta, sigma)
+    assert s.ncol == (K + 1) ** 2 * (2 if beta else 1)
+    f, gn = manufactured_case(s, geom, N, lo, hi, sigma, s.xf, s.normal)
+    f = f.astype(np.float32).astype(np.float64)
+    u, C = b.solve(f, gn)
+    uo, Co, _ = O.dpm_elliptic_solve(s, f, gn)
+    Np = s.sets["Np"]
+    e = rel(u[Np], uo[Np])
+    print(f"elliptic n={s.ncol} rel err on N+ {e:.3e}")
+    assert e < 1e-4
+    b.close()
