@@ -1126,7 +1126,9 @@ int lsq_apply(const LsqFactor &f, const T *b, int ldb, double *C, int nr, cudaSt
     const double *A0 = lsq_matrix(f);
     int *status = reinterpret_cast<int *>(const_cast<double *>(R) + (size_t)n * n);
     if (nr < 1 || nr > kLsqMaxRhs) { set_error("least squares: 1..%d right-hand sides per call", kLsqMaxRhs); return DPM_EINVAL; }
-    // scratch after the factor: y[nr][n], res[nr][m]
+    // scratch after the factor (layout in lsq_factor_impl): the residuals
+    // res[nr][m] (FP32 on the mixed path), z[nr][n], then R^{-1}, the column
+    // scales and the A^T b slices; the y region is not used by the solve
     size_t base = sizeof(double) * ((size_t)m * n + 2 * (size_t)n + (size_t)n * n) + 64;
     double *y = reinterpret_cast<double *>(static_cast<char *>(f.work.p) + base);
     double *res = y + kLsqMaxRhs * (size_t)n;
@@ -1135,9 +1137,9 @@ int lsq_apply(const LsqFactor &f, const T *b, int ldb, double *C, int nr, cudaSt
     (void)status;
     const int mv_blocks = (n * nr * 32 + 255) / 256;
     const double *dsc = f.equilibrated ? Rinv + (size_t)n * n : nullptr;
-    // FP64 refinement steps: each contracts the error by ~kappa(AD)^2 eps_32.
-    // One leaves C ~1e-11 relative, far below the FP32 solver's error; the
-    // FP64 path takes three.
+    // refinement steps (FP64 residual): each contracts the error by
+    // ~kappa(AD)^2 eps_32.  One leaves C ~1e-10 relative, far below the FP32
+    // solver's error; the FP64 path takes three.
     const int refine = f.equilibrated ? (sizeof(T) == sizeof(double) ? 3 : 1) : 1;
     DPM_PROF("lsq_solve", s);
     // A^T b by row slices: about six CTAs per SM in all, at most kAtbMaxSlices
@@ -1218,7 +1220,6 @@ int lsq_apply(const LsqFactor &f, const T *b, int ldb, double *C, int nr, cudaSt
         DPM_LAUNCHED();
         DPM_RET(precondition(1));
     }
-    (void)y;
     return DPM_OK;
 }
 
