@@ -42,15 +42,13 @@ template <class T> __device__ __forceinline__ T minmod3(T a, T b, T c) {
     return (T)0;
 }
 
-// slope of rho at node q along stride st (0 when q or a neighbour is off N^+)
+// slope of rho at a node from its value and its two neighbours' along one axis
+// (ok: the node and both neighbours on N^+, the node's coordinate in [1, N-2];
+// else 0)
 template <class T>
-__device__ __forceinline__ T slope_at(const T *rho, const uint8_t *lab, int64_t q, int64_t st,
-                                      int coord, int N, T inv_h) {
-    if (coord < 1 || coord > N - 2) return (T)0;
-    if (!in_np(lab[q]) || !in_np(lab[q + st]) || !in_np(lab[q - st])) return (T)0;
-    T r0 = rho[q], rp = rho[q + st], rm = rho[q - st];
-    return minmod3<T>((T)2 * (rp - r0) * inv_h, (rp - rm) * ((T)0.5 * inv_h),
-                      (T)2 * (r0 - rm) * inv_h);
+__device__ __forceinline__ T slope_of(bool ok, T rm, T r0, T rp, T inv_h) {
+    return ok ? minmod3<T>((T)2 * (rp - r0) * inv_h, (rp - rm) * ((T)0.5 * inv_h), (T)2 * (r0 - rm) * inv_h)
+              : (T)0;
 }
 
 template <class T>
@@ -74,15 +72,25 @@ __global__ void k_flux(int N, T h, T chi, double dt_d, const double *dt_dev, con
         for (int ax = 0; ax < 3; ++ax) {
             int64_t s = st[ax];
             int cc = coord[ax];
-            // M^+ is >= 2 nodes from the faces, so p +- s and p +- 2s exist
-            T sp = slope_at<T>(rho, lab, p, s, cc, N, inv_h);
-            T sL = slope_at<T>(rho, lab, p - s, s, cc - 1, N, inv_h);
-            T sR = slope_at<T>(rho, lab, p + s, s, cc + 1, N, inv_h);
-            T gp = (c[p + s] - c0) * inv_h;  // grad c at j+1/2
-            T gm = (c0 - c[p - s]) * inv_h;  // grad c at j-1/2
+            // the labels and densities at p +- s and p +- 2s that the three
+            // slopes (at p, p - s, p + s) read, loaded at once; those at p +- 2s
+            // only where that slope's node has a coordinate in [1, N-2]
+            const bool in_c = cc >= 1 && cc <= N - 2, in_l = cc >= 2 && cc <= N - 1,
+                       in_r = cc >= 0 && cc <= N - 3;
+            const uint8_t lm1 = (in_c || in_l) ? lab[p - s] : 0, lp1 = (in_c || in_r) ? lab[p + s] : 0;
+            const uint8_t lm2 = in_l ? lab[p - 2 * s] : 0, lp2 = in_r ? lab[p + 2 * s] : 0;
+            const T rm1 = rho[p - s], rp1 = rho[p + s];
+            const T rm2 = in_l ? rho[p - 2 * s] : (T)0, rp2 = in_r ? rho[p + 2 * s] : (T)0;
+            const T cp1 = c[p + s], cm1 = c[p - s];
+            // p is on M^+, hence on N^+
+            T sp = slope_of<T>(in_c && in_np(lm1) && in_np(lp1), rm1, r0, rp1, inv_h);
+            T sL = slope_of<T>(in_l && in_np(lm1) && in_np(lm2), rm2, rm1, r0, inv_h);
+            T sR = slope_of<T>(in_r && in_np(lp1) && in_np(lp2), r0, rp1, rp2, inv_h);
+            T gp = (cp1 - c0) * inv_h;  // grad c at j+1/2
+            T gm = (c0 - cm1) * inv_h;  // grad c at j-1/2
             T east = r0 + half_h * sp, west = r0 - half_h * sp;
-            T rho_p = gp > 0 ? east : rho[p + s] - half_h * sR;
-            T rho_m = gm > 0 ? rho[p - s] + half_h * sL : west;
+            T rho_p = gp > 0 ? east : rp1 - half_h * sR;
+            T rho_m = gm > 0 ? rm1 + half_h * sL : west;
             g += (chi * rho_p * gp - chi * rho_m * gm) * inv_h;
         }
         f_rho[p] = r0 - dt * g;
