@@ -30,8 +30,9 @@ Readings where the paper is silent or ambiguous:
 
 Parity pins: every function here is checked by tests/test_oracle_*.py against
 closed forms, brute force, library routines or the paper's theorems.  The
-ellipsoid foot point is pinned by its optimality conditions and the sphere
-limit only ("parity unpinned" beyond Newton convergence).
+ellipsoid foot point is pinned by its optimality conditions, brute force,
+the sphere limit and the closed forms on the principal axes ("parity
+unpinned" for general points beyond bisection convergence).
 """
 from __future__ import annotations
 

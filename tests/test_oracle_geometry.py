@@ -2,7 +2,9 @@
 
 Sphere: closed form.  Ellipsoid: the optimality conditions of the closest
 point (on the surface, p - x' parallel to the normal), brute-force distance
-minimisation over a dense surface sample, and the sphere limit."""
+minimisation over a dense surface sample, the sphere limit, and the closed
+forms on the principal axes (outside: the vertex; inside on the shortest axis:
+its vertex)."""
 import numpy as np
 import pytest
 
@@ -55,3 +57,34 @@ def test_ellipsoid_optimality_and_brute_force():
         dmin = np.min(np.linalg.norm(S - P[k], axis=1))
         assert abs(d[k]) <= dmin + 1e-12
         assert abs(d[k]) >= dmin - 5e-5
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_ellipsoid_axis_points_outside(axis):
+    """A point on a principal axis beyond the vertex projects onto the vertex:
+    x' = c +- a_i e_i, d = |t| - a_i, n = +-e_i (closed form)."""
+    g = Geometry.ellipsoid(1.0, 0.8, 0.6, (0.1, -0.2, 0.05))
+    c, a = np.array(g.center), np.array(g.axes)
+    e = np.eye(3)[axis]
+    t = np.array([a[axis] + 0.01, a[axis] + 0.3, -(a[axis] + 0.07), -(a[axis] + 1.0)])
+    P = c + t[:, None] * e
+    xf, d, n = O.foot_point(g, P)
+    sgn = np.sign(t)
+    assert np.allclose(xf, c + (sgn * a[axis])[:, None] * e, atol=1e-13)
+    assert np.allclose(d, np.abs(t) - a[axis], atol=1e-13)
+    assert np.allclose(n, sgn[:, None] * e, atol=1e-13)
+
+
+def test_ellipsoid_shortest_axis_points_inside():
+    """Inside, on the shortest axis, the nearest surface point is that axis's
+    vertex (the other vertices and every off-axis point are farther):
+    d = |t| - a_min < 0."""
+    g = Geometry.ellipsoid(1.0, 0.8, 0.6)
+    t = np.array([0.55, 0.3, 0.05, -0.2, -0.59])
+    P = np.zeros((len(t), 3))
+    P[:, 2] = t
+    xf, d, n = O.foot_point(g, P)
+    sgn = np.sign(t)
+    assert np.allclose(xf, np.stack([0 * t, 0 * t, 0.6 * sgn], 1), atol=1e-12)
+    assert np.allclose(d, np.abs(t) - 0.6, atol=1e-12)
+    assert np.allclose(n[:, 2], sgn, atol=1e-12)
