@@ -105,6 +105,40 @@ def test_cfl_dt_gives_nonnegative_rhs():
         assert dt > 0
 
 
+def _cone(sets, h, G, p):
+    """c = G h (|i - i_p| + |j - j_p| + |k - k_p|): |grad_h c| = G on every face."""
+    N = sets["Np"].shape[0]
+    i, j, k = np.meshgrid(*(np.arange(N),) * 3, indexing="ij")
+    return G * h * (np.abs(i - p[0]) + np.abs(j - p[1]) + np.abs(k - p[2])).astype(np.float64)
+
+
+def test_cfl_dt_denominator_is_the_papers_and_sharp():
+    """eq. cfl_condition: dt = h / (6 chi max|grad_h c|), the 6 read from the
+    golden file.  The bound is sharp: a single spike of density at the bottom of
+    a cone of c (every face gradient equal to G, pointing away from the spike)
+    sends the whole spike out through its six faces, so f_rho at the spike is
+    exactly 0 at the CFL step and -rho at twice the step."""
+    den = json.load(open(os.path.join(GOLD, "paper_parameters.json")))["cfl_denominator"]["value"]
+    g, sets, h, _ = _setup(N=18)
+    p = (9, 9, 9)
+    assert sets["Mp"][p]
+    for G, chi in ((3.0, 1.0), (40.0, 0.5)):
+        c = _cone(sets, h, G, p)
+        dt = O.cfl_dt(c, sets, h, chi)
+        assert dt == pytest.approx(h / (den * chi * G), rel=1e-12)
+        rho = np.zeros_like(c)
+        rho[p] = 7.0
+        f1, _ = O.pks_rhs(rho, c, sets, h, chi, dt)
+        f2, _ = O.pks_rhs(rho, c, sets, h, chi, 2 * dt)
+        assert abs(f1[p]) <= 1e-12 * 7.0
+        assert f2[p] == pytest.approx(-7.0, rel=1e-12)
+        assert f1[sets["Mp"]].min() >= -1e-12 * 7.0
+    # per-axis maxima: the bound is set by the steepest axis
+    X, Y, Z = O.mesh(18, -1.3, 1.3)
+    c = np.where(sets["Np"], 1.0 * X - 4.0 * Y + 2.5 * Z, 0.0)
+    assert O.cfl_dt(c, sets, h, 1.0) == pytest.approx(h / (den * 4.0), rel=1e-9)
+
+
 def test_interior_fluxes_telescope():
     """Sum over M^+ of h^3 g = boundary fluxes; with c flat near gamma it is 0."""
     g, sets, h, (X, Y, Z) = _setup(N=22)
@@ -126,7 +160,56 @@ def test_diagnostics_closed_forms():
     assert d["max_rho"] == 2.0
     # free energy of a constant density with c = 0: rho log rho per cell
     assert d["free_energy"] == pytest.approx(nMp * h ** 3 * 2.0 * np.log(2.0))
-    assert d["m2"] == pytest.approx(h ** 3 * 2.0 * np.sum((X * X + Y * Y + Z * Z)[sets["Mp"]]))
+
+
+def test_second_moment_of_single_nodes():
+    """eq. sd-norm:second-moment for a density that is one unit at a single node
+    p of M^+ and zero elsewhere: M_h = h^3 |x_p|^2, with x_p = lo + (index + 1) h
+    (the node grid); nodes of M^- contribute nothing."""
+    N, lo, hi = 16, -1.3, 1.3
+    g, sets, h, _ = _setup(N=N, lo=lo, hi=hi)
+    for p in [(8, 8, 8), (3, 8, 10), (12, 5, 7), (0, 0, 0)]:
+        rho = np.zeros((N, N, N))
+        rho[p] = 1.0
+        d = O.diagnostics(rho, np.zeros_like(rho), sets, h, N, lo, hi)
+        x = [lo + (q + 1) * h for q in p]
+        want = h ** 3 * (x[0] ** 2 + x[1] ** 2 + x[2] ** 2) if sets["Mp"][p] else 0.0
+        assert d["m2"] == pytest.approx(want, rel=1e-12, abs=1e-300)
+        assert d["mass"] == pytest.approx(h ** 3 if sets["Mp"][p] else 0.0, rel=1e-12, abs=1e-300)
+
+
+def _free_energy_linear_c(sets, h, X, rho0, a, k, ax, grad_coef):
+    """Closed form of eq. sd-norm:free-energy for rho = rho0 on M^+ and
+    c = a + k x_ax on the whole grid: per node rho0 ln rho0 - rho0 c + c^2/2
+    plus grad_coef * (2 h k)^2 (the central differences of a linear c are 2 h k
+    along ax and 0 along the other axes)."""
+    Mp = sets["Mp"]
+    x = X[ax][Mp]
+    n = Mp.sum()
+    return h ** 3 * (n * rho0 * np.log(rho0) - rho0 * np.sum(a + k * x) + 0.5 * np.sum((a + k * x) ** 2)
+                     + n * grad_coef * (2.0 * h * k) ** 2)
+
+
+@pytest.mark.parametrize("ax", [0, 1, 2])
+def test_free_energy_linear_c_closed_form(ax):
+    """Every term of eq. sd-norm:free-energy: the gradient term of a linear c is
+    (2 h k)^2 / (8 h^2) = k^2 / 2 per node whatever h is; -rho c and c^2 / 2
+    against their sums.  A 1/(4 h^2) in place of 1/(8 h^2), a dropped -rho c or
+    a + sign on it each move F by far more than the tolerance."""
+    N, lo, hi = 16, -1.3, 1.3
+    g, sets, h, XYZ = _setup(N=N, lo=lo, hi=hi)
+    rho0, a, k = 1.5, 2.0, 3.0
+    rho = np.where(sets["Np"], rho0, 0.0)
+    c = a + k * XYZ[ax]
+    F = O.diagnostics(rho, c, sets, h, N, lo, hi)["free_energy"]
+    want = _free_energy_linear_c(sets, h, XYZ, rho0, a, k, ax, 1.0 / (8.0 * h * h))
+    assert F == pytest.approx(want, rel=1e-12)
+    # planted mistakes, each evaluated in the same closed form, are all rejected
+    wrong_grad = _free_energy_linear_c(sets, h, XYZ, rho0, a, k, ax, 1.0 / (4.0 * h * h))
+    wrong_rc = want + h ** 3 * rho0 * np.sum((a + k * XYZ[ax])[sets["Mp"]])
+    wrong_sign = want + 2.0 * h ** 3 * rho0 * np.sum((a + k * XYZ[ax])[sets["Mp"]])
+    for w in (wrong_grad, wrong_rc, wrong_sign):
+        assert abs(F - w) > 1e-3 * abs(F)
 
 
 @pytest.fixture(scope="module")
