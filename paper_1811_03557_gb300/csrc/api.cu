@@ -72,7 +72,7 @@ void prof_end(int rec, cudaStream_t s) {
 template <class T>
 int pks_flux(int, double, double, double, const double *, const uint8_t *, const T *, const T *,
              T *, T *, cudaStream_t);
-template <class T> int pks_cfl(int, const uint8_t *, const T *, unsigned int *, cudaStream_t);
+template <class T> int pks_cfl(int, const uint8_t *, const T *, unsigned long long *, cudaStream_t);
 template <class T>
 int pks_diag(int, double, double, const uint8_t *, const T *, const T *, double *, double *,
              cudaStream_t, const double *origin = nullptr);
@@ -192,7 +192,7 @@ struct dpm_pks {
     dpm_pks_params prm{};
     dpm_bep bep;
     DevBuf rho, c, frho, fc;
-    DevBuf gmax;       // uint32[3]
+    DevBuf gmax;       // 3 non-negative doubles as uint64 bit patterns
     DevBuf diag_part;  // double[nblk][6]
     DevBuf diag_out;   // double[6]
     double t = 0, dt_prev = 0;
@@ -648,7 +648,7 @@ template <class T> int pks_alloc(dpm_pks *k, cudaStream_t s) {
     DPM_RET(k->c.alloc(sizeof(T) * n3));
     DPM_RET(k->frho.alloc(sizeof(T) * n3));
     DPM_RET(k->fc.alloc(sizeof(T) * n3));
-    DPM_RET(k->gmax.alloc(sizeof(unsigned int) * 4));
+    DPM_RET(k->gmax.alloc(sizeof(unsigned long long) * 4));
     DPM_RET(k->diag_part.alloc(sizeof(double) * 6 * pks_diag_blocks(k->prm.N)));
     DPM_RET(k->diag_out.alloc(sizeof(double) * 8));
     DPM_CUDA(cudaMemsetAsync(k->diag_out.p, 0, sizeof(double) * 8, s));
@@ -662,13 +662,12 @@ template <class T> int pks_step_one(dpm_pks *k, cudaStream_t s) {
     const double h = b->gi.h;
     double dt = P.dt_max;
     if (P.dt_mode == 1) {
-        unsigned int gm[3];
-        DPM_RET(pks_cfl<T>(N, b->gi.labels.as<uint8_t>(), k->c.as<T>(), k->gmax.as<unsigned int>(), s));
+        double gm[3];
+        DPM_RET(pks_cfl<T>(N, b->gi.labels.as<uint8_t>(), k->c.as<T>(), k->gmax.as<unsigned long long>(), s));
         DPM_CUDA(cudaMemcpyAsync(gm, k->gmax.p, sizeof(gm), cudaMemcpyDeviceToHost, s));
         DPM_CUDA(cudaStreamSynchronize(s));
         for (int ax = 0; ax < 3; ++ax) {
-            float g;
-            memcpy(&g, &gm[ax], sizeof(g));
+            const double g = gm[ax];
             double gmaxv = (double)g / h;  // max |grad_h c| along ax
             if (gmaxv > 0) dt = std::min(dt, h / (6.0 * P.chi * gmaxv));
         }
@@ -722,8 +721,8 @@ template <class T> int pks_step_dev(dpm_pks *k, cudaStream_t s) {
     StepScalars *sc = k->scal.as<StepScalars>();
     const uint8_t *lab = b->gi.labels.as<uint8_t>();
     if (P.dt_mode == 1)
-        DPM_RET(pks_cfl<T>(N, lab, k->c.as<T>(), k->gmax.as<unsigned int>(), s));
-    DPM_RET(pks_step_dt(k->gmax.as<unsigned int>(), h, P.chi, P.dt_max, P.dt_mode, sc, s));
+        DPM_RET(pks_cfl<T>(N, lab, k->c.as<T>(), k->gmax.as<unsigned long long>(), s));
+    DPM_RET(pks_step_dt(k->gmax.as<unsigned long long>(), h, P.chi, P.dt_max, P.dt_mode, sc, s));
     T *frho = k->frho.as<T>(), *fc = k->fc.as<T>();
     DPM_RET(pks_flux<T>(N, h, P.chi, 0.0, &sc->dt, lab, k->rho.as<T>(), k->c.as<T>(), frho, fc, s));
     const bool rebuild = P.dt_mode == 1 || P.rebuild;
@@ -1261,7 +1260,7 @@ template <class T> int dd_pks_alloc(dpm_dd_pks *k, const dpm_gaussian &g0, const
         DPM_RET(sd.c.alloc(sizeof(T) * n3));
         DPM_RET(sd.frho.alloc(sizeof(T) * n3));
         DPM_RET(sd.fc.alloc(sizeof(T) * n3));
-        DPM_RET(sd.gmax.alloc(sizeof(unsigned int) * 4));
+        DPM_RET(sd.gmax.alloc(sizeof(unsigned long long) * 4));
         DPM_RET(sd.diag_part.alloc(sizeof(double) * 6 * pks_diag_blocks(sd.N)));
         DPM_RET(sd.diag_out.alloc(sizeof(double) * 8));
         DPM_CUDA(cudaMemsetAsync(sd.diag_out.p, 0, sizeof(double) * 8, s));
@@ -1280,18 +1279,16 @@ template <class T> int dd_pks_step(dpm_dd_pks *k, cudaStream_t s) {
     if (k->dt_mode == 1) {
         for (int l = 0; l < 2; ++l) {
             DDSub &sd = d->sub[l];
-            DPM_RET(pks_cfl<T>(sd.N, sd.gi.labels.as<uint8_t>(), sd.c.as<T>(), sd.gmax.as<unsigned int>(), s));
+            DPM_RET(pks_cfl<T>(sd.N, sd.gi.labels.as<uint8_t>(), sd.c.as<T>(), sd.gmax.as<unsigned long long>(), s));
         }
-        unsigned int gm[2][3];
+        double gm[2][3];
         for (int l = 0; l < 2; ++l)
             DPM_CUDA(cudaMemcpyAsync(gm[l], d->sub[l].gmax.p, sizeof(gm[l]), cudaMemcpyDeviceToHost, s));
         DPM_CUDA(cudaStreamSynchronize(s));
         for (int l = 0; l < 2; ++l) {
             const double h = d->sub[l].gi.h;
             for (int ax = 0; ax < 3; ++ax) {
-                float g;
-                memcpy(&g, &gm[l][ax], sizeof(g));
-                const double gmaxv = (double)g / h;
+                const double gmaxv = gm[l][ax] / h;
                 if (gmaxv > 0) dt = std::min(dt, h / (6.0 * k->chi * gmaxv));
             }
         }
@@ -1765,7 +1762,7 @@ template <class T> int dd2_pks_alloc(dpm_dd2_pks *k, const dpm_gaussian &g0, con
         DPM_RET(sd.c.alloc(sizeof(T) * n3));
         DPM_RET(sd.frho.alloc(sizeof(T) * n3));
         DPM_RET(sd.fc.alloc(sizeof(T) * n3));
-        DPM_RET(sd.gmax.alloc(sizeof(unsigned int) * 4));
+        DPM_RET(sd.gmax.alloc(sizeof(unsigned long long) * 4));
         DPM_RET(sd.diag_part.alloc(sizeof(double) * 6 * pks_diag_blocks(sd.N)));
         DPM_RET(sd.diag_out.alloc(sizeof(double) * 8));
         DPM_CUDA(cudaMemsetAsync(sd.diag_out.p, 0, sizeof(double) * 8, s));
@@ -1789,18 +1786,16 @@ template <class T> int dd2_pks_step(dpm_dd2_pks *k, cudaStream_t s) {
     if (k->dt_mode == 1) {
         for (int l = 0; l < 2; ++l) {
             DD2Sub &sd = d->sub[l];
-            DPM_RET(pks_cfl<T>(sd.N, sd.gi.labels.as<uint8_t>(), sd.c.as<T>(), sd.gmax.as<unsigned int>(), s));
+            DPM_RET(pks_cfl<T>(sd.N, sd.gi.labels.as<uint8_t>(), sd.c.as<T>(), sd.gmax.as<unsigned long long>(), s));
         }
-        unsigned int gm[2][3];
+        double gm[2][3];
         for (int l = 0; l < 2; ++l)
             DPM_CUDA(cudaMemcpyAsync(gm[l], d->sub[l].gmax.p, sizeof(gm[l]), cudaMemcpyDeviceToHost, s));
         DPM_CUDA(cudaStreamSynchronize(s));
         for (int l = 0; l < 2; ++l) {
             const double h = d->sub[l].gi.h;
             for (int ax = 0; ax < 3; ++ax) {
-                float g;
-                memcpy(&g, &gm[l][ax], sizeof(g));
-                const double gmaxv = (double)g / h;
+                const double gmaxv = gm[l][ax] / h;
                 if (gmaxv > 0) dt = std::min(dt, h / (6.0 * k->chi * gmaxv));
             }
         }
@@ -2250,7 +2245,7 @@ template <class T> int ml_pks_alloc(dpm_ml_pks *k, const dpm_gaussian &g0, const
         DPM_RET(sd.c.alloc(sizeof(T) * n3));
         DPM_RET(sd.frho.alloc(sizeof(T) * n3));
         DPM_RET(sd.fc.alloc(sizeof(T) * n3));
-        DPM_RET(sd.gmax.alloc(sizeof(unsigned int) * 4));
+        DPM_RET(sd.gmax.alloc(sizeof(unsigned long long) * 4));
         DPM_RET(sd.diag_part.alloc(sizeof(double) * 6 * pks_diag_blocks(sd.N)));
         DPM_RET(sd.diag_out.alloc(sizeof(double) * 8));
         DPM_CUDA(cudaMemsetAsync(sd.diag_out.p, 0, sizeof(double) * 8, s));
@@ -2264,19 +2259,17 @@ template <class T> int ml_pks_step(dpm_ml_pks *k, cudaStream_t s) {
     const int L = (int)d->L;
     double dt = k->dt_max;
     if (k->dt_mode == 1) {
-        std::vector<unsigned int> gm(3 * L);
+        std::vector<double> gm(3 * L);
         for (int l = 0; l < L; ++l) {
             MLSub &sd = d->sub[l];
-            DPM_RET(pks_cfl<T>(sd.N, sd.gi.labels.as<uint8_t>(), sd.c.as<T>(), sd.gmax.as<unsigned int>(), s));
-            DPM_CUDA(cudaMemcpyAsync(gm.data() + 3 * l, sd.gmax.p, 3 * sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+            DPM_RET(pks_cfl<T>(sd.N, sd.gi.labels.as<uint8_t>(), sd.c.as<T>(), sd.gmax.as<unsigned long long>(), s));
+            DPM_CUDA(cudaMemcpyAsync(gm.data() + 3 * l, sd.gmax.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
         }
         DPM_CUDA(cudaStreamSynchronize(s));
         for (int l = 0; l < L; ++l) {
             const double h = d->sub[l].gi.h;
             for (int ax = 0; ax < 3; ++ax) {
-                float g;
-                memcpy(&g, &gm[3 * l + ax], sizeof(g));
-                const double gmaxv = (double)g / h;
+                const double gmaxv = gm[3 * l + ax] / h;
                 if (gmaxv > 0) dt = std::min(dt, h / (6.0 * k->chi * gmaxv));
             }
         }

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <mutex>
 #include <vector>
 #include <stdint.h>
 #include <stddef.h>
@@ -50,6 +51,25 @@ struct ProfScope {
         int r_ = (expr);                     \
         if (r_ != DPM_OK) return r_;         \
     } while (0)
+
+// A set-up step that must run once on every device: kernel attributes such
+// as the dynamic shared memory limit belong to each device's context, so a
+// process that uses several devices configures each of them.  `run()` calls
+// `f()` the first time it sees the current device (devices 0..63; any other
+// device runs `f()` on every call) and remembers it only when `f()` succeeds.
+struct PerDeviceOnce {
+    std::mutex mu;
+    uint64_t done = 0;
+    template <class F> int run(F f) {
+        int dev = 0;
+        DPM_CUDA(cudaGetDevice(&dev));
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev >= 0 && dev < 64 && ((done >> dev) & 1ull)) return DPM_OK;
+        const int r = f();
+        if (r == DPM_OK && dev >= 0 && dev < 64) done |= 1ull << dev;
+        return r;
+    }
+};
 
 // Owning device buffer.
 struct DevBuf {
@@ -294,7 +314,7 @@ struct StepScalars {
     long long step;
     int rebuilt, bad;  // bad: a non-positive / non-finite dt was replaced by dt_max
 };
-int pks_step_dt(const unsigned int *gmax, double h, double chi, double dt_max, int mode,
+int pks_step_dt(const unsigned long long *gmax, double h, double chi, double dt_max, int mode,
                 StepScalars *sc, cudaStream_t s);
 int pks_step_end(StepScalars *sc, int rebuilt, cudaStream_t s);
 

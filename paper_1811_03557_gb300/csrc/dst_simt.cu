@@ -473,19 +473,16 @@ __global__ void __launch_bounds__(kThreads) kg_pass_k_inv(const GroupItem<T> *it
 template <class T, int C = 32> size_t smem_rows(int N) { return 2 * (size_t)C * (N + 1) * sizeof(T); }
 template <class T, int C = 32> size_t smem_cols(int N) { return (2 * (size_t)N * C + N) * sizeof(T); }
 
-template <class T, int C = 32> int set_smem_limits(int N) {
-    static int configured = 0;
-    static std::mutex mu;
-    std::lock_guard<std::mutex> lk(mu);
-    size_t need = smem_rows<T, C>(N) > smem_cols<T, C>(N) ? smem_rows<T, C>(N) : smem_cols<T, C>(N);
-    if ((size_t)configured >= need) return DPM_OK;
-    int v = 227 * 1024;
-    DPM_CUDA(cudaFuncSetAttribute(k_pass_k_fwd<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
-    DPM_CUDA(cudaFuncSetAttribute(k_pass_j<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
-    DPM_CUDA(cudaFuncSetAttribute(k_pass_i<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
-    DPM_CUDA(cudaFuncSetAttribute(k_pass_k_inv<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
-    configured = v;
-    return DPM_OK;
+template <class T, int C = 32> int set_smem_limits(int) {
+    static PerDeviceOnce once;
+    return once.run([] {
+        const int v = 227 * 1024;
+        DPM_CUDA(cudaFuncSetAttribute(k_pass_k_fwd<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+        DPM_CUDA(cudaFuncSetAttribute(k_pass_j<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+        DPM_CUDA(cudaFuncSetAttribute(k_pass_i<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+        DPM_CUDA(cudaFuncSetAttribute(k_pass_k_inv<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+        return (int)DPM_OK;
+    });
 }
 
 template <class T, int C> bool tile_fits(int N) {
@@ -661,17 +658,15 @@ int ap_solve_simt(const ApParams &p, const ApRhs<T> *rhs_dev, T *work, cudaStrea
 
 namespace {
 template <class T, int C> int set_group_smem_limits() {
-    static bool done = false;
-    static std::mutex mu;
-    std::lock_guard<std::mutex> lk(mu);
-    if (done) return DPM_OK;
-    const int v = 227 * 1024;
-    DPM_CUDA(cudaFuncSetAttribute(kg_pass_k_fwd<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
-    DPM_CUDA(cudaFuncSetAttribute(kg_pass_j<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
-    DPM_CUDA(cudaFuncSetAttribute(kg_pass_i<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
-    DPM_CUDA(cudaFuncSetAttribute(kg_pass_k_inv<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
-    done = true;
-    return DPM_OK;
+    static PerDeviceOnce once;
+    return once.run([] {
+        const int v = 227 * 1024;
+        DPM_CUDA(cudaFuncSetAttribute(kg_pass_k_fwd<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+        DPM_CUDA(cudaFuncSetAttribute(kg_pass_j<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+        DPM_CUDA(cudaFuncSetAttribute(kg_pass_i<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+        DPM_CUDA(cudaFuncSetAttribute(kg_pass_k_inv<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+        return (int)DPM_OK;
+    });
 }
 
 template <class T, int C>

@@ -858,15 +858,13 @@ int encode_work_map(CUtensorMap *map, float *work, int B) {
 }
 
 int tc_configure() {
-    static bool done = false;
-    static std::mutex mu;
-    std::lock_guard<std::mutex> lk(mu);
-    if (done) return DPM_OK;
-    DPM_CUDA(cudaFuncSetAttribute(k_tc_plane<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-    DPM_CUDA(cudaFuncSetAttribute(k_tc_plane<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-    DPM_CUDA(cudaFuncSetAttribute(k_tc_pencil, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-    done = true;
-    return DPM_OK;
+    static PerDeviceOnce once;
+    return once.run([] {
+        DPM_CUDA(cudaFuncSetAttribute(k_tc_plane<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+        DPM_CUDA(cudaFuncSetAttribute(k_tc_plane<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+        DPM_CUDA(cudaFuncSetAttribute(k_tc_pencil, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+        return (int)DPM_OK;
+    });
 }
 
 }  // namespace

@@ -475,15 +475,13 @@ const uint4 *tc256_sine_blocks() {
 }
 
 int configure256() {
-    static bool done = false;
-    static std::mutex mu;
-    std::lock_guard<std::mutex> lk(mu);
-    if (done) return DPM_OK;
-    DPM_CUDA(cudaFuncSetAttribute(k256_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-    DPM_CUDA(cudaFuncSetAttribute(k256_cols<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-    DPM_CUDA(cudaFuncSetAttribute(k256_cols<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-    done = true;
-    return DPM_OK;
+    static PerDeviceOnce once;
+    return once.run([] {
+        DPM_CUDA(cudaFuncSetAttribute(k256_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+        DPM_CUDA(cudaFuncSetAttribute(k256_cols<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+        DPM_CUDA(cudaFuncSetAttribute(k256_cols<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+        return (int)DPM_OK;
+    });
 }
 
 }  // namespace

@@ -99,33 +99,38 @@ __global__ void k_flux(int N, T h, T chi, double dt_d, const double *dt_dev, con
 }
 
 // gmax[ax] = max |c(p+e) - c(p)|, |c(p) - c(p-e)| over M^+ (as float bits).
+// The maxima are taken in the state precision (|difference| of two state
+// values, as the oracle takes them) and published as the bits of a
+// non-negative double: non-negative IEEE doubles order like their bit
+// patterns, so an integer atomicMax is an exact max and the FP64 path's
+// CFL bound is the oracle's to the last bit for the same c.
 template <class T>
-__global__ void k_cfl(int N, const uint8_t *lab, const T *c, unsigned int *gmax) {
+__global__ void k_cfl(int N, const uint8_t *lab, const T *c, unsigned long long *gmax) {
     const int64_t n3 = (int64_t)N * N * N;
-    float m[3] = {0.f, 0.f, 0.f};
+    T m[3] = {T(0), T(0), T(0)};
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n3;
          p += (int64_t)gridDim.x * blockDim.x) {
         if (!(lab[p] & DPM_LBL_MPLUS)) continue;
         int64_t st[3] = {(int64_t)N * N, (int64_t)N, 1};
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
-            float a = fabsf((float)(c[p + st[ax]] - c[p]));
-            float b = fabsf((float)(c[p] - c[p - st[ax]]));
-            m[ax] = fmaxf(m[ax], fmaxf(a, b));
+            const T a = fabs(c[p + st[ax]] - c[p]);
+            const T b = fabs(c[p] - c[p - st[ax]]);
+            m[ax] = fmax(m[ax], fmax(a, b));
         }
     }
-    __shared__ float shm[3][32];
+    __shared__ T shm[3][32];
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
-        float v = m[ax];
-        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        T v = m[ax];
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
         if ((threadIdx.x & 31) == 0) shm[ax][threadIdx.x >> 5] = v;
     }
     __syncthreads();
     if (threadIdx.x < 3) {
-        float v = 0.f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmaxf(v, shm[threadIdx.x][w]);
-        atomicMax(gmax + threadIdx.x, __float_as_uint(v));
+        T v = T(0);
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmax(v, shm[threadIdx.x][w]);
+        atomicMax(gmax + threadIdx.x, (unsigned long long)__double_as_longlong((double)v));
     }
 }
 
@@ -469,14 +474,13 @@ template int pks_flux<double>(int, double, double, double, const double *, const
 // Step 3 on the device: dt = min(dt_max, CFL bound from the face-gradient
 // maxima, dt_prev) (dt_mode 1; dt_max alone in dt_mode 0), sigma = 1/dt.
 // The arithmetic is the host path's, in FP64.
-__global__ void k_step_dt(const unsigned int *gmax, double h, double chi, double dt_max, int mode,
+__global__ void k_step_dt(const unsigned long long *gmax, double h, double chi, double dt_max, int mode,
                           StepScalars *sc) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double dt = dt_max;
     if (mode == 1) {
         for (int ax = 0; ax < 3; ++ax) {
-            const float g = __uint_as_float(gmax[ax]);
-            const double gm = (double)g / h;
+            const double gm = __longlong_as_double((long long)gmax[ax]) / h;
             if (gm > 0) dt = fmin(dt, h / (6.0 * chi * gm));
         }
         if (sc->step > 0) dt = fmin(dt, sc->dt_prev);
@@ -497,7 +501,7 @@ __global__ void k_step_end(StepScalars *sc, int rebuilt) {
     sc->rebuilt = rebuilt;
 }
 
-int pks_step_dt(const unsigned int *gmax, double h, double chi, double dt_max, int mode,
+int pks_step_dt(const unsigned long long *gmax, double h, double chi, double dt_max, int mode,
                 StepScalars *sc, cudaStream_t s) {
     k_step_dt<<<1, 32, 0, s>>>(gmax, h, chi, dt_max, mode, sc);
     DPM_LAUNCHED();
@@ -511,16 +515,16 @@ int pks_step_end(StepScalars *sc, int rebuilt, cudaStream_t s) {
 }
 
 template <class T>
-int pks_cfl(int N, const uint8_t *lab, const T *c, unsigned int *gmax, cudaStream_t s) {
+int pks_cfl(int N, const uint8_t *lab, const T *c, unsigned long long *gmax, cudaStream_t s) {
     DPM_PROF("pks_cfl", s);
     int64_t n3 = (int64_t)N * N * N;
-    DPM_CUDA(cudaMemsetAsync(gmax, 0, 3 * sizeof(unsigned int), s));
+    DPM_CUDA(cudaMemsetAsync(gmax, 0, 3 * sizeof(unsigned long long), s));
     k_cfl<T><<<reduce_blocks(n3, 256), 256, 0, s>>>(N, lab, c, gmax);
     DPM_LAUNCHED();
     return DPM_OK;
 }
-template int pks_cfl<float>(int, const uint8_t *, const float *, unsigned int *, cudaStream_t);
-template int pks_cfl<double>(int, const uint8_t *, const double *, unsigned int *, cudaStream_t);
+template int pks_cfl<float>(int, const uint8_t *, const float *, unsigned long long *, cudaStream_t);
+template int pks_cfl<double>(int, const uint8_t *, const double *, unsigned long long *, cudaStream_t);
 
 int pks_diag_blocks(int N) { return reduce_blocks((int64_t)N * N * N, kDiagThreads); }
 

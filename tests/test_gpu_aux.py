@@ -75,3 +75,27 @@ def test_full_size_N256_residual_property(ctx):
         # FP32 solution error ~1e-7 relative, amplified by the operator norm sigma + 12/h^2
         bound = 1e-5 * (sigma + 12 / h ** 2) * u[b].abs().max().item()
         assert r < bound, (r, bound)
+
+
+def test_solve_on_a_second_device(ctx):
+    """Kernel attributes (the dynamic shared memory limits above 48 KB) belong to
+    each device's context: after solves on device 0, the same solves on device 1
+    in the same process must still run and agree."""
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs two visible devices")
+    N, B, h, sigma = 128, 2, 2.5 / 129, 1e4 + 1.0
+    q = random_rhs(77, B, N, np.float32)
+    outs = []
+    for dev in (0, 1):
+        with torch.cuda.device(dev):
+            c = ctx if dev == 0 else abi.dpm_ctx_create(1)
+            for prec in (abi.DPM_PREC_FP32, abi.DPM_PREC_TC32):
+                qd = torch.from_numpy(q).to(f"cuda:{dev}")
+                ud = torch.empty_like(qd)
+                abi.dpm_aux_solve_batched(c, N, h, sigma, B, qd, ud, prec)
+                torch.cuda.synchronize(dev)
+                outs.append(ud.cpu().numpy())
+            if dev == 1:
+                abi.dpm_ctx_destroy(c)
+    np.testing.assert_array_equal(outs[0], outs[2])
+    np.testing.assert_array_equal(outs[1], outs[3])

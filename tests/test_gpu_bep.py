@@ -72,7 +72,7 @@ def test_gamma_geometry_matches_oracle(ctx, geom, N, lo, hi):
     b.close()
 
 
-@pytest.mark.parametrize("prec,tol", [(abi.DPM_PREC_FP64, 1e-11), (abi.DPM_PREC_FP32, 1e-4)])
+@pytest.mark.parametrize("prec,tol", [(abi.DPM_PREC_FP64, 1e-11), (abi.DPM_PREC_FP32, 1e-5)])
 @pytest.mark.parametrize("geom,N,lo,hi,K", [(Geometry.sphere(1.0), 32, -1.25, 1.25, 4),
                                             (Geometry.ellipsoid(1.0, 0.8, 0.6), 36, -1.2, 1.2, 3)])
 def test_bep_matrix_matches_oracle(ctx, prec, tol, geom, N, lo, hi, K):
@@ -94,7 +94,7 @@ def manufactured_case(setup_like, geom, N, lo, hi, sigma, xf, normal):
     return f, gn
 
 
-@pytest.mark.parametrize("prec,tol", [(abi.DPM_PREC_FP64, 1e-11), (abi.DPM_PREC_FP32, 1e-4)])
+@pytest.mark.parametrize("prec,tol", [(abi.DPM_PREC_FP64, 1e-11), (abi.DPM_PREC_FP32, 1e-5)])
 def test_elliptic_solve_matches_oracle(ctx, prec, tol):
     """The N=32, K=4 sphere workload: (1/dt+1) u - Lap u = f, Neumann data of
     u = exp(x) sin(y) cos(z)."""
@@ -117,7 +117,7 @@ def test_elliptic_solve_matches_oracle(ctx, prec, tol):
     b.close()
 
 
-@pytest.mark.parametrize("prec,tol", [(abi.DPM_PREC_FP64, 1e-11), (abi.DPM_PREC_FP32, 1e-4)])
+@pytest.mark.parametrize("prec,tol", [(abi.DPM_PREC_FP64, 1e-11), (abi.DPM_PREC_FP32, 1e-5)])
 @pytest.mark.parametrize("K", [9, 12])
 def test_elliptic_solve_many_harmonics(ctx, prec, tol, K):
     """K = 9 and 12 (200 and 338 columns, past the in-shared-memory Cholesky):
@@ -155,5 +155,5 @@ def test_elliptic_solve_factor_sizes(ctx, K, beta):
     Np = s.sets["Np"]
     e = rel(u[Np], uo[Np])
     print(f"elliptic n={s.ncol} rel err on N+ {e:.3e}")
-    assert e < 1e-4
+    assert e < 1e-5, e
     b.close()

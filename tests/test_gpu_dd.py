@@ -41,7 +41,7 @@ def test_shell_classification_bit_exact(ctx):
 
 
 @pytest.mark.parametrize("prec,tol_a,tol_u", [(abi.DPM_PREC_FP64, 1e-11, 1e-11),
-                                              (abi.DPM_PREC_FP32, 1e-4, 1e-4)])
+                                              (abi.DPM_PREC_FP32, 1e-5, 1e-5)])
 def test_dd_bep_and_elliptic_solve_match_oracle(ctx, prec, tol_a, tol_u):
     r1, r2, N1, N2, K, sigma = 0.5, 1.0, 24, 28, 4, 1001.0
     (lo1, hi1), (lo2, hi2) = boxes(N1, N2, r1, r2)
@@ -89,7 +89,7 @@ def test_dd_bep_and_elliptic_solve_match_oracle(ctx, prec, tol_a, tol_u):
 # FP64 with the fixed dt: the CFL mode's dt comes from FP32-rounded gradient
 # maxima on the GPU (a 1e-8 relative difference in dt), so the tight FP64
 # comparison runs at dt_max; the FP32 case runs the CFL mode.
-@pytest.mark.parametrize("prec,mode,tol", [(abi.DPM_PREC_FP64, 0, 1e-10), (abi.DPM_PREC_FP32, 1, 1e-4)])
+@pytest.mark.parametrize("prec,mode,tol", [(abi.DPM_PREC_FP64, 0, 1e-11), (abi.DPM_PREC_FP32, 1, 1e-5)])
 def test_dd_pks_steps_match_oracle(ctx, prec, mode, tol):
     r1, r2, N1, N2 = 0.25, 0.5, 24, 20
     (lo1, hi1), (lo2, hi2) = boxes(N1, N2, r1, r2)
@@ -105,7 +105,7 @@ def test_dd_pks_steps_match_oracle(ctx, prec, mode, tol):
         d = st.diagnostics()
         assert abs(g.dt - dto) <= 1e-6 * dto
         for key in ("mass", "max_rho", "m2", "free_energy"):
-            assert abs(getattr(g, key) - d[key]) <= tol * abs(d[key]), key
+            assert abs(getattr(g, key) - d[key]) <= tol * abs(d[key]), (key, getattr(g, key), d[key])
     dt = torch.float64 if prec == abi.DPM_PREC_FP64 else torch.float32
     for l, sd in enumerate(st.sub):
         rho = torch.empty(sd.N ** 3, dtype=dt, device="cuda")
@@ -114,7 +114,7 @@ def test_dd_pks_steps_match_oracle(ctx, prec, mode, tol):
         torch.cuda.synchronize()
         Np = sd.sets["Np"]
         r_g = rho.cpu().numpy().astype(np.float64).reshape(sd.N, sd.N, sd.N)
-        assert rel(r_g[Np], st.rho[l][Np]) < tol
+        assert rel(r_g[Np], st.rho[l][Np]) < tol, rel(r_g[Np], st.rho[l][Np])
     abi.dpm_dd_pks_destroy(pk)
 
 

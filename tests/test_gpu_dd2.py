@@ -101,7 +101,7 @@ def test_bep_matrix_matches_oracle(ctx, prec):
         abi.dpm_dd2_destroy(d)
     assert A.shape == S.A.shape
     err = np.max(np.abs(A - S.A), axis=0) / np.max(np.abs(S.A), axis=0)
-    assert np.max(err) < (1e-12 if prec == abi.DPM_PREC_FP64 else 2e-5), np.max(err)
+    assert np.max(err) < (1e-12 if prec == abi.DPM_PREC_FP64 else 1e-5), np.max(err)
 
 
 @pytest.mark.parametrize("prec", [abi.DPM_PREC_FP64, abi.DPM_PREC_FP32])
@@ -137,7 +137,7 @@ def test_elliptic_solve_matches_oracle(ctx, prec):
         assert np.max(np.abs(np.where(sd.sets["Mp"], g - u_exact(X, Y, Z), 0))) < 1e-4
 
 
-@pytest.mark.parametrize("prec,tol", [(abi.DPM_PREC_FP64, 1e-10), (abi.DPM_PREC_FP32, 1e-4)])
+@pytest.mark.parametrize("prec,tol", [(abi.DPM_PREC_FP64, 1e-11), (abi.DPM_PREC_FP32, 1e-5)])
 def test_time_loop_matches_oracle(ctx, prec, tol):
     MZ, MG, N1, N2 = 6, 6, 20, 20
     (lo1, hi1, o1), (lo2, hi2, o2) = boxes(N1, N2)
@@ -163,6 +163,6 @@ def test_time_loop_matches_oracle(ctx, prec, tol):
             for got, ref in ((rho, st.rho[l]), (c, st.c[l])):
                 g = got.cpu().numpy().astype(np.float64)
                 r = ref.reshape(-1)
-                assert np.max(np.abs(g[m] - r[m])) <= tol * np.max(np.abs(r[m]))
+                assert np.max(np.abs(g[m] - r[m])) <= tol * np.max(np.abs(r[m])), np.max(np.abs(g[m] - r[m])) / np.max(np.abs(r[m]))
     finally:
         abi.dpm_dd2_pks_destroy(pk)

@@ -37,7 +37,7 @@ def gpu_matrix(ml):
     return A.cpu().numpy().reshape(info.ncol, m).T
 
 
-@pytest.mark.parametrize("prec,tol", [(abi.DPM_PREC_FP64, 1e-12), (abi.DPM_PREC_FP32, 2e-5)])
+@pytest.mark.parametrize("prec,tol", [(abi.DPM_PREC_FP64, 1e-12), (abi.DPM_PREC_FP32, 1e-5)])
 def test_bep_matrix_matches_oracle(ctx, prec, tol):
     K, KG = [3, 4], 3
     S = O.MLSetup((0.0, 0.0, 0.0), RADII, grids(RADII, NS), K, KG, SIGMA)
@@ -107,7 +107,7 @@ def test_elliptic_solve_matches_oracle(ctx, prec):
         assert rel < TOL[prec], rel
 
 
-@pytest.mark.parametrize("prec,tol", [(abi.DPM_PREC_FP64, 1e-10), (abi.DPM_PREC_FP32, 1e-4)])
+@pytest.mark.parametrize("prec,tol", [(abi.DPM_PREC_FP64, 1e-11), (abi.DPM_PREC_FP32, 1e-5)])
 def test_time_loop_matches_oracle(ctx, prec, tol):
     radii, Ns = [0.2, 0.35, 0.5], [20, 24, 28]
     g = grids(radii, Ns)
@@ -133,7 +133,7 @@ def test_time_loop_matches_oracle(ctx, prec, tol):
             for got, ref in ((rho, st.rho[l]), (c, st.c[l])):
                 gg = got.cpu().numpy().astype(np.float64)
                 r = ref.reshape(-1)
-                assert np.max(np.abs(gg[m] - r[m])) <= tol * np.max(np.abs(r[m]))
+                assert np.max(np.abs(gg[m] - r[m])) <= tol * np.max(np.abs(r[m])), np.max(np.abs(gg[m] - r[m])) / np.max(np.abs(r[m]))
     finally:
         abi.dpm_ml_pks_destroy(pk)
 

@@ -1,7 +1,7 @@
 """GPU parity of the N = 256 tensor-core AP solver (six per-axis tcgen05 passes,
 3-term FP16 split) against the oracle: the batched solve directly, and the
-BEP matrix and elliptic solve built on it.  Tolerances as for the FP32 path:
-1e-5 for the AP solve, 1e-4 for results through the least squares."""
+BEP matrix and elliptic solve built on it.  Tolerance 1e-5 relative L-inf,
+as for every FP32 result."""
 import numpy as np
 import pytest
 import torch
@@ -56,7 +56,7 @@ def test_tc256_bep_matrix_and_elliptic_solve(ctx):
     Ag = A.cpu().numpy().reshape(info.ncol, info.n_gin).T
     err = np.max(np.abs(Ag - s.A), axis=0) / np.max(np.abs(s.A), axis=0)
     print(f"TC N=256 BEP max column rel err {err.max():.3e}")
-    assert err.max() < 1e-4
+    assert err.max() < 1e-5, err.max()
     X, Y, Z = O.mesh(N, lo, hi)
     f = (np.exp(-4 * (X ** 2 + Y ** 2 + Z ** 2)) * (1 + X * Y)).astype(np.float32)
     fd = torch.from_numpy(f).cuda()
@@ -67,5 +67,5 @@ def test_tc256_bep_matrix_and_elliptic_solve(ctx):
     Np = s.sets["Np"]
     e = rel(u.cpu().numpy().astype(np.float64)[Np], uo[Np])
     print(f"TC N=256 elliptic rel err {e:.3e}")
-    assert e < 1e-4
+    assert e < 1e-5, e
     abi.dpm_bep_destroy(bep)
