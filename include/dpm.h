@@ -51,6 +51,9 @@ extern "C" {
 #define DPM_PREC_FP64 1  /* FP64 SIMT DST-I, FP64 storage (comparator path) */
 #define DPM_PREC_TC32 2  /* tcgen05 DST-I contractions (3-term f16 split,
                             FP32 accumulate), FP32 storage; N = 128, 256    */
+#define DPM_PREC_FFT32 3 /* FFT-style FP32 DST-I: even/odd fold + Rader
+                            convolutions by length-128 FFTs (N + 1 = 257 is
+                            prime), three passes; FP32 storage; N = 256     */
 
 /* ---- node label bits (one uint8 per node of M^0, Definition 2.1) ------- */
 #define DPM_LBL_MPLUS 1  /* node of M^+ (strict interior of Omega)           */
@@ -155,13 +158,14 @@ int dpm_classify(dpm_ctx *ctx, const dpm_geom *geom, int N, double lo, double hi
  * Lap_h the 7-point Laplacian (eq. stencil:7-point), diagonalised by the 3D
  * DST-I with eigenvalues sigma + (4/h^2) sum_axes sin^2(pi a/(2(N+1))).
  * (The paper's L_{h,dt} = I - dt Lap_h equals dt (sigma - Lap_h), sigma = 1/dt.)
- *   q, u  device arrays [B][N][N][N]: float for DPM_PREC_FP32/TC32, double for
+ *   q, u  device arrays [B][N][N][N]: float for DPM_PREC_FP32/TC32/FFT32, double for
  *         DPM_PREC_FP64.  u may equal q (in place); otherwise they must not
  *         overlap.
  * Requires 2 <= N <= 256, h > 0, sigma >= 0, B >= 1.  DPM_PREC_TC32 requires
  * N = 128 or 256 (DPM_EUNSUPPORTED otherwise) and a 16-byte aligned q (its planes
- * are staged by bulk copies; DPM_EINVAL otherwise).  Scratch: the context's
- * workspace, grown on demand.
+ * are staged by bulk copies; DPM_EINVAL otherwise).  DPM_PREC_FFT32 requires
+ * N = 256 (N + 1 = 257 prime: Rader's algorithm) and a 16-byte aligned q.
+ * Scratch: the context's workspace, grown on demand.
  */
 int dpm_aux_solve_batched(dpm_ctx *ctx, int N, double h, double sigma, int B,
                           const void *q, void *u, int precision, cudaStream_t stream);
@@ -347,7 +351,8 @@ int dpm_profile_reset(void);
  * coefficients (3 (KZ+1)^2, term-major) then the Gamma ones (2 (KG+1)^2)) and
  * solved in the least-squares sense; each sub-domain then applies Green's
  * formula on its own grid.  precision applies per sub-domain; DPM_PREC_TC32
- * falls back to DPM_PREC_FP32 on a grid whose N has no tensor-core solver. */
+ * (DPM_PREC_FFT32) falls back to DPM_PREC_FP32 on a grid whose N has no
+ * tensor-core (FFT-style) solver. */
 typedef struct dpm_dd dpm_dd;
 typedef struct dpm_dd_pks dpm_dd_pks;
 

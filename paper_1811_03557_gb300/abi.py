@@ -19,7 +19,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "dpm.h")
 
 DPM_OK, DPM_EINVAL, DPM_ENOMEM, DPM_ETIMEOUT, DPM_ENUMERIC, DPM_EUNSUPPORTED, DPM_ECUDA = (
     0, -1, -2, -3, -4, -5, -6)
-DPM_PREC_FP32, DPM_PREC_FP64, DPM_PREC_TC32 = 0, 1, 2
+DPM_PREC_FP32, DPM_PREC_FP64, DPM_PREC_TC32, DPM_PREC_FFT32 = 0, 1, 2, 3
 DPM_LBL_MPLUS, DPM_LBL_GIN, DPM_LBL_GEX, DPM_LBL_SHELL = 1, 2, 4, 8
 
 

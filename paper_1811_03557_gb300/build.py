@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdpm.so")
-SOURCES = ["api.cu", "classify.cu", "geometry.cu", "dst_simt.cu", "dst_tc.cu", "dst_tc256.cu", "lsq.cu", "dd.cu", "dd2.cu", "ddml.cu",
+SOURCES = ["api.cu", "classify.cu", "geometry.cu", "dst_simt.cu", "dst_tc.cu", "dst_tc256.cu", "dst_fft256.cu", "lsq.cu", "dd.cu", "dd2.cu", "ddml.cu",
            "pks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -87,7 +87,7 @@ namespace {
 size_t elem_size(int prec) { return prec == DPM_PREC_FP64 ? sizeof(double) : sizeof(float); }
 
 bool prec_ok(int prec) {
-    return prec == DPM_PREC_FP32 || prec == DPM_PREC_FP64 || prec == DPM_PREC_TC32;
+    return prec == DPM_PREC_FP32 || prec == DPM_PREC_FP64 || prec == DPM_PREC_TC32 || prec == DPM_PREC_FFT32;
 }
 
 // Run B right-hand sides through the AP solver in chunks that fit the
@@ -106,11 +106,12 @@ int run_ap(int prec, ApParams p, const std::vector<ApRhs<T>> &rhs, DevBuf &work,
     size_t cb = std::max<size_t>(1, std::min<size_t>(B, kWorkCap / cube));
     size_t extra = 0;  // tensor-core solver: staged shell right-hand sides after the cubes
     if (prec == DPM_PREC_TC32) extra = tc_scratch_elems(p, (int)cb) * sizeof(float);
-    if (prec == DPM_PREC_TC32) {
-        // the tensor-core passes stage dense inputs with bulk copies (16-byte aligned)
+    if (prec == DPM_PREC_TC32 || prec == DPM_PREC_FFT32) {
+        // the tensor-core passes stage dense inputs with bulk copies, the FFT-style
+        // passes read them as float4 (both 16-byte aligned)
         for (const auto &r : rhs)
             if (reinterpret_cast<uintptr_t>(r.f) & 15) {
-                set_error("tensor-core AP solve: f must be 16-byte aligned");
+                set_error("%s AP solve: f must be 16-byte aligned", prec == DPM_PREC_TC32 ? "tensor-core" : "FFT-style");
                 return DPM_EINVAL;
             }
     }
@@ -137,11 +138,12 @@ int run_ap_dev(int prec, ApParams p, const ApRhs<T> *desc_dev, int B, DevBuf &wo
         ApParams q = p;
         q.B = std::min<int>((int)cb, B - b0);
         const ApRhs<T> *d = desc_dev + b0;
-        if (prec == DPM_PREC_TC32) {
+        if (prec == DPM_PREC_TC32 || prec == DPM_PREC_FFT32) {
             if constexpr (sizeof(T) == 4) {
-                DPM_RET(ap_solve_tc(q, d, work.as<float>(), s));
+                if (prec == DPM_PREC_TC32) DPM_RET(ap_solve_tc(q, d, work.as<float>(), s));
+                else DPM_RET(ap_solve_fft256(q, d, work.as<float>(), s));
             } else {
-                set_error("tensor-core solve is FP32-storage only");
+                set_error("tensor-core and FFT-style solves are FP32-storage only");
                 return DPM_EINVAL;
             }
         } else {
@@ -299,6 +301,10 @@ extern "C" int dpm_aux_solve_batched(dpm_ctx *ctx, int N, double h, double sigma
     }
     if (precision == DPM_PREC_TC32 && !tc_supported(N)) {
         set_error("tensor-core solve does not support N=%d", N);
+        return DPM_EUNSUPPORTED;
+    }
+    if (precision == DPM_PREC_FFT32 && !fft_supported(N)) {
+        set_error("FFT-style solve does not support N=%d", N);
         return DPM_EUNSUPPORTED;
     }
     ApParams p;
@@ -498,6 +504,10 @@ int bep_init(dpm_bep *b, dpm_ctx *ctx, const dpm_geom *geom, int N, double lo, d
     if (N > 256) { set_error("N=%d > 256 not supported by the AP solver", N); return DPM_EINVAL; }
     if (precision == DPM_PREC_TC32 && !tc_supported(N)) {
         set_error("tensor-core solve does not support N=%d", N);
+        return DPM_EUNSUPPORTED;
+    }
+    if (precision == DPM_PREC_FFT32 && !fft_supported(N)) {
+        set_error("FFT-style solve does not support N=%d", N);
         return DPM_EUNSUPPORTED;
     }
     b->ctx = ctx;
@@ -1031,6 +1041,7 @@ namespace {
 
 int dd_sub_prec(int requested, int N) {
     if (requested == DPM_PREC_TC32) return tc_supported(N) ? DPM_PREC_TC32 : DPM_PREC_FP32;
+    if (requested == DPM_PREC_FFT32) return fft_supported(N) ? DPM_PREC_FFT32 : DPM_PREC_FP32;
     return requested;
 }
 

@@ -198,6 +198,10 @@ int ap_solve_tc(const ApParams &p, const ApRhs<float> *rhs_dev, float *work, cud
 // N = 256: six out-of-place passes; work holds 2 B N^3 floats.
 int ap_solve_tc256(const ApParams &p, const ApRhs<float> *rhs_dev, float *work, cudaStream_t s);
 int tc256_status_check();
+// N = 256: FFT-style FP32 solver (fold + Rader convolutions), three passes in
+// place; work holds B N^3 floats.
+int ap_solve_fft256(const ApParams &p, const ApRhs<float> *rhs_dev, float *work, cudaStream_t s);
+bool fft_supported(int N);
 // AP workspace cubes per right-hand side (the N = 256 tensor-core solver ping-pongs).
 inline size_t ap_cubes_per_rhs(int prec, int N) { return (prec == 2 && N == 256) ? 2 : 1; }
 // floats of ApParams::scratch the tensor-core solver needs for B right-hand sides
