@@ -48,12 +48,18 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="bound on the oracle's CPU-baseline sample")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=1000,
+    ap.add_argument("--serving-requests", type=int, default=10000,
                     help="requests in the serving leg (0 skips it)")
-    ap.add_argument("--serving-rate", type=float, default=300.0, help="mean arrivals per second")
-    ap.add_argument("--serving-models", type=int, default=16)
+    ap.add_argument("--serving-rate", type=float, default=1500.0, help="mean arrivals per second")
+    ap.add_argument("--serving-models", type=int, default=64)
+    ap.add_argument("--serving-saturated-rate", type=float, default=8000.0,
+                    help="offered rate of the second, saturated serving leg (0 skips it)")
+    ap.add_argument("--serving-saturated-requests", type=int, default=3000)
     ap.add_argument("--no-aux", action="store_true", help="skip the batched aux-solve leg")
     ap.add_argument("--no-graph", action="store_true", help="host-driven steps instead of graph replay")
+    ap.add_argument("--aux-case", default=None,
+                    help="N:B:precision (fp32|tc32|fft32|fp64): time only this batched AP solve, "
+                         "--warmup then --steps calls, and print its own JSON line (profiling cases)")
     return ap.parse_args()
 
 
@@ -347,6 +353,42 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# library profile key -> kernel name in the ncu summaries
+KERNEL_OF_PROF = {"tc_plane_fwd": "k_tc_plane<0>", "tc_pencil": "k_tc_pencil", "tc_plane_inv": "k_tc_plane<1>",
+                  "fft256_plane_fwd": "k_fft_plane_fwd", "fft256_pencil": "k_fft_pencil",
+                  "fft256_plane_inv": "k_fft_plane_inv"}
+
+
+def source_sha(path, root=None):
+    import hashlib
+    with open(os.path.join(root or ROOT, path), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def profile_traffic(kernel, root=None):
+    """DRAM bytes per right-hand side of `kernel` from the tables of profiles/*.md
+    ('| kernel | DRAM bytes per right-hand side | source | source sha256 |'),
+    or None when no table has it or the kernel's source file has changed since
+    the capture (its sha256 prefix differs)."""
+    import glob
+    root = root or ROOT
+    for md in sorted(glob.glob(os.path.join(root, "profiles", "*.md"))):
+        header = False
+        for line in open(md):
+            cells = [c.strip() for c in line.strip().strip("|").split("|")]
+            if len(cells) == 4 and cells[1].startswith("DRAM bytes per right-hand side"):
+                header = True
+                continue
+            if header and len(cells) == 4 and cells[0].replace("\\", "") == kernel:
+                try:
+                    return float(cells[1]) if source_sha(cells[2], root) == cells[3] else None
+                except (OSError, ValueError):
+                    return None
+            if header and not line.startswith("|"):
+                header = False
+    return None
+
+
 def roofline(w, prec, prof, spp):
     """Roofline of the dominant AP-pass kernel (largest device time)."""
     peaks, src = measured_peaks()
@@ -388,13 +430,11 @@ def roofline(w, prec, prof, spp):
     bytes_per = per_kernel.get(name, points * 8.0)
     ach = bytes_per / (rec["ms_per_launch"] / 1e3) / 1e9
     peak = peaks.get("hbm_gbs", 6800.0)
-    # measured DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one
-    # ncu capture of the 162-column BEP batch, per right-hand side; scaled to the
-    # step's average launch (traffic grows with the number of right-hand sides)
-    measured_per_rhs = {"tc_plane_fwd": (0.037332e9 + 1.297840e9) / 162,
-                        "tc_pencil": (1.359097e9 + 1.297749e9) / 162,
-                        "tc_plane_inv": (1.106946e9 + 0.019860e9) / 162}
-    traffic = measured_per_rhs[name] * rhs_per_launch if name in measured_per_rhs else None
+    # measured DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per
+    # right-hand side from the committed ncu summary of these kernels, scaled to
+    # the step's average launch; None when the kernel's source changed since
+    per_rhs = profile_traffic(KERNEL_OF_PROF.get(name, name))
+    traffic = per_rhs * rhs_per_launch if per_rhs is not None else None
     return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s",
             "frac": ach / peak, "traffic": traffic, "bytes_per_launch": bytes_per,
             "peak_source": f"hbm_gbs ({src})"}
@@ -405,11 +445,12 @@ def run_aux(abi, torch, ctx, stream):
     in [-1, 1] (seed 0), inputs resident and larger than L2: the tensor-core
     solver at N = 128 with the 162-column batch, the FP32 SIMT solver and the
     plain FP64 solver (one right-hand side per call) at N = 256, and the N = 256
-    tensor-core solver.  Roofline: 24 bytes per grid point per FP32 solve is the
-    algorithmic minimum (three passes over a cube that does not fit on chip);
-    the three-pass (tensor-core, N = 128), five-pass (SIMT) and assemble +
-    six-pass (tensor-core, N = 256, the last pass writing u) schedules move 24,
-    40 and 56."""
+    tensor-core and FFT-style solvers.  Roofline: 24 bytes per grid point per FP32
+    solve is the algorithmic minimum (three passes over a cube that does not fit
+    on chip); the three-pass (tensor-core N = 128, FFT-style N = 256), five-pass
+    (SIMT) and assemble + six-pass (tensor-core, N = 256, the last pass writing u)
+    schedules move 24, 24, 40 and 56.  The N = 256, K = 12 BEP batch is built with
+    both N = 256 solvers."""
     from paper_1811_03557_gb300.workloads import random_rhs
     peaks, src = measured_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
@@ -450,6 +491,8 @@ def run_aux(abi, torch, ctx, stream):
     ms, v = timed(256, 16, abi.DPM_PREC_TC32, 3)
     # assemble (read f, write q), five out-of-place passes, the last one writing u
     out["tc32_N256_B16"] = leg(ms, v, 256, 16, 56)
+    ms, v = timed(256, 16, abi.DPM_PREC_FFT32, 3)
+    out["fft32_N256_B16"] = leg(ms, v, 256, 16, 24)     # plane, pencil, plane (in place)
     ms, v = timed(256, 16, abi.DPM_PREC_FP32, 3)
     out["fp32_N256_B16"] = leg(ms, v, 256, 16, 40)      # five in-place passes
     out["fp32_N256_B16"]["simt_tile"] = abi.dpm_simt_tile(256, abi.DPM_PREC_FP32, 16)
@@ -460,7 +503,13 @@ def run_aux(abi, torch, ctx, stream):
     # K = 12 (338 columns in one batched solve), sigma = 1/dt + 1, dt = 1e-4
     from paper_1811_03557_gb300.workloads import WORKLOADS
     wb = WORKLOADS["bep_ellipsoid_N256_K12"]
-    for prec, key in ((abi.DPM_PREC_TC32, "bep_build_N256_K12_tc32"),):
+    # the AP phase of the build against the algorithmic bytes of a BEP column:
+    # 16 N^3 (one cube written and read in the middle of the transform; the sparse
+    # input and the trace output are not cubes) + 8 (|gamma| + |gamma_in|)
+    ap_keys = {abi.DPM_PREC_TC32: ("tc256_rhs", "tc256_k", "tc256_j", "tc256_i", "tc256_k_out"),
+               abi.DPM_PREC_FFT32: ("fft256_rhs", "fft256_plane_fwd", "fft256_pencil", "fft256_plane_inv")}
+    for prec, key in ((abi.DPM_PREC_TC32, "bep_build_N256_K12_tc32"),
+                      (abi.DPM_PREC_FFT32, "bep_build_N256_K12_fft32")):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         bep = abi.dpm_bep_build(ctx, wb.geom, wb.N, wb.lo, wb.hi, wb.sigma, wb.K, wb.beta, prec, stream)
@@ -472,15 +521,20 @@ def run_aux(abi, torch, ctx, stream):
         torch.cuda.synchronize()
         t2 = time.perf_counter()
         abi.dpm_profile_enable(False)
-        ap_ms = sum(abi.dpm_profile_read(k)[0] for k in ("tc256_rhs", "tc256_k", "tc256_j", "tc256_i", "tc256_out"))
+        per = {k: abi.dpm_profile_read(k)[0] for k in ap_keys[prec]}
+        ap_ms = sum(per.values())
         fac_ms = sum(abi.dpm_profile_read(k)[0] for k in ("lsq_gram_syrk", "lsq_cholesky"))
         abi.dpm_profile_reset()
+        info = abi.dpm_bep_get_info(bep2)
         abi.dpm_bep_destroy(bep)
         abi.dpm_bep_destroy(bep2)
         ncol = wb.ncol
+        alg = ncol * (16.0 * wb.N ** 3 + 8.0 * (info.n_gamma + info.n_gin))
+        gbs = alg / (ap_ms / 1e3) / 1e9 if ap_ms > 0 else None
         out[key] = {"build_ms": (t2 - t1) * 1e3, "first_build_ms": (t1 - t0) * 1e3, "ap_ms": ap_ms,
-                    "factor_ms": fac_ms, "ncol": ncol,
-                    "ap_grid_pts_per_s": ncol * wb.N ** 3 / (ap_ms / 1e3) if ap_ms > 0 else None}
+                    "ap_kernels_ms": per, "factor_ms": fac_ms, "ncol": ncol,
+                    "ap_grid_pts_per_s": ncol * wb.N ** 3 / (ap_ms / 1e3) if ap_ms > 0 else None,
+                    "ap_alg_bytes": alg, "ap_hbm_gbs": gbs, "ap_frac": gbs / hbm if gbs else None}
     out["peak"] = {"hbm_gbs": hbm, "source": src}
     out["data"] = "uniform [-1, 1] q, seed 0; dense in, dense out; inputs larger than L2"
     return out
@@ -523,43 +577,90 @@ def run_e2e(abi, torch, pks, w, tdt, spp, args, stream):
 
 
 def run_serving(abi, torch, ctx, args):
-    """Serving leg: a seeded Poisson stream of elliptic solves (and a few short
-    PKS runs) over a catalog of resident factorisations drawn from the serving
-    mix (N in {32, 64, 128, 256}, K in 4..12, sigma log-uniform in [1e2, 1e5],
-    spheres and ellipsoids with radius in [0.5, 1]).  Latency is arrival ->
-    solution back in host memory (copies included)."""
+    """Serving legs: seeded Poisson streams of elliptic solves (and a few short
+    PKS runs) over one catalog of resident factorisations drawn from the
+    serving mix (N in {32, 64, 128, 256}, K in 4..12, sigma log-uniform in
+    [1e2, 1e5], spheres and ellipsoids with radius in [0.5, 1]): the stream of
+    --serving-requests at --serving-rate, then a saturated one (arrivals faster
+    than the service rate, so batches form).  Latency is arrival -> solution
+    back in host memory (copies included), split into build wait, slot wait and
+    service (host->device copy, solve, device->host copy on the device)."""
     from paper_1811_03557_gb300.serving import LibraryBackend, ServingEngine
     from paper_1811_03557_gb300.workloads import (pks_run_catalog, poly_gauss_rhs,
                                                   serving_catalog, serving_stream)
     cat = serving_catalog(0, args.serving_models)
     pcat = pks_run_catalog(1, 4)
-    reqs = serving_stream(0, args.serving_requests, args.serving_rate, len(cat), len(pcat), 0.005)
+    legs = [("stream", 0, args.serving_requests, args.serving_rate)]
+    if args.serving_saturated_rate > 0 and args.serving_saturated_requests > 0:
+        legs.append(("saturated", 7, args.serving_saturated_requests, args.serving_saturated_rate))
+    streams = {name: serving_stream(seed, n, rate, len(cat), len(pcat), 0.005) for name, seed, n, rate in legs}
     pool = {}
-    for q in reqs:
-        if q.kind == "solve" and q.rhs_seed not in pool:
-            pool[q.rhs_seed] = torch.from_numpy(poly_gauss_rhs(q.rhs_seed, cat[q.model])).pin_memory()
+    for reqs in streams.values():
+        for q in reqs:
+            if q.kind == "solve" and q.rhs_seed not in pool:
+                pool[q.rhs_seed] = torch.from_numpy(poly_gauss_rhs(q.rhs_seed, cat[q.model])).pin_memory()
     slots, batch = 4, 8
     be = LibraryBackend(ctx, slots, batch, max(m.N for m in cat))
     eng = ServingEngine(be, cat, pcat, n_slots=slots, max_batch=batch, rhs=lambda s, m: pool[s])
     t = time.perf_counter()
     warm = eng.warm()
     t_warm = time.perf_counter() - t
-    l0 = abi.dpm_launch_count()
-    rep = eng.run(reqs)
-    launches = abi.dpm_launch_count() - l0
+    out = {"catalog": len(cat), "resident_after_warm": warm, "warm_s": t_warm, "slots": slots,
+           "max_batch": batch,
+           "latency": "arrival -> solution in pinned host memory (H2D and D2H included)",
+           "precision": "f32 storage (tcgen05 3-term f16 split at N=128, FFT-style FP32 at N=256, "
+                        "SIMT FP32 otherwise), FP64 least squares"}
+    for name, seed, n, rate in legs:
+        l0 = abi.dpm_launch_count()
+        rep = eng.run(streams[name])
+        launches = abi.dpm_launch_count() - l0
+        torch.cuda.synchronize()
+        d = {k: v for k, v in rep.as_dict().items() if k != "errors"}
+        d.update(requests=n, rate_hz=rate, gpu_launches=int(launches), errors=rep.errors)
+        out[name] = d
     eng.shutdown()
     torch.cuda.synchronize()
-    out = {k: v for k, v in rep.as_dict().items() if k != "errors"}
-    out.update(requests=args.serving_requests, rate_hz=args.serving_rate, catalog=len(cat),
-               resident_after_warm=warm, warm_s=t_warm, slots=slots, max_batch=batch,
-               gpu_launches=int(launches), errors=rep.errors,
-               latency="arrival -> solution in pinned host memory (H2D and D2H included)",
-               precision="f32 storage (tcgen05 3-term f16 split at N=128, SIMT FP32 otherwise), FP64 least squares")
     return out
+
+
+def run_aux_case(args):
+    """One batched AP solve configuration alone (a small case for kernel captures)."""
+    import torch
+    from paper_1811_03557_gb300 import abi
+    from paper_1811_03557_gb300.workloads import random_rhs
+    N, B, pname = args.aux_case.split(":")
+    N, B = int(N), int(B)
+    prec = {"fp32": abi.DPM_PREC_FP32, "tc32": abi.DPM_PREC_TC32, "fft32": abi.DPM_PREC_FFT32,
+            "fp64": abi.DPM_PREC_FP64}[pname]
+    torch.cuda.set_device(0)
+    ctx = abi.dpm_ctx_create(0)
+    tdt = torch.float64 if prec == abi.DPM_PREC_FP64 else torch.float32
+    q = torch.from_numpy(random_rhs(0, B, N)).to("cuda", tdt)
+    u = torch.empty_like(q)
+    h, sigma = 2.5 / (N + 1), 1e4 + 1.0
+    stream = torch.cuda.Stream()
+    for _ in range(args.warmup):
+        abi.dpm_aux_solve_batched(ctx, N, h, sigma, B, q, u, prec, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        abi.dpm_aux_solve_batched(ctx, N, h, sigma, B, q, u, prec, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(1, args.steps)
+    peaks, _ = measured_peaks()
+    gbs = 24.0 * B * N ** 3 / (ms / 1e3) / 1e9
+    print(json.dumps({"aux_case": args.aux_case, "ms": ms, "grid_pts_per_s": B * N ** 3 / (ms / 1e3),
+                      "alg_gbs": gbs, "frac": gbs / peaks.get("hbm_gbs", 6800.0)}), flush=True)
+    abi.dpm_ctx_destroy(ctx)
 
 
 def main():
     args = parse()
+    if args.aux_case and args.impl != "reference":
+        run_aux_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

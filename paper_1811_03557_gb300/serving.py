@@ -49,9 +49,9 @@ class LibraryBackend:
 
     Every slot owns a stream, device buffers for `max_batch` right-hand sides
     and solutions of up to max_N^3 values, and a pinned host buffer the
-    solutions come back to.  Storage is FP32: N = 128 and 256 problems use the
-    tensor-core solvers (their sizes), others the FP32 SIMT solver; the least
-    squares and the extension run in FP64 as in dpm_solve.
+    solutions come back to.  Storage is FP32: N = 128 problems use the
+    tensor-core solver, N = 256 the FFT-style solver, others the FP32 SIMT
+    solver; the least squares and the extension run in FP64 as in dpm_solve.
     """
 
     def __init__(self, ctx, n_slots: int, max_batch: int, max_N: int, device: int = 0,
@@ -73,7 +73,11 @@ class LibraryBackend:
     # -- sizes ----------------------------------------------------------------
     def precision(self, model) -> int:
         a = self.abi
-        return a.DPM_PREC_TC32 if (self.tc and model.N in (128, 256)) else a.DPM_PREC_FP32
+        if self.tc and model.N == 128:
+            return a.DPM_PREC_TC32
+        if self.tc and model.N == 256:
+            return a.DPM_PREC_FFT32
+        return a.DPM_PREC_FP32
 
     @staticmethod
     def estimate_bytes(model, max_batch: int, pks: bool = False) -> int:
@@ -85,7 +89,7 @@ class LibraryBackend:
         h = (model.hi - model.lo) / (N + 1)
         ng = int(2.0 * 4.0 * np.pi * (r / h) ** 2) + 1024   # |gamma| (two layers of the surface)
         m = ng // 2 + 512                                    # |gamma_in|
-        per_rhs = 2 * cube if N == 256 else cube                 # the N = 256 TC solver ping-pongs
+        per_rhs = cube                                           # one cube per right-hand side
         build_cubes = min(ncol + 4, (8 << 30) // per_rhs)
         b = build_cubes * per_rhs + 2 * max_batch * per_rhs      # AP workspace
         b += N ** 3 + 16 * N * N + 64 * ng                   # labels, row pointers, index lists
@@ -115,24 +119,31 @@ class LibraryBackend:
     def solve(self, slot: int, handle, model, rhs: list, deliver):
         """Solve len(rhs) requests (host FP32 arrays or tensors of N^3 values) in
         one batch; deliver(i, u_host) is called for each before returning (the
-        view is reused by the slot afterwards)."""
+        view is reused by the slot afterwards).  Returns the batch's device times
+        in ms (CUDA events on the slot's stream): host->device copy, solve,
+        device->host copy."""
         torch = self.torch
         n3 = model.N ** 3
         s = self.streams[slot]
         fd, ud, oh = self.f_dev[slot], self.u_dev[slot], self.out_host[slot]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         with torch.cuda.stream(s):
+            ev[0].record(s)
             for i, f in enumerate(rhs):
                 src = f if isinstance(f, torch.Tensor) else torch.from_numpy(f)
                 fd[i, :n3].copy_(src.reshape(-1), non_blocking=True)
+            ev[1].record(s)
             self.abi.dpm_solve_batched(handle, [fd[i, :n3] for i in range(len(rhs))],
                                        [ud[i, :n3] for i in range(len(rhs))], stream=s)
+            ev[2].record(s)
             for i in range(len(rhs)):
                 oh[i, :n3].copy_(ud[i, :n3], non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(s)
-        ev.synchronize()
+            ev[3].record(s)
+        ev[3].synchronize()
         for i in range(len(rhs)):
             deliver(i, oh[i, :n3])
+        return {"h2d_ms": ev[0].elapsed_time(ev[1]), "solve_ms": ev[1].elapsed_time(ev[2]),
+                "d2h_ms": ev[2].elapsed_time(ev[3])}
 
     # -- PKS runs ---------------------------------------------------------------------
     def pks_create(self, slot: int, pm):
@@ -162,6 +173,7 @@ class _Model:
     handle: object = None
     bytes: int = 0
     last_used: float = 0.0
+    ready_at: float = 0.0        # when the factorisation last became resident
     pending: collections.deque = field(default_factory=collections.deque)
     builds: int = 0
 
@@ -190,6 +202,8 @@ class RequestRecord:
     ok: bool = False
     error: str = ""
     result: dict = field(default_factory=dict)
+    build_wait: float = 0.0      # of the queueing time: waiting for the factorisation to be built
+    gpu: dict = field(default_factory=dict)   # the batch's device times (copies, solve), ms
 
     @property
     def latency(self):
@@ -271,8 +285,7 @@ class ServingEngine:
             def deliver(i, u):
                 if self.on_result is not None:
                     self.on_result(reqs[i], u)
-            be.solve(slot, m.handle, m.spec, rhs, deliver)
-            return None
+            return be.solve(slot, m.handle, m.spec, rhs, deliver)
         if kind == "pks_create":
             return be.pks_create(slot, self.runs[payload].spec)
         if kind == "pks_step":
@@ -340,7 +353,10 @@ class ServingEngine:
                 m = self.models[key]
                 reqs = [m.pending.popleft() for _ in range(min(self.max_batch, len(m.pending)))]
                 for r in reqs:
-                    self.rec[r].dispatch, self.rec[r].batch = now, len(reqs)
+                    rec = self.rec[r]
+                    rec.dispatch, rec.batch = now, len(reqs)
+                    # the part of the wait spent on the factorisation's build
+                    rec.build_wait = max(0.0, m.ready_at - rec.arrival)
                 m.state = "busy"
                 self.inbox[slot].put(("solve", (key, reqs)))
                 self.events.append((now, "solve", (key, len(reqs))))
@@ -375,7 +391,7 @@ class ServingEngine:
                 m.pending.clear()
             else:
                 m.handle, m.bytes = res
-                m.state, m.last_used = "ready", now
+                m.state, m.last_used, m.ready_at = "ready", now, now
                 m.builds += 1
         elif kind == "solve":
             mi, reqs = payload
@@ -384,6 +400,7 @@ class ServingEngine:
             for r in reqs:
                 rec = self.rec[r]
                 rec.done, rec.ok, rec.error = now, err is None, err or ""
+                rec.gpu = dict(res) if isinstance(res, dict) else {}
                 self.n_done += 1
         elif kind == "pks_create":
             r = self.runs[payload]
@@ -512,6 +529,7 @@ class ServingReport:
     max_busy_slots: int
     peak_bytes: int
     by_N: dict
+    breakdown: dict
     errors: list
 
     @staticmethod
@@ -532,6 +550,28 @@ class ServingReport:
             by_N.setdefault(eng.models[r.model].spec.N, []).append(r.latency * 1e3)
         by_N = {str(k): {"n": len(v), "p50_ms": pct(np.array(v), 50), "p99_ms": pct(np.array(v), 99)}
                 for k, v in sorted(by_N.items())}
+        # where a solve's latency goes: queueing (waiting for the factorisation's
+        # build, then for a slot) and service (the batch's copies and solve on the
+        # device, the rest host work), for all solves and for the slowest 1 %
+        comp = {"build_wait_ms": [], "slot_wait_ms": [], "service_ms": [], "h2d_ms": [], "solve_ms": [],
+                "d2h_ms": [], "host_ms": []}
+        for r in sol:
+            q = (r.dispatch - r.arrival) * 1e3
+            bw = min(r.build_wait * 1e3, q)
+            sv = (r.done - r.dispatch) * 1e3
+            g = r.gpu
+            dev = g.get("h2d_ms", 0.0) + g.get("solve_ms", 0.0) + g.get("d2h_ms", 0.0)
+            for k, v in (("build_wait_ms", bw), ("slot_wait_ms", q - bw), ("service_ms", sv),
+                         ("h2d_ms", g.get("h2d_ms", float("nan"))), ("solve_ms", g.get("solve_ms", float("nan"))),
+                         ("d2h_ms", g.get("d2h_ms", float("nan"))), ("host_ms", sv - dev)):
+                comp[k].append(v)
+        breakdown = {}
+        if sol:
+            tail = lat >= np.percentile(lat, 99)
+            for k, v in comp.items():
+                a = np.array(v)
+                breakdown[k] = {"p50": pct(a, 50), "p99": pct(a, 99),
+                                "mean_in_p99_tail": float(np.nanmean(a[tail])) if tail.any() else float("nan")}
         return ServingReport(
             n=len(rec), ok=sum(r.ok for r in rec), failed=sum(not r.ok for r in rec),
             elapsed_s=t_end, solve_p50_ms=pct(lat, 50), solve_p99_ms=pct(lat, 99),
@@ -542,7 +582,7 @@ class ServingReport:
             mean_batch=float(np.mean([e[2][1] for e in solves])) if solves else 0.0,
             builds=sum(1 for e in eng.events if e[1] == "build"),
             evictions=sum(1 for e in eng.events if e[1] == "evict"),
-            max_busy_slots=eng.busy_max, peak_bytes=eng.peak_bytes, by_N=by_N,
+            max_busy_slots=eng.busy_max, peak_bytes=eng.peak_bytes, by_N=by_N, breakdown=breakdown,
             errors=sorted({r.error for r in rec if not r.ok})[:5])
 
     def as_dict(self):

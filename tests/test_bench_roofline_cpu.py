@@ -1,8 +1,10 @@
 """The roofline arithmetic of bench.py on a synthetic kernel profile (no GPU):
 the dominant AP pass is the one with the largest device time; achieved = its
 algorithmic bytes per launch / its time per launch; frac = achieved / peak;
-traffic = the measured DRAM bytes per right-hand side x right-hand sides per
-launch; the SIMT passes are reported against the FP32 (or FP64) ALU peak."""
+traffic = the measured DRAM bytes per right-hand side (from a committed
+profile table, only while the kernel's source is the one captured) x
+right-hand sides per launch; the SIMT passes are reported against the FP32 (or
+FP64) ALU peak."""
 import os
 import sys
 
@@ -21,6 +23,7 @@ def rec(ms_total, launches):
 
 def test_tensor_core_roofline_picks_the_dominant_pass(monkeypatch):
     monkeypatch.setattr(bench, "measured_peaks", lambda: ({"hbm_gbs": 7000.0}, "measured"))
+    monkeypatch.setattr(bench, "profile_traffic", lambda k, root=None: 16.4e6 if k == "k_tc_pencil" else None)
     w = WORKLOADS["pks_sphere_N128_K8"]
     prof = {"tc_plane_fwd": rec(6.8, 20), "tc_pencil": rec(7.2, 20), "tc_plane_inv": rec(7.0, 20),
             "lsq_cholesky": rec(9.9, 10)}  # not an AP pass: never the roofline kernel
@@ -33,7 +36,24 @@ def test_tensor_core_roofline_picks_the_dominant_pass(monkeypatch):
     assert r["achieved"] == pytest.approx(ach)
     assert r["peak"] == 7000.0 and r["frac"] == pytest.approx(ach / 7000.0)
     rhs_per_launch = ((w.ncol + 2) + 2) / 2
-    assert r["traffic"] == pytest.approx((1.359097e9 + 1.297749e9) / 162 * rhs_per_launch)
+    assert r["traffic"] == pytest.approx(16.4e6 * rhs_per_launch)
+
+
+def test_profile_traffic_table_and_staleness(tmp_path):
+    src = "paper_1811_03557_gb300/csrc/dst_tc.cu"
+    (tmp_path / "paper_1811_03557_gb300" / "csrc").mkdir(parents=True)
+    (tmp_path / src).write_text("kernel source v1\n")
+    (tmp_path / "profiles").mkdir()
+    sha = bench.source_sha(src, str(tmp_path))
+    (tmp_path / "profiles" / "k.md").write_text(
+        "# capture\n\n| kernel | DRAM bytes per right-hand side | source | source sha256 |\n"
+        "|---|---|---|---|\n"
+        f"| k_tc_plane\\<1> | 6954321 | {src} | {sha} |\n| k_tc_pencil | 16407091 | {src} | {sha} |\n\ntext\n")
+    assert bench.profile_traffic("k_tc_pencil", str(tmp_path)) == 16407091.0
+    assert bench.profile_traffic("k_tc_plane<1>", str(tmp_path)) == 6954321.0
+    assert bench.profile_traffic("k_fft_pencil", str(tmp_path)) is None
+    (tmp_path / src).write_text("kernel source v2\n")          # the kernel changed: stale
+    assert bench.profile_traffic("k_tc_pencil", str(tmp_path)) is None
 
 
 def test_simt_roofline_is_alu_bound(monkeypatch):

@@ -79,6 +79,7 @@ class FakeBackend:
         self.log.append(("solve", self._key(m), len(rhs)))
         for i, f in enumerate(rhs):
             deliver(i, f * 2.0)
+        return {"h2d_ms": 0.1, "solve_ms": self.solve_s * 1e3, "d2h_ms": 0.1}
 
     def pks_create(self, slot, pm):
         h = self._alloc(pm)
@@ -254,3 +255,25 @@ def test_poly_gauss_rhs_matches_pointwise_definition():
                 for d in range(4))
         assert abs(f[i, j, k] - p * np.exp(-w * (x * x + y * y + z * z))) < 1e-12
     assert np.all(c[np.add.outer(np.add.outer(np.arange(4), np.arange(4)), np.arange(4)) > 3] == 0)
+
+
+def test_latency_breakdown_splits_queueing_and_service():
+    """A cold factorisation: the first requests wait for its build, later ones
+    only for a slot; service holds the backend's device times; for every request
+    build wait + slot wait + service = latency."""
+    cat = _catalog(1)
+    be = FakeBackend(_sizes(cat, 100), build_s=0.05, solve_s=0.01)
+    eng = ServingEngine(be, cat, n_slots=1, max_batch=2, hbm_budget=1000, rhs=lambda s, m: np.ones(4))
+    reqs = _reqs(np.linspace(0, 0.022, 12), [0] * 12)
+    rep = eng.run(reqs)
+    assert rep.ok == 12
+    b = rep.breakdown
+    assert set(b) == {"build_wait_ms", "slot_wait_ms", "service_ms", "h2d_ms", "solve_ms", "d2h_ms", "host_ms"}
+    assert b["build_wait_ms"]["p99"] > 30.0          # the first requests waited for the 50 ms build
+    assert b["solve_ms"]["p50"] == pytest.approx(10.0)
+    assert b["service_ms"]["p50"] >= 10.0
+    for r in eng.rec:
+        q = r.dispatch - r.arrival
+        assert 0.0 <= r.build_wait <= q + 1e-9
+        assert r.latency == pytest.approx(q + (r.done - r.dispatch))
+
