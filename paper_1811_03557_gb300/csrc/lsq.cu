@@ -878,6 +878,23 @@ __global__ void __launch_bounds__(kTriT) k_trisolve32(int n, int nr, const float
 
 }  // namespace
 
+// The dynamic shared-memory limits of the least-squares kernels, raised to the
+// per-CTA maximum once per device.  (Setting each launch's own size before the
+// launch raced between host threads that share a device: one thread could
+// lower the limit between another's set and its launch.)  The limit bounds a
+// launch's request; occupancy follows the size each launch asks for.
+static int lsq_configure() {
+    static PerDeviceOnce once;
+    return once.run([] {
+        const int v = 227 * 1024;
+        DPM_CUDA(cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+        DPM_CUDA(cudaFuncSetAttribute(k_cholesky32, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+        DPM_CUDA(cudaFuncSetAttribute(k_rinv, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+        DPM_CUDA(cudaFuncSetAttribute(k_trisolve32, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+        return (int)DPM_OK;
+    });
+}
+
 static int householder_factor(LsqFactor &f, double *A0, double *w, double *rdiag, double *R,
                               int *status, cudaStream_t s) {
     const int m = f.m, n = f.n;
@@ -961,7 +978,7 @@ static int cholesky_factor(LsqFactor &f, const double *A0, double *R, int *statu
     }
     const size_t smem = nn * sizeof(double);
     const int use_smem = smem <= 200 * 1024 ? 1 : 0;
-    if (use_smem) DPM_CUDA(cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (use_smem) DPM_RET(lsq_configure());
     {
         DPM_PROF("lsq_cholesky", s);
         k_cholesky<<<1, 1024, use_smem ? smem : 0, s>>>(n, G, R, W, use_smem, status);
@@ -1028,7 +1045,7 @@ static int mixed_factor(LsqFactor &f, const double *A0, double *R, double *Rinv,
     *rinv_done = 1;
     f.rinv32 = true;
     f.A32 = Af;
-    DPM_CUDA(cudaFuncSetAttribute(k_cholesky32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    DPM_RET(lsq_configure());
     {
         DPM_PROF("lsq_cholesky", s);
         k_cholesky32<<<1, kCholT, smem, s>>>(n, reinterpret_cast<const float *>(G),
@@ -1106,8 +1123,7 @@ static int lsq_factor_impl(LsqFactor &f, bool sync, cudaStream_t s) {
         const int warps = (int)std::max<size_t>(1, std::min<size_t>(4, (200 * 1024) / per));
         const size_t smem = per * warps;
         if (smem > 227 * 1024) { set_error("least squares: n = %d too large for R^-1", n); return DPM_EINVAL; }
-        if (smem > 48 * 1024)
-            DPM_CUDA(cudaFuncSetAttribute(k_rinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (smem > 48 * 1024) DPM_RET(lsq_configure());
         k_rinv<<<(n + warps - 1) / warps, 32 * warps, smem, s>>>(n, R, Rinv, status);
         DPM_LAUNCHED();
     }
@@ -1193,8 +1209,7 @@ int lsq_apply(const LsqFactor &f, const T *b, int ldb, double *C, int nr, cudaSt
     // z = R^{-T} D y, C (+)= D R^{-1} z
     const size_t tsm = trisolve_smem(n, nr);
     const bool fused = fast32 && f.rinv32 && tsm <= 227 * 1024;
-    if (fused && tsm > 48 * 1024)
-        DPM_CUDA(cudaFuncSetAttribute(k_trisolve32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+    if (fused && tsm > 48 * 1024) DPM_RET(lsq_configure());
     auto precondition = [&](int accumulate) -> int {
         if (fused) {
             k_trisolve32<<<1, kTriT, tsm, s>>>(n, nr, reinterpret_cast<const float *>(Rinv), ypart, S, dsc, C,
