@@ -14,10 +14,14 @@ namespace dpm {
 void set_error(const char *fmt, ...);
 const char *cuda_err(cudaError_t e);
 
+// A failed runtime call also records its error as the thread's last error;
+// it is cleared here (a non-sticky error) so that the next launch check does
+// not report it again.
 #define DPM_CUDA(call)                                                                  \
     do {                                                                                \
         cudaError_t e_ = (call);                                                        \
         if (e_ != cudaSuccess) {                                                        \
+            (void)cudaGetLastError();                                                   \
             dpm::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),      \
                            __FILE__, __LINE__);                                         \
             return e_ == cudaErrorMemoryAllocation ? DPM_ENOMEM : DPM_ECUDA;            \
@@ -70,6 +74,19 @@ struct PerDeviceOnce {
         return r;
     }
 };
+
+// Raise `func`'s dynamic shared-memory limit to the most the current device
+// allows a CTA beside the kernel's own static shared memory.
+inline int raise_dynamic_smem_limit(const void *func) {
+    int dev = 0, optin = 0;
+    DPM_CUDA(cudaGetDevice(&dev));
+    DPM_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa{};
+    DPM_CUDA(cudaFuncGetAttributes(&fa, func));
+    DPM_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  optin - (int)fa.sharedSizeBytes));
+    return DPM_OK;
+}
 
 // Owning device buffer.
 struct DevBuf {

@@ -879,18 +879,17 @@ __global__ void __launch_bounds__(kTriT) k_trisolve32(int n, int nr, const float
 }  // namespace
 
 // The dynamic shared-memory limits of the least-squares kernels, raised to the
-// per-CTA maximum once per device.  (Setting each launch's own size before the
+// per-CTA maximum (less each kernel's static shared memory) once per device.  (Setting each launch's own size before the
 // launch raced between host threads that share a device: one thread could
 // lower the limit between another's set and its launch.)  The limit bounds a
 // launch's request; occupancy follows the size each launch asks for.
 static int lsq_configure() {
     static PerDeviceOnce once;
     return once.run([] {
-        const int v = 227 * 1024;
-        DPM_CUDA(cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
-        DPM_CUDA(cudaFuncSetAttribute(k_cholesky32, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
-        DPM_CUDA(cudaFuncSetAttribute(k_rinv, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
-        DPM_CUDA(cudaFuncSetAttribute(k_trisolve32, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+        DPM_RET(raise_dynamic_smem_limit(reinterpret_cast<const void *>(k_cholesky)));
+        DPM_RET(raise_dynamic_smem_limit(reinterpret_cast<const void *>(k_cholesky32)));
+        DPM_RET(raise_dynamic_smem_limit(reinterpret_cast<const void *>(k_rinv)));
+        DPM_RET(raise_dynamic_smem_limit(reinterpret_cast<const void *>(k_trisolve32)));
         return (int)DPM_OK;
     });
 }
