@@ -350,9 +350,10 @@ int dpm_profile_reset(void);
  * are stacked (rows: gamma_in of Omega_1, then of Omega_2; columns: the Z
  * coefficients (3 (KZ+1)^2, term-major) then the Gamma ones (2 (KG+1)^2)) and
  * solved in the least-squares sense; each sub-domain then applies Green's
- * formula on its own grid.  precision applies per sub-domain; DPM_PREC_TC32
- * (DPM_PREC_FFT32) falls back to DPM_PREC_FP32 on a grid whose N has no
- * tensor-core (FFT-style) solver. */
+ * formula on its own grid.  precision applies per sub-domain: DPM_PREC_TC32
+ * falls back to DPM_PREC_FP32 on a grid whose N has no tensor-core solver;
+ * DPM_PREC_FFT32 uses the FFT-style solver where N has one, else the
+ * tensor-core solver where N has one, else DPM_PREC_FP32. */
 typedef struct dpm_dd dpm_dd;
 typedef struct dpm_dd_pks dpm_dd_pks;
 
@@ -452,6 +453,11 @@ typedef struct {
     double lo2, hi2, origin2[3];  /* Omega_2 (outside Z) */
     int MZ, MG;
     int precision;
+    int gamma_series;  /* unknown series on Gamma: 2 (0 = default) for the 3-term
+                          extension u + d g_N + (d^2/2) d2u/dn2, 1 for the 2-term
+                          extension u + d g_N (Section 4 uses it on the boundary
+                          for Test (B); it stays well conditioned with MG beyond
+                          what the 3-term one tolerates) */
 } dpm_dd2_params;
 
 typedef struct {

@@ -864,7 +864,8 @@ class DD2Subdomain:
 
     def value(self, k, surf, MZ, MG):
         """Value of unknown k's basis density at every node of gamma_l as the
-        given surface's series (1 = Z, 0 = Gamma) would give it."""
+        given surface's series (1 = Z, 0 = Gamma) would give it.  Gamma unknowns
+        k - 3 MZ = t MG + nu: t = 0 the series of u, t = 1 that of d^2u/dn^2."""
         if k < 3 * MZ:
             if surf == 0:
                 return np.zeros(len(self.gamma_idx))
@@ -888,12 +889,16 @@ class DD2Subdomain:
 class DD2Setup:
     """Steps 1-2 of Case 2: both sub-domains, the stacked reduced BEPs
     (eq. reduced_DD2_BEP, l = 1, 2) over the shared Z and Gamma series, and the
-    QR decomposition."""
+    QR decomposition.  gamma_series: the unknown series on Gamma, 2 for the
+    3-term extension u + d g_N + (d^2/2) d^2u/dn^2, 1 for the 2-term extension
+    u + d g_N that the paper uses on the boundary for Test (B) (Section 4, "Basis
+    functions, extension operators and BEPs")."""
 
     def __init__(self, center, R, r_z, z_off, N1, lo1, hi1, origin1, N2, lo2, hi2, origin2, MZ, MG, sigma,
-                 build_bep=True):
+                 build_bep=True, gamma_series=2):
         self.R, self.r_z, self.z_off, self.MZ, self.MG, self.sigma = R, r_z, z_off, MZ, MG, sigma
-        self.ncol = 3 * MZ + 2 * MG
+        self.gamma_series = gamma_series
+        self.ncol = 3 * MZ + gamma_series * MG
         # the sphere's centre in each sub-domain's local frame
         c1 = np.asarray(center, dtype=np.float64) - np.asarray(origin1, dtype=np.float64)
         c2 = np.asarray(center, dtype=np.float64) - np.asarray(origin2, dtype=np.float64)
@@ -1197,10 +1202,11 @@ class DD2PKSState:
     (wedge rows duplicated), effective densities clamped at 0."""
 
     def __init__(self, center, R, r_z, z_off, N1, lo1, hi1, origin1, N2, lo2, hi2, origin2, MZ, MG, chi,
-                 dt_max, rho0, c0, dt_mode="cfl", clamp=True):
+                 dt_max, rho0, c0, dt_mode="cfl", clamp=True, gamma_series=2):
         self.args = (center, R, r_z, z_off, N1, lo1, hi1, origin1, N2, lo2, hi2, origin2, MZ, MG)
+        self.gamma_series = gamma_series
         self.chi, self.dt_max, self.dt_mode, self.clamp = chi, dt_max, dt_mode, clamp
-        base = DD2Setup(*self.args, 1.0 / dt_max, build_bep=False)
+        base = DD2Setup(*self.args, 1.0 / dt_max, build_bep=False, gamma_series=gamma_series)
         self.sub = base.sub
         self.setup, self.dt, self.t = None, None, 0.0
         self.rho, self.c = [], []
@@ -1228,7 +1234,7 @@ class DD2PKSState:
     def step(self):
         dt = self.choose_dt()
         if self.setup is None or dt != self.dt:
-            self.setup = DD2Setup(*self.args, 1.0 / dt)
+            self.setup = DD2Setup(*self.args, 1.0 / dt, gamma_series=self.gamma_series)
         self.dt = dt
         S = self.setup
         rhs = [pks_rhs(r, c, sd.sets, sd.h, self.chi, dt) for r, c, sd in zip(self.rho, self.c, S.sub)]

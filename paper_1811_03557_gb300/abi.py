@@ -75,7 +75,7 @@ class dpm_dd2_params(C.Structure):
     _fields_ = [("center", C.c_double * 3), ("R", C.c_double), ("rz", C.c_double), ("zoff", C.c_double),
                 ("N1", C.c_int), ("lo1", C.c_double), ("hi1", C.c_double), ("origin1", C.c_double * 3),
                 ("N2", C.c_int), ("lo2", C.c_double), ("hi2", C.c_double), ("origin2", C.c_double * 3),
-                ("MZ", C.c_int), ("MG", C.c_int), ("precision", C.c_int)]
+                ("MZ", C.c_int), ("MG", C.c_int), ("precision", C.c_int), ("gamma_series", C.c_int)]
 
 
 class dpm_dd2_info(C.Structure):
@@ -458,13 +458,13 @@ def dpm_profile_reset():
 
 # ---- domain decomposition, Case 2 (interface meeting Gamma) -------------------------
 def dd2_params(center, R, rz, zoff, N1, lo1, hi1, origin1, N2, lo2, hi2, origin2, MZ, MG,
-               precision=DPM_PREC_FP32) -> dpm_dd2_params:
+               precision=DPM_PREC_FP32, gamma_series=2) -> dpm_dd2_params:
     p = dpm_dd2_params()
     for t in range(3):
         p.center[t], p.origin1[t], p.origin2[t] = center[t], origin1[t], origin2[t]
     p.R, p.rz, p.zoff = R, rz, zoff
     p.N1, p.lo1, p.hi1, p.N2, p.lo2, p.hi2 = N1, lo1, hi1, N2, lo2, hi2
-    p.MZ, p.MG, p.precision = MZ, MG, precision
+    p.MZ, p.MG, p.precision, p.gamma_series = MZ, MG, precision, gamma_series
     return p
 
 

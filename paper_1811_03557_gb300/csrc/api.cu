@@ -1041,7 +1041,8 @@ namespace {
 
 int dd_sub_prec(int requested, int N) {
     if (requested == DPM_PREC_TC32) return tc_supported(N) ? DPM_PREC_TC32 : DPM_PREC_FP32;
-    if (requested == DPM_PREC_FFT32) return fft_supported(N) ? DPM_PREC_FFT32 : DPM_PREC_FP32;
+    if (requested == DPM_PREC_FFT32)
+        return fft_supported(N) ? DPM_PREC_FFT32 : tc_supported(N) ? DPM_PREC_TC32 : DPM_PREC_FP32;
     return requested;
 }
 
@@ -1498,6 +1499,9 @@ ApParams dd2_ap(const DD2Sub &sd, double sigma) {
     return p;
 }
 
+// Unknown series on Gamma: 2 (u and d^2u/dn^2, the default) or 1 (u only).
+int dd2_gamma_series(const dpm_dd2_params &P) { return P.gamma_series == 1 ? 1 : 2; }
+
 int dd2_check(const dpm_dd2_params *P) {
     if (!P) { set_error("params is NULL"); return DPM_EINVAL; }
     if (!(P->R > 0 && P->rz > 0)) { set_error("need R > 0, rz > 0"); return DPM_EINVAL; }
@@ -1510,6 +1514,10 @@ int dd2_check(const dpm_dd2_params *P) {
         set_error("MZ in [1, 64], MG in [1, 1024]");
         return DPM_EINVAL;
     }
+    if (P->gamma_series < 0 || P->gamma_series > 2) {
+        set_error("gamma_series must be 0 (default: 2), 1 or 2 (got %d)", P->gamma_series);
+        return DPM_EINVAL;
+    }
     if (!prec_ok(P->precision)) { set_error("unknown precision %d", P->precision); return DPM_EINVAL; }
     if (P->N1 > 256 || P->N2 > 256) { set_error("N1, N2 <= 256"); return DPM_EINVAL; }
     return DPM_OK;
@@ -1520,7 +1528,7 @@ template <class T> int dd2_init(dpm_dd2 *d, dpm_ctx *ctx, const dpm_dd2_params &
     d->prm = P;
     d->storage = P.precision == DPM_PREC_FP64 ? DPM_PREC_FP64 : DPM_PREC_FP32;
     const int MZ = P.MZ, MG = P.MG;
-    d->ncol = 3 * MZ + 2 * MG;
+    d->ncol = 3 * MZ + dd2_gamma_series(P) * MG;
     for (int l = 0; l < 2; ++l) {
         DD2Sub &sd = d->sub[l];
         const double *org = l == 0 ? P.origin1 : P.origin2;
@@ -1599,7 +1607,7 @@ template <class T> int dd2_init(dpm_dd2 *d, dpm_ctx *ctx, const dpm_dd2_params &
         }
         DPM_RET(sd.psi.alloc(sizeof(T) * d->ncol * n1));
         DPM_RET(sd.own.alloc(sizeof(double) * d->ncol * m1));
-        DPM_RET(dd2_columns<T>(n, sd.n_rows, MZ, MG, sd.flags.as<uint8_t>(), sd.dG.as<double>(), sd.dZ.as<double>(),
+        DPM_RET(dd2_columns<T>(n, sd.n_rows, MZ, MG, dd2_gamma_series(P), sd.flags.as<uint8_t>(), sd.dG.as<double>(), sd.dZ.as<double>(),
                                sd.YG.as<double>(), sd.YZ.as<double>(), sd.row_e.as<int>(), sd.row_s.as<uint8_t>(),
                                sd.psi.as<T>(), sd.own.as<double>(), s));
         DPM_RET(sd.trace.alloc(sizeof(T) * (d->ncol + 4) * std::max<int64_t>(g, 1)));
@@ -1677,7 +1685,7 @@ int dd2_solve(dpm_dd2 *d, const void *f1v, const void *f2v, const double *gn1, c
         DD2Sub &sd = d->sub[l];
         const int64_t n = sd.gi.n_gamma;
         T *dn = sd.dens.as<T>();
-        DPM_RET(dd2_extend<T>(n, d->prm.MZ, d->prm.MG, sd.flags.as<uint8_t>(), sd.dG.as<double>(), sd.dZ.as<double>(),
+        DPM_RET(dd2_extend<T>(n, d->prm.MZ, d->prm.MG, dd2_gamma_series(d->prm), sd.flags.as<uint8_t>(), sd.dG.as<double>(), sd.dZ.as<double>(),
                               sd.YG.as<double>(), sd.YZ.as<double>(), C, d->ncol, gn[l], dn, (int)n, 1, 0, s));
         std::vector<ApRhs<T>> gr = {{f[l], dn, u[l], nullptr, 0, 0}};
         DPM_RET(run_ap<T>(sd.prec, dd2_ap(sd, d->sigma), gr, sd.work, sd.desc, s));
@@ -1853,7 +1861,7 @@ template <class T> int dd2_pks_step(dpm_dd2_pks *k, cudaStream_t s) {
         DD2Sub &sd = d->sub[l];
         const int64_t n = sd.gi.n_gamma;
         T *dn = sd.dens.as<T>();
-        DPM_RET(dd2_extend<T>(n, d->prm.MZ, d->prm.MG, sd.flags.as<uint8_t>(), sd.dG.as<double>(), sd.dZ.as<double>(),
+        DPM_RET(dd2_extend<T>(n, d->prm.MZ, d->prm.MG, dd2_gamma_series(d->prm), sd.flags.as<uint8_t>(), sd.dG.as<double>(), sd.dZ.as<double>(),
                               sd.YG.as<double>(), sd.YZ.as<double>(), C, d->ncol, nullptr, dn, (int)n, 2, k->clamp, s));
         g[l] = {{sd.frho.as<T>(), dn, sd.rho.as<T>(), nullptr, 0, 0},
                 {sd.fc.as<T>(), dn + n, sd.c.as<T>(), nullptr, 0, 0}};

@@ -8,7 +8,8 @@
 // gamma_in gives one BEP row per surface (eq. reduced_DD2_BEP).  Unknown k:
 // k < 3 MZ is term t = k / MZ, harmonic nu = k % MZ of the Z series (value
 // {1, s, s^2/2}[t] Y_nu(cos theta_Z), s = |x - c_Z| - rz); else term
-// t = (k - 3 MZ) / MG of the Gamma series ({1, d^2/2}[t] Y_nu(cos theta_G),
+// t = (k - 3 MZ) / MG of the Gamma series ({1, d^2/2}[t] Y_nu(cos theta_G); t = 0 only
+// with one Gamma series, the 2-term extension u + d g_N,
 // d = |x - c| - R), with the zonal harmonics Y_nu = sqrt((2 nu + 1)/(4 pi)) P_nu.
 // On Z the argument of P_nu is cos theta_Z mapped from the range that the part
 // of Z inside Omega spans to [-1, 1]: the same polynomials of degree < MZ in
@@ -160,7 +161,7 @@ __global__ void k_dd2_neumann(int n, const uint8_t *flags, const double *dG, con
 // node, FP64 sums over the harmonics of each series it carries, + d g_N on
 // Gamma values when gn is given, the wedge mean, optional clamp at 0.
 template <class T>
-__global__ void k_dd2_extend(int n, int MZ, int MG, const uint8_t *flags, const double *dG, const double *dZ,
+__global__ void k_dd2_extend(int n, int MZ, int MG, int GS, const uint8_t *flags, const double *dG, const double *dZ,
                              const double *YG, const double *YZ, const double *C, int ldc, const double *gn,
                              T *dens, int ldd, int nr, int clamp) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -177,7 +178,7 @@ __global__ void k_dd2_extend(int n, int MZ, int MG, const uint8_t *flags, const 
                 sz += (cq[nu] + s * cq[MZ + nu] + 0.5 * s * s * cq[2 * MZ + nu]) * yz[nu];
         if (f & 1)
             for (int nu = lane; nu < MG; nu += 32)
-                sg += (cq[3 * MZ + nu] + 0.5 * d * d * cq[3 * MZ + MG + nu]) * yg[nu];
+                sg += (cq[3 * MZ + nu] + (GS == 2 ? 0.5 * d * d * cq[3 * MZ + MG + nu] : 0.0)) * yg[nu];
         for (int o = 16; o > 0; o >>= 1) {
             sz += __shfl_xor_sync(0xffffffffu, sz, o);
             sg += __shfl_xor_sync(0xffffffffu, sg, o);
@@ -225,10 +226,10 @@ int dd2_zonal(int64_t n, int M, const double *x, double a, double b, double *Y, 
 }
 
 template <class T>
-int dd2_columns(int64_t n, int64_t m, int MZ, int MG, const uint8_t *flags, const double *dG,
+int dd2_columns(int64_t n, int64_t m, int MZ, int MG, int GS, const uint8_t *flags, const double *dG,
                 const double *dZ, const double *YG, const double *YZ, const int *row_e, const uint8_t *row_s,
                 T *psi, double *own, cudaStream_t s) {
-    const int ncol = 3 * MZ + 2 * MG;
+    const int ncol = 3 * MZ + GS * MG;
     if (n > 0) {
         k_dd2_psi<T><<<dim3(blocks1(n, 256), ncol), 256, 0, s>>>((int)n, MZ, MG, flags, dG, dZ, YG, YZ, psi);
         DPM_LAUNCHED();
@@ -270,11 +271,11 @@ int dd2_neumann(int64_t n, const uint8_t *flags, const double *dG, const double 
 }
 
 template <class T>
-int dd2_extend(int64_t n, int MZ, int MG, const uint8_t *flags, const double *dG, const double *dZ,
+int dd2_extend(int64_t n, int MZ, int MG, int GS, const uint8_t *flags, const double *dG, const double *dZ,
                const double *YG, const double *YZ, const double *C, int ldc, const double *gn, T *dens,
                int ldd, int nr, int clamp, cudaStream_t s) {
     if (n == 0) return DPM_OK;
-    k_dd2_extend<T><<<blocks1(n * 32, 256), 256, 0, s>>>((int)n, MZ, MG, flags, dG, dZ, YG, YZ, C, ldc, gn,
+    k_dd2_extend<T><<<blocks1(n * 32, 256), 256, 0, s>>>((int)n, MZ, MG, GS, flags, dG, dZ, YG, YZ, C, ldc, gn,
                                                          dens, ldd, nr, clamp);
     DPM_LAUNCHED();
     return DPM_OK;
@@ -289,16 +290,16 @@ int dd2_init_foot(int64_t n, const uint8_t *flags, const double *footG, const do
 }
 
 #define DD2_INST(T)                                                                                        \
-    template int dd2_columns<T>(int64_t, int64_t, int, int, const uint8_t *, const double *, const double *, \
-                                const double *, const double *, const int *, const uint8_t *, T *, double *, \
-                                cudaStream_t);                                                             \
+    template int dd2_columns<T>(int64_t, int64_t, int, int, int, const uint8_t *, const double *,           \
+                                const double *, const double *, const double *, const int *, const uint8_t *, \
+                                T *, double *, cudaStream_t);                                              \
     template int dd2_assemble<T>(int64_t, int64_t, int, const double *, const T *, int64_t, const int *,     \
                                  const double *, const T *, int64_t, const int *, double *, cudaStream_t);  \
     template int dd2_rhs<T>(int64_t, const int *, const int *, const uint8_t *, const T *, const double *,  \
                             const T *, T *, cudaStream_t);                                                 \
     template int dd2_neumann<T>(int64_t, const uint8_t *, const double *, const double *, double *, T *,    \
                                 cudaStream_t);                                                             \
-    template int dd2_extend<T>(int64_t, int, int, const uint8_t *, const double *, const double *,          \
+    template int dd2_extend<T>(int64_t, int, int, int, const uint8_t *, const double *, const double *,     \
                                const double *, const double *, const double *, int, const double *, T *,   \
                                int, int, int, cudaStream_t);
 DD2_INST(float)

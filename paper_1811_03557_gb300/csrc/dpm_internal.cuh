@@ -285,7 +285,7 @@ int dd2_split(const GridIndex &gi, const uint8_t *lab_o, const uint8_t *lab_b, c
               double *cosZ, double *footG, double *footZ, cudaStream_t s);
 int dd2_zonal(int64_t n, int M, const double *x, double a, double b, double *Y, cudaStream_t s);
 template <class T>
-int dd2_columns(int64_t n, int64_t m, int MZ, int MG, const uint8_t *flags, const double *dG,
+int dd2_columns(int64_t n, int64_t m, int MZ, int MG, int GS, const uint8_t *flags, const double *dG,
                 const double *dZ, const double *YG, const double *YZ, const int *row_e, const uint8_t *row_s,
                 T *psi, double *own, cudaStream_t s);
 template <class T>
@@ -299,7 +299,7 @@ template <class T>
 int dd2_neumann(int64_t n, const uint8_t *flags, const double *dG, const double *gn, double *vG, T *veff,
                 cudaStream_t s);
 template <class T>
-int dd2_extend(int64_t n, int MZ, int MG, const uint8_t *flags, const double *dG, const double *dZ,
+int dd2_extend(int64_t n, int MZ, int MG, int GS, const uint8_t *flags, const double *dG, const double *dZ,
                const double *YG, const double *YZ, const double *C, int ldc, const double *gn, T *dens,
                int ldd, int nr, int clamp, cudaStream_t s);
 int dd2_init_foot(int64_t n, const uint8_t *flags, const double *footG, const double *footZ, double *foot,

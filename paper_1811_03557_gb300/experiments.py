@@ -161,7 +161,7 @@ def boxes_test_b(N1: int, N2: int, R: float = 0.5, r1: float = 0.25):
 
 def run_test_b_dd(ctx, N1: int = 128, N2: int = 128, MZ: int = 20, MG: int = 150, precision=None,
                   stop_jump: float = 1000.0, T: float = 0.1, max_steps: int = 200000, record_every: int = 50,
-                  stream=None):
+                  stream=None, gamma_series: int = 1):
     """Test (B) of Section 4 with the domain decomposition of Case 2: the sphere
     r < 0.5 split by the sphere Z of radius 0.25 about the north pole into the
     lens Omega_1 (N1 grid) and the rest (N2 grid); rho0 = 2000 exp(-100 |x -
@@ -169,7 +169,8 @@ def run_test_b_dd(ctx, N1: int = 128, N2: int = 128, MZ: int = 20, MG: int = 150
     Gamma (2-term extension there); dt = 0.5 min(h1, h2)^2 capped by the CFL
     bound of both grids, the coupled BEP rebuilt whenever dt decreases; stop
     once ||rho||_inf changes by more than stop_jump between two steps (the
-    paper's termination rule) or at time T."""
+    paper's termination rule) or at time T.  gamma_series = 1: the 2-term
+    extension u + d g_N on Gamma, as the paper runs Test (B); 2: the 3-term one."""
     import torch
 
     from . import abi
@@ -178,7 +179,8 @@ def run_test_b_dd(ctx, N1: int = 128, N2: int = 128, MZ: int = 20, MG: int = 150
     if precision is None:
         precision = abi.DPM_PREC_TC32
     (lo1, hi1, o1, h1), (lo2, hi2, o2, h2) = boxes_test_b(N1, N2)
-    P = abi.dd2_params((0.0, 0.0, 0.0), 0.5, 0.25, 0.5, N1, lo1, hi1, o1, N2, lo2, hi2, o2, MZ, MG, precision)
+    P = abi.dd2_params((0.0, 0.0, 0.0), 0.5, 0.25, 0.5, N1, lo1, hi1, o1, N2, lo2, hi2, o2, MZ, MG, precision,
+                       gamma_series=gamma_series)
     h = min(h1, h2)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -208,7 +210,8 @@ def run_test_b_dd(ctx, N1: int = 128, N2: int = 128, MZ: int = 20, MG: int = 150
         torch.cuda.synchronize()
         abi.dpm_dd2_pks_destroy(pk)
     wall = time.perf_counter() - t0
-    return {"N1": N1, "N2": N2, "h1": h1, "h2": h2, "MZ": MZ, "MG": MG, "precision": precision,
+    return {"N1": N1, "N2": N2, "h1": h1, "h2": h2, "MZ": MZ, "MG": MG, "gamma_series": gamma_series,
+            "precision": precision,
             "steps": series[-1]["step"] if series else 0, "rebuilds": rebuilds, "stopped": stopped,
             "setup_s": t_setup, "wall_s": wall, "last": series[-1] if series else None, "series": series}
 
@@ -405,6 +408,10 @@ def main(argv=None):
                     help="the uneven-box layered decomposition (ball N=192 + 7 shells), grouped vs separate")
     ap.add_argument("--test-b", default="",
                     help="Test (B) with the Case 2 decomposition: N1/N2/MZ/MG, e.g. 128/128/20/150")
+    ap.add_argument("--gamma-series", type=int, default=1,
+                    help="Test (B): unknown series on Gamma, 1 (the paper's 2-term extension) or 2")
+    ap.add_argument("--precision", choices=["tc32", "fft32", "fp32", "fp64"], default="tc32",
+                    help="Test (B): AP solver (fft32: FFT-style at N = 256, tensor cores at N = 128)")
     a = ap.parse_args(argv)
     ctx = abi.dpm_ctx_create(0)
     if a.layers:
@@ -414,7 +421,9 @@ def main(argv=None):
         return
     if a.test_b:
         N1, N2, MZ, MG = (int(v) for v in a.test_b.split("/"))
-        res = run_test_b_dd(ctx, N1, N2, MZ, MG, T=a.T)
+        prec = {"tc32": abi.DPM_PREC_TC32, "fft32": abi.DPM_PREC_FFT32, "fp32": abi.DPM_PREC_FP32,
+                "fp64": abi.DPM_PREC_FP64}[a.precision]
+        res = run_test_b_dd(ctx, N1, N2, MZ, MG, precision=prec, T=a.T, gamma_series=a.gamma_series)
         abi.dpm_ctx_destroy(ctx)
         if a.out:
             with open(a.out, "w") as f:

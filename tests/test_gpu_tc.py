@@ -109,24 +109,41 @@ def test_tc_pks_step_matches_oracle(ctx):
     abi.dpm_pks_destroy(pks)
 
 
-@pytest.mark.parametrize("n", [128, 256])
-def test_tc_solve_has_no_systematic_bias(ctx, n):
-    """The tensor cores round their FP32 accumulator toward zero; the solvers
-    order the MMAs and scale the spectrum so that the mean relative error of a
-    solve stays well below its maximum (a bias of 2e-6 per solve drifts a
-    10,000-step time loop by 2 %): |sum(u_tc - u_64)| / sum(u_64) < 5e-7 on
-    positive random data, against the FP64 GPU solve (which matches the oracle
-    to 1e-11)."""
+def _unseen_spectra(n):
+    """Positive right-hand sides of two spectra that differ from the dense random
+    and Gaussian data the solvers' rounding compensation was measured on: a
+    linear ramp (energy in the lowest modes, decaying as 1/a) and a handful of
+    point sources (a flat spectrum)."""
+    X, Y, Z = O.mesh(n, -1.0, 1.0)
+    ramp = (X + Y + Z + 3.5).astype(np.float32)
+    spikes = np.zeros((n, n, n), np.float32)
+    rng = np.random.default_rng(n + 7)
+    for _ in range(12):
+        i, j, k = rng.integers(n // 8, n - n // 8, 3)
+        spikes[i, j, k] = rng.uniform(1.0, 3.0)
+    return {"ramp": ramp, "spikes": spikes}
+
+
+@pytest.mark.parametrize("n,prec", [(128, TC), (256, TC), (256, abi.DPM_PREC_FFT32)])
+@pytest.mark.parametrize("kind", ["ramp", "spikes"])
+def test_solve_mean_error_against_oracle(ctx, n, prec, kind):
+    """The mean relative error of a solve against the oracle, |sum(u - u_ref)| /
+    sum(u_ref), on positive data of two spectra the tensor-core solvers' rounding
+    compensation never saw (a bias of 2e-6 per solve drifts a 10,000-step time
+    loop by 2 %).  The tensor cores round their FP32 accumulator toward zero; the
+    tensor-core solvers issue the small cross terms first and scale the
+    spectrum by the mean loss measured on dense random and Gaussian data.  The
+    FFT-style solver rounds to nearest.  Bound: 1e-6, the per-transform FP32
+    error of the dominant mode times the six transforms of a solve."""
     h, sigma = 1.0 / (n - 3), 1.25e5
-    q = np.random.default_rng(n).uniform(0.0, 1.0, (2, n, n, n)).astype(np.float32)
-    q32 = torch.from_numpy(q).cuda()
-    q64 = q32.double()
-    u32, u64 = torch.empty_like(q32), torch.empty_like(q64)
-    abi.dpm_aux_solve_batched(ctx, n, h, sigma, 2, q32, u32, TC)
-    abi.dpm_aux_solve_batched(ctx, n, h, sigma, 2, q64, u64, abi.DPM_PREC_FP64)
+    q = _unseen_spectra(n)[kind]
+    qd = torch.from_numpy(q[None]).cuda()
+    ud = torch.empty_like(qd)
+    abi.dpm_aux_solve_batched(ctx, n, h, sigma, 1, qd, ud, prec)
     torch.cuda.synchronize()
-    d = u32.double() - u64
-    for b in range(2):
-        bias = float(d[b].sum() / u64[b].sum())
-        worst = float(d[b].abs().max() / u64[b].abs().max())
-        assert abs(bias) < 5e-7 and worst < 5e-6, (bias, worst)
+    u = ud.cpu().numpy()[0].astype(np.float64)
+    ref = O.aux_solve(q.astype(np.float64), h, sigma)
+    bias = float(np.sum(u - ref) / np.sum(ref))
+    worst = rel(u, ref)
+    print(f"mean error N={n} prec={prec} {kind}: bias {bias:.2e}, max {worst:.2e}")
+    assert abs(bias) < 1e-6 and worst < 1e-5, (bias, worst)

@@ -203,3 +203,50 @@ def test_dd2_pks_invariants():
         assert d["m2"] > prev["m2"]
         prev = d
     assert abs(prev["mass"] - d0["mass"]) < 5e-3 * d0["mass"]
+
+
+def _setup_gs(N1, N2, MZ, MG, gamma_series):
+    (lo1, hi1, o1), (lo2, hi2, o2) = boxes(N1, N2)
+    return O.DD2Setup((0.0, 0.0, 0.0), R, RZ, R, N1, lo1, hi1, o1, N2, lo2, hi2, o2, MZ, MG, SIGMA,
+                      gamma_series=gamma_series)
+
+
+def test_two_term_gamma_extension_converges():
+    """With the 2-term extension u + d g_N on Gamma (one unknown series there,
+    as the paper's Test (B) runs) the coupled solve still converges under
+    refinement (h ratio 17/33: at least first order), with fewer unknowns and
+    a larger error than the 3-term extension (its dropped (d^2/2) d^2u/dn^2 term
+    is O(h^2) at the grid boundary)."""
+    S = _setup_gs(20, 20, 6, 10, 1)
+    assert S.ncol == 3 * 6 + 10
+    e = solve_errors(S)
+    f = solve_errors(_setup_gs(36, 36, 6, 10, 1))
+    assert all(b < 0.6 * a for a, b in zip(e, f)), (e, f)
+    e3 = solve_errors(_setup_gs(20, 20, 6, 10, 2))
+    assert max(e3) < max(e) < 1e-2
+
+
+def _test_b_peak(gamma_series, MG, steps):
+    """Test (B) data on 32/32 grids: the largest density over `steps` steps."""
+    from paper_1811_03557_gb300.workloads import TEST_B_C0, TEST_B_RHO0
+    (lo1, hi1, o1), (lo2, hi2, o2) = boxes(32, 32)
+    h = min(2 * RZ / 29, 2 * R / 29)
+    st = O.DD2PKSState((0.0, 0.0, 0.0), R, RZ, R, 32, lo1, hi1, o1, 32, lo2, hi2, o2, 8, MG, 1.0, 0.5 * h * h,
+                       TEST_B_RHO0, TEST_B_C0, gamma_series=gamma_series)
+    peak = 0.0
+    for _ in range(steps):
+        st.step()
+        peak = max(peak, st.diagnostics()["max_rho"])
+    return peak
+
+
+def test_test_b_loop_needs_the_two_term_gamma_extension_for_many_harmonics():
+    """The paper runs Test (B) with more Gamma harmonics than grid nodes along a
+    meridian of Omega_2 (150 on 127/63 ... 500 on 255/127).  With one Gamma
+    series (the paper's 2-term extension) 96 harmonics on 32/32 grids stay
+    bounded by the initial density (2000), as the diffusive first steps of
+    Test (B) should; with the extra d^2u/dn^2 series 48 already blow up (the
+    stacked matrix's condition number grows from ~1e5 to ~6e7 and the near-null
+    directions, fitted on gamma_in, swing on gamma_ex)."""
+    assert _test_b_peak(1, 96, 20) < 2000.0
+    assert _test_b_peak(2, 48, 12) > 5000.0
