@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=10000,
                     help="requests in the serving leg (0 skips it)")
-    ap.add_argument("--serving-rate", type=float, default=1500.0, help="mean arrivals per second")
+    ap.add_argument("--serving-rate", type=float, default=1000.0, help="mean arrivals per second")
     ap.add_argument("--serving-models", type=int, default=64)
     ap.add_argument("--serving-saturated-rate", type=float, default=8000.0,
                     help="offered rate of the second, saturated serving leg (0 skips it)")
@@ -293,6 +293,11 @@ def run_ours(args):
     finite = bool(np.isfinite(st.mass) and st.min_rho >= -1e-6 * st.max_rho)
 
     roof = roofline(w, prec, prof, spp)
+    # every AP pass of the step against its own algorithmic bytes (the dominant
+    # one is `roofline`)
+    roof_all = {k: {f: v for f, v in (roofline(w, prec, prof, spp, k) or {}).items()
+                    if f in ("achieved", "frac", "bytes_per_launch", "traffic")}
+                for k in prof if k.startswith("pass") or k.startswith("tc_")}
 
     e2e = None
     if not args.no_e2e:
@@ -341,7 +346,8 @@ def run_ours(args):
                        "step": "PKS step with BEP rebuild (Steps 3-7 incl. 4b), CFL dt <= h^2/4",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": f"inputs larger than L2 ({spp * N ** 3 * 4 / 1e9:.2f} GB batch per step)"},
-            "clocks": clk, "gpu_launches": int(launches), "roofline": roof, "kernels": prof,
+            "clocks": clk, "gpu_launches": int(launches), "roofline": roof, "roofline_passes": roof_all,
+            "kernels": prof,
             "e2e": e2e, "cpu_baseline": cpu, "aux_solve": aux, "sd_dd_test_a": sd_dd, "layers_uneven": layers, "serving": serving,
             "graph": not args.no_graph, "kernel_profile_steps": nprof,
             "sanity": {"finite": bool(finite), "mass": st.mass},
@@ -389,14 +395,18 @@ def profile_traffic(kernel, root=None):
     return None
 
 
-def roofline(w, prec, prof, spp):
-    """Roofline of the dominant AP-pass kernel (largest device time)."""
+def roofline(w, prec, prof, spp, name=None):
+    """Roofline of the dominant AP-pass kernel (largest device time), or of the
+    pass `name`."""
     peaks, src = measured_peaks()
     passes = {k: v for k, v in prof.items() if k.startswith("pass") or k.startswith("tc_")}
     tc = prec == 2
     if not passes:
         return None
-    name, rec = max(passes.items(), key=lambda kv: kv[1]["ms_total"])
+    if name is None:
+        name, rec = max(passes.items(), key=lambda kv: kv[1]["ms_total"])
+    else:
+        rec = passes[name]
     N = w.N
     # right-hand sides per launch: every step runs one batch of (ncol + 2) and one of 2
     batches = [(w.ncol + 2), 2]

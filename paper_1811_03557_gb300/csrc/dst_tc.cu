@@ -595,23 +595,26 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
                 }
             }
 #pragma unroll
-            for (int c0 = kH * hc; c0 < kH * hc + kH; c0 += 16) {
-                float d[16];
-                tc::tmem_ld16(lane_addr + c0, d);
+            for (int c0 = kH * hc; c0 < kH * hc + kH; c0 += 32) {
+                float d[2][16];  // two TMEM loads in flight per wait
+                tc::tmem_ld16(lane_addr + c0, d[0]);
+                tc::tmem_ld16(lane_addr + c0 + 16, d[1]);
                 tc::tmem_wait_ld();
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int c = c0 + u;
-                    const int j = c < kH ? 2 * c : 2 * (c - kH) + 1;
-                    const float val = d[u] * iout;
-                    if (r.out_dense) {
-                        const int64_t pp = pbase + (int64_t)j * kN + L;
-                        float o = val;
-                        if (a.mask_out && !(a.labels[pp] & (DPM_LBL_MPLUS | DPM_LBL_GEX))) o = 0.f;
-                        r.out_dense[pp] = o;
+                for (int q = 0; q < 2; ++q)
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const int c = c0 + 16 * q + u;
+                        const int j = c < kH ? 2 * c : 2 * (c - kH) + 1;
+                        const float val = d[q][u] * iout;
+                        if (r.out_dense) {
+                            const int64_t pp = pbase + (int64_t)j * kN + L;
+                            float o = val;
+                            if (a.mask_out && !(a.labels[pp] & (DPM_LBL_MPLUS | DPM_LBL_GEX))) o = 0.f;
+                            r.out_dense[pp] = o;
+                        }
+                        if (r.out_trace) stage[j * kN + L] = val;
                     }
-                    if (r.out_trace) stage[j * kN + L] = val;
-                }
             }
             if (r.out_trace) {
                 __syncthreads();
@@ -723,16 +726,21 @@ k_tc_pencil(TcArgs a, const ApRhs<float> *rhs, float *work, const __grid_constan
         if (!run_transform(S, tm, phase)) break;
         // ---- phase C: z[a] = D / lambda, fold over a, split -------------------
         float z[kN];  // z[a], a = 0..127 (a = 2a' from sums, 2a'+1 from differences)
+        // 64 columns per TMEM round trip (four loads in flight, one wait)
 #pragma unroll
-        for (int c0 = 0; c0 < 2 * kH; c0 += 16) {
-            float d[16];
-            tc::tmem_ld16(lane_addr + c0, d);
+        for (int c0 = 0; c0 < 2 * kH; c0 += 64) {
+            float d[4][16];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) tc::tmem_ld16(lane_addr + c0 + 16 * q, d[q]);
             tc::tmem_wait_ld();
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const int am = c0 < kH ? 2 * (c0 + u) : 2 * (c0 + u - kH) + 1;
-                z[am] = d[u] * ((c0 < kH ? ie : io) * (1.f / kSScale));
-            }
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int c = c0 + 16 * q + u;
+                    const int am = c < kH ? 2 * c : 2 * (c - kH) + 1;
+                    z[am] = d[q][u] * ((c0 < kH ? ie : io) * (1.f / kSScale));
+                }
         }
         const float wjc = S.w()[jb] + S.w()[t] + sig;
 #pragma unroll
@@ -763,16 +771,20 @@ k_tc_pencil(TcArgs a, const ApRhs<float> *rhs, float *work, const __grid_constan
         }
         // ---- phase E: D3[c][i'] -> Z[i][jb][c] ---------------------------------
 #pragma unroll
-        for (int c0 = 0; c0 < 2 * kH; c0 += 16) {
-            float d[16];
-            tc::tmem_ld16(lane_addr + c0, d);
+        for (int c0 = 0; c0 < 2 * kH; c0 += 64) {
+            float d[4][16];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) tc::tmem_ld16(lane_addr + c0 + 16 * q, d[q]);
             tc::tmem_wait_ld();
             const float sc2 = (c0 < kH ? ie : io) * (1.f / kSScale);
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const int ii = c0 < kH ? 2 * (c0 + u) : 2 * (c0 + u - kH) + 1;
-                base[(size_t)ii * sN2] = d[u] * sc2;
-            }
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int c = c0 + 16 * q + u;
+                    const int ii = c < kH ? 2 * c : 2 * (c - kH) + 1;
+                    base[(size_t)ii * sN2] = d[q][u] * sc2;
+                }
         }
         tc::tc_fence_before_sync();
         __syncthreads();
