@@ -77,6 +77,19 @@ def test_full_size_N256_residual_property(ctx):
         assert r < bound, (r, bound)
 
 
+@pytest.mark.parametrize("prec", [abi.DPM_PREC_FP32, abi.DPM_PREC_FP64])
+def test_full_size_N256_matches_oracle(ctx, prec):
+    """The SIMT solver at N = 256 (the autotuner's widest-row tiles) against the
+    oracle's dense DST-I, one right-hand side, at the path's tolerance."""
+    N = 256
+    h, sigma = 2.4 / 257, 1e4 + 1.0
+    q = random_rhs(13, 1, N, np.float32).astype(np.float64)
+    u = gpu_solve(ctx, q, h, sigma, prec)
+    e = rel_linf(u[0], O.aux_solve(q[0], h, sigma))
+    print(f"SIMT N=256 prec={prec}: rel err {e:.3e}")
+    assert e < TOL[prec], e
+
+
 def test_solve_on_a_second_device(ctx):
     """Kernel attributes (the dynamic shared memory limits above 48 KB) belong to
     each device's context: after solves on device 0, the same solves on device 1
