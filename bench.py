@@ -60,6 +60,11 @@ def parse():
     ap.add_argument("--aux-case", default=None,
                     help="N:B:precision (fp32|tc32|fft32|fp64): time only this batched AP solve, "
                          "--warmup then --steps calls, and print its own JSON line (profiling cases)")
+    ap.add_argument("--bep-case", default=None,
+                    help="N:K:precision (fp32|tc32|fft32|fp64): time only the BEP build of the unit "
+                         "sphere in [-1.25, 1.25]^3 with 2 (K+1)^2 columns (sparse shell right-hand "
+                         "sides in, traces on gamma_in out), --warmup then --steps builds, and print "
+                         "its own JSON line with the AP passes' times (profiling cases)")
     return ap.parse_args()
 
 
@@ -666,10 +671,53 @@ def run_aux_case(args):
     abi.dpm_ctx_destroy(ctx)
 
 
+def run_bep_case(args):
+    """One BEP build alone: the AP passes on sparse shell right-hand sides with
+    trace output, as in every PKS step (a small case for kernel captures)."""
+    import torch
+    from paper_1811_03557_gb300 import abi
+    from paper_1811_03557_gb300.workloads import Geometry
+    N, K, pname = args.bep_case.split(":")
+    N, K = int(N), int(K)
+    prec = {"fp32": abi.DPM_PREC_FP32, "tc32": abi.DPM_PREC_TC32, "fft32": abi.DPM_PREC_FFT32,
+            "fp64": abi.DPM_PREC_FP64}[pname]
+    torch.cuda.set_device(0)
+    ctx = abi.dpm_ctx_create(0)
+    lo, hi = -1.25, 1.25
+    h = (hi - lo) / (N + 1)
+    sigma = 4.0 / (h * h) + 1.0      # 1/dt + 1 at the PKS step's dt = h^2/4
+    stream = torch.cuda.Stream()
+    build = lambda: abi.dpm_bep_build(ctx, Geometry.sphere(1.0), N, lo, hi, sigma, K, 1, prec, stream)
+    for _ in range(args.warmup):
+        abi.dpm_bep_destroy(build())
+    torch.cuda.synchronize()
+    abi.dpm_profile_reset()
+    abi.dpm_profile_enable(True)
+    ms = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        bep = build()
+        torch.cuda.synchronize()
+        ms.append((time.perf_counter() - t0) * 1e3)
+        info = abi.dpm_bep_get_info(bep)
+        abi.dpm_bep_destroy(bep)
+    abi.dpm_profile_enable(False)
+    keys = ("tc_shell_rhs", "tc_plane_fwd", "tc_pencil", "tc_plane_inv", "lsq_gram_syrk", "lsq_cholesky")
+    per = {k: abi.dpm_profile_read(k)[0] / max(1, args.steps) for k in keys}
+    abi.dpm_profile_reset()
+    print(json.dumps({"bep_case": args.bep_case, "ncol": info.ncol, "n_gamma": info.n_gamma,
+                      "n_gin": info.n_gin, "build_ms": float(np.median(ms)) if ms else None,
+                      "kernels_ms": per}), flush=True)
+    abi.dpm_ctx_destroy(ctx)
+
+
 def main():
     args = parse()
     if args.aux_case and args.impl != "reference":
         run_aux_case(args)
+        return
+    if args.bep_case and args.impl != "reference":
+        run_bep_case(args)
         return
     if args.impl == "reference":
         run_reference(args)

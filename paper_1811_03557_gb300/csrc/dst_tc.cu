@@ -77,13 +77,15 @@ struct TcArgs {
 };
 
 __device__ __forceinline__ float pow2_scale(float m, float *inv) {
-    // s = 2^(14 - e) with m = f 2^e, f in [0.5, 1): m*s in [2^13, 2^14)
-    if (!(m > 0.f) || !isfinite(m)) { *inv = 1.f; return 1.f; }
-    int e;
-    frexpf(m, &e);
-    if (e < -100) e = -100;
-    *inv = ldexpf(1.f, e - 14);
-    return ldexpf(1.f, 14 - e);
+    // s = 2^(14 - e) with m = f 2^e, f in [0.5, 1): m*s in [2^13, 2^14); e is
+    // read from the exponent field (a normal m has e = biased exponent - 126),
+    // clamped below at -100 (which also covers subnormal m), and both powers of
+    // two are assembled as exponent fields.  m = 0, inf or NaN: s = 1.
+    const uint32_t be = __float_as_uint(m) >> 23;  // m >= 0: no sign bit
+    const int e = max((int)be - 126, -100);
+    const bool ok = m > 0.f && be < 255u;
+    *inv = ok ? __uint_as_float((uint32_t)(113 + e) << 23) : 1.f;
+    return ok ? __uint_as_float((uint32_t)(141 - e) << 23) : 1.f;
 }
 
 // hi/lo split of two values at once, packed as f16x2 (first value in the low half).
@@ -482,7 +484,10 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
         // warp: 16 rows, two per step; lanes 0-15 take row 2s, lanes 16-31 row
         // 2s+1, lane l' = l mod 16 holding x[4l'..4l'+3] and x[124-4l'..127-4l'],
         // so the fold (sums e, differences o at m' = 4l'+u) is thread-local.
-        // Rows j and 127-j go to A rows 2j and 2j+1 (adjacent TMEM lanes).
+        // Rows p and 127-p (p < 64) go to A rows 16(p/8) + p%8 and that + 8, so
+        // the fold over rows in phase C pairs TMEM lanes L and L^8, and the 8
+        // lanes of a quarter-warp hold 8 consecutive p (conflict-free stores of
+        // the MN-major second operand).
         const int lp = lane & 15, rsel = lane >> 4;
         float xa[8][4], xb[8][4];
 #pragma unroll
@@ -498,7 +503,8 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
 #pragma unroll
         for (int st = 0; st < 8; ++st) {
             const int row = warp * 16 + 2 * st + rsel;
-            const int LL = row < kH ? 2 * row : 2 * (kN - 1 - row) + 1;
+            const int pr = row < kH ? row : kN - 1 - row;
+            const int LL = 16 * (pr >> 3) + (row < kH ? 0 : 8) + (pr & 7);
             float rm = 0.f;
 #pragma unroll
             for (int u = 0; u < 4; ++u) rm = fmaxf(rm, fmaxf(fabsf(xa[st][u]), fabsf(xb[st][u])));
@@ -520,7 +526,7 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
         for (int q = 16; q > 0; q >>= 1) wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, q));
         if (lane == 0) wmax[warp] = wm;
         if (!run_transform(S, tm, phase)) { ok = false; break; }
-        // ---- phase C: fold over rows (lanes L, L^1), A2 in MN-major layout --------
+        // ---- phase C: fold over rows (lanes L, L^8), A2 in MN-major layout --------
         // Columns [32 hc, 32 hc + 32) of the sums (modes 2c') and of the
         // differences (modes 2c'+1) of this thread's row, 16 at a time.
         float amax = 0.f;
@@ -529,9 +535,13 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
         float inv2;
         const float s2 = pow2_scale(256.f * amax, &inv2);
         {
-            const float iD = rowinv[L] * (1.f / kSScale);
-            const int p = L >> 1;
-            unsigned char *thi = S.A((L & 1) ? 2 : 0), *tlo = S.A((L & 1) ? 3 : 1);
+            // row scale, sine-block scale and the second operand's scale in one
+            // factor (powers of two: the products are exact)
+            const float iD = rowinv[L] * (1.f / kSScale) * s2;
+            const int sd = (L >> 3) & 1;            // 0: row p (sums), 1: row 127-p (differences)
+            const float sgn = sd ? -1.f : 1.f;
+            const int p = 8 * (L >> 4) + (L & 7);
+            unsigned char *thi = S.A(sd ? 2 : 0), *tlo = S.A(sd ? 3 : 1);
 #pragma unroll
             for (int c0 = 32 * hc; c0 < 32 * hc + 32; c0 += 16) {
                 float de[16], dd[16];
@@ -542,17 +552,17 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {
                     const float oe = de[u] * iD, od = dd[u] * iD;
-                    const float pe = __shfl_xor_sync(0xffffffffu, oe, 1);
-                    const float pd = __shfl_xor_sync(0xffffffffu, od, 1);
-                    f2[2 * u] = (L & 1) ? (pe - oe) : (oe + pe);
-                    f2[2 * u + 1] = (L & 1) ? (pd - od) : (od + pd);
+                    const float pe = __shfl_xor_sync(0xffffffffu, oe, 8);
+                    const float pd = __shfl_xor_sync(0xffffffffu, od, 8);
+                    f2[2 * u] = fmaf(oe, sgn, pe);  // oe + pe, or pe - oe on row 127-p
+                    f2[2 * u + 1] = fmaf(od, sgn, pd);
                 }
 #pragma unroll
                 for (int q8 = 0; q8 < 4; ++q8) {
                     uint32_t hw[4], lw[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u)
-                        split_pack(f2[8 * q8 + 2 * u] * s2, f2[8 * q8 + 2 * u + 1] * s2, hw[u], lw[u]);
+                        split_pack(f2[8 * q8 + 2 * u], f2[8 * q8 + 2 * u + 1], hw[u], lw[u]);
                     const uint32_t off = mn_off(2 * c0 + 8 * q8, p);
                     *reinterpret_cast<uint4 *>(thi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
                     *reinterpret_cast<uint4 *>(tlo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
@@ -566,21 +576,19 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
         // ---- phase E: D2 (row = c = L); columns [0,64) even j-modes, [64,128) odd --
         const float iout = inv2 * (1.f / kSScale);
         if (!INV) {
-            float *wplane = work + ((size_t)b * kN + i) * kN * kN;
+            // j = 2c' + hc for column c = 64 hc + c' (even modes from the sums, odd
+            // ones from the differences); four TMEM loads in flight per wait
+            float *wrow = work + ((size_t)b * kN + i) * kN * kN + hc * kN + L;
 #pragma unroll
-            for (int c0 = kH * hc; c0 < kH * hc + kH; c0 += 32) {
-                float d0[16], d1[16];
-                tc::tmem_ld16(lane_addr + c0, d0);
-                tc::tmem_ld16(lane_addr + c0 + 16, d1);
+            for (int c0 = 0; c0 < kH; c0 += 64) {
+                float d[4][16];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) tc::tmem_ld16(lane_addr + kH * hc + c0 + 16 * q, d[q]);
                 tc::tmem_wait_ld();
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int c = c0 + u, c1 = c0 + 16 + u;
-                    const int j0 = c < kH ? 2 * c : 2 * (c - kH) + 1;
-                    const int j1 = c1 < kH ? 2 * c1 : 2 * (c1 - kH) + 1;
-                    wplane[j0 * kN + L] = d0[u] * iout;
-                    wplane[j1 * kN + L] = d1[u] * iout;
-                }
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) wrow[2 * (c0 + 16 * q + u) * kN] = d[q][u] * iout;
             }
         } else {
             float *stage = raw;  // 128 x 128 fp32 (the operand region, free again)
@@ -594,27 +602,43 @@ k_tc_plane(TcArgs a, const ApRhs<float> *rhs, float *work) {
                     if (e < ge1) pidx[q] = a.gin[e];
                 }
             }
+            if (r.out_dense) {
 #pragma unroll
-            for (int c0 = kH * hc; c0 < kH * hc + kH; c0 += 32) {
-                float d[2][16];  // two TMEM loads in flight per wait
-                tc::tmem_ld16(lane_addr + c0, d[0]);
-                tc::tmem_ld16(lane_addr + c0 + 16, d[1]);
-                tc::tmem_wait_ld();
+                for (int c0 = kH * hc; c0 < kH * hc + kH; c0 += 32) {
+                    float d[2][16];  // two TMEM loads in flight per wait
+                    tc::tmem_ld16(lane_addr + c0, d[0]);
+                    tc::tmem_ld16(lane_addr + c0 + 16, d[1]);
+                    tc::tmem_wait_ld();
 #pragma unroll
-                for (int q = 0; q < 2; ++q)
+                    for (int q = 0; q < 2; ++q)
 #pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        const int c = c0 + 16 * q + u;
-                        const int j = c < kH ? 2 * c : 2 * (c - kH) + 1;
-                        const float val = d[q][u] * iout;
-                        if (r.out_dense) {
+                        for (int u = 0; u < 16; ++u) {
+                            const int c = c0 + 16 * q + u;
+                            const int j = c < kH ? 2 * c : 2 * (c - kH) + 1;
+                            const float val = d[q][u] * iout;
                             const int64_t pp = pbase + (int64_t)j * kN + L;
                             float o = val;
                             if (a.mask_out && !(a.labels[pp] & (DPM_LBL_MPLUS | DPM_LBL_GEX))) o = 0.f;
                             r.out_dense[pp] = o;
+                            if (r.out_trace) stage[j * kN + L] = val;
                         }
-                        if (r.out_trace) stage[j * kN + L] = val;
-                    }
+                }
+            } else if (r.out_trace) {
+                // trace only (every BEP column): the plane goes to the staging area
+                // (j = 2c' + hc: the even modes from the sums, the odd ones from the
+                // differences), four TMEM loads in flight per wait
+                float *srow = stage + hc * kN + L;
+#pragma unroll
+                for (int c0 = 0; c0 < kH; c0 += 64) {
+                    float d[4][16];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) tc::tmem_ld16(lane_addr + kH * hc + c0 + 16 * q, d[q]);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) srow[2 * (c0 + 16 * q + u) * kN] = d[q][u] * iout;
+                }
             }
             if (r.out_trace) {
                 __syncthreads();
