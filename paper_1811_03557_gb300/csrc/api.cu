@@ -2115,6 +2115,17 @@ template <class T> int ml_init(dpm_ml *d, dpm_ctx *ctx, const dpm_ml_params &P, 
     DPM_RET(d->lsq.A.alloc(sizeof(double) * mtot * d->ncol));
     DPM_RET(d->coef.alloc(sizeof(double) * 4 * d->ncol));
     DPM_RET(d->bvec.alloc(sizeof(T) * 4 * mtot));
+    // the stacked matrix is block-banded: sub-domain l's rows meet only the
+    // series of its own spheres (the ball: sphere 1; shell l: spheres l, l + 1)
+    std::vector<int64_t> row0(1, 0);
+    std::vector<int> c0, c1;
+    for (int l = 0; l < L; ++l) {
+        const int m0 = l == 0 ? 1 : l, m1 = l + 1;
+        row0.push_back(row0.back() + d->sub[l].gi.n_gin);
+        c0.push_back(cm.off[m0 - 1]);
+        c1.push_back(cm.off[m1]);
+    }
+    DPM_RET(lsq_set_band(d->lsq, row0, c0, c1, s));
     return DPM_OK;
 }
 

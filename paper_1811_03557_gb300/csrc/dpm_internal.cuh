@@ -243,6 +243,12 @@ struct LsqFactor {
     bool equilibrated = false;
     bool rinv32 = false;  // R^{-1} stored in FP32 (the in-shared-memory mixed factor)
     const float *A32 = nullptr;  // FP32 copy of A kept by that factor (in X), else null
+    const float *A32s = nullptr; // FP32 copy of A D kept by the mixed factor for larger n (in X)
+    // Optional block structure of a block-banded A (stored dense, zeros outside
+    // the blocks), set by lsq_set_band: int[2n] the row interval [lo, hi) of
+    // each column's nonzeros, then int[2 ceil(m/32)] the column interval of
+    // each 32-row group.  Empty: A is treated as dense.
+    DevBuf band;
     DevBuf A;      // double[m*n] column-major (Householder overwrites it)
     DevBuf tau;    // double[n] Householder scalars
     DevBuf X;      // scratch of the Gram / Cholesky factorisation
@@ -345,6 +351,12 @@ int lsq_factor(LsqFactor &f, const int *cond_flag, cudaStream_t s);
 // The same without the host read of the pivot status (no synchronisation;
 // for stream capture): lsq_status reads it later.
 int lsq_factor_async(LsqFactor &f, cudaStream_t s);
+// Declare A block-banded: block b holds rows [row0[b], row0[b+1]) and is
+// nonzero only in columns [c0[b], c1[b]); every other entry of A is zero.
+// The products with A and A^T then skip the zero blocks (same results: only
+// exact zero terms are left out).  Synchronises s (host arrays are staged).
+int lsq_set_band(LsqFactor &f, const std::vector<int64_t> &row0, const std::vector<int> &c0,
+                 const std::vector<int> &c1, cudaStream_t s);
 int lsq_status(const LsqFactor &f, cudaStream_t s);
 // C[r][0..n) = X b[r] for nr right-hand sides (b: [nr][m] in T, C: [nr][n] double)
 template <class T>

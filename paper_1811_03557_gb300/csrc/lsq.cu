@@ -5,7 +5,9 @@
 // A^T A (up to column equilibration D), A m x n column-major, m >> n:
 //   * mixed precision (the FP32 paths): Gram of an FP32 copy of A over all
 //     SMs (chunk sums in FP64, fixed order), equilibrated by its diagonal and
-//     factored in FP32 in one CTA, R^{-1} kept in FP32 (n <= 168);
+//     factored in FP32 in one CTA, R^{-1} kept in FP32 (n <= 168); for
+//     larger n the Gram of an FP32 copy of A D (D from the column norms),
+//     factored in FP64, with that copy kept for the solves' products with A^T;
 //   * CholeskyQR in FP64 (FP64 SYRK, FP64 Cholesky; optionally equilibrated
 //     with a small diagonal shift);
 //   * Householder QR, one reflector H_j = I - tau_j v_j v_j^T per column
@@ -13,7 +15,9 @@
 // Solve (every step): C = D R^{-1} R^{-T} D A^T b (the semi-normal equations
 // with the original A), then iterative refinement on r = b - A C, the
 // residual always in FP64.  With the factor as a preconditioner the refined C
-// agrees with a backward-stable QR solve; Q is never formed.
+// agrees with a backward-stable QR solve; Q is never formed.  A block-banded
+// A (lsq_set_band: the stacked BEPs of the layered decomposition) is stored
+// dense, but the solves' products skip its zero blocks.
 #include <math.h>
 
 #include <algorithm>
@@ -101,16 +105,31 @@ __global__ void k_extract_r(int m, int n, const double *A, const double *rdiag, 
 // over all SMs; kAtbU rows per thread in flight, fixed-order block sums.  The
 // slices are added (in slice order) where y is consumed (k_trimv).
 constexpr int kAtbQ = 4, kAtbU = 4, kAtbT = 256, kAtbMaxSlices = 16;
+// The rows a CTA of k_atb / k_atb32 visits: its slice [r_begin, r_end), cut to
+// the column's nonzero rows [lo, hi) when A is banded.  The first unrolled
+// group is the one that holds lo, so every row keeps its thread and its place
+// in that thread's sum (the skipped rows hold zeros): the same sums as the
+// dense loop.
+__device__ __forceinline__ void atb_rows(const int *cband, int c, int r_begin, int &r_start, int &r_end) {
+    if (!cband) { r_start = r_begin; return; }
+    const int lo = max(r_begin, cband[2 * c]);
+    r_end = min(r_end, cband[2 * c + 1]);
+    r_start = lo >= r_end ? r_end : r_begin + (lo - r_begin) / (kAtbU * kAtbT) * (kAtbU * kAtbT);
+}
+
 __global__ void __launch_bounds__(kAtbT) k_atb(int m, int n, const double *__restrict__ A0,
                                                const double *__restrict__ b, int ldb,
-                                               double *__restrict__ part, int nr, int rows_per) {
+                                               double *__restrict__ part, int nr, int rows_per,
+                                               const int *__restrict__ cband) {
     __shared__ double sh[kAtbQ][kAtbT / 32];
     const int c = blockIdx.x, sl = blockIdx.y, q0 = blockIdx.z * kAtbQ, nq = min(kAtbQ, nr - q0);
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int r_begin = sl * rows_per, r_end = min(m, r_begin + rows_per);
+    const int r_begin = sl * rows_per;
+    int r_end = min(m, r_begin + rows_per), r_start;
+    atb_rows(cband, c, r_begin, r_start, r_end);
     const double *a = A0 + (size_t)c * m;
     double acc[kAtbQ] = {};
-    for (int r0 = r_begin + t; r0 < r_end; r0 += kAtbU * kAtbT) {
+    for (int r0 = r_start + t; r0 < r_end; r0 += kAtbU * kAtbT) {
         double av[kAtbU];
 #pragma unroll
         for (int u = 0; u < kAtbU; ++u) {
@@ -150,14 +169,17 @@ __global__ void __launch_bounds__(kAtbT) k_atb(int m, int n, const double *__res
 // FP64 (the preconditioner's own error is larger than these roundings).
 __global__ void __launch_bounds__(kAtbT) k_atb32(int m, int n, const float *__restrict__ A32,
                                                  const float *__restrict__ b, int ldb,
-                                                 double *__restrict__ part, int nr, int rows_per) {
+                                                 double *__restrict__ part, int nr, int rows_per,
+                                                 const int *__restrict__ cband) {
     __shared__ double sh[kAtbQ][kAtbT / 32];
     const int c = blockIdx.x, sl = blockIdx.y, q0 = blockIdx.z * kAtbQ, nq = min(kAtbQ, nr - q0);
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int r_begin = sl * rows_per, r_end = min(m, r_begin + rows_per);
+    const int r_begin = sl * rows_per;
+    int r_end = min(m, r_begin + rows_per), r_start;
+    atb_rows(cband, c, r_begin, r_start, r_end);
     const float *a = A32 + (size_t)c * m;
     float acc[kAtbQ] = {};
-    for (int r0 = r_begin + t; r0 < r_end; r0 += kAtbU * kAtbT) {
+    for (int r0 = r_start + t; r0 < r_end; r0 += kAtbU * kAtbT) {
         float av[kAtbU];
 #pragma unroll
         for (int u = 0; u < kAtbU; ++u) {
@@ -206,17 +228,26 @@ __global__ void k_to_double(int m, int nr, const float *__restrict__ b, int ldb,
 // lanes) and up to kAtbQ right-hand sides; its 8 warps take the columns
 // c = w, w + 8, ... and the 8 partial sums are added in warp order.
 constexpr int kResW = 8;
+// With a banded A (rband: the column interval of each 32-row group) each warp
+// starts at its first column of the interval with the same residue mod kResW:
+// the columns left out hold zeros in these rows, so the sums are the dense ones.
 template <class T, class R>
 __global__ void __launch_bounds__(32 * kResW) k_resid(int m, int n, const double *A0, const T *b, int ldb,
-                                                      const double *C, R *res, int nr) {
+                                                      const double *C, R *res, int nr,
+                                                      const int *__restrict__ rband) {
     __shared__ double sh[kResW][kAtbQ][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r = blockIdx.x * 32 + lane;
     const int q0 = blockIdx.y * kAtbQ, nq = min(kAtbQ, nr - q0);
+    int c_lo = 0, c_hi = n;
+    if (rband) {
+        c_lo = rband[2 * blockIdx.x];
+        c_hi = rband[2 * blockIdx.x + 1];
+    }
     double s[kAtbQ] = {};
     if (r < m) {
-        int c = warp;
-        for (; c + 3 * kResW < n; c += 4 * kResW) {
+        int c = c_lo + ((warp - c_lo) % kResW + kResW) % kResW;
+        for (; c + 3 * kResW < c_hi; c += 4 * kResW) {
             double av[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) av[u] = A0[(size_t)(c + u * kResW) * m + r];
@@ -228,7 +259,7 @@ __global__ void __launch_bounds__(32 * kResW) k_resid(int m, int n, const double
                     for (int u = 0; u < 4; ++u) s[q] = fma(av[u], cq[c + u * kResW], s[q]);
                 }
         }
-        for (; c < n; c += kResW) {
+        for (; c < c_hi; c += kResW) {
             const double av = A0[(size_t)c * m + r];
 #pragma unroll
             for (int q = 0; q < kAtbQ; ++q)
@@ -1039,6 +1070,7 @@ static int mixed_factor(LsqFactor &f, const double *A0, double *R, double *Rinv,
         k_cholesky<<<1, 1024, 0, s>>>(n, G, R, G + nn, 0, status);
         DPM_LAUNCHED();
         *rinv_done = 0;
+        f.A32s = Af;  // A D in FP32: the solves' products with A^T
         return DPM_OK;
     }
     *rinv_done = 1;
@@ -1062,6 +1094,50 @@ int lsq_factor(LsqFactor &f, const int *cond_flag, cudaStream_t s) {
 }
 
 int lsq_factor_async(LsqFactor &f, cudaStream_t s) { return lsq_factor_impl(f, false, s); }
+
+int lsq_set_band(LsqFactor &f, const std::vector<int64_t> &row0, const std::vector<int> &c0,
+                 const std::vector<int> &c1, cudaStream_t s) {
+    const int m = f.m, n = f.n;
+    const size_t nb = c0.size();
+    bool ok = m >= 1 && n >= 1 && nb >= 1 && row0.size() == nb + 1 && c1.size() == nb && row0[0] == 0 &&
+              row0[nb] == m;
+    for (size_t b = 0; ok && b < nb; ++b)
+        ok = row0[b] <= row0[b + 1] && 0 <= c0[b] && c0[b] <= c1[b] && c1[b] <= n;
+    if (!ok) { set_error("least squares: inconsistent block structure"); return DPM_EINVAL; }
+    const int ng = (m + 31) / 32;
+    std::vector<int> h(2 * (size_t)n + 2 * (size_t)ng, 0);
+    // each column: the rows from its first block's first row to its last block's last
+    for (int c = 0; c < n; ++c) {
+        int64_t lo = m, hi = 0;
+        for (size_t b = 0; b < nb; ++b)
+            if (c0[b] <= c && c < c1[b] && row0[b] < row0[b + 1]) {
+                lo = std::min(lo, row0[b]);
+                hi = std::max(hi, row0[b + 1]);
+            }
+        if (lo < hi) {
+            h[2 * c] = (int)lo;
+            h[2 * c + 1] = (int)hi;
+        }
+    }
+    // each 32-row group: the union of the column intervals of the blocks it meets
+    for (int g = 0; g < ng; ++g) {
+        const int64_t r0 = 32 * (int64_t)g, r1 = std::min<int64_t>(m, r0 + 32);
+        int lo = n, hi = 0;
+        for (size_t b = 0; b < nb; ++b)
+            if (row0[b] < r1 && r0 < row0[b + 1] && c0[b] < c1[b]) {
+                lo = std::min(lo, c0[b]);
+                hi = std::max(hi, c1[b]);
+            }
+        if (lo < hi) {
+            h[2 * (size_t)n + 2 * g] = lo;
+            h[2 * (size_t)n + 2 * g + 1] = hi;
+        }
+    }
+    DPM_RET(f.band.reserve(sizeof(int) * h.size()));
+    DPM_CUDA(cudaMemcpyAsync(f.band.p, h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice, s));
+    DPM_CUDA(cudaStreamSynchronize(s));  // h goes out of scope
+    return DPM_OK;
+}
 
 int lsq_status(const LsqFactor &f, cudaStream_t s) {
     const int m = f.m, n = f.n;
@@ -1103,6 +1179,7 @@ static int lsq_factor_impl(LsqFactor &f, bool sync, cudaStream_t s) {
     f.equilibrated = false;
     f.rinv32 = false;
     f.A32 = nullptr;
+    f.A32s = nullptr;
     int rinv_done = 0;
     if (f.method == LsqFactor::kHouseholder) {
         DPM_RET(householder_factor(f, A0, w, rdiag, R, status, s));
@@ -1153,8 +1230,11 @@ int lsq_apply(const LsqFactor &f, const T *b, int ldb, double *C, int nr, cudaSt
     const int mv_blocks = (n * nr * 32 + 255) / 256;
     const double *dsc = f.equilibrated ? Rinv + (size_t)n * n : nullptr;
     // refinement steps (FP64 residual): each contracts the error by
-    // ~kappa(AD)^2 eps_32.  One leaves C ~1e-10 relative, far below the FP32
-    // solver's error; the FP64 path takes three.
+    // ~kappa(AD)^2 eps_32, down to the floor the products with A^T set: none
+    // below 1e-10 relative with FP64 products; with FP32 products (the FP32
+    // paths with an FP32 copy of A) about kappa eps_32 |r| / (|A| |C|), still
+    // far below the FP32 solver's own error.  One step on the FP32 paths, three
+    // on the FP64 path.
     const int refine = f.equilibrated ? (sizeof(T) == sizeof(double) ? 3 : 1) : 1;
     DPM_PROF("lsq_solve", s);
     // A^T b by row slices: about six CTAs per SM in all, at most kAtbMaxSlices
@@ -1163,10 +1243,15 @@ int lsq_apply(const LsqFactor &f, const T *b, int ldb, double *C, int nr, cudaSt
     const int rows_per = (m + S - 1) / S;
     S = (m + rows_per - 1) / rows_per;
     double *ypart = const_cast<double *>(Rinv) + (size_t)n * n + n;
-    // FP32 right-hand sides with the factor's FP32 copy of A: the products with
-    // A^T in FP32 (FP64 sums), only the residual in FP64; it is stored in FP32
-    // in res's space
-    const bool fast32 = sizeof(T) == sizeof(float) && f.A32 != nullptr;
+    // FP32 right-hand sides with the factor's FP32 copy of A (or of A D, whose
+    // products already carry the column scales): the products with A^T in FP32
+    // (FP64 sums), only the residual in FP64; it is stored in FP32 in res's space
+    const float *A32 = f.A32 ? f.A32 : (sizeof(T) == sizeof(float) ? f.A32s : nullptr);
+    const bool fast32 = sizeof(T) == sizeof(float) && A32 != nullptr;
+    const bool y_scaled = fast32 && !f.A32;
+    // block-banded A: the column row intervals, then the 32-row column intervals
+    const int *cband = f.band.p ? f.band.as<int>() : nullptr;
+    const int *rband = cband ? cband + 2 * (size_t)n : nullptr;
     const double *bd = nullptr;
     int ldbd = 0;
     if (!fast32) {
@@ -1200,14 +1285,14 @@ int lsq_apply(const LsqFactor &f, const T *b, int ldb, double *C, int nr, cudaSt
     };
     // C = D R^{-1} R^{-T} D A^T b   (D = I unless the factor was equilibrated)
     if (fast32)
-        k_atb32<<<dim3(n, S, qg), kAtbT, 0, s>>>(m, n, f.A32, reinterpret_cast<const float *>(b), ldb, ypart,
-                                                 nr, rows_per);
+        k_atb32<<<dim3(n, S, qg), kAtbT, 0, s>>>(m, n, A32, reinterpret_cast<const float *>(b), ldb, ypart,
+                                                 nr, rows_per, cband);
     else
-        k_atb<<<dim3(n, S, qg), kAtbT, 0, s>>>(m, n, A0, bd, ldbd, ypart, nr, rows_per);
+        k_atb<<<dim3(n, S, qg), kAtbT, 0, s>>>(m, n, A0, bd, ldbd, ypart, nr, rows_per, cband);
     DPM_LAUNCHED();
     // z = R^{-T} D y, C (+)= D R^{-1} z
     const size_t tsm = trisolve_smem(n, nr);
-    const bool fused = fast32 && f.rinv32 && tsm <= 227 * 1024;
+    const bool fused = fast32 && !y_scaled && f.rinv32 && tsm <= 227 * 1024;
     if (fused && tsm > 48 * 1024) DPM_RET(lsq_configure());
     auto precondition = [&](int accumulate) -> int {
         if (fused) {
@@ -1216,20 +1301,22 @@ int lsq_apply(const LsqFactor &f, const T *b, int ldb, double *C, int nr, cudaSt
             DPM_LAUNCHED();
             return DPM_OK;
         }
-        DPM_RET(trimv(true, ypart, z, 0, nullptr, S, dsc));
+        DPM_RET(trimv(true, ypart, z, 0, nullptr, S, y_scaled ? nullptr : dsc));
         return trimv(false, z, C, accumulate, dsc, 1, nullptr);
     };
     DPM_RET(precondition(0));
     // iterative refinement: C += D R^{-1} R^{-T} D A^T (b - A C), the residual in FP64
     for (int it = 0; it < refine; ++it) {
         if (fast32) {
-            k_resid<T, float><<<dim3((m + 31) / 32, qg), 32 * kResW, 0, s>>>(m, n, A0, b, ldb, C, res32, nr);
+            k_resid<T, float><<<dim3((m + 31) / 32, qg), 32 * kResW, 0, s>>>(m, n, A0, b, ldb, C, res32, nr,
+                                                                              rband);
             DPM_LAUNCHED();
-            k_atb32<<<dim3(n, S, qg), kAtbT, 0, s>>>(m, n, f.A32, res32, m, ypart, nr, rows_per);
+            k_atb32<<<dim3(n, S, qg), kAtbT, 0, s>>>(m, n, A32, res32, m, ypart, nr, rows_per, cband);
         } else {
-            k_resid<T, double><<<dim3((m + 31) / 32, qg), 32 * kResW, 0, s>>>(m, n, A0, b, ldb, C, res, nr);
+            k_resid<T, double><<<dim3((m + 31) / 32, qg), 32 * kResW, 0, s>>>(m, n, A0, b, ldb, C, res, nr,
+                                                                               rband);
             DPM_LAUNCHED();
-            k_atb<<<dim3(n, S, qg), kAtbT, 0, s>>>(m, n, A0, res, m, ypart, nr, rows_per);
+            k_atb<<<dim3(n, S, qg), kAtbT, 0, s>>>(m, n, A0, res, m, ypart, nr, rows_per, cband);
         }
         DPM_LAUNCHED();
         DPM_RET(precondition(1));

@@ -270,7 +270,19 @@ def run_layers_uneven(ctx, steps: int = 200, seed: int = 0, precision=None, grou
         torch.cuda.synchronize()
         t_steps = time.perf_counter() - t0
         st = abi.dpm_ml_pks_step(pk, 0, True, stream=stream)
-        info = None
+        # device time per step by kernel family (the library's CUDA events)
+        nprof = 5
+        abi.dpm_profile_reset()
+        abi.dpm_profile_enable(True)
+        abi.dpm_ml_pks_step(pk, nprof, False, stream=stream)
+        torch.cuda.synchronize()
+        abi.dpm_profile_enable(False)
+        fam = {"ap_simt32": "ap_simt32", "ap_simt64": "ap_simt64", "tc": "tc_", "lsq": "lsq_",
+               "flux": "pks_flux", "diag": "pks_diag", "extend": "extend"}
+        device = {k: abi.dpm_profile_read(v)[0] / nprof for k, v in fam.items()}
+        device = {k: v for k, v in device.items() if v > 0}
+        device["all"] = abi.dpm_profile_read(None)[0] / nprof
+        abi.dpm_profile_reset()
         abi.dpm_ml_pks_destroy(pk)
     finally:
         if old is None:
@@ -280,7 +292,7 @@ def run_layers_uneven(ctx, steps: int = 200, seed: int = 0, precision=None, grou
     grid_pts = sum(N ** 3 for N, _, _ in grids)
     return {"radii": radii, "N": [g[0] for g in grids], "K": Ks, "KG": KG, "dt": dt, "steps": steps,
             "grouped": group, "first_step_with_build_s": t_build, "ms_per_step": 1e3 * t_steps / steps,
-            "aps_per_step": 4 * len(grids), "grid_pts_per_step": 4 * grid_pts,
+            "aps_per_step": 4 * len(grids), "grid_pts_per_step": 4 * grid_pts, "device_ms_per_step": device,
             "last": {"t": st.t, "max_rho": st.max_rho, "mass": st.mass, "free_energy": st.free_energy}}
 
 
