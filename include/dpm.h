@@ -569,6 +569,16 @@ int dpm_ml_pks_create(dpm_ctx *ctx, const dpm_ml_params *params, double chi, dou
                       int rebuild, int clamp, const dpm_gaussian *rho0, const dpm_gaussian *c0, dpm_ml_pks **out,
                       cudaStream_t stream);
 int dpm_ml_pks_step(dpm_ml_pks *pks, int nsteps, dpm_pks_stats *stats, cudaStream_t stream);
+/* Graph stepping of the layered loop, as dpm_pks_set_graph (Steps 3-7 of the
+ * main algorithm on every sub-domain, Section 3): dt from the CFL maxima of
+ * all grids by a kernel, every sub-domain's batched solves prepared once (the
+ * SIMT grids' right-hand sides as one group of launches), the whole step
+ * captured in one CUDA graph and replayed per step.  Same kernels and
+ * arithmetic as the default stepping.  Needs dt_mode 0, or rebuild = 1
+ * (DPM_EUNSUPPORTED otherwise); with dt_mode 0 and no rebuild the stacked BEP
+ * of sigma = 1/dt_max is built when graph stepping starts.  on = 0 returns to
+ * the default stepping (synchronises to read the time back). */
+int dpm_ml_pks_set_graph(dpm_ml_pks *pks, int on, cudaStream_t stream);
 int dpm_ml_pks_get_state(dpm_ml_pks *pks, int l, void *rho, void *c, cudaStream_t stream);
 int dpm_ml_pks_destroy(dpm_ml_pks *pks);
 

@@ -164,6 +164,7 @@ _SIGS = {
                                     C.c_int, C.POINTER(dpm_gaussian), C.POINTER(dpm_gaussian),
                                     C.POINTER(C.c_void_p), _P]),
     "dpm_ml_pks_step": (C.c_int, [_P, C.c_int, C.POINTER(dpm_pks_stats), _P]),
+    "dpm_ml_pks_set_graph": (C.c_int, [_P, C.c_int, _P]),
     "dpm_ml_pks_get_state": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "dpm_ml_pks_destroy": (C.c_int, [_P]),
     "dpm_launch_count": (C.c_int64, []),
@@ -578,6 +579,10 @@ def dpm_ml_pks_step(pks, nsteps=1, want_stats=True, stream=None):
     st = dpm_pks_stats()
     _check(lib().dpm_ml_pks_step(pks, nsteps, C.byref(st) if want_stats else None, _stream(stream)))
     return st if want_stats else None
+
+
+def dpm_ml_pks_set_graph(pks, on=True, stream=None):
+    _check(lib().dpm_ml_pks_set_graph(pks, 1 if on else 0, _stream(stream)))
 
 
 def dpm_ml_pks_get_state(pks, l, rho, c, stream=None):

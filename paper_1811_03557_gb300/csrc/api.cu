@@ -153,6 +153,85 @@ int run_ap_dev(int prec, ApParams p, const ApRhs<T> *desc_dev, int B, DevBuf &wo
     return DPM_OK;
 }
 
+// Device-resident time steps replayed as a CUDA graph (the decomposed loops):
+// the step's scalars (dt, sigma, t, step) live in `scal`; the first step runs
+// uncaptured so that every workspace, table and tuned tile it needs exists, the
+// second is captured on a private stream and instantiated, and every step after
+// that is one graph launch.
+struct GraphStepper {
+    int on = 0;
+    bool warm = false;
+    DevBuf scal;  // StepScalars
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cap = nullptr;
+    long long gkernels = 0;  // kernel launches per replay
+    GraphStepper() = default;
+    GraphStepper(const GraphStepper &) = delete;
+    GraphStepper &operator=(const GraphStepper &) = delete;
+    ~GraphStepper() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (cap) cudaStreamDestroy(cap);
+    }
+    StepScalars *sc() const { return scal.as<StepScalars>(); }
+    int push(double t, double dt_prev, int64_t step, int rebuilt, cudaStream_t s) {
+        if (!scal.p) DPM_RET(scal.alloc(sizeof(StepScalars)));
+        StepScalars h{};
+        h.t = t;
+        h.dt_prev = dt_prev;
+        h.step = step;
+        h.rebuilt = rebuilt;
+        DPM_CUDA(cudaMemcpyAsync(scal.p, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+        DPM_CUDA(cudaStreamSynchronize(s));
+        return DPM_OK;
+    }
+    int pull(double &t, double &dt_prev, int64_t &step, int &rebuilt, int *bad, cudaStream_t s) const {
+        StepScalars h{};
+        DPM_CUDA(cudaMemcpyAsync(&h, scal.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+        DPM_CUDA(cudaStreamSynchronize(s));
+        t = h.t;
+        dt_prev = h.dt;
+        step = h.step;
+        rebuilt = h.rebuilt;
+        if (bad) *bad = h.bad;
+        return DPM_OK;
+    }
+    template <class F> int step(F &&dev_step, cudaStream_t s) {
+        if (!gexec) {
+            if (!warm) {
+                DPM_RET(dev_step(s));
+                warm = true;
+                return DPM_OK;
+            }
+            if (!cap) DPM_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+            DPM_CUDA(cudaStreamSynchronize(s));  // the capture stream records only
+            cudaGraph_t g = nullptr;
+            DPM_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed));
+            const long long l0 = g_launches.load();
+            const int r = dev_step(cap);
+            const cudaError_t e = cudaStreamEndCapture(cap, &g);
+            gkernels = g_launches.load() - l0;
+            g_launches.fetch_sub(gkernels);  // counted when replayed
+            if (r != DPM_OK) {
+                if (g) cudaGraphDestroy(g);
+                return r;
+            }
+            DPM_CUDA(e);
+            const cudaError_t ie = cudaGraphInstantiate(&gexec, g, 0);
+            cudaGraphDestroy(g);
+            DPM_CUDA(ie);
+        }
+        DPM_CUDA(cudaGraphLaunch(gexec, s));
+        g_launches.fetch_add(gkernels);
+        return DPM_OK;
+    }
+    void stop() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+        warm = false;
+        on = 0;
+    }
+};
+
 template <class T>
 __global__ void k_neumann_rhs(int m, const T *trace0, const T *dgn, const int *gin_pos,
                               const T *trace1, T *b) {
@@ -1995,6 +2074,16 @@ struct dpm_ml {
     DevBuf coef, bvec, gwork, gitems;
 };
 
+// One batched solve of the device-resident layered step, prepared once: the
+// SIMT grids' right-hand sides as one group, the other grids' descriptors per
+// sub-domain.
+struct MlBatch {
+    DevBuf items;
+    int B = 0, maxN = 0;
+    DevBuf desc[DPM_ML_MAX];
+    int nb[DPM_ML_MAX] = {};
+};
+
 struct dpm_ml_pks {
     dpm_ml ml;
     double chi = 0, dt_max = 0;
@@ -2002,6 +2091,11 @@ struct dpm_ml_pks {
     double t = 0, dt_prev = 0;
     int64_t step = 0;
     int last_rebuilt = 0;
+    // device-resident steps replayed as a CUDA graph (dpm_ml_pks_set_graph):
+    // batch 0 the BEP columns + the particular solutions, 1 the particular
+    // solutions, 2 Green's formula
+    GraphStepper gs;
+    MlBatch batch[3];
 };
 
 namespace {
@@ -2051,6 +2145,22 @@ int ml_run(dpm_ml *d, const std::vector<ApParams> &prm, const std::vector<std::v
     }
     if (!gr.empty()) DPM_RET(ap_solve_simt_group<T>(gp, gr, gof, d->gwork, d->gitems, s));
     return DPM_OK;
+}
+
+// Extension operator (eq. extension_operator) onto sub-domain l's grid boundary: its
+// spheres' series, in FP32 sums for FP32 storage (the FP32 harmonic table is
+// built on first use), FP64 otherwise; densities at dens + q n, q < nr.
+template <class T>
+int ml_extend_sub(dpm_ml *d, int l, const double *C, const double *gn, T *dens, int nr, int clamp, cudaStream_t s) {
+    MLSub &sd = d->sub[l];
+    const int64_t n = sd.gi.n_gamma;
+    const float *phit = nullptr;
+    if (sizeof(T) == 4) {
+        DPM_RET(gamma_phi32(sd.gg, n, s));
+        phit = sd.gg.phi32.as<float>();
+    }
+    return ml_extend<T>(n, sd.gg.nsh, d->cm, sd.sphere.as<uint8_t>(), sd.gg.dist.as<double>(), sd.gg.phi.as<double>(),
+                        phit, l == 0 ? 1 : l, l + 1, C, d->ncol, gn, dens, (int)n, nr, clamp, s);
 }
 
 template <class T> int ml_init(dpm_ml *d, dpm_ctx *ctx, const dpm_ml_params &P, cudaStream_t s) {
@@ -2191,9 +2301,7 @@ int ml_solve(dpm_ml *d, const void *const *fv, const double *gn, void *const *uv
     DPM_RET(lsq_apply<T>(d->lsq, bv, (int)row0, C, 1, s));
     for (int l = 0; l < L; ++l) {
         MLSub &sd = d->sub[l];
-        const int64_t n = sd.gi.n_gamma;
-        DPM_RET(ml_extend<T>(n, sd.gg.nsh, d->cm, sd.sphere.as<uint8_t>(), sd.gg.dist.as<double>(), sd.gg.phi.as<double>(),
-                             C, d->ncol, l == L - 1 ? gn : nullptr, sd.dens.as<T>(), (int)n, 1, 0, s));
+        DPM_RET(ml_extend_sub<T>(d, l, C, l == L - 1 ? gn : nullptr, sd.dens.as<T>(), 1, 0, s));
         rhs[l] = {{static_cast<const T *>(fv[l]), sd.dens.as<T>(), static_cast<T *>(uv[l]), nullptr, 0, 0}};
     }
     DPM_RET(ml_run<T>(d, prm, rhs, s));
@@ -2341,8 +2449,7 @@ template <class T> int ml_pks_step(dpm_ml_pks *k, cudaStream_t s) {
         MLSub &sd = d->sub[l];
         const int64_t n = sd.gi.n_gamma;
         T *dn = sd.dens.as<T>();
-        DPM_RET(ml_extend<T>(n, sd.gg.nsh, d->cm, sd.sphere.as<uint8_t>(), sd.gg.dist.as<double>(), sd.gg.phi.as<double>(),
-                             C, d->ncol, nullptr, dn, (int)n, 2, k->clamp, s));
+        DPM_RET(ml_extend_sub<T>(d, l, C, nullptr, dn, 2, k->clamp, s));
         g[l] = {{sd.frho.as<T>(), dn, sd.rho.as<T>(), nullptr, 0, 0}, {sd.fc.as<T>(), dn + n, sd.c.as<T>(), nullptr, 0, 0}};
     }
     DPM_RET(ml_run<T>(d, prm, g, s));
@@ -2358,7 +2465,191 @@ template <class T> int ml_pks_step(dpm_ml_pks *k, cudaStream_t s) {
     return DPM_OK;
 }
 
+// The device-resident layered step (no host synchronisation, allocation or
+// copy: capturable).  Same kernels and arithmetic as ml_pks_step, with dt and
+// sigma on the device; the stacked BEP is rebuilt on every step unless dt is
+// fixed (dt_mode 0 without rebuild).
+template <class T> std::vector<ApRhs<T>> ml_part_rhs(MLSub &sd) {
+    const int64_t m = sd.gi.n_gin;
+    T *trp = sd.trace.as<T>() + (int64_t)sd.ncl * m;
+    return {{sd.frho.as<T>(), nullptr, nullptr, trp, 0, 0}, {sd.fc.as<T>(), nullptr, nullptr, trp + m, 0, 0}};
+}
+
+template <class T> std::vector<ApRhs<T>> ml_green_rhs(MLSub &sd) {
+    const int64_t n = sd.gi.n_gamma;
+    T *dn = sd.dens.as<T>();
+    return {{sd.frho.as<T>(), dn, sd.rho.as<T>(), nullptr, 0, 0}, {sd.fc.as<T>(), dn + n, sd.c.as<T>(), nullptr, 0, 0}};
+}
+
+bool ml_simt(const MLSub &sd) { return sd.prec == DPM_PREC_FP32 || sd.prec == DPM_PREC_FP64; }
+
+ApParams ml_ap_dev(const MLSub &sd, const StepScalars *sc) {
+    ApParams p = ml_ap(sd, 0.0);
+    p.sigma_dev = &sc->sigma;
+    p.fscale_dev = &sc->sigma;  // L_{h,dt} u = f  <=>  (1/dt - Lap_h) u = f/dt
+    return p;
+}
+
+template <class T> int ml_dev_setup(dpm_ml_pks *k, cudaStream_t s) {
+    dpm_ml *d = &k->ml;
+    const int L = (int)d->L;
+    DPM_RET(k->gs.push(k->t, k->dt_prev, k->step, k->last_rebuilt, s));
+    const StepScalars *sc = k->gs.sc();
+    std::vector<ApParams> prm(L);
+    for (int l = 0; l < L; ++l) prm[l] = ml_ap_dev(d->sub[l], sc);
+    const bool rebuild = k->dt_mode == 1 || k->rebuild;
+    std::vector<std::vector<ApRhs<T>>> rhs[3];
+    for (int kb = 0; kb < 3; ++kb) rhs[kb].resize(L);
+    for (int l = 0; l < L; ++l) {
+        MLSub &sd = d->sub[l];
+        const int64_t n = sd.gi.n_gamma, m = sd.gi.n_gin;
+        if (rebuild) {
+            for (int j = 0; j < sd.ncl; ++j)
+                rhs[0][l].push_back({nullptr, sd.psi.as<T>() + j * n, nullptr, sd.trace.as<T>() + j * m, 0, 0});
+            for (auto &e : ml_part_rhs<T>(sd)) rhs[0][l].push_back(e);
+        }
+        rhs[1][l] = ml_part_rhs<T>(sd);
+        rhs[2][l] = ml_green_rhs<T>(sd);
+    }
+    // the group workspace first (the prepared descriptors point into it)
+    std::vector<ApRhs<T>> gr[3];
+    std::vector<int> gof[3];
+    size_t gbytes = 0;
+    for (int kb = 0; kb < 3; ++kb) {
+        for (int l = 0; l < L; ++l)
+            if (ml_simt(d->sub[l]))
+                for (auto &e : rhs[kb][l]) {
+                    gr[kb].push_back(e);
+                    gof[kb].push_back(l);
+                }
+        gbytes = std::max(gbytes, ap_group_bytes<T>(prm, gof[kb]));
+    }
+    DPM_RET(d->gwork.reserve(std::max<size_t>(gbytes, 16)));
+    for (int kb = 0; kb < 3; ++kb) {
+        MlBatch &bt = k->batch[kb];
+        bt.B = (int)gr[kb].size();
+        DPM_RET(ap_group_build<T>(prm, gr[kb], gof[kb], d->gwork.p, bt.items, &bt.maxN, s));
+        for (int l = 0; l < L; ++l) {
+            MLSub &sd = d->sub[l];
+            bt.nb[l] = 0;
+            if (ml_simt(sd) || rhs[kb][l].empty()) continue;
+            const int B = (int)rhs[kb][l].size();
+            const size_t cube = (size_t)sd.N * sd.N * sd.N * sizeof(T) * ap_cubes_per_rhs(sd.prec, sd.N);
+            const size_t cb = std::max<size_t>(1, std::min<size_t>(B, kWorkCap / cube));
+            size_t extra = 0;
+            if (sd.prec == DPM_PREC_TC32) extra = tc_scratch_elems(prm[l], (int)cb) * sizeof(float);
+            DPM_RET(sd.work.reserve(cb * cube + extra));
+            DPM_RET(bt.desc[l].reserve(sizeof(ApRhs<T>) * B));
+            DPM_CUDA(cudaMemcpyAsync(bt.desc[l].p, rhs[kb][l].data(), sizeof(ApRhs<T>) * B, cudaMemcpyHostToDevice, s));
+            bt.nb[l] = B;
+        }
+    }
+    DPM_CUDA(cudaStreamSynchronize(s));  // the host descriptor vectors go out of scope
+    return DPM_OK;
+}
+
+template <class T> int ml_run_batch(dpm_ml_pks *k, int kb, cudaStream_t s) {
+    dpm_ml *d = &k->ml;
+    const MlBatch &bt = k->batch[kb];
+    DPM_RET(ap_group_launch<T>(bt.items.p, bt.B, bt.maxN, s));
+    for (int l = 0; l < (int)d->L; ++l) {
+        MLSub &sd = d->sub[l];
+        if (bt.nb[l])
+            DPM_RET(run_ap_dev<T>(sd.prec, ml_ap_dev(sd, k->gs.sc()), bt.desc[l].as<ApRhs<T>>(), bt.nb[l], sd.work, s));
+    }
+    return DPM_OK;
+}
+
+template <class T> int ml_step_dev(dpm_ml_pks *k, cudaStream_t s) {
+    dpm_ml *d = &k->ml;
+    const int L = (int)d->L;
+    StepScalars *sc = k->gs.sc();
+    StepGrids g;
+    g.n = L;
+    for (int l = 0; l < L; ++l) {
+        MLSub &sd = d->sub[l];
+        if (k->dt_mode == 1)
+            DPM_RET(pks_cfl<T>(sd.N, sd.gi.labels.as<uint8_t>(), sd.c.as<T>(), sd.gmax.as<unsigned long long>(), s));
+        g.gmax[l] = sd.gmax.as<unsigned long long>();
+        g.h[l] = sd.gi.h;
+    }
+    DPM_RET(pks_step_dt_grids(g, k->chi, k->dt_max, k->dt_mode, sc, s));
+    for (int l = 0; l < L; ++l) {
+        MLSub &sd = d->sub[l];
+        DPM_RET(pks_flux<T>(sd.N, sd.gi.h, k->chi, 0.0, &sc->dt, sd.gi.labels.as<uint8_t>(), sd.rho.as<T>(),
+                            sd.c.as<T>(), sd.frho.as<T>(), sd.fc.as<T>(), s));
+    }
+    const bool rebuild = k->dt_mode == 1 || k->rebuild;
+    const int64_t mtot = d->lsq.m;
+    DPM_RET(ml_run_batch<T>(k, rebuild ? 0 : 1, s));
+    if (rebuild) {
+        DPM_CUDA(cudaMemsetAsync(d->lsq.A.p, 0, sizeof(double) * mtot * d->ncol, s));
+        int64_t row0 = 0;
+        for (int l = 0; l < L; ++l) {
+            MLSub &sd = d->sub[l];
+            DPM_RET(ml_assemble<T>(sd.gi.n_gin, sd.ncl, mtot, row0, sd.cols.as<int>(), sd.psi_in.as<double>(),
+                                   sd.trace.as<T>(), d->lsq.A.as<double>(), s));
+            row0 += sd.gi.n_gin;
+        }
+        DPM_RET(lsq_factor_async(d->lsq, s));
+    }
+    T *bv = d->bvec.as<T>();
+    for (int f = 0; f < 2; ++f) {
+        int64_t row0 = 0;
+        for (int l = 0; l < L; ++l) {
+            MLSub &sd = d->sub[l];
+            const int64_t m = sd.gi.n_gin;
+            const T *trp = sd.trace.as<T>() + (int64_t)sd.ncl * m;
+            DPM_RET(ml_rhs<T>(m, trp + f * m, nullptr, nullptr, nullptr, bv + f * mtot + row0, s));
+            row0 += m;
+        }
+    }
+    double *C = d->coef.as<double>();
+    DPM_RET(lsq_apply<T>(d->lsq, bv, (int)mtot, C, 2, s));
+    for (int l = 0; l < L; ++l) DPM_RET(ml_extend_sub<T>(d, l, C, nullptr, d->sub[l].dens.as<T>(), 2, k->clamp, s));
+    DPM_RET(ml_run_batch<T>(k, 2, s));
+    for (int l = 0; l < L; ++l) {
+        MLSub &sd = d->sub[l];
+        DPM_RET(pks_diag<T>(sd.N, sd.gi.lo, sd.gi.h, sd.gi.labels.as<uint8_t>(), sd.rho.as<T>(), sd.c.as<T>(),
+                            sd.diag_part.as<double>(), sd.diag_out.as<double>(), s));
+    }
+    DPM_RET(pks_step_end(sc, rebuild ? 1 : 0, s));
+    return DPM_OK;
+}
+
 }  // namespace
+
+extern "C" int dpm_ml_pks_set_graph(dpm_ml_pks *k, int on, cudaStream_t s) {
+    if (!k) { set_error("pks is NULL"); return DPM_EINVAL; }
+    dpm_ml *d = &k->ml;
+    const bool f64 = d->storage == DPM_PREC_FP64;
+    if (on) {
+        if (k->dt_mode == 1 && !k->rebuild) {
+            set_error("graph steps need dt_mode 0 or rebuild = 1 (a rebuild only when dt decreases "
+                      "is a host decision)");
+            return DPM_EUNSUPPORTED;
+        }
+        if (k->gs.on) return DPM_OK;
+        DPM_CUDA(cudaSetDevice(d->ctx->device));
+        if (k->dt_mode == 0 && !k->rebuild && (!d->factored || d->sigma != 1.0 / k->dt_max)) {
+            // the fixed-dt step solves against the stacked BEP of sigma = 1/dt_max
+            const double sg = 1.0 / k->dt_max;
+            if (f64) DPM_RET(ml_build_bep<double>(d, sg, nullptr, sg, s));
+            else DPM_RET(ml_build_bep<float>(d, sg, nullptr, sg, s));
+        }
+        if (f64) DPM_RET(ml_dev_setup<double>(k, s));
+        else DPM_RET(ml_dev_setup<float>(k, s));
+        k->gs.on = 1;
+        return DPM_OK;
+    }
+    if (!k->gs.on) return DPM_OK;
+    int bad = 0;
+    DPM_RET(k->gs.pull(k->t, k->dt_prev, k->step, k->last_rebuilt, &bad, s));
+    k->gs.stop();
+    d->factored = true;
+    d->sigma = 1.0 / k->dt_prev;
+    return DPM_OK;
+}
 
 extern "C" int dpm_ml_pks_create(dpm_ctx *ctx, const dpm_ml_params *P, double chi, double dt_max, int dt_mode, int rebuild,
                                  int clamp, const dpm_gaussian *rho0, const dpm_gaussian *c0, dpm_ml_pks **out,
@@ -2399,9 +2690,18 @@ extern "C" int dpm_ml_pks_create(dpm_ctx *ctx, const dpm_ml_params *P, double ch
 
 extern "C" int dpm_ml_pks_step(dpm_ml_pks *k, int nsteps, dpm_pks_stats *stats, cudaStream_t s) {
     if (!k || nsteps < 0) { set_error("pks is NULL or nsteps < 0"); return DPM_EINVAL; }
+    const bool f64 = k->ml.storage == DPM_PREC_FP64;
     for (int i = 0; i < nsteps; ++i) {
-        if (k->ml.storage == DPM_PREC_FP64) DPM_RET(ml_pks_step<double>(k, s));
+        if (k->gs.on)
+            DPM_RET(k->gs.step([&](cudaStream_t st) { return f64 ? ml_step_dev<double>(k, st) : ml_step_dev<float>(k, st); }, s));
+        else if (f64) DPM_RET(ml_pks_step<double>(k, s));
         else DPM_RET(ml_pks_step<float>(k, s));
+    }
+    if (stats && k->gs.on) {
+        int bad = 0;
+        DPM_RET(k->gs.pull(k->t, k->dt_prev, k->step, k->last_rebuilt, &bad, s));
+        if (bad) { set_error("time step was not positive/finite on the device"); return DPM_ENUMERIC; }
+        if (k->last_rebuilt) DPM_RET(lsq_status(k->ml.lsq, s));
     }
     if (stats) {
         const int L = (int)k->ml.L;

@@ -7,6 +7,8 @@
 // ball's only one), with s = |x - c| - rho_m; column k = (sphere m, term t,
 // harmonic nu) has the density {1, s, s^2/2}[t] phi_nu (Gamma: {1, s^2/2}[t])
 // on the nodes of sphere m and zero elsewhere.
+#include <algorithm>
+
 #include "dpm_internal.cuh"
 
 namespace dpm {
@@ -60,6 +62,8 @@ __global__ void k_ml_assemble(int m, int ncl, int64_t mtot, int64_t row0, const 
 
 // u on the grid boundary from the coefficients (nr sets, stride ldc): one warp per
 // node over its sphere's series; + s g_N on Gamma nodes when gn is given; clamp.
+constexpr int kMlExtQ = 4;  // right-hand sides per pass over the FP32 table
+
 template <class T>
 __global__ void k_ml_extend(int n, int nsh, MlColumns cm, const uint8_t *sphere, const double *dist, const double *phi,
                             const double *C, int ldc, const double *gn, T *dens, int ldd, int nr, int clamp) {
@@ -85,6 +89,53 @@ __global__ void k_ml_extend(int n, int nsh, MlColumns cm, const uint8_t *sphere,
             if (clamp && u < 0.0) u = 0.0;
             dens[(size_t)q * ldd + e] = (T)u;
         }
+    }
+}
+
+// FP32 paths: one thread per grid-boundary node, its sphere's harmonics in
+// order from the transposed FP32 table (coalesced loads), the coefficients of
+// the block's spheres mlo..mhi converted to FP32 in shared memory; the three
+// series (two on Gamma) are summed separately in FP32 and combined in FP64,
+// as the single-domain extension does.
+template <class T>
+__global__ void k_ml_extend32(int n, MlColumns cm, int mlo, int mhi, const uint8_t *sphere, const double *dist,
+                              const float *__restrict__ phit, const double *__restrict__ C, int ldc,
+                              const double *gn, T *dens, int ldd, int nr, int clamp) {
+    extern __shared__ float cs32[];
+    const int c0 = cm.off[mlo - 1], ncs = cm.off[mhi] - c0;
+    for (int i = threadIdx.x; i < nr * ncs; i += blockDim.x) cs32[i] = (float)C[(size_t)(i / ncs) * ldc + c0 + i % ncs];
+    __syncthreads();
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const int m = sphere[g], nm = cm.n[m - 1], base = cm.off[m - 1] - c0;
+    const bool gam = m == cm.L;  // Gamma: u and d^2u/dn^2 only
+    const double d = dist[g];
+    for (int q0 = 0; q0 < nr; q0 += kMlExtQ) {
+        const int nq = min(kMlExtQ, nr - q0);
+        float s0[kMlExtQ] = {}, s1[kMlExtQ] = {}, s2[kMlExtQ] = {};
+        for (int nu = 0; nu < nm; ++nu) {
+            const float f = phit[(size_t)nu * n + g];
+#pragma unroll
+            for (int q = 0; q < kMlExtQ; ++q)
+                if (q < nq) {
+                    const float *cp = cs32 + (size_t)(q0 + q) * ncs + base;
+                    s0[q] = fmaf(cp[nu], f, s0[q]);
+                    if (gam) {
+                        s2[q] = fmaf(cp[nm + nu], f, s2[q]);
+                    } else {
+                        s1[q] = fmaf(cp[nm + nu], f, s1[q]);
+                        s2[q] = fmaf(cp[2 * nm + nu], f, s2[q]);
+                    }
+                }
+        }
+#pragma unroll
+        for (int q = 0; q < kMlExtQ; ++q)
+            if (q < nq) {
+                double u = (double)s0[q] + d * (double)s1[q] + 0.5 * d * d * (double)s2[q];
+                if (gam && gn) u += d * gn[g];
+                if (clamp && u < 0.0) u = 0.0;
+                dens[(size_t)(q0 + q) * ldd + g] = (T)u;
+            }
     }
 }
 
@@ -158,8 +209,22 @@ int ml_assemble(int64_t m, int ncl, int64_t mtot, int64_t row0, const int *cols,
 
 template <class T>
 int ml_extend(int64_t n, int nsh, const MlColumns &cm, const uint8_t *sphere, const double *dist, const double *phi,
-              const double *C, int ldc, const double *gn, T *dens, int ldd, int nr, int clamp, cudaStream_t s) {
+              const float *phit, int mlo, int mhi, const double *C, int ldc, const double *gn, T *dens, int ldd,
+              int nr, int clamp, cudaStream_t s) {
     if (n == 0) return DPM_OK;
+    if (phit && sizeof(T) == 4) {
+        // right-hand sides in groups whose FP32 coefficients fit in 48 KB of shared memory
+        const size_t per = sizeof(float) * (size_t)(cm.off[mhi] - cm.off[mlo - 1]);
+        const int grp = (int)std::max<size_t>(1, (48 * 1024) / std::max<size_t>(per, 1));
+        for (int q0 = 0; q0 < nr; q0 += grp) {
+            const int nq = std::min(grp, nr - q0);
+            k_ml_extend32<T><<<nblk(n, 128), 128, per * nq, s>>>((int)n, cm, mlo, mhi, sphere, dist, phit,
+                                                                 C + (size_t)q0 * ldc, ldc, gn,
+                                                                 dens + (size_t)q0 * ldd, ldd, nq, clamp);
+            DPM_LAUNCHED();
+        }
+        return DPM_OK;
+    }
     k_ml_extend<T><<<nblk(n * 32, 256), 256, 0, s>>>((int)n, nsh, cm, sphere, dist, phi, C, ldc, gn, dens, ldd, nr,
                                                      clamp);
     DPM_LAUNCHED();
@@ -188,7 +253,8 @@ int ml_rhs(int64_t m, const T *trp, const T *v, const int *gin_pos, const T *trv
     template int ml_assemble<T>(int64_t, int, int64_t, int64_t, const int *, const double *, const T *, double *, \
                                 cudaStream_t);                                                                   \
     template int ml_extend<T>(int64_t, int, const MlColumns &, const uint8_t *, const double *, const double *,    \
-                              const double *, int, const double *, T *, int, int, int, cudaStream_t);            \
+                              const float *, int, int, const double *, int, const double *, T *, int, int, int,  \
+                              cudaStream_t);                                                                     \
     template int ml_neumann<T>(int64_t, int, const uint8_t *, const double *, const double *, T *, cudaStream_t); \
     template int ml_rhs<T>(int64_t, const T *, const T *, const int *, const T *, T *, cudaStream_t);
 ML_INST(float)

@@ -206,6 +206,18 @@ int ap_solve_simt(const ApParams &p, const ApRhs<T> *rhs_dev, T *work, cudaStrea
 template <class T>
 int ap_solve_simt_group(const std::vector<ApParams> &probs, const std::vector<ApRhs<T>> &rhs,
                         const std::vector<int> &prob_of, DevBuf &work, DevBuf &items_dev, cudaStream_t s);
+// The same group prepared once for replays (a device-resident time step):
+// ap_group_bytes is the workspace the group needs; ap_group_build writes its
+// launch descriptors to items_dev (cubes at `work`, which must hold that many
+// bytes and stay in place), synchronising s; ap_group_launch runs the five
+// passes on them without any host copy or allocation (capturable).
+template <class T>
+size_t ap_group_bytes(const std::vector<ApParams> &probs, const std::vector<int> &prob_of);
+template <class T>
+int ap_group_build(const std::vector<ApParams> &probs, const std::vector<ApRhs<T>> &rhs,
+                   const std::vector<int> &prob_of, void *work, DevBuf &items_dev, int *maxN, cudaStream_t s);
+template <class T>
+int ap_group_launch(const void *items_dev, int B, int maxN, cudaStream_t s);
 // Tuned SIMT tile width for (N, FP64?, B) on the current device, 0 if none.
 int simt_tile_choice(int N, int f64, int B);
 // pre[c][e] for the ncol densities dens + c ng (see ApRhs::pre)
@@ -327,9 +339,13 @@ int ml_columns(int64_t n, int64_t m, int nsh, const MlColumns &cm, int ncl, cons
 template <class T>
 int ml_assemble(int64_t m, int ncl, int64_t mtot, int64_t row0, const int *cols, const double *psi_in, const T *trace,
                 double *A, cudaStream_t s);
+// u on the grid boundary of one sub-domain (spheres mlo..mhi) from the
+// coefficients; FP32 sums from the transposed FP32 table phit when given (T =
+// float), else FP64 from phi.
 template <class T>
 int ml_extend(int64_t n, int nsh, const MlColumns &cm, const uint8_t *sphere, const double *dist, const double *phi,
-              const double *C, int ldc, const double *gn, T *dens, int ldd, int nr, int clamp, cudaStream_t s);
+              const float *phit, int mlo, int mhi, const double *C, int ldc, const double *gn, T *dens, int ldd,
+              int nr, int clamp, cudaStream_t s);
 template <class T>
 int ml_neumann(int64_t n, int L, const uint8_t *sphere, const double *dist, const double *gn, T *v, cudaStream_t s);
 template <class T>
@@ -344,6 +360,15 @@ struct StepScalars {
 int pks_step_dt(const unsigned long long *gmax, double h, double chi, double dt_max, int mode,
                 StepScalars *sc, cudaStream_t s);
 int pks_step_end(StepScalars *sc, int rebuilt, cudaStream_t s);
+// dt from the CFL bounds of several grids (the decomposed loops): the smallest
+// over the grids and axes, as pks_step_dt takes it for one grid.
+constexpr int kMaxStepGrids = 16;
+struct StepGrids {
+    int n = 0;
+    const unsigned long long *gmax[kMaxStepGrids] = {};
+    double h[kMaxStepGrids] = {};
+};
+int pks_step_dt_grids(const StepGrids &g, double chi, double dt_max, int mode, StepScalars *sc, cudaStream_t s);
 
 constexpr int kLsqMaxRhs = 64;  // right-hand sides per lsq_apply call
 // Factor A (already in f.A, m x n col-major): R with R^T R = A^T A.
@@ -374,6 +399,9 @@ template <class T>
 int assemble_bep(const double *psi_in, const T *trace, double *A, int64_t m, int ncol,
                  const int *cond_flag, cudaStream_t s);
 // u_gamma[r][g] = sum phi C0 + d*gN + beta (d^2/2) sum phi C2 (+ clamp)
+// gg.phi32 = the FP32 table of the harmonics, transposed ([nu][node]), built
+// once on demand (the FP32 paths' extensions read it).
+int gamma_phi32(const GammaGeom &gg, int64_t n_gamma, cudaStream_t s);
 template <class T>
 int extend_density(const GammaGeom &gg, int64_t n_gamma, int beta, const double *C, int ldc,
                    const double *neumann, T *dens, int ldd, int nr, int clamp, cudaStream_t s);

@@ -762,6 +762,66 @@ int ap_solve_simt_group(const std::vector<ApParams> &probs, const std::vector<Ap
     }
     return DPM_OK;
 }
+template <class T>
+size_t ap_group_bytes(const std::vector<ApParams> &probs, const std::vector<int> &prob_of) {
+    size_t bytes = 0;
+    for (int pi : prob_of)
+        if (pi >= 0 && pi < (int)probs.size()) bytes += (size_t)probs[pi].N * probs[pi].N * probs[pi].N * sizeof(T);
+    return bytes;
+}
+
+template <class T>
+int ap_group_build(const std::vector<ApParams> &probs, const std::vector<ApRhs<T>> &rhs,
+                   const std::vector<int> &prob_of, void *work, DevBuf &items_dev, int *maxN, cudaStream_t s) {
+    const size_t B = rhs.size();
+    *maxN = 0;
+    if (B == 0) return DPM_OK;
+    if (prob_of.size() != B || B > 65535) {
+        set_error("grouped AP solve: one problem index per right-hand side, at most 65535");
+        return DPM_EINVAL;
+    }
+    std::vector<GroupItem<T>> items(B);
+    size_t off = 0;
+    for (size_t b = 0; b < B; ++b) {
+        const int pi = prob_of[b];
+        if (pi < 0 || pi >= (int)probs.size()) { set_error("grouped AP solve: bad problem index"); return DPM_EINVAL; }
+        const ApParams &p = probs[pi];
+        if (p.N < 2 || p.N > 256) { set_error("grouped AP solve: N=%d outside [2, 256]", p.N); return DPM_EINVAL; }
+        const T *tab = dst_fold_table<T>(p.N);
+        if (!tab) { set_error("grouped AP solve: could not create the DST table"); return DPM_ENOMEM; }
+        GroupItem<T> &g = items[b];
+        g.a = PassArgs{p.N, 1, p.h, p.sigma, p.fscale, p.sigma_dev, p.fscale_dev, p.cond_flag, p.mask_f,
+                       p.mask_out, p.labels, p.shell, p.shell_nb, p.rp_shell, p.gin, p.rp_gin};
+        g.r = rhs[b];
+        g.cube = reinterpret_cast<T *>(static_cast<char *>(work) + off);
+        g.tab = tab;
+        off += (size_t)p.N * p.N * p.N * sizeof(T);
+        *maxN = std::max(*maxN, p.N);
+    }
+    DPM_RET(items_dev.reserve(sizeof(GroupItem<T>) * B));
+    DPM_CUDA(cudaMemcpyAsync(items_dev.p, items.data(), sizeof(GroupItem<T>) * B, cudaMemcpyHostToDevice, s));
+    DPM_CUDA(cudaStreamSynchronize(s));  // `items` goes out of scope
+    return DPM_OK;
+}
+
+template <class T>
+int ap_group_launch(const void *items_dev, int B, int maxN, cudaStream_t s) {
+    if (B == 0) return DPM_OK;
+    const auto *d = static_cast<const GroupItem<T> *>(items_dev);
+    // the tile width rule of ap_solve_simt_group
+    if (maxN > 128) return simt_group_passes<T, 16>(d, B, maxN, s);
+    return simt_group_passes<T, 32>(d, B, maxN, s);
+}
+
+#define DPM_GROUP_INST(T)                                                                                         \
+    template size_t ap_group_bytes<T>(const std::vector<ApParams> &, const std::vector<int> &);                 \
+    template int ap_group_build<T>(const std::vector<ApParams> &, const std::vector<ApRhs<T>> &,                \
+                                   const std::vector<int> &, void *, DevBuf &, int *, cudaStream_t);            \
+    template int ap_group_launch<T>(const void *, int, int, cudaStream_t);
+DPM_GROUP_INST(float)
+DPM_GROUP_INST(double)
+#undef DPM_GROUP_INST
+
 template int ap_solve_simt_group<float>(const std::vector<ApParams> &, const std::vector<ApRhs<float>> &,
                                         const std::vector<int> &, DevBuf &, DevBuf &, cudaStream_t);
 template int ap_solve_simt_group<double>(const std::vector<ApParams> &, const std::vector<ApRhs<double>> &,

@@ -416,6 +416,17 @@ template int assemble_bep<float>(const double *, const float *, double *, int64_
 template int assemble_bep<double>(const double *, const double *, double *, int64_t, int,
                                   const int *, cudaStream_t);
 
+int gamma_phi32(const GammaGeom &gg, int64_t n_gamma, cudaStream_t s) {
+    GammaGeom &g = const_cast<GammaGeom &>(gg);
+    const size_t elems = (size_t)n_gamma * gg.nsh;
+    if (elems == 0 || g.phi32.bytes >= elems * sizeof(float)) return DPM_OK;
+    DPM_RET(g.phi32.alloc(elems * sizeof(float)));
+    k_phi32t<<<blocks_for((int64_t)elems, 256), 256, 0, s>>>((int)n_gamma, gg.nsh, gg.phi.as<double>(),
+                                                              g.phi32.as<float>());
+    DPM_LAUNCHED();
+    return DPM_OK;
+}
+
 template <class T>
 int extend_density(const GammaGeom &gg, int64_t n_gamma, int beta, const double *C, int ldc,
                    const double *neumann, T *dens, int ldd, int nr, int clamp, cudaStream_t s) {
@@ -423,14 +434,8 @@ int extend_density(const GammaGeom &gg, int64_t n_gamma, int beta, const double 
     int64_t threads = n_gamma * 32;
     const unsigned blocks = (unsigned)((threads + 255) / 256);
     if (sizeof(T) == 4) {
-        GammaGeom &g = const_cast<GammaGeom &>(gg);
-        const size_t elems = (size_t)n_gamma * gg.nsh;
-        if (g.phi32.bytes < elems * sizeof(float)) {
-            DPM_RET(g.phi32.alloc(elems * sizeof(float)));
-            k_phi32t<<<blocks_for((int64_t)elems, 256), 256, 0, s>>>((int)n_gamma, gg.nsh, gg.phi.as<double>(),
-                                                                      g.phi32.as<float>());
-            DPM_LAUNCHED();
-        }
+        const GammaGeom &g = gg;
+        DPM_RET(gamma_phi32(gg, n_gamma, s));
         // right-hand sides in groups whose FP32 coefficients fit in 48 KB of shared memory
         const size_t per = sizeof(float) * (size_t)(beta ? 2 : 1) * gg.nsh;
         const int grp = (int)std::max<size_t>(1, (48 * 1024) / per);
@@ -493,6 +498,25 @@ __global__ void k_step_dt(const unsigned long long *gmax, double h, double chi, 
     sc->sigma = 1.0 / dt;
 }
 
+__global__ void k_step_dt_grids(StepGrids g, double chi, double dt_max, int mode, StepScalars *sc) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double dt = dt_max;
+    if (mode == 1) {
+        for (int l = 0; l < g.n; ++l)
+            for (int ax = 0; ax < 3; ++ax) {
+                const double gm = __longlong_as_double((long long)g.gmax[l][ax]) / g.h[l];
+                if (gm > 0) dt = fmin(dt, g.h[l] / (6.0 * chi * gm));
+            }
+        if (sc->step > 0) dt = fmin(dt, sc->dt_prev);
+    }
+    if (!(dt > 0) || !isfinite(dt)) {
+        sc->bad = 1;
+        dt = dt_max;
+    }
+    sc->dt = dt;
+    sc->sigma = 1.0 / dt;
+}
+
 __global__ void k_step_end(StepScalars *sc, int rebuilt) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     sc->t += sc->dt;
@@ -504,6 +528,13 @@ __global__ void k_step_end(StepScalars *sc, int rebuilt) {
 int pks_step_dt(const unsigned long long *gmax, double h, double chi, double dt_max, int mode,
                 StepScalars *sc, cudaStream_t s) {
     k_step_dt<<<1, 32, 0, s>>>(gmax, h, chi, dt_max, mode, sc);
+    DPM_LAUNCHED();
+    return DPM_OK;
+}
+
+int pks_step_dt_grids(const StepGrids &g, double chi, double dt_max, int mode, StepScalars *sc, cudaStream_t s) {
+    if (g.n < 1 || g.n > kMaxStepGrids) { set_error("step dt: 1..%d grids", kMaxStepGrids); return DPM_EINVAL; }
+    k_step_dt_grids<<<1, 32, 0, s>>>(g, chi, dt_max, mode, sc);
     DPM_LAUNCHED();
     return DPM_OK;
 }

@@ -235,13 +235,15 @@ def layered_uneven_config(seed: int = 0, n_shells: int = 7, r_ball: float = 0.4,
     return radii, grids, Ks, 8
 
 
-def run_layers_uneven(ctx, steps: int = 200, seed: int = 0, precision=None, group: bool = True, stream=None):
+def run_layers_uneven(ctx, steps: int = 200, seed: int = 0, precision=None, group: bool = True,
+                      graph: bool = True, stream=None):
     """PKS steps of Test (A)'s data on the uneven-box layered decomposition
     (ball + 7 shells of different N, all sub-domain solves of the SIMT grids in
-    one grouped set of launches per batch).  dt: 0.9 x the CFL bound of the
+    one grouped set of launches per batch; with `graph`, every step one CUDA
+    graph replay of the device-resident step).  dt: 0.9 x the CFL bound of the
     initial c on the finest grid (max |grad c0| = 5000 e^{-1/2}), fixed, so the
-    stacked BEP is built once.  Returns the sizes, the build time and the time
-    per step."""
+    stacked BEP is built once.  Returns the sizes, the build time, the time per
+    step and the device time per step by kernel family (host-driven steps)."""
     import os
 
     import torch
@@ -265,11 +267,17 @@ def run_layers_uneven(ctx, steps: int = 200, seed: int = 0, precision=None, grou
         abi.dpm_ml_pks_step(pk, 1, False, stream=stream)  # Steps 1-2 (the stacked BEP) + the first step
         torch.cuda.synchronize()
         t_build = time.perf_counter() - t0
+        if graph:
+            abi.dpm_ml_pks_set_graph(pk, True, stream=stream)
+            abi.dpm_ml_pks_step(pk, 2, False, stream=stream)  # the uncaptured step, the capture
+            torch.cuda.synchronize()
         t0 = time.perf_counter()
         abi.dpm_ml_pks_step(pk, steps, False, stream=stream)
         torch.cuda.synchronize()
         t_steps = time.perf_counter() - t0
         st = abi.dpm_ml_pks_step(pk, 0, True, stream=stream)
+        if graph:
+            abi.dpm_ml_pks_set_graph(pk, False, stream=stream)
         # device time per step by kernel family (the library's CUDA events)
         nprof = 5
         abi.dpm_profile_reset()
@@ -291,7 +299,7 @@ def run_layers_uneven(ctx, steps: int = 200, seed: int = 0, precision=None, grou
             os.environ["DPM_DD_GROUP"] = old
     grid_pts = sum(N ** 3 for N, _, _ in grids)
     return {"radii": radii, "N": [g[0] for g in grids], "K": Ks, "KG": KG, "dt": dt, "steps": steps,
-            "grouped": group, "first_step_with_build_s": t_build, "ms_per_step": 1e3 * t_steps / steps,
+            "grouped": group, "graph": graph, "first_step_with_build_s": t_build, "ms_per_step": 1e3 * t_steps / steps,
             "aps_per_step": 4 * len(grids), "grid_pts_per_step": 4 * grid_pts, "device_ms_per_step": device,
             "last": {"t": st.t, "max_rho": st.max_rho, "mass": st.mass, "free_energy": st.free_energy}}
 
@@ -427,7 +435,8 @@ def main(argv=None):
     a = ap.parse_args(argv)
     ctx = abi.dpm_ctx_create(0)
     if a.layers:
-        out = [run_layers_uneven(ctx, group=g) for g in (True, False)]
+        out = [run_layers_uneven(ctx, group=True, graph=True), run_layers_uneven(ctx, group=True, graph=False),
+               run_layers_uneven(ctx, group=False, graph=False)]
         abi.dpm_ctx_destroy(ctx)
         print(json.dumps(out))
         return

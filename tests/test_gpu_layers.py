@@ -161,3 +161,70 @@ def test_grouped_launch_matches_separate(ctx):
             del os.environ["DPM_DD_GROUP"]
     for a, b in zip(*states):
         assert np.array_equal(a, b)
+
+
+def _ml_states(pk, Ns, dt):
+    out = []
+    for l, N in enumerate(Ns):
+        rho = torch.empty(N ** 3, dtype=dt, device="cuda")
+        c = torch.empty_like(rho)
+        abi.dpm_ml_pks_get_state(pk, l, rho, c)
+        out.append((rho, c))
+    torch.cuda.synchronize()
+    return [(r.cpu().numpy(), c.cpu().numpy()) for r, c in out]
+
+
+@pytest.mark.parametrize("prec,dt_mode,rebuild", [(abi.DPM_PREC_FP64, 0, 0), (abi.DPM_PREC_FP64, 1, 1),
+                                                  (abi.DPM_PREC_FP32, 0, 0), (abi.DPM_PREC_FP32, 1, 1)])
+def test_graph_steps_match_host_steps_and_oracle(ctx, prec, dt_mode, rebuild):
+    """The layered loop's device-resident steps replayed as a CUDA graph give
+    the host-driven steps' state bit for bit (same kernels, same arithmetic; dt
+    and sigma read from device memory), in fixed-dt mode and in CFL mode with
+    the stacked BEP rebuilt every step; in FP64 also the oracle's at 1e-11.
+    (The FP32 loop's own distance from the oracle grows with the steps on this
+    coupled problem -- max rho 3e-7, 2.4e-6, 6.7e-6, 1.1e-5 after steps 1-4 --
+    and is checked over three steps by test_time_loop_matches_oracle.)"""
+    radii, Ns = [0.2, 0.35, 0.5], [20, 24, 28]
+    g = grids(radii, Ns)
+    h = min((hi - lo) / (N + 1) for N, lo, hi in g)
+    rho0, c0 = Gaussian(200.0, 20.0), Gaussian(100.0, 10.0)
+    P = abi.ml_params((0.0, 0.0, 0.0), radii, g, [2, 2], 2, prec)
+    dt = torch.float64 if prec == abi.DPM_PREC_FP64 else torch.float32
+    nsteps = 4
+    runs = []
+    for graph in (False, True):
+        pk = abi.dpm_ml_pks_create(ctx, P, 1.0, 0.5 * h * h, dt_mode, rebuild, 1, rho0, c0)
+        try:
+            if graph:
+                abi.dpm_ml_pks_set_graph(pk, True)
+            abi.dpm_ml_pks_step(pk, nsteps, False)
+            s = abi.dpm_ml_pks_step(pk, 0, True)
+            runs.append((s, _ml_states(pk, Ns, dt)))
+            if graph:
+                with pytest.raises(abi.DPMError):
+                    bad = abi.dpm_ml_pks_create(ctx, P, 1.0, 0.5 * h * h, 1, 0, 1, rho0, c0)
+                    try:
+                        abi.dpm_ml_pks_set_graph(bad, True)
+                    finally:
+                        abi.dpm_ml_pks_destroy(bad)
+                abi.dpm_ml_pks_set_graph(pk, False)
+                s2 = abi.dpm_ml_pks_step(pk, 1, True)  # back on host stepping
+                assert s2.step == nsteps + 1
+        finally:
+            abi.dpm_ml_pks_destroy(pk)
+    (sh, xh), (sg, xg) = runs
+    assert sg.step == sh.step == nsteps and sg.t == sh.t and sg.dt == sh.dt
+    for (rh, ch), (rg, cg) in zip(xh, xg):
+        for a, b in ((rh, rg), (ch, cg)):
+            rel = np.max(np.abs(a - b)) / np.max(np.abs(a))
+            print(f"layered graph vs host steps prec={prec} dt_mode={dt_mode}: max rel diff {rel:.2e}")
+            assert rel == 0.0, rel
+    if prec != abi.DPM_PREC_FP64:
+        return
+    st = O.MLPKSState((0.0, 0.0, 0.0), radii, g, [2, 2], 2, 1.0, 0.5 * h * h, rho0, c0,
+                      dt_mode="fixed" if dt_mode == 0 else "cfl")
+    for _ in range(nsteps):
+        st.step()
+    d = st.diagnostics()
+    for key in ("mass", "max_rho", "free_energy"):
+        assert abs(getattr(sg, key) - d[key]) <= TOL[prec] * abs(d[key]), (key, getattr(sg, key), d[key])
