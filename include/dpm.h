@@ -311,10 +311,12 @@ int dpm_pks_step(dpm_pks *pks, int nsteps, dpm_pks_stats *stats, cudaStream_t st
  * step in a CUDA graph (on its own capture stream, after one uncaptured step
  * that sizes the workspaces) and replays it on `stream` for each step.  Same
  * kernels and arithmetic as the default stepping, so the results are the
- * same.  Needs dt_mode 0, or rebuild = 1 (a rebuild only when dt decreases is
- * a host decision): DPM_EUNSUPPORTED otherwise.  on = 0 returns to the
- * default stepping (synchronises to read the time back).  The pivot status of
- * the factorisations is checked when statistics are requested.
+ * same.  The BEP is rebuilt every step with rebuild = 1, never with dt_mode 0
+ * (the BEP of sigma = 1/dt_max), and with dt_mode 1 and rebuild = 0 only when
+ * dt decreases (Step 4b): a conditional (if/else) graph node whose condition
+ * a kernel sets from the step's dt.  on = 0 returns to the default stepping
+ * (synchronises to read the time back).  The pivot status of the
+ * factorisations is checked when statistics are requested.
  */
 int dpm_pks_set_graph(dpm_pks *pks, int on, cudaStream_t stream);
 int dpm_pks_get_state(dpm_pks *pks, void *rho, void *c, cudaStream_t stream);
@@ -574,10 +576,11 @@ int dpm_ml_pks_step(dpm_ml_pks *pks, int nsteps, dpm_pks_stats *stats, cudaStrea
  * all grids by a kernel, every sub-domain's batched solves prepared once (the
  * SIMT grids' right-hand sides as one group of launches), the whole step
  * captured in one CUDA graph and replayed per step.  Same kernels and
- * arithmetic as the default stepping.  Needs dt_mode 0, or rebuild = 1
- * (DPM_EUNSUPPORTED otherwise); with dt_mode 0 and no rebuild the stacked BEP
- * of sigma = 1/dt_max is built when graph stepping starts.  on = 0 returns to
- * the default stepping (synchronises to read the time back). */
+ * arithmetic as the default stepping; the stacked BEP is rebuilt as
+ * dpm_pks_set_graph rebuilds it (with dt_mode 1 and rebuild = 0 only when dt
+ * decreases, by a conditional graph node); with dt_mode 0 and no rebuild the
+ * stacked BEP of sigma = 1/dt_max is built when graph stepping starts.  on = 0
+ * returns to the default stepping (synchronises to read the time back). */
 int dpm_ml_pks_set_graph(dpm_ml_pks *pks, int on, cudaStream_t stream);
 int dpm_ml_pks_get_state(dpm_ml_pks *pks, int l, void *rho, void *c, cudaStream_t stream);
 int dpm_ml_pks_destroy(dpm_ml_pks *pks);

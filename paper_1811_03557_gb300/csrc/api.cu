@@ -164,6 +164,7 @@ struct GraphStepper {
     DevBuf scal;  // StepScalars
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t cap = nullptr;
+    cudaStream_t aux = nullptr;  // captures the bodies of conditional nodes
     long long gkernels = 0;  // kernel launches per replay
     GraphStepper() = default;
     GraphStepper(const GraphStepper &) = delete;
@@ -171,15 +172,17 @@ struct GraphStepper {
     ~GraphStepper() {
         if (gexec) cudaGraphExecDestroy(gexec);
         if (cap) cudaStreamDestroy(cap);
+        if (aux) cudaStreamDestroy(aux);
     }
     StepScalars *sc() const { return scal.as<StepScalars>(); }
-    int push(double t, double dt_prev, int64_t step, int rebuilt, cudaStream_t s) {
+    int push(double t, double dt_prev, int64_t step, int rebuilt, int need_build, cudaStream_t s) {
         if (!scal.p) DPM_RET(scal.alloc(sizeof(StepScalars)));
         StepScalars h{};
         h.t = t;
         h.dt_prev = dt_prev;
         h.step = step;
         h.rebuilt = rebuilt;
+        h.need_build = need_build;
         DPM_CUDA(cudaMemcpyAsync(scal.p, &h, sizeof(h), cudaMemcpyHostToDevice, s));
         DPM_CUDA(cudaStreamSynchronize(s));
         return DPM_OK;
@@ -231,6 +234,45 @@ struct GraphStepper {
         on = 0;
     }
 };
+
+// Step 4b inside a captured step: an if/else conditional graph node whose
+// condition a kernel sets from sc->rebuild_now (dt decreased, or no factor for
+// the current sigma yet); `yes` (the rebuild) and `no` are captured into its
+// two bodies on `aux`.  Uncaptured (the warm-up step) `yes` runs: a rebuild at
+// an unchanged sigma reproduces the factor it replaces, bit for bit.  The
+// launch count of a replay is taken with both bodies (an upper bound).
+template <class Y, class N>
+int step_branch(const StepScalars *sc, cudaStream_t s, cudaStream_t &aux, Y &&yes, N &&no) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    cudaGraph_t graph = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    DPM_CUDA(cudaStreamGetCaptureInfo(s, &st, nullptr, &graph, &deps, nullptr, &nd));
+    if (st != cudaStreamCaptureStatusActive) return yes(s);
+    cudaGraphConditionalHandle h;
+    DPM_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 0, 0));
+    DPM_RET(pks_set_rebuild_cond(h, sc, s));
+    DPM_CUDA(cudaStreamGetCaptureInfo(s, &st, nullptr, &graph, &deps, nullptr, &nd));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 2;
+    cudaGraphNode_t node = nullptr;
+    DPM_CUDA(cudaGraphAddNode(&node, graph, deps, nullptr, nd, &cp));
+    if (!aux) DPM_CUDA(cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+        DPM_CUDA(cudaStreamBeginCaptureToGraph(aux, cp.conditional.phGraph_out[b], nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeRelaxed));
+        const int r = b == 0 ? yes(aux) : no(aux);
+        cudaGraph_t body = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(aux, &body);
+        DPM_RET(r);
+        DPM_CUDA(e);
+    }
+    DPM_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return DPM_OK;
+}
 
 template <class T>
 __global__ void k_neumann_rhs(int m, const T *trace0, const T *dgn, const int *gin_pos,
@@ -286,10 +328,12 @@ struct dpm_pks {
     DevBuf desc_rb, desc_green;      // ApRhs: ncol BEP columns + 2 particular; 2 Green's
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t cap = nullptr;      // capture stream
+    cudaStream_t aux = nullptr;      // captures the bodies of the Step 4b conditional node
     int64_t gkernels = 0;            // kernel nodes per replay
     ~dpm_pks() {
         if (gexec) cudaGraphExecDestroy(gexec);
         if (cap) cudaStreamDestroy(cap);
+        if (aux) cudaStreamDestroy(aux);
     }
 };
 
@@ -800,8 +844,10 @@ template <class T> int pks_step_one(dpm_pks *k, cudaStream_t s) {
 
 // One PKS step with dt, sigma and the time kept on the device: no host
 // synchronisation, no allocation and no host copy, so it can be captured in
-// a CUDA graph.  Same kernels and arithmetic as pks_step_one; the BEP is
-// rebuilt on every step unless dt is fixed (dt_mode 0 without rebuild).
+// a CUDA graph.  Same kernels and arithmetic as pks_step_one.  The BEP is
+// rebuilt on every step with rebuild = 1, never with a fixed dt (dt_mode 0),
+// and with the CFL dt (dt_mode 1) when dt decreases (Step 4b): a conditional
+// graph node that a kernel switches from the step's dt.
 template <class T> int pks_step_dev(dpm_pks *k, cudaStream_t s) {
     dpm_bep *b = &k->bep;
     const dpm_pks_params &P = k->prm;
@@ -814,20 +860,25 @@ template <class T> int pks_step_dev(dpm_pks *k, cudaStream_t s) {
     DPM_RET(pks_step_dt(k->gmax.as<unsigned long long>(), h, P.chi, P.dt_max, P.dt_mode, sc, s));
     T *frho = k->frho.as<T>(), *fc = k->fc.as<T>();
     DPM_RET(pks_flux<T>(N, h, P.chi, 0.0, &sc->dt, lab, k->rho.as<T>(), k->c.as<T>(), frho, fc, s));
-    const bool rebuild = P.dt_mode == 1 || P.rebuild;
+    const bool cond = P.dt_mode == 1 && !P.rebuild;  // Step 4b decided on the device
+    const bool rebuild = P.rebuild != 0;
     ApParams p = base_params(b, 0.0);
     p.sigma_dev = &sc->sigma;
     p.fscale_dev = &sc->sigma;  // L_{h,dt} u = f  <=>  (1/dt - Lap_h) u = f/dt
     const int64_t m = b->gi.n_gin, ng = b->gi.n_gamma;
     const ApRhs<T> *rb = k->desc_rb.as<ApRhs<T>>();
-    if (rebuild) {
-        DPM_RET(run_ap_dev<T>(b->prec, p, rb, b->ncol + 2, b->work, s));
+    auto with_rebuild = [&](cudaStream_t st) -> int {
+        DPM_RET(run_ap_dev<T>(b->prec, p, rb, b->ncol + 2, b->work, st));
         DPM_RET(assemble_bep<T>(b->psi_in.as<double>(), b->trace.as<T>(), b->lsq.A.as<double>(), m,
-                                b->ncol, nullptr, s));
-        DPM_RET(lsq_factor_async(b->lsq, s));
-    } else {
-        DPM_RET(run_ap_dev<T>(b->prec, p, rb + b->ncol, 2, b->work, s));
-    }
+                                b->ncol, nullptr, st));
+        return lsq_factor_async(b->lsq, st);
+    };
+    auto particular_only = [&](cudaStream_t st) -> int {
+        return run_ap_dev<T>(b->prec, p, rb + b->ncol, 2, b->work, st);
+    };
+    if (cond) DPM_RET(step_branch(sc, s, k->aux, with_rebuild, particular_only));
+    else if (rebuild) DPM_RET(with_rebuild(s));
+    else DPM_RET(particular_only(s));
     double *C = b->coef.as<double>();
     T *tr0 = b->trace.as<T>() + (int64_t)b->ncol * m;
     DPM_RET(lsq_apply<T>(b->lsq, tr0, (int)m, C, 2, s));
@@ -836,7 +887,7 @@ template <class T> int pks_step_dev(dpm_pks *k, cudaStream_t s) {
     DPM_RET(run_ap_dev<T>(b->prec, p, k->desc_green.as<ApRhs<T>>(), 2, b->work, s));
     DPM_RET(pks_diag<T>(N, b->gi.lo, h, lab, k->rho.as<T>(), k->c.as<T>(), k->diag_part.as<double>(),
                         k->diag_out.as<double>(), s));
-    DPM_RET(pks_step_end(sc, rebuild ? 1 : 0, s));
+    DPM_RET(pks_step_end(sc, cond ? -1 : (rebuild ? 1 : 0), s));
     return DPM_OK;
 }
 
@@ -879,6 +930,8 @@ template <class T> int pks_dev_setup(dpm_pks *k, cudaStream_t s) {
     h.dt_prev = k->dt_prev;
     h.step = k->step;
     h.rebuilt = k->last_rebuilt;
+    // a factor for sigma = 1/dt_prev exists: Step 4b rebuilds only when dt decreases
+    h.need_build = (b->factored && k->dt_prev > 0 && b->sigma == 1.0 / k->dt_prev) ? 0 : 1;
     DPM_CUDA(cudaMemcpyAsync(k->scal.p, &h, sizeof(h), cudaMemcpyHostToDevice, s));
     DPM_CUDA(cudaStreamSynchronize(s));
     return DPM_OK;
@@ -987,11 +1040,6 @@ extern "C" int dpm_pks_set_graph(dpm_pks *k, int on, cudaStream_t s) {
     if (!k) { set_error("pks is NULL"); return DPM_EINVAL; }
     const dpm_pks_params &P = k->prm;
     if (on) {
-        if (P.dt_mode == 1 && !P.rebuild) {
-            set_error("graph steps need dt_mode 0 or rebuild = 1 (a rebuild only when dt decreases "
-                      "is a host decision)");
-            return DPM_EUNSUPPORTED;
-        }
         if (k->graph_on) return DPM_OK;
         DPM_CUDA(cudaSetDevice(k->ctx->device));
         dpm_bep *b = &k->bep;
@@ -2493,11 +2541,12 @@ ApParams ml_ap_dev(const MLSub &sd, const StepScalars *sc) {
 template <class T> int ml_dev_setup(dpm_ml_pks *k, cudaStream_t s) {
     dpm_ml *d = &k->ml;
     const int L = (int)d->L;
-    DPM_RET(k->gs.push(k->t, k->dt_prev, k->step, k->last_rebuilt, s));
+    const int need = (d->factored && k->dt_prev > 0 && d->sigma == 1.0 / k->dt_prev) ? 0 : 1;
+    DPM_RET(k->gs.push(k->t, k->dt_prev, k->step, k->last_rebuilt, need, s));
     const StepScalars *sc = k->gs.sc();
     std::vector<ApParams> prm(L);
     for (int l = 0; l < L; ++l) prm[l] = ml_ap_dev(d->sub[l], sc);
-    const bool rebuild = k->dt_mode == 1 || k->rebuild;
+    const bool rebuild = k->dt_mode == 1 || k->rebuild;  // batch 0 is needed
     std::vector<std::vector<ApRhs<T>>> rhs[3];
     for (int kb = 0; kb < 3; ++kb) rhs[kb].resize(L);
     for (int l = 0; l < L; ++l) {
@@ -2579,20 +2628,25 @@ template <class T> int ml_step_dev(dpm_ml_pks *k, cudaStream_t s) {
         DPM_RET(pks_flux<T>(sd.N, sd.gi.h, k->chi, 0.0, &sc->dt, sd.gi.labels.as<uint8_t>(), sd.rho.as<T>(),
                             sd.c.as<T>(), sd.frho.as<T>(), sd.fc.as<T>(), s));
     }
-    const bool rebuild = k->dt_mode == 1 || k->rebuild;
+    const bool cond = k->dt_mode == 1 && !k->rebuild;  // Step 4b decided on the device
+    const bool rebuild = k->rebuild != 0;
     const int64_t mtot = d->lsq.m;
-    DPM_RET(ml_run_batch<T>(k, rebuild ? 0 : 1, s));
-    if (rebuild) {
-        DPM_CUDA(cudaMemsetAsync(d->lsq.A.p, 0, sizeof(double) * mtot * d->ncol, s));
+    auto with_rebuild = [&](cudaStream_t st) -> int {
+        DPM_RET(ml_run_batch<T>(k, 0, st));
+        DPM_CUDA(cudaMemsetAsync(d->lsq.A.p, 0, sizeof(double) * mtot * d->ncol, st));
         int64_t row0 = 0;
         for (int l = 0; l < L; ++l) {
             MLSub &sd = d->sub[l];
             DPM_RET(ml_assemble<T>(sd.gi.n_gin, sd.ncl, mtot, row0, sd.cols.as<int>(), sd.psi_in.as<double>(),
-                                   sd.trace.as<T>(), d->lsq.A.as<double>(), s));
+                                   sd.trace.as<T>(), d->lsq.A.as<double>(), st));
             row0 += sd.gi.n_gin;
         }
-        DPM_RET(lsq_factor_async(d->lsq, s));
-    }
+        return lsq_factor_async(d->lsq, st);
+    };
+    auto particular_only = [&](cudaStream_t st) -> int { return ml_run_batch<T>(k, 1, st); };
+    if (cond) DPM_RET(step_branch(sc, s, k->gs.aux, with_rebuild, particular_only));
+    else if (rebuild) DPM_RET(with_rebuild(s));
+    else DPM_RET(particular_only(s));
     T *bv = d->bvec.as<T>();
     for (int f = 0; f < 2; ++f) {
         int64_t row0 = 0;
@@ -2613,7 +2667,7 @@ template <class T> int ml_step_dev(dpm_ml_pks *k, cudaStream_t s) {
         DPM_RET(pks_diag<T>(sd.N, sd.gi.lo, sd.gi.h, sd.gi.labels.as<uint8_t>(), sd.rho.as<T>(), sd.c.as<T>(),
                             sd.diag_part.as<double>(), sd.diag_out.as<double>(), s));
     }
-    DPM_RET(pks_step_end(sc, rebuild ? 1 : 0, s));
+    DPM_RET(pks_step_end(sc, cond ? -1 : (rebuild ? 1 : 0), s));
     return DPM_OK;
 }
 
@@ -2624,11 +2678,6 @@ extern "C" int dpm_ml_pks_set_graph(dpm_ml_pks *k, int on, cudaStream_t s) {
     dpm_ml *d = &k->ml;
     const bool f64 = d->storage == DPM_PREC_FP64;
     if (on) {
-        if (k->dt_mode == 1 && !k->rebuild) {
-            set_error("graph steps need dt_mode 0 or rebuild = 1 (a rebuild only when dt decreases "
-                      "is a host decision)");
-            return DPM_EUNSUPPORTED;
-        }
         if (k->gs.on) return DPM_OK;
         DPM_CUDA(cudaSetDevice(d->ctx->device));
         if (k->dt_mode == 0 && !k->rebuild && (!d->factored || d->sigma != 1.0 / k->dt_max)) {

@@ -356,10 +356,16 @@ struct StepScalars {
     double dt, sigma, t, dt_prev;
     long long step;
     int rebuilt, bad;  // bad: a non-positive / non-finite dt was replaced by dt_max
+    // Step 4b on the device: rebuild_now = need_build or dt < dt_prev (set with
+    // dt); need_build = no factor for the current sigma yet (cleared by a rebuild)
+    int rebuild_now, need_build;
 };
 int pks_step_dt(const unsigned long long *gmax, double h, double chi, double dt_max, int mode,
                 StepScalars *sc, cudaStream_t s);
+// rebuilt < 0: the step's rebuild flag is the device's rebuild_now.
 int pks_step_end(StepScalars *sc, int rebuilt, cudaStream_t s);
+// The condition of a conditional graph node (captured steps): rebuild_now.
+int pks_set_rebuild_cond(cudaGraphConditionalHandle h, const StepScalars *sc, cudaStream_t s);
 // dt from the CFL bounds of several grids (the decomposed loops): the smallest
 // over the grids and axes, as pks_step_dt takes it for one grid.
 constexpr int kMaxStepGrids = 16;

@@ -494,6 +494,7 @@ __global__ void k_step_dt(const unsigned long long *gmax, double h, double chi, 
         sc->bad = 1;
         dt = dt_max;
     }
+    sc->rebuild_now = (sc->need_build || dt < sc->dt_prev) ? 1 : 0;
     sc->dt = dt;
     sc->sigma = 1.0 / dt;
 }
@@ -513,6 +514,7 @@ __global__ void k_step_dt_grids(StepGrids g, double chi, double dt_max, int mode
         sc->bad = 1;
         dt = dt_max;
     }
+    sc->rebuild_now = (sc->need_build || dt < sc->dt_prev) ? 1 : 0;
     sc->dt = dt;
     sc->sigma = 1.0 / dt;
 }
@@ -522,7 +524,12 @@ __global__ void k_step_end(StepScalars *sc, int rebuilt) {
     sc->t += sc->dt;
     sc->dt_prev = sc->dt;
     sc->step += 1;
-    sc->rebuilt = rebuilt;
+    sc->rebuilt = rebuilt < 0 ? sc->rebuild_now : rebuilt;
+    if (sc->rebuilt) sc->need_build = 0;
+}
+
+__global__ void k_rebuild_cond(cudaGraphConditionalHandle h, const StepScalars *sc) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(h, sc->rebuild_now ? 1u : 0u);
 }
 
 int pks_step_dt(const unsigned long long *gmax, double h, double chi, double dt_max, int mode,
@@ -535,6 +542,12 @@ int pks_step_dt(const unsigned long long *gmax, double h, double chi, double dt_
 int pks_step_dt_grids(const StepGrids &g, double chi, double dt_max, int mode, StepScalars *sc, cudaStream_t s) {
     if (g.n < 1 || g.n > kMaxStepGrids) { set_error("step dt: 1..%d grids", kMaxStepGrids); return DPM_EINVAL; }
     k_step_dt_grids<<<1, 32, 0, s>>>(g, chi, dt_max, mode, sc);
+    DPM_LAUNCHED();
+    return DPM_OK;
+}
+
+int pks_set_rebuild_cond(cudaGraphConditionalHandle h, const StepScalars *sc, cudaStream_t s) {
+    k_rebuild_cond<<<1, 32, 0, s>>>(h, sc);
     DPM_LAUNCHED();
     return DPM_OK;
 }
