@@ -410,6 +410,15 @@ int dpm_dd_pks_create(dpm_ctx *ctx, const dpm_dd_params *params, double chi, dou
                       int dt_mode, int rebuild, int clamp, const dpm_gaussian *rho0,
                       const dpm_gaussian *c0, dpm_dd_pks **out, cudaStream_t stream);
 int dpm_dd_pks_step(dpm_dd_pks *pks, int nsteps, dpm_pks_stats *stats, cudaStream_t stream);
+/* Graph stepping of the Case 1 loop, as dpm_ml_pks_set_graph (Steps 3-7 of the
+ * main algorithm on both sub-domains, Section 3): dt on the device, the
+ * batched solves of both grids prepared once, the step captured in one CUDA
+ * graph and replayed; the stacked BEP rebuilt as dpm_pks_set_graph rebuilds it
+ * (with dt_mode 1 and rebuild = 0 only when dt decreases).  Same kernels and
+ * arithmetic as the default stepping.  With dt_mode 0 and no rebuild the BEP is
+ * built when graph stepping starts, so the first step then reports rebuilt = 0.
+ * on = 0 returns to the default stepping. */
+int dpm_dd_pks_set_graph(dpm_dd_pks *pks, int on, cudaStream_t stream);
 /* State of sub-domain l (0: ball, 1: shell) into device [N_l^3] arrays. */
 int dpm_dd_pks_get_state(dpm_dd_pks *pks, int l, void *rho, void *c, cudaStream_t stream);
 int dpm_dd_pks_destroy(dpm_dd_pks *pks);
@@ -505,6 +514,9 @@ int dpm_dd2_pks_create(dpm_ctx *ctx, const dpm_dd2_params *params, double chi, d
                        int dt_mode, int rebuild, int clamp, const dpm_gaussian *rho0,
                        const dpm_gaussian *c0, dpm_dd2_pks **out, cudaStream_t stream);
 int dpm_dd2_pks_step(dpm_dd2_pks *pks, int nsteps, dpm_pks_stats *stats, cudaStream_t stream);
+/* Graph stepping of the Case 2 loop (Section 3, eq. reduced_DD2_BEP), as
+ * dpm_dd_pks_set_graph. */
+int dpm_dd2_pks_set_graph(dpm_dd2_pks *pks, int on, cudaStream_t stream);
 int dpm_dd2_pks_get_state(dpm_dd2_pks *pks, int l, void *rho, void *c, cudaStream_t stream);
 int dpm_dd2_pks_destroy(dpm_dd2_pks *pks);
 

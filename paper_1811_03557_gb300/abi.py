@@ -141,6 +141,7 @@ _SIGS = {
                                     C.c_int, C.c_int, C.POINTER(dpm_gaussian), C.POINTER(dpm_gaussian),
                                     C.POINTER(C.c_void_p), _P]),
     "dpm_dd_pks_step": (C.c_int, [_P, C.c_int, C.POINTER(dpm_pks_stats), _P]),
+    "dpm_dd_pks_set_graph": (C.c_int, [_P, C.c_int, _P]),
     "dpm_dd_pks_get_state": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "dpm_dd_pks_destroy": (C.c_int, [_P]),
     "dpm_dd2_build": (C.c_int, [_P, C.POINTER(dpm_dd2_params), C.c_double, C.POINTER(C.c_void_p), _P]),
@@ -153,6 +154,7 @@ _SIGS = {
                                      C.c_int, C.c_int, C.POINTER(dpm_gaussian), C.POINTER(dpm_gaussian),
                                      C.POINTER(C.c_void_p), _P]),
     "dpm_dd2_pks_step": (C.c_int, [_P, C.c_int, C.POINTER(dpm_pks_stats), _P]),
+    "dpm_dd2_pks_set_graph": (C.c_int, [_P, C.c_int, _P]),
     "dpm_dd2_pks_get_state": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "dpm_dd2_pks_destroy": (C.c_int, [_P]),
     "dpm_ml_build": (C.c_int, [_P, C.POINTER(dpm_ml_params), C.c_double, C.POINTER(C.c_void_p), _P]),
@@ -430,6 +432,10 @@ def dpm_dd_pks_step(pks, nsteps=1, want_stats=True, stream=None):
     return st if want_stats else None
 
 
+def dpm_dd_pks_set_graph(pks, on=True, stream=None):
+    _check(lib().dpm_dd_pks_set_graph(pks, 1 if on else 0, _stream(stream)))
+
+
 def dpm_dd_pks_get_state(pks, l, rho, c, stream=None):
     _check(lib().dpm_dd_pks_get_state(pks, l, _ptr(rho), _ptr(c), _stream(stream)))
 
@@ -511,6 +517,10 @@ def dpm_dd2_pks_step(pks, nsteps=1, want_stats=True, stream=None):
     st = dpm_pks_stats()
     _check(lib().dpm_dd2_pks_step(pks, nsteps, C.byref(st) if want_stats else None, _stream(stream)))
     return st if want_stats else None
+
+
+def dpm_dd2_pks_set_graph(pks, on=True, stream=None):
+    _check(lib().dpm_dd2_pks_set_graph(pks, 1 if on else 0, _stream(stream)))
 
 
 def dpm_dd2_pks_get_state(pks, l, rho, c, stream=None):

@@ -274,6 +274,80 @@ int step_branch(const StepScalars *sc, cudaStream_t s, cudaStream_t &aux, Y &&ye
     return DPM_OK;
 }
 
+// The batched solves of a decomposed device-resident step, prepared once: per
+// batch, the SIMT grids' right-hand sides as one group (descriptors in
+// `items`, cubes in the shared group workspace) and every other grid's
+// descriptors on its own (run_ap_dev on the grid's workspace).
+struct PreparedBatch {
+    DevBuf items;
+    int B = 0, maxN = 0;
+    DevBuf desc[DPM_ML_MAX];
+    int nb[DPM_ML_MAX] = {};
+};
+
+// One sub-domain's solver: precision, parameters (sigma read from the device)
+// and workspace.
+struct SubSolve {
+    int prec = 0;
+    ApParams p;
+    DevBuf *work = nullptr;
+};
+
+inline bool simt_prec(int prec) { return prec == DPM_PREC_FP32 || prec == DPM_PREC_FP64; }
+
+// rhs[b][l]: batch b's right-hand sides of sub-domain l.  The group workspace is
+// sized for the largest batch before any descriptor is built (they point into
+// it); synchronises s.
+template <class T>
+int prepare_batches(const std::vector<SubSolve> &subs, const std::vector<std::vector<std::vector<ApRhs<T>>>> &rhs,
+                    PreparedBatch *bt, DevBuf &gwork, cudaStream_t s) {
+    const int L = (int)subs.size(), nbat = (int)rhs.size();
+    if (L > DPM_ML_MAX) { set_error("prepared solves: at most %d sub-domains", DPM_ML_MAX); return DPM_EINVAL; }
+    std::vector<ApParams> prm(L);
+    for (int l = 0; l < L; ++l) prm[l] = subs[l].p;
+    std::vector<std::vector<ApRhs<T>>> gr(nbat);
+    std::vector<std::vector<int>> gof(nbat);
+    size_t gbytes = 0;
+    for (int b = 0; b < nbat; ++b) {
+        for (int l = 0; l < L; ++l)
+            if (simt_prec(subs[l].prec))
+                for (auto &e : rhs[b][l]) {
+                    gr[b].push_back(e);
+                    gof[b].push_back(l);
+                }
+        gbytes = std::max(gbytes, ap_group_bytes<T>(prm, gof[b]));
+    }
+    DPM_RET(gwork.reserve(std::max<size_t>(gbytes, 16)));
+    for (int b = 0; b < nbat; ++b) {
+        PreparedBatch &pb = bt[b];
+        pb.B = (int)gr[b].size();
+        DPM_RET(ap_group_build<T>(prm, gr[b], gof[b], gwork.p, pb.items, &pb.maxN, s));
+        for (int l = 0; l < L; ++l) {
+            pb.nb[l] = 0;
+            if (simt_prec(subs[l].prec) || rhs[b][l].empty()) continue;
+            const int B = (int)rhs[b][l].size();
+            const int N = prm[l].N;
+            const size_t cube = (size_t)N * N * N * sizeof(T) * ap_cubes_per_rhs(subs[l].prec, N);
+            const size_t cb = std::max<size_t>(1, std::min<size_t>(B, kWorkCap / cube));
+            size_t extra = 0;
+            if (subs[l].prec == DPM_PREC_TC32) extra = tc_scratch_elems(prm[l], (int)cb) * sizeof(float);
+            DPM_RET(subs[l].work->reserve(cb * cube + extra));
+            DPM_RET(pb.desc[l].reserve(sizeof(ApRhs<T>) * B));
+            DPM_CUDA(cudaMemcpyAsync(pb.desc[l].p, rhs[b][l].data(), sizeof(ApRhs<T>) * B, cudaMemcpyHostToDevice, s));
+            pb.nb[l] = B;
+        }
+    }
+    DPM_CUDA(cudaStreamSynchronize(s));  // the host descriptor vectors go out of scope
+    return DPM_OK;
+}
+
+template <class T> int run_prepared(const PreparedBatch &pb, const std::vector<SubSolve> &subs, cudaStream_t s) {
+    DPM_RET(ap_group_launch<T>(pb.items.p, pb.B, pb.maxN, s));
+    for (int l = 0; l < (int)subs.size(); ++l)
+        if (pb.nb[l]) DPM_RET(run_ap_dev<T>(subs[l].prec, subs[l].p, pb.desc[l].as<ApRhs<T>>(), pb.nb[l], *subs[l].work, s));
+    return DPM_OK;
+}
+
 template <class T>
 __global__ void k_neumann_rhs(int m, const T *trace0, const T *dgn, const int *gin_pos,
                               const T *trace1, T *b) {
@@ -1162,6 +1236,12 @@ struct dpm_dd_pks {
     double t = 0, dt_prev = 0;
     int64_t step = 0;
     int last_rebuilt = 0;
+    // device-resident steps replayed as a CUDA graph (dpm_dd_pks_set_graph):
+    // batch 0 the BEP columns + the particular solutions, 1 the particular
+    // solutions, 2 Green's formula
+    GraphStepper gs;
+    PreparedBatch batch[3];
+    std::vector<SubSolve> subs;
 };
 
 namespace {
@@ -1490,6 +1570,127 @@ template <class T> int dd_pks_step(dpm_dd_pks *k, cudaStream_t s) {
 
 }  // namespace
 
+namespace {
+
+// The device-resident Case 1 step (no host synchronisation, allocation or
+// copy: capturable).  Same kernels and arithmetic as dd_pks_step, with dt and
+// sigma on the device; the stacked BEP rebuilt every step with rebuild = 1,
+// never with dt_mode 0, and when dt decreases (a conditional graph node) with
+// the CFL dt otherwise.
+template <class T> int dd_dev_setup(dpm_dd_pks *k, cudaStream_t s) {
+    dpm_dd *d = &k->dd;
+    const int need = (d->factored && k->dt_prev > 0 && d->sigma == 1.0 / k->dt_prev) ? 0 : 1;
+    DPM_RET(k->gs.push(k->t, k->dt_prev, k->step, k->last_rebuilt, need, s));
+    const StepScalars *sc = k->gs.sc();
+    k->subs.assign(2, SubSolve{});
+    std::vector<std::vector<std::vector<ApRhs<T>>>> rhs(3, std::vector<std::vector<ApRhs<T>>>(2));
+    const bool rebuild = k->dt_mode == 1 || k->rebuild;  // batch 0 is needed
+    for (int l = 0; l < 2; ++l) {
+        DDSub &sd = d->sub[l];
+        ApParams p = dd_params(sd, 0.0);
+        p.sigma_dev = &sc->sigma;
+        p.fscale_dev = &sc->sigma;  // L_{h,dt} u = f  <=>  (1/dt - Lap_h) u = f/dt
+        k->subs[l] = {sd.prec, p, &sd.work};
+        const int64_t n = sd.gi.n_gamma, m = sd.gi.n_gin;
+        T *trp = sd.trace.as<T>() + (int64_t)sd.ncol_l * m, *dn = sd.dens.as<T>();
+        std::vector<ApRhs<T>> part = {{sd.frho.as<T>(), nullptr, nullptr, trp, 0, 0},
+                                      {sd.fc.as<T>(), nullptr, nullptr, trp + m, 0, 0}};
+        if (rebuild) {
+            for (int j = 0; j < sd.ncol_l; ++j)
+                rhs[0][l].push_back({nullptr, sd.psi.as<T>() + j * n, nullptr, sd.trace.as<T>() + j * m, 0, 0});
+            for (auto &e : part) rhs[0][l].push_back(e);
+        }
+        rhs[1][l] = part;
+        rhs[2][l] = {{sd.frho.as<T>(), dn, sd.rho.as<T>(), nullptr, 0, 0},
+                     {sd.fc.as<T>(), dn + n, sd.c.as<T>(), nullptr, 0, 0}};
+    }
+    return prepare_batches<T>(k->subs, rhs, k->batch, d->gwork, s);
+}
+
+template <class T> int dd_step_dev(dpm_dd_pks *k, cudaStream_t s) {
+    dpm_dd *d = &k->dd;
+    StepScalars *sc = k->gs.sc();
+    StepGrids g;
+    g.n = 2;
+    for (int l = 0; l < 2; ++l) {
+        DDSub &sd = d->sub[l];
+        if (k->dt_mode == 1)
+            DPM_RET(pks_cfl<T>(sd.N, sd.gi.labels.as<uint8_t>(), sd.c.as<T>(), sd.gmax.as<unsigned long long>(), s));
+        g.gmax[l] = sd.gmax.as<unsigned long long>();
+        g.h[l] = sd.gi.h;
+    }
+    DPM_RET(pks_step_dt_grids(g, k->chi, k->dt_max, k->dt_mode, sc, s));
+    T *trp[2];
+    for (int l = 0; l < 2; ++l) {
+        DDSub &sd = d->sub[l];
+        DPM_RET(pks_flux<T>(sd.N, sd.gi.h, k->chi, 0.0, &sc->dt, sd.gi.labels.as<uint8_t>(), sd.rho.as<T>(),
+                            sd.c.as<T>(), sd.frho.as<T>(), sd.fc.as<T>(), s));
+        trp[l] = sd.trace.as<T>() + (int64_t)sd.ncol_l * sd.gi.n_gin;
+    }
+    const bool cond = k->dt_mode == 1 && !k->rebuild;  // Step 4b decided on the device
+    const bool rebuild = k->rebuild != 0;
+    auto with_rebuild = [&](cudaStream_t st) -> int {
+        DPM_RET(run_prepared<T>(k->batch[0], k->subs, st));
+        DPM_RET(dd_assemble<T>(d->sub[0].gi.n_gin, d->sub[1].gi.n_gin, 3 * d->nz, d->ncol,
+                               d->sub[0].psi_in.as<double>(), d->sub[0].trace.as<T>(),
+                               d->sub[1].psi_in.as<double>(), d->sub[1].trace.as<T>(), d->lsq.A.as<double>(), st));
+        return lsq_factor_async(d->lsq, st);
+    };
+    auto particular_only = [&](cudaStream_t st) -> int { return run_prepared<T>(k->batch[1], k->subs, st); };
+    if (cond) DPM_RET(step_branch(sc, s, k->gs.aux, with_rebuild, particular_only));
+    else if (rebuild) DPM_RET(with_rebuild(s));
+    else DPM_RET(particular_only(s));
+    const int64_t m1 = d->sub[0].gi.n_gin, m2 = d->sub[1].gi.n_gin, m = m1 + m2;
+    T *bv = d->bvec.as<T>();
+    for (int f = 0; f < 2; ++f)
+        DPM_RET(dd_rhs<T>(m1, m2, trp[0] + f * m1, trp[1] + f * m2, nullptr, nullptr, nullptr, bv + f * m, s));
+    double *C = d->coef.as<double>();
+    DPM_RET(lsq_apply<T>(d->lsq, bv, (int)m, C, 2, s));
+    for (int l = 0; l < 2; ++l) {
+        DDSub &sd = d->sub[l];
+        const int64_t n = sd.gi.n_gamma;
+        DPM_RET(dd_extend<T>(n, sd.gg.nsh, d->nz, d->ng, sd.gg.phi.as<double>(), sd.gg.dist.as<double>(),
+                             sd.surf.as<uint8_t>(), C, d->ncol, nullptr, sd.dens.as<T>(), (int)n, 2, k->clamp, s));
+    }
+    DPM_RET(run_prepared<T>(k->batch[2], k->subs, s));
+    for (int l = 0; l < 2; ++l) {
+        DDSub &sd = d->sub[l];
+        DPM_RET(pks_diag<T>(sd.N, sd.gi.lo, sd.gi.h, sd.gi.labels.as<uint8_t>(), sd.rho.as<T>(), sd.c.as<T>(),
+                            sd.diag_part.as<double>(), sd.diag_out.as<double>(), s));
+    }
+    DPM_RET(pks_step_end(sc, cond ? -1 : (rebuild ? 1 : 0), s));
+    return DPM_OK;
+}
+
+}  // namespace
+
+extern "C" int dpm_dd_pks_set_graph(dpm_dd_pks *k, int on, cudaStream_t s) {
+    if (!k) { set_error("pks is NULL"); return DPM_EINVAL; }
+    dpm_dd *d = &k->dd;
+    const bool f64 = d->storage == DPM_PREC_FP64;
+    if (on) {
+        if (k->gs.on) return DPM_OK;
+        DPM_CUDA(cudaSetDevice(d->ctx->device));
+        if (k->dt_mode == 0 && !k->rebuild && (!d->factored || d->sigma != 1.0 / k->dt_max)) {
+            // the fixed-dt step solves against the stacked BEP of sigma = 1/dt_max
+            const double sg = 1.0 / k->dt_max;
+            if (f64) DPM_RET(dd_build_bep<double>(d, sg, nullptr, sg, s));
+            else DPM_RET(dd_build_bep<float>(d, sg, nullptr, sg, s));
+        }
+        if (f64) DPM_RET(dd_dev_setup<double>(k, s));
+        else DPM_RET(dd_dev_setup<float>(k, s));
+        k->gs.on = 1;
+        return DPM_OK;
+    }
+    if (!k->gs.on) return DPM_OK;
+    int bad = 0;
+    DPM_RET(k->gs.pull(k->t, k->dt_prev, k->step, k->last_rebuilt, &bad, s));
+    k->gs.stop();
+    d->factored = true;
+    d->sigma = 1.0 / k->dt_prev;
+    return DPM_OK;
+}
+
 extern "C" int dpm_dd_pks_create(dpm_ctx *ctx, const dpm_dd_params *P, double chi, double dt_max,
                                  int dt_mode, int rebuild, int clamp, const dpm_gaussian *rho0,
                                  const dpm_gaussian *c0, dpm_dd_pks **out, cudaStream_t s) {
@@ -1529,9 +1730,18 @@ extern "C" int dpm_dd_pks_create(dpm_ctx *ctx, const dpm_dd_params *P, double ch
 
 extern "C" int dpm_dd_pks_step(dpm_dd_pks *k, int nsteps, dpm_pks_stats *stats, cudaStream_t s) {
     if (!k || nsteps < 0) { set_error("pks is NULL or nsteps < 0"); return DPM_EINVAL; }
+    const bool f64 = k->dd.storage == DPM_PREC_FP64;
     for (int i = 0; i < nsteps; ++i) {
-        if (k->dd.storage == DPM_PREC_FP64) DPM_RET(dd_pks_step<double>(k, s));
+        if (k->gs.on)
+            DPM_RET(k->gs.step([&](cudaStream_t st) { return f64 ? dd_step_dev<double>(k, st) : dd_step_dev<float>(k, st); }, s));
+        else if (f64) DPM_RET(dd_pks_step<double>(k, s));
         else DPM_RET(dd_pks_step<float>(k, s));
+    }
+    if (stats && k->gs.on) {
+        int bad = 0;
+        DPM_RET(k->gs.pull(k->t, k->dt_prev, k->step, k->last_rebuilt, &bad, s));
+        if (bad) { set_error("time step was not positive/finite on the device"); return DPM_ENUMERIC; }
+        if (k->last_rebuilt) DPM_RET(lsq_status(k->dd.lsq, s));
     }
     if (stats) {
         double d[2][6];
@@ -1613,6 +1823,10 @@ struct dpm_dd2_pks {
     double t = 0, dt_prev = 0;
     int64_t step = 0;
     int last_rebuilt = 0;
+    // device-resident steps replayed as a CUDA graph (dpm_dd2_pks_set_graph)
+    GraphStepper gs;
+    PreparedBatch batch[3];
+    std::vector<SubSolve> subs;
 };
 
 namespace {
@@ -2011,6 +2225,133 @@ template <class T> int dd2_pks_step(dpm_dd2_pks *k, cudaStream_t s) {
 
 }  // namespace
 
+namespace {
+
+// The device-resident Case 2 step, as dd_step_dev for Case 1 (same kernels and
+// arithmetic as dd2_pks_step; dt and sigma on the device).
+template <class T> int dd2_dev_setup(dpm_dd2_pks *k, cudaStream_t s) {
+    dpm_dd2 *d = &k->dd;
+    const int need = (d->factored && k->dt_prev > 0 && d->sigma == 1.0 / k->dt_prev) ? 0 : 1;
+    DPM_RET(k->gs.push(k->t, k->dt_prev, k->step, k->last_rebuilt, need, s));
+    const StepScalars *sc = k->gs.sc();
+    k->subs.assign(2, SubSolve{});
+    std::vector<std::vector<std::vector<ApRhs<T>>>> rhs(3, std::vector<std::vector<ApRhs<T>>>(2));
+    const bool rebuild = k->dt_mode == 1 || k->rebuild;  // batch 0 is needed
+    for (int l = 0; l < 2; ++l) {
+        DD2Sub &sd = d->sub[l];
+        ApParams p = dd2_ap(sd, 0.0);
+        p.sigma_dev = &sc->sigma;
+        p.fscale_dev = &sc->sigma;  // L_{h,dt} u = f  <=>  (1/dt - Lap_h) u = f/dt
+        k->subs[l] = {sd.prec, p, &sd.work};
+        const int64_t n = sd.gi.n_gamma, g = sd.gi.n_gin;
+        T *trp = sd.trace.as<T>() + (int64_t)d->ncol * g, *dn = sd.dens.as<T>();
+        std::vector<ApRhs<T>> part = {{sd.frho.as<T>(), nullptr, nullptr, trp, 0, 0},
+                                      {sd.fc.as<T>(), nullptr, nullptr, trp + g, 0, 0}};
+        if (rebuild) {
+            for (int j = 0; j < d->ncol; ++j)
+                rhs[0][l].push_back({nullptr, sd.psi.as<T>() + j * n, nullptr, sd.trace.as<T>() + j * g, 0, 0});
+            for (auto &e : part) rhs[0][l].push_back(e);
+        }
+        rhs[1][l] = part;
+        rhs[2][l] = {{sd.frho.as<T>(), dn, sd.rho.as<T>(), nullptr, 0, 0},
+                     {sd.fc.as<T>(), dn + n, sd.c.as<T>(), nullptr, 0, 0}};
+    }
+    return prepare_batches<T>(k->subs, rhs, k->batch, d->gwork, s);
+}
+
+template <class T> int dd2_step_dev(dpm_dd2_pks *k, cudaStream_t s) {
+    dpm_dd2 *d = &k->dd;
+    StepScalars *sc = k->gs.sc();
+    StepGrids gr;
+    gr.n = 2;
+    for (int l = 0; l < 2; ++l) {
+        DD2Sub &sd = d->sub[l];
+        if (k->dt_mode == 1)
+            DPM_RET(pks_cfl<T>(sd.N, sd.gi.labels.as<uint8_t>(), sd.c.as<T>(), sd.gmax.as<unsigned long long>(), s));
+        gr.gmax[l] = sd.gmax.as<unsigned long long>();
+        gr.h[l] = sd.gi.h;
+    }
+    DPM_RET(pks_step_dt_grids(gr, k->chi, k->dt_max, k->dt_mode, sc, s));
+    T *trp[2];
+    for (int l = 0; l < 2; ++l) {
+        DD2Sub &sd = d->sub[l];
+        DPM_RET(pks_flux<T>(sd.N, sd.gi.h, k->chi, 0.0, &sc->dt, sd.gi.labels.as<uint8_t>(), sd.rho.as<T>(),
+                            sd.c.as<T>(), sd.frho.as<T>(), sd.fc.as<T>(), s));
+        trp[l] = sd.trace.as<T>() + (int64_t)d->ncol * sd.gi.n_gin;
+    }
+    const bool cond = k->dt_mode == 1 && !k->rebuild;  // Step 4b decided on the device
+    const bool rebuild = k->rebuild != 0;
+    auto with_rebuild = [&](cudaStream_t st) -> int {
+        DPM_RET(run_prepared<T>(k->batch[0], k->subs, st));
+        const DD2Sub &a = d->sub[0], &b = d->sub[1];
+        DPM_RET(dd2_assemble<T>(a.n_rows, b.n_rows, d->ncol, a.own.as<double>(), a.trace.as<T>(), a.gi.n_gin,
+                                a.row_i.as<int>(), b.own.as<double>(), b.trace.as<T>(), b.gi.n_gin,
+                                b.row_i.as<int>(), d->lsq.A.as<double>(), st));
+        return lsq_factor_async(d->lsq, st);
+    };
+    auto particular_only = [&](cudaStream_t st) -> int { return run_prepared<T>(k->batch[1], k->subs, st); };
+    if (cond) DPM_RET(step_branch(sc, s, k->gs.aux, with_rebuild, particular_only));
+    else if (rebuild) DPM_RET(with_rebuild(s));
+    else DPM_RET(particular_only(s));
+    const int64_t m = d->sub[0].n_rows + d->sub[1].n_rows;
+    T *bv = d->bvec.as<T>();
+    for (int f = 0; f < 2; ++f) {
+        int64_t off = 0;
+        for (int l = 0; l < 2; ++l) {
+            DD2Sub &sd = d->sub[l];
+            DPM_RET(dd2_rhs<T>(sd.n_rows, sd.row_i.as<int>(), sd.row_e.as<int>(), sd.row_s.as<uint8_t>(),
+                               trp[l] + f * sd.gi.n_gin, nullptr, nullptr, bv + f * m + off, s));
+            off += sd.n_rows;
+        }
+    }
+    double *C = d->coef.as<double>();
+    DPM_RET(lsq_apply<T>(d->lsq, bv, (int)m, C, 2, s));
+    for (int l = 0; l < 2; ++l) {
+        DD2Sub &sd = d->sub[l];
+        const int64_t n = sd.gi.n_gamma;
+        DPM_RET(dd2_extend<T>(n, d->prm.MZ, d->prm.MG, dd2_gamma_series(d->prm), sd.flags.as<uint8_t>(),
+                              sd.dG.as<double>(), sd.dZ.as<double>(), sd.YG.as<double>(), sd.YZ.as<double>(), C,
+                              d->ncol, nullptr, sd.dens.as<T>(), (int)n, 2, k->clamp, s));
+    }
+    DPM_RET(run_prepared<T>(k->batch[2], k->subs, s));
+    for (int l = 0; l < 2; ++l) {
+        DD2Sub &sd = d->sub[l];
+        DPM_RET(pks_diag<T>(sd.N, sd.gi.lo, sd.gi.h, sd.gi.labels.as<uint8_t>(), sd.rho.as<T>(), sd.c.as<T>(),
+                            sd.diag_part.as<double>(), sd.diag_out.as<double>(), s, sd.origin));
+    }
+    DPM_RET(pks_step_end(sc, cond ? -1 : (rebuild ? 1 : 0), s));
+    return DPM_OK;
+}
+
+}  // namespace
+
+extern "C" int dpm_dd2_pks_set_graph(dpm_dd2_pks *k, int on, cudaStream_t s) {
+    if (!k) { set_error("pks is NULL"); return DPM_EINVAL; }
+    dpm_dd2 *d = &k->dd;
+    const bool f64 = d->storage == DPM_PREC_FP64;
+    if (on) {
+        if (k->gs.on) return DPM_OK;
+        DPM_CUDA(cudaSetDevice(d->ctx->device));
+        if (k->dt_mode == 0 && !k->rebuild && (!d->factored || d->sigma != 1.0 / k->dt_max)) {
+            // the fixed-dt step solves against the stacked BEP of sigma = 1/dt_max
+            const double sg = 1.0 / k->dt_max;
+            if (f64) DPM_RET(dd2_build_bep<double>(d, sg, nullptr, sg, s));
+            else DPM_RET(dd2_build_bep<float>(d, sg, nullptr, sg, s));
+        }
+        if (f64) DPM_RET(dd2_dev_setup<double>(k, s));
+        else DPM_RET(dd2_dev_setup<float>(k, s));
+        k->gs.on = 1;
+        return DPM_OK;
+    }
+    if (!k->gs.on) return DPM_OK;
+    int bad = 0;
+    DPM_RET(k->gs.pull(k->t, k->dt_prev, k->step, k->last_rebuilt, &bad, s));
+    k->gs.stop();
+    d->factored = true;
+    d->sigma = 1.0 / k->dt_prev;
+    return DPM_OK;
+}
+
 extern "C" int dpm_dd2_pks_create(dpm_ctx *ctx, const dpm_dd2_params *P, double chi, double dt_max, int dt_mode,
                                   int rebuild, int clamp, const dpm_gaussian *rho0, const dpm_gaussian *c0,
                                   dpm_dd2_pks **out, cudaStream_t s) {
@@ -2050,9 +2391,18 @@ extern "C" int dpm_dd2_pks_create(dpm_ctx *ctx, const dpm_dd2_params *P, double 
 
 extern "C" int dpm_dd2_pks_step(dpm_dd2_pks *k, int nsteps, dpm_pks_stats *stats, cudaStream_t s) {
     if (!k || nsteps < 0) { set_error("pks is NULL or nsteps < 0"); return DPM_EINVAL; }
+    const bool f64 = k->dd.storage == DPM_PREC_FP64;
     for (int i = 0; i < nsteps; ++i) {
-        if (k->dd.storage == DPM_PREC_FP64) DPM_RET(dd2_pks_step<double>(k, s));
+        if (k->gs.on)
+            DPM_RET(k->gs.step([&](cudaStream_t st) { return f64 ? dd2_step_dev<double>(k, st) : dd2_step_dev<float>(k, st); }, s));
+        else if (f64) DPM_RET(dd2_pks_step<double>(k, s));
         else DPM_RET(dd2_pks_step<float>(k, s));
+    }
+    if (stats && k->gs.on) {
+        int bad = 0;
+        DPM_RET(k->gs.pull(k->t, k->dt_prev, k->step, k->last_rebuilt, &bad, s));
+        if (bad) { set_error("time step was not positive/finite on the device"); return DPM_ENUMERIC; }
+        if (k->last_rebuilt) DPM_RET(lsq_status(k->dd.lsq, s));
     }
     if (stats) {
         double dg[2][6];
@@ -2122,16 +2472,6 @@ struct dpm_ml {
     DevBuf coef, bvec, gwork, gitems;
 };
 
-// One batched solve of the device-resident layered step, prepared once: the
-// SIMT grids' right-hand sides as one group, the other grids' descriptors per
-// sub-domain.
-struct MlBatch {
-    DevBuf items;
-    int B = 0, maxN = 0;
-    DevBuf desc[DPM_ML_MAX];
-    int nb[DPM_ML_MAX] = {};
-};
-
 struct dpm_ml_pks {
     dpm_ml ml;
     double chi = 0, dt_max = 0;
@@ -2143,7 +2483,8 @@ struct dpm_ml_pks {
     // batch 0 the BEP columns + the particular solutions, 1 the particular
     // solutions, 2 Green's formula
     GraphStepper gs;
-    MlBatch batch[3];
+    PreparedBatch batch[3];
+    std::vector<SubSolve> subs;
 };
 
 namespace {
@@ -2529,8 +2870,6 @@ template <class T> std::vector<ApRhs<T>> ml_green_rhs(MLSub &sd) {
     return {{sd.frho.as<T>(), dn, sd.rho.as<T>(), nullptr, 0, 0}, {sd.fc.as<T>(), dn + n, sd.c.as<T>(), nullptr, 0, 0}};
 }
 
-bool ml_simt(const MLSub &sd) { return sd.prec == DPM_PREC_FP32 || sd.prec == DPM_PREC_FP64; }
-
 ApParams ml_ap_dev(const MLSub &sd, const StepScalars *sc) {
     ApParams p = ml_ap(sd, 0.0);
     p.sigma_dev = &sc->sigma;
@@ -2544,11 +2883,10 @@ template <class T> int ml_dev_setup(dpm_ml_pks *k, cudaStream_t s) {
     const int need = (d->factored && k->dt_prev > 0 && d->sigma == 1.0 / k->dt_prev) ? 0 : 1;
     DPM_RET(k->gs.push(k->t, k->dt_prev, k->step, k->last_rebuilt, need, s));
     const StepScalars *sc = k->gs.sc();
-    std::vector<ApParams> prm(L);
-    for (int l = 0; l < L; ++l) prm[l] = ml_ap_dev(d->sub[l], sc);
+    k->subs.assign(L, SubSolve{});
+    for (int l = 0; l < L; ++l) k->subs[l] = {d->sub[l].prec, ml_ap_dev(d->sub[l], sc), &d->sub[l].work};
     const bool rebuild = k->dt_mode == 1 || k->rebuild;  // batch 0 is needed
-    std::vector<std::vector<ApRhs<T>>> rhs[3];
-    for (int kb = 0; kb < 3; ++kb) rhs[kb].resize(L);
+    std::vector<std::vector<std::vector<ApRhs<T>>>> rhs(3, std::vector<std::vector<ApRhs<T>>>(L));
     for (int l = 0; l < L; ++l) {
         MLSub &sd = d->sub[l];
         const int64_t n = sd.gi.n_gamma, m = sd.gi.n_gin;
@@ -2560,53 +2898,11 @@ template <class T> int ml_dev_setup(dpm_ml_pks *k, cudaStream_t s) {
         rhs[1][l] = ml_part_rhs<T>(sd);
         rhs[2][l] = ml_green_rhs<T>(sd);
     }
-    // the group workspace first (the prepared descriptors point into it)
-    std::vector<ApRhs<T>> gr[3];
-    std::vector<int> gof[3];
-    size_t gbytes = 0;
-    for (int kb = 0; kb < 3; ++kb) {
-        for (int l = 0; l < L; ++l)
-            if (ml_simt(d->sub[l]))
-                for (auto &e : rhs[kb][l]) {
-                    gr[kb].push_back(e);
-                    gof[kb].push_back(l);
-                }
-        gbytes = std::max(gbytes, ap_group_bytes<T>(prm, gof[kb]));
-    }
-    DPM_RET(d->gwork.reserve(std::max<size_t>(gbytes, 16)));
-    for (int kb = 0; kb < 3; ++kb) {
-        MlBatch &bt = k->batch[kb];
-        bt.B = (int)gr[kb].size();
-        DPM_RET(ap_group_build<T>(prm, gr[kb], gof[kb], d->gwork.p, bt.items, &bt.maxN, s));
-        for (int l = 0; l < L; ++l) {
-            MLSub &sd = d->sub[l];
-            bt.nb[l] = 0;
-            if (ml_simt(sd) || rhs[kb][l].empty()) continue;
-            const int B = (int)rhs[kb][l].size();
-            const size_t cube = (size_t)sd.N * sd.N * sd.N * sizeof(T) * ap_cubes_per_rhs(sd.prec, sd.N);
-            const size_t cb = std::max<size_t>(1, std::min<size_t>(B, kWorkCap / cube));
-            size_t extra = 0;
-            if (sd.prec == DPM_PREC_TC32) extra = tc_scratch_elems(prm[l], (int)cb) * sizeof(float);
-            DPM_RET(sd.work.reserve(cb * cube + extra));
-            DPM_RET(bt.desc[l].reserve(sizeof(ApRhs<T>) * B));
-            DPM_CUDA(cudaMemcpyAsync(bt.desc[l].p, rhs[kb][l].data(), sizeof(ApRhs<T>) * B, cudaMemcpyHostToDevice, s));
-            bt.nb[l] = B;
-        }
-    }
-    DPM_CUDA(cudaStreamSynchronize(s));  // the host descriptor vectors go out of scope
-    return DPM_OK;
+    return prepare_batches<T>(k->subs, rhs, k->batch, d->gwork, s);
 }
 
 template <class T> int ml_run_batch(dpm_ml_pks *k, int kb, cudaStream_t s) {
-    dpm_ml *d = &k->ml;
-    const MlBatch &bt = k->batch[kb];
-    DPM_RET(ap_group_launch<T>(bt.items.p, bt.B, bt.maxN, s));
-    for (int l = 0; l < (int)d->L; ++l) {
-        MLSub &sd = d->sub[l];
-        if (bt.nb[l])
-            DPM_RET(run_ap_dev<T>(sd.prec, ml_ap_dev(sd, k->gs.sc()), bt.desc[l].as<ApRhs<T>>(), bt.nb[l], sd.work, s));
-    }
-    return DPM_OK;
+    return run_prepared<T>(k->batch[kb], k->subs, s);
 }
 
 template <class T> int ml_step_dev(dpm_ml_pks *k, cudaStream_t s) {

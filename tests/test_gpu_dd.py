@@ -174,3 +174,52 @@ def test_grouped_launch_at_larger_grids(ctx):
         finally:
             del os.environ["DPM_DD_GROUP"]
     assert np.array_equal(states[0], states[1])
+
+
+def _dd_run(ctx, P, Ns, dtm, mode, rebuild, graph, steps, prec):
+    pk = abi.dpm_dd_pks_create(ctx, P, 1.0, dtm, mode, rebuild, 1, TEST_A_RHO0, TEST_A_C0)
+    try:
+        if graph:
+            abi.dpm_dd_pks_set_graph(pk, True)
+        flags = [abi.dpm_dd_pks_step(pk, 1, True).rebuilt for _ in range(steps)]
+        st = abi.dpm_dd_pks_step(pk, 0, True)
+        dt = torch.float64 if prec == abi.DPM_PREC_FP64 else torch.float32
+        out = []
+        for l, Nl in enumerate(Ns):
+            rho = torch.empty(Nl ** 3, dtype=dt, device="cuda")
+            c = torch.empty_like(rho)
+            abi.dpm_dd_pks_get_state(pk, l, rho, c)
+            out += [rho, c]
+        torch.cuda.synchronize()
+        if graph:
+            abi.dpm_dd_pks_set_graph(pk, False)
+            assert abi.dpm_dd_pks_step(pk, 1, True).step == steps + 1  # back on host stepping
+        return flags, st, [t.cpu().numpy() for t in out]
+    finally:
+        abi.dpm_dd_pks_destroy(pk)
+
+
+@pytest.mark.parametrize("prec,N1,N2,mode,rebuild", [
+    (abi.DPM_PREC_FP64, 24, 20, 0, 0), (abi.DPM_PREC_FP64, 24, 20, 1, 0),
+    (abi.DPM_PREC_FP32, 24, 20, 1, 1), (abi.DPM_PREC_FP32, 24, 20, 1, 0),
+    (abi.DPM_PREC_TC32, 128, 128, 1, 0)])
+def test_graph_steps_match_host_steps(ctx, prec, N1, N2, mode, rebuild):
+    """Case 1's device-resident steps replayed as a CUDA graph (dt on the device,
+    both grids' solves prepared once: one SIMT group, or the tensor-core solver
+    per grid at N = 128) equal the host-driven steps bit for bit: rebuild flags
+    (Step 4b by a conditional graph node in CFL mode), dt, statistics, state.
+    With a fixed dt the graph path builds the BEP when graph stepping starts, so
+    its first step reports no rebuild where the host path's first step builds."""
+    r1, r2 = 0.25, 0.5
+    (lo1, hi1), (lo2, hi2) = boxes(N1, N2, r1, r2)
+    h = min(2 * r1 / (N1 - 3), 2 * r2 / (N2 - 3))
+    P = abi.dd_params((0.0, 0.0, 0.0), r1, r2, N1, lo1, hi1, N2, lo2, hi2, 1, 1, prec)
+    dtm = 0.5 * h * h if mode == 1 else 1e-6
+    a = _dd_run(ctx, P, (N1, N2), dtm, mode, rebuild, False, 4, prec)
+    b = _dd_run(ctx, P, (N1, N2), dtm, mode, rebuild, True, 4, prec)
+    first = 1 if mode == 0 and not rebuild else 0
+    assert a[0][first:] == b[0][first:], (a[0], b[0])
+    for key in ("t", "dt", "step", "mass", "max_rho", "min_rho", "m2", "free_energy"):
+        assert getattr(a[1], key) == getattr(b[1], key), key
+    for x, y in zip(a[2], b[2]):
+        assert np.array_equal(x, y)

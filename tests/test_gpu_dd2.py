@@ -171,3 +171,46 @@ def test_time_loop_matches_oracle(ctx, prec, tol, gs):
                 assert np.max(np.abs(g[m] - r[m])) <= tol * np.max(np.abs(r[m])), np.max(np.abs(g[m] - r[m])) / np.max(np.abs(r[m]))
     finally:
         abi.dpm_dd2_pks_destroy(pk)
+
+
+def _dd2_run(ctx, P, Ns, dtm, mode, rebuild, graph, steps, prec, rho0, c0):
+    pk = abi.dpm_dd2_pks_create(ctx, P, 1.0, dtm, mode, rebuild, 1, rho0, c0)
+    try:
+        if graph:
+            abi.dpm_dd2_pks_set_graph(pk, True)
+        flags = [abi.dpm_dd2_pks_step(pk, 1, True).rebuilt for _ in range(steps)]
+        st = abi.dpm_dd2_pks_step(pk, 0, True)
+        dt = torch.float64 if prec == abi.DPM_PREC_FP64 else torch.float32
+        out = []
+        for l, Nl in enumerate(Ns):
+            rho = torch.empty(Nl ** 3, dtype=dt, device="cuda")
+            c = torch.empty_like(rho)
+            abi.dpm_dd2_pks_get_state(pk, l, rho, c)
+            out += [rho, c]
+        torch.cuda.synchronize()
+        if graph:
+            abi.dpm_dd2_pks_set_graph(pk, False)
+        return flags, st, [t.cpu().numpy() for t in out]
+    finally:
+        abi.dpm_dd2_pks_destroy(pk)
+
+
+@pytest.mark.parametrize("prec,mode,rebuild", [(abi.DPM_PREC_FP64, 0, 0), (abi.DPM_PREC_FP32, 1, 0),
+                                               (abi.DPM_PREC_FP32, 1, 1)])
+def test_graph_steps_match_host_steps(ctx, prec, mode, rebuild):
+    """Case 2's device-resident steps replayed as a CUDA graph equal the
+    host-driven steps bit for bit (rebuild flags after the first step of the
+    fixed-dt mode, whose BEP the graph path builds when graph stepping starts;
+    dt, statistics, state)."""
+    MZ, MG, N1, N2 = 6, 6, 20, 20
+    h = min(2 * RZ / (N1 - 3), 2 * R / (N2 - 3))
+    rho0, c0 = Gaussian(200.0, 20.0, (0.0, 0.0, 0.25)), Gaussian(100.0, 10.0, (0.0, 0.0, 0.25))
+    P = params(N1, N2, MZ, MG, prec, 1)
+    a = _dd2_run(ctx, P, (N1, N2), 0.5 * h * h, mode, rebuild, False, 4, prec, rho0, c0)
+    b = _dd2_run(ctx, P, (N1, N2), 0.5 * h * h, mode, rebuild, True, 4, prec, rho0, c0)
+    first = 1 if mode == 0 and not rebuild else 0
+    assert a[0][first:] == b[0][first:], (a[0], b[0])
+    for key in ("t", "dt", "step", "mass", "max_rho", "min_rho", "m2", "free_energy"):
+        assert getattr(a[1], key) == getattr(b[1], key), key
+    for x, y in zip(a[2], b[2]):
+        assert np.array_equal(x, y)
