@@ -362,6 +362,16 @@ struct StepScalars {
 };
 int pks_step_dt(const unsigned long long *gmax, double h, double chi, double dt_max, int mode,
                 StepScalars *sc, cudaStream_t s);
+// Expected relative loss of a tensor-core AP solve to the round-toward-zero
+// FP32 accumulation of tcgen05.mma.  A truncating step loses on average half
+// an ulp of the running sum; for sums whose significand m in [1, 2) is
+// log-uniformly distributed the mean of ulp/|sum| = 2^-23/m is 2^-23/(2 ln 2),
+// so a step loses 2^-25/ln 2 (4.3e-8) of the sum.  A folded transform issues
+// its main term (hi*hi, after the small cross terms) in S = K/16 steps whose
+// partial sums are about k/S of the result (k = 1..S, equally sized K slices):
+// (S + 1)/2 full-size steps' worth.  A solve is six transforms (three axes,
+// forward and inverse).  S = 4 (N = 128): 6.45e-7; S = 8 (N = 256): 1.16e-6.
+constexpr double tc_rz_bias(int S) { return 6.0 * 0.5 * (S + 1) * 0x1p-25 / 0.69314718055994531; }
 // rebuilt < 0: the step's rebuild flag is the device's rebuild_now.
 int pks_step_end(StepScalars *sc, int rebuilt, cudaStream_t s);
 // The condition of a conditional graph node (captured steps): rebuild_now.

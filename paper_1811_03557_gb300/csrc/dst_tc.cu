@@ -45,7 +45,7 @@ constexpr int kH = 64;              // fold length
 constexpr uint32_t kTmemCols = 128; // D_E in columns [0,64), D_O in [64,128)
 constexpr float kSScale = 4096.f;   // sine blocks are stored times 2^12
 constexpr uint32_t kWaitIters = 1u << 26;
-constexpr double kRzBias = 5.0e-7;  // see the pencil pass's spectral scale
+constexpr double kRzBias = tc_rz_bias(kH / 16);  // see the pencil pass's spectral scale
 
 // shared-memory layout (offsets from a 1024-aligned base)
 constexpr int kATile = kN * 128;                   // 128 rows x 64 f16 = 16 KB
@@ -686,9 +686,9 @@ k_tc_pencil(TcArgs a, const ApRhs<float> *rhs, float *work, const __grid_constan
     __syncthreads();
     const float sig = (float)(a.sigma_dev ? *a.sigma_dev : a.sigma);
     // (2/(N+1))^3, times 1 + kRzBias: the expected relative loss of the solve to
-    // the tensor cores' round-toward-zero accumulation (4 full-size steps per
-    // transform, 6 transforms; measured mean -4e-7 to -6e-7 on dense random and
-    // Gaussian data, -5e-7 taken), so that long time loops do not drift
+    // the tensor cores' round-toward-zero accumulation (tc_rz_bias: 4 main-term
+    // steps per transform, 6 transforms, 6.45e-7; measured means -4e-7 to -6e-7
+    // on dense random and Gaussian data), so that long time loops do not drift
     const double sc = 2.0 / (kN + 1);
     const float nscale = (float)(sc * sc * sc * (1.0 + kRzBias));
     const int nitems = a.B * kN;

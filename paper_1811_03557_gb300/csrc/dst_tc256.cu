@@ -334,11 +334,11 @@ __global__ void __launch_bounds__(kThreads, 1) k256_cols(LineArgs a) {
     const size_t n3 = (size_t)kN * kN * kN;
     const size_t stride = AXIS == 1 ? (size_t)kN : (size_t)kN * kN;
     // (2/(N+1))^3, times 1 + the expected relative loss of the solve to the tensor
-    // cores' round-toward-zero accumulation (8 full-size steps per transform, 6
-    // transforms; measured mean -1.1e-6 to -1.55e-6 on dense random and Gaussian
-    // data, -1.33e-6 taken), so that long time loops do not drift
+    // cores' round-toward-zero accumulation (tc_rz_bias: kH/16 = 8 main-term steps per
+    // transform, 6 transforms, 1.16e-6; measured means -1.1e-6 to -1.55e-6 on
+    // dense random and Gaussian data), so that long time loops do not drift
     const double sc = 2.0 / (kN + 1);
-    const float nscale = (float)(sc * sc * sc * (1.0 + 1.33e-6));
+    const float nscale = (float)(sc * sc * sc * (1.0 + tc_rz_bias(kH / 16)));
     const float sig = (float)(a.sigma_dev ? *a.sigma_dev : a.sigma);
     for (int it = blockIdx.x >> 1; it < nitems; it += per) {
         const int b = it / (2 * kN), rem = it % (2 * kN);
