@@ -55,6 +55,11 @@ def parse():
     ap.add_argument("--serving-saturated-rate", type=float, default=8000.0,
                     help="offered rate of the second, saturated serving leg (0 skips it)")
     ap.add_argument("--serving-saturated-requests", type=int, default=3000)
+    ap.add_argument("--serving-slots", type=int, default=4,
+                    help="serving worker slots (threads, each with its own stream and buffers)")
+    ap.add_argument("--serving-batch", type=int, default=8, help="right-hand sides per serving batch at most")
+    ap.add_argument("--serving-only", action="store_true",
+                    help="run only the serving legs and print their JSON (tuning runs)")
     ap.add_argument("--no-aux", action="store_true", help="skip the batched aux-solve leg")
     ap.add_argument("--no-graph", action="store_true", help="host-driven steps instead of graph replay")
     ap.add_argument("--aux-case", default=None,
@@ -310,6 +315,16 @@ def run_ours(args):
             abi.dpm_pks_set_graph(pks, True, stream=stream)
         e2e = run_e2e(abi, torch, pks, w, tdt, spp, args, stream)
 
+    # the serving legs run right after the main leg, in the state a serving
+    # process would be in: after the aux, decomposition and layered legs (tens of
+    # GB allocated and freed) its host<->device copies ran 2x slower and its
+    # latency tails 8x longer
+    serving = None
+    if rank == 0 and args.serving_requests > 0:
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        serving = run_serving(abi, torch, ctx, args)
+
     aux = None
     if rank == 0 and not args.no_aux:
         aux = run_aux(abi, torch, ctx, stream)
@@ -329,10 +344,6 @@ def run_ours(args):
         from paper_1811_03557_gb300.experiments import run_layers_uneven
         layers = run_layers_uneven(ctx, steps=200)
         layers["grid_pts_per_s"] = layers["grid_pts_per_step"] / (layers["ms_per_step"] / 1e3)
-
-    serving = None
-    if rank == 0 and args.serving_requests > 0:
-        serving = run_serving(abi, torch, ctx, args)
 
     cpu = None
     if rank == 0:
@@ -614,7 +625,7 @@ def run_serving(abi, torch, ctx, args):
         for q in reqs:
             if q.kind == "solve" and q.rhs_seed not in pool:
                 pool[q.rhs_seed] = torch.from_numpy(poly_gauss_rhs(q.rhs_seed, cat[q.model])).pin_memory()
-    slots, batch = 4, 8
+    slots, batch = args.serving_slots, args.serving_batch
     be = LibraryBackend(ctx, slots, batch, max(m.N for m in cat))
     eng = ServingEngine(be, cat, pcat, n_slots=slots, max_batch=batch, rhs=lambda s, m: pool[s])
     t = time.perf_counter()
@@ -718,6 +729,14 @@ def main():
         return
     if args.bep_case and args.impl != "reference":
         run_bep_case(args)
+        return
+    if args.serving_only and args.impl != "reference":
+        import torch
+        from paper_1811_03557_gb300 import abi
+        torch.cuda.set_device(0)
+        ctx = abi.dpm_ctx_create(0)
+        print(json.dumps({"serving": run_serving(abi, torch, ctx, args)}), flush=True)
+        abi.dpm_ctx_destroy(ctx)
         return
     if args.impl == "reference":
         run_reference(args)
