@@ -18,6 +18,7 @@
 // sums, even a the differences; for odd N the middle node joins odd a only).
 // N+1 = 33, 129, 257 have no radix-2 structure beyond this fold, so the rest
 // of each transform is a dense product with the folded sine table.
+#include <algorithm>
 #include <map>
 #include <math.h>
 #include <mutex>
@@ -148,10 +149,13 @@ __device__ void tile_transform_cm(T *x, T *out, int N, const T *tab) {
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
-        for (int mp = 0; mp < fd.H; ++mp) {
-            int row = even ? mp : N - 1 - mp;
-            V4<T> xv = ld4(x + row * C + 4 * cb);
-            V4<T> sv = ldg4(S + (size_t)mp * ld);
+        // rows mp (sums) or N-1-mp (differences) of the folded tile, walked by pointer
+        const T *xp = x + (even ? 0 : (N - 1) * C) + 4 * cb;
+        const int xstep = even ? C : -C;
+        const T *sp = S;
+        for (int mp = 0; mp < fd.H; ++mp, xp += xstep, sp += ld) {
+            V4<T> xv = ld4(xp);
+            V4<T> sv = ldg4(sp);
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -179,11 +183,14 @@ __device__ void tile_transform_cm(T *x, T *out, int N, const T *tab) {
 template <class T, int C = 32>
 __device__ void tile_transform_rm(T *x, T *out, int N, int ld, const T *tab) {
     FoldDims fd(N);
-    for (int idx = threadIdx.x; idx < fd.H * C; idx += blockDim.x) {
-        int r = idx / fd.H, mp = idx % fd.H;
-        T a = x[r * ld + mp], b = x[r * ld + N - 1 - mp];
-        x[r * ld + mp] = a + b;
-        x[r * ld + N - 1 - mp] = a - b;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int r = threadIdx.x >> 5; r < C; r += nw) {  // a warp per row: no division by N
+        T *xr = x + r * ld;
+        for (int mp = lane; mp < fd.H; mp += 32) {
+            T a = xr[mp], b = xr[N - 1 - mp];
+            xr[mp] = a + b;
+            xr[N - 1 - mp] = a - b;
+        }
     }
     __syncthreads();
     const int nabE = fd.NEp / 4, nabO = fd.NOp / 4;
@@ -200,12 +207,15 @@ __device__ void tile_transform_rm(T *x, T *out, int N, int ld, const T *tab) {
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
         const T *xr = x + 4 * rb * ld;
-        for (int mp = 0; mp < fd.H; ++mp) {
-            int col = even ? mp : N - 1 - mp;
-            V4<T> sv = ldg4(S + (size_t)mp * lds);
+        // columns mp (sums) or N-1-mp (differences) of the folded tile, walked by pointer
+        const T *xp = xr + (even ? 0 : N - 1);
+        const int xstep = even ? 1 : -1;
+        const T *sp = S;
+        for (int mp = 0; mp < fd.H; ++mp, xp += xstep, sp += lds) {
+            V4<T> sv = ldg4(sp);
             T xv[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) xv[i] = xr[i * ld + col];
+            for (int i = 0; i < 4; ++i) xv[i] = xp[i * ld];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -264,16 +274,19 @@ __device__ __forceinline__ void body_k_fwd(const PassArgs &a, const ApRhs<T> &r,
     const int64_t R0 = (int64_t)tile * C;
     const double sig = a.sigma_dev ? *a.sigma_dev : a.sigma;
     const T fs = (T)(a.fscale_dev ? *a.fscale_dev : a.fscale);
-    for (int idx = threadIdx.x; idx < C * N; idx += blockDim.x) {
-        int rr = idx / N, k = idx % N;
-        int64_t R = R0 + rr;
-        T v = (T)0;
-        if (R < nrows && r.f) {
-            int64_t p = R * N + k;
-            v = fs * r.f[p];
-            if (a.mask_f && !(a.labels[p] & DPM_LBL_MPLUS)) v = (T)0;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int rr = threadIdx.x >> 5; rr < C; rr += nw) {  // a warp per row: no division by N
+        const int64_t R = R0 + rr;
+        const bool live = R < nrows && r.f;
+        for (int k = lane; k < N; k += 32) {
+            T v = (T)0;
+            if (live) {
+                const int64_t p = R * N + k;
+                v = fs * r.f[p];
+                if (a.mask_f && !(a.labels[p] & DPM_LBL_MPLUS)) v = (T)0;
+            }
+            x[rr * ld + k] = v;
         }
-        x[rr * ld + k] = v;
     }
     __syncthreads();
     if (r.dens) {
@@ -298,10 +311,10 @@ __device__ __forceinline__ void body_k_fwd(const PassArgs &a, const ApRhs<T> &r,
     }
     tile_transform_rm<T, C>(x, out, N, ld, tab);
     T *w = cube;
-    for (int idx = threadIdx.x; idx < C * N; idx += blockDim.x) {
-        int rr = idx / N, k = idx % N;
-        int64_t R = R0 + rr;
-        if (R < nrows) w[R * N + k] = out[rr * ld + k];
+    for (int rr = threadIdx.x >> 5; rr < C; rr += nw) {
+        const int64_t R = R0 + rr;
+        if (R >= nrows) break;
+        for (int k = lane; k < N; k += 32) w[R * N + k] = out[rr * ld + k];
     }
 }
 
@@ -381,19 +394,19 @@ __device__ __forceinline__ void body_k_inv(const PassArgs &a, const ApRhs<T> &r,
     const int64_t nrows = (int64_t)N * N;
     const int64_t R0 = (int64_t)tile * C;
     const T *w = cube;
-    for (int idx = threadIdx.x; idx < C * N; idx += blockDim.x) {
-        int rr = idx / N, k = idx % N;
-        int64_t R = R0 + rr;
-        x[rr * ld + k] = R < nrows ? w[R * N + k] : (T)0;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int rr = threadIdx.x >> 5; rr < C; rr += nw) {  // a warp per row: no division by N
+        const int64_t R = R0 + rr;
+        for (int k = lane; k < N; k += 32) x[rr * ld + k] = R < nrows ? w[R * N + k] : (T)0;
     }
     __syncthreads();
     tile_transform_rm<T, C>(x, out, N, ld, tab);
     if (r.out_dense) {
-        for (int idx = threadIdx.x; idx < C * N; idx += blockDim.x) {
-            int rr = idx / N, k = idx % N;
-            int64_t R = R0 + rr;
-            if (R < nrows) {
-                int64_t p = R * N + k;
+        for (int rr = threadIdx.x >> 5; rr < C; rr += nw) {
+            const int64_t R = R0 + rr;
+            if (R >= nrows) break;
+            for (int k = lane; k < N; k += 32) {
+                const int64_t p = R * N + k;
                 T v = out[rr * ld + k];
                 if (a.mask_out && !(a.labels[p] & (DPM_LBL_MPLUS | DPM_LBL_GEX))) v = (T)0;
                 r.out_dense[p] = v;
@@ -485,6 +498,14 @@ template <class T, int C = 32> int set_smem_limits(int) {
     });
 }
 
+// Threads per CTA: one per task of the tile transform (4 output modes x 4 of the
+// C columns), at most 256, so that no thread idles through the transform.
+template <int C> int tile_threads(int N) {
+    const FoldDims fd(N);
+    const int tasks = (fd.NEp / 4 + fd.NOp / 4) * (C / 4);
+    return std::min(kThreads, std::max(32, (tasks + 31) / 32 * 32));
+}
+
 template <class T, int C> bool tile_fits(int N) {
     return smem_rows<T, C>(N) <= 227 * 1024 && smem_cols<T, C>(N) <= 227 * 1024;
 }
@@ -498,29 +519,30 @@ int simt_passes(const PassArgs &a, const ApRhs<T> *rhs_dev, T *work, const T *ta
     dim3 grow((unsigned)((nrows + C - 1) / C), a.B);
     dim3 gcol((unsigned)(N * ((N + C - 1) / C)), a.B);
     const bool f64 = sizeof(T) == 8;
+    const int nt = tile_threads<C>(N);
     {
         DPM_PROF(f64 ? "ap_simt64_pass_k_fwd" : "ap_simt32_pass_k_fwd", s);
-        k_pass_k_fwd<T, C><<<grow, kThreads, smem_rows<T, C>(N), s>>>(a, rhs_dev, work, tab);
+        k_pass_k_fwd<T, C><<<grow, nt, smem_rows<T, C>(N), s>>>(a, rhs_dev, work, tab);
         DPM_LAUNCHED();
     }
     {
         DPM_PROF(f64 ? "ap_simt64_pass_j" : "ap_simt32_pass_j", s);
-        k_pass_j<T, C><<<gcol, kThreads, smem_cols<T, C>(N), s>>>(a, rhs_dev, work, tab);
+        k_pass_j<T, C><<<gcol, nt, smem_cols<T, C>(N), s>>>(a, rhs_dev, work, tab);
         DPM_LAUNCHED();
     }
     {
         DPM_PROF(f64 ? "ap_simt64_pass_i" : "ap_simt32_pass_i", s);
-        k_pass_i<T, C><<<gcol, kThreads, smem_cols<T, C>(N), s>>>(a, rhs_dev, work, tab);
+        k_pass_i<T, C><<<gcol, nt, smem_cols<T, C>(N), s>>>(a, rhs_dev, work, tab);
         DPM_LAUNCHED();
     }
     {
         DPM_PROF(f64 ? "ap_simt64_pass_j" : "ap_simt32_pass_j", s);
-        k_pass_j<T, C><<<gcol, kThreads, smem_cols<T, C>(N), s>>>(a, rhs_dev, work, tab);
+        k_pass_j<T, C><<<gcol, nt, smem_cols<T, C>(N), s>>>(a, rhs_dev, work, tab);
         DPM_LAUNCHED();
     }
     {
         DPM_PROF(f64 ? "ap_simt64_pass_k_inv" : "ap_simt32_pass_k_inv", s);
-        k_pass_k_inv<T, C><<<grow, kThreads, smem_rows<T, C>(N), s>>>(a, rhs_dev, work, tab);
+        k_pass_k_inv<T, C><<<grow, nt, smem_rows<T, C>(N), s>>>(a, rhs_dev, work, tab);
         DPM_LAUNCHED();
     }
     return DPM_OK;
@@ -676,29 +698,30 @@ int simt_group_passes(const GroupItem<T> *items, int B, int maxN, cudaStream_t s
     const bool f64 = sizeof(T) == 8;
     const dim3 grow((unsigned)row_tiles<C>(maxN), B), gcol((unsigned)col_tiles<C>(maxN), B);
     const size_t sr = smem_rows<T, C>(maxN), sc = smem_cols<T, C>(maxN);
+    const int nt = tile_threads<C>(maxN);
     {
         DPM_PROF(f64 ? "ap_simt64_pass_k_fwd" : "ap_simt32_pass_k_fwd", s);
-        kg_pass_k_fwd<T, C><<<grow, kThreads, sr, s>>>(items);
+        kg_pass_k_fwd<T, C><<<grow, nt, sr, s>>>(items);
         DPM_LAUNCHED();
     }
     {
         DPM_PROF(f64 ? "ap_simt64_pass_j" : "ap_simt32_pass_j", s);
-        kg_pass_j<T, C><<<gcol, kThreads, sc, s>>>(items);
+        kg_pass_j<T, C><<<gcol, nt, sc, s>>>(items);
         DPM_LAUNCHED();
     }
     {
         DPM_PROF(f64 ? "ap_simt64_pass_i" : "ap_simt32_pass_i", s);
-        kg_pass_i<T, C><<<gcol, kThreads, sc, s>>>(items);
+        kg_pass_i<T, C><<<gcol, nt, sc, s>>>(items);
         DPM_LAUNCHED();
     }
     {
         DPM_PROF(f64 ? "ap_simt64_pass_j" : "ap_simt32_pass_j", s);
-        kg_pass_j<T, C><<<gcol, kThreads, sc, s>>>(items);
+        kg_pass_j<T, C><<<gcol, nt, sc, s>>>(items);
         DPM_LAUNCHED();
     }
     {
         DPM_PROF(f64 ? "ap_simt64_pass_k_inv" : "ap_simt32_pass_k_inv", s);
-        kg_pass_k_inv<T, C><<<grow, kThreads, sr, s>>>(items);
+        kg_pass_k_inv<T, C><<<grow, nt, sr, s>>>(items);
         DPM_LAUNCHED();
     }
     return DPM_OK;
