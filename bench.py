@@ -502,18 +502,23 @@ def run_aux(abi, torch, ctx, stream):
         del q, u
         return ms, B * N ** 3 / (ms / 1e3)
 
-    def leg(ms, v, N, B, sched):
+    def leg(ms, v, N, B, sched, alg_bpp=24):
         # frac: against the algorithmic minimum of a dense solve whose cube does not
         # fit on chip, 24 bytes per grid point (read + write of one cube in each of
-        # three passes); frac_schedule: against the bytes the kernels' schedule moves
-        alg = 24.0 * B * N ** 3 / (ms / 1e3) / 1e9
+        # three passes; 8 when the cube fits in shared memory); frac_schedule:
+        # against the bytes the kernels' schedule moves
+        alg = alg_bpp * B * N ** 3 / (ms / 1e3) / 1e9
         sch = sched * B * N ** 3 / (ms / 1e3) / 1e9
-        return {"ms": ms, "grid_pts_per_s": v, "hbm_gbs": alg, "frac": alg / hbm, "alg_bytes_per_pt": 24,
+        return {"ms": ms, "grid_pts_per_s": v, "hbm_gbs": alg, "frac": alg / hbm, "alg_bytes_per_pt": alg_bpp,
                 "schedule_bytes_per_pt": sched, "schedule_gbs": sch, "frac_schedule": sch / hbm}
 
     out = {}
     ms, v = timed(128, 162, abi.DPM_PREC_TC32, 5)
     out["tc32_N128_B162"] = leg(ms, v, 128, 162, 24)   # plane, pencil, plane
+    # N = 32 (the elliptic workload's grid): the cube in shared memory, one pass;
+    # 1,024 right-hand sides so that the 134 MB in and out exceed L2
+    ms, v = timed(32, 1024, abi.DPM_PREC_FP32, 10)
+    out["fp32_N32_B1024"] = leg(ms, v, 32, 1024, 8, alg_bpp=8)
     ms, v = timed(256, 16, abi.DPM_PREC_TC32, 3)
     # assemble (read f, write q), five out-of-place passes, the last one writing u
     out["tc32_N256_B16"] = leg(ms, v, 256, 16, 56)

@@ -280,7 +280,7 @@ int step_branch(const StepScalars *sc, cudaStream_t s, cudaStream_t &aux, Y &&ye
 // descriptors on its own (run_ap_dev on the grid's workspace).
 struct PreparedBatch {
     DevBuf items;
-    int B = 0, maxN = 0;
+    int B = 0, maxN = 0, minN = 0;
     DevBuf desc[DPM_ML_MAX];
     int nb[DPM_ML_MAX] = {};
 };
@@ -321,7 +321,7 @@ int prepare_batches(const std::vector<SubSolve> &subs, const std::vector<std::ve
     for (int b = 0; b < nbat; ++b) {
         PreparedBatch &pb = bt[b];
         pb.B = (int)gr[b].size();
-        DPM_RET(ap_group_build<T>(prm, gr[b], gof[b], gwork.p, pb.items, &pb.maxN, s));
+        DPM_RET(ap_group_build<T>(prm, gr[b], gof[b], gwork.p, pb.items, &pb.maxN, &pb.minN, s));
         for (int l = 0; l < L; ++l) {
             pb.nb[l] = 0;
             if (simt_prec(subs[l].prec) || rhs[b][l].empty()) continue;
@@ -342,7 +342,7 @@ int prepare_batches(const std::vector<SubSolve> &subs, const std::vector<std::ve
 }
 
 template <class T> int run_prepared(const PreparedBatch &pb, const std::vector<SubSolve> &subs, cudaStream_t s) {
-    DPM_RET(ap_group_launch<T>(pb.items.p, pb.B, pb.maxN, s));
+    DPM_RET(ap_group_launch<T>(pb.items.p, pb.B, pb.maxN, pb.minN, s));
     for (int l = 0; l < (int)subs.size(); ++l)
         if (pb.nb[l]) DPM_RET(run_ap_dev<T>(subs[l].prec, subs[l].p, pb.desc[l].as<ApRhs<T>>(), pb.nb[l], *subs[l].work, s));
     return DPM_OK;

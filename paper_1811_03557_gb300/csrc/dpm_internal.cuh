@@ -215,9 +215,10 @@ template <class T>
 size_t ap_group_bytes(const std::vector<ApParams> &probs, const std::vector<int> &prob_of);
 template <class T>
 int ap_group_build(const std::vector<ApParams> &probs, const std::vector<ApRhs<T>> &rhs,
-                   const std::vector<int> &prob_of, void *work, DevBuf &items_dev, int *maxN, cudaStream_t s);
+                   const std::vector<int> &prob_of, void *work, DevBuf &items_dev, int *maxN, int *minN,
+                   cudaStream_t s);
 template <class T>
-int ap_group_launch(const void *items_dev, int B, int maxN, cudaStream_t s);
+int ap_group_launch(const void *items_dev, int B, int maxN, int minN, cudaStream_t s);
 // Tuned SIMT tile width for (N, FP64?, B) on the current device, 0 if none.
 int simt_tile_choice(int N, int f64, int B);
 // pre[c][e] for the ncol densities dens + c ng (see ApRhs::pre)

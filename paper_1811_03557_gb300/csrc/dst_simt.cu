@@ -18,6 +18,9 @@
 // sums, even a the differences; for odd N the middle node joins odd a only).
 // N+1 = 33, 129, 257 have no radix-2 structure beyond this fold, so the rest
 // of each transform is a dense product with the folded sine table.
+//
+// FP32 grids of N <= 32 take one pass instead (small_body): the whole cube in
+// shared memory, the six transforms line by line, 8 N^3 bytes of HBM traffic.
 #include <algorithm>
 #include <map>
 #include <math.h>
@@ -449,6 +452,13 @@ __global__ void __launch_bounds__(kThreads) k_pass_k_inv(PassArgs a, const ApRhs
 
 // Grouped launches: item b carries its own grid's parameters, right-hand side,
 // cube and sine table; CTAs past the item's tile count return at once.
+// Grids of up to kSmallN points per axis solve in one pass in shared memory
+// (FP32; see small_body).
+constexpr int kSmallN = 32;
+template <class T> __host__ __device__ __forceinline__ bool small_item(int N) {
+    return sizeof(T) == 4 && N <= kSmallN;
+}
+
 template <class T> struct GroupItem {
     PassArgs a;
     ApRhs<T> r;
@@ -461,26 +471,240 @@ template <int C> __host__ __device__ __forceinline__ int col_tiles(int N) { retu
 template <class T, int C>
 __global__ void __launch_bounds__(kThreads) kg_pass_k_fwd(const GroupItem<T> *items) {
     const GroupItem<T> &g = items[blockIdx.y];
-    if ((int)blockIdx.x >= row_tiles<C>(g.a.N)) return;
+    if ((int)blockIdx.x >= row_tiles<C>(g.a.N) || small_item<T>(g.a.N)) return;  // small grids: kg_small
     body_k_fwd<T, C>(g.a, g.r, g.cube, g.tab, blockIdx.x);
 }
 template <class T, int C>
 __global__ void __launch_bounds__(kThreads) kg_pass_j(const GroupItem<T> *items) {
     const GroupItem<T> &g = items[blockIdx.y];
-    if ((int)blockIdx.x >= col_tiles<C>(g.a.N)) return;
+    if ((int)blockIdx.x >= col_tiles<C>(g.a.N) || small_item<T>(g.a.N)) return;  // small grids: kg_small
     body_j<T, C>(g.a, g.r, g.cube, g.tab, blockIdx.x);
 }
 template <class T, int C>
 __global__ void __launch_bounds__(kThreads) kg_pass_i(const GroupItem<T> *items) {
     const GroupItem<T> &g = items[blockIdx.y];
-    if ((int)blockIdx.x >= col_tiles<C>(g.a.N)) return;
+    if ((int)blockIdx.x >= col_tiles<C>(g.a.N) || small_item<T>(g.a.N)) return;  // small grids: kg_small
     body_i<T, C>(g.a, g.r, g.cube, g.tab, blockIdx.x);
 }
 template <class T, int C>
 __global__ void __launch_bounds__(kThreads) kg_pass_k_inv(const GroupItem<T> *items) {
     const GroupItem<T> &g = items[blockIdx.y];
-    if ((int)blockIdx.x >= row_tiles<C>(g.a.N)) return;
+    if ((int)blockIdx.x >= row_tiles<C>(g.a.N) || small_item<T>(g.a.N)) return;  // small grids: kg_small
     body_k_inv<T, C>(g.a, g.r, g.cube, g.tab, blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// Single-pass solve for small grids (FP32, N <= kSmallN): one CTA per
+// right-hand side keeps the whole cube in shared memory (row pitch P = N + 1 or
+// N + 2, odd, so that the lines of every axis are read without bank
+// conflicts), builds q there as pass 1 does, runs the six 1D transforms line
+// by line from registers (k and j forward; i forward, times
+// (2/(N+1))^3/lambda, i inverse; j and k inverse) and writes u and/or the trace
+// as pass 5 does.  The cube crosses HBM once each way: 8 N^3 bytes per
+// right-hand side instead of the five passes' 40 N^3.
+// ---------------------------------------------------------------------------
+constexpr int kSmallThreads = 512;
+__host__ __device__ __forceinline__ int small_pitch(int N) { return (N & 1) ? N + 2 : N + 1; }
+inline size_t small_smem(int N) { return sizeof(float) * ((size_t)N * N * small_pitch(N) + 2 * 256 + 32); }
+
+// Shared-memory layout of the one-pass solve: SE (16 x 16), SO (16 x 16), 32
+// weights, then the cube.
+constexpr int kSmallCube = 2 * 256 + 32;  // float offset of the cube
+
+// One line x[m * st] (m < N) of the cube, starting at float offset `off`, in
+// place: y[a] = sum_m S[a+1][m+1] x[m] (0-based a), by the fold -- sums e against
+// SE (odd modes a+1), differences o against SO (even modes) -- with SE, SO 16 x 16
+// and zero-padded; every output sums over m' in order.  Out of line (it keeps 512
+// threads per CTA within 128 registers); its pointers come from the shared array
+// itself, so every access is a shared-memory one.
+__device__ __noinline__ void small_line(int off, int st, int N) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const float *SE = reinterpret_cast<const float *>(smem_raw);
+    const float *SO = SE + 256;
+    float *x = reinterpret_cast<float *>(smem_raw) + kSmallCube + off;
+    const int H = N >> 1;
+    float e[16], o[16];
+#pragma unroll
+    for (int mp = 0; mp < 16; ++mp) {
+        float u = 0.f, v = 0.f;
+        if (mp < H) {
+            u = x[mp * st];
+            v = x[(N - 1 - mp) * st];
+        } else if (mp == H && (N & 1)) {
+            u = x[mp * st];  // the middle node of an odd line joins the sums only
+        }
+        e[mp] = u + v;
+        o[mp] = u - v;
+    }
+    // odd modes from the sums, stored, then even modes from the differences (every
+    // input is in registers already, so the in-place stores are safe)
+    {
+        float y[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) y[q] = 0.f;
+#pragma unroll
+        for (int mp = 0; mp < 16; ++mp) {
+            const float4 *se = reinterpret_cast<const float4 *>(SE + mp * 16);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 s4 = se[q];
+                y[4 * q] = fmaf(s4.x, e[mp], y[4 * q]);
+                y[4 * q + 1] = fmaf(s4.y, e[mp], y[4 * q + 1]);
+                y[4 * q + 2] = fmaf(s4.z, e[mp], y[4 * q + 2]);
+                y[4 * q + 3] = fmaf(s4.w, e[mp], y[4 * q + 3]);
+            }
+        }
+#pragma unroll
+        for (int ap = 0; ap < 16; ++ap)
+            if (2 * ap < N) x[(2 * ap) * st] = y[ap];
+    }
+    {
+        float y[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) y[q] = 0.f;
+#pragma unroll
+        for (int mp = 0; mp < 16; ++mp) {
+            const float4 *so = reinterpret_cast<const float4 *>(SO + mp * 16);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 t4 = so[q];
+                y[4 * q] = fmaf(t4.x, o[mp], y[4 * q]);
+                y[4 * q + 1] = fmaf(t4.y, o[mp], y[4 * q + 1]);
+                y[4 * q + 2] = fmaf(t4.z, o[mp], y[4 * q + 2]);
+                y[4 * q + 3] = fmaf(t4.w, o[mp], y[4 * q + 3]);
+            }
+        }
+#pragma unroll
+        for (int ap = 0; ap < 16; ++ap)
+            if (2 * ap + 1 < N) x[(2 * ap + 1) * st] = y[ap];
+    }
+}
+
+__device__ void small_body(const PassArgs &a, const ApRhs<float> &r, const float *tab) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (rhs_skipped(r, a.cond_flag)) return;
+    const int N = a.N, P = small_pitch(N), L = N * N;
+    const FoldDims fd(N);
+    float *SE = reinterpret_cast<float *>(smem_raw);  // 16 x 16
+    float *SO = SE + 256;                              // 16 x 16
+    float *w = SO + 256;                               // 32 weights (4/h^2) sin^2(pi (n+1)/(2(N+1)))
+    float *x = SE + kSmallCube;                        // the cube, x[(i N + j) P + k]
+    const int t = threadIdx.x, nt = blockDim.x, lane = t & 31, warp = t >> 5, nw = nt >> 5;
+    const double sig = a.sigma_dev ? *a.sigma_dev : a.sigma;
+    const float fs = (float)(a.fscale_dev ? *a.fscale_dev : a.fscale);
+    for (int q = t; q < 256; q += nt) {
+        const int mp = q >> 4, ap = q & 15;
+        SE[q] = (mp < fd.rowsE && ap < fd.NE) ? tab[(size_t)mp * fd.NEp + ap] : 0.f;
+        SO[q] = (mp < fd.H && ap < fd.NO) ? tab[fd.offO() + (size_t)mp * fd.NOp + ap] : 0.f;
+    }
+    const float w4 = (float)(4.0 / (a.h * a.h));
+    for (int n = t; n < 32; n += nt) w[n] = n < N ? w4 * tab[fd.offW() + n] : 0.f;
+    // q = fscale f on M^+ (everywhere without the mask), as pass 1 builds it
+    for (int row = warp; row < L; row += nw)
+        for (int k = lane; k < N; k += 32) {
+            float v = 0.f;
+            if (r.f) {
+                const int p = row * N + k;
+                v = fs * r.f[p];
+                if (a.mask_f && !(a.labels[p] & DPM_LBL_MPLUS)) v = 0.f;
+            }
+            x[row * P + k] = v;
+        }
+    __syncthreads();
+    if (r.dens) {  // + L[v_gamma] on the M^- shell
+        const float cdiag = (float)(sig + 6.0 / (a.h * a.h));
+        const float coff = (float)(1.0 / (a.h * a.h));
+        const int e0 = a.rp_shell[0], e1 = a.rp_shell[L];
+        for (int e = e0 + t; e < e1; e += nt) {
+            const int p = a.shell[e];
+            const int *nb = a.shell_nb + 8 * (size_t)e;
+            float sum = 0.f;
+#pragma unroll
+            for (int u = 1; u < 7; ++u) {
+                const int g = nb[u];
+                if (g >= 0) sum += r.dens[g];
+            }
+            const float self = nb[0] >= 0 ? r.dens[nb[0]] : 0.f;
+            x[(p / N) * P + p % N] += cdiag * self - coff * sum;
+        }
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int l = t; l < L; l += nt) small_line(l * P, 1, N);  // k
+    __syncthreads();
+#pragma unroll 1
+    for (int l = t; l < L; l += nt) small_line((l / N) * N * P + l % N, P, N);  // j
+    __syncthreads();
+    {
+        const double sc = 2.0 / (N + 1);
+        const float scale = (float)(sc * sc * sc);
+        const float sgT = (float)sig;
+#pragma unroll 1
+        for (int l = t; l < L; l += nt) {  // i: forward, / lambda, inverse
+            const int b = l / N, c = l % N;
+            float *xl = x + b * P + c;
+            const int st = N * P;
+            small_line(b * P + c, st, N);
+            for (int ai = 0; ai < N; ++ai) xl[ai * st] *= scale / (sgT + (w[ai] + w[b] + w[c]));
+            small_line(b * P + c, st, N);
+        }
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int l = t; l < L; l += nt) small_line((l / N) * N * P + l % N, P, N);  // j
+    __syncthreads();
+#pragma unroll 1
+    for (int l = t; l < L; l += nt) small_line(l * P, 1, N);  // k
+    __syncthreads();
+    if (r.out_dense)
+        for (int row = warp; row < L; row += nw)
+            for (int k = lane; k < N; k += 32) {
+                const int p = row * N + k;
+                float v = x[row * P + k];
+                if (a.mask_out && !(a.labels[p] & (DPM_LBL_MPLUS | DPM_LBL_GEX))) v = 0.f;
+                r.out_dense[p] = v;
+            }
+    if (r.out_trace) {
+        const int e0 = a.rp_gin[0], e1 = a.rp_gin[L];
+        for (int e = e0 + t; e < e1; e += nt) {
+            const int p = a.gin[e];
+            r.out_trace[e] = x[(p / N) * P + p % N];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kSmallThreads) k_small(PassArgs a, const ApRhs<float> *rhs, const float *tab) {
+    small_body(a, rhs[blockIdx.x], tab);
+}
+
+__global__ void __launch_bounds__(kSmallThreads) kg_small(const GroupItem<float> *items) {
+    const GroupItem<float> &g = items[blockIdx.x];
+    if (!small_item<float>(g.a.N)) return;
+    small_body(g.a, g.r, g.tab);
+}
+
+int small_configure() {
+    static PerDeviceOnce once;
+    return once.run([] {
+        DPM_RET(raise_dynamic_smem_limit(reinterpret_cast<const void *>(k_small)));
+        return raise_dynamic_smem_limit(reinterpret_cast<const void *>(kg_small));
+    });
+}
+
+int small_launch(const PassArgs &a, const ApRhs<float> *rhs_dev, const float *tab, cudaStream_t s) {
+    DPM_RET(small_configure());
+    DPM_PROF("ap_simt32_small", s);
+    k_small<<<a.B, kSmallThreads, small_smem(a.N), s>>>(a, rhs_dev, tab);
+    DPM_LAUNCHED();
+    return DPM_OK;
+}
+
+int small_group_launch(const GroupItem<float> *items, int B, cudaStream_t s) {
+    DPM_RET(small_configure());
+    DPM_PROF("ap_simt32_small", s);
+    kg_small<<<B, kSmallThreads, small_smem(kSmallN), s>>>(items);
+    DPM_LAUNCHED();
+    return DPM_OK;
 }
 
 template <class T, int C = 32> size_t smem_rows(int N) { return 2 * (size_t)C * (N + 1) * sizeof(T); }
@@ -673,6 +897,9 @@ int ap_solve_simt(const ApParams &p, const ApRhs<T> *rhs_dev, T *work, cudaStrea
     if (!tab) { set_error("AP solve: could not create the DST table"); return DPM_ENOMEM; }
     PassArgs a{N, p.B, p.h, p.sigma, p.fscale, p.sigma_dev, p.fscale_dev, p.cond_flag, p.mask_f,
                p.mask_out, p.labels, p.shell, p.shell_nb, p.rp_shell, p.gin, p.rp_gin};
+    if constexpr (sizeof(T) == 4) {
+        if (small_item<T>(N)) return small_launch(a, rhs_dev, tab, s);  // one pass, no workspace
+    }
     int C = 32;
     DPM_RET(tuned_tile<T>(a, work, tab, s, &C));
     return simt_dispatch<T>(C, a, rhs_dev, work, tab, s);
@@ -776,10 +1003,19 @@ int ap_solve_simt_group(const std::vector<ApParams> &probs, const std::vector<Ap
         DPM_CUDA(cudaMemcpyAsync(items_dev.p, items.data(), sizeof(GroupItem<T>) * (b1 - b0),
                                  cudaMemcpyHostToDevice, s));
         const auto *d = static_cast<const GroupItem<T> *>(items_dev.p);
+        bool any_small = false, any_large = false;
+        for (size_t b = b0; b < b1; ++b) {
+            const bool sm = small_item<T>(probs[prob_of[b]].N);
+            any_small |= sm;
+            any_large |= !sm;
+        }
+        if constexpr (sizeof(T) == 4) {
+            if (any_small) DPM_RET(small_group_launch(d, (int)(b1 - b0), s));
+        }
         // the tile width of the largest grid: 16 when its 32-wide tiles would leave
         // one CTA per SM (N > 128), else 32 (the autotuner's choices at N = 256 / 128)
-        if (maxN > 128) DPM_RET((simt_group_passes<T, 16>(d, (int)(b1 - b0), maxN, s)));
-        else DPM_RET((simt_group_passes<T, 32>(d, (int)(b1 - b0), maxN, s)));
+        if (any_large && maxN > 128) DPM_RET((simt_group_passes<T, 16>(d, (int)(b1 - b0), maxN, s)));
+        else if (any_large) DPM_RET((simt_group_passes<T, 32>(d, (int)(b1 - b0), maxN, s)));
         if (b1 < B) DPM_CUDA(cudaStreamSynchronize(s));  // the items / workspace are reused
         b0 = b1;
     }
@@ -795,9 +1031,11 @@ size_t ap_group_bytes(const std::vector<ApParams> &probs, const std::vector<int>
 
 template <class T>
 int ap_group_build(const std::vector<ApParams> &probs, const std::vector<ApRhs<T>> &rhs,
-                   const std::vector<int> &prob_of, void *work, DevBuf &items_dev, int *maxN, cudaStream_t s) {
+                   const std::vector<int> &prob_of, void *work, DevBuf &items_dev, int *maxN, int *minN,
+                   cudaStream_t s) {
     const size_t B = rhs.size();
     *maxN = 0;
+    *minN = 0;
     if (B == 0) return DPM_OK;
     if (prob_of.size() != B || B > 65535) {
         set_error("grouped AP solve: one problem index per right-hand side, at most 65535");
@@ -820,6 +1058,7 @@ int ap_group_build(const std::vector<ApParams> &probs, const std::vector<ApRhs<T
         g.tab = tab;
         off += (size_t)p.N * p.N * p.N * sizeof(T);
         *maxN = std::max(*maxN, p.N);
+        *minN = b == 0 ? p.N : std::min(*minN, p.N);
     }
     DPM_RET(items_dev.reserve(sizeof(GroupItem<T>) * B));
     DPM_CUDA(cudaMemcpyAsync(items_dev.p, items.data(), sizeof(GroupItem<T>) * B, cudaMemcpyHostToDevice, s));
@@ -828,9 +1067,13 @@ int ap_group_build(const std::vector<ApParams> &probs, const std::vector<ApRhs<T
 }
 
 template <class T>
-int ap_group_launch(const void *items_dev, int B, int maxN, cudaStream_t s) {
+int ap_group_launch(const void *items_dev, int B, int maxN, int minN, cudaStream_t s) {
     if (B == 0) return DPM_OK;
     const auto *d = static_cast<const GroupItem<T> *>(items_dev);
+    if constexpr (sizeof(T) == 4) {
+        if (small_item<T>(minN)) DPM_RET(small_group_launch(d, B, s));
+    }
+    if (small_item<T>(maxN)) return DPM_OK;  // every grid solved in one pass
     // the tile width rule of ap_solve_simt_group
     if (maxN > 128) return simt_group_passes<T, 16>(d, B, maxN, s);
     return simt_group_passes<T, 32>(d, B, maxN, s);
@@ -839,8 +1082,8 @@ int ap_group_launch(const void *items_dev, int B, int maxN, cudaStream_t s) {
 #define DPM_GROUP_INST(T)                                                                                         \
     template size_t ap_group_bytes<T>(const std::vector<ApParams> &, const std::vector<int> &);                 \
     template int ap_group_build<T>(const std::vector<ApParams> &, const std::vector<ApRhs<T>> &,                \
-                                   const std::vector<int> &, void *, DevBuf &, int *, cudaStream_t);            \
-    template int ap_group_launch<T>(const void *, int, int, cudaStream_t);
+                                   const std::vector<int> &, void *, DevBuf &, int *, int *, cudaStream_t);     \
+    template int ap_group_launch<T>(const void *, int, int, int, cudaStream_t);
 DPM_GROUP_INST(float)
 DPM_GROUP_INST(double)
 #undef DPM_GROUP_INST
