@@ -511,79 +511,82 @@ inline size_t small_smem(int N) { return sizeof(float) * ((size_t)N * N * small_
 // weights, then the cube.
 constexpr int kSmallCube = 2 * 256 + 32;  // float offset of the cube
 
-// One line x[m * st] (m < N) of the cube, starting at float offset `off`, in
-// place: y[a] = sum_m S[a+1][m+1] x[m] (0-based a), by the fold -- sums e against
-// SE (odd modes a+1), differences o against SO (even modes) -- with SE, SO 16 x 16
-// and zero-padded; every output sums over m' in order.  Out of line (it keeps 512
+// Two lines x[m * st] (m < N) of the cube, starting at float offsets off0 and off1
+// (off1 < 0: one line), in place: y[a] = sum_m S[a+1][m+1] x[m] (0-based a), by the
+// fold -- sums e against SE (odd modes a+1), differences o against SO (even modes)
+// -- with SE, SO 16 x 16 and zero-padded; every output sums over m' in order.  Two
+// lines per call make each table load feed eight FMAs.  Out of line (it keeps 512
 // threads per CTA within 128 registers); its pointers come from the shared array
 // itself, so every access is a shared-memory one.
-__device__ __noinline__ void small_line(int off, int st, int N) {
+__device__ __noinline__ void small_line2(int off0, int off1, int st, int N) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const float *SE = reinterpret_cast<const float *>(smem_raw);
     const float *SO = SE + 256;
-    float *x = reinterpret_cast<float *>(smem_raw) + kSmallCube + off;
+    float *x0 = reinterpret_cast<float *>(smem_raw) + kSmallCube + off0;
+    float *x1 = reinterpret_cast<float *>(smem_raw) + kSmallCube + (off1 < 0 ? off0 : off1);
+    const bool two = off1 >= 0;
     const int H = N >> 1;
-    float e[16], o[16];
+    float e0[16], o0[16], e1[16], o1[16];
 #pragma unroll
     for (int mp = 0; mp < 16; ++mp) {
-        float u = 0.f, v = 0.f;
+        float u0 = 0.f, v0 = 0.f, u1 = 0.f, v1 = 0.f;
         if (mp < H) {
-            u = x[mp * st];
-            v = x[(N - 1 - mp) * st];
+            u0 = x0[mp * st];
+            v0 = x0[(N - 1 - mp) * st];
+            u1 = x1[mp * st];
+            v1 = x1[(N - 1 - mp) * st];
         } else if (mp == H && (N & 1)) {
-            u = x[mp * st];  // the middle node of an odd line joins the sums only
+            u0 = x0[mp * st];  // the middle node of an odd line joins the sums only
+            u1 = x1[mp * st];
         }
-        e[mp] = u + v;
-        o[mp] = u - v;
+        e0[mp] = u0 + v0;
+        o0[mp] = u0 - v0;
+        e1[mp] = u1 + v1;
+        o1[mp] = u1 - v1;
     }
     // odd modes from the sums, stored, then even modes from the differences (every
     // input is in registers already, so the in-place stores are safe)
-    {
-        float y[16];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) y[q] = 0.f;
+    for (int half = 0; half < 2; ++half) {
+        const float *T = half ? SO : SE;
+        float y0[16], y1[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            y0[q] = 0.f;
+            y1[q] = 0.f;
+        }
 #pragma unroll
         for (int mp = 0; mp < 16; ++mp) {
-            const float4 *se = reinterpret_cast<const float4 *>(SE + mp * 16);
+            const float4 *tr = reinterpret_cast<const float4 *>(T + mp * 16);
+            const float a0 = half ? o0[mp] : e0[mp], a1 = half ? o1[mp] : e1[mp];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float4 s4 = se[q];
-                y[4 * q] = fmaf(s4.x, e[mp], y[4 * q]);
-                y[4 * q + 1] = fmaf(s4.y, e[mp], y[4 * q + 1]);
-                y[4 * q + 2] = fmaf(s4.z, e[mp], y[4 * q + 2]);
-                y[4 * q + 3] = fmaf(s4.w, e[mp], y[4 * q + 3]);
+                const float4 s4 = tr[q];
+                y0[4 * q] = fmaf(s4.x, a0, y0[4 * q]);
+                y0[4 * q + 1] = fmaf(s4.y, a0, y0[4 * q + 1]);
+                y0[4 * q + 2] = fmaf(s4.z, a0, y0[4 * q + 2]);
+                y0[4 * q + 3] = fmaf(s4.w, a0, y0[4 * q + 3]);
+                y1[4 * q] = fmaf(s4.x, a1, y1[4 * q]);
+                y1[4 * q + 1] = fmaf(s4.y, a1, y1[4 * q + 1]);
+                y1[4 * q + 2] = fmaf(s4.z, a1, y1[4 * q + 2]);
+                y1[4 * q + 3] = fmaf(s4.w, a1, y1[4 * q + 3]);
             }
         }
 #pragma unroll
-        for (int ap = 0; ap < 16; ++ap)
-            if (2 * ap < N) x[(2 * ap) * st] = y[ap];
-    }
-    {
-        float y[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) y[q] = 0.f;
-#pragma unroll
-        for (int mp = 0; mp < 16; ++mp) {
-            const float4 *so = reinterpret_cast<const float4 *>(SO + mp * 16);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float4 t4 = so[q];
-                y[4 * q] = fmaf(t4.x, o[mp], y[4 * q]);
-                y[4 * q + 1] = fmaf(t4.y, o[mp], y[4 * q + 1]);
-                y[4 * q + 2] = fmaf(t4.z, o[mp], y[4 * q + 2]);
-                y[4 * q + 3] = fmaf(t4.w, o[mp], y[4 * q + 3]);
+        for (int ap = 0; ap < 16; ++ap) {
+            const int a = 2 * ap + half;
+            if (a < N) {
+                x0[a * st] = y0[ap];
+                if (two) x1[a * st] = y1[ap];
             }
         }
-#pragma unroll
-        for (int ap = 0; ap < 16; ++ap)
-            if (2 * ap + 1 < N) x[(2 * ap + 1) * st] = y[ap];
     }
 }
 
 __device__ void small_body(const PassArgs &a, const ApRhs<float> &r, const float *tab) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (rhs_skipped(r, a.cond_flag)) return;
-    const int N = a.N, P = small_pitch(N), L = N * N;
+    const int N = a.N, P = small_pitch(N), L = N * N, Lp = (L + 1) / 2;  // lines, line pairs (l, l + Lp)
     const FoldDims fd(N);
     float *SE = reinterpret_cast<float *>(smem_raw);  // 16 x 16
     float *SO = SE + 256;                              // 16 x 16
@@ -630,31 +633,40 @@ __device__ void small_body(const PassArgs &a, const ApRhs<float> &r, const float
     }
     __syncthreads();
 #pragma unroll 1
-    for (int l = t; l < L; l += nt) small_line(l * P, 1, N);  // k
+    for (int l = t; l < Lp; l += nt) small_line2(l * P, l + Lp < L ? (l + Lp) * P : -1, 1, N);  // k
     __syncthreads();
 #pragma unroll 1
-    for (int l = t; l < L; l += nt) small_line((l / N) * N * P + l % N, P, N);  // j
+    for (int l = t; l < Lp; l += nt) {  // j
+        const int l1 = l + Lp;
+        small_line2((l / N) * N * P + l % N, l1 < L ? (l1 / N) * N * P + l1 % N : -1, P, N);
+    }
     __syncthreads();
     {
         const double sc = 2.0 / (N + 1);
         const float scale = (float)(sc * sc * sc);
         const float sgT = (float)sig;
 #pragma unroll 1
-        for (int l = t; l < L; l += nt) {  // i: forward, / lambda, inverse
-            const int b = l / N, c = l % N;
-            float *xl = x + b * P + c;
-            const int st = N * P;
-            small_line(b * P + c, st, N);
-            for (int ai = 0; ai < N; ++ai) xl[ai * st] *= scale / (sgT + (w[ai] + w[b] + w[c]));
-            small_line(b * P + c, st, N);
+        for (int l = t; l < Lp; l += nt) {  // i: forward, / lambda, inverse
+            const int st = N * P, l1 = l + Lp;
+            const int b0 = l / N, c0 = l % N, b1 = l1 / N, c1 = l1 % N;
+            const int off1 = l1 < L ? b1 * P + c1 : -1;
+            small_line2(b0 * P + c0, off1, st, N);
+            for (int ai = 0; ai < N; ++ai) {
+                x[b0 * P + c0 + ai * st] *= scale / (sgT + (w[ai] + w[b0] + w[c0]));
+                if (off1 >= 0) x[off1 + ai * st] *= scale / (sgT + (w[ai] + w[b1] + w[c1]));
+            }
+            small_line2(b0 * P + c0, off1, st, N);
         }
     }
     __syncthreads();
 #pragma unroll 1
-    for (int l = t; l < L; l += nt) small_line((l / N) * N * P + l % N, P, N);  // j
+    for (int l = t; l < Lp; l += nt) {  // j
+        const int l1 = l + Lp;
+        small_line2((l / N) * N * P + l % N, l1 < L ? (l1 / N) * N * P + l1 % N : -1, P, N);
+    }
     __syncthreads();
 #pragma unroll 1
-    for (int l = t; l < L; l += nt) small_line(l * P, 1, N);  // k
+    for (int l = t; l < Lp; l += nt) small_line2(l * P, l + Lp < L ? (l + Lp) * P : -1, 1, N);  // k
     __syncthreads();
     if (r.out_dense)
         for (int row = warp; row < L; row += nw)
