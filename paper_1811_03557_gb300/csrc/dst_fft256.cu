@@ -272,12 +272,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_fft_p
     for (int item = cid; item < a.B * kN; item += ncl) {
         const int b = item / kN, i = item - b * kN;
         const size_t plane = (size_t)b * n3 + (size_t)i * kN * kN;
-        // ---- load rows j in [128 r, 128 r + 128) (128 KB) --------------------------
+        // ---- load rows j in [128 r, 128 r + 128) (128 KB; all 16 float4 loads of a
+        //      thread in flight at once: nothing overlaps this copy) -----------------
         float4 *D4 = reinterpret_cast<float4 *>(D);
         const size_t off = plane + (size_t)kM * r * kN;  // first float of the half plane
         if (a.from_work) {
             const float4 *src = reinterpret_cast<const float4 *>(a.work + off);
-#pragma unroll 4
+#pragma unroll 16
             for (int e = tid; e < kPlaneF2 / 2; e += kThreads) D4[e] = src[e];
         } else {
             const ApRhs<float> rb = a.rhs[b];
@@ -403,7 +404,7 @@ __global__ void __launch_bounds__(kPenThreads, 2) k_fft_pencil(PassArgs256 a) {
         const int b = item / tiles, tile = item - b * tiles;
         const size_t base = (size_t)b * n3 + (size_t)tile * kPenSlots * 2;  // float offset in plane 0
         // ---- load: 256 rows i of 32 slots (256 B each) -----------------------------
-#pragma unroll 4
+#pragma unroll 8
         for (int e = tid; e < kN * kPenSlots / 2; e += kPenThreads) {
             const int i = e >> 4, q = e & 15;
             const float4 v = *reinterpret_cast<const float4 *>(a.work + base + (size_t)i * kN * kN + 4 * q);
@@ -504,7 +505,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) k_fft_p
         // ---- load [k-pair][j-mode] of this CTA's j-mode half, natural layout -------
         const float4 *src = reinterpret_cast<const float4 *>(a.work + off);
         float4 *D4 = reinterpret_cast<float4 *>(D);
-#pragma unroll 4
+#pragma unroll 16
         for (int e = tid; e < kPlaneF2 / 2; e += kThreads) D4[e] = src[e];
         cl.sync();
         // ---- j unfold across the pair: CTA 0 U = A0 + A1, CTA 1 V = A0 - A1 ---------
