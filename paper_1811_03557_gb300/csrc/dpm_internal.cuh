@@ -257,6 +257,10 @@ struct LsqFactor {
     bool rinv32 = false;  // R^{-1} stored in FP32 (the in-shared-memory mixed factor)
     const float *A32 = nullptr;  // FP32 copy of A kept by that factor (in X), else null
     const float *A32s = nullptr; // FP32 copy of A D kept by the mixed factor for larger n (in X)
+    // A as two floats, A = Ahi + Alo to ~2^-48 (mixed factor, n > 168): the FP32
+    // paths' residual b - A C in two-float arithmetic instead of FP64
+    const float *Ahi = nullptr, *Alo = nullptr;
+    DevBuf A2;
     // Optional block structure of a block-banded A (stored dense, zeros outside
     // the blocks), set by lsq_set_band: int[2n] the row interval [lo, hi) of
     // each column's nonzeros, then int[2 ceil(m/32)] the column interval of

@@ -398,8 +398,10 @@ __global__ void k_scale32(int m, const double *__restrict__ A, const double *__r
     }
 }
 
-// Af = float(A), column-major like A (the Gram products read FP32 operands)
-__global__ void k_to_float(size_t total, const double *__restrict__ A, float *__restrict__ Af) {
+// Af = float(A), column-major like A (the Gram products read FP32 operands);
+// with lo: also lo = float(A - Af), so that A = Af + lo to about 2^-48 relative
+__global__ void k_to_float(size_t total, const double *__restrict__ A, float *__restrict__ Af,
+                           float *__restrict__ lo) {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t e0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e0 < total; e0 += kAtbU * stride) {
         double v[kAtbU];
@@ -407,7 +409,70 @@ __global__ void k_to_float(size_t total, const double *__restrict__ A, float *__
         for (int u = 0; u < kAtbU; ++u) v[u] = e0 + u * stride < total ? A[e0 + u * stride] : 0.0;
 #pragma unroll
         for (int u = 0; u < kAtbU; ++u)
-            if (e0 + u * stride < total) Af[e0 + u * stride] = (float)v[u];
+            if (e0 + u * stride < total) {
+                const float hi = (float)v[u];
+                Af[e0 + u * stride] = hi;
+                if (lo) lo[e0 + u * stride] = (float)(v[u] - (double)hi);
+            }
+    }
+}
+
+// C as two floats per entry (hi, lo): the residual's coefficients
+__global__ void k_split_coef(int total, const double *__restrict__ C, float *__restrict__ hi,
+                             float *__restrict__ lo) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const double c = C[e];
+        const float h = (float)c;
+        hi[e] = h;
+        lo[e] = (float)(c - (double)h);
+    }
+}
+
+// res[q][r] = b[q][r] - sum_c A[r][c] C[q][c] in two-float arithmetic (the FP32
+// paths): A = Ahi + Alo and C = Chi + Clo; each product's rounding error from an
+// FMA (exact), the small cross terms in FP32, the running sum by TwoSum into a
+// (sum, error) pair; the warps' pairs are added in FP64 at the end.  About 2^-44
+// of the sums' magnitude, far below the FP32 rounding of the stored residual,
+// at the FP32 rate instead of GB300's FP64 rate.  Same CTA and column layout as
+// k_resid (32 rows x kResW warps, banded column intervals).
+__global__ void __launch_bounds__(32 * kResW) k_resid2f(int m, int n, const float *__restrict__ Ahi,
+                                                        const float *__restrict__ Alo, const float *b, int ldb,
+                                                        const float *__restrict__ Chi,
+                                                        const float *__restrict__ Clo, float *res, int nr,
+                                                        const int *__restrict__ rband) {
+    __shared__ double sh[kResW][kAtbQ][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = blockIdx.x * 32 + lane;
+    const int q0 = blockIdx.y * kAtbQ, nq = min(kAtbQ, nr - q0);
+    int c_lo = 0, c_hi = n;
+    if (rband) {
+        c_lo = rband[2 * blockIdx.x];
+        c_hi = rband[2 * blockIdx.x + 1];
+    }
+    float S[kAtbQ] = {}, E[kAtbQ] = {};
+    if (r < m) {
+        for (int c = c_lo + ((warp - c_lo) % kResW + kResW) % kResW; c < c_hi; c += kResW) {
+            const float ah = Ahi[(size_t)c * m + r], al = Alo[(size_t)c * m + r];
+#pragma unroll
+            for (int q = 0; q < kAtbQ; ++q)
+                if (q < nq) {
+                    const float ch = Chi[(size_t)(q0 + q) * n + c], cl = Clo[(size_t)(q0 + q) * n + c];
+                    const float p = ah * ch;
+                    const float t = fmaf(ah, cl, fmaf(al, ch, fmaf(ah, ch, -p)));  // ah ch - p exact, + cross
+                    const float sn = S[q] + p, bb = sn - S[q];
+                    E[q] += ((S[q] - (sn - bb)) + (p - bb)) + t;  // TwoSum error + small terms
+                    S[q] = sn;
+                }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kAtbQ; ++q) sh[warp][q][lane] = (double)S[q] + (double)E[q];
+    __syncthreads();
+    if (warp < nq && r < m) {
+        double v = 0.0;
+#pragma unroll
+        for (int w = 0; w < kResW; ++w) v += sh[w][warp][lane];
+        res[(size_t)(q0 + warp) * m + r] = (float)((double)b[(size_t)(q0 + warp) * ldb + r] - v);
     }
 }
 
@@ -1048,9 +1113,18 @@ static int mixed_factor(LsqFactor &f, const double *A0, double *R, double *Rinv,
         DPM_PROF("lsq_gram_syrk", s);
         if (in_smem) {
             // Gram of float(A); the Cholesky kernel equilibrates it by its diagonal
-            k_to_float<<<4 * 152, 256, 0, s>>>((size_t)m * n, A0, Af);
+            k_to_float<<<4 * 152, 256, 0, s>>>((size_t)m * n, A0, Af, nullptr);
             DPM_LAUNCHED();
         } else {
+            // the two-float copy of A for the residual, A = hi + lo: its split costs
+            // FP64 operations per entry, repaid by the FP32-rate residuals of the
+            // many steps a factor of this size serves (n > 168: the decompositions)
+            DPM_RET(f.A2.reserve(sizeof(float) * (size_t)m * n * 2));
+            k_to_float<<<4 * 152, 256, 0, s>>>((size_t)m * n, A0, f.A2.as<float>(),
+                                                f.A2.as<float>() + (size_t)m * n);
+            DPM_LAUNCHED();
+            f.Ahi = f.A2.as<float>();
+            f.Alo = f.Ahi + (size_t)m * n;
             k_colscale<<<n, 1024, 0, s>>>(m, A0, dscale);
             DPM_LAUNCHED();
             k_scale32<<<dim3(8, n), 256, 0, s>>>(m, A0, dscale, Af);
@@ -1180,6 +1254,8 @@ static int lsq_factor_impl(LsqFactor &f, bool sync, cudaStream_t s) {
     f.rinv32 = false;
     f.A32 = nullptr;
     f.A32s = nullptr;
+    f.Ahi = nullptr;
+    f.Alo = nullptr;
     int rinv_done = 0;
     if (f.method == LsqFactor::kHouseholder) {
         DPM_RET(householder_factor(f, A0, w, rdiag, R, status, s));
@@ -1306,8 +1382,20 @@ int lsq_apply(const LsqFactor &f, const T *b, int ldb, double *C, int nr, cudaSt
     };
     DPM_RET(precondition(0));
     // iterative refinement: C += D R^{-1} R^{-T} D A^T (b - A C), the residual in FP64
+    // (two-float on the FP32 paths)
     for (int it = 0; it < refine; ++it) {
-        if (fast32) {
+        if (fast32 && f.Alo) {
+            // two-float residual: the coefficients split once per refinement step
+            float *chi = reinterpret_cast<float *>(z), *clo = chi + (size_t)nr * n;
+            k_split_coef<<<(unsigned)std::min(((size_t)nr * n + 255) / 256, (size_t)152), 256, 0, s>>>(nr * n, C,
+                                                                                                   chi, clo);
+            DPM_LAUNCHED();
+            k_resid2f<<<dim3((m + 31) / 32, qg), 32 * kResW, 0, s>>>(m, n, f.Ahi, f.Alo,
+                                                                     reinterpret_cast<const float *>(b), ldb, chi,
+                                                                     clo, res32, nr, rband);
+            DPM_LAUNCHED();
+            k_atb32<<<dim3(n, S, qg), kAtbT, 0, s>>>(m, n, A32, res32, m, ypart, nr, rows_per, cband);
+        } else if (fast32) {
             k_resid<T, float><<<dim3((m + 31) / 32, qg), 32 * kResW, 0, s>>>(m, n, A0, b, ldb, C, res32, nr,
                                                                               rband);
             DPM_LAUNCHED();
