@@ -97,7 +97,7 @@ template const double *dst_fold_table<double>(int);
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 
 template <class T> struct V4 { T v[4]; };
 
@@ -110,15 +110,6 @@ __device__ __forceinline__ V4<double> ld4(const double *p) {
     double2 b = *reinterpret_cast<const double2 *>(p + 2);
     return {{a.x, a.y, b.x, b.y}};
 }
-__device__ __forceinline__ V4<float> ldg4(const float *p) {
-    float4 a = __ldg(reinterpret_cast<const float4 *>(p));
-    return {{a.x, a.y, a.z, a.w}};
-}
-__device__ __forceinline__ V4<double> ldg4(const double *p) {
-    double2 a = __ldg(reinterpret_cast<const double2 *>(p));
-    double2 b = __ldg(reinterpret_cast<const double2 *>(p + 2));
-    return {{a.x, a.y, b.x, b.y}};
-}
 __device__ __forceinline__ void st4(float *p, const float *v) {
     *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
@@ -127,65 +118,149 @@ __device__ __forceinline__ void st4(double *p, const double *v) {
     *reinterpret_cast<double2 *>(p + 2) = make_double2(v[2], v[3]);
 }
 
+// The folded sine tables reach the transforms through shared memory, KC table
+// rows (fold indices m') at a time: both parities' rows [m0, m0 + KC) are one
+// contiguous run each in the table, copied with 16-byte cp.async (L2 only)
+// into one of two buffers while the other is being read.  Every thread of the
+// CTA reads every staged row, so the table crosses the L2 -> SM path once per
+// tile and transform instead of once per warp that misses in L1 (the tiles
+// leave L1 too small to hold a table of N > 128).
+template <class T> __host__ __device__ constexpr int kc_rows() { return sizeof(T) == 4 ? 16 : 8; }
+template <class T> __host__ __device__ size_t chunk_elems(int N) {  // one buffer
+    const FoldDims fd(N);
+    return (size_t)kc_rows<T>() * (fd.NEp + fd.NOp);
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// One element global -> shared, asynchronously; valid = false writes zero and
+// reads nothing (src must still be a global address).  The tiles' loads are
+// issued this way, all of a thread's elements in flight at once, instead of
+// one dependent HBM round trip per element.
+__device__ __forceinline__ void cp_async_elem(float *dst, const float *src, bool valid) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double *dst, const double *src, bool valid) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Copy table rows [m0, m0 + KC) into sb: SE rows (m' < rowsE) at [0, KC NEp),
+// SO rows (m' < H) at [KC NEp, KC (NEp + NOp)).  Rows past the end are not copied
+// and never read.
+template <class T>
+__device__ __forceinline__ void stage_rows(T *sb, const T *tab, const FoldDims &fd, int m0) {
+    constexpr int KC = kc_rows<T>(), V = 16 / (int)sizeof(T);
+    const int nE = max(0, min(KC, fd.rowsE - m0)) * (fd.NEp / V);
+    const int nO = max(0, min(KC, fd.H - m0)) * (fd.NOp / V);
+    const T *srcE = tab + (size_t)m0 * fd.NEp, *srcO = tab + fd.offO() + (size_t)m0 * fd.NOp;
+    T *dO = sb + KC * fd.NEp;
+    for (int v = threadIdx.x; v < nE + nO; v += blockDim.x) {
+        if (v < nE) cp_async16(sb + v * V, srcE + v * V);
+        else cp_async16(dO + (v - nE) * V, srcO + (v - nE) * V);
+    }
+    cp_async_commit();
+}
+
+// The contraction of a folded tile against the staged table.  A task is 4
+// output modes (a' block ab: the sums' modes for ab < NEp/4, the differences'
+// after) x 4 tile lines (block lb); xfirst(even) and xstep(even) give the
+// first folded operand of the task's lines and the stride between fold indices;
+// X(xp, mm) reads the 4 operands of fold index mm; put(abp, even, acc) stores.
+// Per output the terms are summed in the order m' = 0, 1, ... (the middle node
+// of odd N last among the sums).
+template <class T, int C, class XFirst, class Load, class Put>
+__device__ __forceinline__ void tile_contract(const T *tab, T *sb, const FoldDims &fd, XFirst xfirst,
+                                              int xstep_e, int xstep_o, Load load, Put put) {
+    constexpr int KC = kc_rows<T>();
+    const int nabE = fd.NEp / 4, nabO = fd.NOp / 4;
+    const int ntask = (nabE + nabO) * (C / 4);
+    const int nchunk = (fd.rowsE + KC - 1) / KC;
+    const size_t half = (size_t)KC * (fd.NEp + fd.NOp);
+    for (int t0 = 0; t0 < ntask; t0 += blockDim.x) {  // rounds: block-uniform
+        if (t0 > 0) {
+            __syncthreads();  // the previous round has read both buffers
+            stage_rows(sb, tab, fd, 0);
+        }
+        const int t = t0 + (int)threadIdx.x;
+        const bool live = t < ntask;
+        const int lb = t % (C / 4), ab = t / (C / 4);
+        const bool even = ab < nabE;
+        const int abp = even ? ab : ab - nabE;
+        const int soff = even ? 4 * abp : KC * fd.NEp + 4 * abp;
+        const int lds = even ? fd.NEp : fd.NOp;
+        const int mend = even ? fd.rowsE : fd.H;
+        const int xstep = even ? xstep_e : xstep_o;
+        const T *xp = xfirst(even, lb);
+        T acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
+        for (int c = 0; c < nchunk; ++c) {
+            cp_async_wait_all();
+            __syncthreads();  // chunk c has landed; every thread is done with chunk c - 1
+            if (c + 1 < nchunk) stage_rows(sb + ((c + 1) & 1) * half, tab, fd, (c + 1) * KC);
+            const int m0 = c * KC;
+            const int mc = live ? min(KC, mend - m0) : 0;
+            const T *sp = sb + (c & 1) * half + soff;
+            for (int mm = 0; mm < mc; ++mm, xp += xstep, sp += lds) {
+                const V4<T> sv = ld4(sp);
+                T xv[4];
+                load(xp, xv);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fma(sv.v[i], xv[j], acc[i][j]);
+            }
+        }
+        if (live) put(abp, even, lb, acc);
+    }
+}
+
 // Column-major tile: x[m][c] (m = transform index, C columns, row stride C).
-// out[a][c] = sum_m S[a][m] x[m][c].  x is folded in place.
+// out[a][c] = sum_m S[a][m] x[m][c].  x is folded in place; sb: two table
+// chunks of shared memory.
 template <class T, int C = 32>
-__device__ void tile_transform_cm(T *x, T *out, int N, const T *tab) {
+__device__ void tile_transform_cm(T *x, T *out, int N, const T *tab, T *sb) {
     FoldDims fd(N);
+    stage_rows(sb, tab, fd, 0);
     for (int idx = threadIdx.x; idx < fd.H * C; idx += blockDim.x) {
         int mp = idx / C, c = idx % C;
         T a = x[mp * C + c], b = x[(N - 1 - mp) * C + c];
         x[mp * C + c] = a + b;
         x[(N - 1 - mp) * C + c] = a - b;
     }
-    __syncthreads();
-    const int nabE = fd.NEp / 4, nabO = fd.NOp / 4;
-    const int ntask = (nabE + nabO) * (C / 4);
-    for (int t = threadIdx.x; t < ntask; t += blockDim.x) {
-        int cb = t % (C / 4), ab = t / (C / 4);
-        bool even = ab < nabE;  // output a0 even <=> a odd <=> folded sums
-        int abp = even ? ab : ab - nabE;
-        const T *S = even ? tab + 4 * abp : tab + fd.offO() + 4 * abp;
-        int ld = even ? fd.NEp : fd.NOp;
-        T acc[4][4];
+    // (the first barrier of the contraction orders the fold before its reads)
+    tile_contract<T, C>(
+        tab, sb, fd, [&](bool even, int cb) -> const T * { return x + (even ? 0 : (N - 1) * C) + 4 * cb; },
+        C, -C,
+        [](const T *xp, T *xv) {
+            const V4<T> v = ld4(xp);
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) xv[j] = v.v[j];
+        },
+        [&](int abp, bool even, int cb, T (&acc)[4][4]) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
-        // rows mp (sums) or N-1-mp (differences) of the folded tile, walked by pointer
-        const T *xp = x + (even ? 0 : (N - 1) * C) + 4 * cb;
-        const int xstep = even ? C : -C;
-        const T *sp = S;
-        for (int mp = 0; mp < fd.H; ++mp, xp += xstep, sp += ld) {
-            V4<T> xv = ld4(xp);
-            V4<T> sv = ldg4(sp);
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(sv.v[i], xv.v[j], acc[i][j]);
-        }
-        if (even && (N & 1)) {
-            V4<T> xv = ld4(x + fd.H * C + 4 * cb);
-            V4<T> sv = ldg4(S + (size_t)fd.H * ld);
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(sv.v[i], xv.v[j], acc[i][j]);
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            int a0 = even ? 2 * (4 * abp + i) : 2 * (4 * abp + i) + 1;
-            if (a0 < N) st4(out + a0 * C + 4 * cb, acc[i]);
-        }
-    }
+            for (int i = 0; i < 4; ++i) {
+                int a0 = even ? 2 * (4 * abp + i) : 2 * (4 * abp + i) + 1;
+                if (a0 < N) st4(out + a0 * C + 4 * cb, acc[i]);
+            }
+        });
     __syncthreads();
 }
 
 // Row-major tile: x[r][m] (C rows, row stride ld = N + 1).
-// out[r][a] = sum_m S[a][m] x[r][m].  x is folded in place.
+// out[r][a] = sum_m S[a][m] x[r][m].  x is folded in place; sb as above.
 template <class T, int C = 32>
-__device__ void tile_transform_rm(T *x, T *out, int N, int ld, const T *tab) {
+__device__ void tile_transform_rm(T *x, T *out, int N, int ld, const T *tab, T *sb) {
     FoldDims fd(N);
+    stage_rows(sb, tab, fd, 0);
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int r = threadIdx.x >> 5; r < C; r += nw) {  // a warp per row: no division by N
         T *xr = x + r * ld;
@@ -195,53 +270,24 @@ __device__ void tile_transform_rm(T *x, T *out, int N, int ld, const T *tab) {
             xr[N - 1 - mp] = a - b;
         }
     }
-    __syncthreads();
-    const int nabE = fd.NEp / 4, nabO = fd.NOp / 4;
-    const int ntask = (nabE + nabO) * (C / 4);
-    for (int t = threadIdx.x; t < ntask; t += blockDim.x) {
-        int rb = t % (C / 4), ab = t / (C / 4);
-        bool even = ab < nabE;
-        int abp = even ? ab : ab - nabE;
-        const T *S = even ? tab + 4 * abp : tab + fd.offO() + 4 * abp;
-        int lds = even ? fd.NEp : fd.NOp;
-        T acc[4][4];  // [row][a]
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
-        const T *xr = x + 4 * rb * ld;
-        // columns mp (sums) or N-1-mp (differences) of the folded tile, walked by pointer
-        const T *xp = xr + (even ? 0 : N - 1);
-        const int xstep = even ? 1 : -1;
-        const T *sp = S;
-        for (int mp = 0; mp < fd.H; ++mp, xp += xstep, sp += lds) {
-            V4<T> sv = ldg4(sp);
-            T xv[4];
+    tile_contract<T, C>(
+        tab, sb, fd, [&](bool even, int rb) -> const T * { return x + 4 * rb * ld + (even ? 0 : N - 1); },
+        1, -1,
+        [ld](const T *xp, T *xv) {
 #pragma unroll
             for (int i = 0; i < 4; ++i) xv[i] = xp[i * ld];
+        },
+        [&](int abp, bool even, int rb, T (&acc)[4][4]) {
+            // acc[j][i]: mode 4 abp + j of row 4 rb + i
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) {
+                int a0 = even ? 2 * (4 * abp + j) : 2 * (4 * abp + j) + 1;
+                if (a0 < N) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(xv[i], sv.v[j], acc[i][j]);
-        }
-        if (even && (N & 1)) {
-            V4<T> sv = ldg4(S + (size_t)fd.H * lds);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                T xm = xr[i * ld + fd.H];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(xm, sv.v[j], acc[i][j]);
+                    for (int i = 0; i < 4; ++i) out[(4 * rb + i) * ld + a0] = acc[j][i];
+                }
             }
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            int a0 = even ? 2 * (4 * abp + j) : 2 * (4 * abp + j) + 1;
-            if (a0 < N) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) out[(4 * rb + i) * ld + a0] = acc[i][j];
-            }
-        }
-    }
+        });
     __syncthreads();
 }
 
@@ -273,23 +319,34 @@ __device__ __forceinline__ void body_k_fwd(const PassArgs &a, const ApRhs<T> &r,
     if (rhs_skipped(r, a.cond_flag)) return;
     T *x = reinterpret_cast<T *>(smem_raw);
     T *out = x + C * ld;
+    T *sb = out + C * ld;
     const int64_t nrows = (int64_t)N * N;
     const int64_t R0 = (int64_t)tile * C;
     const double sig = a.sigma_dev ? *a.sigma_dev : a.sigma;
     const T fs = (T)(a.fscale_dev ? *a.fscale_dev : a.fscale);
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int rr = threadIdx.x >> 5; rr < C; rr += nw) {  // a warp per row: no division by N
-        const int64_t R = R0 + rr;
-        const bool live = R < nrows && r.f;
-        for (int k = lane; k < N; k += 32) {
-            T v = (T)0;
-            if (live) {
-                const int64_t p = R * N + k;
-                v = fs * r.f[p];
-                if (a.mask_f && !(a.labels[p] & DPM_LBL_MPLUS)) v = (T)0;
-            }
-            x[rr * ld + k] = v;
+    if (r.f) {
+        // f copied in, then scaled and masked by the thread that copied it
+        for (int rr = threadIdx.x >> 5; rr < C; rr += nw) {  // a warp per row: no division by N
+            const int64_t R = R0 + rr;
+            for (int k = lane; k < N; k += 32)
+                cp_async_elem(x + rr * ld + k, R < nrows ? r.f + R * N + k : r.f, R < nrows);
         }
+        cp_async_commit();
+        cp_async_wait_all();
+        for (int rr = threadIdx.x >> 5; rr < C; rr += nw) {
+            const int64_t R = R0 + rr;
+            if (R >= nrows) break;
+            for (int k = lane; k < N; k += 32) {
+                const int64_t p = R * N + k;
+                T v = fs * x[rr * ld + k];
+                if (a.mask_f && !(a.labels[p] & DPM_LBL_MPLUS)) v = (T)0;
+                x[rr * ld + k] = v;
+            }
+        }
+    } else {
+        for (int rr = threadIdx.x >> 5; rr < C; rr += nw)
+            for (int k = lane; k < N; k += 32) x[rr * ld + k] = (T)0;
     }
     __syncthreads();
     if (r.dens) {
@@ -312,7 +369,7 @@ __device__ __forceinline__ void body_k_fwd(const PassArgs &a, const ApRhs<T> &r,
         }
         __syncthreads();
     }
-    tile_transform_rm<T, C>(x, out, N, ld, tab);
+    tile_transform_rm<T, C>(x, out, N, ld, tab, sb);
     T *w = cube;
     for (int rr = threadIdx.x >> 5; rr < C; rr += nw) {
         const int64_t R = R0 + rr;
@@ -331,13 +388,16 @@ __device__ __forceinline__ void body_j(const PassArgs &a, const ApRhs<T> &r, T *
     const int i = tile / nkc, kc = (tile % nkc) * C;
     T *x = reinterpret_cast<T *>(smem_raw);
     T *out = x + N * C;
+    T *sb = out + N * C;
     T *w = cube + (size_t)i * N * N;
     for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
         int j = idx / C, c = idx % C;
-        x[j * C + c] = (kc + c < N) ? w[(size_t)j * N + kc + c] : (T)0;
+        cp_async_elem(x + j * C + c, kc + c < N ? w + (size_t)j * N + kc + c : w, kc + c < N);
     }
+    cp_async_commit();
+    cp_async_wait_all();
     __syncthreads();
-    tile_transform_cm<T, C>(x, out, N, tab);
+    tile_transform_cm<T, C>(x, out, N, tab, sb);
     for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
         int j = idx / C, c = idx % C;
         if (kc + c < N) w[(size_t)j * N + kc + c] = out[j * C + c];
@@ -355,6 +415,7 @@ __device__ __forceinline__ void body_i(const PassArgs &a, const ApRhs<T> &r, T *
     T *x = reinterpret_cast<T *>(smem_raw);
     T *out = x + N * C;
     T *wt = out + N * C;  // N weights (4/h^2) sin^2(pi (n+1)/(2(N+1)))
+    T *sb = wt + ((N + 3) & ~3);
     T *w = cube + (size_t)j * N;
     const size_t si = (size_t)N * N;
     const double sig = a.sigma_dev ? *a.sigma_dev : a.sigma;
@@ -363,10 +424,12 @@ __device__ __forceinline__ void body_i(const PassArgs &a, const ApRhs<T> &r, T *
     for (int n = threadIdx.x; n < N; n += blockDim.x) wt[n] = w4 * s2[n];
     for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
         int i = idx / C, c = idx % C;
-        x[i * C + c] = (kc + c < N) ? w[(size_t)i * si + kc + c] : (T)0;
+        cp_async_elem(x + i * C + c, kc + c < N ? w + (size_t)i * si + kc + c : w, kc + c < N);
     }
+    cp_async_commit();
+    cp_async_wait_all();
     __syncthreads();
-    tile_transform_cm<T, C>(x, out, N, tab);
+    tile_transform_cm<T, C>(x, out, N, tab, sb);
     const double sc = 2.0 / (N + 1);
     const T scale = (T)(sc * sc * sc);
     const T sgT = (T)sig;
@@ -377,7 +440,7 @@ __device__ __forceinline__ void body_i(const PassArgs &a, const ApRhs<T> &r, T *
         x[ai * C + c] = out[ai * C + c] * (scale / lam);
     }
     __syncthreads();
-    tile_transform_cm<T, C>(x, out, N, tab);
+    tile_transform_cm<T, C>(x, out, N, tab, sb);
     for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
         int i = idx / C, c = idx % C;
         if (kc + c < N) w[(size_t)i * si + kc + c] = out[i * C + c];
@@ -394,16 +457,19 @@ __device__ __forceinline__ void body_k_inv(const PassArgs &a, const ApRhs<T> &r,
     if (rhs_skipped(r, a.cond_flag)) return;
     T *x = reinterpret_cast<T *>(smem_raw);
     T *out = x + C * ld;
+    T *sb = out + C * ld;
     const int64_t nrows = (int64_t)N * N;
     const int64_t R0 = (int64_t)tile * C;
     const T *w = cube;
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int rr = threadIdx.x >> 5; rr < C; rr += nw) {  // a warp per row: no division by N
         const int64_t R = R0 + rr;
-        for (int k = lane; k < N; k += 32) x[rr * ld + k] = R < nrows ? w[R * N + k] : (T)0;
+        for (int k = lane; k < N; k += 32) cp_async_elem(x + rr * ld + k, R < nrows ? w + R * N + k : w, R < nrows);
     }
+    cp_async_commit();
+    cp_async_wait_all();
     __syncthreads();
-    tile_transform_rm<T, C>(x, out, N, ld, tab);
+    tile_transform_rm<T, C>(x, out, N, ld, tab, sb);
     if (r.out_dense) {
         for (int rr = threadIdx.x >> 5; rr < C; rr += nw) {
             const int64_t R = R0 + rr;
@@ -719,8 +785,13 @@ int small_group_launch(const GroupItem<float> *items, int B, cudaStream_t s) {
     return DPM_OK;
 }
 
-template <class T, int C = 32> size_t smem_rows(int N) { return 2 * (size_t)C * (N + 1) * sizeof(T); }
-template <class T, int C = 32> size_t smem_cols(int N) { return (2 * (size_t)N * C + N) * sizeof(T); }
+// tile regions, then two table chunks (16-byte aligned)
+template <class T, int C = 32> size_t smem_rows(int N) {
+    return (2 * (size_t)C * (N + 1) + 2 * chunk_elems<T>(N)) * sizeof(T);
+}
+template <class T, int C = 32> size_t smem_cols(int N) {
+    return (2 * (size_t)N * C + ((N + 3) & ~3) + 2 * chunk_elems<T>(N)) * sizeof(T);
+}
 
 template <class T, int C = 32> int set_smem_limits(int) {
     static PerDeviceOnce once;
@@ -735,7 +806,8 @@ template <class T, int C = 32> int set_smem_limits(int) {
 }
 
 // Threads per CTA: one per task of the tile transform (4 output modes x 4 of the
-// C columns), at most 256, so that no thread idles through the transform.
+// C columns), at most 512, so that every task of a tile runs in one sweep over the
+// staged table.
 template <int C> int tile_threads(int N) {
     const FoldDims fd(N);
     const int tasks = (fd.NEp / 4 + fd.NOp / 4) * (C / 4);
