@@ -225,16 +225,18 @@ __device__ __forceinline__ void tile_contract(const T *tab, T *sb, const FoldDim
 
 // Column-major tile: x[m][c] (m = transform index, C columns, row stride C).
 // out[a][c] = sum_m S[a][m] x[m][c].  x is folded in place; sb: two table
-// chunks of shared memory.
+// chunks of shared memory.  blockDim.x is a multiple of C.
 template <class T, int C = 32>
 __device__ void tile_transform_cm(T *x, T *out, int N, const T *tab, T *sb) {
     FoldDims fd(N);
     stage_rows(sb, tab, fd, 0);
-    for (int idx = threadIdx.x; idx < fd.H * C; idx += blockDim.x) {
-        int mp = idx / C, c = idx % C;
-        T a = x[mp * C + c], b = x[(N - 1 - mp) * C + c];
-        x[mp * C + c] = a + b;
-        x[(N - 1 - mp) * C + c] = a - b;
+    {
+        const int c = threadIdx.x % C, R = blockDim.x / C;  // a fixed column per thread
+        for (int mp = threadIdx.x / C; mp < fd.H; mp += R) {
+            T a = x[mp * C + c], b = x[(N - 1 - mp) * C + c];
+            x[mp * C + c] = a + b;
+            x[(N - 1 - mp) * C + c] = a - b;
+        }
     }
     // (the first barrier of the contraction orders the fold before its reads)
     tile_contract<T, C>(
@@ -390,18 +392,16 @@ __device__ __forceinline__ void body_j(const PassArgs &a, const ApRhs<T> &r, T *
     T *out = x + N * C;
     T *sb = out + N * C;
     T *w = cube + (size_t)i * N * N;
-    for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
-        int j = idx / C, c = idx % C;
-        cp_async_elem(x + j * C + c, kc + c < N ? w + (size_t)j * N + kc + c : w, kc + c < N);
-    }
+    const int c = threadIdx.x % C, R = blockDim.x / C;  // a fixed column per thread
+    const bool cv = kc + c < N;
+    for (int j = threadIdx.x / C; j < N; j += R)
+        cp_async_elem(x + j * C + c, cv ? w + (size_t)j * N + kc + c : w, cv);
     cp_async_commit();
     cp_async_wait_all();
     __syncthreads();
     tile_transform_cm<T, C>(x, out, N, tab, sb);
-    for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
-        int j = idx / C, c = idx % C;
-        if (kc + c < N) w[(size_t)j * N + kc + c] = out[j * C + c];
-    }
+    if (cv)
+        for (int j = threadIdx.x / C; j < N; j += R) w[(size_t)j * N + kc + c] = out[j * C + c];
 }
 
 // Pass 3: along i, forward, scale/lambda, inverse; tiles [i][kc..kc+C) at fixed j.
@@ -422,10 +422,10 @@ __device__ __forceinline__ void body_i(const PassArgs &a, const ApRhs<T> &r, T *
     const T w4 = (T)(4.0 / (a.h * a.h));
     const T *s2 = tab + FoldDims(N).offW();
     for (int n = threadIdx.x; n < N; n += blockDim.x) wt[n] = w4 * s2[n];
-    for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
-        int i = idx / C, c = idx % C;
-        cp_async_elem(x + i * C + c, kc + c < N ? w + (size_t)i * si + kc + c : w, kc + c < N);
-    }
+    const int c = threadIdx.x % C, R = blockDim.x / C;  // a fixed column per thread
+    const bool cv = kc + c < N;
+    for (int i = threadIdx.x / C; i < N; i += R)
+        cp_async_elem(x + i * C + c, cv ? w + (size_t)i * si + kc + c : w, cv);
     cp_async_commit();
     cp_async_wait_all();
     __syncthreads();
@@ -433,18 +433,18 @@ __device__ __forceinline__ void body_i(const PassArgs &a, const ApRhs<T> &r, T *
     const double sc = 2.0 / (N + 1);
     const T scale = (T)(sc * sc * sc);
     const T sgT = (T)sig;
-    for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
-        int ai = idx / C, c = idx % C;
-        int kk = kc + c < N ? kc + c : N - 1;
-        T lam = sgT + (wt[ai] + wt[j] + wt[kk]);
-        x[ai * C + c] = out[ai * C + c] * (scale / lam);
+    {
+        const int kk = cv ? kc + c : N - 1;
+        const T wj = wt[j], wk = wt[kk];
+        for (int ai = threadIdx.x / C; ai < N; ai += R) {
+            T lam = sgT + (wt[ai] + wj + wk);
+            x[ai * C + c] = out[ai * C + c] * (scale / lam);
+        }
     }
     __syncthreads();
     tile_transform_cm<T, C>(x, out, N, tab, sb);
-    for (int idx = threadIdx.x; idx < N * C; idx += blockDim.x) {
-        int i = idx / C, c = idx % C;
-        if (kc + c < N) w[(size_t)i * si + kc + c] = out[i * C + c];
-    }
+    if (cv)
+        for (int i = threadIdx.x / C; i < N; i += R) w[(size_t)i * si + kc + c] = out[i * C + c];
 }
 
 // Pass 5: inverse along k, then the dense output (masked to N^+) and/or the
@@ -811,7 +811,8 @@ template <class T, int C = 32> int set_smem_limits(int) {
 template <int C> int tile_threads(int N) {
     const FoldDims fd(N);
     const int tasks = (fd.NEp / 4 + fd.NOp / 4) * (C / 4);
-    return std::min(kThreads, std::max(32, (tasks + 31) / 32 * 32));
+    const int q = C > 32 ? C : 32;  // a multiple of C: the column loops keep one column per thread
+    return std::min(kThreads, std::max(q, (tasks + q - 1) / q * q));
 }
 
 template <class T, int C> bool tile_fits(int N) {
@@ -990,6 +991,10 @@ int ap_solve_simt(const ApParams &p, const ApRhs<T> *rhs_dev, T *work, cudaStrea
 }
 
 namespace {
+// Tile width of a grouped launch, set by its largest grid: 32 while two
+// 32-wide CTAs fit on an SM, else 16 (FP64 above N ~ 150).
+template <class T> int group_width(int maxN) { return 2 * smem_cols<T, 32>(maxN) <= 227 * 1024 ? 32 : 16; }
+
 template <class T, int C> int set_group_smem_limits() {
     static PerDeviceOnce once;
     return once.run([] {
@@ -1096,9 +1101,7 @@ int ap_solve_simt_group(const std::vector<ApParams> &probs, const std::vector<Ap
         if constexpr (sizeof(T) == 4) {
             if (any_small) DPM_RET(small_group_launch(d, (int)(b1 - b0), s));
         }
-        // the tile width of the largest grid: 16 when its 32-wide tiles would leave
-        // one CTA per SM (N > 128), else 32 (the autotuner's choices at N = 256 / 128)
-        if (any_large && maxN > 128) DPM_RET((simt_group_passes<T, 16>(d, (int)(b1 - b0), maxN, s)));
+        if (any_large && group_width<T>(maxN) == 16) DPM_RET((simt_group_passes<T, 16>(d, (int)(b1 - b0), maxN, s)));
         else if (any_large) DPM_RET((simt_group_passes<T, 32>(d, (int)(b1 - b0), maxN, s)));
         if (b1 < B) DPM_CUDA(cudaStreamSynchronize(s));  // the items / workspace are reused
         b0 = b1;
@@ -1158,8 +1161,7 @@ int ap_group_launch(const void *items_dev, int B, int maxN, int minN, cudaStream
         if (small_item<T>(minN)) DPM_RET(small_group_launch(d, B, s));
     }
     if (small_item<T>(maxN)) return DPM_OK;  // every grid solved in one pass
-    // the tile width rule of ap_solve_simt_group
-    if (maxN > 128) return simt_group_passes<T, 16>(d, B, maxN, s);
+    if (group_width<T>(maxN) == 16) return simt_group_passes<T, 16>(d, B, maxN, s);
     return simt_group_passes<T, 32>(d, B, maxN, s);
 }
 
