@@ -132,8 +132,9 @@ def test_solve_mean_error_against_oracle(ctx, n, prec, kind):
     compensation never saw (a bias of 2e-6 per solve drifts a 10,000-step time
     loop by 2 %).  The tensor cores round their FP32 accumulator toward zero; the
     tensor-core solvers issue the small cross terms first and scale the
-    spectrum by the mean loss measured on dense random and Gaussian data.  The
-    FFT-style solver rounds to nearest.  Bound: 1e-6, the per-transform FP32
+    spectrum by the expected loss of that rounding, derived from the number of
+    accumulation steps per transform (half an ulp per step, six transforms), not
+    fitted to data.  The FFT-style solver rounds to nearest.  Bound: 1e-6, the per-transform FP32
     error of the dominant mode times the six transforms of a solve."""
     h, sigma = 1.0 / (n - 3), 1.25e5
     q = _unseen_spectra(n)[kind]
