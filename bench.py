@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--precision", choices=["fp32", "tc32", "fp64"], default="tc32")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="bound on the oracle's CPU-baseline sample")
+    ap.add_argument("--cpu-fft-seconds", type=float, default=2.0,
+                    help="bound on the scipy DST-I context sample (0 skips it)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=10000,
                     help="requests in the serving leg (0 skips it)")
@@ -173,6 +175,36 @@ def oracle_sample(w, seconds, log=None):
         if (el >= seconds and n >= 2) or n >= Psi.shape[1]:
             break
     return n, el
+
+
+def fft_ap_solve(q, h, sigma, workers=1):
+    """(sigma - Lap_h) u = q with zero Dirichlet data through scipy.fft's DST-I
+    (the fast-Poisson route of the paper's FFTW-based solver): the CPU context
+    figure reported beside the oracle.  Not used by the library."""
+    import scipy.fft as sf
+    N = q.shape[0]
+    wt = (4.0 / (h * h)) * np.sin(np.pi * np.arange(1, N + 1) / (2.0 * (N + 1))) ** 2
+    lam = sigma + wt[:, None, None] + wt[None, :, None] + wt[None, None, :]
+    return sf.idstn(sf.dstn(q, type=1, workers=workers) / lam, type=1, workers=workers)
+
+
+def cpu_fft_sample(w, seconds, cores):
+    """Dense AP solves of the workload's grid by fft_ap_solve on `cores` host
+    threads for about `seconds` (FP64, uniform q in [-1, 1], seed 0)."""
+    N = w.N
+    h, sigma = (w.hi - w.lo) / (N + 1), 1.0 / w.dt
+    q = np.random.default_rng(0).uniform(-1.0, 1.0, (N, N, N))
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        fft_ap_solve(q, h, sigma, cores)
+        n += 1
+        el = time.perf_counter() - t0
+        if (el >= seconds and n >= 2) or n >= 500:
+            break
+    return {"value": n * N ** 3 / el, "unit": UNIT, "cores": cores,
+            "kind": "scipy.fft DST-I (FP64), context beside the oracle",
+            "sample": f"{n} dense AP solves at N={N}, {el:.1f} s"}
 
 
 def blas_threads():
@@ -350,6 +382,9 @@ def run_ours(args):
         n, el = oracle_sample(w, args.cpu_seconds)
         cpu = {"value": n * N ** 3 / el, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
                "sample": f"{n} BEP-column AP solves at N={N} (numpy FP64 dense DST-I), {el:.1f} s"}
+    cpu_fft = None
+    if rank == 0 and args.cpu_fft_seconds > 0:
+        cpu_fft = cpu_fft_sample(w, args.cpu_fft_seconds, os.cpu_count() or 1)
 
     if rank == 0:
         line = {
@@ -364,7 +399,7 @@ def run_ours(args):
                        "l2": f"inputs larger than L2 ({spp * N ** 3 * 4 / 1e9:.2f} GB batch per step)"},
             "clocks": clk, "gpu_launches": int(launches), "roofline": roof, "roofline_passes": roof_all,
             "kernels": prof,
-            "e2e": e2e, "cpu_baseline": cpu, "aux_solve": aux, "sd_dd_test_a": sd_dd, "layers_uneven": layers, "serving": serving,
+            "e2e": e2e, "cpu_baseline": cpu, "cpu_fft_context": cpu_fft, "aux_solve": aux, "sd_dd_test_a": sd_dd, "layers_uneven": layers, "serving": serving,
             "graph": not args.no_graph, "kernel_profile_steps": nprof,
             "sanity": {"finite": bool(finite), "mass": st.mass},
         }
