@@ -102,9 +102,11 @@ struct KC { float hi, lo; };
 constexpr KC kSqrtHalf{0.70710677f, 1.21016175e-08f};
 __device__ __forceinline__ float kmul(float x, KC c) { return fmaf(x, c.hi, x * c.lo); }
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex sums and differences as packed two-lane FP32 adds (each lane rounded
+// as a scalar add; a - b is a + (-b) exactly).
 __device__ __forceinline__ float2 cneg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __fadd2_rn(a, cneg(b)); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
