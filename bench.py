@@ -245,7 +245,8 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": w.name, "N": w.N, "K": w.K, "ncol": w.ncol,
-                   "step": f"bounded sample of the step's AP solves (~{sample_s:.0f} s of oracle work)"},
+                   "step": f"bounded sample of the step's AP solves (up to {sample_s:.0f} s of oracle work "
+                           f"or the step's {w.ncol} BEP columns, whichever ends first)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{tot_n} BEP-column AP solves at N={w.N} over {len(per)} steps"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
