@@ -17,7 +17,9 @@
 // folding x_m +- x_{N+1-m} first halves the multiply-adds (odd a read the
 // sums, even a the differences; for odd N the middle node joins odd a only).
 // N+1 = 33, 129, 257 have no radix-2 structure beyond this fold, so the rest
-// of each transform is a dense product with the folded sine table.
+// of each transform is a dense product with the folded sine table.  Tiles
+// arrive by asynchronous element copies; the table reaches the product through
+// shared memory in double-buffered chunks of rows (see stage_rows).
 //
 // FP32 grids of N <= 32 take one pass instead (small_body): the whole cube in
 // shared memory, the six transforms line by line, 8 N^3 bytes of HBM traffic.
