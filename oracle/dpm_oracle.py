@@ -30,9 +30,10 @@ Readings where the paper is silent or ambiguous:
 
 Parity pins: every function here is checked by tests/test_oracle_*.py against
 closed forms, brute force, library routines or the paper's theorems.  The
-ellipsoid foot point is pinned by its optimality conditions, brute force,
-the sphere limit and the closed forms on the principal axes ("parity
-unpinned" for general points beyond bisection convergence).
+ellipsoid foot point is pinned by its optimality conditions (a stationary
+point of the distance), the brute-force global minimum over a fine
+parametric sample, the sphere limit and the closed forms on the principal
+axes.
 """
 from __future__ import annotations
 
