@@ -165,6 +165,8 @@ int dpm_classify(dpm_ctx *ctx, const dpm_geom *geom, int N, double lo, double hi
  * N = 128 or 256 (DPM_EUNSUPPORTED otherwise) and a 16-byte aligned q (its planes
  * are staged by bulk copies; DPM_EINVAL otherwise).  DPM_PREC_FFT32 requires
  * N = 256 (N + 1 = 257 prime: Rader's algorithm) and a 16-byte aligned q.
+ * DPM_PREC_FP32 solves grids of N <= 32 in one pass with each cube in shared
+ * memory (no workspace), larger ones in five passes over the workspace.
  * Scratch: the context's workspace, grown on demand.
  */
 int dpm_aux_solve_batched(dpm_ctx *ctx, int N, double h, double sigma, int B,
@@ -205,9 +207,10 @@ int dpm_aux_solve_batched_noalloc(int N, double h, double sigma, int B, const fl
  * else 32.  Every output is summed in the same order for each width, so the
  * choice changes the run time only, never the result.  Environment: DPM_SIMT_TILE
  * = 16|32|64 forces a width; DPM_AUTOTUNE=0 keeps 32.  The no-alloc solve
- * always uses 32.
+ * always uses 32.  FP32 grids of N <= 32 take the one-pass solve and have no
+ * tile width.
  * dpm_simt_tile writes to *tile the width tuned on the current device for
- * (N, precision, B), or 0 if none has been tuned yet.
+ * (N, precision, B), or 0 if none has been tuned (or none applies).
  */
 int dpm_simt_tile(int N, int precision, int B, int *tile);
 
