@@ -1,6 +1,8 @@
 """The SIMT solver's tile width (16, 32 or 64 grid lines per CTA) changes its
 run time only: every width gives bit-identical auxiliary solves (ragged N, so
-the last tile is partial for each width) and bit-identical BEP matrices (the
+the last tile is partial for each width; at N = 150 the 64-wide tiles have more
+4 x 4 tasks than a CTA has threads, two rounds over the staged sine table) and
+bit-identical BEP matrices (the
 shell density sums and the gamma_in traces read per-tile row ranges), and the
 autotuner picks one of the widths whose shared memory fits."""
 import os
@@ -42,7 +44,7 @@ def solve(ctx, q, h, sigma, prec):
 
 
 @pytest.mark.parametrize("prec", [abi.DPM_PREC_FP32, abi.DPM_PREC_FP64])
-@pytest.mark.parametrize("N", [37, 70])
+@pytest.mark.parametrize("N", [37, 70, 150])
 def test_every_tile_width_gives_the_same_bits(ctx, prec, N):
     B, h, sigma = 3, 1.0 / (N + 1), 1001.0
     q = random_rhs(1000 + N, B, N, np.float64)
